@@ -1,0 +1,178 @@
+"""CPU oracle for the Graph-VQE energy / gradient path (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
+``bench.py`` may import this package.  The product library never loads it.
+
+``gvqe_oracle.c`` is the plain complex128 gate-by-gate simulator (Section IV-B,
+Eq. 4, 6, 7, 13); ``dense.py`` is an independent dense-matrix model for tiny
+registers and ``closed_form.py`` holds closed forms used as pins.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gvqe_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+
+def build(force: bool = False, src: str = _SRC, out: str = _LIB_PATH) -> str:
+    """Compile the C oracle with gcc + OpenMP into a shared library; returns its path."""
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Build (if needed) and load the oracle library."""
+    global _lib
+    with _lock:
+        if path is None and _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build() if path is None else path)
+        d = ctypes.c_double
+        i = ctypes.c_int
+        p = ctypes.c_void_p
+        lib.oracle_state.argtypes = [i, i, p, p]
+        lib.oracle_apply_hamiltonian.argtypes = [i, i, p, p, p, p]
+        lib.oracle_energy.argtypes = [i, i, p, i, p, p, p, p]
+        lib.oracle_energy_grad.argtypes = [i, i, p, i, p, p, p, p]
+        lib.oracle_param_shift_grad.argtypes = [i, i, p, i, p, p, p, p]
+        lib.oracle_partial_work.argtypes = [i, i, i, p, p, p, p]
+        lib.oracle_max_threads.restype = i
+        lib.oracle_set_threads.argtypes = [i]
+        for f in ("oracle_state", "oracle_apply_hamiltonian", "oracle_energy",
+                  "oracle_energy_grad", "oracle_param_shift_grad", "oracle_partial_work"):
+            getattr(lib, f).restype = i
+        del d
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+class _HamArgs:
+    """Flat (strings, coeffs) buffers kept alive for one call."""
+
+    def __init__(self, n: int, strings, coeffs):
+        strings = list(strings)
+        for s in strings:
+            if len(s) != n:
+                raise ValueError(f"Pauli string {s!r} has length {len(s)} != {n}")
+        self.m = len(strings)
+        self.buf = np.frombuffer("".join(strings).encode("ascii") or b"\0", dtype=np.uint8).copy()
+        self.c = np.ascontiguousarray(coeffs, dtype=np.float64).reshape(-1).copy()
+        if self.c.size == 0:
+            self.c = np.zeros(1)
+
+
+def _ham(ham_or_strings, coeffs=None):
+    if coeffs is None:
+        return ham_or_strings.n_qubits, ham_or_strings.strings, ham_or_strings.coeffs
+    return None, ham_or_strings, coeffs
+
+
+def set_threads(n: int) -> None:
+    load().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(load().oracle_max_threads())
+
+
+def state(n: int, reps: int, theta, lib: Optional[ctypes.CDLL] = None) -> np.ndarray:
+    """|psi(theta)> as complex128 [2^n] (Section IV-B ansatz, RY+CX)."""
+    lib = lib or load()
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+    assert th.size == n * (reps + 1)
+    out = np.empty(2 << n, dtype=np.float64)
+    _check(lib.oracle_state(n, reps, _ptr(th), _ptr(out)), "state")
+    return out.view(np.complex128)
+
+
+def apply_hamiltonian(n: int, strings, coeffs, psi, lib: Optional[ctypes.CDLL] = None) -> np.ndarray:
+    """H psi, term by term (Eq. 6)."""
+    lib = lib or load()
+    h = _HamArgs(n, strings, coeffs)
+    v = np.ascontiguousarray(psi, dtype=np.complex128).reshape(-1)
+    assert v.size == 1 << n
+    out = np.empty(1 << n, dtype=np.complex128)
+    _check(lib.oracle_apply_hamiltonian(n, h.m, _ptr(h.buf), _ptr(h.c), _ptr(v), _ptr(out)),
+           "apply_hamiltonian")
+    return out
+
+
+def energy(n: int, reps: int, theta, strings, coeffs, lib: Optional[ctypes.CDLL] = None,
+           with_imag: bool = False):
+    """E = <psi|H|psi> (Eq. 4)."""
+    lib = lib or load()
+    h = _HamArgs(n, strings, coeffs)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+    e = np.zeros(1)
+    ei = np.zeros(1)
+    _check(lib.oracle_energy(n, reps, _ptr(th), h.m, _ptr(h.buf), _ptr(h.c), _ptr(e), _ptr(ei)),
+           "energy")
+    return (float(e[0]), float(ei[0])) if with_imag else float(e[0])
+
+
+def energy_grad(n: int, reps: int, theta, strings, coeffs,
+                lib: Optional[ctypes.CDLL] = None) -> Tuple[float, np.ndarray]:
+    """(E, dE/dtheta) by the gate-by-gate adjoint sweep."""
+    lib = lib or load()
+    h = _HamArgs(n, strings, coeffs)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+    e = np.zeros(1)
+    g = np.zeros(th.size)
+    _check(lib.oracle_energy_grad(n, reps, _ptr(th), h.m, _ptr(h.buf), _ptr(h.c), _ptr(e), _ptr(g)),
+           "energy_grad")
+    return float(e[0]), g
+
+
+def param_shift_grad(n: int, reps: int, theta, strings, coeffs, mask=None,
+                     lib: Optional[ctypes.CDLL] = None) -> np.ndarray:
+    """dE/dtheta by the parameter-shift rule (Eq. 13); inactive entries are 0."""
+    lib = lib or load()
+    h = _HamArgs(n, strings, coeffs)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+    g = np.zeros(th.size)
+    if mask is None:
+        mp = ctypes.c_void_p(0)
+    else:
+        mk = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        mp = _ptr(mk)
+    _check(lib.oracle_param_shift_grad(n, reps, _ptr(th), h.m, _ptr(h.buf), _ptr(h.c), mp, _ptr(g)),
+           "param_shift_grad")
+    return g
+
+
+def partial_work(n: int, n_gates: int, strings, coeffs, theta,
+                 lib: Optional[ctypes.CDLL] = None) -> float:
+    """Run a bounded slice of one evaluation (n_gates RY gates + len(strings) terms)."""
+    lib = lib or load()
+    h = _HamArgs(n, strings, coeffs)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+    out = np.zeros(1)
+    _check(lib.oracle_partial_work(n, n_gates, h.m, _ptr(h.buf), _ptr(h.c), _ptr(th), _ptr(out)),
+           "partial_work")
+    return float(out[0])

@@ -1,0 +1,99 @@
+"""Dense-matrix brute force for tiny registers (n <= 10), used only to pin the oracle.
+
+Every operator is an explicit 2^n x 2^n matrix assembled from Kronecker
+products of 2x2 matrices, with no bit manipulation at all, so it shares no
+method with the gate-by-gate oracle:
+
+* RY(theta) from Eq. 7, CNOT as |0><0|_c (x) I + |1><1|_c (x) X_t;
+* Pauli strings as the Kronecker product of their letters (Eq. 6);
+* U(theta) = product of every gate matrix in circuit order (Section IV-B);
+* E = psi^dagger H psi (Eq. 4); the gradient by the parameter-shift rule
+  (Eq. 13) on this dense model.
+
+Qubit q is bit q of the basis index, so the Kronecker product runs from
+qubit n-1 (leftmost factor) down to qubit 0.
+"""
+from __future__ import annotations
+
+import math
+from functools import reduce
+from typing import Dict, Sequence
+
+import numpy as np
+
+I2 = np.eye(2, dtype=np.complex128)
+X2 = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+Y2 = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+Z2 = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+P0 = np.array([[1, 0], [0, 0]], dtype=np.complex128)
+P1 = np.array([[0, 0], [0, 1]], dtype=np.complex128)
+LETTER: Dict[str, np.ndarray] = {"I": I2, "X": X2, "Y": Y2, "Z": Z2}
+
+MAX_QUBITS = 10
+
+
+def ry(theta: float) -> np.ndarray:
+    """Eq. 7."""
+    c, s = math.cos(theta / 2), math.sin(theta / 2)
+    return np.array([[c, -s], [s, c]], dtype=np.complex128)
+
+
+def embed(ops: Dict[int, np.ndarray], n: int) -> np.ndarray:
+    """Kronecker product with ops[q] on qubit q and identity elsewhere."""
+    factors = [ops.get(q, I2) for q in reversed(range(n))]
+    return reduce(np.kron, factors)
+
+
+def cnot(ctl: int, tgt: int, n: int) -> np.ndarray:
+    return embed({ctl: P0}, n) + embed({ctl: P1, tgt: X2}, n)
+
+
+def pauli(string: str) -> np.ndarray:
+    n = len(string)
+    return embed({q: LETTER[string[q]] for q in range(n)}, n)
+
+
+def hamiltonian(strings: Sequence[str], coeffs) -> np.ndarray:
+    n = len(strings[0])
+    h = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+    for s, c in zip(strings, coeffs):
+        h += float(c) * pauli(s)
+    return h
+
+
+def circuit(n: int, reps: int, theta) -> np.ndarray:
+    """U(theta): RY layer, then reps x [CX(0,1), ..., CX(n-2,n-1); RY layer]."""
+    assert n <= MAX_QUBITS
+    th = np.asarray(theta, dtype=np.float64).reshape(-1)
+    u = np.eye(1 << n, dtype=np.complex128)
+    for r in range(reps + 1):
+        if r > 0:
+            for q in range(n - 1):
+                u = cnot(q, q + 1, n) @ u
+        for q in range(n):
+            u = embed({q: ry(th[r * n + q])}, n) @ u
+    return u
+
+
+def state(n: int, reps: int, theta) -> np.ndarray:
+    return circuit(n, reps, theta)[:, 0]
+
+
+def energy(n: int, reps: int, theta, strings, coeffs) -> float:
+    psi = state(n, reps, theta)
+    return float(np.real(np.vdot(psi, hamiltonian(strings, coeffs) @ psi)))
+
+
+def param_shift_grad(n: int, reps: int, theta, strings, coeffs) -> np.ndarray:
+    th = np.asarray(theta, dtype=np.float64).reshape(-1)
+    h = hamiltonian(strings, coeffs)
+    g = np.zeros_like(th)
+    for p in range(th.size):
+        vals = []
+        for sh in (+math.pi / 2, -math.pi / 2):
+            t = th.copy()
+            t[p] += sh
+            psi = circuit(n, reps, t)[:, 0]
+            vals.append(float(np.real(np.vdot(psi, h @ psi))))
+        g[p] = 0.5 * (vals[0] - vals[1])
+    return g
