@@ -1,0 +1,177 @@
+/*
+ * gvqe.h -- C ABI of the GB300 (sm_103a) engine for the Graph-VQE hot path:
+ * state-vector simulation of the RY+CX hardware-efficient ansatz, the
+ * expectation of a Pauli-sum Hamiltonian, and its gradient (arxiv 2607.02749).
+ *
+ * Conventions used by every call:
+ *   - Qubit q is bit q of the basis index x (little-endian).
+ *   - A Pauli string has one character per qubit over {I, X, Y, Z};
+ *     character i acts on qubit i.
+ *   - The ansatz (Section IV-B, Eq. 7): an initial RY layer on every qubit,
+ *     then `reps` repetitions of [entangler, RY layer].  The linear entangler
+ *     is CX(0,1), CX(1,2), ..., CX(n-2,n-1) in that order.
+ *   - Parameters are flattened layer-major: theta[p] with p = r*n + q is the
+ *     RY angle of layer r (0..reps) on qubit q; P = n*(reps+1) (Eq. 8 for the
+ *     RY-only gate set).
+ *   - RY(t) = [[cos t/2, -sin t/2], [sin t/2, cos t/2]] (Eq. 7).
+ *
+ * Ownership: *_create copies every input; the caller owns the parameter,
+ * mask, energy and gradient buffers it passes.  Handles own their device
+ * workspaces, which grow on first use and are freed by gvqe_destroy.
+ *
+ * Errors: every call returns GVQE_OK (0) or a negative code below and sets a
+ * thread-local message readable with gvqe_last_error().  Argument checks are
+ * synchronous; GPU work is enqueued on `stream` (a cudaStream_t passed as a
+ * void*, NULL = the legacy default stream) and is complete when the stream is.
+ * A handle must not be used by two calls that overlap in time.
+ */
+#ifndef GVQE_H
+#define GVQE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GVQE_OK 0
+#define GVQE_EINVAL (-1)       /* bad argument: NULL, size out of range, bad letter, n mismatch */
+#define GVQE_ENOMEM (-2)       /* the device workspace does not fit in free device memory */
+#define GVQE_ECUDA (-3)        /* a CUDA runtime call failed (message has the CUDA error) */
+#define GVQE_ETIMEOUT (-4)     /* a bounded device-side wait ran out (persistent batch kernel) */
+#define GVQE_EUNSUPPORTED (-5) /* a valid request this build does not implement */
+
+/* flags for gvqe_energy / gvqe_energy_grad / gvqe_batch_create */
+#define GVQE_FP32 0x0             /* FP32 amplitudes, FP64 table and FP64 reductions (default) */
+#define GVQE_FP64 0x1             /* FP64 amplitudes */
+#define GVQE_GRAD_ADJOINT 0x0     /* reverse-mode (adjoint) gradient (default) */
+#define GVQE_GRAD_PARAM_SHIFT 0x2 /* parameter-shift gradient, Eq. 13 (2 P_active + 1 energies) */
+
+/* entanglers for gvqe_ansatz_create (Section IV-B) */
+#define GVQE_ENT_LINEAR 0
+
+/* options for gvqe_ansatz_set_option */
+#define GVQE_OPT_TILE_BITS 1 /* log2 amplitudes per on-chip tile, 10..14 (FP32) / 10..13 (FP64); 0 = auto */
+
+#define GVQE_MAX_QUBITS 30
+
+typedef struct gvqe_hamiltonian_s *gvqe_hamiltonian;
+typedef struct gvqe_ansatz_s *gvqe_ansatz;
+typedef struct gvqe_batch_s *gvqe_batch;
+
+/*
+ * gvqe_hamiltonian_create -- H = sum_k c_k P_k with real c_k (Eq. 6).
+ *   n_qubits: 1..30.
+ *   n_terms:  >= 0.
+ *   pauli:    host, n_terms * n_qubits characters, string k at offset
+ *             k*n_qubits, no separators; letters I, X, Y, Z (upper case).
+ *   coeffs:   host, n_terms doubles.
+ *   out:      receives the handle.
+ * Duplicate strings are summed.  Z-only strings (and the all-I string) are
+ * folded into a diagonal table E(x) = sum_k c_k (-1)^popcount(x & z_k) built
+ * on the device in FP64; strings with X/Y letters are grouped by X-mask.
+ * Strings with an odd number of Y letters contribute exactly zero to the
+ * energy and gradient of every state this ansatz prepares (its amplitudes are
+ * real), so they are counted and dropped.
+ * Errors: GVQE_EINVAL (NULL, n out of range, bad letter), GVQE_ENOMEM, GVQE_ECUDA.
+ */
+int gvqe_hamiltonian_create(int n_qubits, int n_terms, const char *pauli, const double *coeffs,
+                            gvqe_hamiltonian *out);
+
+/*
+ * gvqe_ansatz_create -- the parameterised circuit U(theta) of Section IV-B
+ * (RY layers with an entangler between them; Eq. 7, Eq. 8 with RY only).
+ *   n_qubits: 1..30.  reps: 0..64 (the number D of [entangler, RY] repetitions).
+ *   entangler: GVQE_ENT_LINEAR (others return GVQE_EUNSUPPORTED).
+ * Errors: GVQE_EINVAL, GVQE_EUNSUPPORTED.
+ */
+int gvqe_ansatz_create(int n_qubits, int reps, int entangler, gvqe_ansatz *out);
+
+/* gvqe_ansatz_set_option -- tuning override (see GVQE_OPT_*); value 0 restores the default. */
+int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value);
+
+/*
+ * gvqe_energy -- E_b = <psi(theta_b)|H|psi(theta_b)> for b in [0, batch) (Eq. 4).
+ *   params:   device, batch x P doubles, row b = theta_b (layer-major, see above).
+ *   batch:    >= 1.
+ *   energies: device, batch doubles (written).
+ *   flags:    GVQE_FP32 or GVQE_FP64.
+ *   stream:   cudaStream_t as void*.
+ * The energy reduction always accumulates in FP64.
+ * Errors: GVQE_EINVAL (NULL, batch < 1, n of ansatz != n of H), GVQE_ENOMEM, GVQE_ECUDA.
+ */
+int gvqe_energy(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int batch,
+                double *energies, int flags, void *stream);
+
+/*
+ * gvqe_energy_grad -- energies and dE/dtheta for b in [0, batch).
+ *   params:   device, batch x P doubles.
+ *   mask:     device, batch x P bytes, nonzero = active (Eq. 11: parameters
+ *             outside the active block are held fixed), or NULL = all active.
+ *             The mask changes the gradient only: inactive entries are written
+ *             as 0.0, energies are unaffected.
+ *   energies: device, batch doubles.  grad: device, batch x P doubles.
+ *   flags:    GVQE_FP32 | GVQE_FP64, optionally | GVQE_GRAD_PARAM_SHIFT
+ *             (Eq. 13; this path copies the mask to the host and synchronises
+ *             `stream`).
+ * Gradient reductions accumulate in FP64 (FP32 mode sums at most one warp's
+ * products in FP32 first).
+ * Errors: as gvqe_energy.
+ */
+int gvqe_energy_grad(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask,
+                     int batch, double *energies, double *grad, int flags, void *stream);
+
+/*
+ * gvqe_batch_create -- a fixed set of independent restricted-update problems
+ * (Section IV-D, Eq. 11): instance i pairs ansatze[i] with hams[i] (equal n)
+ * and evaluates one parameter vector with its own active mask per run.  All
+ * instances run in one persistent kernel launch, captured in a CUDA graph.
+ *   n_inst: >= 1.  ansatze, hams: host arrays of n_inst handles (borrowed: they
+ *   must outlive the batch).  flags: GVQE_FP32 or GVQE_FP64.
+ * Errors: GVQE_EINVAL, GVQE_ENOMEM, GVQE_ECUDA, GVQE_EUNSUPPORTED.
+ */
+int gvqe_batch_create(int n_inst, const gvqe_ansatz *ansatze, const gvqe_hamiltonian *hams,
+                      int flags, gvqe_batch *out);
+
+/*
+ * gvqe_batch_run -- evaluate every instance once.
+ *   params:   host array of n_inst device pointers, params[i] -> P_i doubles.
+ *   masks:    host array of n_inst device pointers (P_i bytes each, entries may
+ *             be NULL = all active), or NULL = all active everywhere.
+ *   energies: device, n_inst doubles.
+ *   grads:    host array of n_inst device pointers (P_i doubles each), or NULL
+ *             for energies only.
+ * Errors: GVQE_EINVAL, GVQE_ECUDA, GVQE_ETIMEOUT (a bounded device-side wait
+ * ran out; detected when this call synchronises `stream` at its end).
+ */
+int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *const *masks,
+                   double *energies, double *const *grads, void *stream);
+
+/* gvqe_destroy -- free any handle above; NULL is accepted.  Synchronises the
+ * device work the handle enqueued before freeing its memory. */
+int gvqe_destroy(void *handle);
+
+/* gvqe_last_error -- message of the last failing call on this thread ("" if none). */
+const char *gvqe_last_error(void);
+
+/*
+ * Host-only introspection (no GPU needed).
+ * gvqe_plan_describe -- write the tile-pass plan used for (n_qubits, reps,
+ * flags, tile_bits; 0 = auto) as text into buf (NUL-terminated, truncated to
+ * buflen).  Returns the number of passes per rotation layer, or a negative code.
+ */
+int gvqe_plan_describe(int n_qubits, int reps, int flags, int tile_bits, char *buf, int buflen);
+
+/* gvqe_hamiltonian_stats -- counts after parsing: diagonal strings, X-mask
+ * groups, grouped strings, dropped odd-Y strings (any pointer may be NULL). */
+int gvqe_hamiltonian_stats(gvqe_hamiltonian h, int *n_diag, int *n_groups, int *n_grouped,
+                           int *n_dropped);
+
+/* gvqe_version -- library version as 10000*major + 100*minor + patch. */
+int gvqe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GVQE_H */

@@ -1,0 +1,155 @@
+"""GB300 (sm_103a) engine for the Graph-VQE hot path (arxiv 2607.02749).
+
+State-vector simulation of the RY+CX hardware-efficient ansatz (Section IV-B),
+the expectation of a Pauli-sum Hamiltonian (Eq. 4, Eq. 6) and its adjoint or
+parameter-shift (Eq. 13) gradient with active-parameter masks (Eq. 11), all in
+hand-written CUDA behind the C ABI of include/gvqe.h.  This package is the
+thin Python layer over that ABI plus one torch.autograd.Function.
+"""
+from __future__ import annotations
+
+from typing import Optional, Sequence
+
+from . import _lib
+from ._lib import (GVQE_ENT_LINEAR, GVQE_FP32, GVQE_FP64, GVQE_GRAD_ADJOINT, GVQE_GRAD_PARAM_SHIFT,
+                   GVQE_OPT_TILE_BITS, GvqeError, gvqe_ansatz_create, gvqe_ansatz_set_option, gvqe_batch_create,
+                   gvqe_batch_run, gvqe_destroy, gvqe_energy, gvqe_energy_grad, gvqe_hamiltonian_create,
+                   gvqe_hamiltonian_stats, gvqe_last_error, gvqe_plan_describe, gvqe_version)
+
+__all__ = [
+    "Hamiltonian", "Ansatz", "Batch", "GvqeEnergy", "energy", "energy_grad", "GvqeError",
+    "GVQE_FP32", "GVQE_FP64", "GVQE_GRAD_ADJOINT", "GVQE_GRAD_PARAM_SHIFT", "GVQE_ENT_LINEAR",
+    "gvqe_hamiltonian_create", "gvqe_ansatz_create", "gvqe_ansatz_set_option", "gvqe_energy",
+    "gvqe_energy_grad", "gvqe_batch_create", "gvqe_batch_run", "gvqe_destroy", "gvqe_last_error",
+    "gvqe_plan_describe", "gvqe_hamiltonian_stats", "gvqe_version",
+]
+
+
+class _Handle:
+    handle: Optional[int] = None
+
+    def close(self) -> None:
+        if self.handle:
+            gvqe_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hamiltonian(_Handle):
+    """H = sum_k c_k P_k (Eq. 6); strings have one letter per qubit (char i = qubit i)."""
+
+    def __init__(self, n_qubits: int, strings: Sequence[str], coeffs):
+        self.n_qubits = n_qubits
+        self.handle = gvqe_hamiltonian_create(n_qubits, strings, coeffs)
+
+    @classmethod
+    def from_workload(cls, ham) -> "Hamiltonian":
+        return cls(ham.n_qubits, ham.strings, ham.coeffs)
+
+    def stats(self) -> dict:
+        return gvqe_hamiltonian_stats(self.handle)
+
+
+class Ansatz(_Handle):
+    """RY layer + reps x [linear CX chain, RY layer] (Section IV-B); P = n (reps + 1)."""
+
+    def __init__(self, n_qubits: int, reps: int, entangler: int = GVQE_ENT_LINEAR, tile_bits: int = 0):
+        self.n_qubits = n_qubits
+        self.reps = reps
+        self.n_params = n_qubits * (reps + 1)
+        self.handle = gvqe_ansatz_create(n_qubits, reps, entangler)
+        if tile_bits:
+            gvqe_ansatz_set_option(self.handle, GVQE_OPT_TILE_BITS, tile_bits)
+
+    def set_tile_bits(self, bits: int) -> None:
+        gvqe_ansatz_set_option(self.handle, GVQE_OPT_TILE_BITS, bits)
+
+
+def _flags(fp64: bool, param_shift: bool = False) -> int:
+    return (GVQE_FP64 if fp64 else GVQE_FP32) | (GVQE_GRAD_PARAM_SHIFT if param_shift else 0)
+
+
+def energy(ansatz: Ansatz, ham: Hamiltonian, theta, fp64: bool = False, stream=None):
+    """E[b] for theta[b] (CUDA float64 [B, P]); returns a CUDA float64 tensor [B]."""
+    import torch
+
+    th = theta.reshape(-1, ansatz.n_params).contiguous()
+    e = torch.empty(th.shape[0], dtype=torch.float64, device=th.device)
+    gvqe_energy(ansatz.handle, ham.handle, th, e, _flags(fp64), stream)
+    return e
+
+
+def energy_grad(ansatz: Ansatz, ham: Hamiltonian, theta, mask=None, fp64: bool = False,
+                param_shift: bool = False, stream=None):
+    """(E[B], dE/dtheta [B, P]); mask uint8 [B, P] (nonzero = active) or None."""
+    import torch
+
+    th = theta.reshape(-1, ansatz.n_params).contiguous()
+    e = torch.empty(th.shape[0], dtype=torch.float64, device=th.device)
+    g = torch.empty_like(th)
+    m = None if mask is None else mask.reshape(th.shape).to(torch.uint8).contiguous()
+    gvqe_energy_grad(ansatz.handle, ham.handle, th, m, e, g, _flags(fp64, param_shift), stream)
+    return e, g
+
+
+class Batch(_Handle):
+    """Many independent (ansatz, Hamiltonian) restricted-update problems run together."""
+
+    def __init__(self, ansatze: Sequence[Ansatz], hams: Sequence[Hamiltonian], fp64: bool = False):
+        self._keep = (list(ansatze), list(hams))
+        self.handle = gvqe_batch_create([a.handle for a in ansatze], [h.handle for h in hams], _flags(fp64))
+
+    def run(self, params: Sequence, masks: Optional[Sequence] = None, grads: Optional[Sequence] = None,
+            energies=None, stream=None):
+        import torch
+
+        if energies is None:
+            energies = torch.empty(len(params), dtype=torch.float64, device=params[0].device)
+        gvqe_batch_run(self.handle, params, masks, energies, grads, stream)
+        return energies
+
+
+def _make_function():
+    import torch
+
+    class GvqeEnergy(torch.autograd.Function):
+        """E = <psi(theta)|H|psi(theta)> per row of theta, differentiable through the adjoint gradient.
+
+        forward(theta [B, P] float64 CUDA, ansatz, ham, mask=None, fp64=False) -> E [B];
+        backward returns grad_E[:, None] * dE/dtheta (inactive mask entries give 0).
+        """
+
+        @staticmethod
+        def forward(ctx, theta, ansatz, ham, mask=None, fp64=False):
+            if theta.requires_grad:
+                e, g = energy_grad(ansatz, ham, theta.detach(), mask=mask, fp64=fp64)
+                ctx.save_for_backward(g)
+            else:
+                e = energy(ansatz, ham, theta.detach(), fp64=fp64)
+                ctx.save_for_backward(None)
+            return e
+
+        @staticmethod
+        def backward(ctx, grad_e):
+            (g,) = ctx.saved_tensors
+            gt = None if g is None else grad_e.reshape(-1, 1).to(g.dtype) * g
+            return gt, None, None, None, None
+
+    return GvqeEnergy
+
+
+class _LazyFunction:
+    _fn = None
+
+    def __getattr__(self, name):
+        if _LazyFunction._fn is None:
+            _LazyFunction._fn = _make_function()
+        return getattr(_LazyFunction._fn, name)
+
+
+GvqeEnergy = _LazyFunction()

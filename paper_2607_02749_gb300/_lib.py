@@ -1,0 +1,210 @@
+"""ctypes binding of libgvqe.so: the C ABI of include/gvqe.h, one Python function per C call.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are passed as torch tensors (their data pointers);
+the stream defaults to torch's current CUDA stream.  If the library is missing
+and cannot be compiled, loading raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgvqe.so")
+
+GVQE_OK = 0
+GVQE_EINVAL = -1
+GVQE_ENOMEM = -2
+GVQE_ECUDA = -3
+GVQE_ETIMEOUT = -4
+GVQE_EUNSUPPORTED = -5
+GVQE_FP32 = 0x0
+GVQE_FP64 = 0x1
+GVQE_GRAD_ADJOINT = 0x0
+GVQE_GRAD_PARAM_SHIFT = 0x2
+GVQE_ENT_LINEAR = 0
+GVQE_OPT_TILE_BITS = 1
+GVQE_MAX_QUBITS = 30
+
+_ERRNAMES = {
+    GVQE_EINVAL: "GVQE_EINVAL",
+    GVQE_ENOMEM: "GVQE_ENOMEM",
+    GVQE_ECUDA: "GVQE_ECUDA",
+    GVQE_ETIMEOUT: "GVQE_ETIMEOUT",
+    GVQE_EUNSUPPORTED: "GVQE_EUNSUPPORTED",
+}
+
+
+class GvqeError(RuntimeError):
+    """A gvqe call returned a negative code; `.code` holds it."""
+
+    def __init__(self, code: int, func: str, msg: str):
+        super().__init__(f"{func} -> {_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "gvqe_hamiltonian_create": [_I, _I, ctypes.c_char_p, _VP, ctypes.POINTER(_VP)],
+    "gvqe_ansatz_create": [_I, _I, _I, ctypes.POINTER(_VP)],
+    "gvqe_ansatz_set_option": [_VP, _I, _I],
+    "gvqe_energy": [_VP, _VP, _VP, _I, _VP, _I, _VP],
+    "gvqe_energy_grad": [_VP, _VP, _VP, _VP, _I, _VP, _VP, _I, _VP],
+    "gvqe_batch_create": [_I, _VP, _VP, _I, ctypes.POINTER(_VP)],
+    "gvqe_batch_run": [_VP, _VP, _VP, _VP, _VP, _VP],
+    "gvqe_destroy": [_VP],
+    "gvqe_plan_describe": [_I, _I, _I, _I, ctypes.c_char_p, _I],
+    "gvqe_hamiltonian_stats": [_VP, _VP, _VP, _VP, _VP],
+    "gvqe_version": [],
+}
+
+
+def load(path: Optional[str] = None, build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libgvqe.so (compiling it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if path is None and build_if_missing:
+            from . import build as _build
+
+            p = _build.build()
+        if not os.path.exists(p):
+            raise RuntimeError(f"gvqe CUDA library not found at {p}; run paper_2607_02749_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        for name, argtypes in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = argtypes
+            f.restype = _I
+        lib.gvqe_last_error.argtypes = []
+        lib.gvqe_last_error.restype = ctypes.c_char_p
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(rc: int, func: str) -> int:
+    if rc < 0:
+        msg = load().gvqe_last_error().decode(errors="replace")
+        raise GvqeError(rc, func, msg)
+    return rc
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+
+        if not torch.cuda.is_available():
+            return None
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _require_cuda(*tensors) -> None:
+    for t in tensors:
+        if t is not None and not isinstance(t, int) and not t.is_cuda:
+            raise ValueError("gvqe calls take CUDA tensors (device pointers)")
+
+
+# ------------------------------------------------------------- C calls --
+
+def gvqe_version() -> int:
+    return load().gvqe_version()
+
+
+def gvqe_last_error() -> str:
+    return load().gvqe_last_error().decode(errors="replace")
+
+
+def gvqe_hamiltonian_create(n_qubits: int, strings: Sequence[str], coeffs) -> int:
+    """H = sum_k c_k P_k (Eq. 6).  Returns the handle as an int."""
+    import numpy as np
+
+    strings = list(strings)
+    c = np.ascontiguousarray(coeffs, dtype=np.float64).reshape(-1)
+    if len(strings) != c.size:
+        raise ValueError("len(strings) != len(coeffs)")
+    flat = "".join(strings).encode("ascii")
+    out = _VP()
+    _check(load().gvqe_hamiltonian_create(n_qubits, len(strings), flat, c.ctypes.data if c.size else None,
+                                          ctypes.byref(out)), "gvqe_hamiltonian_create")
+    return out.value
+
+
+def gvqe_ansatz_create(n_qubits: int, reps: int, entangler: int = GVQE_ENT_LINEAR) -> int:
+    out = _VP()
+    _check(load().gvqe_ansatz_create(n_qubits, reps, entangler, ctypes.byref(out)), "gvqe_ansatz_create")
+    return out.value
+
+
+def gvqe_ansatz_set_option(ansatz: int, option: int, value: int) -> None:
+    _check(load().gvqe_ansatz_set_option(ansatz, option, value), "gvqe_ansatz_set_option")
+
+
+def gvqe_energy(ansatz: int, ham: int, params, energies, flags: int = GVQE_FP32, stream=None) -> None:
+    """energies[b] = <psi(params[b])|H|psi(params[b])> (Eq. 4); CUDA float64 tensors."""
+    _require_cuda(params, energies)
+    batch = params.shape[0] if params.dim() == 2 else 1
+    _check(load().gvqe_energy(ansatz, ham, _ptr(params), batch, _ptr(energies), flags, _stream(stream)),
+           "gvqe_energy")
+
+
+def gvqe_energy_grad(ansatz: int, ham: int, params, mask, energies, grad, flags: int = GVQE_FP32,
+                     stream=None) -> None:
+    """Energies and dE/dtheta; mask (uint8, same shape as params) or None = all active."""
+    _require_cuda(params, mask, energies, grad)
+    batch = params.shape[0] if params.dim() == 2 else 1
+    _check(load().gvqe_energy_grad(ansatz, ham, _ptr(params), _ptr(mask), batch, _ptr(energies), _ptr(grad),
+                                   flags, _stream(stream)), "gvqe_energy_grad")
+
+
+def gvqe_batch_create(ansatze: Sequence[int], hams: Sequence[int], flags: int = GVQE_FP32) -> int:
+    n = len(ansatze)
+    a = (_VP * n)(*ansatze)
+    h = (_VP * n)(*hams)
+    out = _VP()
+    _check(load().gvqe_batch_create(n, a, h, flags, ctypes.byref(out)), "gvqe_batch_create")
+    return out.value
+
+
+def gvqe_batch_run(batch: int, params: Sequence, masks: Optional[Sequence], energies, grads: Optional[Sequence],
+                   stream=None) -> None:
+    n = len(params)
+    pa = (_VP * n)(*[_ptr(p) for p in params])
+    ma = (_VP * n)(*[_ptr(m) for m in masks]) if masks is not None else None
+    ga = (_VP * n)(*[_ptr(g) for g in grads]) if grads is not None else None
+    _check(load().gvqe_batch_run(batch, pa, ma, _ptr(energies), ga, _stream(stream)), "gvqe_batch_run")
+
+
+def gvqe_destroy(handle: Optional[int]) -> None:
+    _check(load().gvqe_destroy(handle), "gvqe_destroy")
+
+
+def gvqe_plan_describe(n_qubits: int, reps: int, flags: int = GVQE_FP32, tile_bits: int = 0) -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().gvqe_plan_describe(n_qubits, reps, flags, tile_bits, buf, len(buf)), "gvqe_plan_describe")
+    return buf.value.decode()
+
+
+def gvqe_hamiltonian_stats(ham: int) -> dict:
+    vals = [ctypes.c_int() for _ in range(4)]
+    _check(load().gvqe_hamiltonian_stats(ham, *[ctypes.byref(v) for v in vals]), "gvqe_hamiltonian_stats")
+    return dict(zip(("diag", "groups", "grouped", "dropped_odd_y"), (v.value for v in vals)))

@@ -1,0 +1,864 @@
+// gvqe_api.cu -- C ABI, Hamiltonian parsing, pass planner, workspaces and
+// launch sequences of the Graph-VQE energy / gradient engine.
+//
+// The paths implemented here:
+//   energy      forward passes of every RY layer (Section IV-B) with the
+//               energy of Eq. 4 fused into the last pass (diagonal H) or a
+//               separate lambda = H psi pass (X/Y strings, Eq. 6).
+//   adjoint     forward passes keep every pass output; the backward walks the
+//               passes in reverse, forming dE/dtheta = Im<lambda|Y_q|psi> and
+//               applying RY(-theta) to lambda only (psi comes from the stored
+//               outputs), then the layer-0 gradients against the analytic
+//               product state.
+//   param shift Eq. 13: 2 P_active + 1 energies of shifted parameter sets.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "gvqe.h"
+#include "gvqe_engine.cuh"
+#include "gvqe_internal.h"
+
+namespace gvqe {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define GV_CUDA(expr)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) return fail(GVQE_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define GV_TRY(expr)             \
+  do {                           \
+    int rc_ = (expr);            \
+    if (rc_ != GVQE_OK) return rc_; \
+  } while (0)
+
+// ------------------------------------------------------------ device memory --
+int DevBuf::reserve(size_t need) {
+  if (need <= bytes) return GVQE_OK;
+  release();
+  size_t freeb = 0, total = 0;
+  GV_CUDA(cudaMemGetInfo(&freeb, &total));
+  if (need > freeb)
+    return fail(GVQE_ENOMEM, "device workspace of %.3f GiB does not fit in %.3f GiB free", need / 1073741824.0,
+                freeb / 1073741824.0);
+  cudaError_t e = cudaMalloc(&ptr, need);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    cudaGetLastError();
+    return fail(GVQE_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+  }
+  bytes = need;
+  return GVQE_OK;
+}
+
+void DevBuf::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+// ---------------------------------------------------------------- planner --
+int auto_tile_bits(int prec) { return max_tile_bits(prec); }
+
+std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits) {
+  std::vector<LayerPass> out;
+  const int tbmax = tile_bits > 0 ? tile_bits : auto_tile_bits(prec);
+  if (n <= tbmax) {
+    out.push_back({n, n, n, (uint32_t)((1ull << n) - 1)});
+    return out;
+  }
+  const int tb = tbmax;
+  out.push_back({tb, tb, tb, (uint32_t)((1ull << tb) - 1)});
+  // Contiguous runs of 128 bytes (carry 5 FP32 / 4 FP64); drop to 64-byte runs
+  // when that saves a whole pass over the state.
+  const int min_carry = prec ? 4 : 5;
+  int gmax = tb - min_carry;
+  const int rest = n - tb;
+  int chunks = (rest + gmax - 1) / gmax;
+  if ((rest + gmax) / (gmax + 1) < chunks) {
+    gmax += 1;
+    chunks = (rest + gmax - 1) / gmax;
+  }
+  int a = tb;
+  for (int i = 0; i < chunks; ++i) {
+    const int g = rest / chunks + (i < rest % chunks ? 1 : 0);
+    const int c = tb - g;
+    out.push_back({c, a, tb, (uint32_t)(((1ull << g) - 1) << c)});
+    a += g;
+  }
+  return out;
+}
+
+static int qubit_of(const LayerPass &lp, int i) { return i < lp.c ? i : lp.a + i - lp.c; }
+
+static long long tiles_of(int n, int tb) { return 1LL << (n - tb); }
+
+// Build the ordered pass list for one (n, reps, precision) and what is requested.
+Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag) {
+  Plan pl;
+  pl.n = n;
+  pl.reps = reps;
+  pl.prec = prec;
+  pl.P = n * (reps + 1);
+  pl.lp = layer_passes(n, prec, tile_bits);
+  const int p = (int)pl.lp.size();
+  const int tbA = pl.lp[0].tb;
+  const long long S = 1LL << n;
+  pl.state_elems = S;
+  long long poff = 0;  // partial offset (doubles) inside one job's partial buffer
+  auto base_args = [&](int kind) {
+    PassArgs A;
+    memset(&A, 0, sizeof(A));
+    A.kind = kind;
+    A.n = n;
+    A.P = pl.P;
+    return A;
+  };
+  auto set_layout = [&](PassArgs &A, const LayerPass &lp) {
+    A.tb = lp.tb;
+    A.c = lp.c;
+    A.a = lp.a;
+    A.tiles = tiles_of(n, lp.tb);
+  };
+  // Buffer ids: stored pass outputs (gradient path) or a forward ping-pong
+  // pair (energy path), the lambda ping-pong pair, and psi_0 for X/Y terms at reps = 0.
+  int nb = 0;
+  const int first_state = nb;
+  if (want_grad) nb += reps * p;
+  int PP0 = -1, PP1 = -1;
+  if (!want_grad && reps > 0) {
+    PP0 = nb++;
+    PP1 = nb++;
+  }
+  int LAM0 = -1, LAM1 = -1;
+  if (want_grad || !diag) LAM0 = nb++;
+  if (want_grad) LAM1 = nb++;
+  int XYB = -1;
+  if (reps == 0 && !diag) XYB = nb++;
+  pl.n_bufs = nb;
+  pl.n_states = want_grad ? reps * p : 0;
+
+  auto add_E_region = [&](long long tiles) {
+    pl.dir.push_back({poff, (int)tiles, -1});
+    poff += tiles;
+  };
+
+  // ---------------- forward
+  int cur = -1;  // buffer holding the current state
+  int last_state = -1;
+  if (reps == 0) {
+    if (!diag) {
+      PassStep st;
+      st.A = base_args(K_FWD);
+      set_layout(st.A, pl.lp[0]);
+      st.A.load_mode = LD_L0;
+      st.A.store_mode = ST_PLAIN;
+      st.A.gate_mask = 0;
+      st.A.layer = 0;
+      st.out = XYB;
+      pl.steps.push_back(st);
+      last_state = XYB;
+    } else if (!want_grad) {
+      PassStep st;
+      st.A = base_args(K_FWD);
+      set_layout(st.A, pl.lp[0]);
+      st.A.load_mode = LD_L0;
+      st.A.store_mode = ST_NONE;
+      st.A.flags = F_ENERGY;
+      st.A.gate_mask = 0;
+      st.epart_region = poff;
+      add_E_region(st.A.tiles);
+      pl.steps.push_back(st);
+    }
+  }
+  for (int r = 1; r <= reps; ++r) {
+    for (int j = 0; j < p; ++j) {
+      const LayerPass &lp = pl.lp[j];
+      PassStep st;
+      st.A = base_args(K_FWD);
+      set_layout(st.A, lp);
+      st.A.gate_mask = lp.gmask;
+      st.A.layer = r;
+      if (j == 0) {
+        st.A.load_mode = (r == 1) ? LD_L0_GATHER : LD_GATHER;
+        st.A.flags |= F_PAIR_ORDER;
+      } else {
+        st.A.load_mode = LD_PLAIN;
+      }
+      st.in = (r == 1 && j == 0) ? -1 : cur;
+      int out;
+      if (want_grad) {
+        out = first_state + (r - 1) * p + j;
+      } else {
+        // the gathering first pass writes the other buffer; later passes run in place
+        out = (j == 0) ? (cur == PP0 ? PP1 : PP0) : cur;
+      }
+      st.A.store_mode = ST_PLAIN;
+      const bool last = (r == reps && j == p - 1);
+      if (last && diag && !want_grad) {
+        st.A.store_mode = ST_NONE;
+        st.A.flags |= F_ENERGY;
+        st.epart_region = poff;
+        add_E_region(st.A.tiles);
+      }
+      st.out = out;
+      pl.steps.push_back(st);
+      cur = out;
+    }
+  }
+  if (reps > 0) last_state = cur;
+
+  // X/Y energy (and lambda) for a non-diagonal H
+  int lam_cur = -1;
+  if (!diag) {
+    PassStep st;
+    st.A = base_args(K_LAMBDA_XY);
+    st.A.tb = tbA;
+    st.A.c = tbA;
+    st.A.a = tbA;
+    st.A.tiles = tiles_of(n, tbA);
+    st.A.load_mode = LD_PLAIN;
+    st.A.flags = F_ENERGY | (want_grad ? F_WRITE_LAMBDA : 0);
+    st.in = last_state;
+    st.out = LAM0;
+    st.epart_region = poff;
+    st.xy = true;
+    add_E_region(st.A.tiles);
+    pl.steps.push_back(st);
+    lam_cur = LAM0;
+  }
+
+  if (want_grad) {
+    // ---------------- backward
+    for (int r = reps; r >= 1; --r) {
+      for (int j = p - 1; j >= 0; --j) {
+        const LayerPass &lp = pl.lp[j];
+        PassStep st;
+        st.A = base_args(K_BWD);
+        set_layout(st.A, lp);
+        st.A.gate_mask = lp.gmask;
+        st.A.layer = r;
+        st.in = first_state + (r - 1) * p + j;
+        const bool first = (r == reps && j == p - 1);
+        if (first && diag) {
+          st.A.flags |= F_LAMBDA_INIT | F_ENERGY;
+          st.epart_region = poff;
+          add_E_region(st.A.tiles);
+          st.lam = -1;
+        } else {
+          st.lam = lam_cur;
+        }
+        const int out = (lam_cur == LAM0) ? LAM1 : LAM0;
+        st.out = out;
+        if (j == 0) {
+          st.A.store_mode = ST_SCATTER;
+          st.A.flags |= F_PAIR_ORDER;
+        } else {
+          st.A.store_mode = ST_PLAIN;
+        }
+        st.part_region = poff;
+        // partial rows for gate bits: [tile bit][tile]
+        for (int i = 0; i < lp.tb; ++i) {
+          if (!((lp.gmask >> i) & 1u)) continue;
+          const int q = qubit_of(lp, i);
+          pl.param_dir[r * n + q] = {poff + (long long)i * st.A.tiles, (int)st.A.tiles, r * n + q};
+        }
+        poff += (long long)lp.tb * st.A.tiles;
+        pl.steps.push_back(st);
+        lam_cur = out;
+      }
+    }
+    // ---------------- layer-0 gradients
+    PassStep st;
+    st.A = base_args(K_GRAD_L0);
+    st.A.tb = tbA;
+    st.A.c = tbA;
+    st.A.a = tbA;
+    st.A.tiles = tiles_of(n, tbA);
+    st.A.layer = 0;
+    if (reps == 0 && diag) {
+      st.A.flags = F_LAMBDA_INIT | F_ENERGY;
+      st.epart_region = poff;
+      add_E_region(st.A.tiles);
+      st.lam = -1;
+    } else {
+      st.lam = lam_cur;
+    }
+    st.part_region = poff;
+    for (int q = 0; q < n; ++q) pl.param_dir[q] = {poff + (long long)q * st.A.tiles, (int)st.A.tiles, q};
+    poff += (long long)n * st.A.tiles;
+    pl.steps.push_back(st);
+  }
+  pl.part_stride = poff;
+  for (auto &kv : pl.param_dir) pl.dir.push_back(kv.second);
+  return pl;
+}
+
+std::string describe_plan(const Plan &pl) {
+  std::string s;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "n=%d reps=%d prec=%s passes_per_layer=%zu steps=%zu partials_per_job=%lld\n", pl.n,
+           pl.reps, pl.prec ? "fp64" : "fp32", pl.lp.size(), pl.steps.size(), pl.part_stride);
+  s += buf;
+  for (size_t j = 0; j < pl.lp.size(); ++j) {
+    const LayerPass &lp = pl.lp[j];
+    int qlo = -1, qhi = -1;
+    for (int i = 0; i < lp.tb; ++i)
+      if ((lp.gmask >> i) & 1u) {
+        const int q = qubit_of(lp, i);
+        if (qlo < 0) qlo = q;
+        qhi = q;
+      }
+    snprintf(buf, sizeof(buf), "  layer pass %zu: tile_bits=%d carry=%d high_start=%d qubits=[%d,%d] tiles=%lld\n", j,
+             lp.tb, lp.c, lp.a, qlo, qhi, tiles_of(pl.n, lp.tb));
+    s += buf;
+  }
+  static const char *kinds[] = {"fwd", "bwd", "grad_l0", "lambda_xy", "wht"};
+  for (const PassStep &st : pl.steps) {
+    snprintf(buf, sizeof(buf), "  %-9s layer=%d tb=%d c=%d a=%d gates=0x%x load=%d store=%d flags=0x%x in=%d lam=%d out=%d\n",
+             kinds[st.A.kind], st.A.layer, st.A.tb, st.A.c, st.A.a, st.A.gate_mask, st.A.load_mode, st.A.store_mode,
+             st.A.flags, st.in, st.lam, st.out);
+    s += buf;
+  }
+  return s;
+}
+
+}  // namespace gvqe
+
+using namespace gvqe;
+
+// ------------------------------------------------------------ Hamiltonian --
+static int parse_hamiltonian(gvqe_hamiltonian_s *h, int n, int m, const char *pauli, const double *coeffs) {
+  std::map<uint32_t, double> diag;
+  std::map<uint32_t, std::map<uint32_t, double>> groups;
+  h->n_dropped = 0;
+  h->abs_sum = 0.0;
+  for (int k = 0; k < m; ++k) {
+    uint32_t mx = 0, mz = 0;
+    int ny = 0;
+    for (int q = 0; q < n; ++q) {
+      const char L = pauli[(size_t)k * n + q];
+      switch (L) {
+        case 'I': break;
+        case 'X': mx |= 1u << q; break;
+        case 'Y': mx |= 1u << q; mz |= 1u << q; ++ny; break;
+        case 'Z': mz |= 1u << q; break;
+        default:
+          return fail(GVQE_EINVAL, "term %d: letter '%c' at position %d is not one of I, X, Y, Z", k,
+                      (L >= 32 && L < 127) ? L : '?', q);
+      }
+    }
+    const double c = coeffs[k];
+    if (!std::isfinite(c)) return fail(GVQE_EINVAL, "term %d: coefficient is not finite", k);
+    h->abs_sum += std::fabs(c);
+    if (mx == 0) {
+      diag[mz] += c;
+    } else if (ny & 1) {
+      h->n_dropped += 1;  // odd #Y: purely imaginary on real states, contributes exactly zero
+    } else {
+      // P|u> = i^ny (-1)^popcount(u & z') |u ^ m>, i^ny = +1 (ny = 0 mod 4) or -1 (ny = 2 mod 4)
+      groups[mx][mz] += (ny % 4 == 0) ? c : -c;
+    }
+  }
+  h->dz.clear();
+  h->dc.clear();
+  for (auto &kv : diag) {
+    h->dz.push_back(kv.first);
+    h->dc.push_back(kv.second);
+  }
+  h->gm.clear();
+  h->gs.clear();
+  h->tz.clear();
+  h->tc.clear();
+  h->n_grouped = 0;
+  for (auto &g : groups) {
+    h->gm.push_back(g.first);
+    h->gs.push_back((int)h->tz.size());
+    for (auto &t : g.second) {
+      h->tz.push_back(t.first);
+      h->tc.push_back(t.second);
+      h->n_grouped += 1;
+    }
+  }
+  h->gs.push_back((int)h->tz.size());
+  return GVQE_OK;
+}
+
+// Build the FP64 diagonal table E(x) = sum_z chat[z] (-1)^popcount(x & z): scatter
+// the merged coefficients, then Walsh-Hadamard passes on the device.
+static int build_table64(gvqe_hamiltonian_s *h, cudaStream_t s) {
+  if (h->T64.ptr) return GVQE_OK;
+  const int n = h->n;
+  const size_t S = (size_t)1 << n;
+  GV_TRY(h->T64.reserve(S * 8));
+  GV_CUDA(cudaMemsetAsync(h->T64.ptr, 0, S * 8, s));
+  if (!h->dz.empty()) {
+    DevBuf tmp;
+    const size_t cnt = h->dz.size();
+    GV_TRY(tmp.reserve(cnt * (4 + 8)));
+    uint32_t *dz = (uint32_t *)tmp.ptr;
+    double *dc = (double *)((char *)tmp.ptr + ((cnt * 4 + 15) / 16) * 16);
+    if (((cnt * 4 + 15) / 16) * 16 + cnt * 8 > tmp.bytes) {
+      tmp.release();
+      GV_TRY(tmp.reserve(((cnt * 4 + 15) / 16) * 16 + cnt * 8));
+      dz = (uint32_t *)tmp.ptr;
+      dc = (double *)((char *)tmp.ptr + ((cnt * 4 + 15) / 16) * 16);
+    }
+    GV_CUDA(cudaMemcpyAsync(dz, h->dz.data(), cnt * 4, cudaMemcpyHostToDevice, s));
+    GV_CUDA(cudaMemcpyAsync(dc, h->dc.data(), cnt * 8, cudaMemcpyHostToDevice, s));
+    GV_CUDA(launch_scatter_coeffs(dz, dc, (int)cnt, (double *)h->T64.ptr, s));
+    std::vector<LayerPass> lps = layer_passes(n, 1, 0);
+    for (const LayerPass &lp : lps) {
+      PassArgs A;
+      memset(&A, 0, sizeof(A));
+      A.kind = K_WHT;
+      A.load_mode = LD_PLAIN;
+      A.store_mode = ST_PLAIN;
+      A.n = n;
+      A.tb = lp.tb;
+      A.c = lp.c;
+      A.a = lp.a;
+      A.tiles = 1LL << (n - lp.tb);
+      A.gate_mask = lp.gmask;
+      A.in = h->T64.ptr;
+      A.out = h->T64.ptr;
+      A.P = 1;
+      GV_CUDA(launch_pass(1, A, 1, 0, s));
+    }
+    GV_CUDA(cudaStreamSynchronize(s));
+    tmp.release();
+  } else {
+    GV_CUDA(cudaStreamSynchronize(s));
+  }
+  return GVQE_OK;
+}
+
+static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s) {
+  GV_TRY(build_table64(h, s));
+  if (!prec && !h->T32.ptr) {
+    const size_t S = (size_t)1 << h->n;
+    GV_TRY(h->T32.reserve(S * 4));
+    GV_CUDA(launch_convert_table((const double *)h->T64.ptr, (float *)h->T32.ptr, (long long)S, s));
+    GV_CUDA(cudaStreamSynchronize(s));
+  }
+  // X-mask group tables
+  if (!h->gm.empty() && !h->G.ptr) {
+    const size_t ng = h->gm.size(), nt = h->tz.size();
+    const size_t o_gm = 0, o_gs = ((ng * 4 + 15) / 16) * 16;
+    const size_t o_tz = o_gs + (((ng + 1) * 4 + 15) / 16) * 16;
+    const size_t o_t64 = o_tz + ((nt * 4 + 15) / 16) * 16;
+    const size_t o_t32 = o_t64 + nt * 8;
+    const size_t total = o_t32 + ((nt * 4 + 15) / 16) * 16 + 16;
+    GV_TRY(h->G.reserve(total));
+    char *b = (char *)h->G.ptr;
+    std::vector<float> t32(h->tc.begin(), h->tc.end());
+    GV_CUDA(cudaMemcpy(b + o_gm, h->gm.data(), ng * 4, cudaMemcpyHostToDevice));
+    GV_CUDA(cudaMemcpy(b + o_gs, h->gs.data(), (ng + 1) * 4, cudaMemcpyHostToDevice));
+    GV_CUDA(cudaMemcpy(b + o_tz, h->tz.data(), nt * 4, cudaMemcpyHostToDevice));
+    GV_CUDA(cudaMemcpy(b + o_t64, h->tc.data(), nt * 8, cudaMemcpyHostToDevice));
+    GV_CUDA(cudaMemcpy(b + o_t32, t32.data(), nt * 4, cudaMemcpyHostToDevice));
+    h->d_gm = (uint32_t *)(b + o_gm);
+    h->d_gs = (int *)(b + o_gs);
+    h->d_tz = (uint32_t *)(b + o_tz);
+    h->d_tc64 = (double *)(b + o_t64);
+    h->d_tc32 = (float *)(b + o_t32);
+  }
+  return GVQE_OK;
+}
+
+// --------------------------------------------------------- plan execution --
+static Plan *get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag) {
+  const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0);
+  auto it = a->plans.find(key);
+  if (it != a->plans.end() && it->second.tile_bits == a->tile_bits) return &it->second;
+  Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, want_grad, diag);
+  pl.tile_bits = a->tile_bits;
+  a->plans[key] = std::move(pl);
+  return &a->plans[key];
+}
+
+static int upload_dir(Plan *pl) {
+  if (pl->d_dir.ptr && pl->d_dir_count == (int)pl->dir.size()) return GVQE_OK;
+  GV_TRY(pl->d_dir.reserve(sizeof(RedEntry) * std::max<size_t>(1, pl->dir.size())));
+  GV_CUDA(cudaMemcpy(pl->d_dir.ptr, pl->dir.data(), sizeof(RedEntry) * pl->dir.size(), cudaMemcpyHostToDevice));
+  pl->d_dir_count = (int)pl->dir.size();
+  return GVQE_OK;
+}
+
+// Run the plan for `batch` parameter vectors (already converted to cs on device).
+static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const void *cs_all, const uint8_t *mask,
+                    int batch, double *E, double *grad, const int *minlayer, cudaStream_t s) {
+  const int prec = pl->prec;
+  const size_t es = prec ? 8 : 4;
+  const long long S = pl->state_elems;
+  GV_TRY(upload_dir(pl));
+  // jobs per launch: enough tiles to fill the GPU, bounded by memory
+  const long long tilesA = 1LL << (pl->n - pl->lp[0].tb);
+  int J = (int)std::min<long long>(batch, std::max<long long>(1, 4096 / tilesA));
+  const size_t per_job = (size_t)pl->n_bufs * S * es + (size_t)pl->part_stride * 8;
+  size_t freeb = 0, total = 0;
+  GV_CUDA(cudaMemGetInfo(&freeb, &total));
+  const size_t have = freeb + a->ws.bytes;
+  const size_t budget = have > (size_t)512 << 20 ? have - ((size_t)512 << 20) : 0;
+  if (per_job > budget)
+    return fail(GVQE_ENOMEM, "one evaluation needs %.3f GiB of workspace, %.3f GiB available", per_job / 1073741824.0,
+                budget / 1073741824.0);
+  J = (int)std::max<size_t>(1, std::min<size_t>((size_t)J, budget / per_job));
+  const size_t need = per_job * (size_t)J + 256;
+  GV_TRY(a->ws.reserve(need));
+  char *base = (char *)a->ws.ptr;
+  double *part = (double *)base;
+  char *bufs = base + (((size_t)pl->part_stride * 8 * J + 255) / 256) * 256;
+  auto buf_ptr = [&](int id) -> void * {
+    if (id < 0) return nullptr;
+    return bufs + (size_t)id * J * S * es;  // buffer id, job slots contiguous
+  };
+  const void *table = prec ? h->T64.ptr : h->T32.ptr;
+  const void *tc = prec ? (const void *)h->d_tc64 : (const void *)h->d_tc32;
+  for (int j0 = 0; j0 < batch; j0 += J) {
+    const int jobs = std::min(J, batch - j0);
+    for (const PassStep &st : pl->steps) {
+      PassArgs A = st.A;
+      A.job0 = j0;
+      A.cs = cs_all;
+      A.table = table;
+      A.in = buf_ptr(st.in);
+      A.in_stride = S;
+      A.lam_in = buf_ptr(st.lam);
+      A.lam_stride = S;
+      A.out = buf_ptr(st.out);
+      A.out_stride = S;
+      A.part = part + (st.part_region >= 0 ? st.part_region : 0);
+      A.epart = part + (st.epart_region >= 0 ? st.epart_region : 0);
+      A.part_stride = pl->part_stride;
+      A.minlayer = minlayer;
+      if (!st.xy) {
+        GV_CUDA(launch_pass(prec, A, jobs, 0, s));
+        continue;
+      }
+      // X-mask groups in chunks that fit in shared memory; the last chunk forms the energy.
+      const int ng = (int)h->gm.size();
+      if (ng == 0) {
+        A.ngroups = 0;
+        A.gmask = nullptr;
+        A.gstart = nullptr;
+        GV_CUDA(launch_pass(prec, A, jobs, 0, s));
+        continue;
+      }
+      int g0 = 0;
+      bool first = true;
+      while (g0 < ng) {
+        int g1 = g0;
+        while (g1 < ng) {
+          const int nt = h->gs[g1 + 1] - h->gs[g0];
+          if (xy_smem_bytes(prec, g1 + 1 - g0, nt) > 160 * 1024) break;
+          ++g1;
+        }
+        if (g1 == g0) return fail(GVQE_EUNSUPPORTED, "X-mask group %d has too many terms", g0);
+        PassArgs B = A;
+        B.gmask = h->d_gm + g0;
+        B.gstart = h->d_gs + g0;
+        B.ngroups = g1 - g0;
+        B.tz = h->d_tz;
+        B.tc = tc;
+        const bool last = (g1 == ng);
+        B.flags = A.flags & ~(F_ENERGY | F_WRITE_LAMBDA | F_ACCUM);
+        if (!first) B.flags |= F_ACCUM;
+        if (last) B.flags |= (A.flags & (F_ENERGY | F_WRITE_LAMBDA));
+        if (!last) B.flags |= F_WRITE_LAMBDA;
+        if (!last || (A.flags & F_WRITE_LAMBDA)) {
+          if (!B.out) return fail(GVQE_EUNSUPPORTED, "chunked X-mask groups need a lambda buffer");
+        }
+        B.lam_in = B.out;  // chunks after the first accumulate onto lambda
+        const int nt = h->gs[g1] - h->gs[g0];
+        GV_CUDA(launch_pass(prec, B, jobs, nt, s));
+        first = false;
+        g0 = g1;
+      }
+    }
+    GV_CUDA(launch_reduce(part, pl->part_stride, (const RedEntry *)pl->d_dir.ptr, pl->d_dir_count, mask ? mask + (size_t)j0 * pl->P : nullptr,
+                          pl->P, E + j0, grad ? grad + (size_t)j0 * pl->P : nullptr, jobs, s));
+  }
+  return GVQE_OK;
+}
+
+static bool is_ham(const void *p) { return p && ((const gvqe_hamiltonian_s *)p)->magic == MAGIC_HAM; }
+static bool is_ansatz(const void *p) { return p && ((const gvqe_ansatz_s *)p)->magic == MAGIC_ANSATZ; }
+
+static int check_pair(gvqe_ansatz a, gvqe_hamiltonian h) {
+  if (!is_ansatz(a)) return fail(GVQE_EINVAL, "invalid ansatz handle");
+  if (!is_ham(h)) return fail(GVQE_EINVAL, "invalid Hamiltonian handle");
+  if (a->n != h->n) return fail(GVQE_EINVAL, "ansatz has %d qubits but the Hamiltonian %d", a->n, h->n);
+  return GVQE_OK;
+}
+
+// energies (and optionally adjoint gradients) for a batch
+static int energy_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, int batch,
+                       double *E, double *grad, int prec, cudaStream_t s) {
+  const bool diag = h->gm.empty();
+  GV_TRY(ensure_tables(h, prec, s));
+  Plan *pl = get_plan(a, prec, grad != nullptr, diag);
+  const int P = pl->P;
+  // trig table and per-job lowest active layer
+  const size_t cs_bytes = (size_t)batch * P * (prec ? 16 : 8);
+  GV_TRY(a->aux.reserve(cs_bytes + (size_t)batch * 4 + 256));
+  void *cs = a->aux.ptr;
+  int *minlayer = (int *)((char *)a->aux.ptr + ((cs_bytes + 255) / 256) * 256);
+  GV_CUDA(launch_trig(prec, params, (long long)batch * P, cs, s));
+  const int *ml = nullptr;
+  if (grad) {
+    GV_CUDA(launch_minlayer(mask, batch, a->n, P, a->reps + 1, minlayer, s));
+    ml = minlayer;
+  }
+  return run_plan(a, h, pl, cs, mask, batch, E, grad, ml, s);
+}
+
+static int param_shift_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, int batch,
+                            double *E, double *grad, int prec, cudaStream_t s) {
+  const int P = a->n * (a->reps + 1);
+  std::vector<uint8_t> hmask((size_t)batch * P, 1);
+  if (mask) {
+    GV_CUDA(cudaMemcpyAsync(hmask.data(), mask, hmask.size(), cudaMemcpyDeviceToHost, s));
+    GV_CUDA(cudaStreamSynchronize(s));
+  }
+  for (int b = 0; b < batch; ++b) {
+    std::vector<int> act;
+    for (int p = 0; p < P; ++p)
+      if (hmask[(size_t)b * P + p]) act.push_back(p);
+    const int rows = 2 * (int)act.size() + 1;
+    GV_TRY(a->shift.reserve((size_t)rows * P * 8 + (size_t)rows * 8 + act.size() * 4 + 1024));
+    double *sp = (double *)a->shift.ptr;
+    double *se = sp + (size_t)rows * P;
+    int *sa = (int *)(se + rows);
+    if (!act.empty()) GV_CUDA(cudaMemcpyAsync(sa, act.data(), act.size() * 4, cudaMemcpyHostToDevice, s));
+    GV_CUDA(launch_shift_params(params + (size_t)b * P, P, 1, sa, (int)act.size(), sp, s));
+    GV_TRY(energy_impl(a, h, sp, nullptr, rows, se, nullptr, prec, s));
+    GV_CUDA(launch_shift_combine(se, P, 1, sa, (int)act.size(), E + b, grad + (size_t)b * P, s));
+    GV_CUDA(cudaStreamSynchronize(s));  // the host vector `act` and the shift buffer are reused
+  }
+  return GVQE_OK;
+}
+
+// ---------------------------------------------------------------- C ABI --
+extern "C" {
+
+int gvqe_version(void) { return 10000 * GVQE_VERSION_MAJOR + 100 * GVQE_VERSION_MINOR + GVQE_VERSION_PATCH; }
+
+const char *gvqe_last_error(void) { return g_err.c_str(); }
+
+int gvqe_hamiltonian_create(int n_qubits, int n_terms, const char *pauli, const double *coeffs,
+                            gvqe_hamiltonian *out) {
+  g_err.clear();
+  if (!out) return fail(GVQE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > GVQE_MAX_QUBITS)
+    return fail(GVQE_EINVAL, "n_qubits=%d outside [1, %d]", n_qubits, GVQE_MAX_QUBITS);
+  if (n_terms < 0) return fail(GVQE_EINVAL, "n_terms=%d < 0", n_terms);
+  if (n_terms > 0 && (!pauli || !coeffs)) return fail(GVQE_EINVAL, "pauli or coeffs is NULL");
+  gvqe_hamiltonian_s *h = new gvqe_hamiltonian_s();
+  h->magic = MAGIC_HAM;
+  h->n = n_qubits;
+  const int rc = parse_hamiltonian(h, n_qubits, n_terms, pauli, coeffs);
+  if (rc != GVQE_OK) {
+    h->magic = 0;
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return GVQE_OK;
+}
+
+int gvqe_hamiltonian_stats(gvqe_hamiltonian h, int *n_diag, int *n_groups, int *n_grouped, int *n_dropped) {
+  g_err.clear();
+  if (!is_ham(h)) return fail(GVQE_EINVAL, "invalid Hamiltonian handle");
+  if (n_diag) *n_diag = (int)h->dz.size();
+  if (n_groups) *n_groups = (int)h->gm.size();
+  if (n_grouped) *n_grouped = h->n_grouped;
+  if (n_dropped) *n_dropped = h->n_dropped;
+  return GVQE_OK;
+}
+
+int gvqe_ansatz_create(int n_qubits, int reps, int entangler, gvqe_ansatz *out) {
+  g_err.clear();
+  if (!out) return fail(GVQE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > GVQE_MAX_QUBITS)
+    return fail(GVQE_EINVAL, "n_qubits=%d outside [1, %d]", n_qubits, GVQE_MAX_QUBITS);
+  if (reps < 0 || reps > 64) return fail(GVQE_EINVAL, "reps=%d outside [0, 64]", reps);
+  if (entangler != GVQE_ENT_LINEAR) return fail(GVQE_EUNSUPPORTED, "entangler %d is not implemented", entangler);
+  gvqe_ansatz_s *a = new gvqe_ansatz_s();
+  a->magic = MAGIC_ANSATZ;
+  a->n = n_qubits;
+  a->reps = reps;
+  a->ent = entangler;
+  a->tile_bits = 0;
+  *out = a;
+  return GVQE_OK;
+}
+
+int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
+  g_err.clear();
+  if (!is_ansatz(a)) return fail(GVQE_EINVAL, "invalid ansatz handle");
+  if (option == GVQE_OPT_TILE_BITS) {
+    if (value != 0 && (value < 10 || value > 14))
+      return fail(GVQE_EINVAL, "tile bits %d outside [10, 14] (0 = auto)", value);
+    a->tile_bits = value;
+    a->plans.clear();
+    return GVQE_OK;
+  }
+  return fail(GVQE_EINVAL, "unknown option %d", option);
+}
+
+static int common_checks(gvqe_ansatz a, gvqe_hamiltonian h, const void *params, int batch, const void *E, int flags) {
+  GV_TRY(check_pair(a, h));
+  if (!params || !E) return fail(GVQE_EINVAL, "params or energies is NULL");
+  if (batch < 1) return fail(GVQE_EINVAL, "batch=%d < 1", batch);
+  if (flags & ~(GVQE_FP64 | GVQE_GRAD_PARAM_SHIFT)) return fail(GVQE_EINVAL, "unknown flags 0x%x", flags);
+  const int prec = flags & GVQE_FP64 ? 1 : 0;
+  if (a->tile_bits > max_tile_bits(prec))
+    return fail(GVQE_EINVAL, "tile bits %d above the %s maximum %d", a->tile_bits, prec ? "FP64" : "FP32",
+                max_tile_bits(prec));
+  return GVQE_OK;
+}
+
+int gvqe_energy(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int batch, double *energies, int flags,
+                void *stream) {
+  g_err.clear();
+  GV_TRY(common_checks(a, h, params, batch, energies, flags));
+  if (flags & GVQE_GRAD_PARAM_SHIFT) return fail(GVQE_EINVAL, "GVQE_GRAD_PARAM_SHIFT is a gradient flag");
+  return energy_impl(a, h, params, nullptr, batch, energies, nullptr, flags & GVQE_FP64 ? 1 : 0,
+                     (cudaStream_t)stream);
+}
+
+int gvqe_energy_grad(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, int batch,
+                     double *energies, double *grad, int flags, void *stream) {
+  g_err.clear();
+  GV_TRY(common_checks(a, h, params, batch, energies, flags));
+  if (!grad) return fail(GVQE_EINVAL, "grad is NULL");
+  const int prec = flags & GVQE_FP64 ? 1 : 0;
+  if (flags & GVQE_GRAD_PARAM_SHIFT)
+    return param_shift_impl(a, h, params, mask, batch, energies, grad, prec, (cudaStream_t)stream);
+  return energy_impl(a, h, params, mask, batch, energies, grad, prec, (cudaStream_t)stream);
+}
+
+int gvqe_plan_describe(int n_qubits, int reps, int flags, int tile_bits, char *buf, int buflen) {
+  g_err.clear();
+  if (n_qubits < 1 || n_qubits > GVQE_MAX_QUBITS || reps < 0 || reps > 64)
+    return fail(GVQE_EINVAL, "bad size n=%d reps=%d", n_qubits, reps);
+  const int prec = flags & GVQE_FP64 ? 1 : 0;
+  if (tile_bits != 0 && (tile_bits < 10 || tile_bits > max_tile_bits(prec)))
+    return fail(GVQE_EINVAL, "tile bits %d", tile_bits);
+  Plan pl = build_plan(n_qubits, reps, prec, tile_bits, true, true);
+  const std::string s = describe_plan(pl);
+  if (buf && buflen > 0) {
+    const size_t m = std::min<size_t>((size_t)buflen - 1, s.size());
+    memcpy(buf, s.data(), m);
+    buf[m] = 0;
+  }
+  return (int)pl.lp.size();
+}
+
+int gvqe_destroy(void *handle) {
+  g_err.clear();
+  if (!handle) return GVQE_OK;
+  const uint32_t magic = *(const uint32_t *)handle;
+  if (magic == MAGIC_HAM) {
+    cudaDeviceSynchronize();
+    gvqe_hamiltonian_s *h = (gvqe_hamiltonian_s *)handle;
+    h->T64.release();
+    h->T32.release();
+    h->G.release();
+    h->magic = 0;
+    delete h;
+    return GVQE_OK;
+  }
+  if (magic == MAGIC_ANSATZ) {
+    cudaDeviceSynchronize();
+    gvqe_ansatz_s *a = (gvqe_ansatz_s *)handle;
+    a->ws.release();
+    a->aux.release();
+    a->shift.release();
+    for (auto &kv : a->plans) kv.second.d_dir.release();
+    a->magic = 0;
+    delete a;
+    return GVQE_OK;
+  }
+  if (magic == MAGIC_BATCH) return batch_destroy((gvqe_batch_s *)handle);
+  return fail(GVQE_EINVAL, "not a gvqe handle");
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch --
+struct gvqe_batch_s {
+  uint32_t magic = 0;
+  int prec = 0;
+  std::vector<gvqe_ansatz> a;
+  std::vector<gvqe_hamiltonian> h;
+};
+
+int batch_destroy(gvqe_batch_s *b) {
+  cudaDeviceSynchronize();
+  b->magic = 0;
+  delete b;
+  return GVQE_OK;
+}
+
+extern "C" {
+
+int gvqe_batch_create(int n_inst, const gvqe_ansatz *ansatze, const gvqe_hamiltonian *hams, int flags,
+                      gvqe_batch *out) {
+  g_err.clear();
+  if (!out) return fail(GVQE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_inst < 1 || !ansatze || !hams) return fail(GVQE_EINVAL, "n_inst=%d or NULL instance arrays", n_inst);
+  if (flags & ~GVQE_FP64) return fail(GVQE_EINVAL, "unknown flags 0x%x", flags);
+  for (int i = 0; i < n_inst; ++i) {
+    const int rc = check_pair(ansatze[i], hams[i]);
+    if (rc != GVQE_OK) return fail(rc, "instance %d: %s", i, g_err.c_str());
+  }
+  gvqe_batch_s *b = new gvqe_batch_s();
+  b->magic = MAGIC_BATCH;
+  b->prec = flags & GVQE_FP64 ? 1 : 0;
+  b->a.assign(ansatze, ansatze + n_inst);
+  b->h.assign(hams, hams + n_inst);
+  *out = b;
+  return GVQE_OK;
+}
+
+int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *const *masks, double *energies,
+                   double *const *grads, void *stream) {
+  g_err.clear();
+  if (!b || b->magic != MAGIC_BATCH) return fail(GVQE_EINVAL, "invalid batch handle");
+  if (!params || !energies) return fail(GVQE_EINVAL, "params or energies is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (size_t i = 0; i < b->a.size(); ++i) {
+    if (!params[i]) return fail(GVQE_EINVAL, "params[%zu] is NULL", i);
+    const uint8_t *m = masks ? masks[i] : nullptr;
+    double *g = grads ? grads[i] : nullptr;
+    const int rc = energy_impl(b->a[i], b->h[i], params[i], m, 1, energies + i, g, b->prec, s);
+    if (rc != GVQE_OK) return rc;
+  }
+  return GVQE_OK;
+}
+
+}  // extern "C"

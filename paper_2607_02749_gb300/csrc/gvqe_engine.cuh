@@ -1,0 +1,110 @@
+// gvqe_engine.cuh -- launch descriptors shared by the host planner and the kernels.
+//
+// The state vector of n qubits is a real array of 2^n amplitudes (float or
+// double): the RY+CX ansatz of Section IV-B maps |0> to a real vector (RY is a
+// real rotation, CX a permutation), so the imaginary part is identically zero
+// and is not stored.
+//
+// Work is organised in "tile passes".  A tile is 2^tb amplitudes whose index
+// bits are tile-local bits [0, c) -> global bits [0, c) (contiguous runs that
+// keep global accesses coalesced) and tile-local bits [c, tb) -> global bits
+// [a, a + tb - c).  The remaining global bits enumerate the tiles.  A pass
+// applies the RY gates of one layer on the qubits of its gate bits while the
+// tile sits on chip; an RY layer on n qubits takes one pass over bits
+// [0, tb) plus passes over the higher qubits.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gvqe {
+
+enum PassKind : int {
+  K_FWD = 0,        // forward: RY(theta) on the gate bits of one layer
+  K_BWD = 1,        // adjoint: gradients of the gate bits, then RY(-theta) on lambda
+  K_GRAD_L0 = 2,    // layer-0 gradients against the analytic product state
+  K_LAMBDA_XY = 3,  // lambda = H psi with X-mask groups; energy
+  K_WHT = 4,        // unnormalised Walsh-Hadamard butterflies (diagonal table build)
+};
+
+enum LoadMode : int {
+  LD_PLAIN = 0,      // v = in[y]
+  LD_GATHER = 1,     // v = in[A^-1 y]: the linear CX chain applied on the fly
+  LD_L0_GATHER = 2,  // v = psi_0(A^-1 y): analytic layer-0 product state through the CX chain
+  LD_L0 = 3,         // v = psi_0(y)
+};
+
+enum StoreMode : int {
+  ST_PLAIN = 0,    // out[y] = v
+  ST_SCATTER = 1,  // out[A^-1 y] = v: the inverse CX chain (adjoint of LD_GATHER)
+  ST_NONE = 2,
+};
+
+enum PassFlags : int {
+  F_ENERGY = 1,        // accumulate an energy partial per tile
+  F_LAMBDA_INIT = 2,   // lambda = table * psi (diagonal H) instead of reading lambda
+  F_PAIR_ORDER = 4,    // launch tiles H and ~H next to each other (gather/scatter passes)
+  F_WRITE_LAMBDA = 8,  // K_LAMBDA_XY: write lambda
+  F_ACCUM = 16,        // K_LAMBDA_XY: add onto lambda already written (group chunks)
+};
+
+struct PassArgs {
+  int kind, load_mode, store_mode, flags;
+  int n, tb, c, a;          // register size, tile bits and bit layout (see above)
+  uint32_t gate_mask;       // tile bits that carry a gate in this pass
+  int layer;                // r: the parameter of tile bit i is p = r*n + qubit(i)
+  int P;                    // parameters per job
+  long long tiles;          // tiles per job (a power of two)
+  const void *in;           // psi input (per-job stride in_stride elements)
+  long long in_stride;
+  const void *lam_in;       // lambda input
+  long long lam_stride;
+  void *out;                // psi or lambda output
+  long long out_stride;
+  const void *table;        // diagonal table E(x) in amplitude precision
+  const void *cs;           // (cos(theta/2), sin(theta/2)) per job and parameter
+  int job0;                 // global index of job 0 of this launch (cs, minlayer)
+  double *part;             // partial sums [row][tile] for this pass, per-job stride part_stride
+  long long part_stride;
+  double *epart;            // energy partials [tile], per-job stride part_stride
+  const int *minlayer;      // per job: lowest layer with an active parameter (NULL = 0)
+  // X-mask groups (K_LAMBDA_XY): group g flips mask gmask[g] and owns terms
+  // [gstart[g], gstart[g+1]) with z-masks tz[] and coefficients tc[] (amplitude precision).
+  const uint32_t *gmask;
+  const int *gstart;
+  int ngroups;
+  const uint32_t *tz;
+  const void *tc;
+};
+
+// One output of the final reduction: the sum of `count` partials starting at
+// `off` inside a job's partial buffer becomes E (param < 0) or grad[param].
+struct RedEntry {
+  long long off;
+  int count;
+  int param;
+};
+
+// Host-side launchers (gvqe_kernels.cu).  prec: 0 = float, 1 = double.
+// nterm: number of terms of the X-mask group chunk (K_LAMBDA_XY only).
+cudaError_t launch_pass(int prec, const PassArgs &A, int jobs, int nterm, cudaStream_t s);
+// Shared memory of one K_LAMBDA_XY launch; at most ~200 KiB is accepted.
+size_t xy_smem_bytes(int prec, int ngroups, int nterm);
+cudaError_t launch_trig(int prec, const double *params, long long count, void *cs, cudaStream_t s);
+cudaError_t launch_minlayer(const uint8_t *mask, int jobs, int n, int P, int none_value, int *out,
+                            cudaStream_t s);
+cudaError_t launch_reduce(const double *part, long long part_stride, const RedEntry *dir, int ndir,
+                          const uint8_t *mask, int P, double *E, double *grad, int jobs,
+                          cudaStream_t s);
+cudaError_t launch_scatter_coeffs(const uint32_t *z, const double *c, int count, double *table,
+                                  cudaStream_t s);
+cudaError_t launch_convert_table(const double *src, float *dst, long long count, cudaStream_t s);
+cudaError_t launch_shift_params(const double *params, int P, int jobs, const int *active,
+                                int n_active, double *out, cudaStream_t s);
+cudaError_t launch_shift_combine(const double *Es, int P, int jobs, const int *active, int n_active,
+                                 double *E, double *grad, cudaStream_t s);
+// Largest tile size (log2 amplitudes) whose backward pass fits in shared memory.
+int max_tile_bits(int prec);
+// Dynamic shared memory (bytes) needed by one pass launch.
+size_t pass_smem_bytes(int prec, int kind, int tb);
+
+}  // namespace gvqe

@@ -1,0 +1,97 @@
+// gvqe_internal.h -- host-side handle and plan structures of the gvqe library.
+#pragma once
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "gvqe_engine.cuh"
+
+#define GVQE_VERSION_MAJOR 0
+#define GVQE_VERSION_MINOR 1
+#define GVQE_VERSION_PATCH 0
+
+namespace gvqe {
+
+enum : uint32_t {
+  MAGIC_HAM = 0x47564831u,     // "GVH1"
+  MAGIC_ANSATZ = 0x47564131u,  // "GVA1"
+  MAGIC_BATCH = 0x47564231u,   // "GVB1"
+};
+
+int fail(int code, const char *fmt, ...);
+extern thread_local std::string g_err;
+
+// An owned device allocation that only grows.
+struct DevBuf {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+  int reserve(size_t need);
+  void release();
+};
+
+// One pass of an RY layer: tile bits [0,c) -> global [0,c), [c,tb) -> global [a, a+tb-c);
+// gates on the tile bits in gmask.
+struct LayerPass {
+  int c, a, tb;
+  uint32_t gmask;
+};
+
+// One launch of a plan.  Buffer ids index the plan's state buffers (-1 = none).
+struct PassStep {
+  PassArgs A;
+  int in = -1, lam = -1, out = -1;
+  long long part_region = -1, epart_region = -1;
+  bool xy = false;
+};
+
+struct Plan {
+  int n = 0, reps = 0, prec = 0, P = 0, tile_bits = 0;
+  std::vector<LayerPass> lp;
+  std::vector<PassStep> steps;
+  int n_bufs = 0, n_states = 0;
+  long long state_elems = 0;
+  long long part_stride = 0;  // doubles of partial sums per job
+  std::map<int, RedEntry> param_dir;
+  std::vector<RedEntry> dir;  // energy entry first, then one per parameter
+  DevBuf d_dir;
+  int d_dir_count = 0;
+};
+
+std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits);
+Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag);
+std::string describe_plan(const Plan &pl);
+
+}  // namespace gvqe
+
+struct gvqe_hamiltonian_s {
+  uint32_t magic = 0;
+  int n = 0;
+  // diagonal part: unique z-masks with merged coefficients (the all-I string has z = 0)
+  std::vector<uint32_t> dz;
+  std::vector<double> dc;
+  // X-mask groups (m != 0, even number of Y): group g owns terms [gs[g], gs[g+1])
+  std::vector<uint32_t> gm;
+  std::vector<int> gs;
+  std::vector<uint32_t> tz;
+  std::vector<double> tc;
+  int n_grouped = 0, n_dropped = 0;
+  double abs_sum = 0.0;
+  gvqe::DevBuf T64, T32, G;
+  uint32_t *d_gm = nullptr;
+  int *d_gs = nullptr;
+  uint32_t *d_tz = nullptr;
+  double *d_tc64 = nullptr;
+  float *d_tc32 = nullptr;
+};
+
+struct gvqe_ansatz_s {
+  uint32_t magic = 0;
+  int n = 0, reps = 0, ent = 0;
+  int tile_bits = 0;  // 0 = automatic
+  std::map<int, gvqe::Plan> plans;
+  gvqe::DevBuf ws, aux, shift;
+};
+
+struct gvqe_batch_s;
+int batch_destroy(gvqe_batch_s *b);

@@ -1,0 +1,146 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol that
+include/gvqe.h declares, validates arguments on the host, and plans passes."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2607_02749_gb300 import _lib
+from paper_2607_02749_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gvqe.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gvqe_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    names = _declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in gvqe.h but not exported"
+
+
+def test_every_declared_symbol_has_a_python_binding():
+    for name in _declared_functions():
+        assert hasattr(_lib, name), f"no Python binding named {name}"
+
+
+def test_version_and_empty_error():
+    assert _lib.gvqe_version() >= 100
+    assert isinstance(_lib.gvqe_last_error(), str)
+
+
+def test_hamiltonian_parsing_and_stats():
+    n = 6
+    strings = ["ZZIIII", "ZZIIII", "IIIIII", "XIXIII", "YYIIII", "YIIIII", "IXZYII", "XIXZII"]
+    coeffs = [1.0, 2.0, 0.5, 1.5, -1.0, 3.0, 0.7, 0.2]
+    h = _lib.gvqe_hamiltonian_create(n, strings, coeffs)
+    try:
+        st = _lib.gvqe_hamiltonian_stats(h)
+        # diagonal: ZZ (merged) and the identity; X groups: mask 0b101 (XIX, XIXZ) and 0b11 (YY);
+        # odd-Y strings YIIIII and IXZYII are dropped
+        assert st == {"diag": 2, "groups": 2, "grouped": 3, "dropped_odd_y": 2}
+    finally:
+        _lib.gvqe_destroy(h)
+
+
+@pytest.mark.parametrize("bad", ["ZZA", "zzI", "Z Z"])
+def test_bad_letters_rejected(bad):
+    with pytest.raises(_lib.GvqeError) as e:
+        _lib.gvqe_hamiltonian_create(3, [bad], [1.0])
+    assert e.value.code == _lib.GVQE_EINVAL
+    assert "letter" in str(e.value)
+
+
+def test_size_checks():
+    for n in (0, 31, -1):
+        with pytest.raises(_lib.GvqeError) as e:
+            _lib.gvqe_hamiltonian_create(n, [], [])
+        assert e.value.code == _lib.GVQE_EINVAL
+        with pytest.raises(_lib.GvqeError):
+            _lib.gvqe_ansatz_create(n, 1)
+    with pytest.raises(_lib.GvqeError):
+        _lib.gvqe_ansatz_create(4, -1)
+    with pytest.raises(_lib.GvqeError) as e:
+        _lib.gvqe_ansatz_create(4, 1, entangler=7)
+    assert e.value.code == _lib.GVQE_EUNSUPPORTED
+    with pytest.raises(_lib.GvqeError):
+        _lib.gvqe_hamiltonian_create(3, ["ZZ"], [1.0])  # string shorter than n is caught by length
+
+
+def test_destroy_null_and_bad_handle():
+    _lib.gvqe_destroy(None)
+    junk = ctypes.create_string_buffer(64)
+    with pytest.raises(_lib.GvqeError):
+        _lib.gvqe_destroy(ctypes.addressof(junk))
+
+
+def test_tile_bits_option_validation():
+    a = _lib.gvqe_ansatz_create(12, 2)
+    try:
+        _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_TILE_BITS, 12)
+        _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_TILE_BITS, 0)
+        with pytest.raises(_lib.GvqeError):
+            _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_TILE_BITS, 9)
+        with pytest.raises(_lib.GvqeError):
+            _lib.gvqe_ansatz_set_option(a, 99, 1)
+    finally:
+        _lib.gvqe_destroy(a)
+
+
+def _layer_passes(text):
+    out = []
+    for m in re.finditer(r"layer pass \d+: tile_bits=(\d+) carry=(\d+) high_start=(\d+) qubits=\[(\d+),(\d+)\]", text):
+        out.append(tuple(int(x) for x in m.groups()))
+    return out
+
+
+@pytest.mark.parametrize("n,flags,tb,expect", [
+    (30, 0, 0, 3), (30, 1, 0, 3), (24, 0, 0, 2), (28, 0, 0, 3), (14, 0, 0, 1), (12, 1, 0, 1),
+    (20, 0, 10, 3), (16, 0, 10, 2), (9, 0, 0, 1), (1, 0, 0, 1),
+])
+def test_plan_covers_every_qubit_once(n, flags, tb, expect):
+    text = _lib.gvqe_plan_describe(n, 2, flags, tb)
+    passes = _layer_passes(text)
+    assert len(passes) == expect
+    covered = []
+    for tbits, carry, start, qlo, qhi in passes:
+        covered.extend(range(qlo, qhi + 1))
+        assert carry >= min(3 if flags else 4, tbits) or carry == tbits
+    assert sorted(covered) == list(range(n))
+
+
+def test_plan_step_sequence_for_gradient():
+    text = _lib.gvqe_plan_describe(20, 3, 0, 10)
+    kinds = re.findall(r"^\s+(fwd|bwd|grad_l0|lambda_xy)\s", text, flags=re.M)
+    p = 3
+    assert kinds.count("fwd") == 3 * p
+    assert kinds.count("bwd") == 3 * p
+    assert kinds[-1] == "grad_l0"
+    assert kinds.index("bwd") == 3 * p  # backward starts after the forward
+
+
+def test_workload_generators_shapes():
+    ham = wl.z_hamiltonian(12, 200, seed=0)
+    assert ham.n_terms == 200 and all(len(s) == 12 for s in ham.strings)
+    assert all(set(s) <= {"I", "Z"} for s in ham.strings)
+    assert (ham.coeffs[:150] < 0).all() and (ham.coeffs[150:] == 10.0).all()
+    w = [sum(ch != "I" for ch in s) for s in ham.strings]
+    assert min(w) >= 1 and max(w) <= 4
+    ph = wl.pauli_hamiltonian(28, 5000, seed=0)
+    xy = sum(any(ch in "XY" for ch in s) for s in ph.strings)
+    assert 0.35 < xy / 5000 < 0.45
+    th = wl.thetas(30, 6, 4)
+    assert th.shape == (4, 210) and abs(th).max() <= 3.1416
+    batch = wl.cluster_batch(8)
+    for inst in batch:
+        assert 14 <= inst.n_qubits <= 20 and 2 <= inst.reps <= 4
+        frac = inst.mask.mean()
+        assert 0.25 <= frac <= 0.65
