@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Benchmark of the Graph-VQE energy + adjoint-gradient path on GB300.
+
+Default workload (one GPU): n = 30 qubits, reps = 6 (P = 210 parameters), a
+diagonal folding-style Hamiltonian of 20,000 Z-strings (15,000 contact terms
+c ~ U(-7.5, -0.1), 5,000 penalty terms c = +10), 4 parameter vectors per
+step, FP32 amplitudes with FP64 table and reductions.  One step = one
+gvqe_energy_grad call for the 4 vectors (energies and the full adjoint
+gradient).  Inputs are synthetic and seeded.
+
+Printed JSON line (rank 0): metric/value/unit (E+grad evaluations per second,
+device-timed with CUDA events on the launching stream), e2e (same metric through
+the public API with pinned host inputs copied in and results copied out every
+step), roofline of the dominant kernel (algorithmic bytes / measured launch
+time vs the measured HBM copy bandwidth), the FP64 parameter-shift comparator
+on the same GPU, FP32-vs-FP64 errors, clocks during the timed region and the
+CPU oracle baseline.
+
+--impl reference times the CPU oracle (the plain complex128 gate-by-gate
+simulator in oracle/) on bounded samples of the same workload instead.
+
+Multi-GPU: one process per GPU (torchrun); each rank evaluates its own 4
+parameter vectors (independent units, no data-path collective: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "E+grad evals/s at n=30: FP32 adjoint vs FP64 param-shift; HBM GB/s vs peak"
+UNIT = "E+grad/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gvqe", choices=["gvqe", "reference"])
+    ap.add_argument("--workload", default="n30_reps6_z20000")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true", help="skip the FP64 comparator legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload_sweeps(n: int, reps: int, n_terms: int):
+    """Full-state sweeps of the plain gate-by-gate oracle for one E+grad."""
+    ry = (reps + 1) * n          # forward RY gates
+    cx = reps * (n - 1)          # forward CNOTs
+    # forward + backward (gradient inner product + two inverse gates per RY, two CNOTs per CNOT)
+    gate_sweeps = ry + cx + ry * 3 + cx * 2
+    return gate_sweeps, n_terms
+
+
+def oracle_sample(n: int, reps: int, ham, n_gates: int = 2, n_terms: int = 2):
+    """Time a bounded sample of the oracle on the full-size state and scale to one E+grad."""
+    import oracle
+
+    t_gate, t_term = oracle.sweep_times(n, n_gates, ham.strings[:n_terms], ham.coeffs[:n_terms])
+    gs, ts = workload_sweeps(n, reps, ham.n_terms)
+    sec = gs * t_gate + ts * t_term
+    return {
+        "value": 1.0 / sec,
+        "unit": UNIT,
+        "cores": oracle.max_threads(),
+        "kind": "oracle",
+        "sample": (f"oracle complex128 at n={n}: {n_gates} RY sweeps ({t_gate:.3f} s each) and {n_terms} "
+                   f"Pauli-term sweeps ({t_term:.3f} s each), scaled to one E+grad = {gs} gate sweeps + "
+                   f"{ts} term sweeps = {sec:.0f} s"),
+    }
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gvqe_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("gvqe_kernels.cu", "gvqe_engine.cuh"):
+        with open(os.path.join(ROOT, "paper_2607_02749_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, bytes_per_launch_units: float):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if not e or e.get("source_hash") != kernel_source_hash():
+            return None
+        return e["dram_bytes_per_amplitude"] * bytes_per_launch_units
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2607_02749_gb300 import workloads as wl
+
+    w = wl.WORKLOADS[args.workload]
+    ham, _ = wl.make_workload(args.workload, batch=1)
+    n, reps = w["n"], w["reps"]
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(n, reps, ham, n_gates=1, n_terms=1)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            last = r
+    value = statistics.median(vals)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 4 * 1000.0 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": args.workload, "n_qubits": n, "reps": reps, "n_terms": w["terms"],
+                   "batch": 4, "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                         "sample": "per step: " + last["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_gvqe(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_2607_02749_gb300 as gv
+    from paper_2607_02749_gb300 import _lib
+    from paper_2607_02749_gb300 import workloads as wl
+
+    w = wl.WORKLOADS[args.workload]
+    n, reps, B = w["n"], w["reps"], w["batch"]
+    ham, _ = wl.make_workload(args.workload, batch=1)
+    theta = wl.thetas(n, reps, B, seed=1 + rank)
+    P = n * (reps + 1)
+    dev = torch.device("cuda", local)
+    h = gv.Hamiltonian.from_workload(ham)
+    a = gv.Ansatz(n, reps)
+    th = torch.as_tensor(theta, dtype=torch.float64, device=dev)
+    E = torch.empty(B, dtype=torch.float64, device=dev)
+    G = torch.empty(B, P, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        _lib.gvqe_energy_grad(a.handle, h.handle, th, None, E, G, _lib.GVQE_FP32, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_index = int(cvd.split(",")[local])
+        except ValueError:
+            pass
+    clocks = ClockSampler(gpu_index)
+    _lib.gvqe_profile_reset()
+    _lib.gvqe_profile_enable(True)
+    n_launch0 = _lib.gvqe_launch_count()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    _lib.gvqe_profile_enable(False)
+    launches = _lib.gvqe_launch_count() - n_launch0
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    units = ws * B * args.steps
+    value = units / (ms / 1000.0)
+
+    # roofline of the dominant kernel kind, measured live over the timed region
+    prof = {k: _lib.gvqe_profile_read(k) for k in range(5)}
+    names = {0: "k_fwd", 1: "k_bwd", 2: "k_grad_l0", 3: "k_lambda_xy", 4: "k_wht"}
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    pk = prof[dom]
+    peak, peak_src = measured_peaks()
+    achieved = pk["bytes"] / (pk["ms"] / 1000.0) / 1e9 if pk["ms"] > 0 else 0.0
+    per_launch_bytes = pk["bytes"] / max(1, pk["launches"])
+    amps_per_launch = 2.0 ** n
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "traffic": ncu_traffic(names[dom], amps_per_launch),
+        "kernel": names[dom], "launches": pk["launches"], "avg_launch_ms": pk["ms"] / max(1, pk["launches"]),
+        "algorithmic_bytes_per_launch": per_launch_bytes, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+        if peak_src == "measured" else "fallback",
+        "per_kind": {names[k]: {"launches": prof[k]["launches"], "ms": prof[k]["ms"],
+                                "GBps": (prof[k]["bytes"] / (prof[k]["ms"] / 1000.0) / 1e9) if prof[k]["ms"] else 0.0}
+                     for k in prof if prof[k]["launches"]},
+    }
+    _lib.gvqe_profile_reset()
+
+    # e2e through the public API: pinned host inputs in, results out, every step
+    th_host = torch.as_tensor(theta, dtype=torch.float64).pin_memory()
+    e_host = torch.empty(B, dtype=torch.float64).pin_memory()
+    g_host = torch.empty(B, P, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        e_d, g_d = gv.energy_grad(a, h, th_host.to(dev, non_blocking=True))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e_d, g_d = gv.energy_grad(a, h, th_host.to(dev, non_blocking=True))
+        e_host.copy_(e_d, non_blocking=True)
+        g_host.copy_(g_d, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = t.item()
+    e2e = {"value": ws * B * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": B * P * 8,
+           "d2h_bytes_per_step": B * 8 + B * P * 8}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n_qubits": n, "reps": reps, "n_params": P,
+                   "n_terms": w["terms"], "batch_per_gpu": B, "global_batch": B * ws,
+                   "amplitudes": "fp32 (real: RY+CX keeps the state real), fp64 table and reductions",
+                   "l2": "inputs larger than L2 (4 GiB state per pass)", "parallelism": f"replicas x{ws}"},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
+    }
+
+    if rank == 0 and not args.no_comparators:
+        # FP32 vs FP64 mode on vector 0, and the FP64 parameter-shift comparator (Eq. 13)
+        e32, g32 = E[0].item(), G[0].cpu().numpy()
+        t0 = time.perf_counter()
+        e64, g64 = gv.energy_grad(a, h, th[:1], fp64=True)
+        torch.cuda.synchronize()
+        t_adj64 = time.perf_counter() - t0
+        e64, g64 = e64.item(), g64[0].cpu().numpy()
+        scale = ham.abs_sum()
+        out["errors_vs_fp64"] = {"dE_over_sum_abs_c": abs(e32 - e64) / scale,
+                                 "grad_rel_l2": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
+                                 "sum_abs_c": scale, "E_fp64": e64}
+        mask = torch.zeros(1, P, dtype=torch.uint8, device=dev)
+        mask[0, P - 1] = 1
+        gv.energy_grad(a, h, th[:1], mask=mask, fp64=True, param_shift=True)  # warm the path
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, gps = gv.energy_grad(a, h, th[:1], mask=mask, fp64=True, param_shift=True)
+        torch.cuda.synchronize()
+        t_3 = time.perf_counter() - t0
+        t_grad = t_3 * (2 * P + 1) / 3.0
+        out["fp64_param_shift"] = {
+            "value": 1.0 / t_grad, "unit": UNIT,
+            "sample": f"3 FP64 energies (1 active parameter) took {t_3:.3f} s; one gradient = {2 * P + 1} energies",
+            "fp64_adjoint_value": 1.0 / t_adj64,
+            "check_dE_dtheta_last": {"param_shift": float(gps[0, P - 1].item()), "adjoint_fp64": float(g64[P - 1])},
+        }
+        out["speedup_fp32_adjoint_vs_fp64_param_shift"] = value / ws / (1.0 / t_grad)
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = oracle_sample(n, reps, ham)
+        except Exception as exc:  # pragma: no cover - host out of memory
+            out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                                   "sample": f"failed: {exc}"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gvqe(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

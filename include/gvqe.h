@@ -170,6 +170,29 @@ int gvqe_hamiltonian_stats(gvqe_hamiltonian h, int *n_diag, int *n_groups, int *
 /* gvqe_version -- library version as 10000*major + 100*minor + patch. */
 int gvqe_version(void);
 
+/*
+ * Launch accounting and per-kernel timing (for benchmarks).
+ * gvqe_launch_count -- number of kernels this library has enqueued in this
+ *   process so far (all handles, all streams).
+ * gvqe_profile_enable -- when `on` is nonzero, every tile-pass launch is
+ *   bracketed by two CUDA events recorded on the launching stream, and its
+ *   algorithmic bytes (each state, table and lambda element it must read or
+ *   write, counted once) are recorded.  0 turns recording off.
+ * gvqe_profile_read -- waits for the recorded events, then returns for one
+ *   kernel kind (GVQE_PROF_*) the number of launches, their summed device time
+ *   in ms and their summed algorithmic bytes; any pointer may be NULL.
+ * gvqe_profile_reset -- drops all recorded launches.
+ */
+#define GVQE_PROF_FWD 0       /* forward rotation passes */
+#define GVQE_PROF_BWD 1       /* adjoint passes (gradient + inverse rotation) */
+#define GVQE_PROF_GRAD_L0 2   /* layer-0 gradient pass */
+#define GVQE_PROF_LAMBDA_XY 3 /* H psi with X-mask groups */
+#define GVQE_PROF_WHT 4       /* diagonal-table Walsh-Hadamard passes */
+int64_t gvqe_launch_count(void);
+int gvqe_profile_enable(int on);
+int gvqe_profile_read(int kind, int64_t *launches, double *ms, double *bytes);
+int gvqe_profile_reset(void);
+
 #ifdef __cplusplus
 }
 #endif

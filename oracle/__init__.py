@@ -52,10 +52,12 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         lib.oracle_energy_grad.argtypes = [i, i, p, i, p, p, p, p]
         lib.oracle_param_shift_grad.argtypes = [i, i, p, i, p, p, p, p]
         lib.oracle_partial_work.argtypes = [i, i, i, p, p, p, p]
+        lib.oracle_sweep_times.argtypes = [i, i, i, p, p, p, p]
         lib.oracle_max_threads.restype = i
         lib.oracle_set_threads.argtypes = [i]
         for f in ("oracle_state", "oracle_apply_hamiltonian", "oracle_energy",
-                  "oracle_energy_grad", "oracle_param_shift_grad", "oracle_partial_work"):
+                  "oracle_energy_grad", "oracle_param_shift_grad", "oracle_partial_work",
+                  "oracle_sweep_times"):
             getattr(lib, f).restype = i
         del d
         if path is None:
@@ -176,3 +178,13 @@ def partial_work(n: int, n_gates: int, strings, coeffs, theta,
     _check(lib.oracle_partial_work(n, n_gates, h.m, _ptr(h.buf), _ptr(h.c), _ptr(th), _ptr(out)),
            "partial_work")
     return float(out[0])
+
+
+def sweep_times(n: int, n_gates: int, strings, coeffs, lib: Optional[ctypes.CDLL] = None):
+    """Seconds per RY sweep and per Pauli-term sweep of the oracle on a 2^n state."""
+    lib = lib or load()
+    h = _HamArgs(n, strings, coeffs)
+    tg = np.zeros(1)
+    tt = np.zeros(1)
+    _check(lib.oracle_sweep_times(n, n_gates, h.m, _ptr(h.buf), _ptr(h.c), _ptr(tg), _ptr(tt)), "sweep_times")
+    return float(tg[0]), float(tt[0])

@@ -325,3 +325,46 @@ int oracle_partial_work(int n, int n_gates, int n_terms, const char *pauli,
     free(out);
     return rc;
 }
+
+/*
+ * Timing helper for the CPU baseline: on one 2^n state, times `n_gates` RY
+ * sweeps (apply_ry) and `n_terms` Pauli-term sweeps (apply_pauli_term) of the
+ * oracle separately, excluding allocation.  Writes seconds per sweep.
+ */
+int oracle_sweep_times(int n, int n_gates, int n_terms, const char *pauli, const double *coeffs,
+                       double *sec_per_gate, double *sec_per_term) {
+    if (n < 1 || n > ORACLE_MAX_QUBITS || n_gates < 1 || n_terms < 1 || !pauli || !coeffs ||
+        !sec_per_gate || !sec_per_term)
+        return ORACLE_EINVAL;
+    const size_t dim = (size_t)1 << n;
+    cplx *psi = (cplx *)malloc(sizeof(cplx) * dim);
+    cplx *out = (cplx *)malloc(sizeof(cplx) * dim);
+    if (!psi || !out) { free(psi); free(out); return ORACLE_ENOMEM; }
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < (int64_t)dim; ++x) { psi[x] = 0.0; out[x] = 0.0; }
+    psi[0] = 1.0;
+#ifdef _OPENMP
+    double t0 = omp_get_wtime();
+#else
+    double t0 = 0.0;
+#endif
+    for (int g = 0; g < n_gates; ++g) apply_ry(psi, n, g % n, 0.1 + 0.01 * g);
+#ifdef _OPENMP
+    double t1 = omp_get_wtime();
+#else
+    double t1 = 0.0;
+#endif
+    int rc = ORACLE_OK;
+    for (int k = 0; k < n_terms && !rc; ++k)
+        rc = apply_pauli_term(out, psi, n, pauli + (size_t)k * (size_t)n, coeffs[k]);
+#ifdef _OPENMP
+    double t2 = omp_get_wtime();
+#else
+    double t2 = 0.0;
+#endif
+    *sec_per_gate = (t1 - t0) / n_gates;
+    *sec_per_term = (t2 - t1) / n_terms;
+    free(psi);
+    free(out);
+    return rc;
+}

@@ -28,6 +28,11 @@ GVQE_GRAD_PARAM_SHIFT = 0x2
 GVQE_ENT_LINEAR = 0
 GVQE_OPT_TILE_BITS = 1
 GVQE_MAX_QUBITS = 30
+GVQE_PROF_FWD = 0
+GVQE_PROF_BWD = 1
+GVQE_PROF_GRAD_L0 = 2
+GVQE_PROF_LAMBDA_XY = 3
+GVQE_PROF_WHT = 4
 
 _ERRNAMES = {
     GVQE_EINVAL: "GVQE_EINVAL",
@@ -63,6 +68,9 @@ _SIGS = {
     "gvqe_plan_describe": [_I, _I, _I, _I, ctypes.c_char_p, _I],
     "gvqe_hamiltonian_stats": [_VP, _VP, _VP, _VP, _VP],
     "gvqe_version": [],
+    "gvqe_profile_enable": [_I],
+    "gvqe_profile_read": [_I, _VP, _VP, _VP],
+    "gvqe_profile_reset": [],
 }
 
 
@@ -84,6 +92,8 @@ def load(path: Optional[str] = None, build_if_missing: bool = True) -> ctypes.CD
             f = getattr(lib, name)
             f.argtypes = argtypes
             f.restype = _I
+        lib.gvqe_launch_count.argtypes = []
+        lib.gvqe_launch_count.restype = ctypes.c_int64
         lib.gvqe_last_error.argtypes = []
         lib.gvqe_last_error.restype = ctypes.c_char_p
         if path is None:
@@ -208,3 +218,26 @@ def gvqe_hamiltonian_stats(ham: int) -> dict:
     vals = [ctypes.c_int() for _ in range(4)]
     _check(load().gvqe_hamiltonian_stats(ham, *[ctypes.byref(v) for v in vals]), "gvqe_hamiltonian_stats")
     return dict(zip(("diag", "groups", "grouped", "dropped_odd_y"), (v.value for v in vals)))
+
+
+def gvqe_launch_count() -> int:
+    """Kernels this library has enqueued in this process so far."""
+    return int(load().gvqe_launch_count())
+
+
+def gvqe_profile_enable(on: bool) -> None:
+    _check(load().gvqe_profile_enable(1 if on else 0), "gvqe_profile_enable")
+
+
+def gvqe_profile_read(kind: int) -> dict:
+    """{launches, ms, bytes} summed over recorded launches of one kernel kind (GVQE_PROF_*)."""
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    by = ctypes.c_double()
+    _check(load().gvqe_profile_read(kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)),
+           "gvqe_profile_read")
+    return {"launches": n.value, "ms": ms.value, "bytes": by.value}
+
+
+def gvqe_profile_reset() -> None:
+    _check(load().gvqe_profile_reset(), "gvqe_profile_reset")

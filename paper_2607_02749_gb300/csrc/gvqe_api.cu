@@ -16,7 +16,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -74,6 +76,87 @@ void DevBuf::release() {
   if (ptr) cudaFree(ptr);
   ptr = nullptr;
   bytes = 0;
+}
+
+// ------------------------------------------------- launch accounting --
+static std::atomic<long long> g_launches{0};
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int kind;
+  double bytes;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof_pending;
+static long long g_prof_n[5] = {0, 0, 0, 0, 0};
+static double g_prof_ms[5] = {0, 0, 0, 0, 0};
+static double g_prof_bytes[5] = {0, 0, 0, 0, 0};
+
+void count_launches(int k) { g_launches += k; }
+
+// Bytes a pass must move at minimum: every element it reads or writes, once.
+static double pass_bytes(int prec, const PassArgs &A, int jobs) {
+  const double S = std::ldexp(1.0, A.n) * (prec ? 8 : 4) * jobs;
+  double b = 0;
+  switch (A.kind) {
+    case K_FWD:
+    case K_WHT:
+      if (A.load_mode == LD_PLAIN || A.load_mode == LD_GATHER) b += S;
+      if (A.store_mode != ST_NONE) b += S;
+      if (A.flags & F_ENERGY) b += S;
+      break;
+    case K_BWD:
+      b = 3 * S;
+      break;
+    case K_GRAD_L0:
+      b = S;
+      break;
+    case K_LAMBDA_XY:
+      b = 2 * S + ((A.flags & F_WRITE_LAMBDA) ? S : 0);
+      break;
+  }
+  return b;
+}
+
+static cudaError_t launch_step(int prec, const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
+  ProfRec rec{};
+  bool prof;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof = g_prof_on;
+  }
+  if (prof) {
+    cudaEventCreate(&rec.a);
+    cudaEventCreate(&rec.b);
+    cudaEventRecord(rec.a, s);
+  }
+  const cudaError_t e = launch_pass(prec, A, jobs, nterm, s);
+  ++g_launches;
+  if (prof) {
+    cudaEventRecord(rec.b, s);
+    rec.kind = A.kind;
+    rec.bytes = pass_bytes(prec, A, jobs);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_pending.push_back(rec);
+  }
+  return e;
+}
+
+static void prof_drain() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (ProfRec &r : g_prof_pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(r.b);
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess && r.kind >= 0 && r.kind < 5) {
+      g_prof_n[r.kind] += 1;
+      g_prof_ms[r.kind] += ms;
+      g_prof_bytes[r.kind] += r.bytes;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof_pending.clear();
 }
 
 // ---------------------------------------------------------------- planner --
@@ -442,7 +525,7 @@ static int build_table64(gvqe_hamiltonian_s *h, cudaStream_t s) {
       A.in = h->T64.ptr;
       A.out = h->T64.ptr;
       A.P = 1;
-      GV_CUDA(launch_pass(1, A, 1, 0, s));
+      GV_CUDA(launch_step(1, A, 1, 0, s));
     }
     GV_CUDA(cudaStreamSynchronize(s));
     tmp.release();
@@ -552,7 +635,7 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
       A.part_stride = pl->part_stride;
       A.minlayer = minlayer;
       if (!st.xy) {
-        GV_CUDA(launch_pass(prec, A, jobs, 0, s));
+        GV_CUDA(launch_step(prec, A, jobs, 0, s));
         continue;
       }
       // X-mask groups in chunks that fit in shared memory; the last chunk forms the energy.
@@ -561,7 +644,7 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
         A.ngroups = 0;
         A.gmask = nullptr;
         A.gstart = nullptr;
-        GV_CUDA(launch_pass(prec, A, jobs, 0, s));
+        GV_CUDA(launch_step(prec, A, jobs, 0, s));
         continue;
       }
       int g0 = 0;
@@ -590,11 +673,12 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
         }
         B.lam_in = B.out;  // chunks after the first accumulate onto lambda
         const int nt = h->gs[g1] - h->gs[g0];
-        GV_CUDA(launch_pass(prec, B, jobs, nt, s));
+        GV_CUDA(launch_step(prec, B, jobs, nt, s));
         first = false;
         g0 = g1;
       }
     }
+    count_launches(1);
     GV_CUDA(launch_reduce(part, pl->part_stride, (const RedEntry *)pl->d_dir.ptr, pl->d_dir_count, mask ? mask + (size_t)j0 * pl->P : nullptr,
                           pl->P, E + j0, grad ? grad + (size_t)j0 * pl->P : nullptr, jobs, s));
   }
@@ -624,9 +708,11 @@ static int energy_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, 
   void *cs = a->aux.ptr;
   int *minlayer = (int *)((char *)a->aux.ptr + ((cs_bytes + 255) / 256) * 256);
   GV_CUDA(launch_trig(prec, params, (long long)batch * P, cs, s));
+  count_launches(1);
   const int *ml = nullptr;
   if (grad) {
     GV_CUDA(launch_minlayer(mask, batch, a->n, P, a->reps + 1, minlayer, s));
+    count_launches(1);
     ml = minlayer;
   }
   return run_plan(a, h, pl, cs, mask, batch, E, grad, ml, s);
@@ -651,8 +737,10 @@ static int param_shift_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *par
     int *sa = (int *)(se + rows);
     if (!act.empty()) GV_CUDA(cudaMemcpyAsync(sa, act.data(), act.size() * 4, cudaMemcpyHostToDevice, s));
     GV_CUDA(launch_shift_params(params + (size_t)b * P, P, 1, sa, (int)act.size(), sp, s));
+    count_launches(1);
     GV_TRY(energy_impl(a, h, sp, nullptr, rows, se, nullptr, prec, s));
     GV_CUDA(launch_shift_combine(se, P, 1, sa, (int)act.size(), E + b, grad + (size_t)b * P, s));
+    count_launches(1);
     GV_CUDA(cudaStreamSynchronize(s));  // the host vector `act` and the shift buffer are reused
   }
   return GVQE_OK;
@@ -660,6 +748,38 @@ static int param_shift_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *par
 
 // ---------------------------------------------------------------- C ABI --
 extern "C" {
+
+int64_t gvqe_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int gvqe_profile_enable(int on) {
+  g_err.clear();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return GVQE_OK;
+}
+
+int gvqe_profile_read(int kind, int64_t *launches, double *ms, double *bytes) {
+  g_err.clear();
+  if (kind < 0 || kind > 4) return fail(GVQE_EINVAL, "profile kind %d", kind);
+  prof_drain();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (launches) *launches = g_prof_n[kind];
+  if (ms) *ms = g_prof_ms[kind];
+  if (bytes) *bytes = g_prof_bytes[kind];
+  return GVQE_OK;
+}
+
+int gvqe_profile_reset(void) {
+  g_err.clear();
+  prof_drain();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (int k = 0; k < 5; ++k) {
+    g_prof_n[k] = 0;
+    g_prof_ms[k] = 0;
+    g_prof_bytes[k] = 0;
+  }
+  return GVQE_OK;
+}
 
 int gvqe_version(void) { return 10000 * GVQE_VERSION_MAJOR + 100 * GVQE_VERSION_MINOR + GVQE_VERSION_PATCH; }
 

@@ -174,6 +174,9 @@ WORKLOADS = {
     "n24_reps4_z2000": dict(n=24, reps=4, terms=2000, batch=16, kind="z"),
     # n=30, reps=6, FP32 (and FP64 mode): 20,000 Z-strings, 4 thetas.
     "n30_reps6_z20000": dict(n=30, reps=6, terms=20000, batch=4, kind="z"),
+    # n=27, reps=2, FP32: 2,000 Z-strings, 1 theta: a profiling-size case (512 MiB state,
+    # larger than L2, a few GiB on the device in total).
+    "n27_reps2_z2000": dict(n=27, reps=2, terms=2000, batch=1, kind="z"),
     # n=28, reps=5, FP32: 5,000 strings over {I,X,Y,Z}, 8 thetas.
     "n28_reps5_pauli5000": dict(n=28, reps=5, terms=5000, batch=8, kind="pauli"),
 }
