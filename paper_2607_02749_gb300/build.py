@@ -19,6 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgvqe.so")
 SOURCES = ["gvqe_api.cu", "gvqe_kernels.cu"]
+# gvqe_inst.cu is compiled once per (amplitude type, tile bits) pair
+INSTANCES = [(t, tb) for t in ("float", "double") for tb in (10, 11, 12, 13)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               f"-I{INCLUDE}", f"-I{CSRC}"]
@@ -43,9 +45,10 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def _compile(src: str, extra: List[str]) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(job, extra: List[str]) -> str:
+    src, defs, tag = job
+    obj = os.path.join(BUILD, os.path.splitext(src)[0] + tag + ".o")
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *defs, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -58,8 +61,13 @@ def build(force: bool = False, verbose: bool = False, extra: Optional[List[str]]
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = list(extra or [])
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
+    jobs = [(s, [], "") for s in SOURCES]
+    jobs += [("gvqe_inst.cu", [f"-DGVQE_INST_T={t}", f"-DGVQE_INST_TB={tb}"], f"_{t}_{tb}") for t, tb in INSTANCES]
+    # the heaviest units first
+    jobs.sort(key=lambda j: (j[0] != "gvqe_inst.cu", -int(j[1][1].split("=")[1]) if j[1] else 0))
+    workers = max(1, min(len(jobs), os.cpu_count() or 4))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        objs = list(ex.map(lambda j: _compile(j, extra), jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)

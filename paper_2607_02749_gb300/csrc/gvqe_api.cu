@@ -160,7 +160,9 @@ static void prof_drain() {
 }
 
 // ---------------------------------------------------------------- planner --
-int auto_tile_bits(int prec) { return max_tile_bits(prec); }
+// 2^13 FP32 / 2^12 FP64 amplitudes per tile: a backward tile (psi + lambda) is
+// 64 KiB, so two CTAs share an SM, and n = 30 still takes three passes per layer.
+int auto_tile_bits(int prec) { return prec ? 12 : 13; }
 
 std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits) {
   std::vector<LayerPass> out;
@@ -839,8 +841,8 @@ int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
   g_err.clear();
   if (!is_ansatz(a)) return fail(GVQE_EINVAL, "invalid ansatz handle");
   if (option == GVQE_OPT_TILE_BITS) {
-    if (value != 0 && (value < 10 || value > 14))
-      return fail(GVQE_EINVAL, "tile bits %d outside [10, 14] (0 = auto)", value);
+    if (value != 0 && (value < 10 || value > 13))
+      return fail(GVQE_EINVAL, "tile bits %d outside [10, 13] (0 = auto)", value);
     a->tile_bits = value;
     a->plans.clear();
     return GVQE_OK;

@@ -84,6 +84,21 @@ struct RedEntry {
   int param;
 };
 
+// Shared-memory layout of one chunk of X-mask groups: [gmask][gstart][tz][tc], 16-byte aligned parts.
+struct XyLayout {
+  size_t gm, gs, tz, tc, total;
+};
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline XyLayout xy_layout(int ngroups, int nterm, int elem) {
+  XyLayout l;
+  l.gm = 0;
+  l.gs = align16((size_t)ngroups * 4);
+  l.tz = align16(l.gs + (size_t)(ngroups + 1) * 4);
+  l.tc = align16(l.tz + (size_t)nterm * 4);
+  l.total = align16(l.tc + (size_t)nterm * elem);
+  return l;
+}
+
 // Host-side launchers (gvqe_kernels.cu).  prec: 0 = float, 1 = double.
 // nterm: number of terms of the X-mask group chunk (K_LAMBDA_XY only).
 cudaError_t launch_pass(int prec, const PassArgs &A, int jobs, int nterm, cudaStream_t s);

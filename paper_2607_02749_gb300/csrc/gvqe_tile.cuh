@@ -1,0 +1,908 @@
+// gvqe_tile.cuh -- the tile-pass kernels of the gvqe engine (templates).
+//
+// A CTA owns one tile of 2^TB real amplitudes; each of its 2^(TB-5) threads
+// holds 32 amplitudes in registers at a time, and the tile moves through
+// register "rounds":
+//   round L: registers <-> tile bits 5..9, lanes <-> bits 0..4, warps <-> bits 10..
+//            (global loads/stores here are coalesced warp accesses)
+//   round M: registers <-> tile bits 0..4 (one 32-amplitude group per thread,
+//            16-byte vector shared-memory accesses)
+//   round H: registers <-> tile bits 10..TB-1
+// RY gates on the bits held in registers are applied in registers (FP32:
+// packed f32x2 FMAs on amplitude pairs); shared memory only transposes the
+// tile between rounds.  The shared tile is swizzled (16-byte chunk index XOR
+// the 32-amplitude group index) so both access shapes are conflict-free.
+//
+// Global indices are 32-bit element offsets inside one state (n <= 30).
+// Layout FULL: tile bits == global bits [0, TB) (the first pass of a layer,
+// tile t covers elements [t 2^TB, (t+1) 2^TB)).  Layout STRIDED: tile bits
+// [0, c) -> global [0, c), tile bits [c, TB) -> global [a, a + TB - c).
+//
+// Accumulation: energies and gradients sum one thread's products and one
+// warp's lanes in the amplitude precision, then everything above a warp in
+// FP64 in a fixed order (deterministic).
+#pragma once
+#include <cstdint>
+
+#include "gvqe_engine.cuh"
+
+namespace gvqe {
+
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+  using type = float2;
+};
+template <>
+struct V2<double> {
+  using type = double2;
+};
+
+constexpr int ROUND = 32;  // amplitudes per thread per round (5 register bits)
+
+// ------------------------------------------------------------- f32x2 ops --
+__device__ __forceinline__ unsigned long long pk(float2 v) {
+  return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
+}
+__device__ __forceinline__ unsigned long long pk(float a, float b) {
+  return ((unsigned long long)__float_as_uint(b) << 32) | __float_as_uint(a);
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+  return make_float2(__uint_as_float((unsigned)r), __uint_as_float((unsigned)(r >> 32)));
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+// --------------------------------------------------------- register block --
+// 32 amplitudes of one round; register bit j of the element index k is mapped
+// to a tile bit by the round.
+template <typename T>
+struct Reg32;
+
+// float: element k lives in v[k >> 1].x / .y, so register bits >= 1 pair whole
+// float2 values and run as packed f32x2 arithmetic.
+template <>
+struct Reg32<float> {
+  float2 v[16];
+  __device__ __forceinline__ float get(int k) const { return (k & 1) ? v[k >> 1].y : v[k >> 1].x; }
+  __device__ __forceinline__ void set(int k, float x) {
+    if (k & 1)
+      v[k >> 1].y = x;
+    else
+      v[k >> 1].x = x;
+  }
+  // RY on register bit JB: (a, b) -> (c a - s b, s a + c b)
+  template <int JB>
+  __device__ __forceinline__ void rot(float c, float s) {
+    if constexpr (JB == 0) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const float a = v[m].x, b = v[m].y;
+        v[m].x = c * a - s * b;
+        v[m].y = s * a + c * b;
+      }
+    } else {
+      constexpr int B = 1 << (JB - 1);
+      const unsigned long long c2 = pk(c, c), s2 = pk(s, s), ns2 = pk(-s, -s);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m & B) continue;
+        const unsigned long long a = pk(v[m]), b = pk(v[m | B]);
+        v[m] = upk(fma2(ns2, b, mul2(c2, a)));
+        v[m | B] = upk(fma2(s2, a, mul2(c2, b)));
+      }
+    }
+  }
+  // unnormalised Walsh-Hadamard butterfly: (a, b) -> (a + b, a - b)
+  template <int JB>
+  __device__ __forceinline__ void wht() {
+    if constexpr (JB == 0) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const float a = v[m].x, b = v[m].y;
+        v[m].x = a + b;
+        v[m].y = a - b;
+      }
+    } else {
+      constexpr int B = 1 << (JB - 1);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m & B) continue;
+        const unsigned long long a = pk(v[m]), b = pk(v[m | B]);
+        v[m] = upk(add2(a, b));
+        v[m | B] = upk(sub2(a, b));
+      }
+    }
+  }
+  // this = psi: sum over pairs (k0, k1 = k0 | bit) of lam[k1] psi[k0] - lam[k0] psi[k1]
+  template <int JB>
+  __device__ __forceinline__ float grad(const Reg32 &lam) const {
+    if constexpr (JB == 0) {
+      float acc = 0.f;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) acc += lam.v[m].y * v[m].x - lam.v[m].x * v[m].y;
+      return acc;
+    } else {
+      constexpr int B = 1 << (JB - 1);
+      unsigned long long p = 0, q = 0;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m & B) continue;
+        p = fma2(pk(lam.v[m | B]), pk(v[m]), p);
+        q = fma2(pk(lam.v[m]), pk(v[m | B]), q);
+      }
+      const float2 r = upk(sub2(p, q));
+      return r.x + r.y;
+    }
+  }
+};
+
+template <>
+struct Reg32<double> {
+  double v[32];
+  __device__ __forceinline__ double get(int k) const { return v[k]; }
+  __device__ __forceinline__ void set(int k, double x) { v[k] = x; }
+  template <int JB>
+  __device__ __forceinline__ void rot(double c, double s) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k & (1 << JB)) continue;
+      const double a = v[k], b = v[k | (1 << JB)];
+      v[k] = c * a - s * b;
+      v[k | (1 << JB)] = s * a + c * b;
+    }
+  }
+  template <int JB>
+  __device__ __forceinline__ void wht() {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k & (1 << JB)) continue;
+      const double a = v[k], b = v[k | (1 << JB)];
+      v[k] = a + b;
+      v[k | (1 << JB)] = a - b;
+    }
+  }
+  template <int JB>
+  __device__ __forceinline__ double grad(const Reg32 &lam) const {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k & (1 << JB)) continue;
+      acc += lam.v[k | (1 << JB)] * v[k] - lam.v[k] * v[k | (1 << JB)];
+    }
+    return acc;
+  }
+};
+
+// ----------------------------------------------------------------- helpers --
+template <typename T>
+__device__ __forceinline__ int swz(int i) {
+  constexpr int CH = 16 / (int)sizeof(T);  // amplitudes per 16-byte chunk
+  return i ^ (((i >> 5) & 7) * CH);
+}
+
+__device__ __forceinline__ uint32_t tile_of_block(uint32_t bx, uint32_t tiles, bool pair) {
+  if (!pair || tiles < 2) return bx;
+  const uint32_t u = bx >> 1;
+  return (bx & 1) ? (u ^ (tiles - 1)) : u;
+}
+
+__device__ __forceinline__ uint32_t tile_base(uint32_t t, int c, int a, int tb) {
+  const int lo = a - c;
+  const uint32_t tlo = t & ((1u << lo) - 1);
+  const uint32_t thi = t >> lo;
+  return (tlo << c) | (thi << (a + tb - c));
+}
+
+// x = A^-1 y for the linear CX chain (y = prefix XOR of x); n <= 30 so 32 bits suffice.
+__device__ __forceinline__ uint32_t cx_inv(uint32_t y, uint32_t nmask) { return (y ^ (y << 1)) & nmask; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Global offset of a tile bit under the STRIDED layout.
+__device__ __forceinline__ uint32_t gbit(int t, int c, int a) { return 1u << (t < c ? t : a + t - c); }
+
+template <int NB, bool WHT, typename T, typename T2>
+__device__ __forceinline__ void round_gates(Reg32<T> &r, const T2 *gcs, uint32_t gmask, int tbit0, bool inverse) {
+#define GVQE_GATE(J)                                         \
+  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) {             \
+    if (WHT) {                                               \
+      r.template wht<J>();                                   \
+    } else {                                                 \
+      const T2 cs = gcs[tbit0 + J];                          \
+      r.template rot<J>(cs.x, inverse ? -cs.y : cs.y);       \
+    }                                                        \
+  }
+  GVQE_GATE(0)
+  GVQE_GATE(1)
+  GVQE_GATE(2)
+  GVQE_GATE(3)
+  GVQE_GATE(4)
+#undef GVQE_GATE
+}
+
+// Gradient partials of one round, reduced over the warp; lane 0 stores them.
+template <int NB, typename T>
+__device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> &lam, uint32_t gmask, int tbit0,
+                                            double *wred, int lane) {
+#define GVQE_GRAD(J)                                        \
+  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) {            \
+    const T gsum = warp_sum(psi.template grad<J>(lam));     \
+    if (lane == 0) wred[tbit0 + J] = (double)gsum;          \
+  }
+  GVQE_GRAD(0)
+  GVQE_GRAD(1)
+  GVQE_GRAD(2)
+  GVQE_GRAD(3)
+  GVQE_GRAD(4)
+#undef GVQE_GRAD
+}
+
+// --------------------------------------------------- shared-memory rounds --
+// Round L: element k of thread (lane, warp w) is tile index lane + 32 k + 1024 w.
+template <typename T>
+__device__ __forceinline__ void sts_L(T *s, int lane, int w, const Reg32<T> &r) {
+  constexpr int CH = 16 / (int)sizeof(T);
+#pragma unroll
+  for (int k = 0; k < ROUND; ++k) s[(lane ^ ((k & 7) * CH)) + 32 * k + 1024 * w] = r.get(k);
+}
+template <typename T>
+__device__ __forceinline__ void lds_L(const T *s, int lane, int w, Reg32<T> &r) {
+  constexpr int CH = 16 / (int)sizeof(T);
+#pragma unroll
+  for (int k = 0; k < ROUND; ++k) r.set(k, s[(lane ^ ((k & 7) * CH)) + 32 * k + 1024 * w]);
+}
+// Round M: group G's 32 consecutive amplitudes as 16-byte chunks in swizzled order.
+__device__ __forceinline__ void lds_M(const float *s, int G, Reg32<float> &r) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float4 q = *reinterpret_cast<const float4 *>(s + (G << 5) + ((c ^ (G & 7)) << 2));
+    r.v[2 * c] = make_float2(q.x, q.y);
+    r.v[2 * c + 1] = make_float2(q.z, q.w);
+  }
+}
+__device__ __forceinline__ void sts_M(float *s, int G, const Reg32<float> &r) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    *reinterpret_cast<float4 *>(s + (G << 5) + ((c ^ (G & 7)) << 2)) =
+        make_float4(r.v[2 * c].x, r.v[2 * c].y, r.v[2 * c + 1].x, r.v[2 * c + 1].y);
+}
+__device__ __forceinline__ void lds_M(const double *s, int G, Reg32<double> &r) {
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const double2 q = *reinterpret_cast<const double2 *>(s + (G << 5) + ((c ^ (G & 7)) << 1));
+    r.v[2 * c] = q.x;
+    r.v[2 * c + 1] = q.y;
+  }
+}
+__device__ __forceinline__ void sts_M(double *s, int G, const Reg32<double> &r) {
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+    *reinterpret_cast<double2 *>(s + (G << 5) + ((c ^ (G & 7)) << 1)) = make_double2(r.v[2 * c], r.v[2 * c + 1]);
+}
+// Round H: thread tid handles groups gidx = tid + it*NT; element k = it<<H | j is tile index gidx + (j<<10).
+template <int TB>
+__device__ __forceinline__ int gidx_H(int tid, int k) {
+  constexpr int H = TB - 10;
+  constexpr int NT = 1 << (TB - 5);
+  return tid + (k >> H) * NT;
+}
+template <int TB, typename T>
+__device__ __forceinline__ void lds_H(const T *s, int tid, Reg32<T> &r) {
+  constexpr int H = TB - 10;
+#pragma unroll
+  for (int k = 0; k < ROUND; ++k) {
+    const int g = gidx_H<TB>(tid, k);
+    r.set(k, s[swz<T>(g) + ((k & ((1 << H) - 1)) << 10)]);
+  }
+}
+template <int TB, typename T>
+__device__ __forceinline__ void sts_H(T *s, int tid, const Reg32<T> &r) {
+  constexpr int H = TB - 10;
+#pragma unroll
+  for (int k = 0; k < ROUND; ++k) {
+    const int g = gidx_H<TB>(tid, k);
+    s[swz<T>(g) + ((k & ((1 << H) - 1)) << 10)] = r.get(k);
+  }
+}
+
+// Global element offsets of a thread's round-L and round-H elements.
+template <int TB, bool FULL>
+struct GIdx {
+  uint32_t baseL;   // offset of element k = 0 in round L
+  uint32_t SL[5];   // offset of register bit j in round L
+  uint32_t SH[5];   // offset of register bit j (< H) in round H
+  int c, a;
+  uint32_t tbase;
+  __device__ __forceinline__ void init(uint32_t tb_, int c_, int a_, int lane, int w) {
+    tbase = tb_;
+    c = c_;
+    a = a_;
+    if (FULL) {
+      baseL = tbase + lane + (w << 10);
+    } else {
+      uint32_t lo = 0;
+#pragma unroll
+      for (int b = 0; b < 5; ++b)
+        if ((lane >> b) & 1) lo += gbit(b, c, a);
+      uint32_t wo = 0;
+#pragma unroll
+      for (int b = 0; b < TB - 10; ++b)
+        if ((w >> b) & 1) wo += gbit(10 + b, c, a);
+      baseL = tbase + lo + wo;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) SL[j] = gbit(5 + j, c, a);
+#pragma unroll
+      for (int j = 0; j < 5; ++j) SH[j] = (j < TB - 10) ? gbit(10 + j, c, a) : 0u;
+    }
+  }
+  __device__ __forceinline__ uint32_t L(int k) const {
+    if (FULL) return baseL + 32u * k;
+    uint32_t o = baseL;
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+      if ((k >> j) & 1) o += SL[j];
+    return o;
+  }
+  // offset of group gidx's element j = 0 in round H (the tile bits 0..9 of gidx)
+  __device__ __forceinline__ uint32_t Hbase(int gidx) const {
+    if (FULL) return tbase + gidx;
+    uint32_t o = tbase;
+#pragma unroll
+    for (int b = 0; b < 10; ++b)
+      if ((gidx >> b) & 1) o += gbit(b, c, a);
+    return o;
+  }
+  __device__ __forceinline__ uint32_t Hoff(int j) const {
+    if (FULL) return (uint32_t)j << 10;
+    uint32_t o = 0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+      if ((j >> b) & 1) o += SH[b];
+    return o;
+  }
+};
+
+template <typename T2>
+__device__ __forceinline__ void load_gate_coeffs(const PassArgs &A, const T2 *cs, T2 *gcs, int tid) {
+  if (tid < 16) {
+    T2 v;
+    v.x = 1;
+    v.y = 0;
+    if (tid < A.tb && ((A.gate_mask >> tid) & 1u)) {
+      const int q = tid < A.c ? tid : A.a + tid - A.c;
+      v = cs[A.layer * A.n + q];
+    }
+    gcs[tid] = v;
+  }
+}
+
+// Layer-0 product state psi_0(x) = prod_q f_q(x_q), f(0) = cos(t/2), f(1) = sin(t/2), tabulated
+// per tile: bits 0..6 (lo), bits 7..TB-1 (mid), bit TB together with the tile's bits above (hi).
+template <typename T, typename T2, int TB>
+struct L0Tables {
+  T lo[128];
+  T mid[128];
+  T hi[2];
+  __device__ __forceinline__ void build(const T2 *l0, int n, uint32_t xbase, int tid, int nthreads) {
+    for (int m = tid; m < 256; m += nthreads) {
+      const int hi7 = m >> 7, mm = m & 127;
+      T p = T(1);
+      const int q0 = hi7 ? 7 : 0;
+      const int q1 = hi7 ? TB : 7;
+      for (int q = q0; q < q1 && q < n; ++q) p *= ((mm >> (q - q0)) & 1) ? l0[q].y : l0[q].x;
+      if (hi7)
+        mid[mm] = p;
+      else
+        lo[mm] = p;
+    }
+    if (tid < 2) {
+      T p = T(1);
+      if (TB < n) p = tid ? l0[TB].y : l0[TB].x;
+      for (int q = TB + 1; q < n; ++q) p *= ((xbase >> q) & 1) ? l0[q].y : l0[q].x;
+      hi[tid] = p;
+    }
+  }
+  __device__ __forceinline__ T operator()(uint32_t x) const {
+    return lo[x & 127] * mid[(x >> 7) & ((1u << (TB - 7)) - 1)] * hi[(x >> TB) & 1];
+  }
+};
+
+// ------------------------------------------------------ forward tile pass --
+template <typename T, int TB, bool FULL, int LOAD, bool WHT>
+__global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 8 : 4) / (sizeof(T) == 8 ? 2 : 1))
+k_fwd(const PassArgs A) {
+  using T2 = typename V2<T>::type;
+  constexpr int NT = 1 << (TB - 5);
+  constexpr int NW = NT / 32;
+  constexpr int H = TB - 10;
+  constexpr bool L0 = (LOAD == LD_L0 || LOAD == LD_L0_GATHER);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *s = reinterpret_cast<T *>(smem_raw);
+  __shared__ T2 gcs[16];
+  __shared__ double ered[NW];
+  __shared__ L0Tables<T, T2, TB> tab;
+
+  const int job = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t t = tile_of_block(blockIdx.x, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
+  const uint32_t tbase = tile_base(t, A.c, A.a, TB);
+  const uint32_t nmask = (A.n >= 32) ? 0xffffffffu : ((1u << A.n) - 1);
+  const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
+  if (!WHT) load_gate_coeffs(A, cs, gcs, tid);
+  if constexpr (L0) {
+    const uint32_t xbase = (LOAD == LD_L0_GATHER) ? cx_inv(tbase, nmask) : tbase;
+    tab.build(cs, A.n, xbase, tid, NT);
+  }
+  __syncthreads();
+  const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
+  T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
+  const uint32_t gm = A.gate_mask;
+  GIdx<TB, FULL> gi;
+  gi.init(tbase, A.c, A.a, lane, w);
+
+  Reg32<T> r;
+  // round L: global -> registers (tile bits 5..9) -> gates -> shared
+#pragma unroll
+  for (int k = 0; k < ROUND; ++k) {
+    const uint32_t y = gi.L(k);
+    T v;
+    if constexpr (LOAD == LD_PLAIN)
+      v = in[y];
+    else if constexpr (LOAD == LD_GATHER)
+      v = in[cx_inv(y, nmask)];
+    else if constexpr (LOAD == LD_L0_GATHER)
+      v = tab(cx_inv(y, nmask));
+    else
+      v = tab(y);
+    r.set(k, v);
+  }
+  round_gates<5, WHT>(r, gcs, gm, 5, false);
+  sts_L(s, lane, w, r);
+  __syncthreads();
+  // round M: tile bits 0..4
+  if (gm & 0x1Fu) {
+    lds_M(s, tid, r);
+    round_gates<5, WHT>(r, gcs, gm, 0, false);
+    sts_M(s, tid, r);
+    __syncthreads();
+  }
+  // round H: tile bits 10..TB-1, then the store and the energy epilogue
+  lds_H<TB>(s, tid, r);
+  round_gates<H, WHT>(r, gcs, gm, 10, false);
+  const T *table = reinterpret_cast<const T *>(A.table);
+  const bool store = A.store_mode != ST_NONE;
+  const bool energy = (A.flags & F_ENERGY) != 0;
+  T eacc = T(0);
+#pragma unroll
+  for (int it = 0; it < (1 << (15 - TB)); ++it) {
+    const uint32_t hb = gi.Hbase(tid + it * NT);
+#pragma unroll
+    for (int j = 0; j < (1 << H); ++j) {
+      const int k = (it << H) | j;
+      const uint32_t y = hb + gi.Hoff(j);
+      const T v = r.get(k);
+      if (store) out[y] = v;
+      if (energy) eacc += v * v * table[y];
+    }
+  }
+  if (energy) {
+    eacc = warp_sum(eacc);
+    if (lane == 0) ered[w] = (double)eacc;
+    __syncthreads();
+    if (tid == 0) {
+      double e = 0.0;
+#pragma unroll
+      for (int ww = 0; ww < NW; ++ww) e += ered[ww];
+      A.epart[(size_t)job * A.part_stride + t] = e;
+    }
+  }
+}
+
+// ------------------------------------------------------ backward tile pass --
+// lambda and psi are both at the point right after this pass's gates.  Rounds
+// L, M, H read both and form the gradients (all at that same point); round H
+// then applies RY(-theta) to lambda on its bits, rounds M and L follow on
+// theirs, and round L writes lambda (through the inverse CX chain for the
+// first pass of a layer, layout FULL).
+template <typename T, int TB, bool FULL>
+__global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 4 : 2) / (sizeof(T) == 8 ? 2 : 1))
+k_bwd(const PassArgs A) {
+  using T2 = typename V2<T>::type;
+  constexpr int NT = 1 << (TB - 5);
+  constexpr int NW = NT / 32;
+  constexpr int H = TB - 10;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sp = reinterpret_cast<T *>(smem_raw);
+  T *sl = sp + (1 << TB);
+  __shared__ T2 gcs[16];
+  __shared__ double gred[NW][16];
+  __shared__ double ered[NW];
+
+  const int job = blockIdx.y;
+  if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.layer < A.minlayer[A.job0 + job]) return;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t t = tile_of_block(blockIdx.x, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
+  const uint32_t tbase = tile_base(t, A.c, A.a, TB);
+  const uint32_t nmask = (1u << A.n) - 1;
+  const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
+  load_gate_coeffs(A, cs, gcs, tid);
+  __syncthreads();
+  const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
+  const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
+  const T *table = reinterpret_cast<const T *>(A.table);
+  T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
+  const uint32_t gm = A.gate_mask;
+  const bool init = (A.flags & F_LAMBDA_INIT) != 0;
+  GIdx<TB, FULL> gi;
+  gi.init(tbase, A.c, A.a, lane, w);
+
+  Reg32<T> psi, lam;
+  T eacc = T(0);
+  // round L
+  if (init) {
+#pragma unroll
+    for (int k = 0; k < ROUND; ++k) {
+      const uint32_t y = gi.L(k);
+      const T p = in[y];
+      const T l = table[y] * p;
+      psi.set(k, p);
+      lam.set(k, l);
+      eacc += p * l;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < ROUND; ++k) {
+      const uint32_t y = gi.L(k);
+      psi.set(k, in[y]);
+      lam.set(k, lin[y]);
+    }
+  }
+  round_grads<5>(psi, lam, gm, 5, gred[w], lane);
+  sts_L(sp, lane, w, psi);
+  sts_L(sl, lane, w, lam);
+  if (A.flags & F_ENERGY) {
+    eacc = warp_sum(eacc);
+    if (lane == 0) ered[w] = (double)eacc;
+  }
+  __syncthreads();
+  // round M (gradients only)
+  if (gm & 0x1Fu) {
+    lds_M(sp, tid, psi);
+    lds_M(sl, tid, lam);
+    round_grads<5>(psi, lam, gm, 0, gred[w], lane);
+  }
+  // round H: gradients, then RY(-theta) on lambda
+  lds_H<TB>(sp, tid, psi);
+  lds_H<TB>(sl, tid, lam);
+  round_grads<H>(psi, lam, gm, 10, gred[w], lane);
+  round_gates<H, false>(lam, gcs, gm, 10, true);
+  __syncthreads();  // every thread has read the tile before lambda is overwritten
+  sts_H<TB>(sl, tid, lam);
+  __syncthreads();
+  if (gm & 0x1Fu) {
+    lds_M(sl, tid, lam);
+    round_gates<5, false>(lam, gcs, gm, 0, true);
+    sts_M(sl, tid, lam);
+    __syncthreads();
+  }
+  lds_L(sl, lane, w, lam);
+  round_gates<5, false>(lam, gcs, gm, 5, true);
+#pragma unroll
+  for (int k = 0; k < ROUND; ++k) {
+    const uint32_t y = gi.L(k);
+    if constexpr (FULL)
+      out[cx_inv(y, nmask)] = lam.get(k);
+    else
+      out[y] = lam.get(k);
+  }
+
+  double *part = A.part + (size_t)job * A.part_stride;
+  if (tid < TB && ((gm >> tid) & 1u)) {
+    double g = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) g += gred[ww][tid];
+    part[(size_t)tid * A.tiles + t] = g;
+  }
+  if ((A.flags & F_ENERGY) && tid == 0) {
+    double e = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) e += ered[ww];
+    A.epart[(size_t)job * A.part_stride + t] = e;
+  }
+}
+
+// ------------------------------------------------ layer-0 gradient pass --
+// g_{0,q} = sum_x lambda_0[x] prod_{q' != q} f_q'(x_q') d_q(x_q) with
+// f(0) = cos(t/2), f(1) = sin(t/2), d(0) = -sin(t/2), d(1) = cos(t/2): the
+// adjoint formula evaluated against the layer-0 product state.  The tile is
+// global bits [0, TB); the product over the register bits 5..9 is tabulated.
+template <typename T, int TB>
+__global__ void __launch_bounds__(1 << (TB - 5)) k_grad_l0(const PassArgs A) {
+  using T2 = typename V2<T>::type;
+  constexpr int NT = 1 << (TB - 5);
+  constexpr int NW = NT / 32;
+  constexpr int NV = 11;  // per-thread values reduced over the warp
+  __shared__ T2 l0cs[32];
+  __shared__ T RF[ROUND], RD[5][ROUND];
+  __shared__ double wv[NW][NV];
+  __shared__ double ered[NW];
+  __shared__ double fhi_d[32];
+  __shared__ double fhi_all;
+
+  const int job = blockIdx.y;
+  if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.minlayer[A.job0 + job] > 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t t = blockIdx.x;
+  const int n = A.n;
+  const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
+  if (tid < n) l0cs[tid] = cs[tid];
+  __syncthreads();
+  if (tid < ROUND) {
+    T f = T(1);
+    for (int j = 0; j < 5; ++j) {
+      const T2 c = l0cs[5 + j];
+      f *= ((tid >> j) & 1) ? c.y : c.x;
+    }
+    RF[tid] = f;
+    for (int j = 0; j < 5; ++j) {
+      T g = T(1);
+      for (int i = 0; i < 5; ++i) {
+        const T2 c = l0cs[5 + i];
+        const int b = (tid >> i) & 1;
+        g *= (i == j) ? (b ? c.x : -c.y) : (b ? c.y : c.x);
+      }
+      RD[j][tid] = g;
+    }
+  }
+  if (tid < 32) {
+    const int q = TB + tid;
+    if (tid == 0) {
+      double f = 1.0;
+      for (int qq = TB; qq < n; ++qq) {
+        const T2 c = l0cs[qq];
+        f *= ((t >> (qq - TB)) & 1) ? (double)c.y : (double)c.x;
+      }
+      fhi_all = f;
+    }
+    if (q < n) {
+      double f = 1.0;
+      for (int qq = TB; qq < n; ++qq) {
+        const T2 c = l0cs[qq];
+        const int b = (int)((t >> (qq - TB)) & 1);
+        f *= (qq == q) ? (b ? (double)c.x : -(double)c.y) : (b ? (double)c.y : (double)c.x);
+      }
+      fhi_d[tid] = f;
+    }
+  }
+  __syncthreads();
+
+  T lane_f = T(1), lane_d[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const T2 c = l0cs[j];
+    lane_f *= ((lane >> j) & 1) ? c.y : c.x;
+  }
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    T g = T(1);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const T2 c = l0cs[i];
+      const int b = (lane >> i) & 1;
+      g *= (i == j) ? (b ? c.x : -c.y) : (b ? c.y : c.x);
+    }
+    lane_d[j] = g;
+  }
+  T warp_f = T(1);
+  for (int j = 10; j < TB; ++j) {
+    const T2 c = l0cs[j];
+    warp_f *= ((w >> (j - 10)) & 1) ? c.y : c.x;
+  }
+
+  const bool init = (A.flags & F_LAMBDA_INIT) != 0;
+  const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
+  const T *table = reinterpret_cast<const T *>(A.table);
+  const uint32_t tbase = t << TB;
+  const T fhi_t = (T)fhi_all;
+  T S = T(0), Sj[5] = {T(0), T(0), T(0), T(0), T(0)};
+  T eacc = T(0);
+#pragma unroll
+  for (int k = 0; k < ROUND; ++k) {
+    const uint32_t x = tbase + lane + 32 * k + 1024 * w;
+    T lam;
+    if (init) {
+      const T psi0 = lane_f * RF[k] * warp_f * fhi_t;
+      lam = table[x] * psi0;
+      eacc += psi0 * lam;
+    } else {
+      lam = lin[x];
+    }
+    S += lam * RF[k];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) Sj[j] += lam * RD[j][k];
+  }
+  T vals[NV];
+  vals[0] = lane_f * S;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) vals[1 + j] = lane_f * Sj[j];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) vals[6 + j] = lane_d[j] * S;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const T r = warp_sum(vals[i]);
+    if (lane == 0) wv[w][i] = (double)r;
+  }
+  if (init) {
+    eacc = warp_sum(eacc);
+    if (lane == 0) ered[w] = (double)eacc;
+  }
+  __syncthreads();
+
+  double *part = A.part + (size_t)job * A.part_stride;
+  if (tid < n) {
+    const int q = tid;
+    double g = 0.0;
+    const double fh = fhi_all;
+    for (int ww = 0; ww < NW; ++ww) {
+      double wf = 1.0, wd = 1.0;
+      for (int j = 10; j < TB; ++j) {
+        const T2 c = l0cs[j];
+        const int b = (ww >> (j - 10)) & 1;
+        const double fj = b ? (double)c.y : (double)c.x;
+        wf *= fj;
+        wd *= (j == q) ? (b ? (double)c.x : -(double)c.y) : fj;
+      }
+      if (q < 5)
+        g += wf * wv[ww][6 + q];
+      else if (q < 10)
+        g += wf * wv[ww][1 + (q - 5)];
+      else if (q < TB)
+        g += wd * wv[ww][0];
+      else
+        g += wf * wv[ww][0];
+    }
+    g *= (q < TB) ? fh : fhi_d[q - TB];
+    part[(size_t)q * A.tiles + t] = g;
+  }
+  if (init && tid == 0) {
+    double e = 0.0;
+    for (int ww = 0; ww < NW; ++ww) e += ered[ww];
+    A.epart[(size_t)job * A.part_stride + t] = e;
+  }
+}
+
+// ----------------------------------------- lambda = H psi with X-mask groups --
+// lambda[x] = E(x) psi[x] + sum_groups D_m(x ^ m) psi[x ^ m] with
+// D_m(u) = sum_{k in group} c_k (-1)^popcount(u & z_k) (c_k carries the i^#Y sign).
+template <typename T, int TB>
+__global__ void __launch_bounds__(1 << (TB - 5)) k_lambda_xy(const PassArgs A) {
+  constexpr int NT = 1 << (TB - 5);
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nterm = A.ngroups > 0 ? A.gstart[A.ngroups] - A.gstart[0] : 0;
+  const XyLayout lay = xy_layout(A.ngroups, nterm, (int)sizeof(T));
+  uint32_t *sgm = reinterpret_cast<uint32_t *>(smem_raw + lay.gm);
+  int *sgs = reinterpret_cast<int *>(smem_raw + lay.gs);
+  uint32_t *stz = reinterpret_cast<uint32_t *>(smem_raw + lay.tz);
+  T *stc = reinterpret_cast<T *>(smem_raw + lay.tc);
+  __shared__ double ered[NW];
+  const int job = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t t = blockIdx.x;
+  const int t0 = A.ngroups > 0 ? A.gstart[0] : 0;
+  for (int i = tid; i < A.ngroups; i += NT) sgm[i] = A.gmask[i];
+  for (int i = tid; i <= A.ngroups; i += NT) sgs[i] = A.gstart[i] - t0;
+  for (int i = tid; i < nterm; i += NT) {
+    stz[i] = A.tz[t0 + i];
+    stc[i] = reinterpret_cast<const T *>(A.tc)[t0 + i];
+  }
+  __syncthreads();
+  const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
+  const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
+  const T *table = reinterpret_cast<const T *>(A.table);
+  T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
+  const uint32_t tbase = t << TB;
+  T eacc = T(0);
+  for (int k = 0; k < ROUND; ++k) {
+    const uint32_t x = tbase + lane + 32 * k + 1024 * w;
+    const T p = in[x];
+    T acc = (A.flags & F_ACCUM) ? lin[x] : table[x] * p;
+    for (int g = 0; g < A.ngroups; ++g) {
+      const uint32_t u = x ^ sgm[g];
+      const T pu = in[u];
+      T d = T(0);
+      for (int j = sgs[g]; j < sgs[g + 1]; ++j) d += (__popc(u & stz[j]) & 1) ? -stc[j] : stc[j];
+      acc += d * pu;
+    }
+    if (A.flags & F_WRITE_LAMBDA) out[x] = acc;
+    eacc += p * acc;
+  }
+  if (A.flags & F_ENERGY) {
+    eacc = warp_sum(eacc);
+    if (lane == 0) ered[w] = (double)eacc;
+    __syncthreads();
+    if (tid == 0) {
+      double e = 0.0;
+      for (int ww = 0; ww < NW; ++ww) e += ered[ww];
+      A.epart[(size_t)job * A.part_stride + t] = e;
+    }
+  }
+}
+
+// ------------------------------------------------------------- launcher --
+template <typename K>
+static cudaError_t launch_k(K k, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const PassArgs &A) {
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<grid, block, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename T, int TB>
+cudaError_t launch_tb(const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
+  const dim3 grid((unsigned)A.tiles, (unsigned)jobs);
+  const dim3 block(1 << (TB - 5));
+  const size_t tile = sizeof(T) << TB;
+  const bool full = A.c >= TB;
+  switch (A.kind) {
+    case K_FWD:
+      if (!full) {
+        if (A.load_mode != LD_PLAIN) return cudaErrorInvalidValue;
+        return launch_k(k_fwd<T, TB, false, LD_PLAIN, false>, grid, block, tile, s, A);
+      }
+      switch (A.load_mode) {
+        case LD_PLAIN: return launch_k(k_fwd<T, TB, true, LD_PLAIN, false>, grid, block, tile, s, A);
+        case LD_GATHER: return launch_k(k_fwd<T, TB, true, LD_GATHER, false>, grid, block, tile, s, A);
+        case LD_L0_GATHER: return launch_k(k_fwd<T, TB, true, LD_L0_GATHER, false>, grid, block, tile, s, A);
+        case LD_L0: return launch_k(k_fwd<T, TB, true, LD_L0, false>, grid, block, tile, s, A);
+        default: return cudaErrorInvalidValue;
+      }
+    case K_WHT:
+      if (full) return launch_k(k_fwd<T, TB, true, LD_PLAIN, true>, grid, block, tile, s, A);
+      return launch_k(k_fwd<T, TB, false, LD_PLAIN, true>, grid, block, tile, s, A);
+    case K_BWD:
+      // the first pass of a layer (layout FULL) writes lambda through the inverse CX chain
+      if (full != (A.store_mode == ST_SCATTER)) return cudaErrorInvalidValue;
+      if (full) return launch_k(k_bwd<T, TB, true>, grid, block, 2 * tile, s, A);
+      return launch_k(k_bwd<T, TB, false>, grid, block, 2 * tile, s, A);
+    case K_GRAD_L0:
+      return launch_k(k_grad_l0<T, TB>, grid, block, 0, s, A);
+    case K_LAMBDA_XY: {
+      const size_t smem = xy_layout(A.ngroups, nterm, (int)sizeof(T)).total;
+      if (smem > 200 * 1024) return cudaErrorInvalidValue;
+      return launch_k(k_lambda_xy<T, TB>, grid, block, smem, s, A);
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gvqe

@@ -103,7 +103,7 @@ def _layer_passes(text):
 
 
 @pytest.mark.parametrize("n,flags,tb,expect", [
-    (30, 0, 0, 3), (30, 1, 0, 3), (24, 0, 0, 2), (28, 0, 0, 3), (14, 0, 0, 1), (12, 1, 0, 1),
+    (30, 0, 0, 3), (30, 1, 0, 3), (24, 0, 0, 3), (24, 0, 12, 3), (28, 0, 0, 3), (13, 0, 0, 1), (14, 0, 0, 2), (12, 1, 0, 1),
     (20, 0, 10, 3), (16, 0, 10, 2), (9, 0, 0, 1), (1, 0, 0, 1),
 ])
 def test_plan_covers_every_qubit_once(n, flags, tb, expect):
