@@ -51,7 +51,7 @@ extern "C" {
 #define GVQE_ENT_LINEAR 0
 
 /* options for gvqe_ansatz_set_option */
-#define GVQE_OPT_TILE_BITS 1 /* log2 amplitudes per on-chip tile, 10..13; 0 = auto (13 FP32, 12 FP64) */
+#define GVQE_OPT_TILE_BITS 1 /* log2 amplitudes per on-chip tile, 10..13 (FP64: 10..12); 0 = auto (13 FP32, 12 FP64) */
 
 #define GVQE_MAX_QUBITS 30
 

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgvqe.so")
 SOURCES = ["gvqe_api.cu", "gvqe_kernels.cu"]
 # gvqe_inst.cu is compiled once per (amplitude type, tile bits) pair
-INSTANCES = [(t, tb) for t in ("float", "double") for tb in (10, 11, 12, 13)]
+INSTANCES = [("float", tb) for tb in (10, 11, 12, 13)] + [("double", tb) for tb in (10, 11, 12)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               f"-I{INCLUDE}", f"-I{CSRC}"]

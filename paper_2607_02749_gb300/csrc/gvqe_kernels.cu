@@ -320,12 +320,14 @@ __global__ void k_shift_combine(const double *__restrict__ Es, int P, int jobs, 
 }  // namespace
 
 // --------------------------------------------------------------- launchers --
-int max_tile_bits(int prec) { return 13; }
+// The backward pass holds 3 rotating tiles in shared memory (227 KiB max):
+// 2^13 FP32 (96 KiB, two CTAs per SM) or 2^12 FP64 (96 KiB).
+int max_tile_bits(int prec) { return prec ? 12 : 13; }
 
 size_t pass_smem_bytes(int prec, int kind, int tb) {
   const size_t es = prec ? 8 : 4;
   if (tb < 10) return 0;
-  if (kind == K_BWD) return 2 * (es << tb);
+  if (kind == K_BWD) return 3 * (es << tb);
   if (kind == K_FWD || kind == K_WHT) return es << tb;
   return 0;
 }
@@ -343,7 +345,9 @@ static cudaError_t launch_typed(const PassArgs &A, int jobs, int nterm, cudaStre
     case 10: return launch_tb<T, 10>(A, jobs, nterm, s);
     case 11: return launch_tb<T, 11>(A, jobs, nterm, s);
     case 12: return launch_tb<T, 12>(A, jobs, nterm, s);
-    case 13: return launch_tb<T, 13>(A, jobs, nterm, s);
+    case 13:
+      if constexpr (sizeof(T) == 4) return launch_tb<T, 13>(A, jobs, nterm, s);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

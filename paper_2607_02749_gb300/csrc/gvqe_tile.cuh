@@ -144,14 +144,16 @@ struct Reg32<float> {
       return acc;
     } else {
       constexpr int B = 1 << (JB - 1);
-      unsigned long long p = 0, q = 0;
+      unsigned long long p[2] = {0, 0}, q[2] = {0, 0};
+      int u = 0;
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         if (m & B) continue;
-        p = fma2(pk(lam.v[m | B]), pk(v[m]), p);
-        q = fma2(pk(lam.v[m]), pk(v[m | B]), q);
+        p[u & 1] = fma2(pk(lam.v[m | B]), pk(v[m]), p[u & 1]);
+        q[u & 1] = fma2(pk(lam.v[m]), pk(v[m | B]), q[u & 1]);
+        ++u;
       }
-      const float2 r = upk(sub2(p, q));
+      const float2 r = upk(sub2(add2(p[0], p[1]), add2(q[0], q[1])));
       return r.x + r.y;
     }
   }
@@ -229,6 +231,7 @@ __device__ __forceinline__ uint32_t gbit(int t, int c, int a) { return 1u << (t 
 
 template <int NB, bool WHT, typename T, typename T2>
 __device__ __forceinline__ void round_gates(Reg32<T> &r, const T2 *gcs, uint32_t gmask, int tbit0, bool inverse) {
+  // gcs[i] = (cos, sin) of tile bit i
 #define GVQE_GATE(J)                                         \
   if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) {             \
     if (WHT) {                                               \
@@ -331,62 +334,87 @@ __device__ __forceinline__ void sts_H(T *s, int tid, const Reg32<T> &r) {
   }
 }
 
+// Gray-code order of the 32 (or 2^H) register elements: consecutive elements
+// differ in one register bit, so a strided global offset advances by one add.
+__host__ __device__ constexpr int gray(int k) { return k ^ (k >> 1); }
+__host__ __device__ constexpr int gray_bit(int k) {  // register bit flipped between gray(k-1) and gray(k)
+  return (k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : (k & 8) ? 3 : 4;
+}
+
 // Global element offsets of a thread's round-L and round-H elements.
 template <int TB, bool FULL>
 struct GIdx {
   uint32_t baseL;   // offset of element k = 0 in round L
   uint32_t SL[5];   // offset of register bit j in round L
   uint32_t SH[5];   // offset of register bit j (< H) in round H
+  uint32_t cm;
   int c, a;
   uint32_t tbase;
+  __device__ __forceinline__ uint32_t g(uint32_t i) const { return tbase + (i & cm) + ((i >> c) << a); }
   __device__ __forceinline__ void init(uint32_t tb_, int c_, int a_, int lane, int w) {
     tbase = tb_;
     c = c_;
     a = a_;
+    cm = (1u << c) - 1;
     if (FULL) {
       baseL = tbase + lane + (w << 10);
     } else {
-      uint32_t lo = 0;
-#pragma unroll
-      for (int b = 0; b < 5; ++b)
-        if ((lane >> b) & 1) lo += gbit(b, c, a);
-      uint32_t wo = 0;
-#pragma unroll
-      for (int b = 0; b < TB - 10; ++b)
-        if ((w >> b) & 1) wo += gbit(10 + b, c, a);
-      baseL = tbase + lo + wo;
+      baseL = g((uint32_t)(lane + (w << 10)));
 #pragma unroll
       for (int j = 0; j < 5; ++j) SL[j] = gbit(5 + j, c, a);
 #pragma unroll
       for (int j = 0; j < 5; ++j) SH[j] = (j < TB - 10) ? gbit(10 + j, c, a) : 0u;
     }
   }
-  __device__ __forceinline__ uint32_t L(int k) const {
-    if (FULL) return baseL + 32u * k;
-    uint32_t o = baseL;
-#pragma unroll
-    for (int j = 0; j < 5; ++j)
-      if ((k >> j) & 1) o += SL[j];
-    return o;
-  }
   // offset of group gidx's element j = 0 in round H (the tile bits 0..9 of gidx)
-  __device__ __forceinline__ uint32_t Hbase(int gidx) const {
-    if (FULL) return tbase + gidx;
-    uint32_t o = tbase;
-#pragma unroll
-    for (int b = 0; b < 10; ++b)
-      if ((gidx >> b) & 1) o += gbit(b, c, a);
-    return o;
-  }
-  __device__ __forceinline__ uint32_t Hoff(int j) const {
-    if (FULL) return (uint32_t)j << 10;
-    uint32_t o = 0;
-#pragma unroll
-    for (int b = 0; b < 5; ++b)
-      if ((j >> b) & 1) o += SH[b];
-    return o;
-  }
+  __device__ __forceinline__ uint32_t Hbase(int gidx) const { return FULL ? tbase + gidx : g((uint32_t)gidx); }
 };
+
+// Visit the 32 round-L elements of a thread: f(k, global offset).  STRIDED
+// offsets are generated in Gray-code order (one add per element).
+template <int TB, bool FULL, typename F>
+__device__ __forceinline__ void for_L(const GIdx<TB, FULL> &gi, F &&f) {
+  if (FULL) {
+#pragma unroll
+    for (int k = 0; k < ROUND; ++k) f(k, gi.baseL + 32u * k);
+  } else {
+    uint32_t o = gi.baseL;
+#pragma unroll
+    for (int k = 0; k < ROUND; ++k) {
+      const int e = gray(k);
+      if (k > 0) {
+        const int j = gray_bit(k);
+        o = ((e >> j) & 1) ? o + gi.SL[j] : o - gi.SL[j];
+      }
+      f(e, o);
+    }
+  }
+}
+
+// Visit the 32 round-H elements of a thread: f(k, global offset).
+template <int TB, bool FULL, typename F>
+__device__ __forceinline__ void for_H(const GIdx<TB, FULL> &gi, int tid, F &&f) {
+  constexpr int H = TB - 10;
+  constexpr int NT = 1 << (TB - 5);
+#pragma unroll
+  for (int it = 0; it < (1 << (15 - TB)); ++it) {
+    uint32_t o = gi.Hbase(tid + it * NT);
+#pragma unroll
+    for (int jj = 0; jj < (1 << H); ++jj) {
+      int j = jj;
+      if (FULL) {
+        f((it << H) | j, o + ((uint32_t)j << 10));
+      } else {
+        j = gray(jj);
+        if (jj > 0) {
+          const int b = gray_bit(jj);
+          o = ((j >> b) & 1) ? o + gi.SH[b] : o - gi.SH[b];
+        }
+        f((it << H) | j, o);
+      }
+    }
+  }
+}
 
 template <typename T2>
 __device__ __forceinline__ void load_gate_coeffs(const PassArgs &A, const T2 *cs, T2 *gcs, int tid) {
@@ -435,7 +463,7 @@ struct L0Tables {
 
 // ------------------------------------------------------ forward tile pass --
 template <typename T, int TB, bool FULL, int LOAD, bool WHT>
-__global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 8 : 4) / (sizeof(T) == 8 ? 2 : 1))
+__global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 6 : 3) / (sizeof(T) == 8 ? 2 : 1))
 k_fwd(const PassArgs A) {
   using T2 = typename V2<T>::type;
   constexpr int NT = 1 << (TB - 5);
@@ -468,9 +496,7 @@ k_fwd(const PassArgs A) {
 
   Reg32<T> r;
   // round L: global -> registers (tile bits 5..9) -> gates -> shared
-#pragma unroll
-  for (int k = 0; k < ROUND; ++k) {
-    const uint32_t y = gi.L(k);
+  for_L(gi, [&](int k, uint32_t y) {
     T v;
     if constexpr (LOAD == LD_PLAIN)
       v = in[y];
@@ -481,7 +507,7 @@ k_fwd(const PassArgs A) {
     else
       v = tab(y);
     r.set(k, v);
-  }
+  });
   round_gates<5, WHT>(r, gcs, gm, 5, false);
   sts_L(s, lane, w, r);
   __syncthreads();
@@ -499,18 +525,11 @@ k_fwd(const PassArgs A) {
   const bool store = A.store_mode != ST_NONE;
   const bool energy = (A.flags & F_ENERGY) != 0;
   T eacc = T(0);
-#pragma unroll
-  for (int it = 0; it < (1 << (15 - TB)); ++it) {
-    const uint32_t hb = gi.Hbase(tid + it * NT);
-#pragma unroll
-    for (int j = 0; j < (1 << H); ++j) {
-      const int k = (it << H) | j;
-      const uint32_t y = hb + gi.Hoff(j);
-      const T v = r.get(k);
-      if (store) out[y] = v;
-      if (energy) eacc += v * v * table[y];
-    }
-  }
+  for_H(gi, tid, [&](int k, uint32_t y) {
+    const T v = r.get(k);
+    if (store) out[y] = v;
+    if (energy) eacc += v * v * table[y];
+  });
   if (energy) {
     eacc = warp_sum(eacc);
     if (lane == 0) ered[w] = (double)eacc;
@@ -525,21 +544,41 @@ k_fwd(const PassArgs A) {
 }
 
 // ------------------------------------------------------ backward tile pass --
+// Asynchronous 16-byte global -> shared copies (L1 bypassed).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Persistent CTAs walk the tiles blockIdx.x, +gridDim.x, ...  Each CTA owns
+// three tile-sized shared buffers that rotate: tile k reads psi from P and
+// lambda from L while the next tile's psi streams into the free buffer F
+// (issued when tile k starts) and its lambda into P (issued once round H is
+// done with psi).  Two CTAs share an SM.
+//
 // lambda and psi are both at the point right after this pass's gates.  Rounds
 // L, M, H read both and form the gradients (all at that same point); round H
 // then applies RY(-theta) to lambda on its bits, rounds M and L follow on
 // theirs, and round L writes lambda (through the inverse CX chain for the
-// first pass of a layer, layout FULL).
+// first pass of a layer, layout FULL).  Gradient and energy partials are
+// written per tile.
 template <typename T, int TB, bool FULL>
-__global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 4 : 2) / (sizeof(T) == 8 ? 2 : 1))
+__global__ void __launch_bounds__(1 << (TB - 5), (sizeof(T) == 4) ? 2 : 1)
 k_bwd(const PassArgs A) {
   using T2 = typename V2<T>::type;
   constexpr int NT = 1 << (TB - 5);
   constexpr int NW = NT / 32;
   constexpr int H = TB - 10;
+  constexpr int TILE = 1 << TB;
+  constexpr int CH = 16 / (int)sizeof(T);  // amplitudes per 16-byte chunk
+  constexpr int CPT = TILE / CH / NT;      // chunks per thread per array
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sp = reinterpret_cast<T *>(smem_raw);
-  T *sl = sp + (1 << TB);
+  T *buf = reinterpret_cast<T *>(smem_raw);  // three rotating tiles
   __shared__ T2 gcs[16];
   __shared__ double gred[NW][16];
   __shared__ double ered[NW];
@@ -547,94 +586,127 @@ k_bwd(const PassArgs A) {
   const int job = blockIdx.y;
   if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.layer < A.minlayer[A.job0 + job]) return;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const uint32_t t = tile_of_block(blockIdx.x, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
-  const uint32_t tbase = tile_base(t, A.c, A.a, TB);
+  const uint32_t tiles = (uint32_t)A.tiles;
+  const bool pair = (A.flags & F_PAIR_ORDER) != 0;
   const uint32_t nmask = (1u << A.n) - 1;
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   load_gate_coeffs(A, cs, gcs, tid);
-  __syncthreads();
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
-  const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
-  const T *table = reinterpret_cast<const T *>(A.table);
-  T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
-  const uint32_t gm = A.gate_mask;
   const bool init = (A.flags & F_LAMBDA_INIT) != 0;
-  GIdx<TB, FULL> gi;
-  gi.init(tbase, A.c, A.a, lane, w);
-
-  Reg32<T> psi, lam;
-  T eacc = T(0);
-  // round L
-  if (init) {
-#pragma unroll
-    for (int k = 0; k < ROUND; ++k) {
-      const uint32_t y = gi.L(k);
-      const T p = in[y];
-      const T l = table[y] * p;
-      psi.set(k, p);
-      lam.set(k, l);
-      eacc += p * l;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < ROUND; ++k) {
-      const uint32_t y = gi.L(k);
-      psi.set(k, in[y]);
-      lam.set(k, lin[y]);
-    }
-  }
-  round_grads<5>(psi, lam, gm, 5, gred[w], lane);
-  sts_L(sp, lane, w, psi);
-  sts_L(sl, lane, w, lam);
-  if (A.flags & F_ENERGY) {
-    eacc = warp_sum(eacc);
-    if (lane == 0) ered[w] = (double)eacc;
-  }
-  __syncthreads();
-  // round M (gradients only)
-  if (gm & 0x1Fu) {
-    lds_M(sp, tid, psi);
-    lds_M(sl, tid, lam);
-    round_grads<5>(psi, lam, gm, 0, gred[w], lane);
-  }
-  // round H: gradients, then RY(-theta) on lambda
-  lds_H<TB>(sp, tid, psi);
-  lds_H<TB>(sl, tid, lam);
-  round_grads<H>(psi, lam, gm, 10, gred[w], lane);
-  round_gates<H, false>(lam, gcs, gm, 10, true);
-  __syncthreads();  // every thread has read the tile before lambda is overwritten
-  sts_H<TB>(sl, tid, lam);
-  __syncthreads();
-  if (gm & 0x1Fu) {
-    lds_M(sl, tid, lam);
-    round_gates<5, false>(lam, gcs, gm, 0, true);
-    sts_M(sl, tid, lam);
-    __syncthreads();
-  }
-  lds_L(sl, lane, w, lam);
-  round_gates<5, false>(lam, gcs, gm, 5, true);
-#pragma unroll
-  for (int k = 0; k < ROUND; ++k) {
-    const uint32_t y = gi.L(k);
-    if constexpr (FULL)
-      out[cx_inv(y, nmask)] = lam.get(k);
-    else
-      out[y] = lam.get(k);
-  }
-
+  const T *lsrc = init ? reinterpret_cast<const T *>(A.table)
+                       : reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
+  T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
   double *part = A.part + (size_t)job * A.part_stride;
-  if (tid < TB && ((gm >> tid) & 1u)) {
-    double g = 0.0;
+  const uint32_t gm = A.gate_mask;
+  const uint32_t cm = (1u << A.c) - 1;
+
+  // copy one array of tile bx into shared tile dst (one commit group)
+  auto issue = [&](const T *src, uint32_t bx, T *dst) {
+    const uint32_t t = tile_of_block(bx, tiles, pair);
+    const uint32_t tbase = tile_base(t, A.c, A.a, TB);
 #pragma unroll
-    for (int ww = 0; ww < NW; ++ww) g += gred[ww][tid];
-    part[(size_t)tid * A.tiles + t] = g;
+    for (int m = 0; m < CPT; ++m) {
+      const uint32_t i = (uint32_t)(tid + m * NT) * CH;
+      const uint32_t go = FULL ? tbase + i : tbase + (i & cm) + ((i >> A.c) << A.a);
+      cp_async16(dst + swz<T>((int)i), src + go);
+    }
+    cp_async_commit();
+  };
+
+  uint32_t bx = blockIdx.x;
+  int P = 0, L = 1, F = 2;  // buffer roles
+  if (bx < tiles) {
+    issue(in, bx, buf + P * TILE);
+    issue(lsrc, bx, buf + L * TILE);
   }
-  if ((A.flags & F_ENERGY) && tid == 0) {
-    double e = 0.0;
+  __syncthreads();  // gate coefficients visible
+  for (; bx < tiles; bx += gridDim.x) {
+    const uint32_t nbx = bx + gridDim.x;
+    const bool more = nbx < tiles;
+    if (more)
+      issue(in, nbx, buf + F * TILE);  // next psi into the free buffer
+    else
+      cp_async_commit();
+    cp_async_wait<1>();  // this tile's psi and lambda have landed
+    __syncthreads();
+    T *sp = buf + P * TILE;
+    T *sl = buf + L * TILE;
+    const uint32_t t = tile_of_block(bx, tiles, pair);
+    GIdx<TB, FULL> gi;
+    gi.init(tile_base(t, A.c, A.a, TB), A.c, A.a, lane, w);
+
+    Reg32<T> psi, lam;
+    // round L (from shared)
+    lds_L(sp, lane, w, psi);
+    lds_L(sl, lane, w, lam);
+    if (init) {
+      T eacc = T(0);
 #pragma unroll
-    for (int ww = 0; ww < NW; ++ww) e += ered[ww];
-    A.epart[(size_t)job * A.part_stride + t] = e;
+      for (int k = 0; k < ROUND; ++k) {
+        const T p = psi.get(k);
+        const T l = lam.get(k) * p;  // the buffer holds the table: lambda = E(x) psi
+        lam.set(k, l);
+        eacc += p * l;
+      }
+      sts_L(sl, lane, w, lam);
+      eacc = warp_sum(eacc);
+      if (lane == 0) ered[w] = (double)eacc;
+    }
+    round_grads<5>(psi, lam, gm, 5, gred[w], lane);
+    if (init) __syncthreads();  // lambda = E psi is in shared before round M reads it
+    // round M (gradients only)
+    if (gm & 0x1Fu) {
+      lds_M(sp, tid, psi);
+      lds_M(sl, tid, lam);
+      round_grads<5>(psi, lam, gm, 0, gred[w], lane);
+    }
+    // round H: gradients, then RY(-theta) on lambda
+    lds_H<TB>(sp, tid, psi);
+    lds_H<TB>(sl, tid, lam);
+    round_grads<H>(psi, lam, gm, 10, gred[w], lane);
+    round_gates<H, false>(lam, gcs, gm, 10, true);
+    __syncthreads();  // psi fully read; lambda may be overwritten
+    if (more)
+      issue(lsrc, nbx, sp);  // next lambda into the psi buffer
+    else
+      cp_async_commit();
+    sts_H<TB>(sl, tid, lam);
+    __syncthreads();
+    if (gm & 0x1Fu) {
+      lds_M(sl, tid, lam);
+      round_gates<5, false>(lam, gcs, gm, 0, true);
+      sts_M(sl, tid, lam);
+      __syncthreads();
+    }
+    lds_L(sl, lane, w, lam);
+    round_gates<5, false>(lam, gcs, gm, 5, true);
+    for_L(gi, [&](int k, uint32_t y) {
+      if constexpr (FULL)
+        out[cx_inv(y, nmask)] = lam.get(k);
+      else
+        out[y] = lam.get(k);
+    });
+    __syncthreads();  // gred / ered complete, lambda buffer fully read
+    if (tid < TB && ((gm >> tid) & 1u)) {
+      double g = 0.0;
+#pragma unroll
+      for (int ww = 0; ww < NW; ++ww) g += gred[ww][tid];
+      part[(size_t)tid * tiles + t] = g;
+    }
+    if ((A.flags & F_ENERGY) && tid == 0) {
+      double e = 0.0;
+#pragma unroll
+      for (int ww = 0; ww < NW; ++ww) e += ered[ww];
+      A.epart[(size_t)job * A.part_stride + t] = e;
+    }
+    // rotate: next psi is in F, next lambda in P, the lambda buffer becomes free
+    const int nP = F, nL = P, nF = L;
+    P = nP;
+    L = nL;
+    F = nF;
+    __syncthreads();  // gred / ered may be reused
   }
+  cp_async_wait<0>();
 }
 
 // ------------------------------------------------ layer-0 gradient pass --
@@ -856,9 +928,19 @@ __global__ void __launch_bounds__(1 << (TB - 5)) k_lambda_xy(const PassArgs A) {
 }
 
 // ------------------------------------------------------------- launcher --
+inline int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  }
+  return n;
+}
+
 template <typename K>
 static cudaError_t launch_k(K k, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const PassArgs &A) {
-  if (smem > 48 * 1024) {
+  if (smem > 0) {  // dynamic + static shared memory may cross the 48 KiB default
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -888,11 +970,18 @@ cudaError_t launch_tb(const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
     case K_WHT:
       if (full) return launch_k(k_fwd<T, TB, true, LD_PLAIN, true>, grid, block, tile, s, A);
       return launch_k(k_fwd<T, TB, false, LD_PLAIN, true>, grid, block, tile, s, A);
-    case K_BWD:
+    case K_BWD: {
       // the first pass of a layer (layout FULL) writes lambda through the inverse CX chain
       if (full != (A.store_mode == ST_SCATTER)) return cudaErrorInvalidValue;
-      if (full) return launch_k(k_bwd<T, TB, true>, grid, block, 2 * tile, s, A);
-      return launch_k(k_bwd<T, TB, false>, grid, block, 2 * tile, s, A);
+      // persistent CTAs: as many as fit on the device at once, split over the jobs
+      const int per_sm = (sizeof(T) == 4) ? 2 : 1;
+      long long ctas = (long long)num_sms() * per_sm / jobs;
+      if (ctas < 1) ctas = 1;
+      if (ctas > A.tiles) ctas = A.tiles;
+      const dim3 pgrid((unsigned)ctas, (unsigned)jobs);
+      if (full) return launch_k(k_bwd<T, TB, true>, pgrid, block, 3 * tile, s, A);
+      return launch_k(k_bwd<T, TB, false>, pgrid, block, 3 * tile, s, A);
+    }
     case K_GRAD_L0:
       return launch_k(k_grad_l0<T, TB>, grid, block, 0, s, A);
     case K_LAMBDA_XY: {
