@@ -62,6 +62,17 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks (a timed region's duration), or value itself alone."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -152,7 +163,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("gvqe_kernels.cu", "gvqe_engine.cuh"):
+    for f in ("gvqe_tile.cuh", "gvqe_kernels.cu", "gvqe_engine.cuh"):
         with open(os.path.join(ROOT, "paper_2607_02749_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -268,11 +279,7 @@ def run_gvqe(args):
     clk = clocks.stop()
     _lib.gvqe_profile_enable(False)
     launches = _lib.gvqe_launch_count() - n_launch0
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     units = ws * B * args.steps
     value = units / (ms / 1000.0)
 
@@ -311,11 +318,7 @@ def run_gvqe(args):
         e_host.copy_(e_d, non_blocking=True)
         g_host.copy_(g_d, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e = {"value": ws * B * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": B * P * 8,
            "d2h_bytes_per_step": B * 8 + B * P * 8}
 
