@@ -147,6 +147,30 @@ int gvqe_batch_create(int n_inst, const gvqe_ansatz *ansatze, const gvqe_hamilto
 int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *const *masks,
                    double *energies, double *const *grads, void *stream);
 
+/*
+ * gvqe_energy_static -- the energies of gvqe_energy, computed without any
+ * device allocation.  The paper has no counterpart: this is for callers that
+ * cannot allocate device memory when they need an energy (inside a stream
+ * capture that must not allocate, under a runtime that owns every device
+ * allocation of the process or enforces a fixed memory budget, or in a loop
+ * that cannot afford the first-call workspace allocation of gvqe_energy).
+ *   a, h:     handles as for gvqe_energy; h must be diagonal (I/Z letters only,
+ *             else GVQE_EUNSUPPORTED).
+ *   params:   device, batch x P doubles.  energies: device, batch doubles.
+ *   flags:    GVQE_FP32 or GVQE_FP64.  stream: cudaStream_t as void*.
+ * All scratch (diagonal table, trig table, state vectors, partial sums) comes
+ * from one file-scope device array of GVQE_STATIC_SCRATCH_BYTES that every GPU
+ * loading this library holds until the process exits; requests that need more
+ * (about n <= 19 at batch 1) return GVQE_EINVAL with the required size.  The
+ * first call on each device looks up the array's device address (make it
+ * before any stream capture).  Every call reuses the same array and clears what
+ * must start at zero; calls whose GPU work overlaps in time race on it.
+ * Errors: GVQE_EINVAL, GVQE_EUNSUPPORTED, GVQE_ECUDA.
+ */
+#define GVQE_STATIC_SCRATCH_BYTES (16 * 1024 * 1024)
+int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int batch,
+                       double *energies, int flags, void *stream);
+
 /* gvqe_destroy -- free any handle above; NULL is accepted.  Synchronises the
  * device work the handle enqueued before freeing its memory. */
 int gvqe_destroy(void *handle);

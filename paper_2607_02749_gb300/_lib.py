@@ -28,6 +28,7 @@ GVQE_GRAD_PARAM_SHIFT = 0x2
 GVQE_ENT_LINEAR = 0
 GVQE_OPT_TILE_BITS = 1
 GVQE_MAX_QUBITS = 30
+GVQE_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 GVQE_PROF_FWD = 0
 GVQE_PROF_BWD = 1
 GVQE_PROF_GRAD_L0 = 2
@@ -63,6 +64,7 @@ _SIGS = {
     "gvqe_energy": [_VP, _VP, _VP, _I, _VP, _I, _VP],
     "gvqe_energy_grad": [_VP, _VP, _VP, _VP, _I, _VP, _VP, _I, _VP],
     "gvqe_batch_create": [_I, _VP, _VP, _I, ctypes.POINTER(_VP)],
+    "gvqe_energy_static": [_VP, _VP, _VP, _I, _VP, _I, _VP],
     "gvqe_batch_run": [_VP, _VP, _VP, _VP, _VP, _VP],
     "gvqe_destroy": [_VP],
     "gvqe_plan_describe": [_I, _I, _I, _I, ctypes.c_char_p, _I],
@@ -184,6 +186,22 @@ def gvqe_energy_grad(ansatz: int, ham: int, params, mask, energies, grad, flags:
     batch = params.shape[0] if params.dim() == 2 else 1
     _check(load().gvqe_energy_grad(ansatz, ham, _ptr(params), _ptr(mask), batch, _ptr(energies), _ptr(grad),
                                    flags, _stream(stream)), "gvqe_energy_grad")
+
+
+def gvqe_energy_static(ansatz: int, ham: int, params, energies, flags: int = GVQE_FP32, stream=None) -> None:
+    """Energies as gvqe_energy, with no device allocation at all.
+
+    For callers that cannot allocate device memory when they need an energy
+    (inside a stream capture, under an allocator or memory budget they do not
+    control): every scratch buffer comes from one fixed device array of
+    GVQE_STATIC_SCRATCH_BYTES inside the library, so only small registers fit
+    (about n <= 19 at batch 1) and the Hamiltonian must be diagonal.  The first
+    call on a device looks the array up; calls that overlap on the GPU race on it.
+    """
+    _require_cuda(params, energies)
+    batch = params.shape[0] if params.dim() == 2 else 1
+    _check(load().gvqe_energy_static(ansatz, ham, _ptr(params), batch, _ptr(energies), flags, _stream(stream)),
+           "gvqe_energy_static")
 
 
 def gvqe_batch_create(ansatze: Sequence[int], hams: Sequence[int], flags: int = GVQE_FP32) -> int:
