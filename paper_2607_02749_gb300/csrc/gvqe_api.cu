@@ -930,57 +930,10 @@ int gvqe_destroy(void *handle) {
 
 }  // extern "C"
 
-// ------------------------------------------------------------------ batch --
-struct gvqe_batch_s {
-  uint32_t magic = 0;
-  int prec = 0;
-  std::vector<gvqe_ansatz> a;
-  std::vector<gvqe_hamiltonian> h;
-};
-
-int batch_destroy(gvqe_batch_s *b) {
-  cudaDeviceSynchronize();
-  b->magic = 0;
-  delete b;
-  return GVQE_OK;
+// ------------------------------------------- helpers for the batch path --
+int energy_one(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, double *E, double *grad,
+               int prec, cudaStream_t s) {
+  return energy_impl(a, h, params, mask, 1, E, grad, prec, s);
 }
 
-extern "C" {
-
-int gvqe_batch_create(int n_inst, const gvqe_ansatz *ansatze, const gvqe_hamiltonian *hams, int flags,
-                      gvqe_batch *out) {
-  g_err.clear();
-  if (!out) return fail(GVQE_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (n_inst < 1 || !ansatze || !hams) return fail(GVQE_EINVAL, "n_inst=%d or NULL instance arrays", n_inst);
-  if (flags & ~GVQE_FP64) return fail(GVQE_EINVAL, "unknown flags 0x%x", flags);
-  for (int i = 0; i < n_inst; ++i) {
-    const int rc = check_pair(ansatze[i], hams[i]);
-    if (rc != GVQE_OK) return fail(rc, "instance %d: %s", i, g_err.c_str());
-  }
-  gvqe_batch_s *b = new gvqe_batch_s();
-  b->magic = MAGIC_BATCH;
-  b->prec = flags & GVQE_FP64 ? 1 : 0;
-  b->a.assign(ansatze, ansatze + n_inst);
-  b->h.assign(hams, hams + n_inst);
-  *out = b;
-  return GVQE_OK;
-}
-
-int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *const *masks, double *energies,
-                   double *const *grads, void *stream) {
-  g_err.clear();
-  if (!b || b->magic != MAGIC_BATCH) return fail(GVQE_EINVAL, "invalid batch handle");
-  if (!params || !energies) return fail(GVQE_EINVAL, "params or energies is NULL");
-  cudaStream_t s = (cudaStream_t)stream;
-  for (size_t i = 0; i < b->a.size(); ++i) {
-    if (!params[i]) return fail(GVQE_EINVAL, "params[%zu] is NULL", i);
-    const uint8_t *m = masks ? masks[i] : nullptr;
-    double *g = grads ? grads[i] : nullptr;
-    const int rc = energy_impl(b->a[i], b->h[i], params[i], m, 1, energies + i, g, b->prec, s);
-    if (rc != GVQE_OK) return rc;
-  }
-  return GVQE_OK;
-}
-
-}  // extern "C"
+int prepare_tables(gvqe_hamiltonian h, int prec, cudaStream_t s) { return ensure_tables(h, prec, s); }

@@ -1,0 +1,568 @@
+// gvqe_batch.cu -- many independent restricted-update problems (Section IV-D,
+// Eq. 11) in one persistent kernel launch, replayed from a CUDA graph.
+//
+// Work items are (instance, step, tile) triples.  Each instance's steps are:
+// PREP (cos/sin of its parameters, lowest active layer of its mask), the tile
+// passes of its plan (forward, backward, layer-0 gradient), and REDUCE (its
+// energy and gradient from the partial sums).  CTAs claim items from one
+// global ticket counter in a fixed stage-major order (every instance's step s
+// before any instance's step s + 1).  An item waits, with a bounded spin, until
+// every tile of the previous step of its own instance has finished.  A wait only
+// ever targets items with smaller tickets, which were claimed earlier by CTAs
+// that are running, so the smallest unfinished item can always proceed: the
+// schedule cannot deadlock, whatever the number of resident CTAs.  A wait that
+// outlives its budget sets an error word, skips its work and still signals
+// completion; the host reports GVQE_ETIMEOUT.
+//
+// Producers publish with __threadfence() + atomicAdd on the step's counter;
+// consumers spin on an acquire load, then every state load goes through L2.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "gvqe.h"
+#include "gvqe_internal.h"
+#include "gvqe_tile.cuh"
+
+namespace gvqe {
+
+enum StepKind : int { S_PREP = 0, S_PASS = 1, S_REDUCE = 2 };
+
+struct BatchStep {
+  PassArgs A;        // pass arguments with this instance's buffers (job 0 of one)
+  int kind;          // StepKind
+  int inst;          // instance index
+  int dep;           // step this one waits for (-1: none)
+  unsigned dep_need; // completions of `dep` required (its item count)
+  unsigned items;    // items of this step
+  const RedEntry *dir;  // REDUCE: directory of the instance
+  int ndir;
+  int n, reps;       // PREP: register size and repetitions
+};
+
+struct BatchIO {
+  const double *params;  // P doubles
+  const uint8_t *mask;   // P bytes or NULL (all active)
+  double *grad;          // P doubles or NULL
+  double *energy;        // one double
+};
+
+struct BatchArgs {
+  const BatchStep *steps;
+  const unsigned *seg_start;  // first ticket of each step in schedule order
+  const int *seg_step;        // step index of each segment
+  int nseg;
+  unsigned total;
+  unsigned *ticket;
+  unsigned *done;             // completions per step (+ spare counters)
+  int *err;
+  const BatchIO *io;
+  long long timeout_cycles;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename T>
+__device__ void batch_prep(const BatchStep &st, const BatchIO &io) {
+  using T2 = typename V2<T>::type;
+  const PassArgs &A = st.A;
+  T2 *cs = reinterpret_cast<T2 *>(const_cast<void *>(A.cs));
+  for (int p = threadIdx.x; p < A.P; p += blockDim.x) {
+    double s, c;
+    sincos(0.5 * io.params[p], &s, &c);
+    T2 v;
+    v.x = (T)c;
+    v.y = (T)s;
+    cs[p] = v;
+  }
+  if (threadIdx.x == 0) {
+    int m = st.reps + 1;  // nothing active: no backward pass needed
+    if (io.mask == nullptr) {
+      m = 0;
+    } else {
+      for (int p = 0; p < A.P; ++p)
+        if (io.mask[p]) {
+          m = p / st.n;
+          break;
+        }
+    }
+    *const_cast<int *>(A.minlayer) = m;
+  }
+}
+
+__device__ void batch_reduce(const BatchStep &st, const BatchIO &io) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double *part = st.A.part;
+  for (int e = wid; e < st.ndir; e += nw) {
+    const RedEntry d = st.dir[e];
+    double s = 0.0;
+    for (int i = lane; i < d.count; i += 32) s += __ldcg(part + d.off + i);
+    s = warp_sum(s);
+    if (lane == 0) {
+      if (d.param < 0) {
+        *io.energy = s;
+      } else if (io.grad != nullptr) {
+        const bool on = io.mask == nullptr || io.mask[d.param] != 0;
+        io.grad[d.param] = on ? s : 0.0;
+      }
+    }
+  }
+}
+
+template <typename T, int TB>
+__device__ void batch_pass(const PassArgs &A, uint32_t tile) {
+  const bool full = A.c >= TB;
+  switch (A.kind) {
+    case K_FWD:
+      if (!full) {
+        fwd_tile<T, TB, false, LD_PLAIN, false>(A, 0, tile);
+      } else {
+        switch (A.load_mode) {
+          case LD_PLAIN: fwd_tile<T, TB, true, LD_PLAIN, false>(A, 0, tile); break;
+          case LD_GATHER: fwd_tile<T, TB, true, LD_GATHER, false>(A, 0, tile); break;
+          case LD_L0_GATHER: fwd_tile<T, TB, true, LD_L0_GATHER, false>(A, 0, tile); break;
+          default: fwd_tile<T, TB, true, LD_L0, false>(A, 0, tile); break;
+        }
+      }
+      break;
+    case K_BWD:
+      if (full)
+        bwd_tile<T, TB, true>(A, 0, tile);
+      else
+        bwd_tile<T, TB, false>(A, 0, tile);
+      break;
+    case K_GRAD_L0:
+      grad_l0_tile<T, TB>(A, 0, tile);
+      break;
+    default:
+      break;
+  }
+}
+
+template <typename T, int TB>
+__global__ void __launch_bounds__(1 << (TB - 5), 2) k_batch(const BatchArgs B) {
+  __shared__ unsigned s_item;
+  __shared__ int s_ok;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(B.ticket, 1u);
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= B.total) break;
+    // segment of this ticket: the last one whose start is <= item
+    int lo = 0, hi = B.nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (B.seg_start[mid] <= item)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const int si = B.seg_step[lo];
+    const unsigned tile = item - B.seg_start[lo];
+    const BatchStep &st = B.steps[si];
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      if (st.dep >= 0 && ld_acquire(B.done + st.dep) < st.dep_need) {
+        const long long t0 = clock64();
+        while (ld_acquire(B.done + st.dep) < st.dep_need) {
+          if (clock64() - t0 > B.timeout_cycles) {
+            atomicOr(B.err, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (s_ok) {
+      const BatchIO io = B.io[st.inst];
+      if (st.kind == S_PREP)
+        batch_prep<T>(st, io);
+      else if (st.kind == S_REDUCE)
+        batch_reduce(st, io);
+      else
+        batch_pass<T, TB>(st.A, tile);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(B.done + (si), 1u);
+    }
+  }
+}
+
+// ------------------------------------------------------------------- host --
+// (the dynamic shared-memory limit is raised by batch_occupancy before capture)
+template <typename T, int TB>
+static cudaError_t launch_batch(const BatchArgs &B, int ctas, size_t smem, cudaStream_t s) {
+  k_batch<T, TB><<<ctas, 1 << (TB - 5), smem, s>>>(B);
+  return cudaGetLastError();
+}
+
+template <typename T, int TB>
+static int batch_occupancy(size_t smem) {
+  int per = 0;
+  cudaFuncSetAttribute(k_batch<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<T, TB>, 1 << (TB - 5), smem) != cudaSuccess)
+    per = 1;
+  return std::max(1, per);
+}
+
+}  // namespace gvqe
+
+using namespace gvqe;
+
+// One compiled schedule (energy-only or energy + gradient).
+struct BatchSchedule {
+  bool built = false;
+  DevBuf dev;  // steps, segments, counters, io, workspace
+  BatchArgs args{};
+  int ctas = 0;
+  size_t smem = 0;
+  std::vector<Plan> plans;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int nsteps = 0;
+  int counters = 0;
+};
+
+struct gvqe_batch_s {
+  uint32_t magic = 0;
+  int prec = 0;
+  bool persistent = false;
+  std::vector<gvqe_ansatz> a;
+  std::vector<gvqe_hamiltonian> h;
+  BatchSchedule sched[2];  // [0] energies only, [1] energies + gradients
+  std::vector<BatchIO> io_host;
+  bool io_valid[2] = {false, false};
+};
+
+namespace {
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int tile_bits_for(int prec) { return prec ? 12 : 13; }
+
+long long wait_budget_cycles() {
+  // bounded device-side waits: GVQE_WAIT_TIMEOUT_MS (default 2000 ms) at ~2 GHz
+  long long ms = 2000;
+  if (const char *e = getenv("GVQE_WAIT_TIMEOUT_MS")) ms = std::max(1LL, atoll(e));
+  return ms * 2000000LL;
+}
+
+#define GB_CUDA(expr)                                                                         \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) return fail(GVQE_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));  \
+  } while (0)
+
+int build_schedule(gvqe_batch_s *b, int want_grad) {
+  BatchSchedule &sc = b->sched[want_grad];
+  const int prec = b->prec;
+  const int TB = tile_bits_for(prec);
+  const size_t es = prec ? 8 : 4;
+  const int ni = (int)b->a.size();
+  sc.plans.clear();
+  sc.plans.reserve(ni);
+  for (int i = 0; i < ni; ++i) sc.plans.push_back(build_plan(b->a[i]->n, b->a[i]->reps, prec, TB, want_grad != 0, true));
+
+  // device layout: [steps][seg_start][seg_step][counters][io][per-instance workspace]
+  std::vector<BatchStep> steps;
+  std::vector<std::vector<int>> inst_steps(ni);
+  for (int i = 0; i < ni; ++i) {
+    const Plan &pl = sc.plans[i];
+    BatchStep prep{};
+    prep.kind = S_PREP;
+    prep.inst = i;
+    prep.items = 1;
+    prep.n = pl.n;
+    prep.reps = pl.reps;
+    inst_steps[i].push_back((int)steps.size());
+    steps.push_back(prep);
+    for (const PassStep &ps : pl.steps) {
+      BatchStep st{};
+      st.kind = S_PASS;
+      st.inst = i;
+      st.A = ps.A;
+      st.items = (unsigned)ps.A.tiles;
+      inst_steps[i].push_back((int)steps.size());
+      steps.push_back(st);
+    }
+    BatchStep red{};
+    red.kind = S_REDUCE;
+    red.inst = i;
+    red.items = 1;
+    red.ndir = (int)pl.dir.size();
+    inst_steps[i].push_back((int)steps.size());
+    steps.push_back(red);
+  }
+  const int nsteps = (int)steps.size();
+  for (int i = 0; i < ni; ++i)
+    for (size_t k = 1; k < inst_steps[i].size(); ++k) {
+      BatchStep &st = steps[inst_steps[i][k]];
+      st.dep = inst_steps[i][k - 1];
+      st.dep_need = steps[st.dep].items;
+    }
+  // host-injected fault for tests: the first pass of instance 0 waits on a counter nothing signals
+  const bool inject = getenv("GVQE_TEST_UNSATISFIABLE_WAIT") != nullptr;
+  if (inject && inst_steps[0].size() > 1) {
+    BatchStep &st = steps[inst_steps[0][1]];
+    st.dep = nsteps;  // a spare counter
+    st.dep_need = 1;
+  }
+  // stage-major schedule; within a stage the larger instances first
+  std::vector<int> order(ni);
+  for (int i = 0; i < ni; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->a[x]->n > b->a[y]->n; });
+  std::vector<unsigned> seg_start;
+  std::vector<int> seg_step;
+  unsigned tick = 0;
+  size_t max_stage = 0;
+  for (int i = 0; i < ni; ++i) max_stage = std::max(max_stage, inst_steps[i].size());
+  for (size_t s = 0; s < max_stage; ++s)
+    for (int i : order) {
+      if (s >= inst_steps[i].size()) continue;
+      const int si = inst_steps[i][s];
+      seg_start.push_back(tick);
+      seg_step.push_back(si);
+      tick += steps[si].items;
+    }
+  const int nseg = (int)seg_start.size();
+  const int counters = nsteps + 1;
+
+  // workspace offsets
+  size_t off = 0;
+  const size_t o_steps = off;
+  off = up256(off + sizeof(BatchStep) * nsteps);
+  const size_t o_segs = off;
+  off = up256(off + sizeof(unsigned) * nseg);
+  const size_t o_segstep = off;
+  off = up256(off + sizeof(int) * nseg);
+  const size_t o_ctr = off;  // ticket, err, done[counters]
+  off = up256(off + sizeof(unsigned) * (2 + counters));
+  const size_t o_io = off;
+  off = up256(off + sizeof(BatchIO) * ni);
+  const size_t o_dir = off;
+  size_t dir_total = 0;
+  for (int i = 0; i < ni; ++i) dir_total += sc.plans[i].dir.size();
+  off = up256(off + sizeof(RedEntry) * dir_total);
+  std::vector<size_t> o_inst(ni);
+  for (int i = 0; i < ni; ++i) {
+    const Plan &pl = sc.plans[i];
+    o_inst[i] = off;
+    off = up256(off + (size_t)pl.P * 2 * es);                   // cs
+    off = up256(off + sizeof(int));                              // minlayer
+    off = up256(off + (size_t)pl.part_stride * 8);               // partials
+    off = up256(off + (size_t)pl.n_bufs * pl.state_elems * es);  // state buffers
+  }
+  {
+    const int rc = sc.dev.reserve(off);
+    if (rc != GVQE_OK) return rc;
+  }
+  char *base = (char *)sc.dev.ptr;
+  // resolve the pointers of every step
+  size_t dir_off = 0;
+  for (int i = 0; i < ni; ++i) {
+    const Plan &pl = sc.plans[i];
+    char *ib = base + o_inst[i];
+    void *cs = ib;
+    char *p = ib + up256((size_t)pl.P * 2 * es);
+    int *ml = (int *)p;
+    p += 256;
+    double *part = (double *)p;
+    p += up256((size_t)pl.part_stride * 8);
+    char *bufs = p;
+    auto buf = [&](int id) -> void * { return id < 0 ? nullptr : bufs + (size_t)id * pl.state_elems * es; };
+    const void *table = prec ? b->h[i]->T64.ptr : b->h[i]->T32.ptr;
+    const RedEntry *dir = (const RedEntry *)(base + o_dir) + dir_off;
+    for (size_t k = 0; k < inst_steps[i].size(); ++k) {
+      BatchStep &st = steps[inst_steps[i][k]];
+      st.A.cs = cs;
+      st.A.minlayer = ml;
+      st.A.P = pl.P;
+      st.A.part = part;
+      st.A.part_stride = pl.part_stride;
+      if (st.kind == S_PASS) {
+        const PassStep &ps = pl.steps[k - 1];
+        st.A.job0 = 0;
+        st.A.table = table;
+        st.A.in = buf(ps.in);
+        st.A.in_stride = pl.state_elems;
+        st.A.lam_in = buf(ps.lam);
+        st.A.lam_stride = pl.state_elems;
+        st.A.out = buf(ps.out);
+        st.A.out_stride = pl.state_elems;
+        st.A.part = part + (ps.part_region >= 0 ? ps.part_region : 0);
+        st.A.epart = part + (ps.epart_region >= 0 ? ps.epart_region : 0);
+      } else if (st.kind == S_REDUCE) {
+        st.dir = dir;
+      }
+    }
+    dir_off += pl.dir.size();
+  }
+  std::vector<RedEntry> dirs;
+  dirs.reserve(dir_total);
+  for (int i = 0; i < ni; ++i) dirs.insert(dirs.end(), sc.plans[i].dir.begin(), sc.plans[i].dir.end());
+  GB_CUDA(cudaMemcpy(base + o_steps, steps.data(), sizeof(BatchStep) * nsteps, cudaMemcpyHostToDevice));
+  GB_CUDA(cudaMemcpy(base + o_segs, seg_start.data(), sizeof(unsigned) * nseg, cudaMemcpyHostToDevice));
+  GB_CUDA(cudaMemcpy(base + o_segstep, seg_step.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice));
+  if (!dirs.empty()) GB_CUDA(cudaMemcpy(base + o_dir, dirs.data(), sizeof(RedEntry) * dirs.size(), cudaMemcpyHostToDevice));
+
+  BatchArgs &B = sc.args;
+  B.steps = (const BatchStep *)(base + o_steps);
+  B.seg_start = (const unsigned *)(base + o_segs);
+  B.seg_step = (const int *)(base + o_segstep);
+  B.nseg = nseg;
+  B.total = tick;
+  B.ticket = (unsigned *)(base + o_ctr);
+  B.err = (int *)(base + o_ctr + sizeof(unsigned));
+  B.done = (unsigned *)(base + o_ctr + 2 * sizeof(unsigned));
+  B.io = (const BatchIO *)(base + o_io);
+  B.timeout_cycles = wait_budget_cycles();
+  sc.nsteps = nsteps;
+  sc.counters = counters;
+  // one CTA's shared memory: the largest of a forward tile and a backward tile (psi + lambda)
+  sc.smem = 2 * (es << TB);
+  int sms = 1, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per = prec ? batch_occupancy<double, 12>(sc.smem) : batch_occupancy<float, 13>(sc.smem);
+  sc.ctas = std::max(1, sms * per);
+
+  // the graph: clear ticket, error word and counters, then the persistent launch
+  cudaStream_t cap;
+  GB_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(base + o_ctr, 0, sizeof(unsigned) * (2 + counters), cap);
+    if (prec)
+      launch_batch<double, 12>(B, sc.ctas, sc.smem, cap);
+    else
+      launch_batch<float, 13>(B, sc.ctas, sc.smem, cap);
+    e = cudaStreamEndCapture(cap, &sc.graph);
+  }
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return fail(GVQE_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
+  GB_CUDA(cudaGraphInstantiate(&sc.exec, sc.graph, 0));
+  sc.built = true;
+  b->io_valid[want_grad] = false;
+  return GVQE_OK;
+}
+
+int batch_loop(gvqe_batch_s *b, const double *const *params, const uint8_t *const *masks, double *energies,
+               double *const *grads, cudaStream_t s);
+
+}  // namespace
+
+int batch_destroy(gvqe_batch_s *b) {
+  cudaDeviceSynchronize();
+  for (BatchSchedule &sc : b->sched) {
+    if (sc.exec) cudaGraphExecDestroy(sc.exec);
+    if (sc.graph) cudaGraphDestroy(sc.graph);
+    sc.dev.release();
+  }
+  b->magic = 0;
+  delete b;
+  return GVQE_OK;
+}
+
+// energy / gradient of one instance through the regular path (gvqe_api.cu)
+int energy_one(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, double *E, double *grad,
+               int prec, cudaStream_t s);
+int prepare_tables(gvqe_hamiltonian h, int prec, cudaStream_t s);
+
+namespace {
+int batch_loop(gvqe_batch_s *b, const double *const *params, const uint8_t *const *masks, double *energies,
+               double *const *grads, cudaStream_t s) {
+  for (size_t i = 0; i < b->a.size(); ++i) {
+    const int rc = energy_one(b->a[i], b->h[i], params[i], masks ? masks[i] : nullptr, energies + i,
+                              grads ? grads[i] : nullptr, b->prec, s);
+    if (rc != GVQE_OK) return rc;
+  }
+  return GVQE_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int gvqe_batch_create(int n_inst, const gvqe_ansatz *ansatze, const gvqe_hamiltonian *hams, int flags,
+                      gvqe_batch *out) {
+  g_err.clear();
+  if (!out) return fail(GVQE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_inst < 1 || !ansatze || !hams) return fail(GVQE_EINVAL, "n_inst=%d or NULL instance arrays", n_inst);
+  if (flags & ~GVQE_FP64) return fail(GVQE_EINVAL, "unknown flags 0x%x", flags);
+  const int prec = flags & GVQE_FP64 ? 1 : 0;
+  bool persistent = true;
+  for (int i = 0; i < n_inst; ++i) {
+    gvqe_ansatz a = ansatze[i];
+    gvqe_hamiltonian h = hams[i];
+    if (!a || a->magic != MAGIC_ANSATZ) return fail(GVQE_EINVAL, "instance %d: invalid ansatz handle", i);
+    if (!h || h->magic != MAGIC_HAM) return fail(GVQE_EINVAL, "instance %d: invalid Hamiltonian handle", i);
+    if (a->n != h->n) return fail(GVQE_EINVAL, "instance %d: ansatz has %d qubits, Hamiltonian %d", i, a->n, h->n);
+    // the persistent kernel runs one tile size and diagonal Hamiltonians
+    if (a->n < tile_bits_for(prec) || !h->gm.empty()) persistent = false;
+  }
+  for (int i = 0; i < n_inst; ++i) {
+    const int rc = prepare_tables(hams[i], prec, nullptr);
+    if (rc != GVQE_OK) return rc;
+  }
+  gvqe_batch_s *b = new gvqe_batch_s();
+  b->magic = MAGIC_BATCH;
+  b->prec = prec;
+  b->persistent = persistent;
+  b->a.assign(ansatze, ansatze + n_inst);
+  b->h.assign(hams, hams + n_inst);
+  *out = b;
+  return GVQE_OK;
+}
+
+int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *const *masks, double *energies,
+                   double *const *grads, void *stream) {
+  g_err.clear();
+  if (!b || b->magic != MAGIC_BATCH) return fail(GVQE_EINVAL, "invalid batch handle");
+  if (!params || !energies) return fail(GVQE_EINVAL, "params or energies is NULL");
+  const size_t ni = b->a.size();
+  for (size_t i = 0; i < ni; ++i) {
+    if (!params[i]) return fail(GVQE_EINVAL, "params[%zu] is NULL", i);
+    if (grads && !grads[i]) return fail(GVQE_EINVAL, "grads[%zu] is NULL", i);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!b->persistent) return batch_loop(b, params, masks, energies, grads, s);
+  const int g = grads ? 1 : 0;
+  BatchSchedule &sc = b->sched[g];
+  if (!sc.built) {
+    const int rc = build_schedule(b, g);
+    if (rc != GVQE_OK) return rc;
+  }
+  std::vector<BatchIO> io(ni);
+  for (size_t i = 0; i < ni; ++i) {
+    io[i].params = params[i];
+    io[i].mask = masks ? masks[i] : nullptr;
+    io[i].grad = grads ? grads[i] : nullptr;
+    io[i].energy = energies + i;
+  }
+  if (!b->io_valid[g] || b->io_host.size() != ni || memcmp(io.data(), b->io_host.data(), sizeof(BatchIO) * ni) != 0) {
+    GB_CUDA(cudaMemcpyAsync((void *)sc.args.io, io.data(), sizeof(BatchIO) * ni, cudaMemcpyHostToDevice, s));
+    b->io_host = io;
+    b->io_valid[g] = true;
+    b->io_valid[1 - g] = false;
+  }
+  GB_CUDA(cudaGraphLaunch(sc.exec, s));
+  count_launches(1);
+  GB_CUDA(cudaStreamSynchronize(s));
+  int err = 0;
+  GB_CUDA(cudaMemcpy(&err, sc.args.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) return fail(GVQE_ETIMEOUT, "a bounded device-side wait of the batch kernel ran out (error word %d)", err);
+  return GVQE_OK;
+}
+
+}  // extern "C"

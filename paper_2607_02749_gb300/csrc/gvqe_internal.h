@@ -59,6 +59,7 @@ struct Plan {
 };
 
 std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits);
+void count_launches(int k);
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag);
 std::string describe_plan(const Plan &pl);
 

@@ -462,9 +462,11 @@ struct L0Tables {
 };
 
 // ------------------------------------------------------ forward tile pass --
+// One tile of a forward pass: tile block index tb_idx of job `job` (the pairing
+// of tiles H and ~H for gathering passes is applied here).  State loads go
+// through L2 (ld.global.cg), so data written by other SMs is never read stale.
 template <typename T, int TB, bool FULL, int LOAD, bool WHT>
-__global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 6 : 3) / (sizeof(T) == 8 ? 2 : 1))
-k_fwd(const PassArgs A) {
+__device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb_idx) {
   using T2 = typename V2<T>::type;
   constexpr int NT = 1 << (TB - 5);
   constexpr int NW = NT / 32;
@@ -476,9 +478,8 @@ k_fwd(const PassArgs A) {
   __shared__ double ered[NW];
   __shared__ L0Tables<T, T2, TB> tab;
 
-  const int job = blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const uint32_t t = tile_of_block(blockIdx.x, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
+  const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
   const uint32_t tbase = tile_base(t, A.c, A.a, TB);
   const uint32_t nmask = (A.n >= 32) ? 0xffffffffu : ((1u << A.n) - 1);
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
@@ -499,9 +500,9 @@ k_fwd(const PassArgs A) {
   for_L(gi, [&](int k, uint32_t y) {
     T v;
     if constexpr (LOAD == LD_PLAIN)
-      v = in[y];
+      v = __ldcg(in + y);
     else if constexpr (LOAD == LD_GATHER)
-      v = in[cx_inv(y, nmask)];
+      v = __ldcg(in + cx_inv(y, nmask));
     else if constexpr (LOAD == LD_L0_GATHER)
       v = tab(cx_inv(y, nmask));
     else
@@ -541,6 +542,13 @@ k_fwd(const PassArgs A) {
       A.epart[(size_t)job * A.part_stride + t] = e;
     }
   }
+  __syncthreads();  // shared tile and coefficients free for the caller's next tile
+}
+
+template <typename T, int TB, bool FULL, int LOAD, bool WHT>
+__global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 6 : 3) / (sizeof(T) == 8 ? 2 : 1))
+k_fwd(const PassArgs A) {
+  fwd_tile<T, TB, FULL, LOAD, WHT>(A, blockIdx.y, blockIdx.x);
 }
 
 // ------------------------------------------------------ backward tile pass --
@@ -709,13 +717,106 @@ k_bwd(const PassArgs A) {
   cp_async_wait<0>();
 }
 
+// One tile of a backward pass with the loads straight into registers (no
+// prefetch); used by the persistent batch kernel, where the next work item is
+// a tile of any step.  Same rounds and results as k_bwd.
+template <typename T, int TB, bool FULL>
+__device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb_idx) {
+  using T2 = typename V2<T>::type;
+  constexpr int NT = 1 << (TB - 5);
+  constexpr int NW = NT / 32;
+  constexpr int H = TB - 10;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sp = reinterpret_cast<T *>(smem_raw);
+  T *sl = sp + (1 << TB);
+  __shared__ T2 gcs[16];
+  __shared__ double gred[NW][16];
+  __shared__ double ered[NW];
+
+  if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.layer < A.minlayer[A.job0 + job]) return;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
+  const uint32_t tbase = tile_base(t, A.c, A.a, TB);
+  const uint32_t nmask = (1u << A.n) - 1;
+  const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
+  load_gate_coeffs(A, cs, gcs, tid);
+  __syncthreads();
+  const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
+  const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
+  const T *table = reinterpret_cast<const T *>(A.table);
+  T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
+  const uint32_t gm = A.gate_mask;
+  const bool init = (A.flags & F_LAMBDA_INIT) != 0;
+  GIdx<TB, FULL> gi;
+  gi.init(tbase, A.c, A.a, lane, w);
+
+  Reg32<T> psi, lam;
+  T eacc = T(0);
+  for_L(gi, [&](int k, uint32_t y) {
+    const T p = __ldcg(in + y);
+    const T l = init ? table[y] * p : __ldcg(lin + y);
+    psi.set(k, p);
+    lam.set(k, l);
+    eacc += p * l;
+  });
+  round_grads<5>(psi, lam, gm, 5, gred[w], lane);
+  sts_L(sp, lane, w, psi);
+  sts_L(sl, lane, w, lam);
+  if (A.flags & F_ENERGY) {
+    eacc = warp_sum(eacc);
+    if (lane == 0) ered[w] = (double)eacc;
+  }
+  __syncthreads();
+  if (gm & 0x1Fu) {
+    lds_M(sp, tid, psi);
+    lds_M(sl, tid, lam);
+    round_grads<5>(psi, lam, gm, 0, gred[w], lane);
+  }
+  lds_H<TB>(sp, tid, psi);
+  lds_H<TB>(sl, tid, lam);
+  round_grads<H>(psi, lam, gm, 10, gred[w], lane);
+  round_gates<H, false>(lam, gcs, gm, 10, true);
+  __syncthreads();
+  sts_H<TB>(sl, tid, lam);
+  __syncthreads();
+  if (gm & 0x1Fu) {
+    lds_M(sl, tid, lam);
+    round_gates<5, false>(lam, gcs, gm, 0, true);
+    sts_M(sl, tid, lam);
+    __syncthreads();
+  }
+  lds_L(sl, lane, w, lam);
+  round_gates<5, false>(lam, gcs, gm, 5, true);
+  for_L(gi, [&](int k, uint32_t y) {
+    if constexpr (FULL)
+      out[cx_inv(y, nmask)] = lam.get(k);
+    else
+      out[y] = lam.get(k);
+  });
+  __syncthreads();
+  double *part = A.part + (size_t)job * A.part_stride;
+  if (tid < TB && ((gm >> tid) & 1u)) {
+    double g = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) g += gred[ww][tid];
+    part[(size_t)tid * A.tiles + t] = g;
+  }
+  if ((A.flags & F_ENERGY) && tid == 0) {
+    double e = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) e += ered[ww];
+    A.epart[(size_t)job * A.part_stride + t] = e;
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------ layer-0 gradient pass --
 // g_{0,q} = sum_x lambda_0[x] prod_{q' != q} f_q'(x_q') d_q(x_q) with
 // f(0) = cos(t/2), f(1) = sin(t/2), d(0) = -sin(t/2), d(1) = cos(t/2): the
 // adjoint formula evaluated against the layer-0 product state.  The tile is
 // global bits [0, TB); the product over the register bits 5..9 is tabulated.
 template <typename T, int TB>
-__global__ void __launch_bounds__(1 << (TB - 5)) k_grad_l0(const PassArgs A) {
+__device__ __forceinline__ void grad_l0_tile(const PassArgs &A, int job, uint32_t t) {
   using T2 = typename V2<T>::type;
   constexpr int NT = 1 << (TB - 5);
   constexpr int NW = NT / 32;
@@ -727,10 +828,8 @@ __global__ void __launch_bounds__(1 << (TB - 5)) k_grad_l0(const PassArgs A) {
   __shared__ double fhi_d[32];
   __shared__ double fhi_all;
 
-  const int job = blockIdx.y;
   if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.minlayer[A.job0 + job] > 0) return;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const uint32_t t = blockIdx.x;
   const int n = A.n;
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   if (tid < n) l0cs[tid] = cs[tid];
@@ -813,7 +912,7 @@ __global__ void __launch_bounds__(1 << (TB - 5)) k_grad_l0(const PassArgs A) {
       lam = table[x] * psi0;
       eacc += psi0 * lam;
     } else {
-      lam = lin[x];
+      lam = __ldcg(lin + x);
     }
     S += lam * RF[k];
 #pragma unroll
@@ -867,6 +966,12 @@ __global__ void __launch_bounds__(1 << (TB - 5)) k_grad_l0(const PassArgs A) {
     for (int ww = 0; ww < NW; ++ww) e += ered[ww];
     A.epart[(size_t)job * A.part_stride + t] = e;
   }
+  __syncthreads();
+}
+
+template <typename T, int TB>
+__global__ void __launch_bounds__(1 << (TB - 5)) k_grad_l0(const PassArgs A) {
+  grad_l0_tile<T, TB>(A, blockIdx.y, blockIdx.x);
 }
 
 // ----------------------------------------- lambda = H psi with X-mask groups --

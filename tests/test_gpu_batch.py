@@ -1,0 +1,105 @@
+"""The persistent batched path (gvqe_batch_*): many independent restricted-update
+problems (uneven qubit counts, own Hamiltonians, own active masks) in one
+persistent launch replayed from a CUDA graph, checked against single calls and
+the oracle, plus the bounded device-side wait returning GVQE_ETIMEOUT."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_02749_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2607_02749_gb300 as gv  # noqa: E402
+from paper_2607_02749_gb300 import _lib  # noqa: E402
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _setup(insts, fp64=False):
+    ans = [gv.Ansatz(i.n_qubits, i.reps) for i in insts]
+    hams = [gv.Hamiltonian.from_workload(i.ham) for i in insts]
+    b = gv.Batch(ans, hams, fp64=fp64)
+    params = [_dev(i.theta[0]) for i in insts]
+    masks = [_dev(i.mask[0], torch.uint8) for i in insts]
+    return ans, hams, b, params, masks
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_persistent_batch_matches_single_calls_and_oracle(fp64):
+    insts = wl.cluster_batch(10, qubit_range=(13, 17), reps_range=(1, 3), terms_per_qubit=20)
+    ans, hams, b, params, masks = _setup(insts, fp64)
+    grads = [torch.full_like(p, float("nan")) for p in params]
+    for rep in range(2):  # the graph is replayed
+        e = b.run(params, masks=masks, grads=grads).cpu().numpy()
+        for k, i in enumerate(insts):
+            scale = i.ham.abs_sum()
+            e1, g1 = gv.energy_grad(ans[k], hams[k], params[k], mask=masks[k], fp64=fp64)
+            g = grads[k].cpu().numpy()
+            g1 = g1.cpu().numpy()[0]
+            tol_e = (1e-10 if fp64 else 2e-5) * scale
+            assert abs(e[k] - e1.item()) <= tol_e
+            assert np.all(g[i.mask[0] == 0] == 0.0)
+            if fp64:
+                assert np.max(np.abs(g - g1)) <= 1e-9 * scale
+            else:
+                assert np.linalg.norm(g - g1) <= 1e-4 * max(np.linalg.norm(g1), 1e-3 * scale)
+            if rep == 0 and k < 3:
+                e_ref, g_ref = oracle.energy_grad(i.n_qubits, i.reps, i.theta[0], i.ham.strings, i.ham.coeffs)
+                g_ref = np.where(i.mask[0] == 1, g_ref, 0.0)
+                assert abs(e[k] - e_ref) <= tol_e
+                assert np.linalg.norm(g - g_ref) <= (1e-9 if fp64 else 1e-4) * max(np.linalg.norm(g_ref), scale * 1e-3)
+
+
+def test_persistent_batch_energies_only_and_pointer_change():
+    insts = wl.cluster_batch(6, qubit_range=(13, 16), reps_range=(2, 3), terms_per_qubit=10)
+    ans, hams, b, params, masks = _setup(insts)
+    e = b.run(params).cpu().numpy()
+    for k in range(len(insts)):
+        assert abs(e[k] - gv.energy(ans[k], hams[k], params[k]).item()) <= 2e-5 * insts[k].ham.abs_sum()
+    # new parameter buffers between runs are picked up
+    params2 = [p.clone() * 0.5 for p in params]
+    e2 = b.run(params2).cpu().numpy()
+    for k in range(len(insts)):
+        assert abs(e2[k] - gv.energy(ans[k], hams[k], params2[k]).item()) <= 2e-5 * insts[k].ham.abs_sum()
+
+
+def test_cluster_workload_256_instances():
+    insts = wl.cluster_batch(256)
+    ans, hams, b, params, masks = _setup(insts)
+    grads = [torch.empty_like(p) for p in params]
+    e = b.run(params, masks=masks, grads=grads).cpu().numpy()
+    for k in (0, 17, 100, 255):
+        i = insts[k]
+        e1, g1 = gv.energy_grad(ans[k], hams[k], params[k], mask=masks[k])
+        scale = i.ham.abs_sum()
+        assert abs(e[k] - e1.item()) <= 2e-5 * scale
+        g1 = g1.cpu().numpy()[0]
+        assert np.linalg.norm(grads[k].cpu().numpy() - g1) <= 1e-4 * max(np.linalg.norm(g1), 1e-3 * scale)
+
+
+def test_bounded_wait_returns_timeout_and_context_survives():
+    insts = wl.cluster_batch(3, qubit_range=(13, 14), reps_range=(1, 1), terms_per_qubit=5)
+    os.environ["GVQE_TEST_UNSATISFIABLE_WAIT"] = "1"
+    os.environ["GVQE_WAIT_TIMEOUT_MS"] = "20"
+    try:
+        ans, hams, b, params, masks = _setup(insts)
+        with pytest.raises(_lib.GvqeError) as err:
+            b.run(params)
+        assert err.value.code == _lib.GVQE_ETIMEOUT
+    finally:
+        del os.environ["GVQE_TEST_UNSATISFIABLE_WAIT"]
+        del os.environ["GVQE_WAIT_TIMEOUT_MS"]
+    # the context is still usable: a fresh batch runs and agrees with single calls
+    ans, hams, b, params, masks = _setup(insts)
+    e = b.run(params).cpu().numpy()
+    for k in range(len(insts)):
+        assert abs(e[k] - gv.energy(ans[k], hams[k], params[k]).item()) <= 2e-5 * insts[k].ham.abs_sum()
