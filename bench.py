@@ -183,6 +183,47 @@ def ncu_traffic(kernel: str, bytes_per_launch_units: float):
         return None
 
 
+def cluster_leg(steps: int):
+    """256 independent restricted-update problems (n ~ U{14..20}, reps ~ U{2..4}, own
+    Z-string Hamiltonians and 30-60% active masks) in one persistent launch per run."""
+    import torch
+
+    import paper_2607_02749_gb300 as gv
+    from paper_2607_02749_gb300 import _lib
+    from paper_2607_02749_gb300 import workloads as wl
+
+    insts = wl.cluster_batch(256)
+    ans = [gv.Ansatz(i.n_qubits, i.reps) for i in insts]
+    hams = [gv.Hamiltonian.from_workload(i.ham) for i in insts]
+    b = gv.Batch(ans, hams)
+    params = [torch.as_tensor(i.theta[0], dtype=torch.float64, device="cuda") for i in insts]
+    masks = [torch.as_tensor(i.mask[0], dtype=torch.uint8, device="cuda") for i in insts]
+    grads = [torch.empty_like(p) for p in params]
+    energies = torch.empty(len(insts), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        b.run(params, masks=masks, grads=grads, energies=energies)
+    torch.cuda.synchronize()
+    n0 = _lib.gvqe_launch_count()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        b.run(params, masks=masks, grads=grads, energies=energies)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    launches = (_lib.gvqe_launch_count() - n0) / steps
+    # the same instances one gvqe_energy_grad call at a time, for comparison
+    e1 = torch.empty(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(len(insts)):
+        _lib.gvqe_energy_grad(ans[k].handle, hams[k].handle, params[k], masks[k], e1, grads[k])
+    torch.cuda.synchronize()
+    dt_loop = time.perf_counter() - t0
+    amps = sum(2 ** i.n_qubits for i in insts)
+    return {"value": len(insts) / dt, "unit": "E+grad/s", "instances": len(insts), "ms_per_run": dt * 1e3,
+            "launches_per_run": launches, "per_instance_calls_ms": dt_loop * 1e3,
+            "total_amplitudes": amps, "timing": "wall clock around synchronous gvqe_batch_run calls"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -361,6 +402,9 @@ def run_gvqe(args):
             "check_dE_dtheta_last": {"param_shift": float(gps[0, P - 1].item()), "adjoint_fp64": float(g64[P - 1])},
         }
         out["speedup_fp32_adjoint_vs_fp64_param_shift"] = value / ws / (1.0 / t_grad)
+
+    if rank == 0 and not args.no_comparators:
+        out["cluster_batch"] = cluster_leg(args.steps)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
