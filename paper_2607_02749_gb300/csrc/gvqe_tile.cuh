@@ -91,6 +91,18 @@ struct Reg32<float> {
     else
       v[k >> 1].x = x;
   }
+  // RY on register bit JB >= 1 with pre-packed coefficient pairs (c,c), (s,s), (-s,-s)
+  template <int JB>
+  __device__ __forceinline__ void rot_pk(unsigned long long c2, unsigned long long s2, unsigned long long ns2) {
+    constexpr int B = 1 << (JB - 1);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      if (m & B) continue;
+      const unsigned long long a = pk(v[m]), b = pk(v[m | B]);
+      v[m] = upk(fma2(ns2, b, mul2(c2, a)));
+      v[m | B] = upk(fma2(s2, a, mul2(c2, b)));
+    }
+  }
   // RY on register bit JB: (a, b) -> (c a - s b, s a + c b)
   template <int JB>
   __device__ __forceinline__ void rot(float c, float s) {
@@ -229,17 +241,40 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Global offset of a tile bit under the STRIDED layout.
 __device__ __forceinline__ uint32_t gbit(int t, int c, int a) { return 1u << (t < c ? t : a + t - c); }
 
-template <int NB, bool WHT, typename T, typename T2>
-__device__ __forceinline__ void round_gates(Reg32<T> &r, const T2 *gcs, uint32_t gmask, int tbit0, bool inverse) {
-  // gcs[i] = (cos, sin) of tile bit i
-#define GVQE_GATE(J)                                         \
-  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) {             \
-    if (WHT) {                                               \
-      r.template wht<J>();                                   \
-    } else {                                                 \
-      const T2 cs = gcs[tbit0 + J];                          \
-      r.template rot<J>(cs.x, inverse ? -cs.y : cs.y);       \
-    }                                                        \
+// Gate coefficients of one pass, per tile bit: (cos, sin) and, for FP32, the
+// packed pairs (c,c), (s,s), (-s,-s) the f32x2 rotations take, built once per CTA.
+template <typename T2>
+struct GateTab {
+  T2 cs[16];
+  unsigned long long c2[16], s2[16], ns2[16];
+  __device__ __forceinline__ void pack(int tid) {
+    if (tid < 16) {
+      const float c = (float)cs[tid].x, s = (float)cs[tid].y;
+      c2[tid] = pk(c, c);
+      s2[tid] = pk(s, s);
+      ns2[tid] = pk(-s, -s);
+    }
+  }
+};
+
+// PACKED: FP32 rotations take the pre-packed pairs of the table (fewer registers
+// live when false: the pairs are packed at the call).
+template <int NB, bool WHT, bool PACKED = true, typename T, typename T2>
+__device__ __forceinline__ void round_gates(Reg32<T> &r, const GateTab<T2> &gt, uint32_t gmask, int tbit0,
+                                            bool inverse) {
+  // register bit j holds tile bit tbit0 + j; RY(theta), or RY(-theta) when inverse
+#define GVQE_GATE(J)                                                                       \
+  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) {                                           \
+    if (WHT) {                                                                             \
+      r.template wht<J>();                                                                 \
+    } else if constexpr (PACKED && sizeof(T) == 4 && J > 0) {                              \
+      const int tb_ = tbit0 + J;                                                           \
+      r.template rot_pk<(J > 0 ? J : 1)>(gt.c2[tb_], inverse ? gt.ns2[tb_] : gt.s2[tb_],   \
+                                         inverse ? gt.s2[tb_] : gt.ns2[tb_]);              \
+    } else {                                                                               \
+      const T2 cs = gt.cs[tbit0 + J];                                                      \
+      r.template rot<J>(cs.x, inverse ? -cs.y : cs.y);                                     \
+    }                                                                                      \
   }
   GVQE_GATE(0)
   GVQE_GATE(1)
@@ -249,21 +284,49 @@ __device__ __forceinline__ void round_gates(Reg32<T> &r, const T2 *gcs, uint32_t
 #undef GVQE_GATE
 }
 
-// Gradient partials of one round, reduced over the warp; lane 0 stores them.
+// Gradient partials of one round: the (up to 5, padded to 8) per-thread sums are
+// reduced over the warp with a transposed butterfly (each exchange halves the
+// values a lane carries), then lane (j << 2) holds value j and stores it.
 template <int NB, typename T>
 __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> &lam, uint32_t gmask, int tbit0,
                                             double *wred, int lane) {
-#define GVQE_GRAD(J)                                        \
-  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) {            \
-    const T gsum = warp_sum(psi.template grad<J>(lam));     \
-    if (lane == 0) wred[tbit0 + J] = (double)gsum;          \
+  T v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = T(0);
+#define GVQE_GV(J) \
+  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) v[J] = psi.template grad<J>(lam);
+  GVQE_GV(0)
+  GVQE_GV(1)
+  GVQE_GV(2)
+  GVQE_GV(3)
+  GVQE_GV(4)
+#undef GVQE_GV
+  // stage 1: lanes with bit 4 set keep values 4..7, the others 0..3
+  const bool b4 = (lane >> 4) & 1;
+  T u[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const T mine = b4 ? v[4 + j] : v[j];
+    const T other = b4 ? v[j] : v[4 + j];
+    u[j] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
   }
-  GVQE_GRAD(0)
-  GVQE_GRAD(1)
-  GVQE_GRAD(2)
-  GVQE_GRAD(3)
-  GVQE_GRAD(4)
-#undef GVQE_GRAD
+  const bool b3 = (lane >> 3) & 1;
+  T t2[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const T mine = b3 ? u[2 + j] : u[j];
+    const T other = b3 ? u[j] : u[2 + j];
+    t2[j] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
+  }
+  const bool b2 = (lane >> 2) & 1;
+  T r = (b2 ? t2[1] : t2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? t2[0] : t2[1], 4);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  // lane holds value index (b4 << 2) | (b3 << 1) | b2
+  if ((lane & 3) == 0) {
+    const int j = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if (j < NB && ((gmask >> (tbit0 + j)) & 1u)) wred[tbit0 + j] = (double)r;
+  }
 }
 
 // --------------------------------------------------- shared-memory rounds --
@@ -474,7 +537,7 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   constexpr bool L0 = (LOAD == LD_L0 || LOAD == LD_L0_GATHER);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *s = reinterpret_cast<T *>(smem_raw);
-  __shared__ T2 gcs[16];
+  __shared__ GateTab<T2> gt;
   __shared__ double ered[NW];
   __shared__ L0Tables<T, T2, TB> tab;
 
@@ -483,7 +546,9 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   const uint32_t tbase = tile_base(t, A.c, A.a, TB);
   const uint32_t nmask = (A.n >= 32) ? 0xffffffffu : ((1u << A.n) - 1);
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
-  if (!WHT) load_gate_coeffs(A, cs, gcs, tid);
+  if (!WHT) {
+    load_gate_coeffs(A, cs, gt.cs, tid);
+  }
   if constexpr (L0) {
     const uint32_t xbase = (LOAD == LD_L0_GATHER) ? cx_inv(tbase, nmask) : tbase;
     tab.build(cs, A.n, xbase, tid, NT);
@@ -509,19 +574,19 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
       v = tab(y);
     r.set(k, v);
   });
-  round_gates<5, WHT>(r, gcs, gm, 5, false);
+  round_gates<5, WHT, false>(r, gt, gm, 5, false);
   sts_L(s, lane, w, r);
   __syncthreads();
   // round M: tile bits 0..4
   if (gm & 0x1Fu) {
     lds_M(s, tid, r);
-    round_gates<5, WHT>(r, gcs, gm, 0, false);
+    round_gates<5, WHT, false>(r, gt, gm, 0, false);
     sts_M(s, tid, r);
     __syncthreads();
   }
   // round H: tile bits 10..TB-1, then the store and the energy epilogue
   lds_H<TB>(s, tid, r);
-  round_gates<H, WHT>(r, gcs, gm, 10, false);
+  round_gates<H, WHT, false>(r, gt, gm, 10, false);
   const T *table = reinterpret_cast<const T *>(A.table);
   const bool store = A.store_mode != ST_NONE;
   const bool energy = (A.flags & F_ENERGY) != 0;
@@ -546,7 +611,7 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
 }
 
 template <typename T, int TB, bool FULL, int LOAD, bool WHT>
-__global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 6 : 3) / (sizeof(T) == 8 ? 2 : 1))
+__global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 8 : 4) / (sizeof(T) == 8 ? 2 : 1))
 k_fwd(const PassArgs A) {
   fwd_tile<T, TB, FULL, LOAD, WHT>(A, blockIdx.y, blockIdx.x);
 }
@@ -587,7 +652,7 @@ k_bwd(const PassArgs A) {
   constexpr int CPT = TILE / CH / NT;      // chunks per thread per array
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *buf = reinterpret_cast<T *>(smem_raw);  // three rotating tiles
-  __shared__ T2 gcs[16];
+  __shared__ GateTab<T2> gt;
   __shared__ double gred[NW][16];
   __shared__ double ered[NW];
 
@@ -598,7 +663,8 @@ k_bwd(const PassArgs A) {
   const bool pair = (A.flags & F_PAIR_ORDER) != 0;
   const uint32_t nmask = (1u << A.n) - 1;
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
-  load_gate_coeffs(A, cs, gcs, tid);
+  load_gate_coeffs(A, cs, gt.cs, tid);
+  if (sizeof(T) == 4) gt.pack(tid);
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
   const bool init = (A.flags & F_LAMBDA_INIT) != 0;
   const T *lsrc = init ? reinterpret_cast<const T *>(A.table)
@@ -672,7 +738,7 @@ k_bwd(const PassArgs A) {
     lds_H<TB>(sp, tid, psi);
     lds_H<TB>(sl, tid, lam);
     round_grads<H>(psi, lam, gm, 10, gred[w], lane);
-    round_gates<H, false>(lam, gcs, gm, 10, true);
+    round_gates<H, false>(lam, gt, gm, 10, true);
     __syncthreads();  // psi fully read; lambda may be overwritten
     if (more)
       issue(lsrc, nbx, sp);  // next lambda into the psi buffer
@@ -682,12 +748,12 @@ k_bwd(const PassArgs A) {
     __syncthreads();
     if (gm & 0x1Fu) {
       lds_M(sl, tid, lam);
-      round_gates<5, false>(lam, gcs, gm, 0, true);
+      round_gates<5, false>(lam, gt, gm, 0, true);
       sts_M(sl, tid, lam);
       __syncthreads();
     }
     lds_L(sl, lane, w, lam);
-    round_gates<5, false>(lam, gcs, gm, 5, true);
+    round_gates<5, false>(lam, gt, gm, 5, true);
     for_L(gi, [&](int k, uint32_t y) {
       if constexpr (FULL)
         out[cx_inv(y, nmask)] = lam.get(k);
@@ -729,7 +795,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sp = reinterpret_cast<T *>(smem_raw);
   T *sl = sp + (1 << TB);
-  __shared__ T2 gcs[16];
+  __shared__ GateTab<T2> gt;
   __shared__ double gred[NW][16];
   __shared__ double ered[NW];
 
@@ -739,7 +805,8 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   const uint32_t tbase = tile_base(t, A.c, A.a, TB);
   const uint32_t nmask = (1u << A.n) - 1;
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
-  load_gate_coeffs(A, cs, gcs, tid);
+  load_gate_coeffs(A, cs, gt.cs, tid);
+  if (sizeof(T) == 4) gt.pack(tid);
   __syncthreads();
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
   const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
@@ -775,18 +842,18 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   lds_H<TB>(sp, tid, psi);
   lds_H<TB>(sl, tid, lam);
   round_grads<H>(psi, lam, gm, 10, gred[w], lane);
-  round_gates<H, false>(lam, gcs, gm, 10, true);
+  round_gates<H, false>(lam, gt, gm, 10, true);
   __syncthreads();
   sts_H<TB>(sl, tid, lam);
   __syncthreads();
   if (gm & 0x1Fu) {
     lds_M(sl, tid, lam);
-    round_gates<5, false>(lam, gcs, gm, 0, true);
+    round_gates<5, false>(lam, gt, gm, 0, true);
     sts_M(sl, tid, lam);
     __syncthreads();
   }
   lds_L(sl, lane, w, lam);
-  round_gates<5, false>(lam, gcs, gm, 5, true);
+  round_gates<5, false>(lam, gt, gm, 5, true);
   for_L(gi, [&](int k, uint32_t y) {
     if constexpr (FULL)
       out[cx_inv(y, nmask)] = lam.get(k);
