@@ -259,21 +259,21 @@ struct GateTab {
 
 // PACKED: FP32 rotations take the pre-packed pairs of the table (fewer registers
 // live when false: the pairs are packed at the call).
-template <int NB, bool WHT, bool PACKED = true, typename T, typename T2>
+template <int NB, bool WHT, bool PACKED = true, int RO = 0, typename T, typename T2>
 __device__ __forceinline__ void round_gates(Reg32<T> &r, const GateTab<T2> &gt, uint32_t gmask, int tbit0,
                                             bool inverse) {
-  // register bit j holds tile bit tbit0 + j; RY(theta), or RY(-theta) when inverse
+  // register bit RO + j holds tile bit tbit0 + j; RY(theta), or RY(-theta) when inverse
 #define GVQE_GATE(J)                                                                       \
   if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) {                                           \
     if (WHT) {                                                                             \
-      r.template wht<J>();                                                                 \
-    } else if constexpr (PACKED && sizeof(T) == 4 && J > 0) {                              \
+      r.template wht<J + RO>();                                                            \
+    } else if constexpr (PACKED && sizeof(T) == 4 && J + RO > 0) {                         \
       const int tb_ = tbit0 + J;                                                           \
-      r.template rot_pk<(J > 0 ? J : 1)>(gt.c2[tb_], inverse ? gt.ns2[tb_] : gt.s2[tb_],   \
-                                         inverse ? gt.s2[tb_] : gt.ns2[tb_]);              \
+      r.template rot_pk<(J + RO > 0 ? J + RO : 1)>(gt.c2[tb_], inverse ? gt.ns2[tb_] : gt.s2[tb_], \
+                                                   inverse ? gt.s2[tb_] : gt.ns2[tb_]);   \
     } else {                                                                               \
       const T2 cs = gt.cs[tbit0 + J];                                                      \
-      r.template rot<J>(cs.x, inverse ? -cs.y : cs.y);                                     \
+      r.template rot<J + RO>(cs.x, inverse ? -cs.y : cs.y);                                \
     }                                                                                      \
   }
   GVQE_GATE(0)
@@ -287,14 +287,14 @@ __device__ __forceinline__ void round_gates(Reg32<T> &r, const GateTab<T2> &gt, 
 // Gradient partials of one round: the (up to 5, padded to 8) per-thread sums are
 // reduced over the warp with a transposed butterfly (each exchange halves the
 // values a lane carries), then lane (j << 2) holds value j and stores it.
-template <int NB, typename T>
+template <int NB, int RO = 0, typename T>
 __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> &lam, uint32_t gmask, int tbit0,
                                             double *wred, int lane) {
   T v[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = T(0);
 #define GVQE_GV(J) \
-  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) v[J] = psi.template grad<J>(lam);
+  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) v[J] = psi.template grad<(J + RO < 5 ? J + RO : 4)>(lam);
   GVQE_GV(0)
   GVQE_GV(1)
   GVQE_GV(2)
@@ -371,29 +371,33 @@ __device__ __forceinline__ void sts_M(double *s, int G, const Reg32<double> &r) 
   for (int c = 0; c < 16; ++c)
     *reinterpret_cast<double2 *>(s + (G << 5) + ((c ^ (G & 7)) << 1)) = make_double2(r.v[2 * c], r.v[2 * c + 1]);
 }
-// Round H: thread tid handles groups gidx = tid + it*NT; element k = it<<H | j is tile index gidx + (j<<10).
+// Round H: thread tid handles groups gidx = tid + it*NT (IT = 15 - TB bits of it);
+// element k = (j << IT) | it is tile index gidx + (j << 10), so register bits
+// IT.. hold tile bits 10..TB-1 and register bit 0 is a group bit without a gate.
 template <int TB>
 __device__ __forceinline__ int gidx_H(int tid, int k) {
-  constexpr int H = TB - 10;
+  constexpr int IT = 15 - TB;
   constexpr int NT = 1 << (TB - 5);
-  return tid + (k >> H) * NT;
+  return tid + (k & ((1 << IT) - 1)) * NT;
+}
+template <int TB>
+__device__ __forceinline__ int jH(int k) {
+  return k >> (15 - TB);
 }
 template <int TB, typename T>
 __device__ __forceinline__ void lds_H(const T *s, int tid, Reg32<T> &r) {
-  constexpr int H = TB - 10;
 #pragma unroll
   for (int k = 0; k < ROUND; ++k) {
     const int g = gidx_H<TB>(tid, k);
-    r.set(k, s[swz<T>(g) + ((k & ((1 << H) - 1)) << 10)]);
+    r.set(k, s[swz<T>(g) + (jH<TB>(k) << 10)]);
   }
 }
 template <int TB, typename T>
 __device__ __forceinline__ void sts_H(T *s, int tid, const Reg32<T> &r) {
-  constexpr int H = TB - 10;
 #pragma unroll
   for (int k = 0; k < ROUND; ++k) {
     const int g = gidx_H<TB>(tid, k);
-    s[swz<T>(g) + ((k & ((1 << H) - 1)) << 10)] = r.get(k);
+    s[swz<T>(g) + (jH<TB>(k) << 10)] = r.get(k);
   }
 }
 
@@ -466,14 +470,14 @@ __device__ __forceinline__ void for_H(const GIdx<TB, FULL> &gi, int tid, F &&f) 
     for (int jj = 0; jj < (1 << H); ++jj) {
       int j = jj;
       if (FULL) {
-        f((it << H) | j, o + ((uint32_t)j << 10));
+        f((j << (15 - TB)) | it, o + ((uint32_t)j << 10));
       } else {
         j = gray(jj);
         if (jj > 0) {
           const int b = gray_bit(jj);
           o = ((j >> b) & 1) ? o + gi.SH[b] : o - gi.SH[b];
         }
-        f((it << H) | j, o);
+        f((j << (15 - TB)) | it, o);
       }
     }
   }
@@ -586,16 +590,20 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   }
   // round H: tile bits 10..TB-1, then the store and the energy epilogue
   lds_H<TB>(s, tid, r);
-  round_gates<H, WHT, false>(r, gt, gm, 10, false);
+  round_gates<H, WHT, false, 15 - TB>(r, gt, gm, 10, false);
   const T *table = reinterpret_cast<const T *>(A.table);
   const bool store = A.store_mode != ST_NONE;
   const bool energy = (A.flags & F_ENERGY) != 0;
   T eacc = T(0);
-  for_H(gi, tid, [&](int k, uint32_t y) {
-    const T v = r.get(k);
-    if (store) out[y] = v;
-    if (energy) eacc += v * v * table[y];
-  });
+  if (!energy) {
+    for_H(gi, tid, [&](int k, uint32_t y) { out[y] = r.get(k); });
+  } else {
+    for_H(gi, tid, [&](int k, uint32_t y) {
+      const T v = r.get(k);
+      if (store) out[y] = v;
+      eacc += v * v * table[y];
+    });
+  }
   if (energy) {
     eacc = warp_sum(eacc);
     if (lane == 0) ered[w] = (double)eacc;
@@ -737,8 +745,8 @@ k_bwd(const PassArgs A) {
     // round H: gradients, then RY(-theta) on lambda
     lds_H<TB>(sp, tid, psi);
     lds_H<TB>(sl, tid, lam);
-    round_grads<H>(psi, lam, gm, 10, gred[w], lane);
-    round_gates<H, false>(lam, gt, gm, 10, true);
+    round_grads<H, 15 - TB>(psi, lam, gm, 10, gred[w], lane);
+    round_gates<H, false, true, 15 - TB>(lam, gt, gm, 10, true);
     __syncthreads();  // psi fully read; lambda may be overwritten
     if (more)
       issue(lsrc, nbx, sp);  // next lambda into the psi buffer
@@ -841,8 +849,8 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   }
   lds_H<TB>(sp, tid, psi);
   lds_H<TB>(sl, tid, lam);
-  round_grads<H>(psi, lam, gm, 10, gred[w], lane);
-  round_gates<H, false>(lam, gt, gm, 10, true);
+  round_grads<H, 15 - TB>(psi, lam, gm, 10, gred[w], lane);
+  round_gates<H, false, true, 15 - TB>(lam, gt, gm, 10, true);
   __syncthreads();
   sts_H<TB>(sl, tid, lam);
   __syncthreads();
