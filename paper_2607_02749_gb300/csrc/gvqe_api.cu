@@ -198,7 +198,7 @@ static int qubit_of(const LayerPass &lp, int i) { return i < lp.c ? i : lp.a + i
 static long long tiles_of(int n, int tb) { return 1LL << (n - tb); }
 
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
-Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag) {
+Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0) {
   Plan pl;
   pl.n = n;
   pl.reps = reps;
@@ -376,9 +376,17 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
     PassStep st;
     st.A = base_args(K_GRAD_L0);
     st.A.tb = tbA;
-    st.A.c = tbA;
     st.A.a = tbA;
-    st.A.tiles = tiles_of(n, tbA);
+    if (n > 9 && !tile_grad_l0) {  // n <= 9 runs in the whole-register kernel
+      int mb = 0;
+      long long slots = 1;
+      grad_l0_layout(n, prec, &mb, &slots);
+      st.A.c = mb;
+      st.A.tiles = slots;
+    } else {
+      st.A.c = tbA;
+      st.A.tiles = tiles_of(n, tbA);
+    }
     st.A.layer = 0;
     if (reps == 0 && diag) {
       st.A.flags = F_LAMBDA_INIT | F_ENERGY;

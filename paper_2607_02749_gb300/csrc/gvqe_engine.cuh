@@ -119,6 +119,13 @@ cudaError_t launch_shift_combine(const double *Es, int P, int jobs, const int *a
                                  double *E, double *grad, cudaStream_t s);
 // Largest tile size (log2 amplitudes) whose backward pass fits in shared memory.
 int max_tile_bits(int prec);
+// Multiprocessors of the current device (queried once).
+int num_sms_cached();
+// Layer-0 gradient pass (gvqe_grad_l0.cu).  Its PassArgs use c = mb, the
+// number of 1024-amplitude chunks (log2) one warp folds into a group, and
+// tiles = the warps per job, which is also the number of partials per qubit.
+void grad_l0_layout(int n, int prec, int *mb, long long *slots);
+cudaError_t launch_grad_l0(int prec, const PassArgs &A, int jobs, cudaStream_t s);
 // Dynamic shared memory (bytes) needed by one pass launch.
 size_t pass_smem_bytes(int prec, int kind, int tb);
 

@@ -60,7 +60,10 @@ struct Plan {
 
 std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits);
 void count_launches(int k);
-Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag);
+// tile_grad_l0: lay the layer-0 gradient partials out per tile (one CTA of
+// tile bits per partial), as the persistent batch kernel computes them,
+// instead of per warp of the standalone layer-0 gradient pass.
+Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false);
 std::string describe_plan(const Plan &pl);
 
 }  // namespace gvqe

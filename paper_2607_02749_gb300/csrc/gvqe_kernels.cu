@@ -352,8 +352,19 @@ static cudaError_t launch_typed(const PassArgs &A, int jobs, int nterm, cudaStre
   }
 }
 
+int num_sms_cached() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    n = (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) ? v : 1;
+  }
+  return n;
+}
+
 cudaError_t launch_pass(int prec, const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
   if (jobs < 1 || A.tiles < 1) return cudaErrorInvalidValue;
+  if (A.kind == K_GRAD_L0 && A.n > SMALL_MAXN) return launch_grad_l0(prec, A, jobs, s);
   return prec ? launch_typed<double>(A, jobs, nterm, s) : launch_typed<float>(A, jobs, nterm, s);
 }
 

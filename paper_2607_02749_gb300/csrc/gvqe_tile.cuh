@@ -781,12 +781,13 @@ k_bwd(const PassArgs A) {
       for (int ww = 0; ww < NW; ++ww) e += ered[ww];
       A.epart[(size_t)job * A.part_stride + t] = e;
     }
-    // rotate: next psi is in F, next lambda in P, the lambda buffer becomes free
+    // rotate: next psi is in F, next lambda in P, the lambda buffer becomes free.
+    // The barrier at the top of the next iteration orders these partial reads
+    // before the next tile's gred / ered writes.
     const int nP = F, nL = P, nF = L;
     P = nP;
     L = nL;
     F = nF;
-    __syncthreads();  // gred / ered may be reused
   }
   cp_async_wait<0>();
 }
@@ -1044,11 +1045,6 @@ __device__ __forceinline__ void grad_l0_tile(const PassArgs &A, int job, uint32_
   __syncthreads();
 }
 
-template <typename T, int TB>
-__global__ void __launch_bounds__(1 << (TB - 5)) k_grad_l0(const PassArgs A) {
-  grad_l0_tile<T, TB>(A, blockIdx.y, blockIdx.x);
-}
-
 // ----------------------------------------- lambda = H psi with X-mask groups --
 // lambda[x] = E(x) psi[x] + sum_groups D_m(x ^ m) psi[x ^ m] with
 // D_m(u) = sum_{k in group} c_k (-1)^popcount(u & z_k) (c_k carries the i^#Y sign).
@@ -1162,8 +1158,6 @@ cudaError_t launch_tb(const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
       if (full) return launch_k(k_bwd<T, TB, true>, pgrid, block, 3 * tile, s, A);
       return launch_k(k_bwd<T, TB, false>, pgrid, block, 3 * tile, s, A);
     }
-    case K_GRAD_L0:
-      return launch_k(k_grad_l0<T, TB>, grid, block, 0, s, A);
     case K_LAMBDA_XY: {
       const size_t smem = xy_layout(A.ngroups, nterm, (int)sizeof(T)).total;
       if (smem > 200 * 1024) return cudaErrorInvalidValue;
