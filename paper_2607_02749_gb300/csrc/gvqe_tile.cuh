@@ -532,7 +532,7 @@ struct L0Tables {
 // One tile of a forward pass: tile block index tb_idx of job `job` (the pairing
 // of tiles H and ~H for gathering passes is applied here).  State loads go
 // through L2 (ld.global.cg), so data written by other SMs is never read stale.
-template <typename T, int TB, bool FULL, int LOAD, bool WHT>
+template <typename T, int TB, bool FULL, int LOAD, bool WHT, bool REUSE = true>
 __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb_idx) {
   using T2 = typename V2<T>::type;
   constexpr int NT = 1 << (TB - 5);
@@ -580,14 +580,15 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   });
   round_gates<5, WHT, false>(r, gt, gm, 5, false);
   sts_L(s, lane, w, r);
-  __syncthreads();
-  // round M: tile bits 0..4
+  // round M: tile bits 0..4.  Layouts L and M of warp w both cover tile
+  // amplitudes [1024 w, 1024 w + 1024), so the warp only syncs with itself.
   if (gm & 0x1Fu) {
+    __syncwarp();
     lds_M(s, tid, r);
     round_gates<5, WHT, false>(r, gt, gm, 0, false);
     sts_M(s, tid, r);
-    __syncthreads();
   }
+  __syncthreads();
   // round H: tile bits 10..TB-1, then the store and the energy epilogue
   lds_H<TB>(s, tid, r);
   round_gates<H, WHT, false, 15 - TB>(r, gt, gm, 10, false);
@@ -615,13 +616,13 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
       A.epart[(size_t)job * A.part_stride + t] = e;
     }
   }
-  __syncthreads();  // shared tile and coefficients free for the caller's next tile
+  if (REUSE) __syncthreads();  // shared tile and coefficients free for the caller's next tile
 }
 
 template <typename T, int TB, bool FULL, int LOAD, bool WHT>
 __global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 8 : 4) / (sizeof(T) == 8 ? 2 : 1))
 k_fwd(const PassArgs A) {
-  fwd_tile<T, TB, FULL, LOAD, WHT>(A, blockIdx.y, blockIdx.x);
+  fwd_tile<T, TB, FULL, LOAD, WHT, false>(A, blockIdx.y, blockIdx.x);
 }
 
 // ------------------------------------------------------ backward tile pass --
@@ -661,8 +662,8 @@ k_bwd(const PassArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *buf = reinterpret_cast<T *>(smem_raw);  // three rotating tiles
   __shared__ GateTab<T2> gt;
-  __shared__ double gred[NW][16];
-  __shared__ double ered[NW];
+  __shared__ double gred[2][NW][16];  // by tile parity: a warp may start the next
+  __shared__ double ered[2][NW];      // tile while warp 0 still sums this one
 
   const int job = blockIdx.y;
   if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.layer < A.minlayer[A.job0 + job]) return;
@@ -682,13 +683,14 @@ k_bwd(const PassArgs A) {
   const uint32_t gm = A.gate_mask;
   const uint32_t cm = (1u << A.c) - 1;
 
-  // copy one array of tile bx into shared tile dst (one commit group)
+  // copy one array of tile bx into shared tile dst (one commit group); warp w
+  // copies tile amplitudes [1024 w, 1024 w + 1024), the ones its rounds L and M read
   auto issue = [&](const T *src, uint32_t bx, T *dst) {
     const uint32_t t = tile_of_block(bx, tiles, pair);
     const uint32_t tbase = tile_base(t, A.c, A.a, TB);
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
-      const uint32_t i = (uint32_t)(tid + m * NT) * CH;
+      const uint32_t i = (uint32_t)((lane + 32 * m) * CH + 1024 * w);
       const uint32_t go = FULL ? tbase + i : tbase + (i & cm) + ((i >> A.c) << A.a);
       cp_async16(dst + swz<T>((int)i), src + go);
     }
@@ -697,6 +699,7 @@ k_bwd(const PassArgs A) {
 
   uint32_t bx = blockIdx.x;
   int P = 0, L = 1, F = 2;  // buffer roles
+  int par = 0;              // tile parity (gred / ered)
   if (bx < tiles) {
     issue(in, bx, buf + P * TILE);
     issue(lsrc, bx, buf + L * TILE);
@@ -709,8 +712,8 @@ k_bwd(const PassArgs A) {
       issue(in, nbx, buf + F * TILE);  // next psi into the free buffer
     else
       cp_async_commit();
-    cp_async_wait<1>();  // this tile's psi and lambda have landed
-    __syncthreads();
+    cp_async_wait<1>();  // this tile's psi and lambda have landed (this warp's part)
+    __syncwarp();
     T *sp = buf + P * TILE;
     T *sl = buf + L * TILE;
     const uint32_t t = tile_of_block(bx, tiles, pair);
@@ -732,20 +735,21 @@ k_bwd(const PassArgs A) {
       }
       sts_L(sl, lane, w, lam);
       eacc = warp_sum(eacc);
-      if (lane == 0) ered[w] = (double)eacc;
+      if (lane == 0) ered[par][w] = (double)eacc;
     }
-    round_grads<5>(psi, lam, gm, 5, gred[w], lane);
-    if (init) __syncthreads();  // lambda = E psi is in shared before round M reads it
+    round_grads<5>(psi, lam, gm, 5, gred[par][w], lane);
+    if (init) __syncwarp();  // lambda = E psi is in shared before round M reads it
     // round M (gradients only)
     if (gm & 0x1Fu) {
       lds_M(sp, tid, psi);
       lds_M(sl, tid, lam);
-      round_grads<5>(psi, lam, gm, 0, gred[w], lane);
+      round_grads<5>(psi, lam, gm, 0, gred[par][w], lane);
     }
-    // round H: gradients, then RY(-theta) on lambda
+    // round H: gradients, then RY(-theta) on lambda.  Its layout crosses warps.
+    __syncthreads();
     lds_H<TB>(sp, tid, psi);
     lds_H<TB>(sl, tid, lam);
-    round_grads<H, 15 - TB>(psi, lam, gm, 10, gred[w], lane);
+    round_grads<H, 15 - TB>(psi, lam, gm, 10, gred[par][w], lane);
     round_gates<H, false, true, 15 - TB>(lam, gt, gm, 10, true);
     __syncthreads();  // psi fully read; lambda may be overwritten
     if (more)
@@ -758,7 +762,7 @@ k_bwd(const PassArgs A) {
       lds_M(sl, tid, lam);
       round_gates<5, false>(lam, gt, gm, 0, true);
       sts_M(sl, tid, lam);
-      __syncthreads();
+      __syncwarp();  // M -> L stays inside the warp's 1024 amplitudes
     }
     lds_L(sl, lane, w, lam);
     round_gates<5, false>(lam, gt, gm, 5, true);
@@ -768,22 +772,24 @@ k_bwd(const PassArgs A) {
       else
         out[y] = lam.get(k);
     });
-    __syncthreads();  // gred / ered complete, lambda buffer fully read
+    // gred / ered of this tile were written before the round-H barriers
     if (tid < TB && ((gm >> tid) & 1u)) {
       double g = 0.0;
 #pragma unroll
-      for (int ww = 0; ww < NW; ++ww) g += gred[ww][tid];
+      for (int ww = 0; ww < NW; ++ww) g += gred[par][ww][tid];
       part[(size_t)tid * tiles + t] = g;
     }
     if ((A.flags & F_ENERGY) && tid == 0) {
       double e = 0.0;
 #pragma unroll
-      for (int ww = 0; ww < NW; ++ww) e += ered[ww];
+      for (int ww = 0; ww < NW; ++ww) e += ered[par][ww];
       A.epart[(size_t)job * A.part_stride + t] = e;
     }
-    // rotate: next psi is in F, next lambda in P, the lambda buffer becomes free.
-    // The barrier at the top of the next iteration orders these partial reads
-    // before the next tile's gred / ered writes.
+    // rotate: next psi is in F, next lambda in P, the lambda buffer becomes
+    // free.  Warp w refills only its own part of it, which only it still
+    // reads; gred / ered of this parity are rewritten two tiles later, after
+    // the next tile's round-H barrier, which warp 0 passes only after the sums above.
+    par ^= 1;
     const int nP = F, nL = P, nF = L;
     P = nP;
     L = nL;
