@@ -85,6 +85,8 @@ template <>
 struct Reg32<float> {
   float2 v[16];
   __device__ __forceinline__ float get(int k) const { return (k & 1) ? v[k >> 1].y : v[k >> 1].x; }
+  __device__ __forceinline__ float2 pair(int m) const { return v[m]; }
+  __device__ __forceinline__ void set_pair(int m, float2 p) { v[m] = p; }
   __device__ __forceinline__ void set(int k, float x) {
     if (k & 1)
       v[k >> 1].y = x;
@@ -176,6 +178,11 @@ struct Reg32<double> {
   double v[32];
   __device__ __forceinline__ double get(int k) const { return v[k]; }
   __device__ __forceinline__ void set(int k, double x) { v[k] = x; }
+  __device__ __forceinline__ double2 pair(int m) const { return make_double2(v[2 * m], v[2 * m + 1]); }
+  __device__ __forceinline__ void set_pair(int m, double2 p) {
+    v[2 * m] = p.x;
+    v[2 * m + 1] = p.y;
+  }
   template <int JB>
   __device__ __forceinline__ void rot(double c, double s) {
 #pragma unroll
@@ -287,12 +294,14 @@ __device__ __forceinline__ void round_gates(Reg32<T> &r, const GateTab<T2> &gt, 
 // Gradient partials of one round: the (up to 5, padded to 8) per-thread sums are
 // reduced over the warp with a transposed butterfly (each exchange halves the
 // values a lane carries), then lane (j << 2) holds value j and stores it.
-template <int NB, int RO = 0, typename T>
+// X5: also the gate of tile bit 5 on register bit 1 (round H), in slot 5.
+template <int NB, int RO = 0, bool X5 = false, typename T>
 __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> &lam, uint32_t gmask, int tbit0,
                                             double *wred, int lane) {
   T v[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = T(0);
+  if (X5 && ((gmask >> 5) & 1u)) v[5] = psi.template grad<1>(lam);
 #define GVQE_GV(J) \
   if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) v[J] = psi.template grad<(J + RO < 5 ? J + RO : 4)>(lam);
   GVQE_GV(0)
@@ -325,25 +334,36 @@ __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> 
   // lane holds value index (b4 << 2) | (b3 << 1) | b2
   if ((lane & 3) == 0) {
     const int j = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-    if (j < NB && ((gmask >> (tbit0 + j)) & 1u)) wred[tbit0 + j] = (double)r;
+    if (j < NB && ((gmask >> (tbit0 + j)) & 1u))
+      wred[tbit0 + j] = (double)r;
+    else if (X5 && j == 5 && ((gmask >> 5) & 1u))
+      wred[5] = (double)r;
   }
 }
 
 // --------------------------------------------------- shared-memory rounds --
-// Round L: element k of thread (lane, warp w) is tile index lane + 32 k + 1024 w.
+// In every round register bit 0 holds tile bit 0, so a thread's elements
+// 2m and 2m+1 are neighbours in the tile and in global memory: rounds L and H
+// move them as one 8-byte (FP32) or 16-byte (FP64) access.
+//
+// Round L: element k = 2m + e of thread (lane, warp w) is tile index
+// e + 2 lane + 64 m + 1024 w: register bits 1..4 hold tile bits 6..9, the lane
+// tile bits 1..5, the warp tile bits 10...
+__device__ __forceinline__ int idx_L(int lane, int w, int m) { return (lane << 1) + (m << 6) + (w << 10); }
 template <typename T>
 __device__ __forceinline__ void sts_L(T *s, int lane, int w, const Reg32<T> &r) {
-  constexpr int CH = 16 / (int)sizeof(T);
+  using T2 = typename V2<T>::type;
 #pragma unroll
-  for (int k = 0; k < ROUND; ++k) s[(lane ^ ((k & 7) * CH)) + 32 * k + 1024 * w] = r.get(k);
+  for (int m = 0; m < ROUND / 2; ++m) *reinterpret_cast<T2 *>(s + swz<T>(idx_L(lane, w, m))) = r.pair(m);
 }
 template <typename T>
 __device__ __forceinline__ void lds_L(const T *s, int lane, int w, Reg32<T> &r) {
-  constexpr int CH = 16 / (int)sizeof(T);
+  using T2 = typename V2<T>::type;
 #pragma unroll
-  for (int k = 0; k < ROUND; ++k) r.set(k, s[(lane ^ ((k & 7) * CH)) + 32 * k + 1024 * w]);
+  for (int m = 0; m < ROUND / 2; ++m) r.set_pair(m, *reinterpret_cast<const T2 *>(s + swz<T>(idx_L(lane, w, m))));
 }
-// Round M: group G's 32 consecutive amplitudes as 16-byte chunks in swizzled order.
+// Round M: group G's 32 consecutive amplitudes (register bits 0..4 = tile
+// bits 0..4) as 16-byte chunks in swizzled order.
 __device__ __forceinline__ void lds_M(const float *s, int G, Reg32<float> &r) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -371,116 +391,96 @@ __device__ __forceinline__ void sts_M(double *s, int G, const Reg32<double> &r) 
   for (int c = 0; c < 16; ++c)
     *reinterpret_cast<double2 *>(s + (G << 5) + ((c ^ (G & 7)) << 1)) = make_double2(r.v[2 * c], r.v[2 * c + 1]);
 }
-// Round H: thread tid handles groups gidx = tid + it*NT (IT = 15 - TB bits of it);
-// element k = (j << IT) | it is tile index gidx + (j << 10), so register bits
-// IT.. hold tile bits 10..TB-1 and register bit 0 is a group bit without a gate.
+// Round H: element k = 2m + e of thread tid is tile index e + idx_H(tid, m).
+// Register bit 1 holds tile bit 5, register bits 2..1+H tile bits 10..TB-1
+// (H = TB - 10) and the remaining register bits tile bits TB-3..9; the thread
+// index covers tile bits 1..4 (its low four bits) and 6.. (the rest).  Only
+// register bits 1..1+H carry gates here: tile bit 5 and the high tile bits.
 template <int TB>
-__device__ __forceinline__ int gidx_H(int tid, int k) {
-  constexpr int IT = 15 - TB;
-  constexpr int NT = 1 << (TB - 5);
-  return tid + (k & ((1 << IT) - 1)) * NT;
+__device__ __forceinline__ int idx_H_thread(int tid) { return ((tid & 15) << 1) | ((tid >> 4) << 6); }
+template <int TB>
+__host__ __device__ constexpr int tbit_H(int j) {  // tile bit of pair-index bit j (register bit j + 1)
+  return j == 0 ? 5 : (j <= TB - 10 ? 9 + j : TB - 3 + (j - 1 - (TB - 10)));
 }
 template <int TB>
-__device__ __forceinline__ int jH(int k) {
-  return k >> (15 - TB);
+__device__ __forceinline__ int idx_H_pair(int m) {
+  int o = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) o |= ((m >> j) & 1) << tbit_H<TB>(j);
+  return o;
 }
 template <int TB, typename T>
 __device__ __forceinline__ void lds_H(const T *s, int tid, Reg32<T> &r) {
+  using T2 = typename V2<T>::type;
+  const int b = idx_H_thread<TB>(tid);
 #pragma unroll
-  for (int k = 0; k < ROUND; ++k) {
-    const int g = gidx_H<TB>(tid, k);
-    r.set(k, s[swz<T>(g) + (jH<TB>(k) << 10)]);
-  }
+  for (int m = 0; m < ROUND / 2; ++m) r.set_pair(m, *reinterpret_cast<const T2 *>(s + swz<T>(b | idx_H_pair<TB>(m))));
 }
 template <int TB, typename T>
 __device__ __forceinline__ void sts_H(T *s, int tid, const Reg32<T> &r) {
+  using T2 = typename V2<T>::type;
+  const int b = idx_H_thread<TB>(tid);
 #pragma unroll
-  for (int k = 0; k < ROUND; ++k) {
-    const int g = gidx_H<TB>(tid, k);
-    s[swz<T>(g) + (jH<TB>(k) << 10)] = r.get(k);
-  }
+  for (int m = 0; m < ROUND / 2; ++m) *reinterpret_cast<T2 *>(s + swz<T>(b | idx_H_pair<TB>(m))) = r.pair(m);
 }
 
-// Gray-code order of the 32 (or 2^H) register elements: consecutive elements
-// differ in one register bit, so a strided global offset advances by one add.
+// Gray-code order of the 16 element pairs: consecutive pairs differ in one
+// pair-index bit, so a strided global offset advances by one add.
 __host__ __device__ constexpr int gray(int k) { return k ^ (k >> 1); }
-__host__ __device__ constexpr int gray_bit(int k) {  // register bit flipped between gray(k-1) and gray(k)
-  return (k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : (k & 8) ? 3 : 4;
+__host__ __device__ constexpr int gray_bit(int k) {  // bit flipped between gray(k-1) and gray(k)
+  return (k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : 3;
 }
 
-// Global element offsets of a thread's round-L and round-H elements.
+// Global element offsets of a thread's round-L and round-H pairs.  Tile bit
+// 0 is global bit 0 in both layouts (the STRIDED carry is at least 3), so
+// element 2m + 1 sits right after element 2m.
 template <int TB, bool FULL>
 struct GIdx {
-  uint32_t baseL;   // offset of element k = 0 in round L
-  uint32_t SL[5];   // offset of register bit j in round L
-  uint32_t SH[5];   // offset of register bit j (< H) in round H
+  uint32_t baseL;  // offset of pair 0 in round L
+  uint32_t SL[4];  // offset of pair-index bit j in round L (tile bit 6 + j)
+  uint32_t baseH;  // offset of pair 0 in round H
+  uint32_t SH[4];  // offset of pair-index bit j in round H (tile bit tbit_H(j))
   uint32_t cm;
   int c, a;
   uint32_t tbase;
   __device__ __forceinline__ uint32_t g(uint32_t i) const { return tbase + (i & cm) + ((i >> c) << a); }
-  __device__ __forceinline__ void init(uint32_t tb_, int c_, int a_, int lane, int w) {
+  __device__ __forceinline__ void init(uint32_t tb_, int c_, int a_, int lane, int w, int tid) {
     tbase = tb_;
     c = c_;
     a = a_;
     cm = (1u << c) - 1;
-    if (FULL) {
-      baseL = tbase + lane + (w << 10);
-    } else {
-      baseL = g((uint32_t)(lane + (w << 10)));
+    const uint32_t iL = (uint32_t)idx_L(lane, w, 0), iH = (uint32_t)idx_H_thread<TB>(tid);
+    baseL = FULL ? tbase + iL : g(iL);
+    baseH = FULL ? tbase + iH : g(iH);
 #pragma unroll
-      for (int j = 0; j < 5; ++j) SL[j] = gbit(5 + j, c, a);
-#pragma unroll
-      for (int j = 0; j < 5; ++j) SH[j] = (j < TB - 10) ? gbit(10 + j, c, a) : 0u;
+    for (int j = 0; j < 4; ++j) {
+      SL[j] = FULL ? (1u << (6 + j)) : gbit(6 + j, c, a);
+      SH[j] = FULL ? (1u << tbit_H<TB>(j)) : gbit(tbit_H<TB>(j), c, a);
     }
   }
-  // offset of group gidx's element j = 0 in round H (the tile bits 0..9 of gidx)
-  __device__ __forceinline__ uint32_t Hbase(int gidx) const { return FULL ? tbase + gidx : g((uint32_t)gidx); }
 };
 
-// Visit the 32 round-L elements of a thread: f(k, global offset).  STRIDED
-// offsets are generated in Gray-code order (one add per element).
-template <int TB, bool FULL, typename F>
-__device__ __forceinline__ void for_L(const GIdx<TB, FULL> &gi, F &&f) {
-  if (FULL) {
+// Visit a thread's 16 element pairs of round L (or H): f(m, global offset of element 2m).
+template <typename F>
+__device__ __forceinline__ void for_pairs(uint32_t base, const uint32_t (&S)[4], F &&f) {
+  uint32_t o = base;
 #pragma unroll
-    for (int k = 0; k < ROUND; ++k) f(k, gi.baseL + 32u * k);
-  } else {
-    uint32_t o = gi.baseL;
-#pragma unroll
-    for (int k = 0; k < ROUND; ++k) {
-      const int e = gray(k);
-      if (k > 0) {
-        const int j = gray_bit(k);
-        o = ((e >> j) & 1) ? o + gi.SL[j] : o - gi.SL[j];
-      }
-      f(e, o);
+  for (int k = 0; k < ROUND / 2; ++k) {
+    const int m = gray(k);
+    if (k > 0) {
+      const int j = gray_bit(k);
+      o = ((m >> j) & 1) ? o + S[j] : o - S[j];
     }
+    f(m, o);
   }
 }
-
-// Visit the 32 round-H elements of a thread: f(k, global offset).
 template <int TB, bool FULL, typename F>
-__device__ __forceinline__ void for_H(const GIdx<TB, FULL> &gi, int tid, F &&f) {
-  constexpr int H = TB - 10;
-  constexpr int NT = 1 << (TB - 5);
-#pragma unroll
-  for (int it = 0; it < (1 << (15 - TB)); ++it) {
-    uint32_t o = gi.Hbase(tid + it * NT);
-#pragma unroll
-    for (int jj = 0; jj < (1 << H); ++jj) {
-      int j = jj;
-      if (FULL) {
-        f((j << (15 - TB)) | it, o + ((uint32_t)j << 10));
-      } else {
-        j = gray(jj);
-        if (jj > 0) {
-          const int b = gray_bit(jj);
-          o = ((j >> b) & 1) ? o + gi.SH[b] : o - gi.SH[b];
-        }
-        f((j << (15 - TB)) | it, o);
-      }
-    }
-  }
+__device__ __forceinline__ void for_L(const GIdx<TB, FULL> &gi, F &&f) {
+  for_pairs(gi.baseL, gi.SL, f);
+}
+template <int TB, bool FULL, typename F>
+__device__ __forceinline__ void for_H(const GIdx<TB, FULL> &gi, F &&f) {
+  for_pairs(gi.baseH, gi.SH, f);
 }
 
 template <typename T2>
@@ -562,23 +562,30 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
   const uint32_t gm = A.gate_mask;
   GIdx<TB, FULL> gi;
-  gi.init(tbase, A.c, A.a, lane, w);
+  gi.init(tbase, A.c, A.a, lane, w, tid);
 
   Reg32<T> r;
-  // round L: global -> registers (tile bits 5..9) -> gates -> shared
-  for_L(gi, [&](int k, uint32_t y) {
-    T v;
-    if constexpr (LOAD == LD_PLAIN)
-      v = __ldcg(in + y);
-    else if constexpr (LOAD == LD_GATHER)
-      v = __ldcg(in + cx_inv(y, nmask));
-    else if constexpr (LOAD == LD_L0_GATHER)
-      v = tab(cx_inv(y, nmask));
-    else
-      v = tab(y);
-    r.set(k, v);
+  // round L: global -> registers (tile bits 6..9) -> gates -> shared.  The
+  // inverse CX chain maps the pair (y, y + 1) to (x, x ^ 3), x = A^-1 y.
+  for_L(gi, [&](int m, uint32_t y) {
+    T2 v;
+    if constexpr (LOAD == LD_PLAIN) {
+      v = __ldcg(reinterpret_cast<const T2 *>(in + y));
+    } else if constexpr (LOAD == LD_GATHER) {
+      const uint32_t x = cx_inv(y, nmask);
+      v.x = __ldcg(in + x);
+      v.y = __ldcg(in + (x ^ 3u));
+    } else if constexpr (LOAD == LD_L0_GATHER) {
+      const uint32_t x = cx_inv(y, nmask);
+      v.x = tab(x);
+      v.y = tab(x ^ 3u);
+    } else {
+      v.x = tab(y);
+      v.y = tab(y + 1);
+    }
+    r.set_pair(m, v);
   });
-  round_gates<5, WHT, false>(r, gt, gm, 5, false);
+  round_gates<4, WHT, false, 1>(r, gt, gm, 6, false);
   sts_L(s, lane, w, r);
   // round M: tile bits 0..4.  Layouts L and M of warp w both cover tile
   // amplitudes [1024 w, 1024 w + 1024), so the warp only syncs with itself.
@@ -589,20 +596,21 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
     sts_M(s, tid, r);
   }
   __syncthreads();
-  // round H: tile bits 10..TB-1, then the store and the energy epilogue
+  // round H: tile bits 5 and 10..TB-1, then the store and the energy epilogue
   lds_H<TB>(s, tid, r);
-  round_gates<H, WHT, false, 15 - TB>(r, gt, gm, 10, false);
+  round_gates<1, WHT, false, 1>(r, gt, gm, 5, false);
+  round_gates<H, WHT, false, 2>(r, gt, gm, 10, false);
   const T *table = reinterpret_cast<const T *>(A.table);
   const bool store = A.store_mode != ST_NONE;
   const bool energy = (A.flags & F_ENERGY) != 0;
   T eacc = T(0);
   if (!energy) {
-    for_H(gi, tid, [&](int k, uint32_t y) { out[y] = r.get(k); });
+    for_H(gi, [&](int m, uint32_t y) { *reinterpret_cast<T2 *>(out + y) = r.pair(m); });
   } else {
-    for_H(gi, tid, [&](int k, uint32_t y) {
-      const T v = r.get(k);
-      if (store) out[y] = v;
-      eacc += v * v * table[y];
+    for_H(gi, [&](int m, uint32_t y) {
+      const T2 v = r.pair(m);
+      if (store) *reinterpret_cast<T2 *>(out + y) = v;
+      eacc += v.x * v.x * table[y] + v.y * v.y * table[y + 1];
     });
   }
   if (energy) {
@@ -718,7 +726,7 @@ k_bwd(const PassArgs A) {
     T *sl = buf + L * TILE;
     const uint32_t t = tile_of_block(bx, tiles, pair);
     GIdx<TB, FULL> gi;
-    gi.init(tile_base(t, A.c, A.a, TB), A.c, A.a, lane, w);
+    gi.init(tile_base(t, A.c, A.a, TB), A.c, A.a, lane, w, tid);
 
     Reg32<T> psi, lam;
     // round L (from shared)
@@ -737,7 +745,7 @@ k_bwd(const PassArgs A) {
       eacc = warp_sum(eacc);
       if (lane == 0) ered[par][w] = (double)eacc;
     }
-    round_grads<5>(psi, lam, gm, 5, gred[par][w], lane);
+    round_grads<4, 1>(psi, lam, gm, 6, gred[par][w], lane);
     if (init) __syncwarp();  // lambda = E psi is in shared before round M reads it
     // round M (gradients only)
     if (gm & 0x1Fu) {
@@ -749,8 +757,9 @@ k_bwd(const PassArgs A) {
     __syncthreads();
     lds_H<TB>(sp, tid, psi);
     lds_H<TB>(sl, tid, lam);
-    round_grads<H, 15 - TB>(psi, lam, gm, 10, gred[par][w], lane);
-    round_gates<H, false, true, 15 - TB>(lam, gt, gm, 10, true);
+    round_grads<H, 2, true>(psi, lam, gm, 10, gred[par][w], lane);
+    round_gates<H, false, true, 2>(lam, gt, gm, 10, true);
+    round_gates<1, false, true, 1>(lam, gt, gm, 5, true);
     __syncthreads();  // psi fully read; lambda may be overwritten
     if (more)
       issue(lsrc, nbx, sp);  // next lambda into the psi buffer
@@ -765,12 +774,16 @@ k_bwd(const PassArgs A) {
       __syncwarp();  // M -> L stays inside the warp's 1024 amplitudes
     }
     lds_L(sl, lane, w, lam);
-    round_gates<5, false>(lam, gt, gm, 5, true);
-    for_L(gi, [&](int k, uint32_t y) {
-      if constexpr (FULL)
-        out[cx_inv(y, nmask)] = lam.get(k);
-      else
-        out[y] = lam.get(k);
+    round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
+    for_L(gi, [&](int m, uint32_t y) {
+      const T2 v = lam.pair(m);
+      if constexpr (FULL) {
+        const uint32_t x = cx_inv(y, nmask);
+        out[x] = v.x;
+        out[x ^ 3u] = v.y;
+      } else {
+        *reinterpret_cast<T2 *>(out + y) = v;
+      }
     });
     // gred / ered of this tile were written before the round-H barriers
     if (tid < TB && ((gm >> tid) & 1u)) {
@@ -830,18 +843,24 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   const uint32_t gm = A.gate_mask;
   const bool init = (A.flags & F_LAMBDA_INIT) != 0;
   GIdx<TB, FULL> gi;
-  gi.init(tbase, A.c, A.a, lane, w);
+  gi.init(tbase, A.c, A.a, lane, w, tid);
 
   Reg32<T> psi, lam;
   T eacc = T(0);
-  for_L(gi, [&](int k, uint32_t y) {
-    const T p = __ldcg(in + y);
-    const T l = init ? table[y] * p : __ldcg(lin + y);
-    psi.set(k, p);
-    lam.set(k, l);
-    eacc += p * l;
+  for_L(gi, [&](int m, uint32_t y) {
+    const T2 p = __ldcg(reinterpret_cast<const T2 *>(in + y));
+    T2 l;
+    if (init) {
+      l.x = table[y] * p.x;
+      l.y = table[y + 1] * p.y;
+    } else {
+      l = __ldcg(reinterpret_cast<const T2 *>(lin + y));
+    }
+    psi.set_pair(m, p);
+    lam.set_pair(m, l);
+    eacc += p.x * l.x + p.y * l.y;
   });
-  round_grads<5>(psi, lam, gm, 5, gred[w], lane);
+  round_grads<4, 1>(psi, lam, gm, 6, gred[w], lane);
   sts_L(sp, lane, w, psi);
   sts_L(sl, lane, w, lam);
   if (A.flags & F_ENERGY) {
@@ -856,8 +875,9 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   }
   lds_H<TB>(sp, tid, psi);
   lds_H<TB>(sl, tid, lam);
-  round_grads<H, 15 - TB>(psi, lam, gm, 10, gred[w], lane);
-  round_gates<H, false, true, 15 - TB>(lam, gt, gm, 10, true);
+  round_grads<H, 2, true>(psi, lam, gm, 10, gred[w], lane);
+  round_gates<H, false, true, 2>(lam, gt, gm, 10, true);
+  round_gates<1, false, true, 1>(lam, gt, gm, 5, true);
   __syncthreads();
   sts_H<TB>(sl, tid, lam);
   __syncthreads();
@@ -868,12 +888,16 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
     __syncthreads();
   }
   lds_L(sl, lane, w, lam);
-  round_gates<5, false>(lam, gt, gm, 5, true);
-  for_L(gi, [&](int k, uint32_t y) {
-    if constexpr (FULL)
-      out[cx_inv(y, nmask)] = lam.get(k);
-    else
-      out[y] = lam.get(k);
+  round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
+  for_L(gi, [&](int m, uint32_t y) {
+    const T2 v = lam.pair(m);
+    if constexpr (FULL) {
+      const uint32_t x = cx_inv(y, nmask);
+      out[x] = v.x;
+      out[x ^ 3u] = v.y;
+    } else {
+      *reinterpret_cast<T2 *>(out + y) = v;
+    }
   });
   __syncthreads();
   double *part = A.part + (size_t)job * A.part_stride;
