@@ -163,7 +163,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("gvqe_tile.cuh", "gvqe_kernels.cu", "gvqe_engine.cuh"):
+    for f in ("gvqe_tile.cuh", "gvqe_kernels.cu", "gvqe_engine.cuh", "gvqe_grad_l0.cu"):
         with open(os.path.join(ROOT, "paper_2607_02749_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
