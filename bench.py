@@ -224,6 +224,46 @@ def cluster_leg(steps: int):
             "total_amplitudes": amps, "timing": "wall clock around synchronous gvqe_batch_run calls"}
 
 
+def readout_leg(n: int, reps: int, ham, steps: int):
+    """Readout of the benchmark's state (Section IV-E, Section V-A): most probable
+    bitstring, 8192 shots and CVaR at alpha = 0.2, FP32, one parameter vector."""
+    import numpy as np
+    import torch
+
+    import paper_2607_02749_gb300 as gv
+    from paper_2607_02749_gb300 import workloads as wl
+
+    a = gv.Ansatz(n, reps)
+    h = gv.Hamiltonian.from_workload(ham)
+    th = torch.as_tensor(wl.thetas(n, reps, 1, seed=1)[0], dtype=torch.float64, device="cuda")
+    u = torch.as_tensor(np.random.Generator(np.random.PCG64(0)).random(8192), device="cuda")
+    r = gv.readout(a, h, th, alpha=0.2, uniforms=u)
+    gv.readout(a, None, th, alpha=0.0, shots=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r = gv.readout(a, h, th, alpha=0.2, uniforms=u)
+    torch.cuda.synchronize()
+    t_all = (time.perf_counter() - t0) / steps
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        gv.readout(a, None, th, alpha=0.0, shots=0)
+    torch.cuda.synchronize()
+    t_state = (time.perf_counter() - t0) / steps
+    amps = 2 ** n
+    # CVaR search: the FP64 table once for its range, once per histogram pass
+    # and once for the tail sums; the amplitudes once for the tail sums
+    cvar_bytes = (8 * (r.passes + 2) + 4) * amps
+    a.close()
+    h.close()
+    return {"ms_per_readout": t_all * 1e3, "ms_state_and_argmax": t_state * 1e3,
+            "ms_shots_and_cvar": (t_all - t_state) * 1e3, "shots": 8192, "alpha": 0.2,
+            "cvar_histogram_passes": r.passes, "cvar_min_bytes": cvar_bytes,
+            "cvar_GBps": cvar_bytes / max(t_all - t_state, 1e-9) / 1e9,
+            "argmax": r.argmax, "p_max": r.p_max, "cvar": r.cvar, "total": r.total,
+            "timing": "wall clock around synchronous gvqe_readout calls (state preparation included)"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -405,6 +445,7 @@ def run_gvqe(args):
 
     if rank == 0 and not args.no_comparators:
         out["cluster_batch"] = cluster_leg(args.steps)
+        out["readout"] = readout_leg(n, reps, ham, max(1, min(args.steps, 3)))
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:

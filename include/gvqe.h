@@ -171,6 +171,42 @@ int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *con
 int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int batch,
                        double *energies, int flags, void *stream);
 
+/*
+ * gvqe_readout -- read out the prepared state |psi(theta)> (Section IV-E:
+ * sample the final state, take the most probable bitstring; Section V-A:
+ * 8192 shots, seed 0, and the CVaR-alpha objective of Section II).
+ * p(x) = |psi(x)|^2 over the 2^n computational basis states, total = sum_x p(x)
+ * (1 up to rounding; shots and CVaR use p / total).
+ *   a, h:     handles with equal n; h is only read when alpha > 0 and may be
+ *             NULL otherwise.
+ *   params:   device, P doubles (one parameter vector).
+ *   flags:    GVQE_FP32 or GVQE_FP64 (state precision; p, sums and the CVaR
+ *             are FP64 either way).
+ *   alpha:    CVaR level in (0, 1], or 0 to skip it.  CVaR_alpha =
+ *             (1/alpha) * integral_0^alpha F^-1(u) du, F the distribution of
+ *             the outcome energy E(x) = <x|H|x> (the I/Z terms of H) under p:
+ *             the mean energy of the lowest-energy alpha fraction of outcomes,
+ *             the boundary outcome counted fractionally.
+ *   n_shots:  >= 0.  uniforms: device, n_shots doubles in [0, 1) (the caller's
+ *             random numbers; NULL when n_shots is 0).  shots: device,
+ *             n_shots int64 (or NULL when n_shots is 0): shot k is the
+ *             smallest x whose cumulative probability (in increasing x)
+ *             exceeds uniforms[k] * total.
+ *   stats:    device, 4 doubles: p(argmax), CVaR_alpha (NaN when alpha is 0),
+ *             total, and the number of histogram passes the CVaR search made
+ *             over the state (0 when alpha is 0).  argmax: device, 1 int64: the
+ *             most probable x (smallest x on ties).
+ * Deterministic (fixed summation orders, integer histogram counts).  The
+ * CVaR search reads small histograms back to the host, so the call
+ * synchronises `stream`.
+ * Errors: GVQE_EINVAL (bad handle or pointer, alpha outside [0, 1],
+ * n_shots < 0), GVQE_ENOMEM, GVQE_ECUDA, GVQE_EUNSUPPORTED (CVaR search did
+ * not converge).
+ */
+int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int flags, double alpha,
+                 int n_shots, const double *uniforms, int64_t *shots, double *stats, int64_t *argmax,
+                 void *stream);
+
 /* gvqe_destroy -- free any handle above; NULL is accepted.  Synchronises the
  * device work the handle enqueued before freeing its memory. */
 int gvqe_destroy(void *handle);

@@ -14,14 +14,14 @@ from . import _lib
 from ._lib import (GVQE_ENT_LINEAR, GVQE_FP32, GVQE_FP64, GVQE_GRAD_ADJOINT, GVQE_GRAD_PARAM_SHIFT,
                    GVQE_OPT_TILE_BITS, GvqeError, gvqe_ansatz_create, gvqe_ansatz_set_option, gvqe_batch_create,
                    gvqe_batch_run, gvqe_destroy, gvqe_energy, gvqe_energy_grad, gvqe_hamiltonian_create,
-                   gvqe_hamiltonian_stats, gvqe_last_error, gvqe_plan_describe, gvqe_version)
+                   gvqe_hamiltonian_stats, gvqe_last_error, gvqe_plan_describe, gvqe_readout, gvqe_version)
 
 __all__ = [
-    "Hamiltonian", "Ansatz", "Batch", "GvqeEnergy", "energy", "energy_grad", "GvqeError",
+    "Hamiltonian", "Ansatz", "Batch", "GvqeEnergy", "energy", "energy_grad", "readout", "Readout", "GvqeError",
     "GVQE_FP32", "GVQE_FP64", "GVQE_GRAD_ADJOINT", "GVQE_GRAD_PARAM_SHIFT", "GVQE_ENT_LINEAR",
     "gvqe_hamiltonian_create", "gvqe_ansatz_create", "gvqe_ansatz_set_option", "gvqe_energy",
     "gvqe_energy_grad", "gvqe_batch_create", "gvqe_batch_run", "gvqe_destroy", "gvqe_last_error",
-    "gvqe_plan_describe", "gvqe_hamiltonian_stats", "gvqe_version",
+    "gvqe_plan_describe", "gvqe_hamiltonian_stats", "gvqe_readout", "gvqe_version",
 ]
 
 
@@ -95,6 +95,44 @@ def energy_grad(ansatz: Ansatz, ham: Hamiltonian, theta, mask=None, fp64: bool =
     m = None if mask is None else mask.reshape(th.shape).to(torch.uint8).contiguous()
     gvqe_energy_grad(ansatz.handle, ham.handle, th, m, e, g, _flags(fp64, param_shift), stream)
     return e, g
+
+
+class Readout:
+    """Result of readout(): the most probable bitstring, its probability, the
+    shots, CVaR_alpha of the outcome energy and the total probability."""
+
+    def __init__(self, argmax: int, p_max: float, cvar: float, total: float, shots, passes: int = 0):
+        self.argmax, self.p_max, self.cvar, self.total, self.shots = argmax, p_max, cvar, total, shots
+        self.passes = passes  # histogram passes of the CVaR search
+
+    def bitstring(self, n: int) -> str:
+        """The most probable x as a string whose character q is qubit q."""
+        return "".join("1" if (self.argmax >> q) & 1 else "0" for q in range(n))
+
+
+def readout(ansatz: Ansatz, ham: Optional[Hamiltonian], theta, alpha: float = 0.2, shots: int = 8192,
+            seed: Optional[int] = 0, uniforms=None, fp64: bool = False, stream=None) -> Readout:
+    """Read out |psi(theta)> (Section IV-E; 8192 shots with seed 0 and CVaR
+    alpha = 0.2 as in Section V-A).  The shots use `uniforms` (CUDA float64, in
+    [0, 1)) or, when None, `shots` draws of numpy's PCG64(seed) made on the host.
+    alpha = 0 skips the CVaR (ham may then be None)."""
+    import numpy as np
+    import torch
+
+    th = theta.reshape(-1).to(torch.float64).contiguous()
+    dev = th.device
+    if uniforms is None and shots > 0:
+        u = np.random.Generator(np.random.PCG64(seed)).random(shots)
+        uniforms = torch.as_tensor(u, dtype=torch.float64, device=dev)
+    n_shots = 0 if uniforms is None else int(uniforms.numel())
+    out = torch.empty(max(1, n_shots), dtype=torch.int64, device=dev)
+    stats = torch.empty(4, dtype=torch.float64, device=dev)
+    amax = torch.empty(1, dtype=torch.int64, device=dev)
+    gvqe_readout(ansatz.handle, None if ham is None else ham.handle, th, alpha,
+                 None if n_shots == 0 else uniforms.contiguous(), out if n_shots else None, stats, amax,
+                 _flags(fp64), stream)
+    st = stats.cpu().tolist()
+    return Readout(int(amax.item()), st[0], st[1], st[2], out[:n_shots], int(st[3]))
 
 
 class Batch(_Handle):

@@ -66,6 +66,7 @@ _SIGS = {
     "gvqe_batch_create": [_I, _VP, _VP, _I, ctypes.POINTER(_VP)],
     "gvqe_energy_static": [_VP, _VP, _VP, _I, _VP, _I, _VP],
     "gvqe_batch_run": [_VP, _VP, _VP, _VP, _VP, _VP],
+    "gvqe_readout": [_VP, _VP, _VP, _I, ctypes.c_double, _I, _VP, _VP, _VP, _VP, _VP],
     "gvqe_destroy": [_VP],
     "gvqe_plan_describe": [_I, _I, _I, _I, ctypes.c_char_p, _I],
     "gvqe_hamiltonian_stats": [_VP, _VP, _VP, _VP, _VP],
@@ -202,6 +203,19 @@ def gvqe_energy_static(ansatz: int, ham: int, params, energies, flags: int = GVQ
     batch = params.shape[0] if params.dim() == 2 else 1
     _check(load().gvqe_energy_static(ansatz, ham, _ptr(params), batch, _ptr(energies), flags, _stream(stream)),
            "gvqe_energy_static")
+
+
+def gvqe_readout(ansatz: int, ham: Optional[int], params, alpha: float, uniforms, shots, stats, argmax,
+                 flags: int = GVQE_FP32, stream=None) -> None:
+    """Readout of |psi(params)>: most probable x, shots by inverse CDF, CVaR-alpha (alpha 0 skips it).
+
+    stats (4 doubles) <- p(argmax), CVaR, total probability, CVaR histogram passes; argmax (1 int64);
+    shots (int64, one per uniform).  Synchronises the stream.
+    """
+    _require_cuda(params, uniforms, shots, stats, argmax)
+    n_shots = 0 if uniforms is None else int(uniforms.numel())
+    _check(load().gvqe_readout(ansatz, ham, _ptr(params), flags, float(alpha), n_shots, _ptr(uniforms),
+                               _ptr(shots), _ptr(stats), _ptr(argmax), _stream(stream)), "gvqe_readout")
 
 
 def gvqe_batch_create(ansatze: Sequence[int], hams: Sequence[int], flags: int = GVQE_FP32) -> int:

@@ -198,7 +198,8 @@ static int qubit_of(const LayerPass &lp, int i) { return i < lp.c ? i : lp.a + i
 static long long tiles_of(int n, int tb) { return 1LL << (n - tb); }
 
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
-Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0) {
+Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0,
+                bool state_only) {
   Plan pl;
   pl.n = n;
   pl.reps = reps;
@@ -235,7 +236,11 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
     PP1 = nb++;
   }
   int LAM0 = -1, LAM1 = -1;
-  if (want_grad || !diag) LAM0 = nb++;
+  if (state_only) {  // the forward passes alone, the final state kept in a buffer
+    want_grad = false;
+    diag = false;
+  }
+  if (want_grad || (!diag && !state_only)) LAM0 = nb++;
   if (want_grad) LAM1 = nb++;
   int XYB = -1;
   if (reps == 0 && !diag) XYB = nb++;
@@ -311,6 +316,11 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
     }
   }
   if (reps > 0) last_state = cur;
+  if (state_only) {
+    pl.final_buf = last_state;
+    pl.part_stride = 0;
+    return pl;
+  }
 
   // X/Y energy (and lambda) for a non-diagonal H
   int lam_cur = -1;
@@ -579,11 +589,11 @@ static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s) {
 }
 
 // --------------------------------------------------------- plan execution --
-static Plan *get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag) {
-  const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0);
+static Plan *get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool state_only = false) {
+  const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0) | (state_only ? 8 : 0);
   auto it = a->plans.find(key);
   if (it != a->plans.end() && it->second.tile_bits == a->tile_bits) return &it->second;
-  Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, want_grad, diag);
+  Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, want_grad, diag, false, state_only);
   pl.tile_bits = a->tile_bits;
   a->plans[key] = std::move(pl);
   return &a->plans[key];
@@ -598,8 +608,10 @@ static int upload_dir(Plan *pl) {
 }
 
 // Run the plan for `batch` parameter vectors (already converted to cs on device).
+// With a state-only plan, *state receives job 0's final state (batch must be 1).
 static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const void *cs_all, const uint8_t *mask,
-                    int batch, double *E, double *grad, const int *minlayer, cudaStream_t s) {
+                    int batch, double *E, double *grad, const int *minlayer, cudaStream_t s,
+                    void **state = nullptr) {
   const int prec = pl->prec;
   const size_t es = prec ? 8 : 4;
   const long long S = pl->state_elems;
@@ -625,8 +637,9 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
     if (id < 0) return nullptr;
     return bufs + (size_t)id * J * S * es;  // buffer id, job slots contiguous
   };
-  const void *table = prec ? h->T64.ptr : h->T32.ptr;
-  const void *tc = prec ? (const void *)h->d_tc64 : (const void *)h->d_tc32;
+  const void *table = h ? (prec ? h->T64.ptr : h->T32.ptr) : nullptr;
+  const void *tc = h ? (prec ? (const void *)h->d_tc64 : (const void *)h->d_tc32) : nullptr;
+  if (state) *state = buf_ptr(pl->final_buf);
   for (int j0 = 0; j0 < batch; j0 += J) {
     const int jobs = std::min(J, batch - j0);
     for (const PassStep &st : pl->steps) {
@@ -688,6 +701,7 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
         g0 = g1;
       }
     }
+    if (pl->dir.empty()) continue;
     count_launches(1);
     GV_CUDA(launch_reduce(part, pl->part_stride, (const RedEntry *)pl->d_dir.ptr, pl->d_dir_count, mask ? mask + (size_t)j0 * pl->P : nullptr,
                           pl->P, E + j0, grad ? grad + (size_t)j0 * pl->P : nullptr, jobs, s));
@@ -890,6 +904,149 @@ int gvqe_energy_grad(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, co
   return energy_impl(a, h, params, mask, batch, energies, grad, prec, (cudaStream_t)stream);
 }
 
+// ----------------------------------------------------------------- readout --
+static unsigned long long double_to_key(double d) {
+  unsigned long long b;
+  memcpy(&b, &d, sizeof(b));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+static double key_to_double(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  double d;
+  memcpy(&d, &b, sizeof(d));
+  return d;
+}
+
+int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int flags, double alpha, int n_shots,
+                 const double *uniforms, int64_t *shots, double *stats, int64_t *argmax, void *stream) {
+  g_err.clear();
+  if (!is_ansatz(a)) return fail(GVQE_EINVAL, "invalid ansatz handle");
+  if (!params || !stats || !argmax) return fail(GVQE_EINVAL, "params, stats and argmax must be device pointers");
+  if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(GVQE_EINVAL, "alpha %g is outside [0, 1]", alpha);
+  if (n_shots < 0 || (n_shots > 0 && (!uniforms || !shots)))
+    return fail(GVQE_EINVAL, "n_shots %d needs uniforms and shots", n_shots);
+  if (alpha > 0.0) GV_TRY(check_pair(a, h));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int prec = flags & GVQE_FP64 ? 1 : 0;
+  const int n = a->n;
+  // the state
+  Plan *pl = get_plan(a, prec, false, false, true);
+  const int P = pl->P;
+  GV_TRY(a->aux.reserve((size_t)P * (prec ? 16 : 8) + 256));
+  GV_CUDA(launch_trig(prec, params, P, a->aux.ptr, s));
+  count_launches(1);
+  void *psi = nullptr;
+  GV_TRY(run_plan(a, nullptr, pl, a->aux.ptr, nullptr, 1, nullptr, nullptr, nullptr, s, &psi));
+  if (!psi) return fail(GVQE_EUNSUPPORTED, "the state plan kept no state");
+  // workspace: chunk sums, maxima, indices, cdf, bin edges and masses, extremes, tail partials
+  const long long nch = 1LL << (n - readout_chunk_bits(n));
+  const int nparts = readout_tail_parts();
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t o_cmax = up(8 * nch), o_cidx = o_cmax + up(8 * nch), o_cdf = o_cidx + up(8 * nch);
+  const size_t o_edges = o_cdf + up(8 * (nch + 1)), o_mass = o_edges + up(8 * (RO_BINS + 1));
+  const size_t o_ext = o_mass + up(8 * RO_BINS), o_part = o_ext + up(8 * 4);
+  const size_t total_bytes = o_part + up(8 * 3 * (size_t)nparts);
+  GV_TRY(a->ro.reserve(total_bytes));
+  char *w = (char *)a->ro.ptr;
+  double *csum = (double *)w, *cmax = (double *)(w + o_cmax), *cdf = (double *)(w + o_cdf);
+  long long *cidx = (long long *)(w + o_cidx);
+  unsigned long long *edges = (unsigned long long *)(w + o_edges);
+  double *part = (double *)(w + o_part);
+  unsigned long long *mass = (unsigned long long *)(w + o_mass), *ext = (unsigned long long *)(w + o_ext);
+  GV_CUDA(launch_ro_prob(prec, psi, n, csum, cmax, cidx, cdf, stats, (long long *)argmax, s));
+  count_launches(2);
+  if (n_shots > 0) {
+    GV_CUDA(launch_ro_sample(prec, psi, n, cdf, uniforms, n_shots, (long long *)shots, s));
+    count_launches(1);
+  }
+  if (alpha == 0.0) {
+    const double tail[3] = {std::nan(""), 0.0, 0.0};  // stats[1], and stats[3] = 0 passes
+    GV_CUDA(cudaMemcpyAsync(stats + 1, &tail[0], sizeof(double), cudaMemcpyHostToDevice, s));
+    GV_CUDA(cudaMemcpyAsync(stats + 3, &tail[1], sizeof(double), cudaMemcpyHostToDevice, s));
+    GV_CUDA(cudaStreamSynchronize(s));
+    return GVQE_OK;
+  }
+  // CVaR: the alpha-quantile tau of E under p by histogram passes, then the tail sums
+  GV_TRY(ensure_tables(h, 1, s));
+  const double *E = (const double *)h->T64.ptr;
+  unsigned long long hext[4] = {0ull, ~0ull, 0ull, 0ull};
+  GV_CUDA(cudaMemcpyAsync(ext, hext, sizeof(hext), cudaMemcpyHostToDevice, s));
+  GV_CUDA(launch_ro_minmax(E, n, ext, s));
+  count_launches(1);
+  GV_CUDA(cudaMemcpyAsync(hext, ext, sizeof(hext), cudaMemcpyDeviceToHost, s));
+  GV_CUDA(cudaStreamSynchronize(s));
+  // bins of equal energy width over [lo, hi), passed as the keys of their edges
+  double lo = key_to_double(hext[1]);
+  double hi = std::nextafter(key_to_double(hext[2]), HUGE_VAL);
+  std::vector<double> hedges(RO_BINS + 1);
+  std::vector<unsigned long long> hkeys(RO_BINS + 1), hmass(RO_BINS);
+  unsigned long long target = 0, below = 0;  // mass under the current range
+  double tau = 0.0;
+  bool done = false;
+  int passes = 0;
+  for (int pass = 0; pass < 48 && !done; ++pass) {
+    ++passes;
+    const double wdt = (hi - lo) / RO_BINS;
+    for (int k = 0; k < RO_BINS; ++k) hedges[k] = std::min(hi, lo + wdt * k);
+    hedges[0] = lo;
+    hedges[RO_BINS] = hi;
+    for (int k = 1; k <= RO_BINS; ++k) hedges[k] = std::max(hedges[k], hedges[k - 1]);
+    for (int k = 0; k <= RO_BINS; ++k) hkeys[k] = double_to_key(hedges[k]);
+    unsigned long long z[4] = {0ull, ~0ull, 0ull, 0ull};
+    GV_CUDA(cudaMemcpyAsync(edges, hkeys.data(), 8 * (RO_BINS + 1), cudaMemcpyHostToDevice, s));
+    GV_CUDA(cudaMemsetAsync(mass, 0, 8 * RO_BINS, s));
+    GV_CUDA(cudaMemcpyAsync(ext, z, sizeof(z), cudaMemcpyHostToDevice, s));
+    GV_CUDA(launch_ro_hist(prec, psi, E, n, edges, mass, ext, s));
+    count_launches(1);
+    GV_CUDA(cudaMemcpyAsync(hmass.data(), mass, 8 * RO_BINS, cudaMemcpyDeviceToHost, s));
+    GV_CUDA(cudaMemcpyAsync(hext, ext, sizeof(hext), cudaMemcpyDeviceToHost, s));
+    GV_CUDA(cudaStreamSynchronize(s));
+    if (pass == 0) {
+      unsigned long long tot = 0;
+      for (int k = 0; k < RO_BINS; ++k) tot += hmass[k];
+      if (tot == 0) return fail(GVQE_EUNSUPPORTED, "the state has no probability mass");
+      const double t = alpha * (double)tot;
+      target = t < 1.0 ? 1ull : (unsigned long long)t;
+      if (target > tot) target = tot;
+    }
+    if (hext[1] == hext[2]) {  // one energy value left in the range
+      tau = key_to_double(hext[1]);
+      done = true;
+      break;
+    }
+    // the first bin where the mass at or below it reaches the target (the
+    // last populated bin if rounding leaves the target above the total)
+    unsigned long long cum = below, at_b = below, before_last = below;
+    int b = -1, lastnz = -1;
+    for (int k = 0; k < RO_BINS; ++k) {
+      if (hmass[k] == 0) continue;
+      if (cum + hmass[k] >= target) {
+        b = k;
+        at_b = cum;
+        break;
+      }
+      lastnz = k;
+      before_last = cum;
+      cum += hmass[k];
+    }
+    if (b < 0) {
+      b = lastnz;
+      at_b = before_last;
+    }
+    if (b < 0) return fail(GVQE_EUNSUPPORTED, "CVaR search lost the quantile");
+    below = at_b;
+    lo = hedges[b];
+    hi = hedges[b + 1];
+  }
+  if (!done) return fail(GVQE_EUNSUPPORTED, "CVaR search did not converge");
+  GV_CUDA(launch_ro_cvar(prec, psi, E, n, alpha, tau, part, stats, s));
+  count_launches(2);
+  const double npass = passes;
+  GV_CUDA(cudaMemcpyAsync(stats + 3, &npass, sizeof(double), cudaMemcpyHostToDevice, s));
+  GV_CUDA(cudaStreamSynchronize(s));
+  return GVQE_OK;
+}
+
 int gvqe_plan_describe(int n_qubits, int reps, int flags, int tile_bits, char *buf, int buflen) {
   g_err.clear();
   if (n_qubits < 1 || n_qubits > GVQE_MAX_QUBITS || reps < 0 || reps > 64)
@@ -927,6 +1084,7 @@ int gvqe_destroy(void *handle) {
     a->ws.release();
     a->aux.release();
     a->shift.release();
+    a->ro.release();
     for (auto &kv : a->plans) kv.second.d_dir.release();
     a->magic = 0;
     delete a;

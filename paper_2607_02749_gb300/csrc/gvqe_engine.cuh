@@ -117,6 +117,27 @@ cudaError_t launch_shift_params(const double *params, int P, int jobs, const int
                                 int n_active, double *out, cudaStream_t s);
 cudaError_t launch_shift_combine(const double *Es, int P, int jobs, const int *active, int n_active,
                                  double *E, double *grad, cudaStream_t s);
+// Readout of a prepared state (gvqe_readout.cu).  Chunks of 2^readout_chunk_bits(n)
+// amplitudes; RO_BINS histogram bins per CVaR search pass.
+constexpr int RO_BINS = 2048;
+int readout_chunk_bits(int n);
+int readout_tail_parts();
+// csum/cmax/cidx: [chunks], cdf: [chunks + 1]; writes stats[0] (largest p),
+// stats[2] (total) and argmax[0].
+cudaError_t launch_ro_prob(int prec, const void *psi, int n, double *csum, double *cmax, long long *cidx,
+                           double *cdf, double *stats, long long *argmax, cudaStream_t s);
+cudaError_t launch_ro_sample(int prec, const void *psi, int n, const double *cdf, const double *u, int nshots,
+                             long long *shots, cudaStream_t s);
+// ext[1] / ext[2]: order-preserving keys of the smallest / largest E (atomic min / max).
+cudaError_t launch_ro_minmax(const double *E, int n, unsigned long long *ext, cudaStream_t s);
+// edges: RO_BINS + 1 device keys, the order-preserving unsigned images of
+// non-decreasing bin-edge energies; gmass: RO_BINS counters; ext[1..2] as
+// described in the kernel.
+cudaError_t launch_ro_hist(int prec, const void *psi, const double *E, int n, const unsigned long long *edges,
+                           unsigned long long *gmass, unsigned long long *ext, cudaStream_t s);
+// part: 3 * readout_tail_parts() doubles; writes stats[1].
+cudaError_t launch_ro_cvar(int prec, const void *psi, const double *E, int n, double alpha, double tau,
+                           double *part, double *stats, cudaStream_t s);
 // Largest tile size (log2 amplitudes) whose backward pass fits in shared memory.
 int max_tile_bits(int prec);
 // Multiprocessors of the current device (queried once).

@@ -54,6 +54,7 @@ struct Plan {
   long long part_stride = 0;  // doubles of partial sums per job
   std::map<int, RedEntry> param_dir;
   std::vector<RedEntry> dir;  // energy entry first, then one per parameter
+  int final_buf = -1;         // state-only plans: buffer of the final state
   DevBuf d_dir;
   int d_dir_count = 0;
 };
@@ -63,7 +64,9 @@ void count_launches(int k);
 // tile_grad_l0: lay the layer-0 gradient partials out per tile (one CTA of
 // tile bits per partial), as the persistent batch kernel computes them,
 // instead of per warp of the standalone layer-0 gradient pass.
-Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false);
+// state_only: the forward passes alone, the final state kept (Plan::final_buf).
+Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false,
+                bool state_only = false);
 std::string describe_plan(const Plan &pl);
 
 }  // namespace gvqe
@@ -94,7 +97,7 @@ struct gvqe_ansatz_s {
   int n = 0, reps = 0, ent = 0;
   int tile_bits = 0;  // 0 = automatic
   std::map<int, gvqe::Plan> plans;
-  gvqe::DevBuf ws, aux, shift;
+  gvqe::DevBuf ws, aux, shift, ro;
 };
 
 struct gvqe_batch_s;
