@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--workload", default="n30_reps6_z20000")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true", help="skip the FP64 comparator legs")
+    ap.add_argument("--only-readout", action="store_true",
+                    help="run only the readout leg on the workload and print its JSON object")
     return ap.parse_args()
 
 
@@ -314,6 +316,11 @@ def run_gvqe(args):
     w = wl.WORKLOADS[args.workload]
     n, reps, B = w["n"], w["reps"], w["batch"]
     ham, _ = wl.make_workload(args.workload, batch=1)
+    if args.only_readout:
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "readout": readout_leg(n, reps, ham, max(1, args.steps))}),
+                  flush=True)
+        return 0
     theta = wl.thetas(n, reps, B, seed=1 + rank)
     P = n * (reps + 1)
     dev = torch.device("cuda", local)

@@ -945,7 +945,8 @@ int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int fl
   const size_t o_cmax = up(8 * nch), o_cidx = o_cmax + up(8 * nch), o_cdf = o_cidx + up(8 * nch);
   const size_t o_edges = o_cdf + up(8 * (nch + 1)), o_mass = o_edges + up(8 * (RO_BINS + 1));
   const size_t o_ext = o_mass + up(8 * RO_BINS), o_part = o_ext + up(8 * 4);
-  const size_t total_bytes = o_part + up(8 * 3 * (size_t)nparts);
+  const size_t o_es = o_part + up(8 * 3 * (size_t)nparts);  // energies at the shots
+  const size_t total_bytes = o_es + up(8 * (size_t)std::max(n_shots, 1));
   GV_TRY(a->ro.reserve(total_bytes));
   char *w = (char *)a->ro.ptr;
   double *csum = (double *)w, *cmax = (double *)(w + o_cmax), *cdf = (double *)(w + o_cdf);
@@ -970,21 +971,14 @@ int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int fl
   GV_TRY(ensure_tables(h, 1, s));
   const double *E = (const double *)h->T64.ptr;
   unsigned long long hext[4] = {0ull, ~0ull, 0ull, 0ull};
-  GV_CUDA(cudaMemcpyAsync(ext, hext, sizeof(hext), cudaMemcpyHostToDevice, s));
-  GV_CUDA(launch_ro_minmax(E, n, ext, s));
-  count_launches(1);
-  GV_CUDA(cudaMemcpyAsync(hext, ext, sizeof(hext), cudaMemcpyDeviceToHost, s));
-  GV_CUDA(cudaStreamSynchronize(s));
-  // bins of equal energy width over [lo, hi), passed as the keys of their edges
-  double lo = key_to_double(hext[1]);
-  double hi = std::nextafter(key_to_double(hext[2]), HUGE_VAL);
   std::vector<double> hedges(RO_BINS + 1);
   std::vector<unsigned long long> hkeys(RO_BINS + 1), hmass(RO_BINS);
-  unsigned long long target = 0, below = 0;  // mass under the current range
-  double tau = 0.0;
-  bool done = false;
+  unsigned long long tot = 0, target = 0, below = 0;  // integer masses; below: under the current range
+  double lo = 0.0, hi = 0.0, tau = 0.0;
+  bool done = false, bracket = false;
   int passes = 0;
-  for (int pass = 0; pass < 48 && !done; ++pass) {
+  // one histogram pass over [lo, hi) (with_outside: also the masses outside it)
+  auto hist_pass = [&](bool with_outside) -> int {
     ++passes;
     const double wdt = (hi - lo) / RO_BINS;
     for (int k = 0; k < RO_BINS; ++k) hedges[k] = std::min(hi, lo + wdt * k);
@@ -996,19 +990,67 @@ int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int fl
     GV_CUDA(cudaMemcpyAsync(edges, hkeys.data(), 8 * (RO_BINS + 1), cudaMemcpyHostToDevice, s));
     GV_CUDA(cudaMemsetAsync(mass, 0, 8 * RO_BINS, s));
     GV_CUDA(cudaMemcpyAsync(ext, z, sizeof(z), cudaMemcpyHostToDevice, s));
-    GV_CUDA(launch_ro_hist(prec, psi, E, n, edges, mass, ext, s));
+    GV_CUDA(launch_ro_hist(prec, psi, E, n, edges, mass, ext, with_outside ? 1 : 0, s));
     count_launches(1);
     GV_CUDA(cudaMemcpyAsync(hmass.data(), mass, 8 * RO_BINS, cudaMemcpyDeviceToHost, s));
     GV_CUDA(cudaMemcpyAsync(hext, ext, sizeof(hext), cudaMemcpyDeviceToHost, s));
     GV_CUDA(cudaStreamSynchronize(s));
-    if (pass == 0) {
-      unsigned long long tot = 0;
-      for (int k = 0; k < RO_BINS; ++k) tot += hmass[k];
-      if (tot == 0) return fail(GVQE_EUNSUPPORTED, "the state has no probability mass");
-      const double t = alpha * (double)tot;
-      target = t < 1.0 ? 1ull : (unsigned long long)t;
-      if (target > tot) target = tot;
+    return GVQE_OK;
+  };
+  auto in_range_mass = [&]() {
+    unsigned long long m = 0;
+    for (int k = 0; k < RO_BINS; ++k) m += hmass[k];
+    return m;
+  };
+  auto set_target = [&]() -> int {
+    if (tot == 0) return fail(GVQE_EUNSUPPORTED, "the state has no probability mass");
+    const double t = alpha * (double)tot;
+    target = t < 1.0 ? 1ull : (unsigned long long)t;
+    if (target > tot) target = tot;
+    return GVQE_OK;
+  };
+  // A bracket from the shots' energies: their empirical alpha-quantile +- 4
+  // standard errors.  One pass checks that it holds the quantile (and counts the
+  // mass below and above it); otherwise the search starts from the full range.
+  if (n_shots >= 256 && alpha < 1.0) {
+    double *es = (double *)(w + o_es);
+    GV_CUDA(launch_ro_gather(E, (const long long *)shots, n_shots, es, s));
+    count_launches(1);
+    std::vector<double> hes((size_t)n_shots);
+    GV_CUDA(cudaMemcpyAsync(hes.data(), es, 8 * (size_t)n_shots, cudaMemcpyDeviceToHost, s));
+    GV_CUDA(cudaStreamSynchronize(s));
+    std::sort(hes.begin(), hes.end());
+    const double K = n_shots, d = 4.0 * std::sqrt(alpha * (1.0 - alpha) / K) + 2.0 / K;
+    if (alpha - d > 0.0 && alpha + d < 1.0) {
+      const long long ilo = (long long)std::floor((alpha - d) * K);
+      const long long ihi = std::min<long long>(n_shots - 1, (long long)std::ceil((alpha + d) * K));
+      lo = hes[(size_t)ilo];
+      hi = std::nextafter(hes[(size_t)ihi], HUGE_VAL);
+      GV_TRY(hist_pass(true));
+      tot = hext[0] + in_range_mass() + hext[3];
+      GV_TRY(set_target());
+      below = hext[0];
+      bracket = below < target && target <= below + in_range_mass();
     }
+  }
+  if (!bracket) {
+    const unsigned long long mm[4] = {0ull, ~0ull, 0ull, 0ull};
+    GV_CUDA(cudaMemcpyAsync(ext, mm, sizeof(mm), cudaMemcpyHostToDevice, s));
+    GV_CUDA(launch_ro_minmax(E, n, ext, s));
+    count_launches(1);
+    GV_CUDA(cudaMemcpyAsync(hext, ext, sizeof(hext), cudaMemcpyDeviceToHost, s));
+    GV_CUDA(cudaStreamSynchronize(s));
+    lo = key_to_double(hext[1]);
+    hi = std::nextafter(key_to_double(hext[2]), HUGE_VAL);
+    below = 0;
+    GV_TRY(hist_pass(false));
+    if (tot == 0) {
+      tot = in_range_mass();
+      GV_TRY(set_target());
+    }
+  }
+  for (int pass = 0; pass < 48; ++pass) {
+    if (pass > 0) GV_TRY(hist_pass(false));
     if (hext[1] == hext[2]) {  // one energy value left in the range
       tau = key_to_double(hext[1]);
       done = true;

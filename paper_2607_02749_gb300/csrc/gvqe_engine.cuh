@@ -133,8 +133,11 @@ cudaError_t launch_ro_minmax(const double *E, int n, unsigned long long *ext, cu
 // edges: RO_BINS + 1 device keys, the order-preserving unsigned images of
 // non-decreasing bin-edge energies; gmass: RO_BINS counters; ext[1..2] as
 // described in the kernel.
+// below != 0: also the integer mass under the range into ext[0].
 cudaError_t launch_ro_hist(int prec, const void *psi, const double *E, int n, const unsigned long long *edges,
-                           unsigned long long *gmass, unsigned long long *ext, cudaStream_t s);
+                           unsigned long long *gmass, unsigned long long *ext, int below, cudaStream_t s);
+// out[k] = E[shots[k]] for k < nshots.
+cudaError_t launch_ro_gather(const double *E, const long long *shots, int nshots, double *out, cudaStream_t s);
 // part: 3 * readout_tail_parts() doubles; writes stats[1].
 cudaError_t launch_ro_cvar(int prec, const void *psi, const double *E, int n, double alpha, double tau,
                            double *part, double *stats, cudaStream_t s);

@@ -248,12 +248,13 @@ __global__ void __launch_bounds__(RO_NT) k_ro_minmax(const double *E, long long 
 // One pass of the quantile search over the keys [edges[0], edges[RO_BINS]):
 // the integer mass (p * 2^60) of every bin [edges[b], edges[b+1]) and the keys
 // of the smallest and largest E inside the range (ext[1], ext[2]).  The edges
-// are the keys of evenly spaced energies.  Only x inside the range read their
-// amplitude (the mass below the range is known from earlier passes).
+// are the keys of evenly spaced energies.  With `below` set, the masses under
+// and above the range are summed too (ext[0], ext[3]); otherwise only x inside
+// the range read their amplitude (the mass below is known from earlier passes).
 template <typename T>
 __global__ void __launch_bounds__(RO_NT) k_ro_hist(const T *psi, const double *E, long long N,
                                                    const unsigned long long *edges, unsigned long long *gmass,
-                                                   unsigned long long *ext) {
+                                                   unsigned long long *ext, int below) {
   __shared__ unsigned long long se[RO_BINS + 1];
   __shared__ unsigned long long sm[RO_BINS];
   __shared__ unsigned long long smin, smax;
@@ -267,8 +268,18 @@ __global__ void __launch_bounds__(RO_NT) k_ro_hist(const T *psi, const double *E
   }
   __syncthreads();
   const unsigned long long lo = se[0], hi = se[RO_BINS];
-  unsigned long long kmin = ~0ull, kmax = 0ull;
+  const unsigned long long lo_read = below ? 0ull : lo;   // keys in [lo_read, hi_read) read psi
+  const unsigned long long hi_read = below ? ~0ull : hi;
+  unsigned long long kmin = ~0ull, kmax = 0ull, qbelow = 0ull, qabove = 0ull;
   auto add = [&](unsigned long long k, T v) {
+    if (k < lo) {
+      qbelow += qmass(v);
+      return;
+    }
+    if (k >= hi) {
+      qabove += qmass(v);
+      return;
+    }
     const unsigned long long q = qmass(v);
     int b = 0;  // largest b with edges[b] <= k
 #pragma unroll
@@ -284,8 +295,8 @@ __global__ void __launch_bounds__(RO_NT) k_ro_hist(const T *psi, const double *E
     key_pair(E, i, k[0], k[1], raw[0], raw[1]);
     const bool two = i + st < N2;
     if (two) key_pair(E, i + st, k[2], k[3], raw[2], raw[3]);
-    const bool in0 = k[0] >= lo && k[0] < hi, in1 = k[1] >= lo && k[1] < hi;
-    const bool in2 = two && k[2] >= lo && k[2] < hi, in3 = two && k[3] >= lo && k[3] < hi;
+    const bool in0 = k[0] >= lo_read && k[0] < hi_read, in1 = k[1] >= lo_read && k[1] < hi_read;
+    const bool in2 = two && k[2] >= lo_read && k[2] < hi_read, in3 = two && k[3] >= lo_read && k[3] < hi_read;
     if (in0 || in1) {
       T v0, v1;
       amp_pair(psi, i, v0, v1);
@@ -301,6 +312,8 @@ __global__ void __launch_bounds__(RO_NT) k_ro_hist(const T *psi, const double *E
   }
   atomicMin(&smin, kmin);
   atomicMax(&smax, kmax);
+  if (qbelow) atomicAdd(&ext[0], qbelow);  // integer: order-independent
+  if (qabove) atomicAdd(&ext[3], qabove);
   __syncthreads();
   for (int i = threadIdx.x; i < RO_BINS; i += RO_NT)
     if (sm[i]) atomicAdd(&gmass[i], sm[i]);
@@ -310,20 +323,39 @@ __global__ void __launch_bounds__(RO_NT) k_ro_hist(const T *psi, const double *E
   }
 }
 
+// Energies at the shots, out[k] = E[shots[k]].
+__global__ void k_ro_gather(const double *E, const long long *shots, int nshots, double *out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nshots) out[k] = E[shots[k]];
+}
+
 // Tail sums for the CVaR: per CTA sum of p*E and p over E < tau, and of p over
 // E == tau (fixed per-thread order, fixed tree).
+// Compensated (Kahan) running sum in the amplitude precision: FP32 amplitudes
+// keep the tail sums off the (slow) FP64 pipe; FP64 amplitudes sum in FP64.
+template <typename T>
+struct KSum {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T x) {
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(RO_NT) k_ro_tail(const T *psi, const double *E, long long N,
                                                    unsigned long long ktau, double *part) {
   __shared__ double r[3][RO_NT];
-  double sb = 0.0, pb = 0.0, pa = 0.0;
+  KSum<T> ksb, kpb, kpa;
   auto add = [&](unsigned long long k, T v, unsigned long long bits) {
-    const double p = (double)v * (double)v;
+    const T p = v * v;
     if (k < ktau) {
-      sb += p * __longlong_as_double((long long)bits);
-      pb += p;
+      ksb.add(p * (T)__longlong_as_double((long long)bits));
+      kpb.add(p);
     } else {
-      pa += p;
+      kpa.add(p);
     }
   };
   const long long N2 = N >> 1, st = (long long)gridDim.x * RO_NT;
@@ -346,9 +378,9 @@ __global__ void __launch_bounds__(RO_NT) k_ro_tail(const T *psi, const double *E
     }
   }
   const int tid = threadIdx.x;
-  r[0][tid] = sb;
-  r[1][tid] = pb;
-  r[2][tid] = pa;
+  r[0][tid] = (double)ksb.s - (double)ksb.c;
+  r[1][tid] = (double)kpb.s - (double)kpb.c;
+  r[2][tid] = (double)kpa.s - (double)kpa.c;
   __syncthreads();
   for (int w = RO_NT / 2; w > 0; w >>= 1) {
     if (tid < w)
@@ -415,11 +447,17 @@ cudaError_t launch_ro_minmax(const double *E, int n, unsigned long long *ext, cu
 }
 
 cudaError_t launch_ro_hist(int prec, const void *psi, const double *E, int n, const unsigned long long *edges,
-                           unsigned long long *gmass, unsigned long long *ext, cudaStream_t s) {
+                           unsigned long long *gmass, unsigned long long *ext, int below, cudaStream_t s) {
   if (prec)
-    k_ro_hist<double><<<ro_grid(), RO_NT, 0, s>>>((const double *)psi, E, 1LL << n, edges, gmass, ext);
+    k_ro_hist<double><<<ro_grid(), RO_NT, 0, s>>>((const double *)psi, E, 1LL << n, edges, gmass, ext, below);
   else
-    k_ro_hist<float><<<ro_grid(), RO_NT, 0, s>>>((const float *)psi, E, 1LL << n, edges, gmass, ext);
+    k_ro_hist<float><<<ro_grid(), RO_NT, 0, s>>>((const float *)psi, E, 1LL << n, edges, gmass, ext, below);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ro_gather(const double *E, const long long *shots, int nshots, double *out, cudaStream_t s) {
+  if (nshots <= 0) return cudaSuccess;
+  k_ro_gather<<<(nshots + 255) / 256, 256, 0, s>>>(E, shots, nshots, out);
   return cudaGetLastError();
 }
 
