@@ -350,17 +350,45 @@ __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> 
 // e + 2 lane + 64 m + 1024 w: register bits 1..4 hold tile bits 6..9, the lane
 // tile bits 1..5, the warp tile bits 10...
 __device__ __forceinline__ int idx_L(int lane, int w, int m) { return (lane << 1) + (m << 6) + (w << 10); }
-template <typename T>
-__device__ __forceinline__ void sts_L(T *s, int lane, int w, const Reg32<T> &r) {
-  using T2 = typename V2<T>::type;
+
+// Per-thread parts of the swizzled round-L and round-H offsets.  The swizzle
+// XORs tile bits 2..4 (FP32; 1..3 for FP64) with tile bits 5..7, and in both
+// layouts the XORed bits come from the thread index alone while bits 5..7 come
+// from the thread index and at most two pair-index bits.  So pair m of round L
+// sits at L[m & 3] + 64 m and pair m of round H at H[m & 3] + idx_H_pair(m):
+// a few per-thread bases plus compile-time offsets.
+struct SBase {
+  int L[4];
+  int H[4];
+};
+template <int TB>
+__device__ __forceinline__ int idx_H_thread(int tid);
+template <int TB, typename T>
+__device__ __forceinline__ SBase sbase(int tid) {
+  constexpr int CH = 16 / (int)sizeof(T);
+  const int lane = tid & 31, w = tid >> 5;
+  SBase b;
 #pragma unroll
-  for (int m = 0; m < ROUND / 2; ++m) *reinterpret_cast<T2 *>(s + swz<T>(idx_L(lane, w, m))) = r.pair(m);
+  for (int j = 0; j < 4; ++j) b.L[j] = ((lane << 1) ^ ((((lane >> 4) & 1) | (j << 1)) * CH)) + (w << 10);
+  const int thr = idx_H_thread<TB>(tid);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int b7 = TB >= 11 ? ((tid >> 5) & 1) : ((j >> 1) & 1);  // tile bit 7: thread bit 5 or pair bit 1
+    b.H[j] = thr ^ (((j & 1) | (((tid >> 4) & 1) << 1) | (b7 << 2)) * CH);
+  }
+  return b;
 }
 template <typename T>
-__device__ __forceinline__ void lds_L(const T *s, int lane, int w, Reg32<T> &r) {
+__device__ __forceinline__ void sts_L(T *s, const SBase &sb, const Reg32<T> &r) {
   using T2 = typename V2<T>::type;
 #pragma unroll
-  for (int m = 0; m < ROUND / 2; ++m) r.set_pair(m, *reinterpret_cast<const T2 *>(s + swz<T>(idx_L(lane, w, m))));
+  for (int m = 0; m < ROUND / 2; ++m) *reinterpret_cast<T2 *>(s + sb.L[m & 3] + (m << 6)) = r.pair(m);
+}
+template <typename T>
+__device__ __forceinline__ void lds_L(const T *s, const SBase &sb, Reg32<T> &r) {
+  using T2 = typename V2<T>::type;
+#pragma unroll
+  for (int m = 0; m < ROUND / 2; ++m) r.set_pair(m, *reinterpret_cast<const T2 *>(s + sb.L[m & 3] + (m << 6)));
 }
 // Round M: group G's 32 consecutive amplitudes (register bits 0..4 = tile
 // bits 0..4) as 16-byte chunks in swizzled order.
@@ -410,18 +438,17 @@ __device__ __forceinline__ int idx_H_pair(int m) {
   return o;
 }
 template <int TB, typename T>
-__device__ __forceinline__ void lds_H(const T *s, int tid, Reg32<T> &r) {
+__device__ __forceinline__ void lds_H(const T *s, const SBase &sb, Reg32<T> &r) {
   using T2 = typename V2<T>::type;
-  const int b = idx_H_thread<TB>(tid);
 #pragma unroll
-  for (int m = 0; m < ROUND / 2; ++m) r.set_pair(m, *reinterpret_cast<const T2 *>(s + swz<T>(b | idx_H_pair<TB>(m))));
+  for (int m = 0; m < ROUND / 2; ++m)
+    r.set_pair(m, *reinterpret_cast<const T2 *>(s + sb.H[m & 3] + idx_H_pair<TB>(m)));
 }
 template <int TB, typename T>
-__device__ __forceinline__ void sts_H(T *s, int tid, const Reg32<T> &r) {
+__device__ __forceinline__ void sts_H(T *s, const SBase &sb, const Reg32<T> &r) {
   using T2 = typename V2<T>::type;
-  const int b = idx_H_thread<TB>(tid);
 #pragma unroll
-  for (int m = 0; m < ROUND / 2; ++m) *reinterpret_cast<T2 *>(s + swz<T>(b | idx_H_pair<TB>(m))) = r.pair(m);
+  for (int m = 0; m < ROUND / 2; ++m) *reinterpret_cast<T2 *>(s + sb.H[m & 3] + idx_H_pair<TB>(m)) = r.pair(m);
 }
 
 // Gray-code order of the 16 element pairs: consecutive pairs differ in one
@@ -546,6 +573,7 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   __shared__ L0Tables<T, T2, TB> tab;
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const SBase sb = sbase<TB, T>(tid);
   const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
   const uint32_t tbase = tile_base(t, A.c, A.a, TB);
   const uint32_t nmask = (A.n >= 32) ? 0xffffffffu : ((1u << A.n) - 1);
@@ -586,7 +614,7 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
     r.set_pair(m, v);
   });
   round_gates<4, WHT, false, 1>(r, gt, gm, 6, false);
-  sts_L(s, lane, w, r);
+  sts_L(s, sb, r);
   // round M: tile bits 0..4.  Layouts L and M of warp w both cover tile
   // amplitudes [1024 w, 1024 w + 1024), so the warp only syncs with itself.
   if (gm & 0x1Fu) {
@@ -597,7 +625,7 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   }
   __syncthreads();
   // round H: tile bits 5 and 10..TB-1, then the store and the energy epilogue
-  lds_H<TB>(s, tid, r);
+  lds_H<TB>(s, sb, r);
   round_gates<1, WHT, false, 1>(r, gt, gm, 5, false);
   round_gates<H, WHT, false, 2>(r, gt, gm, 10, false);
   const T *table = reinterpret_cast<const T *>(A.table);
@@ -676,6 +704,7 @@ k_bwd(const PassArgs A) {
   const int job = blockIdx.y;
   if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.layer < A.minlayer[A.job0 + job]) return;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const SBase sb = sbase<TB, T>(tid);
   const uint32_t tiles = (uint32_t)A.tiles;
   const bool pair = (A.flags & F_PAIR_ORDER) != 0;
   const uint32_t nmask = (1u << A.n) - 1;
@@ -730,8 +759,8 @@ k_bwd(const PassArgs A) {
 
     Reg32<T> psi, lam;
     // round L (from shared)
-    lds_L(sp, lane, w, psi);
-    lds_L(sl, lane, w, lam);
+    lds_L(sp, sb, psi);
+    lds_L(sl, sb, lam);
     if (init) {
       T eacc = T(0);
 #pragma unroll
@@ -741,7 +770,7 @@ k_bwd(const PassArgs A) {
         lam.set(k, l);
         eacc += p * l;
       }
-      sts_L(sl, lane, w, lam);
+      sts_L(sl, sb, lam);
       eacc = warp_sum(eacc);
       if (lane == 0) ered[par][w] = (double)eacc;
     }
@@ -755,8 +784,8 @@ k_bwd(const PassArgs A) {
     }
     // round H: gradients, then RY(-theta) on lambda.  Its layout crosses warps.
     __syncthreads();
-    lds_H<TB>(sp, tid, psi);
-    lds_H<TB>(sl, tid, lam);
+    lds_H<TB>(sp, sb, psi);
+    lds_H<TB>(sl, sb, lam);
     round_grads<H, 2, true>(psi, lam, gm, 10, gred[par][w], lane);
     round_gates<H, false, true, 2>(lam, gt, gm, 10, true);
     round_gates<1, false, true, 1>(lam, gt, gm, 5, true);
@@ -765,7 +794,7 @@ k_bwd(const PassArgs A) {
       issue(lsrc, nbx, sp);  // next lambda into the psi buffer
     else
       cp_async_commit();
-    sts_H<TB>(sl, tid, lam);
+    sts_H<TB>(sl, sb, lam);
     __syncthreads();
     if (gm & 0x1Fu) {
       lds_M(sl, tid, lam);
@@ -773,7 +802,7 @@ k_bwd(const PassArgs A) {
       sts_M(sl, tid, lam);
       __syncwarp();  // M -> L stays inside the warp's 1024 amplitudes
     }
-    lds_L(sl, lane, w, lam);
+    lds_L(sl, sb, lam);
     round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
     for_L(gi, [&](int m, uint32_t y) {
       const T2 v = lam.pair(m);
@@ -829,6 +858,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
 
   if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.layer < A.minlayer[A.job0 + job]) return;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const SBase sb = sbase<TB, T>(tid);
   const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
   const uint32_t tbase = tile_base(t, A.c, A.a, TB);
   const uint32_t nmask = (1u << A.n) - 1;
@@ -861,8 +891,8 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
     eacc += p.x * l.x + p.y * l.y;
   });
   round_grads<4, 1>(psi, lam, gm, 6, gred[w], lane);
-  sts_L(sp, lane, w, psi);
-  sts_L(sl, lane, w, lam);
+  sts_L(sp, sb, psi);
+  sts_L(sl, sb, lam);
   if (A.flags & F_ENERGY) {
     eacc = warp_sum(eacc);
     if (lane == 0) ered[w] = (double)eacc;
@@ -873,13 +903,13 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
     lds_M(sl, tid, lam);
     round_grads<5>(psi, lam, gm, 0, gred[w], lane);
   }
-  lds_H<TB>(sp, tid, psi);
-  lds_H<TB>(sl, tid, lam);
+  lds_H<TB>(sp, sb, psi);
+  lds_H<TB>(sl, sb, lam);
   round_grads<H, 2, true>(psi, lam, gm, 10, gred[w], lane);
   round_gates<H, false, true, 2>(lam, gt, gm, 10, true);
   round_gates<1, false, true, 1>(lam, gt, gm, 5, true);
   __syncthreads();
-  sts_H<TB>(sl, tid, lam);
+  sts_H<TB>(sl, sb, lam);
   __syncthreads();
   if (gm & 0x1Fu) {
     lds_M(sl, tid, lam);
@@ -887,7 +917,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
     sts_M(sl, tid, lam);
     __syncthreads();
   }
-  lds_L(sl, lane, w, lam);
+  lds_L(sl, sb, lam);
   round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
   for_L(gi, [&](int m, uint32_t y) {
     const T2 v = lam.pair(m);
