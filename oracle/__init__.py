@@ -55,6 +55,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         lib.oracle_sweep_times.argtypes = [i, i, i, p, p, p, p]
         lib.oracle_max_threads.restype = i
         lib.oracle_set_threads.argtypes = [i]
+        lib.oracle_set_entangler.argtypes = [i]
+        lib.oracle_set_entangler.restype = i
         for f in ("oracle_state", "oracle_apply_hamiltonian", "oracle_energy",
                   "oracle_energy_grad", "oracle_param_shift_grad", "oracle_partial_work",
                   "oracle_sweep_times"):
@@ -97,6 +99,27 @@ def _ham(ham_or_strings, coeffs=None):
 
 def set_threads(n: int) -> None:
     load().oracle_set_threads(int(n))
+
+
+ENT_LINEAR, ENT_CIRCULAR, ENT_FULL = 0, 1, 2
+
+
+class entangler:
+    """Context manager selecting the oracle's entangler (Section IV-B):
+    ENT_LINEAR (default), ENT_CIRCULAR (CX(n-1,0) first, then the linear chain)
+    or ENT_FULL (CX(i,j) for all i < j in lexicographic order)."""
+
+    def __init__(self, ent: int, lib: Optional[ctypes.CDLL] = None):
+        self.ent = int(ent)
+        self.lib = lib
+
+    def __enter__(self):
+        _check((self.lib or load()).oracle_set_entangler(self.ent), "set_entangler")
+        return self
+
+    def __exit__(self, *exc):
+        (self.lib or load()).oracle_set_entangler(ENT_LINEAR)
+        return False
 
 
 def max_threads() -> int:

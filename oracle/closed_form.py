@@ -149,6 +149,37 @@ def basis_state_energy(n: int, reps: int, flips, strings, coeffs) -> float:
     return tot
 
 
+def entangler_map(x: int, n: int, ent: int = 0) -> int:
+    """Basis index after one entangler layer as a closed-form GF(2) map (no gate list):
+    linear: y_j = x_0 ^ ... ^ x_j (each CX(q, q+1) adds the updated bit q to bit q+1);
+    circular: the same after x_0 ^= x_{n-1} (the wrap-around CX(n-1, 0) acts first);
+    full: y_j = x_j ^ x_{j-1}, since bit j collects x_i and, through CX(i, j) after
+    bit i was updated, the running sums of the lower bits, which cancel pairwise."""
+    if ent == 2:
+        return (x ^ (x << 1)) & ((1 << n) - 1)
+    if ent == 1 and n > 1:
+        x ^= (x >> (n - 1)) & 1
+    y = 0
+    acc = 0
+    for q in range(n):
+        acc ^= (x >> q) & 1
+        y |= acc << q
+    return y
+
+
+def basis_state_index(n: int, reps: int, flips, ent: int = 0) -> int:
+    """Every angle in {0, pi}: the index y of the final signed basis state |y>."""
+    f = np.asarray(flips, dtype=np.int64).reshape(-1)
+    x = 0
+    for r in range(reps + 1):
+        if r > 0:
+            x = entangler_map(x, n, ent)
+        for q in range(n):
+            if f[r * n + q]:
+                x ^= 1 << q
+    return x
+
+
 def zero_angle_energy(strings, coeffs) -> float:
     """theta = 0: sum of coefficients of strings with only I/Z letters."""
     return float(sum(float(c) for s, c in zip(strings, coeffs) if all(ch in "IZ" for ch in s)))

@@ -61,30 +61,41 @@ def hamiltonian(strings: Sequence[str], coeffs) -> np.ndarray:
     return h
 
 
-def circuit(n: int, reps: int, theta) -> np.ndarray:
-    """U(theta): RY layer, then reps x [CX(0,1), ..., CX(n-2,n-1); RY layer]."""
+def entangler_pairs(n: int, ent: int = 0):
+    """(control, target) list of an entangler: 0 linear CX(0,1)..CX(n-2,n-1);
+    1 circular: CX(n-1,0) first, then linear; 2 full: CX(i,j), i < j, lexicographic."""
+    if ent == 2:
+        return [(i, j) for i in range(n) for j in range(i + 1, n)]
+    pairs = [(q, q + 1) for q in range(n - 1)]
+    if ent == 1 and n > 1:
+        pairs = [(n - 1, 0)] + pairs
+    return pairs
+
+
+def circuit(n: int, reps: int, theta, ent: int = 0) -> np.ndarray:
+    """U(theta): RY layer, then reps x [entangler; RY layer] as explicit matrices."""
     assert n <= MAX_QUBITS
     th = np.asarray(theta, dtype=np.float64).reshape(-1)
     u = np.eye(1 << n, dtype=np.complex128)
     for r in range(reps + 1):
         if r > 0:
-            for q in range(n - 1):
-                u = cnot(q, q + 1, n) @ u
+            for c, t in entangler_pairs(n, ent):
+                u = cnot(c, t, n) @ u
         for q in range(n):
             u = embed({q: ry(th[r * n + q])}, n) @ u
     return u
 
 
-def state(n: int, reps: int, theta) -> np.ndarray:
-    return circuit(n, reps, theta)[:, 0]
+def state(n: int, reps: int, theta, ent: int = 0) -> np.ndarray:
+    return circuit(n, reps, theta, ent)[:, 0]
 
 
-def energy(n: int, reps: int, theta, strings, coeffs) -> float:
-    psi = state(n, reps, theta)
+def energy(n: int, reps: int, theta, strings, coeffs, ent: int = 0) -> float:
+    psi = state(n, reps, theta, ent)
     return float(np.real(np.vdot(psi, hamiltonian(strings, coeffs) @ psi)))
 
 
-def param_shift_grad(n: int, reps: int, theta, strings, coeffs) -> np.ndarray:
+def param_shift_grad(n: int, reps: int, theta, strings, coeffs, ent: int = 0) -> np.ndarray:
     th = np.asarray(theta, dtype=np.float64).reshape(-1)
     h = hamiltonian(strings, coeffs)
     g = np.zeros_like(th)
@@ -93,7 +104,7 @@ def param_shift_grad(n: int, reps: int, theta, strings, coeffs) -> np.ndarray:
         for sh in (+math.pi / 2, -math.pi / 2):
             t = th.copy()
             t[p] += sh
-            psi = circuit(n, reps, t)[:, 0]
+            psi = circuit(n, reps, t, ent)[:, 0]
             vals.append(float(np.real(np.vdot(psi, h @ psi))))
         g[p] = 0.5 * (vals[0] - vals[1])
     return g

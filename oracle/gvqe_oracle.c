@@ -19,7 +19,8 @@
  *
  * Conventions (readings where the paper is silent): qubit q is bit q of the
  * basis index x; character i of a Pauli string acts on qubit i; the linear
- * entangler is CX(0,1), CX(1,2), ..., CX(n-2,n-1) applied in that order.
+ * entangler is CX(0,1), CX(1,2), ..., CX(n-2,n-1) applied in that order (the
+ * circular and full entanglers are listed at entangler_gates below).
  *
  * Every gate is applied one at a time in circuit order; there is no fusion,
  * no table, no Walsh-Hadamard transform and no grouping of terms.
@@ -90,14 +91,54 @@ static void apply_cx(cplx *psi, int n, int ctl, int tgt) {
     }
 }
 
-/* Linear (nearest-neighbour) entangler of Section IV-B, gates in ascending order. */
-static void apply_linear_entangler(cplx *psi, int n) {
-    for (int q = 0; q + 1 < n; ++q) apply_cx(psi, n, q, q + 1);
+/*
+ * Entanglers of Section IV-B as ordered CNOT lists (control, target):
+ *   0 linear:   CX(0,1), CX(1,2), ..., CX(n-2,n-1)
+ *   1 circular: CX(n-1,0) (the wrap-around), then the linear list
+ *   2 full:     CX(i,j) for every i < j, i ascending, j ascending within i
+ * The entangler in use is a process-wide setting of this test oracle.
+ */
+static int g_entangler = 0;
+
+int oracle_set_entangler(int ent) {
+    if (ent < 0 || ent > 2) return ORACLE_EINVAL;
+    g_entangler = ent;
+    return ORACLE_OK;
 }
 
-/* Inverse of the linear entangler: the same CNOTs in descending order. */
-static void apply_linear_entangler_inverse(cplx *psi, int n) {
-    for (int q = n - 2; q >= 0; --q) apply_cx(psi, n, q, q + 1);
+static int entangler_gates(int n, int *ctl, int *tgt) {
+    int k = 0;
+    if (g_entangler == 2) {
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                ctl[k] = i;
+                tgt[k++] = j;
+            }
+        return k;
+    }
+    if (g_entangler == 1 && n > 1) {
+        ctl[k] = n - 1;
+        tgt[k++] = 0;
+    }
+    for (int q = 0; q + 1 < n; ++q) {
+        ctl[k] = q;
+        tgt[k++] = q + 1;
+    }
+    return k;
+}
+
+/* The entangler, one gate at a time in its order. */
+static void apply_entangler(cplx *psi, int n) {
+    int ctl[ORACLE_MAX_QUBITS * ORACLE_MAX_QUBITS], tgt[ORACLE_MAX_QUBITS * ORACLE_MAX_QUBITS];
+    const int k = entangler_gates(n, ctl, tgt);
+    for (int g = 0; g < k; ++g) apply_cx(psi, n, ctl[g], tgt[g]);
+}
+
+/* Its inverse: the same CNOTs in reverse order (each is its own inverse). */
+static void apply_entangler_inverse(cplx *psi, int n) {
+    int ctl[ORACLE_MAX_QUBITS * ORACLE_MAX_QUBITS], tgt[ORACLE_MAX_QUBITS * ORACLE_MAX_QUBITS];
+    const int k = entangler_gates(n, ctl, tgt);
+    for (int g = k - 1; g >= 0; --g) apply_cx(psi, n, ctl[g], tgt[g]);
 }
 
 /* U(theta)|0> for the RY+CX ansatz (Section IV-B, Eq. 7-8). */
@@ -107,7 +148,7 @@ static void prepare_state(cplx *psi, int n, int reps, const double *theta) {
     psi[0] = 1.0;
     for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[q]);
     for (int r = 1; r <= reps; ++r) {
-        apply_linear_entangler(psi, n);
+        apply_entangler(psi, n);
         for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[r * n + q]);
     }
 }
@@ -261,8 +302,8 @@ int oracle_energy_grad(int n, int reps, const double *theta, int n_terms, const 
             apply_ry(lam, n, q, -theta[p]);
         }
         if (r > 0) {
-            apply_linear_entangler_inverse(psi, n);
-            apply_linear_entangler_inverse(lam, n);
+            apply_entangler_inverse(psi, n);
+            apply_entangler_inverse(lam, n);
         }
     }
     free(psi);

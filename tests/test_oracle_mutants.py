@@ -22,9 +22,17 @@ MUTANTS = {
     "ry_sign": ("psi[x] = c * a - s * b;", "psi[x] = c * a + s * b;"),
     "ry_half_angle": ("const double c = cos(0.5 * theta), s = sin(0.5 * theta);",
                       "const double c = cos(theta), s = sin(theta);"),
-    "cx_direction": ("apply_cx(psi, n, q, q + 1);\n}", "apply_cx(psi, n, q + 1, q);\n}"),
-    "cx_order": ("for (int q = 0; q + 1 < n; ++q) apply_cx(psi, n, q, q + 1);",
-                 "for (int q = n - 2; q >= 0; --q) apply_cx(psi, n, q, q + 1);"),
+    "cx_direction": ("ctl[k] = q;\n        tgt[k++] = q + 1;", "ctl[k] = q + 1;\n        tgt[k++] = q;"),
+    "cx_order": ("for (int g = 0; g < k; ++g) apply_cx(psi, n, ctl[g], tgt[g]);",
+                 "for (int g = k - 1; g >= 0; --g) apply_cx(psi, n, ctl[g], tgt[g]);"),
+    "circular_wrap_after_chain": (
+        "    if (g_entangler == 1 && n > 1) {\n        ctl[k] = n - 1;\n        tgt[k++] = 0;\n    }\n"
+        "    for (int q = 0; q + 1 < n; ++q) {\n        ctl[k] = q;\n        tgt[k++] = q + 1;\n    }\n",
+        "    for (int q = 0; q + 1 < n; ++q) {\n        ctl[k] = q;\n        tgt[k++] = q + 1;\n    }\n"
+        "    if (g_entangler == 1 && n > 1) {\n        ctl[k] = n - 1;\n        tgt[k++] = 0;\n    }\n"),
+    "circular_wrap_direction": ("        ctl[k] = n - 1;\n        tgt[k++] = 0;", "        ctl[k] = 0;\n        tgt[k++] = n - 1;"),
+    "full_controls_descending": ("for (int i = 0; i < n; ++i)\n            for (int j = i + 1; j < n; ++j)",
+                                 "for (int i = n - 1; i >= 0; --i)\n            for (int j = i + 1; j < n; ++j)"),
     "y_phase": ("phase *= b ? -I : I;", "phase *= b ? I : -I;"),
     "z_sign_dropped": ("if (b) phase = -phase;", "(void)b;"),
     "last_term_dropped": ("for (int k = 0; k < n_terms; ++k) {", "for (int k = 0; k + 1 < n_terms; ++k) {"),
@@ -69,6 +77,18 @@ def _pins_pass(lib) -> bool:
         e1 = oracle.energy(n, 1, t1, ham.strings, ham.coeffs, lib=lib)
         if abs(e1 - closed_form.heisenberg_reps1_energy(n, t1, ham.strings, ham.coeffs)) > 1e-12 * ham.abs_sum():
             return False
+        # circular and full: the dense model, and the basis-index maps of closed_form
+        for ent in (oracle.ENT_CIRCULAR, oracle.ENT_FULL):
+            with oracle.entangler(ent, lib=lib):
+                if np.max(np.abs(oracle.state(n, reps, th, lib=lib) - dense.state(n, reps, th, ent))) > 1e-12:
+                    return False
+                flips = np.random.default_rng(ent).integers(0, 2, size=n * (reps + 1))
+                psi = oracle.state(n, reps, np.where(flips == 1, math.pi, 0.0), lib=lib)
+                if int(np.argmax(np.abs(psi))) != closed_form.basis_state_index(n, reps, flips, ent):
+                    return False
+                e, g = oracle.energy_grad(n, reps, th, strings, coeffs, lib=lib)
+                if np.max(np.abs(g - dense.param_shift_grad(n, reps, th, strings, coeffs, ent))) > 1e-11 * scale:
+                    return False
         return True
     except RuntimeError:
         return False

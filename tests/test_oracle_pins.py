@@ -191,3 +191,36 @@ def test_masked_param_shift_zeroes_inactive_entries():
     _, full = oracle.energy_grad(n, reps, th, ham.strings, ham.coeffs)
     assert np.all(g[mask == 0] == 0.0)
     assert np.max(np.abs(g[mask == 1] - full[mask == 1])) < 1e-12 * ham.abs_sum()
+
+
+@pytest.mark.parametrize("ent", [oracle.ENT_LINEAR, oracle.ENT_CIRCULAR, oracle.ENT_FULL])
+def test_entangler_pins(ent):
+    """Circular and full entanglers (Section IV-B): the C oracle equals the dense
+    matrix model, signed basis states follow the closed-form GF(2) index maps,
+    and the adjoint gradient equals the dense parameter-shift gradient."""
+    rng = np.random.default_rng(11 + ent)
+    for n, reps in ((1, 2), (2, 2), (3, 1), (5, 2), (7, 1)):
+        th = wl.thetas(n, reps, 1, seed=n + ent)[0]
+        ham = wl.pauli_hamiltonian(n, 10, seed=n)
+        with oracle.entangler(ent):
+            psi = oracle.state(n, reps, th)
+            assert np.max(np.abs(psi - dense.state(n, reps, th, ent))) < 1e-12
+            flips = rng.integers(0, 2, size=n * (reps + 1))
+            b = oracle.state(n, reps, np.where(flips == 1, math.pi, 0.0))
+            assert int(np.argmax(np.abs(b))) == closed_form.basis_state_index(n, reps, flips, ent)
+            e, g = oracle.energy_grad(n, reps, th, ham.strings, ham.coeffs)
+        scale = ham.abs_sum()
+        assert abs(e - dense.energy(n, reps, th, ham.strings, ham.coeffs, ent)) < 1e-12 * scale
+        assert np.max(np.abs(g - dense.param_shift_grad(n, reps, th, ham.strings, ham.coeffs, ent))) < 1e-11 * scale
+
+
+def test_entangler_maps_are_the_cnot_products():
+    """The closed-form maps agree with the CNOT lists applied to bit vectors."""
+    for n in range(1, 9):
+        for ent in (0, 1, 2):
+            for x in range(1 << n):
+                y = x
+                for c, t in dense.entangler_pairs(n, ent):
+                    if (y >> c) & 1:
+                        y ^= 1 << t
+                assert y == closed_form.entangler_map(x, n, ent)
