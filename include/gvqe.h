@@ -9,7 +9,7 @@
  *     character i acts on qubit i.
  *   - The ansatz (Section IV-B, Eq. 7): an initial RY layer on every qubit,
  *     then `reps` repetitions of [entangler, RY layer].  The linear entangler
- *     is CX(0,1), CX(1,2), ..., CX(n-2,n-1) in that order.
+ *     is CX(0,1), CX(1,2), ..., CX(n-2,n-1) in that order (others below).
  *   - Parameters are flattened layer-major: theta[p] with p = r*n + q is the
  *     RY angle of layer r (0..reps) on qubit q; P = n*(reps+1) (Eq. 8 for the
  *     RY-only gate set).
@@ -47,8 +47,13 @@ extern "C" {
 #define GVQE_GRAD_ADJOINT 0x0     /* reverse-mode (adjoint) gradient (default) */
 #define GVQE_GRAD_PARAM_SHIFT 0x2 /* parameter-shift gradient, Eq. 13 (2 P_active + 1 energies) */
 
-/* entanglers for gvqe_ansatz_create (Section IV-B) */
+/* entanglers for gvqe_ansatz_create (Section IV-B), each an ordered CNOT list:
+ * LINEAR   CX(0,1), CX(1,2), ..., CX(n-2,n-1)
+ * CIRCULAR CX(n-1,0) (the wrap-around) first, then the LINEAR list
+ * FULL     CX(i,j) for every i < j, i ascending, j ascending within i */
 #define GVQE_ENT_LINEAR 0
+#define GVQE_ENT_CIRCULAR 1
+#define GVQE_ENT_FULL 2
 
 /* options for gvqe_ansatz_set_option */
 #define GVQE_OPT_TILE_BITS 1 /* log2 amplitudes per on-chip tile, 10..13 (FP64: 10..12); 0 = auto (13 FP32, 12 FP64) */
@@ -82,8 +87,8 @@ int gvqe_hamiltonian_create(int n_qubits, int n_terms, const char *pauli, const 
  * gvqe_ansatz_create -- the parameterised circuit U(theta) of Section IV-B
  * (RY layers with an entangler between them; Eq. 7, Eq. 8 with RY only).
  *   n_qubits: 1..30.  reps: 0..64 (the number D of [entangler, RY] repetitions).
- *   entangler: GVQE_ENT_LINEAR (others return GVQE_EUNSUPPORTED).
- * Errors: GVQE_EINVAL, GVQE_EUNSUPPORTED.
+ *   entangler: GVQE_ENT_LINEAR, GVQE_ENT_CIRCULAR or GVQE_ENT_FULL.
+ * Errors: GVQE_EINVAL.
  */
 int gvqe_ansatz_create(int n_qubits, int reps, int entangler, gvqe_ansatz *out);
 

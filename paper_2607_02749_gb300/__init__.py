@@ -11,7 +11,7 @@ from __future__ import annotations
 from typing import Optional, Sequence
 
 from . import _lib
-from ._lib import (GVQE_ENT_LINEAR, GVQE_FP32, GVQE_FP64, GVQE_GRAD_ADJOINT, GVQE_GRAD_PARAM_SHIFT,
+from ._lib import (GVQE_ENT_CIRCULAR, GVQE_ENT_FULL, GVQE_ENT_LINEAR, GVQE_FP32, GVQE_FP64, GVQE_GRAD_ADJOINT, GVQE_GRAD_PARAM_SHIFT,
                    GVQE_OPT_TILE_BITS, GvqeError, gvqe_ansatz_create, gvqe_ansatz_set_option, gvqe_batch_create,
                    gvqe_batch_run, gvqe_destroy, gvqe_energy, gvqe_energy_grad, gvqe_hamiltonian_create,
                    gvqe_hamiltonian_stats, gvqe_last_error, gvqe_plan_describe, gvqe_readout, gvqe_version)
@@ -19,6 +19,7 @@ from ._lib import (GVQE_ENT_LINEAR, GVQE_FP32, GVQE_FP64, GVQE_GRAD_ADJOINT, GVQ
 __all__ = [
     "Hamiltonian", "Ansatz", "Batch", "GvqeEnergy", "energy", "energy_grad", "readout", "Readout", "GvqeError",
     "GVQE_FP32", "GVQE_FP64", "GVQE_GRAD_ADJOINT", "GVQE_GRAD_PARAM_SHIFT", "GVQE_ENT_LINEAR",
+    "GVQE_ENT_CIRCULAR", "GVQE_ENT_FULL",
     "gvqe_hamiltonian_create", "gvqe_ansatz_create", "gvqe_ansatz_set_option", "gvqe_energy",
     "gvqe_energy_grad", "gvqe_batch_create", "gvqe_batch_run", "gvqe_destroy", "gvqe_last_error",
     "gvqe_plan_describe", "gvqe_hamiltonian_stats", "gvqe_readout", "gvqe_version",
@@ -56,11 +57,13 @@ class Hamiltonian(_Handle):
 
 
 class Ansatz(_Handle):
-    """RY layer + reps x [linear CX chain, RY layer] (Section IV-B); P = n (reps + 1)."""
+    """RY layer + reps x [entangler, RY layer] (Section IV-B); P = n (reps + 1).
+    entangler: GVQE_ENT_LINEAR (default), GVQE_ENT_CIRCULAR or GVQE_ENT_FULL."""
 
     def __init__(self, n_qubits: int, reps: int, entangler: int = GVQE_ENT_LINEAR, tile_bits: int = 0):
         self.n_qubits = n_qubits
         self.reps = reps
+        self.entangler = entangler
         self.n_params = n_qubits * (reps + 1)
         self.handle = gvqe_ansatz_create(n_qubits, reps, entangler)
         if tile_bits:

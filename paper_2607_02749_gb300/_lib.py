@@ -26,6 +26,8 @@ GVQE_FP64 = 0x1
 GVQE_GRAD_ADJOINT = 0x0
 GVQE_GRAD_PARAM_SHIFT = 0x2
 GVQE_ENT_LINEAR = 0
+GVQE_ENT_CIRCULAR = 1
+GVQE_ENT_FULL = 2
 GVQE_OPT_TILE_BITS = 1
 GVQE_MAX_QUBITS = 30
 GVQE_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024

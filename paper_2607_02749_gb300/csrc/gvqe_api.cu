@@ -199,7 +199,7 @@ static long long tiles_of(int n, int tb) { return 1LL << (n - tb); }
 
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0,
-                bool state_only) {
+                bool state_only, int ent) {
   Plan pl;
   pl.n = n;
   pl.reps = reps;
@@ -217,6 +217,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
     A.kind = kind;
     A.n = n;
     A.P = pl.P;
+    A.ent = ent;
     return A;
   };
   auto set_layout = [&](PassArgs &A, const LayerPass &lp) {
@@ -290,7 +291,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
       st.A.layer = r;
       if (j == 0) {
         st.A.load_mode = (r == 1) ? LD_L0_GATHER : LD_GATHER;
-        st.A.flags |= F_PAIR_ORDER;
+        if (ent != ENT_FULL) st.A.flags |= F_PAIR_ORDER;
       } else {
         st.A.load_mode = LD_PLAIN;
       }
@@ -366,7 +367,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
         st.out = out;
         if (j == 0) {
           st.A.store_mode = ST_SCATTER;
-          st.A.flags |= F_PAIR_ORDER;
+          if (ent != ENT_FULL) st.A.flags |= F_PAIR_ORDER;
         } else {
           st.A.store_mode = ST_PLAIN;
         }
@@ -593,7 +594,7 @@ static Plan *get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, boo
   const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0) | (state_only ? 8 : 0);
   auto it = a->plans.find(key);
   if (it != a->plans.end() && it->second.tile_bits == a->tile_bits) return &it->second;
-  Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, want_grad, diag, false, state_only);
+  Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, want_grad, diag, false, state_only, a->ent);
   pl.tile_bits = a->tile_bits;
   a->plans[key] = std::move(pl);
   return &a->plans[key];
@@ -848,7 +849,8 @@ int gvqe_ansatz_create(int n_qubits, int reps, int entangler, gvqe_ansatz *out) 
   if (n_qubits < 1 || n_qubits > GVQE_MAX_QUBITS)
     return fail(GVQE_EINVAL, "n_qubits=%d outside [1, %d]", n_qubits, GVQE_MAX_QUBITS);
   if (reps < 0 || reps > 64) return fail(GVQE_EINVAL, "reps=%d outside [0, 64]", reps);
-  if (entangler != GVQE_ENT_LINEAR) return fail(GVQE_EUNSUPPORTED, "entangler %d is not implemented", entangler);
+  if (entangler != GVQE_ENT_LINEAR && entangler != GVQE_ENT_CIRCULAR && entangler != GVQE_ENT_FULL)
+    return fail(GVQE_EINVAL, "entangler %d is not one of GVQE_ENT_LINEAR, _CIRCULAR, _FULL", entangler);
   gvqe_ansatz_s *a = new gvqe_ansatz_s();
   a->magic = MAGIC_ANSATZ;
   a->n = n_qubits;

@@ -33,6 +33,27 @@ enum LoadMode : int {
   LD_L0 = 3,         // v = psi_0(y)
 };
 
+// Entanglers (Section IV-B).  As a map of basis indices each is GF(2)-linear,
+// y = A x; passes need x = A^-1 y (gather for psi, scatter for lambda):
+//   ENT_LINEAR   CX(0,1)..CX(n-2,n-1): y = prefix XOR of x,  x = y ^ (y << 1)
+//   ENT_CIRCULAR CX(n-1,0), then linear: x = C(y ^ (y << 1)), C: bit 0 ^= bit n-1
+//   ENT_FULL     CX(i,j) for all i < j, lexicographic: y = x ^ (x << 1), x = prefix XOR of y
+enum Entangler : int { ENT_LINEAR = 0, ENT_CIRCULAR = 1, ENT_FULL = 2 };
+
+__host__ __device__ inline uint32_t ent_inv(uint32_t y, uint32_t nmask, int ent, int n) {
+  if (ent == ENT_FULL) {
+    uint32_t x = y;
+    x ^= x << 1;
+    x ^= x << 2;
+    x ^= x << 4;
+    x ^= x << 8;
+    x ^= x << 16;
+    return x & nmask;
+  }
+  const uint32_t z = (y ^ (y << 1)) & nmask;
+  return ent == ENT_CIRCULAR ? z ^ ((z >> (n - 1)) & 1u) : z;
+}
+
 enum StoreMode : int {
   ST_PLAIN = 0,    // out[y] = v
   ST_SCATTER = 1,  // out[A^-1 y] = v: the inverse CX chain (adjoint of LD_GATHER)
@@ -42,7 +63,7 @@ enum StoreMode : int {
 enum PassFlags : int {
   F_ENERGY = 1,        // accumulate an energy partial per tile
   F_LAMBDA_INIT = 2,   // lambda = table * psi (diagonal H) instead of reading lambda
-  F_PAIR_ORDER = 4,    // launch tiles H and ~H next to each other (gather/scatter passes)
+  F_PAIR_ORDER = 4,    // launch tiles H and ~H next to each other (linear/circular gather and scatter passes)
   F_WRITE_LAMBDA = 8,  // K_LAMBDA_XY: write lambda
   F_ACCUM = 16,        // K_LAMBDA_XY: add onto lambda already written (group chunks)
 };
@@ -63,6 +84,7 @@ struct PassArgs {
   const void *table;        // diagonal table E(x) in amplitude precision
   const void *cs;           // (cos(theta/2), sin(theta/2)) per job and parameter
   int job0;                 // global index of job 0 of this launch (cs, minlayer)
+  int ent;                  // entangler (LD_GATHER, LD_L0_GATHER, ST_SCATTER)
   double *part;             // partial sums [row][tile] for this pass, per-job stride part_stride
   long long part_stride;
   double *epart;            // energy partials [tile], per-job stride part_stride

@@ -66,7 +66,7 @@ void count_launches(int k);
 // instead of per warp of the standalone layer-0 gradient pass.
 // state_only: the forward passes alone, the final state kept (Plan::final_buf).
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false,
-                bool state_only = false);
+                bool state_only = false, int ent = ENT_LINEAR);
 std::string describe_plan(const Plan &pl);
 
 }  // namespace gvqe

@@ -23,8 +23,6 @@ struct V2<double> {
   using type = double2;
 };
 
-// x = A^-1 y for the linear CX chain (y = prefix XOR of x).
-__device__ __forceinline__ long long cx_inv(long long y, long long nmask) { return (y ^ (y << 1)) & nmask; }
 
 template <typename T, typename T2>
 __device__ __forceinline__ T product_state(long long x, const T2 *l0, int n) {
@@ -35,12 +33,12 @@ __device__ __forceinline__ T product_state(long long x, const T2 *l0, int n) {
 
 template <typename T, typename T2>
 __device__ __forceinline__ T load_val(int mode, const T *__restrict__ in, long long y, long long nmask,
-                                      const T2 *l0, int n) {
+                                      const T2 *l0, int n, int ent) {
   switch (mode) {
     case LD_GATHER:
-      return in[cx_inv(y, nmask)];
+      return in[ent_inv((uint32_t)y, (uint32_t)nmask, ent, n)];
     case LD_L0_GATHER:
-      return product_state<T>(cx_inv(y, nmask), l0, n);
+      return product_state<T>(ent_inv((uint32_t)y, (uint32_t)nmask, ent, n), l0, n);
     case LD_L0:
       return product_state<T>(y, l0, n);
     default:
@@ -49,11 +47,12 @@ __device__ __forceinline__ T load_val(int mode, const T *__restrict__ in, long l
 }
 
 template <typename T>
-__device__ __forceinline__ void store_val(int mode, T *__restrict__ out, long long y, long long nmask, T v) {
+__device__ __forceinline__ void store_val(int mode, T *__restrict__ out, long long y, long long nmask, T v, int n,
+                                          int ent) {
   if (mode == ST_PLAIN)
     out[y] = v;
   else if (mode == ST_SCATTER)
-    out[cx_inv(y, nmask)] = v;
+    out[ent_inv((uint32_t)y, (uint32_t)nmask, ent, n)] = v;
 }
 
 template <typename T>
@@ -115,7 +114,7 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
   for (int i = 0; i <= SMALL_MAXN; ++i) red[tid][i] = 0.0;
 
   if (A.kind == K_FWD || A.kind == K_WHT) {
-    for (int x = tid; x < N; x += SMALL_NT) sp[x] = load_val<T>(A.load_mode, in, x, nmask, l0cs, n);
+    for (int x = tid; x < N; x += SMALL_NT) sp[x] = load_val<T>(A.load_mode, in, x, nmask, l0cs, n, A.ent);
     __syncthreads();
     for (int b = 0; b < n; ++b) {
       if (!((gm >> b) & 1u)) continue;
@@ -135,7 +134,7 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
       __syncthreads();
     }
     for (int x = tid; x < N; x += SMALL_NT) {
-      store_val(A.store_mode, out, x, nmask, sp[x]);
+      store_val(A.store_mode, out, x, nmask, sp[x], n, A.ent);
       if (A.flags & F_ENERGY) red[tid][0] += (double)(sp[x] * sp[x] * table[x]);
     }
   } else if (A.kind == K_BWD) {
@@ -167,7 +166,7 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
       }
       __syncthreads();
     }
-    for (int x = tid; x < N; x += SMALL_NT) store_val(A.store_mode, out, x, nmask, sl[x]);
+    for (int x = tid; x < N; x += SMALL_NT) store_val(A.store_mode, out, x, nmask, sl[x], n, A.ent);
   } else if (A.kind == K_GRAD_L0) {
     const bool init = (A.flags & F_LAMBDA_INIT) != 0;
     for (int x = tid; x < N; x += SMALL_NT) {

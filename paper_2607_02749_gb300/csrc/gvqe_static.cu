@@ -76,7 +76,7 @@ extern "C" int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const doubl
   cudaStream_t s = (cudaStream_t)stream;
 
   // The energy plan: forward passes with the energy fused into the last one.
-  const Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, false, true);
+  const Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, false, true, false, false, a->ent);
   const int n = a->n, P = pl.P;
   const size_t S = (size_t)1 << n;
   const size_t es = prec ? 8 : 4;

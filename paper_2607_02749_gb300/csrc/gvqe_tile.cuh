@@ -235,8 +235,6 @@ __device__ __forceinline__ uint32_t tile_base(uint32_t t, int c, int a, int tb) 
   return (tlo << c) | (thi << (a + tb - c));
 }
 
-// x = A^-1 y for the linear CX chain (y = prefix XOR of x); n <= 30 so 32 bits suffice.
-__device__ __forceinline__ uint32_t cx_inv(uint32_t y, uint32_t nmask) { return (y ^ (y << 1)) & nmask; }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -531,7 +529,10 @@ struct L0Tables {
   T lo[128];
   T mid[128];
   T hi[2];
-  __device__ __forceinline__ void build(const T2 *l0, int n, uint32_t xbase, int tid, int nthreads) {
+  // xbase: x of the tile's first element; hflip: the bits above TB that flip,
+  // together with bit TB, across the tile (0 unless the map flips them all)
+  __device__ __forceinline__ void build(const T2 *l0, int n, uint32_t xbase, uint32_t hflip, int tid,
+                                        int nthreads) {
     for (int m = tid; m < 256; m += nthreads) {
       const int hi7 = m >> 7, mm = m & 127;
       T p = T(1);
@@ -546,7 +547,8 @@ struct L0Tables {
     if (tid < 2) {
       T p = T(1);
       if (TB < n) p = tid ? l0[TB].y : l0[TB].x;
-      for (int q = TB + 1; q < n; ++q) p *= ((xbase >> q) & 1) ? l0[q].y : l0[q].x;
+      const uint32_t xh = xbase ^ ((((uint32_t)tid ^ (xbase >> TB)) & 1u) ? hflip : 0u);
+      for (int q = TB + 1; q < n; ++q) p *= ((xh >> q) & 1) ? l0[q].y : l0[q].x;
       hi[tid] = p;
     }
   }
@@ -577,13 +579,15 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
   const uint32_t tbase = tile_base(t, A.c, A.a, TB);
   const uint32_t nmask = (A.n >= 32) ? 0xffffffffu : ((1u << A.n) - 1);
+  const uint32_t d1 = ent_inv(1u, nmask, A.ent, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   if (!WHT) {
     load_gate_coeffs(A, cs, gt.cs, tid);
   }
   if constexpr (L0) {
-    const uint32_t xbase = (LOAD == LD_L0_GATHER) ? cx_inv(tbase, nmask) : tbase;
-    tab.build(cs, A.n, xbase, tid, NT);
+    const uint32_t xbase = (LOAD == LD_L0_GATHER) ? ent_inv(tbase, nmask, A.ent, A.n) : tbase;
+    const uint32_t hflip = (LOAD == LD_L0_GATHER && A.ent == ENT_FULL) ? (nmask & ~((2u << TB) - 1u)) : 0u;
+    tab.build(cs, A.n, xbase, hflip, tid, NT);
   }
   __syncthreads();
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
@@ -600,13 +604,13 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
     if constexpr (LOAD == LD_PLAIN) {
       v = __ldcg(reinterpret_cast<const T2 *>(in + y));
     } else if constexpr (LOAD == LD_GATHER) {
-      const uint32_t x = cx_inv(y, nmask);
+      const uint32_t x = ent_inv(y, nmask, A.ent, A.n);
       v.x = __ldcg(in + x);
-      v.y = __ldcg(in + (x ^ 3u));
+      v.y = __ldcg(in + (x ^ d1));
     } else if constexpr (LOAD == LD_L0_GATHER) {
-      const uint32_t x = cx_inv(y, nmask);
+      const uint32_t x = ent_inv(y, nmask, A.ent, A.n);
       v.x = tab(x);
-      v.y = tab(x ^ 3u);
+      v.y = tab(x ^ d1);
     } else {
       v.x = tab(y);
       v.y = tab(y + 1);
@@ -708,6 +712,7 @@ k_bwd(const PassArgs A) {
   const uint32_t tiles = (uint32_t)A.tiles;
   const bool pair = (A.flags & F_PAIR_ORDER) != 0;
   const uint32_t nmask = (1u << A.n) - 1;
+  const uint32_t d1 = ent_inv(1u, nmask, A.ent, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   load_gate_coeffs(A, cs, gt.cs, tid);
   if (sizeof(T) == 4) gt.pack(tid);
@@ -807,9 +812,9 @@ k_bwd(const PassArgs A) {
     for_L(gi, [&](int m, uint32_t y) {
       const T2 v = lam.pair(m);
       if constexpr (FULL) {
-        const uint32_t x = cx_inv(y, nmask);
+        const uint32_t x = ent_inv(y, nmask, A.ent, A.n);
         out[x] = v.x;
-        out[x ^ 3u] = v.y;
+        out[x ^ d1] = v.y;
       } else {
         *reinterpret_cast<T2 *>(out + y) = v;
       }
@@ -862,6 +867,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
   const uint32_t tbase = tile_base(t, A.c, A.a, TB);
   const uint32_t nmask = (1u << A.n) - 1;
+  const uint32_t d1 = ent_inv(1u, nmask, A.ent, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   load_gate_coeffs(A, cs, gt.cs, tid);
   if (sizeof(T) == 4) gt.pack(tid);
@@ -922,9 +928,9 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   for_L(gi, [&](int m, uint32_t y) {
     const T2 v = lam.pair(m);
     if constexpr (FULL) {
-      const uint32_t x = cx_inv(y, nmask);
+      const uint32_t x = ent_inv(y, nmask, A.ent, A.n);
       out[x] = v.x;
-      out[x ^ 3u] = v.y;
+      out[x ^ d1] = v.y;
     } else {
       *reinterpret_cast<T2 *>(out + y) = v;
     }

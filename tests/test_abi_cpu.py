@@ -70,7 +70,9 @@ def test_size_checks():
         _lib.gvqe_ansatz_create(4, -1)
     with pytest.raises(_lib.GvqeError) as e:
         _lib.gvqe_ansatz_create(4, 1, entangler=7)
-    assert e.value.code == _lib.GVQE_EUNSUPPORTED
+    assert e.value.code == _lib.GVQE_EINVAL
+    for ent in (_lib.GVQE_ENT_LINEAR, _lib.GVQE_ENT_CIRCULAR, _lib.GVQE_ENT_FULL):
+        _lib.gvqe_destroy(_lib.gvqe_ansatz_create(4, 1, entangler=ent))
     with pytest.raises(_lib.GvqeError):
         _lib.gvqe_hamiltonian_create(3, ["ZZ"], [1.0])  # string shorter than n is caught by length
 
