@@ -503,6 +503,22 @@ template <int TB, bool FULL, typename F>
 __device__ __forceinline__ void for_L(const GIdx<TB, FULL> &gi, F &&f) {
   for_pairs(gi.baseL, gi.SL, f);
 }
+// Round-L pairs of a FULL-layout pass through the entangler map: f(m, x) with
+// x = A^-1 y of element 2m.  A^-1 is GF(2)-linear and the Gray-code walk flips
+// one bit of y per step, so x advances by one XOR with that bit's image.
+template <int TB, typename F>
+__device__ __forceinline__ void for_L_ent(const GIdx<TB, true> &gi, uint32_t nmask, int ent, int n, F &&f) {
+  uint32_t d[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) d[j] = ent_inv(gi.SL[j], nmask, ent, n);
+  uint32_t x = ent_inv(gi.baseL, nmask, ent, n);
+#pragma unroll
+  for (int k = 0; k < ROUND / 2; ++k) {
+    const int m = gray(k);
+    if (k > 0) x ^= d[gray_bit(k)];
+    f(m, x);
+  }
+}
 template <int TB, bool FULL, typename F>
 __device__ __forceinline__ void for_H(const GIdx<TB, FULL> &gi, F &&f) {
   for_pairs(gi.baseH, gi.SH, f);
@@ -599,24 +615,30 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   Reg32<T> r;
   // round L: global -> registers (tile bits 6..9) -> gates -> shared.  The
   // inverse CX chain maps the pair (y, y + 1) to (x, x ^ 3), x = A^-1 y.
-  for_L(gi, [&](int m, uint32_t y) {
-    T2 v;
-    if constexpr (LOAD == LD_PLAIN) {
-      v = __ldcg(reinterpret_cast<const T2 *>(in + y));
-    } else if constexpr (LOAD == LD_GATHER) {
-      const uint32_t x = ent_inv(y, nmask, A.ent, A.n);
-      v.x = __ldcg(in + x);
-      v.y = __ldcg(in + (x ^ d1));
-    } else if constexpr (LOAD == LD_L0_GATHER) {
-      const uint32_t x = ent_inv(y, nmask, A.ent, A.n);
-      v.x = tab(x);
-      v.y = tab(x ^ d1);
-    } else {
-      v.x = tab(y);
-      v.y = tab(y + 1);
-    }
-    r.set_pair(m, v);
-  });
+  if constexpr (FULL && (LOAD == LD_GATHER || LOAD == LD_L0_GATHER)) {
+    for_L_ent(gi, nmask, A.ent, A.n, [&](int m, uint32_t x) {
+      T2 v;
+      if constexpr (LOAD == LD_GATHER) {
+        v.x = __ldcg(in + x);
+        v.y = __ldcg(in + (x ^ d1));
+      } else {
+        v.x = tab(x);
+        v.y = tab(x ^ d1);
+      }
+      r.set_pair(m, v);
+    });
+  } else {
+    for_L(gi, [&](int m, uint32_t y) {
+      T2 v;
+      if constexpr (LOAD == LD_PLAIN) {
+        v = __ldcg(reinterpret_cast<const T2 *>(in + y));
+      } else {
+        v.x = tab(y);
+        v.y = tab(y + 1);
+      }
+      r.set_pair(m, v);
+    });
+  }
   round_gates<4, WHT, false, 1>(r, gt, gm, 6, false);
   sts_L(s, sb, r);
   // round M: tile bits 0..4.  Layouts L and M of warp w both cover tile
@@ -809,6 +831,7 @@ k_bwd(const PassArgs A) {
     }
     lds_L(sl, sb, lam);
     round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
+    // (the scatter computes each x from y: measured faster here than the XOR walk)
     for_L(gi, [&](int m, uint32_t y) {
       const T2 v = lam.pair(m);
       if constexpr (FULL) {
@@ -925,16 +948,15 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   }
   lds_L(sl, sb, lam);
   round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
-  for_L(gi, [&](int m, uint32_t y) {
-    const T2 v = lam.pair(m);
-    if constexpr (FULL) {
-      const uint32_t x = ent_inv(y, nmask, A.ent, A.n);
+  if constexpr (FULL) {
+    for_L_ent(gi, nmask, A.ent, A.n, [&](int m, uint32_t x) {
+      const T2 v = lam.pair(m);
       out[x] = v.x;
       out[x ^ d1] = v.y;
-    } else {
-      *reinterpret_cast<T2 *>(out + y) = v;
-    }
-  });
+    });
+  } else {
+    for_L(gi, [&](int m, uint32_t y) { *reinterpret_cast<T2 *>(out + y) = lam.pair(m); });
+  }
   __syncthreads();
   double *part = A.part + (size_t)job * A.part_stride;
   if (tid < TB && ((gm >> tid) & 1u)) {
