@@ -266,6 +266,32 @@ def readout_leg(n: int, reps: int, ham, steps: int):
             "timing": "wall clock around synchronous gvqe_readout calls (state preparation included)"}
 
 
+def entangler_leg(n: int, reps: int, ham, steps: int):
+    """E+grad/s of the benchmark workload (one vector) with each entangler of Section IV-B."""
+    import torch
+
+    import paper_2607_02749_gb300 as gv
+    from paper_2607_02749_gb300 import workloads as wl
+
+    h = gv.Hamiltonian.from_workload(ham)
+    th = torch.as_tensor(wl.thetas(n, reps, 1, seed=1), dtype=torch.float64, device="cuda")
+    out = {}
+    for name, ent in (("linear", gv.GVQE_ENT_LINEAR), ("circular", gv.GVQE_ENT_CIRCULAR), ("full", gv.GVQE_ENT_FULL)):
+        a = gv.Ansatz(n, reps, entangler=ent)
+        e, g = gv.energy_grad(a, h, th)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            e, g = gv.energy_grad(a, h, th)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / steps
+        out[name] = {"value": 1.0 / dt, "unit": UNIT, "E": float(e.item())}
+        a.close()
+    h.close()
+    out["timing"] = "wall clock around synchronous single-vector gvqe_energy_grad calls (FP32 adjoint)"
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -453,6 +479,7 @@ def run_gvqe(args):
     if rank == 0 and not args.no_comparators:
         out["cluster_batch"] = cluster_leg(args.steps)
         out["readout"] = readout_leg(n, reps, ham, max(1, min(args.steps, 3)))
+        out["entanglers"] = entangler_leg(n, reps, ham, max(1, min(args.steps, 3)))
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
