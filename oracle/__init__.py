@@ -102,12 +102,16 @@ def set_threads(n: int) -> None:
 
 
 ENT_LINEAR, ENT_CIRCULAR, ENT_FULL = 0, 1, 2
+ENT_REVERSE_LINEAR, ENT_PAIRWISE, ENT_SCA = 3, 4, 5
 
 
 class entangler:
-    """Context manager selecting the oracle's entangler (Section IV-B):
-    ENT_LINEAR (default), ENT_CIRCULAR (CX(n-1,0) first, then the linear chain)
-    or ENT_FULL (CX(i,j) for all i < j in lexicographic order)."""
+    """Context manager selecting the oracle's entangler (Section IV-B, Table 2):
+    ENT_LINEAR (default), ENT_CIRCULAR (CX(n-1,0) first, then the linear chain),
+    ENT_FULL (CX(i,j) for all i < j in lexicographic order), ENT_REVERSE_LINEAR
+    (the linear chain in descending order), ENT_PAIRWISE (even-start pairs, then
+    odd-start pairs) or ENT_SCA (the circular list rotated right by the layer's
+    offset r - 1, control and target swapped on odd offsets)."""
 
     def __init__(self, ent: int, lib: Optional[ctypes.CDLL] = None):
         self.ent = int(ent)

@@ -149,22 +149,63 @@ def basis_state_energy(n: int, reps: int, flips, strings, coeffs) -> float:
     return tot
 
 
-def entangler_map(x: int, n: int, ent: int = 0) -> int:
-    """Basis index after one entangler layer as a closed-form GF(2) map (no gate list):
-    linear: y_j = x_0 ^ ... ^ x_j (each CX(q, q+1) adds the updated bit q to bit q+1);
-    circular: the same after x_0 ^= x_{n-1} (the wrap-around CX(n-1, 0) acts first);
-    full: y_j = x_j ^ x_{j-1}, since bit j collects x_i and, through CX(i, j) after
-    bit i was updated, the running sums of the lower bits, which cancel pairwise."""
-    if ent == 2:
-        return (x ^ (x << 1)) & ((1 << n) - 1)
-    if ent == 1 and n > 1:
-        x ^= (x >> (n - 1)) & 1
-    y = 0
-    acc = 0
+def _prefix_xor(x: int, n: int) -> int:
+    """Bit j of the result is x_0 ^ ... ^ x_j."""
+    y = acc = 0
     for q in range(n):
         acc ^= (x >> q) & 1
         y |= acc << q
     return y
+
+
+def entangler_map(x: int, n: int, ent: int = 0, layer: int = 1) -> int:
+    """Basis index after the entangler of layer `layer` as a closed-form GF(2) map
+    (no gate list):
+    linear: y_j = x_0 ^ ... ^ x_j (each CX(q, q+1) adds the updated bit q to bit q+1);
+    circular: the same after x_0 ^= x_{n-1} (the wrap-around CX(n-1, 0) acts first);
+    full: y_j = x_j ^ x_{j-1}, since bit j collects x_i and, through CX(i, j) after
+    bit i was updated, the running sums of the lower bits, which cancel pairwise;
+    reverse linear: y_j = x_j ^ x_{j-1} as well (in descending order every CX(q, q+1)
+    still sees the original bit q);
+    pairwise: odd j: y_j = x_j ^ x_{j-1}; even j >= 2: y_j = x_j ^ x_{j-1} ^ x_{j-2}
+    (the second half adds the updated odd bit j-1);
+    SCA, offset o = layer - 1, s = n-1-o mod n, in the frame z_k = x_{s+k mod n}
+    (the direction follows the parity of o itself, not of o mod n):
+    even o: w_k = z_0 ^ ... ^ z_k, then w_0 ^= w_{n-1} (the last gate closes the ring);
+    odd o: w_k = z_k ^ z_{k+1} for k < n-1, w_{n-1} = z_{n-1} ^ w_0; y_{s+k mod n} = w_k."""
+    mask = (1 << n) - 1
+    if ent in (2, 3):
+        return (x ^ (x << 1)) & mask
+    if ent == 4:
+        y = 0
+        for j in range(n):
+            b = (x >> j) & 1
+            if j >= 1:
+                b ^= (x >> (j - 1)) & 1
+            if j >= 2 and j % 2 == 0:
+                b ^= (x >> (j - 2)) & 1
+            y |= b << j
+        return y
+    if ent == 5:
+        if n < 2:
+            return x
+        o = (layer - 1) % n
+        s = (n - 1 - o) % n
+        z = [(x >> ((s + k) % n)) & 1 for k in range(n)]
+        if (layer - 1) % 2 == 0:
+            w = [0] * n
+            acc = 0
+            for k in range(n):
+                acc ^= z[k]
+                w[k] = acc
+            w[0] ^= w[n - 1]
+        else:
+            w = [z[k] ^ z[k + 1] for k in range(n - 1)] + [0]
+            w[n - 1] = z[n - 1] ^ w[0]
+        return sum(w[k] << ((s + k) % n) for k in range(n))
+    if ent == 1 and n > 1:
+        x ^= (x >> (n - 1)) & 1
+    return _prefix_xor(x, n)
 
 
 def basis_state_index(n: int, reps: int, flips, ent: int = 0) -> int:
@@ -173,7 +214,7 @@ def basis_state_index(n: int, reps: int, flips, ent: int = 0) -> int:
     x = 0
     for r in range(reps + 1):
         if r > 0:
-            x = entangler_map(x, n, ent)
+            x = entangler_map(x, n, ent, r)
         for q in range(n):
             if f[r * n + q]:
                 x ^= 1 << q

@@ -61,11 +61,26 @@ def hamiltonian(strings: Sequence[str], coeffs) -> np.ndarray:
     return h
 
 
-def entangler_pairs(n: int, ent: int = 0):
-    """(control, target) list of an entangler: 0 linear CX(0,1)..CX(n-2,n-1);
-    1 circular: CX(n-1,0) first, then linear; 2 full: CX(i,j), i < j, lexicographic."""
+def entangler_pairs(n: int, ent: int = 0, layer: int = 1):
+    """(control, target) list of the entangler of layer `layer` (1 .. reps):
+    0 linear CX(0,1)..CX(n-2,n-1); 1 circular: CX(n-1,0) first, then linear;
+    2 full: CX(i,j), i < j, lexicographic; 3 reverse linear: CX(n-2,n-1) down to
+    CX(0,1); 4 pairwise: CX(i,i+1) for even i, then for odd i; 5 SCA: with offset
+    o = layer - 1, the wrap-around chain of n gates CX(s+k, s+k+1) (indices mod n)
+    starting at s = n-1-o, each gate reversed to CX(s+k+1, s+k) when o is odd."""
     if ent == 2:
         return [(i, j) for i in range(n) for j in range(i + 1, n)]
+    if ent == 3:
+        return [(q, q + 1) for q in reversed(range(n - 1))]
+    if ent == 4:
+        return [(q, q + 1) for q in range(0, n - 1, 2)] + [(q, q + 1) for q in range(1, n - 1, 2)]
+    if ent == 5:
+        if n < 2:
+            return []
+        o = (layer - 1) % n
+        s = (n - 1 - o) % n
+        chain = [((s + k) % n, (s + k + 1) % n) for k in range(n)]
+        return [(t, c) for c, t in chain] if (layer - 1) % 2 else chain
     pairs = [(q, q + 1) for q in range(n - 1)]
     if ent == 1 and n > 1:
         pairs = [(n - 1, 0)] + pairs
@@ -79,7 +94,7 @@ def circuit(n: int, reps: int, theta, ent: int = 0) -> np.ndarray:
     u = np.eye(1 << n, dtype=np.complex128)
     for r in range(reps + 1):
         if r > 0:
-            for c, t in entangler_pairs(n, ent):
+            for c, t in entangler_pairs(n, ent, r):
                 u = cnot(c, t, n) @ u
         for q in range(n):
             u = embed({q: ry(th[r * n + q])}, n) @ u

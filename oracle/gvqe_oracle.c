@@ -20,7 +20,7 @@
  * Conventions (readings where the paper is silent): qubit q is bit q of the
  * basis index x; character i of a Pauli string acts on qubit i; the linear
  * entangler is CX(0,1), CX(1,2), ..., CX(n-2,n-1) applied in that order (the
- * circular and full entanglers are listed at entangler_gates below).
+ * other entanglers are listed at entangler_gates below).
  *
  * Every gate is applied one at a time in circuit order; there is no fusion,
  * no table, no Walsh-Hadamard transform and no grouping of terms.
@@ -92,21 +92,30 @@ static void apply_cx(cplx *psi, int n, int ctl, int tgt) {
 }
 
 /*
- * Entanglers of Section IV-B as ordered CNOT lists (control, target):
- *   0 linear:   CX(0,1), CX(1,2), ..., CX(n-2,n-1)
- *   1 circular: CX(n-1,0) (the wrap-around), then the linear list
- *   2 full:     CX(i,j) for every i < j, i ascending, j ascending within i
+ * Entanglers as ordered CNOT lists (control, target).  Section IV-B names
+ * linear, circular and full; Section V-A and Table 2 add reverse linear,
+ * pairwise and SCA (shifted-circular-alternating).  The paper prints none of
+ * the orders; these are the readings used throughout:
+ *   0 linear:         CX(0,1), CX(1,2), ..., CX(n-2,n-1)
+ *   1 circular:       CX(n-1,0) (the wrap-around), then the linear list
+ *   2 full:           CX(i,j) for every i < j, i ascending, j ascending within i
+ *   3 reverse linear: CX(n-2,n-1), CX(n-3,n-2), ..., CX(0,1)
+ *   4 pairwise:       CX(i,i+1) for even i ascending, then for odd i ascending
+ *   5 SCA:            in entangler layer r (r = 1 .. reps, offset o = r - 1) the
+ *                     circular list rotated right by o mod n (its last o gates
+ *                     move to the front), with control and target swapped in
+ *                     every gate when o is odd
  * The entangler in use is a process-wide setting of this test oracle.
  */
 static int g_entangler = 0;
 
 int oracle_set_entangler(int ent) {
-    if (ent < 0 || ent > 2) return ORACLE_EINVAL;
+    if (ent < 0 || ent > 5) return ORACLE_EINVAL;
     g_entangler = ent;
     return ORACLE_OK;
 }
 
-static int entangler_gates(int n, int *ctl, int *tgt) {
+static int entangler_gates(int n, int layer, int *ctl, int *tgt) {
     int k = 0;
     if (g_entangler == 2) {
         for (int i = 0; i < n; ++i)
@@ -116,7 +125,22 @@ static int entangler_gates(int n, int *ctl, int *tgt) {
             }
         return k;
     }
-    if (g_entangler == 1 && n > 1) {
+    if (g_entangler == 3) {
+        for (int q = n - 2; q >= 0; --q) {
+            ctl[k] = q;
+            tgt[k++] = q + 1;
+        }
+        return k;
+    }
+    if (g_entangler == 4) {
+        for (int start = 0; start < 2; ++start)
+            for (int q = start; q + 1 < n; q += 2) {
+                ctl[k] = q;
+                tgt[k++] = q + 1;
+            }
+        return k;
+    }
+    if ((g_entangler == 1 || g_entangler == 5) && n > 1) {
         ctl[k] = n - 1;
         tgt[k++] = 0;
     }
@@ -124,20 +148,34 @@ static int entangler_gates(int n, int *ctl, int *tgt) {
         ctl[k] = q;
         tgt[k++] = q + 1;
     }
+    if (g_entangler == 5 && k > 0) {
+        /* rotate the circular list right by o, then swap roles for odd o */
+        const int o = (layer - 1) % k;
+        int c2[ORACLE_MAX_QUBITS], t2[ORACLE_MAX_QUBITS];
+        for (int g = 0; g < k; ++g) {
+            c2[(g + o) % k] = ctl[g];
+            t2[(g + o) % k] = tgt[g];
+        }
+        const int swap = (layer - 1) & 1;
+        for (int g = 0; g < k; ++g) {
+            ctl[g] = swap ? t2[g] : c2[g];
+            tgt[g] = swap ? c2[g] : t2[g];
+        }
+    }
     return k;
 }
 
-/* The entangler, one gate at a time in its order. */
-static void apply_entangler(cplx *psi, int n) {
+/* The entangler of layer r (r >= 1), one gate at a time in its order. */
+static void apply_entangler(cplx *psi, int n, int layer) {
     int ctl[ORACLE_MAX_QUBITS * ORACLE_MAX_QUBITS], tgt[ORACLE_MAX_QUBITS * ORACLE_MAX_QUBITS];
-    const int k = entangler_gates(n, ctl, tgt);
+    const int k = entangler_gates(n, layer, ctl, tgt);
     for (int g = 0; g < k; ++g) apply_cx(psi, n, ctl[g], tgt[g]);
 }
 
 /* Its inverse: the same CNOTs in reverse order (each is its own inverse). */
-static void apply_entangler_inverse(cplx *psi, int n) {
+static void apply_entangler_inverse(cplx *psi, int n, int layer) {
     int ctl[ORACLE_MAX_QUBITS * ORACLE_MAX_QUBITS], tgt[ORACLE_MAX_QUBITS * ORACLE_MAX_QUBITS];
-    const int k = entangler_gates(n, ctl, tgt);
+    const int k = entangler_gates(n, layer, ctl, tgt);
     for (int g = k - 1; g >= 0; --g) apply_cx(psi, n, ctl[g], tgt[g]);
 }
 
@@ -148,7 +186,7 @@ static void prepare_state(cplx *psi, int n, int reps, const double *theta) {
     psi[0] = 1.0;
     for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[q]);
     for (int r = 1; r <= reps; ++r) {
-        apply_entangler(psi, n);
+        apply_entangler(psi, n, r);
         for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[r * n + q]);
     }
 }
@@ -302,8 +340,8 @@ int oracle_energy_grad(int n, int reps, const double *theta, int n_terms, const 
             apply_ry(lam, n, q, -theta[p]);
         }
         if (r > 0) {
-            apply_entangler_inverse(psi, n);
-            apply_entangler_inverse(lam, n);
+            apply_entangler_inverse(psi, n, r);
+            apply_entangler_inverse(lam, n, r);
         }
     }
     free(psi);

@@ -26,13 +26,23 @@ MUTANTS = {
     "cx_order": ("for (int g = 0; g < k; ++g) apply_cx(psi, n, ctl[g], tgt[g]);",
                  "for (int g = k - 1; g >= 0; --g) apply_cx(psi, n, ctl[g], tgt[g]);"),
     "circular_wrap_after_chain": (
-        "    if (g_entangler == 1 && n > 1) {\n        ctl[k] = n - 1;\n        tgt[k++] = 0;\n    }\n"
+        "    if ((g_entangler == 1 || g_entangler == 5) && n > 1) {\n        ctl[k] = n - 1;\n        tgt[k++] = 0;\n    }\n"
         "    for (int q = 0; q + 1 < n; ++q) {\n        ctl[k] = q;\n        tgt[k++] = q + 1;\n    }\n",
         "    for (int q = 0; q + 1 < n; ++q) {\n        ctl[k] = q;\n        tgt[k++] = q + 1;\n    }\n"
-        "    if (g_entangler == 1 && n > 1) {\n        ctl[k] = n - 1;\n        tgt[k++] = 0;\n    }\n"),
+        "    if ((g_entangler == 1 || g_entangler == 5) && n > 1) {\n        ctl[k] = n - 1;\n        tgt[k++] = 0;\n    }\n"),
     "circular_wrap_direction": ("        ctl[k] = n - 1;\n        tgt[k++] = 0;", "        ctl[k] = 0;\n        tgt[k++] = n - 1;"),
     "full_controls_descending": ("for (int i = 0; i < n; ++i)\n            for (int j = i + 1; j < n; ++j)",
                                  "for (int i = n - 1; i >= 0; --i)\n            for (int j = i + 1; j < n; ++j)"),
+    "reverse_linear_ascending": ("for (int q = n - 2; q >= 0; --q) {", "for (int q = 0; q <= n - 2; ++q) {"),
+    "pairwise_odd_pairs_first": ("for (int start = 0; start < 2; ++start)", "for (int start = 1; start >= 0; --start)"),
+    "pairwise_one_half_only": ("for (int start = 0; start < 2; ++start)", "for (int start = 0; start < 1; ++start)"),
+    "sca_rotated_left": ("c2[(g + o) % k] = ctl[g];\n            t2[(g + o) % k] = tgt[g];",
+                         "c2[(g + k - o) % k] = ctl[g];\n            t2[(g + k - o) % k] = tgt[g];"),
+    "sca_never_swapped": ("const int swap = (layer - 1) & 1;", "const int swap = 0;"),
+    "sca_swapped_on_even": ("const int swap = (layer - 1) & 1;", "const int swap = layer & 1;"),
+    "sca_offset_from_layer": ("const int o = (layer - 1) % k;", "const int o = layer % k;"),
+    "adjoint_wrong_layer_entangler": ("apply_entangler_inverse(psi, n, r);\n            apply_entangler_inverse(lam, n, r);",
+                                      "apply_entangler_inverse(psi, n, 1);\n            apply_entangler_inverse(lam, n, 1);"),
     "y_phase": ("phase *= b ? -I : I;", "phase *= b ? I : -I;"),
     "z_sign_dropped": ("if (b) phase = -phase;", "(void)b;"),
     "last_term_dropped": ("for (int k = 0; k < n_terms; ++k) {", "for (int k = 0; k + 1 < n_terms; ++k) {"),
@@ -77,8 +87,9 @@ def _pins_pass(lib) -> bool:
         e1 = oracle.energy(n, 1, t1, ham.strings, ham.coeffs, lib=lib)
         if abs(e1 - closed_form.heisenberg_reps1_energy(n, t1, ham.strings, ham.coeffs)) > 1e-12 * ham.abs_sum():
             return False
-        # circular and full: the dense model, and the basis-index maps of closed_form
-        for ent in (oracle.ENT_CIRCULAR, oracle.ENT_FULL):
+        # the other entanglers: the dense model, and the basis-index maps of closed_form
+        for ent in (oracle.ENT_CIRCULAR, oracle.ENT_FULL, oracle.ENT_REVERSE_LINEAR, oracle.ENT_PAIRWISE,
+                    oracle.ENT_SCA):
             with oracle.entangler(ent, lib=lib):
                 if np.max(np.abs(oracle.state(n, reps, th, lib=lib) - dense.state(n, reps, th, ent))) > 1e-12:
                     return False

@@ -193,13 +193,17 @@ def test_masked_param_shift_zeroes_inactive_entries():
     assert np.max(np.abs(g[mask == 1] - full[mask == 1])) < 1e-12 * ham.abs_sum()
 
 
-@pytest.mark.parametrize("ent", [oracle.ENT_LINEAR, oracle.ENT_CIRCULAR, oracle.ENT_FULL])
+ALL_ENTS = [oracle.ENT_LINEAR, oracle.ENT_CIRCULAR, oracle.ENT_FULL, oracle.ENT_REVERSE_LINEAR,
+            oracle.ENT_PAIRWISE, oracle.ENT_SCA]
+
+
+@pytest.mark.parametrize("ent", ALL_ENTS)
 def test_entangler_pins(ent):
-    """Circular and full entanglers (Section IV-B): the C oracle equals the dense
+    """Every entangler (Section IV-B, Table 2): the C oracle equals the dense
     matrix model, signed basis states follow the closed-form GF(2) index maps,
     and the adjoint gradient equals the dense parameter-shift gradient."""
     rng = np.random.default_rng(11 + ent)
-    for n, reps in ((1, 2), (2, 2), (3, 1), (5, 2), (7, 1)):
+    for n, reps in ((1, 2), (2, 3), (3, 1), (4, 3), (5, 2), (7, 1)):
         th = wl.thetas(n, reps, 1, seed=n + ent)[0]
         ham = wl.pauli_hamiltonian(n, 10, seed=n)
         with oracle.entangler(ent):
@@ -217,10 +221,75 @@ def test_entangler_pins(ent):
 def test_entangler_maps_are_the_cnot_products():
     """The closed-form maps agree with the CNOT lists applied to bit vectors."""
     for n in range(1, 9):
-        for ent in (0, 1, 2):
+        for ent in ALL_ENTS:
+            for layer in (1, 2, 3, 4) if ent == oracle.ENT_SCA else (1,):
+                for x in range(1 << n):
+                    y = x
+                    for c, t in dense.entangler_pairs(n, ent, layer):
+                        if (y >> c) & 1:
+                            y ^= 1 << t
+                    assert y == closed_form.entangler_map(x, n, ent, layer)
+
+
+def _entangler_unitary(n, ent, layer=1):
+    u = np.eye(1 << n)
+    for c, t in dense.entangler_pairs(n, ent, layer):
+        u = dense.cnot(c, t, n) @ u
+    return u
+
+
+def test_reverse_linear_is_the_full_entangler():
+    """A textbook identity: the descending CX chain and the all-pairs CX list in
+    lexicographic order are the same unitary."""
+    for n in range(2, 7):
+        assert np.array_equal(_entangler_unitary(n, oracle.ENT_REVERSE_LINEAR), _entangler_unitary(n, oracle.ENT_FULL))
+        assert not np.array_equal(_entangler_unitary(n, oracle.ENT_REVERSE_LINEAR),
+                                  _entangler_unitary(n, oracle.ENT_LINEAR)) or n == 2
+
+
+def _kron_layer(n, pairs):
+    """One layer of disjoint nearest-neighbour CNOTs CX(q, q+1) built by Kronecker
+    products (qubit q is bit q, so the rightmost factor is qubit 0)."""
+    cx = np.array([[1, 0, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0], [0, 1, 0, 0]], dtype=float)  # ctl bit 0, tgt bit 1
+    ops, q = [], 0
+    starts = {c for c, _ in pairs}
+    while q < n:
+        if q in starts:
+            ops.append(cx)
+            q += 2
+        else:
+            ops.append(np.eye(2))
+            q += 1
+    u = np.eye(1)
+    for op in ops:
+        u = np.kron(op, u)
+    return u
+
+
+def test_pairwise_is_two_layers_of_disjoint_cnots():
+    for n in range(2, 8):
+        even = [(q, q + 1) for q in range(0, n - 1, 2)]
+        odd = [(q, q + 1) for q in range(1, n - 1, 2)]
+        want = _kron_layer(n, odd) @ _kron_layer(n, even)
+        assert np.array_equal(_entangler_unitary(n, oracle.ENT_PAIRWISE), want)
+
+
+def test_sca_is_the_shifted_circular_entangler_alternating_direction():
+    """SCA at offset o = layer - 1 is the circular entangler with every qubit q
+    relabelled q - o (mod n); on odd offsets every CNOT is reversed, which is
+    conjugation of the whole list by Hadamards on every qubit."""
+    for n in range(2, 7):
+        circ = _entangler_unitary(n, oracle.ENT_CIRCULAR)
+        hn = dense.embed({q: np.array([[1, 1], [1, -1]]) / math.sqrt(2) for q in range(n)}, n).real
+        for layer in range(1, 2 * n + 2):
+            o = layer - 1
+            perm = np.zeros((1 << n, 1 << n))
             for x in range(1 << n):
-                y = x
-                for c, t in dense.entangler_pairs(n, ent):
-                    if (y >> c) & 1:
-                        y ^= 1 << t
-                assert y == closed_form.entangler_map(x, n, ent)
+                xr = 0
+                for q in range(n):
+                    xr |= ((x >> q) & 1) << ((q - o) % n)
+                perm[xr, x] = 1.0
+            want = perm @ circ @ perm.T
+            if o % 2:
+                want = hn @ want @ hn
+            assert np.allclose(_entangler_unitary(n, oracle.ENT_SCA, layer), want, atol=1e-12), (n, layer)
