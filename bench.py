@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-comparators", action="store_true", help="skip the FP64 comparator legs")
     ap.add_argument("--only-readout", action="store_true",
                     help="run only the readout leg on the workload and print its JSON object")
+    ap.add_argument("--only-entanglers", action="store_true",
+                    help="run only the entangler leg on the workload and print its JSON object")
     return ap.parse_args()
 
 
@@ -267,7 +269,7 @@ def readout_leg(n: int, reps: int, ham, steps: int):
 
 
 def entangler_leg(n: int, reps: int, ham, steps: int):
-    """E+grad/s of the benchmark workload (one vector) with each entangler of Section IV-B."""
+    """E+grad/s of the benchmark workload (one vector) with each entangler (Section IV-B, Table 2)."""
     import torch
 
     import paper_2607_02749_gb300 as gv
@@ -276,7 +278,9 @@ def entangler_leg(n: int, reps: int, ham, steps: int):
     h = gv.Hamiltonian.from_workload(ham)
     th = torch.as_tensor(wl.thetas(n, reps, 1, seed=1), dtype=torch.float64, device="cuda")
     out = {}
-    for name, ent in (("linear", gv.GVQE_ENT_LINEAR), ("circular", gv.GVQE_ENT_CIRCULAR), ("full", gv.GVQE_ENT_FULL)):
+    for name, ent in (("linear", gv.GVQE_ENT_LINEAR), ("circular", gv.GVQE_ENT_CIRCULAR), ("full", gv.GVQE_ENT_FULL),
+                      ("reverse_linear", gv.GVQE_ENT_REVERSE_LINEAR), ("pairwise", gv.GVQE_ENT_PAIRWISE),
+                      ("sca", gv.GVQE_ENT_SCA)):
         a = gv.Ansatz(n, reps, entangler=ent)
         e, g = gv.energy_grad(a, h, th)
         torch.cuda.synchronize()
@@ -346,6 +350,11 @@ def run_gvqe(args):
         if rank == 0:
             print(json.dumps({"workload": args.workload, "readout": readout_leg(n, reps, ham, max(1, args.steps))}),
                   flush=True)
+        return 0
+    if args.only_entanglers:
+        if rank == 0:
+            print(json.dumps({"workload": args.workload,
+                              "entanglers": entangler_leg(n, reps, ham, max(1, args.steps))}), flush=True)
         return 0
     theta = wl.thetas(n, reps, B, seed=1 + rank)
     P = n * (reps + 1)

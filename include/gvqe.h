@@ -47,13 +47,23 @@ extern "C" {
 #define GVQE_GRAD_ADJOINT 0x0     /* reverse-mode (adjoint) gradient (default) */
 #define GVQE_GRAD_PARAM_SHIFT 0x2 /* parameter-shift gradient, Eq. 13 (2 P_active + 1 energies) */
 
-/* entanglers for gvqe_ansatz_create (Section IV-B), each an ordered CNOT list:
- * LINEAR   CX(0,1), CX(1,2), ..., CX(n-2,n-1)
- * CIRCULAR CX(n-1,0) (the wrap-around) first, then the LINEAR list
- * FULL     CX(i,j) for every i < j, i ascending, j ascending within i */
+/* entanglers for gvqe_ansatz_create (Section IV-B names the first three; Table 2
+ * runs the method with all six), each an ordered CNOT list; r = 1..reps is the
+ * entangler layer:
+ * LINEAR         CX(0,1), CX(1,2), ..., CX(n-2,n-1)
+ * CIRCULAR       CX(n-1,0) (the wrap-around) first, then the LINEAR list
+ * FULL           CX(i,j) for every i < j, i ascending, j ascending within i
+ * REVERSE_LINEAR CX(n-2,n-1), CX(n-3,n-2), ..., CX(0,1) (the same unitary as FULL)
+ * PAIRWISE       CX(i,i+1) for even i ascending, then for odd i ascending
+ * SCA            the CIRCULAR list rotated right by (r-1) mod n (its last gates
+ *                move to the front), every CX(c,t) turned into CX(t,c) when r-1
+ *                is odd (shifted-circular-alternating) */
 #define GVQE_ENT_LINEAR 0
 #define GVQE_ENT_CIRCULAR 1
 #define GVQE_ENT_FULL 2
+#define GVQE_ENT_REVERSE_LINEAR 3
+#define GVQE_ENT_PAIRWISE 4
+#define GVQE_ENT_SCA 5
 
 /* options for gvqe_ansatz_set_option */
 #define GVQE_OPT_TILE_BITS 1 /* log2 amplitudes per on-chip tile, 10..13 (FP64: 10..12); 0 = auto (13 FP32, 12 FP64) */
@@ -87,8 +97,9 @@ int gvqe_hamiltonian_create(int n_qubits, int n_terms, const char *pauli, const 
  * gvqe_ansatz_create -- the parameterised circuit U(theta) of Section IV-B
  * (RY layers with an entangler between them; Eq. 7, Eq. 8 with RY only).
  *   n_qubits: 1..30.  reps: 0..64 (the number D of [entangler, RY] repetitions).
- *   entangler: GVQE_ENT_LINEAR, GVQE_ENT_CIRCULAR or GVQE_ENT_FULL.
- * Errors: GVQE_EINVAL.
+ *   entangler: one of GVQE_ENT_LINEAR .. GVQE_ENT_SCA.
+ * Errors: GVQE_EINVAL; GVQE_EUNSUPPORTED if the layer-1 gather of this
+ * entangler cannot use split product-state tables (none of the six at 1..30).
  */
 int gvqe_ansatz_create(int n_qubits, int reps, int entangler, gvqe_ansatz *out);
 
@@ -226,6 +237,17 @@ const char *gvqe_last_error(void);
  * buflen).  Returns the number of passes per rotation layer, or a negative code.
  */
 int gvqe_plan_describe(int n_qubits, int reps, int flags, int tile_bits, char *buf, int buflen);
+
+/*
+ * gvqe_entangler_inverse -- basis-index map of one entangler layer (Section
+ * IV-B, Table 2): the entangler of layer r (1..reps) sends |x> to |A x>, a
+ * GF(2)-linear permutation of basis indices; this writes x[i] = A^-1 y[i] for
+ * count indices, the map the gathering passes apply.  Host arrays (y, x may
+ * alias); every y[i] must lie in [0, 2^n_qubits).
+ * Errors: GVQE_EINVAL (bad entangler, n, layer, count < 0, NULL, y out of range).
+ */
+int gvqe_entangler_inverse(int entangler, int n_qubits, int layer, const long long *y, long long *x,
+                           long long count);
 
 /* gvqe_hamiltonian_stats -- counts after parsing: diagonal strings, X-mask
  * groups, grouped strings, dropped odd-Y strings (any pointer may be NULL). */

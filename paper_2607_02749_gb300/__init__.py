@@ -11,18 +11,20 @@ from __future__ import annotations
 from typing import Optional, Sequence
 
 from . import _lib
-from ._lib import (GVQE_ENT_CIRCULAR, GVQE_ENT_FULL, GVQE_ENT_LINEAR, GVQE_FP32, GVQE_FP64, GVQE_GRAD_ADJOINT, GVQE_GRAD_PARAM_SHIFT,
+from ._lib import (GVQE_ENT_CIRCULAR, GVQE_ENT_FULL, GVQE_ENT_LINEAR, GVQE_ENT_PAIRWISE, GVQE_ENT_REVERSE_LINEAR,
+                   GVQE_ENT_SCA, GVQE_FP32, GVQE_FP64, GVQE_GRAD_ADJOINT, GVQE_GRAD_PARAM_SHIFT,
                    GVQE_OPT_TILE_BITS, GvqeError, gvqe_ansatz_create, gvqe_ansatz_set_option, gvqe_batch_create,
                    gvqe_batch_run, gvqe_destroy, gvqe_energy, gvqe_energy_grad, gvqe_hamiltonian_create,
-                   gvqe_hamiltonian_stats, gvqe_last_error, gvqe_plan_describe, gvqe_readout, gvqe_version)
+                   gvqe_entangler_inverse, gvqe_hamiltonian_stats, gvqe_last_error, gvqe_plan_describe,
+                   gvqe_readout, gvqe_version)
 
 __all__ = [
     "Hamiltonian", "Ansatz", "Batch", "GvqeEnergy", "energy", "energy_grad", "readout", "Readout", "GvqeError",
     "GVQE_FP32", "GVQE_FP64", "GVQE_GRAD_ADJOINT", "GVQE_GRAD_PARAM_SHIFT", "GVQE_ENT_LINEAR",
-    "GVQE_ENT_CIRCULAR", "GVQE_ENT_FULL",
+    "GVQE_ENT_CIRCULAR", "GVQE_ENT_FULL", "GVQE_ENT_REVERSE_LINEAR", "GVQE_ENT_PAIRWISE", "GVQE_ENT_SCA",
     "gvqe_hamiltonian_create", "gvqe_ansatz_create", "gvqe_ansatz_set_option", "gvqe_energy",
     "gvqe_energy_grad", "gvqe_batch_create", "gvqe_batch_run", "gvqe_destroy", "gvqe_last_error",
-    "gvqe_plan_describe", "gvqe_hamiltonian_stats", "gvqe_readout", "gvqe_version",
+    "gvqe_plan_describe", "gvqe_hamiltonian_stats", "gvqe_readout", "gvqe_version", "gvqe_entangler_inverse",
 ]
 
 
@@ -58,7 +60,8 @@ class Hamiltonian(_Handle):
 
 class Ansatz(_Handle):
     """RY layer + reps x [entangler, RY layer] (Section IV-B); P = n (reps + 1).
-    entangler: GVQE_ENT_LINEAR (default), GVQE_ENT_CIRCULAR or GVQE_ENT_FULL."""
+    entangler: GVQE_ENT_LINEAR (default), GVQE_ENT_CIRCULAR, GVQE_ENT_FULL, GVQE_ENT_REVERSE_LINEAR,
+    GVQE_ENT_PAIRWISE or GVQE_ENT_SCA (Section IV-B, Table 2)."""
 
     def __init__(self, n_qubits: int, reps: int, entangler: int = GVQE_ENT_LINEAR, tile_bits: int = 0):
         self.n_qubits = n_qubits

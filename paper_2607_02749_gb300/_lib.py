@@ -28,6 +28,9 @@ GVQE_GRAD_PARAM_SHIFT = 0x2
 GVQE_ENT_LINEAR = 0
 GVQE_ENT_CIRCULAR = 1
 GVQE_ENT_FULL = 2
+GVQE_ENT_REVERSE_LINEAR = 3
+GVQE_ENT_PAIRWISE = 4
+GVQE_ENT_SCA = 5
 GVQE_OPT_TILE_BITS = 1
 GVQE_MAX_QUBITS = 30
 GVQE_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
@@ -71,6 +74,7 @@ _SIGS = {
     "gvqe_readout": [_VP, _VP, _VP, _I, ctypes.c_double, _I, _VP, _VP, _VP, _VP, _VP],
     "gvqe_destroy": [_VP],
     "gvqe_plan_describe": [_I, _I, _I, _I, ctypes.c_char_p, _I],
+    "gvqe_entangler_inverse": [_I, _I, _I, _VP, _VP, ctypes.c_longlong],
     "gvqe_hamiltonian_stats": [_VP, _VP, _VP, _VP, _VP],
     "gvqe_version": [],
     "gvqe_profile_enable": [_I],
@@ -246,6 +250,17 @@ def gvqe_plan_describe(n_qubits: int, reps: int, flags: int = GVQE_FP32, tile_bi
     buf = ctypes.create_string_buffer(1 << 16)
     _check(load().gvqe_plan_describe(n_qubits, reps, flags, tile_bits, buf, len(buf)), "gvqe_plan_describe")
     return buf.value.decode()
+
+
+def gvqe_entangler_inverse(entangler: int, n_qubits: int, layer: int, y) -> "np.ndarray":
+    """x = A^-1 y for the entangler of layer `layer` (host only, no GPU)."""
+    import numpy as np
+
+    ya = np.ascontiguousarray(np.asarray(y, dtype=np.int64).reshape(-1))
+    xa = np.empty_like(ya)
+    _check(load().gvqe_entangler_inverse(entangler, n_qubits, layer, ya.ctypes.data, xa.ctypes.data, ya.size),
+           "gvqe_entangler_inverse")
+    return xa
 
 
 def gvqe_hamiltonian_stats(ham: int) -> dict:

@@ -195,6 +195,126 @@ std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits) {
 
 static int qubit_of(const LayerPass &lp, int i) { return i < lp.c ? i : lp.a + i - lp.c; }
 
+// ------------------------------------------------------------- entanglers --
+// The closed form of A^-1 for the entangler of layer r (1 .. reps).
+EntMap ent_map(int ent, int n, int r) {
+  EntMap e;
+  memset(&e, 0, sizeof(e));
+  e.form = EF_DIFF;
+  if (n < 2) return e;  // no CNOT: the identity, which EF_DIFF is on one bit
+  const uint32_t nmask = (uint32_t)((1ull << n) - 1);
+  switch (ent) {
+    case ENT_CIRCULAR:
+      e.form = EF_WRAP_DIFF;
+      break;
+    case ENT_FULL:
+    case ENT_REVERSE_LINEAR:
+      e.form = EF_PREFIX;
+      break;
+    case ENT_PAIRWISE:
+      e.form = EF_PAIRS;
+      e.m1 = 0x55555554u & nmask;  // odd-start half: targets the even bits >= 2
+      e.m2 = 0xAAAAAAAAu & nmask;  // even-start half: targets the odd bits
+      break;
+    case ENT_SCA: {
+      const int o = (r - 1) % n;
+      e.s = (n - 1 - o) % n;
+      if ((r - 1) & 1)
+        e.form = EF_RING_REV;
+      else
+        e.form = (o == 0) ? EF_WRAP_DIFF : EF_RING;  // offset 0 is the circular entangler
+      break;
+    }
+    default:
+      break;
+  }
+  return e;
+}
+
+// y = A x from the columns of A^-1 (Gauss-Jordan over GF(2); n <= 32).
+static uint32_t ent_forward(const EntMap &e, int n, uint32_t x) {
+  const uint32_t nmask = (n >= 32) ? 0xffffffffu : ((1u << n) - 1);
+  // rows[j]: bit i set when bit j of A^-1 e_i is set; aug[j]: the identity
+  uint32_t rows[32], aug[32];
+  for (int j = 0; j < n; ++j) {
+    rows[j] = 0;
+    aug[j] = 1u << j;
+  }
+  for (int i = 0; i < n; ++i) {
+    const uint32_t c = ent_inv(1u << i, nmask, e, n);
+    for (int j = 0; j < n; ++j)
+      if ((c >> j) & 1u) rows[j] |= 1u << i;
+  }
+  for (int col = 0; col < n; ++col) {
+    int piv = -1;
+    for (int j = col; j < n; ++j)
+      if ((rows[j] >> col) & 1u) {
+        piv = j;
+        break;
+      }
+    if (piv < 0) return 0;  // not invertible: cannot happen for a CNOT product
+    std::swap(rows[col], rows[piv]);
+    std::swap(aug[col], aug[piv]);
+    for (int j = 0; j < n; ++j)
+      if (j != col && ((rows[j] >> col) & 1u)) {
+        rows[j] ^= rows[col];
+        aug[j] ^= aug[col];
+      }
+  }
+  // rows is now the identity, aug = (A^-1)^-1 = A as rows: bit j of A x = parity(aug[j] & x)
+  uint32_t y = 0;
+  for (int j = 0; j < n; ++j) y |= (uint32_t)(__builtin_parity(aug[j] & x)) << j;
+  return y;
+}
+
+// Tile pairing of a gathering pass whose tiles are y bits [0, tb): over one tile
+// the x bits >= tb of x = A^-1 y flip along one vector k (or stay); the tile
+// t ^ (A(k << tb) >> tb) then reads the other halves of the same sectors.
+static uint32_t ent_pair_mask(const EntMap &e, int n, int tb) {
+  if (n <= tb) return 0;
+  const uint32_t nmask = (n >= 32) ? 0xffffffffu : ((1u << n) - 1);
+  uint32_t k = 0;
+  for (int i = 0; i < tb; ++i) {
+    const uint32_t v = ent_inv(1u << i, nmask, e, n) >> tb;
+    if (v == 0) continue;
+    if (k != 0 && v != k) return 0;  // more than one direction: keep the plain order
+    k = v;
+  }
+  if (k == 0) return 0;
+  const uint32_t pm = (ent_forward(e, n, k << tb) >> tb) & (uint32_t)((1ull << (n - tb)) - 1);
+  return pm == 1 ? 0 : pm;  // t ^ 1 is already the launch neighbour of t
+}
+
+// Layer-0 product-state tables of a gathering pass: x bits above tb must take
+// two values across a tile, told apart by one x bit kbit <= tb.
+bool ent_l0_split(const EntMap &e, int n, int tb, int *kbit, uint32_t *hflip) {
+  *kbit = tb;
+  *hflip = 0;
+  if (n <= tb + 1) return true;
+  const uint32_t nmask = (n >= 32) ? 0xffffffffu : ((1u << n) - 1);
+  const uint32_t him = nmask & ~((2u << tb) - 1u);
+  uint32_t h = 0, g = 0, col[32];
+  for (int i = 0; i < tb; ++i) {
+    col[i] = ent_inv(1u << i, nmask, e, n);
+    const uint32_t v = col[i] & him;
+    if (v == 0) continue;
+    if (h != 0 && v != h) return false;
+    h = v;
+    g |= 1u << i;
+  }
+  if (h == 0) return true;
+  for (int b = tb; b >= 0; --b) {
+    bool ok = true;
+    for (int i = 0; i < tb && ok; ++i) ok = (((col[i] >> b) & 1u) == ((g >> i) & 1u));
+    if (ok) {
+      *kbit = b;
+      *hflip = h;
+      return true;
+    }
+  }
+  return false;
+}
+
 static long long tiles_of(int n, int tb) { return 1LL << (n - tb); }
 
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
@@ -217,7 +337,6 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
     A.kind = kind;
     A.n = n;
     A.P = pl.P;
-    A.ent = ent;
     return A;
   };
   auto set_layout = [&](PassArgs &A, const LayerPass &lp) {
@@ -291,7 +410,9 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
       st.A.layer = r;
       if (j == 0) {
         st.A.load_mode = (r == 1) ? LD_L0_GATHER : LD_GATHER;
-        if (ent != ENT_FULL) st.A.flags |= F_PAIR_ORDER;
+        st.A.em = ent_map(ent, n, r);
+        st.A.pair_mask = ent_pair_mask(st.A.em, n, lp.tb);
+        if (r == 1) ent_l0_split(st.A.em, n, lp.tb, &st.A.l0_kbit, &st.A.l0_hflip);
       } else {
         st.A.load_mode = LD_PLAIN;
       }
@@ -367,7 +488,8 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
         st.out = out;
         if (j == 0) {
           st.A.store_mode = ST_SCATTER;
-          if (ent != ENT_FULL) st.A.flags |= F_PAIR_ORDER;
+          st.A.em = ent_map(ent, n, r);
+          st.A.pair_mask = ent_pair_mask(st.A.em, n, lp.tb);
         } else {
           st.A.store_mode = ST_PLAIN;
         }
@@ -849,8 +971,16 @@ int gvqe_ansatz_create(int n_qubits, int reps, int entangler, gvqe_ansatz *out) 
   if (n_qubits < 1 || n_qubits > GVQE_MAX_QUBITS)
     return fail(GVQE_EINVAL, "n_qubits=%d outside [1, %d]", n_qubits, GVQE_MAX_QUBITS);
   if (reps < 0 || reps > 64) return fail(GVQE_EINVAL, "reps=%d outside [0, 64]", reps);
-  if (entangler != GVQE_ENT_LINEAR && entangler != GVQE_ENT_CIRCULAR && entangler != GVQE_ENT_FULL)
-    return fail(GVQE_EINVAL, "entangler %d is not one of GVQE_ENT_LINEAR, _CIRCULAR, _FULL", entangler);
+  if (entangler < GVQE_ENT_LINEAR || entangler > GVQE_ENT_SCA)
+    return fail(GVQE_EINVAL, "entangler %d is not one of GVQE_ENT_LINEAR .. GVQE_ENT_SCA", entangler);
+  // the layer-1 gather builds the analytic product state from split tables
+  for (int tb = 10; tb <= 13; ++tb) {
+    int kbit;
+    uint32_t hflip;
+    if (!ent_l0_split(ent_map(entangler, n_qubits, 1), n_qubits, tb, &kbit, &hflip))
+      return fail(GVQE_EUNSUPPORTED, "entangler %d at n=%d: layer-1 gather tables do not split", entangler,
+                  n_qubits);
+  }
   gvqe_ansatz_s *a = new gvqe_ansatz_s();
   a->magic = MAGIC_ANSATZ;
   a->n = n_qubits;
@@ -1088,6 +1218,22 @@ int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int fl
   const double npass = passes;
   GV_CUDA(cudaMemcpyAsync(stats + 3, &npass, sizeof(double), cudaMemcpyHostToDevice, s));
   GV_CUDA(cudaStreamSynchronize(s));
+  return GVQE_OK;
+}
+
+int gvqe_entangler_inverse(int entangler, int n_qubits, int layer, const long long *y, long long *x,
+                           long long count) {
+  g_err.clear();
+  if (entangler < GVQE_ENT_LINEAR || entangler > GVQE_ENT_SCA) return fail(GVQE_EINVAL, "entangler %d", entangler);
+  if (n_qubits < 1 || n_qubits > GVQE_MAX_QUBITS) return fail(GVQE_EINVAL, "n_qubits=%d", n_qubits);
+  if (layer < 1) return fail(GVQE_EINVAL, "layer=%d < 1", layer);
+  if (count < 0 || (count > 0 && (!y || !x))) return fail(GVQE_EINVAL, "bad arrays");
+  const EntMap e = ent_map(entangler, n_qubits, layer);
+  const long long dim = 1LL << n_qubits;
+  const uint32_t nmask = (uint32_t)(dim - 1);
+  for (long long i = 0; i < count; ++i)
+    if (y[i] < 0 || y[i] >= dim) return fail(GVQE_EINVAL, "y[%lld]=%lld outside [0, 2^%d)", i, y[i], n_qubits);
+  for (long long i = 0; i < count; ++i) x[i] = (long long)ent_inv((uint32_t)y[i], nmask, e, n_qubits);
   return GVQE_OK;
 }
 

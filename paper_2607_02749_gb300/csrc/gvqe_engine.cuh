@@ -33,15 +33,57 @@ enum LoadMode : int {
   LD_L0 = 3,         // v = psi_0(y)
 };
 
-// Entanglers (Section IV-B).  As a map of basis indices each is GF(2)-linear,
-// y = A x; passes need x = A^-1 y (gather for psi, scatter for lambda):
-//   ENT_LINEAR   CX(0,1)..CX(n-2,n-1): y = prefix XOR of x,  x = y ^ (y << 1)
-//   ENT_CIRCULAR CX(n-1,0), then linear: x = C(y ^ (y << 1)), C: bit 0 ^= bit n-1
-//   ENT_FULL     CX(i,j) for all i < j, lexicographic: y = x ^ (x << 1), x = prefix XOR of y
-enum Entangler : int { ENT_LINEAR = 0, ENT_CIRCULAR = 1, ENT_FULL = 2 };
+// Entanglers (Section IV-B; Table 2 adds reverse linear, pairwise and SCA).  As
+// a map of basis indices each entangler layer is GF(2)-linear, y = A x; passes
+// need x = A^-1 y (gather for psi, scatter for lambda):
+//   ENT_LINEAR          CX(0,1)..CX(n-2,n-1): y = prefix XOR of x,  x = y ^ (y << 1)
+//   ENT_CIRCULAR        CX(n-1,0), then linear: x = C(y ^ (y << 1)), C: bit 0 ^= bit n-1
+//   ENT_FULL            CX(i,j) for all i < j, lexicographic: y = x ^ (x << 1), x = prefix XOR of y
+//   ENT_REVERSE_LINEAR  CX(n-2,n-1) down to CX(0,1): the same map as full
+//   ENT_PAIRWISE        CX(i,i+1) for even i, then odd i: A = O E, x = E(O(y)) with
+//                       E: odd bits ^= the bit below, O: even bits >= 2 ^= the bit below
+//   ENT_SCA             layer r, offset o = r - 1: the circular list rotated right by
+//                       o mod n, control and target swapped for odd o; in the frame
+//                       z_k = y_{s+k mod n}, s = n-1-o mod n, it is a ring of CX(k, k+1)
+//                       closed by CX(n-1, 0) (even o), or of CX(k+1, k) closed by
+//                       CX(0, n-1) (odd o)
+enum Entangler : int {
+  ENT_LINEAR = 0,
+  ENT_CIRCULAR = 1,
+  ENT_FULL = 2,
+  ENT_REVERSE_LINEAR = 3,
+  ENT_PAIRWISE = 4,
+  ENT_SCA = 5,
+};
 
-__host__ __device__ inline uint32_t ent_inv(uint32_t y, uint32_t nmask, int ent, int n) {
-  if (ent == ENT_FULL) {
+// The closed form of one layer's A^-1.
+enum EntForm : int {
+  EF_DIFF = 0,       // x = y ^ (y << 1)
+  EF_WRAP_DIFF = 1,  // EF_DIFF, then bit 0 ^= bit n-1
+  EF_PREFIX = 2,     // x_j = y_0 ^ ... ^ y_j
+  EF_PAIRS = 3,      // z = y ^ ((y << 1) & m1), x = z ^ ((z << 1) & m2)
+  EF_RING = 4,       // frame z = rot_s(y): z_0 ^= z_{n-1}, then EF_DIFF, rotated back
+  EF_RING_REV = 5,   // frame z = rot_s(y): z_{n-1} ^= z_0, then suffix XOR, rotated back
+};
+
+struct EntMap {
+  int form;
+  int s;            // EF_RING*: the frame's origin qubit
+  uint32_t m1, m2;  // EF_PAIRS: target masks of the odd-start and even-start halves
+};
+
+// x = y rotated so that bit s lands on bit 0, within n bits (0 <= s < n)
+__host__ __device__ inline uint32_t rot_down(uint32_t y, int s, int n, uint32_t nmask) {
+  return (uint32_t)((((uint64_t)y << (n - s)) | ((uint64_t)y >> s)) & nmask);
+}
+__host__ __device__ inline uint32_t rot_up(uint32_t y, int s, int n, uint32_t nmask) {
+  return (uint32_t)((((uint64_t)y << s) | ((uint64_t)y >> (n - s))) & nmask);
+}
+
+// One closed form, chosen at compile time (kernels hoist the choice out of loops).
+template <int F>
+__host__ __device__ inline uint32_t ent_inv_f(uint32_t y, uint32_t nmask, const EntMap &e, int n) {
+  if constexpr (F == EF_PREFIX) {
     uint32_t x = y;
     x ^= x << 1;
     x ^= x << 2;
@@ -49,9 +91,39 @@ __host__ __device__ inline uint32_t ent_inv(uint32_t y, uint32_t nmask, int ent,
     x ^= x << 8;
     x ^= x << 16;
     return x & nmask;
+  } else if constexpr (F == EF_WRAP_DIFF) {
+    const uint32_t z = (y ^ (y << 1)) & nmask;
+    return z ^ ((z >> (n - 1)) & 1u);
+  } else if constexpr (F == EF_PAIRS) {
+    const uint32_t z = y ^ ((y << 1) & e.m1);
+    return z ^ ((z << 1) & e.m2);
+  } else if constexpr (F == EF_RING) {
+    uint32_t z = rot_down(y, e.s, n, nmask);
+    z ^= (z >> (n - 1)) & 1u;
+    return rot_up((z ^ (z << 1)) & nmask, e.s, n, nmask);
+  } else if constexpr (F == EF_RING_REV) {
+    uint32_t z = rot_down(y, e.s, n, nmask);
+    z ^= (z & 1u) << (n - 1);
+    z ^= z >> 1;
+    z ^= z >> 2;
+    z ^= z >> 4;
+    z ^= z >> 8;
+    z ^= z >> 16;
+    return rot_up(z, e.s, n, nmask);
+  } else {
+    return (y ^ (y << 1)) & nmask;
   }
-  const uint32_t z = (y ^ (y << 1)) & nmask;
-  return ent == ENT_CIRCULAR ? z ^ ((z >> (n - 1)) & 1u) : z;
+}
+
+__host__ __device__ inline uint32_t ent_inv(uint32_t y, uint32_t nmask, const EntMap &e, int n) {
+  switch (e.form) {
+    case EF_WRAP_DIFF: return ent_inv_f<EF_WRAP_DIFF>(y, nmask, e, n);
+    case EF_PREFIX: return ent_inv_f<EF_PREFIX>(y, nmask, e, n);
+    case EF_PAIRS: return ent_inv_f<EF_PAIRS>(y, nmask, e, n);
+    case EF_RING: return ent_inv_f<EF_RING>(y, nmask, e, n);
+    case EF_RING_REV: return ent_inv_f<EF_RING_REV>(y, nmask, e, n);
+    default: return ent_inv_f<EF_DIFF>(y, nmask, e, n);
+  }
 }
 
 enum StoreMode : int {
@@ -63,7 +135,7 @@ enum StoreMode : int {
 enum PassFlags : int {
   F_ENERGY = 1,        // accumulate an energy partial per tile
   F_LAMBDA_INIT = 2,   // lambda = table * psi (diagonal H) instead of reading lambda
-  F_PAIR_ORDER = 4,    // launch tiles H and ~H next to each other (linear/circular gather and scatter passes)
+  // (4 unused: tile pairing is PassArgs::pair_mask)
   F_WRITE_LAMBDA = 8,  // K_LAMBDA_XY: write lambda
   F_ACCUM = 16,        // K_LAMBDA_XY: add onto lambda already written (group chunks)
 };
@@ -84,7 +156,10 @@ struct PassArgs {
   const void *table;        // diagonal table E(x) in amplitude precision
   const void *cs;           // (cos(theta/2), sin(theta/2)) per job and parameter
   int job0;                 // global index of job 0 of this launch (cs, minlayer)
-  int ent;                  // entangler (LD_GATHER, LD_L0_GATHER, ST_SCATTER)
+  EntMap em;                // this layer's entangler, x = A^-1 y (LD_GATHER, LD_L0_GATHER, ST_SCATTER)
+  uint32_t pair_mask;       // launch tiles t and t ^ pair_mask next to each other (0: in order)
+  int l0_kbit;              // LD_L0_GATHER: the x bit that tells the two values of x's bits above tb
+  uint32_t l0_hflip;        // ... and the bits above tb that flip with it
   double *part;             // partial sums [row][tile] for this pass, per-job stride part_stride
   long long part_stride;
   double *epart;            // energy partials [tile], per-job stride part_stride

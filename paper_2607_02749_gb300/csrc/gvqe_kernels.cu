@@ -33,7 +33,7 @@ __device__ __forceinline__ T product_state(long long x, const T2 *l0, int n) {
 
 template <typename T, typename T2>
 __device__ __forceinline__ T load_val(int mode, const T *__restrict__ in, long long y, long long nmask,
-                                      const T2 *l0, int n, int ent) {
+                                      const T2 *l0, int n, const EntMap &ent) {
   switch (mode) {
     case LD_GATHER:
       return in[ent_inv((uint32_t)y, (uint32_t)nmask, ent, n)];
@@ -48,7 +48,7 @@ __device__ __forceinline__ T load_val(int mode, const T *__restrict__ in, long l
 
 template <typename T>
 __device__ __forceinline__ void store_val(int mode, T *__restrict__ out, long long y, long long nmask, T v, int n,
-                                          int ent) {
+                                          const EntMap &ent) {
   if (mode == ST_PLAIN)
     out[y] = v;
   else if (mode == ST_SCATTER)
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
   for (int i = 0; i <= SMALL_MAXN; ++i) red[tid][i] = 0.0;
 
   if (A.kind == K_FWD || A.kind == K_WHT) {
-    for (int x = tid; x < N; x += SMALL_NT) sp[x] = load_val<T>(A.load_mode, in, x, nmask, l0cs, n, A.ent);
+    for (int x = tid; x < N; x += SMALL_NT) sp[x] = load_val<T>(A.load_mode, in, x, nmask, l0cs, n, A.em);
     __syncthreads();
     for (int b = 0; b < n; ++b) {
       if (!((gm >> b) & 1u)) continue;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
       __syncthreads();
     }
     for (int x = tid; x < N; x += SMALL_NT) {
-      store_val(A.store_mode, out, x, nmask, sp[x], n, A.ent);
+      store_val(A.store_mode, out, x, nmask, sp[x], n, A.em);
       if (A.flags & F_ENERGY) red[tid][0] += (double)(sp[x] * sp[x] * table[x]);
     }
   } else if (A.kind == K_BWD) {
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
       }
       __syncthreads();
     }
-    for (int x = tid; x < N; x += SMALL_NT) store_val(A.store_mode, out, x, nmask, sl[x], n, A.ent);
+    for (int x = tid; x < N; x += SMALL_NT) store_val(A.store_mode, out, x, nmask, sl[x], n, A.em);
   } else if (A.kind == K_GRAD_L0) {
     const bool init = (A.flags & F_LAMBDA_INIT) != 0;
     for (int x = tid; x < N; x += SMALL_NT) {

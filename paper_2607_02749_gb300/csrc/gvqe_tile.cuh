@@ -222,10 +222,16 @@ __device__ __forceinline__ int swz(int i) {
   return i ^ (((i >> 5) & 7) * CH);
 }
 
-__device__ __forceinline__ uint32_t tile_of_block(uint32_t bx, uint32_t tiles, bool pair) {
-  if (!pair || tiles < 2) return bx;
-  const uint32_t u = bx >> 1;
-  return (bx & 1) ? (u ^ (tiles - 1)) : u;
+// Launch order of tiles: block bx runs tile t; with pair_mask != 0 the tiles t and
+// t ^ pair_mask (whose gathers read the two halves of the same sectors) run next
+// to each other: block 2u + b runs tile u' ^ (b ? pair_mask : 0), u' = u with a 0
+// inserted at the highest bit of pair_mask.
+__device__ __forceinline__ uint32_t tile_of_block(uint32_t bx, uint32_t tiles, uint32_t pair_mask) {
+  if (pair_mask == 0 || tiles < 2) return bx;
+  const int hb = 31 - __clz(pair_mask);
+  const uint32_t v = bx >> 1;
+  const uint32_t u = ((v >> hb) << (hb + 1)) | (v & ((1u << hb) - 1u));
+  return (bx & 1) ? (u ^ pair_mask) : u;
 }
 
 __device__ __forceinline__ uint32_t tile_base(uint32_t t, int c, int a, int tb) {
@@ -507,11 +513,11 @@ __device__ __forceinline__ void for_L(const GIdx<TB, FULL> &gi, F &&f) {
 // x = A^-1 y of element 2m.  A^-1 is GF(2)-linear and the Gray-code walk flips
 // one bit of y per step, so x advances by one XOR with that bit's image.
 template <int TB, typename F>
-__device__ __forceinline__ void for_L_ent(const GIdx<TB, true> &gi, uint32_t nmask, int ent, int n, F &&f) {
+__device__ __forceinline__ void for_L_ent(const GIdx<TB, true> &gi, uint32_t nmask, const EntMap &em, int n, F &&f) {
   uint32_t d[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) d[j] = ent_inv(gi.SL[j], nmask, ent, n);
-  uint32_t x = ent_inv(gi.baseL, nmask, ent, n);
+  for (int j = 0; j < 4; ++j) d[j] = ent_inv(gi.SL[j], nmask, em, n);
+  uint32_t x = ent_inv(gi.baseL, nmask, em, n);
 #pragma unroll
   for (int k = 0; k < ROUND / 2; ++k) {
     const int m = gray(k);
@@ -542,18 +548,18 @@ __device__ __forceinline__ void load_gate_coeffs(const PassArgs &A, const T2 *cs
 // per tile: bits 0..6 (lo), bits 7..TB-1 (mid), bit TB together with the tile's bits above (hi).
 template <typename T, typename T2, int TB>
 struct L0Tables {
-  T lo[128];
-  T mid[128];
-  T hi[2];
-  // xbase: x of the tile's first element; hflip: the bits above TB that flip,
-  // together with bit TB, across the tile (0 unless the map flips them all)
-  __device__ __forceinline__ void build(const T2 *l0, int n, uint32_t xbase, uint32_t hflip, int tid,
+  T lo[128];   // x bits 0..6
+  T mid[128];  // x bits 7..TB
+  T hi[2];     // x bits above TB
+  // Across one tile x = xbase ^ (a linear image of the tile's y bits): the bits
+  // above TB take two values, told apart by x bit kbit, and differ in hflip.
+  __device__ __forceinline__ void build(const T2 *l0, int n, uint32_t xbase, int kbit, uint32_t hflip, int tid,
                                         int nthreads) {
     for (int m = tid; m < 256; m += nthreads) {
       const int hi7 = m >> 7, mm = m & 127;
       T p = T(1);
       const int q0 = hi7 ? 7 : 0;
-      const int q1 = hi7 ? TB : 7;
+      const int q1 = hi7 ? TB + 1 : 7;
       for (int q = q0; q < q1 && q < n; ++q) p *= ((mm >> (q - q0)) & 1) ? l0[q].y : l0[q].x;
       if (hi7)
         mid[mm] = p;
@@ -562,14 +568,13 @@ struct L0Tables {
     }
     if (tid < 2) {
       T p = T(1);
-      if (TB < n) p = tid ? l0[TB].y : l0[TB].x;
-      const uint32_t xh = xbase ^ ((((uint32_t)tid ^ (xbase >> TB)) & 1u) ? hflip : 0u);
+      const uint32_t xh = xbase ^ ((((uint32_t)tid ^ (xbase >> kbit)) & 1u) ? hflip : 0u);
       for (int q = TB + 1; q < n; ++q) p *= ((xh >> q) & 1) ? l0[q].y : l0[q].x;
       hi[tid] = p;
     }
   }
-  __device__ __forceinline__ T operator()(uint32_t x) const {
-    return lo[x & 127] * mid[(x >> 7) & ((1u << (TB - 7)) - 1)] * hi[(x >> TB) & 1];
+  __device__ __forceinline__ T operator()(uint32_t x, int kbit) const {
+    return lo[x & 127] * mid[(x >> 7) & ((1u << (TB - 6)) - 1)] * hi[(x >> kbit) & 1];
   }
 };
 
@@ -592,18 +597,18 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const SBase sb = sbase<TB, T>(tid);
-  const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
+  const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, A.pair_mask);
   const uint32_t tbase = tile_base(t, A.c, A.a, TB);
   const uint32_t nmask = (A.n >= 32) ? 0xffffffffu : ((1u << A.n) - 1);
-  const uint32_t d1 = ent_inv(1u, nmask, A.ent, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
+  const uint32_t d1 = ent_inv(1u, nmask, A.em, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   if (!WHT) {
     load_gate_coeffs(A, cs, gt.cs, tid);
   }
   if constexpr (L0) {
-    const uint32_t xbase = (LOAD == LD_L0_GATHER) ? ent_inv(tbase, nmask, A.ent, A.n) : tbase;
-    const uint32_t hflip = (LOAD == LD_L0_GATHER && A.ent == ENT_FULL) ? (nmask & ~((2u << TB) - 1u)) : 0u;
-    tab.build(cs, A.n, xbase, hflip, tid, NT);
+    const uint32_t xbase = (LOAD == LD_L0_GATHER) ? ent_inv(tbase, nmask, A.em, A.n) : tbase;
+    const uint32_t hflip = (LOAD == LD_L0_GATHER) ? A.l0_hflip : 0u;
+    tab.build(cs, A.n, xbase, A.l0_kbit, hflip, tid, NT);
   }
   __syncthreads();
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
@@ -616,14 +621,15 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   // round L: global -> registers (tile bits 6..9) -> gates -> shared.  The
   // inverse CX chain maps the pair (y, y + 1) to (x, x ^ 3), x = A^-1 y.
   if constexpr (FULL && (LOAD == LD_GATHER || LOAD == LD_L0_GATHER)) {
-    for_L_ent(gi, nmask, A.ent, A.n, [&](int m, uint32_t x) {
+    const int kbit = A.l0_kbit;
+    for_L_ent(gi, nmask, A.em, A.n, [&](int m, uint32_t x) {
       T2 v;
       if constexpr (LOAD == LD_GATHER) {
         v.x = __ldcg(in + x);
         v.y = __ldcg(in + (x ^ d1));
       } else {
-        v.x = tab(x);
-        v.y = tab(x ^ d1);
+        v.x = tab(x, kbit);
+        v.y = tab(x ^ d1, kbit);
       }
       r.set_pair(m, v);
     });
@@ -633,8 +639,8 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
       if constexpr (LOAD == LD_PLAIN) {
         v = __ldcg(reinterpret_cast<const T2 *>(in + y));
       } else {
-        v.x = tab(y);
-        v.y = tab(y + 1);
+        v.x = tab(y, TB);
+        v.y = tab(y + 1, TB);
       }
       r.set_pair(m, v);
     });
@@ -732,9 +738,9 @@ k_bwd(const PassArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const SBase sb = sbase<TB, T>(tid);
   const uint32_t tiles = (uint32_t)A.tiles;
-  const bool pair = (A.flags & F_PAIR_ORDER) != 0;
+  const uint32_t pair = A.pair_mask;
   const uint32_t nmask = (1u << A.n) - 1;
-  const uint32_t d1 = ent_inv(1u, nmask, A.ent, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
+  const uint32_t d1 = ent_inv(1u, nmask, A.em, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   load_gate_coeffs(A, cs, gt.cs, tid);
   if (sizeof(T) == 4) gt.pack(tid);
@@ -831,17 +837,33 @@ k_bwd(const PassArgs A) {
     }
     lds_L(sl, sb, lam);
     round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
-    // (the scatter computes each x from y: measured faster here than the XOR walk)
-    for_L(gi, [&](int m, uint32_t y) {
-      const T2 v = lam.pair(m);
-      if constexpr (FULL) {
-        const uint32_t x = ent_inv(y, nmask, A.ent, A.n);
+    // (the short closed forms compute each x from y: measured faster here than
+    // the XOR walk, which the other forms take)
+    if (!FULL || A.em.form <= EF_PREFIX) {
+      const EntMap em = A.em;
+      for_L(gi, [&](int m, uint32_t y) {
+        const T2 v = lam.pair(m);
+        if constexpr (FULL) {
+          uint32_t x;
+          if (em.form == EF_PREFIX) {
+            x = ent_inv_f<EF_PREFIX>(y, nmask, em, A.n);
+          } else {
+            x = ent_inv_f<EF_DIFF>(y, nmask, em, A.n);
+            if (em.form == EF_WRAP_DIFF) x ^= (x >> (A.n - 1)) & 1u;
+          }
+          out[x] = v.x;
+          out[x ^ d1] = v.y;
+        } else {
+          *reinterpret_cast<T2 *>(out + y) = v;
+        }
+      });
+    } else if constexpr (FULL) {
+      for_L_ent(gi, nmask, A.em, A.n, [&](int m, uint32_t x) {
+        const T2 v = lam.pair(m);
         out[x] = v.x;
         out[x ^ d1] = v.y;
-      } else {
-        *reinterpret_cast<T2 *>(out + y) = v;
-      }
-    });
+      });
+    }
     // gred / ered of this tile were written before the round-H barriers
     if (tid < TB && ((gm >> tid) & 1u)) {
       double g = 0.0;
@@ -887,10 +909,10 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.layer < A.minlayer[A.job0 + job]) return;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const SBase sb = sbase<TB, T>(tid);
-  const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, (A.flags & F_PAIR_ORDER) != 0);
+  const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, A.pair_mask);
   const uint32_t tbase = tile_base(t, A.c, A.a, TB);
   const uint32_t nmask = (1u << A.n) - 1;
-  const uint32_t d1 = ent_inv(1u, nmask, A.ent, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
+  const uint32_t d1 = ent_inv(1u, nmask, A.em, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   load_gate_coeffs(A, cs, gt.cs, tid);
   if (sizeof(T) == 4) gt.pack(tid);
@@ -949,7 +971,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   lds_L(sl, sb, lam);
   round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
   if constexpr (FULL) {
-    for_L_ent(gi, nmask, A.ent, A.n, [&](int m, uint32_t x) {
+    for_L_ent(gi, nmask, A.em, A.n, [&](int m, uint32_t x) {
       const T2 v = lam.pair(m);
       out[x] = v.x;
       out[x ^ d1] = v.y;

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2607_02749_gb300 import _lib
@@ -71,7 +72,7 @@ def test_size_checks():
     with pytest.raises(_lib.GvqeError) as e:
         _lib.gvqe_ansatz_create(4, 1, entangler=7)
     assert e.value.code == _lib.GVQE_EINVAL
-    for ent in (_lib.GVQE_ENT_LINEAR, _lib.GVQE_ENT_CIRCULAR, _lib.GVQE_ENT_FULL):
+    for ent in ALL_ENTS:
         _lib.gvqe_destroy(_lib.gvqe_ansatz_create(4, 1, entangler=ent))
     with pytest.raises(_lib.GvqeError):
         _lib.gvqe_hamiltonian_create(3, ["ZZ"], [1.0])  # string shorter than n is caught by length
@@ -146,3 +147,36 @@ def test_workload_generators_shapes():
         assert 14 <= inst.n_qubits <= 20 and 2 <= inst.reps <= 4
         frac = inst.mask.mean()
         assert 0.25 <= frac <= 0.65
+
+
+ALL_ENTS = (_lib.GVQE_ENT_LINEAR, _lib.GVQE_ENT_CIRCULAR, _lib.GVQE_ENT_FULL, _lib.GVQE_ENT_REVERSE_LINEAR,
+            _lib.GVQE_ENT_PAIRWISE, _lib.GVQE_ENT_SCA)
+
+
+def test_every_entangler_creates_at_every_size():
+    # creation checks that the layer-1 gather of every tile size splits its product-state tables
+    for ent in ALL_ENTS:
+        for n in range(1, _lib.GVQE_MAX_QUBITS + 1):
+            _lib.gvqe_destroy(_lib.gvqe_ansatz_create(n, 3, entangler=ent))
+
+
+def test_entangler_inverse_matches_the_oracle_maps():
+    """The library's closed forms of A^-1 (the ones its gathers and scatters use)
+    invert the oracle's closed-form entangler maps, for every layer offset."""
+    from oracle import closed_form
+
+    rng = np.random.default_rng(3)
+    for ent in ALL_ENTS:
+        for n in (1, 2, 3, 5, 8, 13, 14, 21, 30):
+            for layer in (1, 2, 3, 4, n + 1, n + 2):
+                xs = rng.integers(0, 1 << n, size=64) if n > 6 else np.arange(1 << n)
+                ys = np.array([closed_form.entangler_map(int(x), n, ent, layer) for x in xs])
+                got = _lib.gvqe_entangler_inverse(ent, n, layer, ys)
+                assert np.array_equal(got, xs), (ent, n, layer)
+
+
+def test_entangler_inverse_rejects_bad_arguments():
+    for args in ((6, 4, 1, [0]), (0, 0, 1, [0]), (0, 4, 0, [0]), (0, 4, 1, [16]), (0, 4, 1, [-1])):
+        with pytest.raises(_lib.GvqeError) as e:
+            _lib.gvqe_entangler_inverse(*args)
+        assert e.value.code == _lib.GVQE_EINVAL

@@ -1,4 +1,5 @@
-"""Circular and full entanglers (Section IV-B) on the GPU against the oracle:
+"""Circular, full, reverse-linear, pairwise and SCA entanglers (Section IV-B,
+Table 2) on the GPU against the oracle:
 energies and adjoint gradients (FP32 and FP64, whole-register and tile paths,
 diagonal and X/Y Hamiltonians), the parameter-shift comparator, readout, the
 persistent batch with mixed entanglers, and a full-size run against FP64."""
@@ -17,7 +18,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 import paper_2607_02749_gb300 as gv  # noqa: E402
 
-ENTS = [gv.GVQE_ENT_CIRCULAR, gv.GVQE_ENT_FULL]
+ENTS = [gv.GVQE_ENT_CIRCULAR, gv.GVQE_ENT_FULL, gv.GVQE_ENT_REVERSE_LINEAR, gv.GVQE_ENT_PAIRWISE, gv.GVQE_ENT_SCA]
 
 
 def _ref(n, reps, th, ham, ent):
@@ -91,8 +92,9 @@ def test_readout_with_entangler(ent):
 
 
 def test_batch_with_mixed_entanglers():
-    insts = wl.cluster_batch(6, qubit_range=(13, 16), reps_range=(1, 3), terms_per_qubit=20)
-    ents = [gv.GVQE_ENT_LINEAR, gv.GVQE_ENT_CIRCULAR, gv.GVQE_ENT_FULL] * 2
+    insts = wl.cluster_batch(12, qubit_range=(13, 16), reps_range=(1, 3), terms_per_qubit=20)
+    ents = [gv.GVQE_ENT_LINEAR] + ENTS
+    ents = ents * 2
     ans = [gv.Ansatz(i.n_qubits, i.reps, entangler=e) for i, e in zip(insts, ents)]
     hams = [gv.Hamiltonian.from_workload(i.ham) for i in insts]
     b = gv.Batch(ans, hams, fp64=True)
@@ -119,3 +121,19 @@ def test_fullsize_fp32_against_fp64(ent):
     assert abs(e32.item() - e64.item()) <= 2e-5 * scale
     g32, g64 = g32.cpu().numpy()[0], g64.cpu().numpy()[0]
     assert np.linalg.norm(g32 - g64) <= 1e-4 * max(np.linalg.norm(g64), 1e-3 * scale)
+
+
+@pytest.mark.parametrize("ent", [gv.GVQE_ENT_SCA, gv.GVQE_ENT_PAIRWISE])
+def test_deep_circuit_offsets(ent):
+    # SCA cycles its offset through every residue mod n (n = 11, reps = 13);
+    # FP64 against the oracle, tile passes at 10 tile bits (two strided passes)
+    n, reps = 11, 13
+    ham = wl.pauli_hamiltonian(n, 120, seed=8)
+    th = wl.thetas(n, reps, 1, seed=9)
+    a = gv.Ansatz(n, reps, entangler=ent)
+    a.set_tile_bits(10)
+    h = gv.Hamiltonian.from_workload(ham)
+    e, g = gv.energy_grad(a, h, torch.as_tensor(th, device="cuda"), fp64=True)
+    er, gr = _ref(n, reps, th[0], ham, ent)
+    assert abs(e.item() - er) <= 1e-10 * ham.abs_sum()
+    assert np.max(np.abs(g.cpu().numpy()[0] - gr)) <= 1e-9 * ham.abs_sum()
