@@ -229,7 +229,7 @@ def cluster_leg(steps: int):
 
 
 def readout_leg(n: int, reps: int, ham, steps: int):
-    """Readout of the benchmark's state (Section IV-E, Section V-A): most probable
+    """Readout of the benchmark's state (Section IV-F, Section V-A): most probable
     bitstring, 8192 shots and CVaR at alpha = 0.2, FP32, one parameter vector."""
     import numpy as np
     import torch

@@ -188,9 +188,9 @@ int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, 
                        double *energies, int flags, void *stream);
 
 /*
- * gvqe_readout -- read out the prepared state |psi(theta)> (Section IV-E:
+ * gvqe_readout -- read out the prepared state |psi(theta)> (Section IV-F:
  * sample the final state, take the most probable bitstring; Section V-A:
- * 8192 shots, seed 0, and the CVaR-alpha objective of Section II).
+ * 8192 shots, seed 0, and the CVaR-alpha objective of Section III).
  * p(x) = |psi(x)|^2 over the 2^n computational basis states, total = sum_x p(x)
  * (1 up to rounding; shots and CVaR use p / total).
  *   a, h:     handles with equal n; h is only read when alpha > 0 and may be

@@ -5,7 +5,9 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
 
 ``gvqe_oracle.c`` is the plain complex128 gate-by-gate simulator (Section IV-B,
 Eq. 4, 6, 7, 13); ``dense.py`` is an independent dense-matrix model for tiny
-registers and ``closed_form.py`` holds closed forms used as pins.
+registers and ``closed_form.py`` holds closed forms used as pins;
+``readout.py`` is the readout of Section IV-F and ``graph.py`` the interaction
+graph and Louvain partitioning of Section IV-C.
 """
 from __future__ import annotations
 

@@ -3,9 +3,9 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
 ``bench.py`` may import this module.
 
-Section IV-E: the final state |psi(theta*)> is sampled over the computational
+Section IV-F: the final state |psi(theta*)> is sampled over the computational
 basis states and the bitstring of highest probability is taken.  Section V-A:
-8192 shots, seed 0.  Section II (with Section V-A's alpha = 0.2): CVaR-alpha,
+8192 shots, seed 0.  Section III (with Section V-A's alpha = 0.2): CVaR-alpha,
 the average energy of the lowest-alpha fraction of measurement outcomes.
 
 The definitions used here:

@@ -118,7 +118,7 @@ class Readout:
 
 def readout(ansatz: Ansatz, ham: Optional[Hamiltonian], theta, alpha: float = 0.2, shots: int = 8192,
             seed: Optional[int] = 0, uniforms=None, fp64: bool = False, stream=None) -> Readout:
-    """Read out |psi(theta)> (Section IV-E; 8192 shots with seed 0 and CVaR
+    """Read out |psi(theta)> (Section IV-F; 8192 shots with seed 0 and CVaR
     alpha = 0.2 as in Section V-A).  The shots use `uniforms` (CUDA float64, in
     [0, 1)) or, when None, `shots` draws of numpy's PCG64(seed) made on the host.
     alpha = 0 skips the CVaR (ham may then be None)."""

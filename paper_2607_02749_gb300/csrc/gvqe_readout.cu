@@ -1,6 +1,6 @@
-// gvqe_readout.cu -- readout of a prepared state (Section IV-E, Section V-A):
+// gvqe_readout.cu -- readout of a prepared state (Section IV-F, Section V-A):
 // probabilities p(x) = |psi(x)|^2, the most probable bitstring, inverse-CDF
-// shot sampling, and the CVaR-alpha of the outcome energy E(x) (Section II).
+// shot sampling, and the CVaR-alpha of the outcome energy E(x) (Section III).
 //
 // Everything is summed in FP64 in fixed orders.  The CVaR search narrows the
 // alpha-quantile of E with histograms whose bin masses are integer (p scaled
