@@ -249,6 +249,40 @@ int gvqe_plan_describe(int n_qubits, int reps, int flags, int tile_bits, char *b
 int gvqe_entangler_inverse(int entangler, int n_qubits, int layer, const long long *y, long long *x,
                            long long count);
 
+/*
+ * Host-only Hamiltonian partitioning (Section IV-C; no GPU needed).
+ *
+ * gvqe_interaction_graph -- the weighted qubit interaction graph of Eq. 9:
+ * w[i*n + j] = sum of |c_k| over the terms whose letters on qubits i and j
+ * (i != j) are both non-identity; w[i*n + i] = 0.
+ *   n_qubits: 1..GVQE_GRAPH_MAX_NODES.  pauli / coeffs as for
+ *   gvqe_hamiltonian_create (host; duplicates are simply added).
+ *   w: host, n_qubits^2 doubles (written).
+ * Errors: GVQE_EINVAL (sizes, NULL, a letter outside IXYZ, a non-finite c).
+ *
+ * gvqe_partition -- blocks of qubits by the Louvain method: local moving of
+ * nodes to the neighbouring community of largest modularity gain, then
+ * aggregation, until a level moves nothing; maximising Eq. 10 with a
+ * resolution gamma (gamma = 1 is Eq. 10 as printed):
+ *   Q = 1/(2m) sum_ij [w_ij - gamma k_i k_j / (2m)] delta(c_i, c_j).
+ * Then blocks smaller than min_block are merged: the smallest block (lowest
+ * label on ties) joins the block it shares the most weight with (lowest label
+ * on ties), or, sharing none, the smallest other block, until every block has
+ * min_block qubits or one block is left.  Deterministic: nodes are visited in
+ * ascending order, a node moves only when the best gain beats staying by more
+ * than a relative 1e-12, near-equal gains go to the lowest community label.
+ *   w: host, n x n, symmetric, finite, >= 0, zero diagonal.
+ *   resolution: gamma >= 0.  min_block: S_min >= 1.
+ *   block_of: host, n ints (written): block of node i, blocks numbered in
+ *   order of their lowest node.  n_blocks, modularity: written if not NULL
+ *   (Q of the final blocks at this gamma).
+ * Errors: GVQE_EINVAL.
+ */
+#define GVQE_GRAPH_MAX_NODES 1024
+int gvqe_interaction_graph(int n_qubits, int n_terms, const char *pauli, const double *coeffs, double *w);
+int gvqe_partition(int n, const double *w, double resolution, int min_block, int *block_of, int *n_blocks,
+                   double *modularity);
+
 /* gvqe_hamiltonian_stats -- counts after parsing: diagonal strings, X-mask
  * groups, grouped strings, dropped odd-Y strings (any pointer may be NULL). */
 int gvqe_hamiltonian_stats(gvqe_hamiltonian h, int *n_diag, int *n_groups, int *n_grouped,

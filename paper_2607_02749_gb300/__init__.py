@@ -15,8 +15,8 @@ from ._lib import (GVQE_ENT_CIRCULAR, GVQE_ENT_FULL, GVQE_ENT_LINEAR, GVQE_ENT_P
                    GVQE_ENT_SCA, GVQE_FP32, GVQE_FP64, GVQE_GRAD_ADJOINT, GVQE_GRAD_PARAM_SHIFT,
                    GVQE_OPT_TILE_BITS, GvqeError, gvqe_ansatz_create, gvqe_ansatz_set_option, gvqe_batch_create,
                    gvqe_batch_run, gvqe_destroy, gvqe_energy, gvqe_energy_grad, gvqe_hamiltonian_create,
-                   gvqe_entangler_inverse, gvqe_hamiltonian_stats, gvqe_last_error, gvqe_plan_describe,
-                   gvqe_readout, gvqe_version)
+                   gvqe_entangler_inverse, gvqe_hamiltonian_stats, gvqe_interaction_graph, gvqe_last_error,
+                   gvqe_partition, gvqe_plan_describe, gvqe_readout, gvqe_version)
 
 __all__ = [
     "Hamiltonian", "Ansatz", "Batch", "GvqeEnergy", "energy", "energy_grad", "readout", "Readout", "GvqeError",
@@ -25,6 +25,7 @@ __all__ = [
     "gvqe_hamiltonian_create", "gvqe_ansatz_create", "gvqe_ansatz_set_option", "gvqe_energy",
     "gvqe_energy_grad", "gvqe_batch_create", "gvqe_batch_run", "gvqe_destroy", "gvqe_last_error",
     "gvqe_plan_describe", "gvqe_hamiltonian_stats", "gvqe_readout", "gvqe_version", "gvqe_entangler_inverse",
+    "gvqe_interaction_graph", "gvqe_partition",
 ]
 
 

@@ -75,6 +75,8 @@ _SIGS = {
     "gvqe_destroy": [_VP],
     "gvqe_plan_describe": [_I, _I, _I, _I, ctypes.c_char_p, _I],
     "gvqe_entangler_inverse": [_I, _I, _I, _VP, _VP, ctypes.c_longlong],
+    "gvqe_interaction_graph": [_I, _I, ctypes.c_char_p, _VP, _VP],
+    "gvqe_partition": [_I, _VP, ctypes.c_double, _I, _VP, _VP, _VP],
     "gvqe_hamiltonian_stats": [_VP, _VP, _VP, _VP, _VP],
     "gvqe_version": [],
     "gvqe_profile_enable": [_I],
@@ -261,6 +263,40 @@ def gvqe_entangler_inverse(entangler: int, n_qubits: int, layer: int, y) -> "np.
     _check(load().gvqe_entangler_inverse(entangler, n_qubits, layer, ya.ctypes.data, xa.ctypes.data, ya.size),
            "gvqe_entangler_inverse")
     return xa
+
+
+def gvqe_interaction_graph(n_qubits: int, strings, coeffs) -> "np.ndarray":
+    """Eq. 9 weighted interaction graph (host only, no GPU): n x n, symmetric."""
+    import numpy as np
+
+    strings = list(strings)
+    for s in strings:
+        if len(s) != n_qubits:
+            raise GvqeError(GVQE_EINVAL, "gvqe_interaction_graph", f"string {s!r} does not have {n_qubits} letters")
+    flat = "".join(strings).encode("ascii")
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64).reshape(-1))
+    if c.size != len(strings):
+        raise GvqeError(GVQE_EINVAL, "gvqe_interaction_graph", "one coefficient per string")
+    w = np.zeros((n_qubits, n_qubits))
+    _check(load().gvqe_interaction_graph(n_qubits, len(strings), flat, c.ctypes.data, w.ctypes.data),
+           "gvqe_interaction_graph")
+    return w
+
+
+def gvqe_partition(w, resolution: float = 1.0, min_block: int = 1):
+    """Louvain blocks of the graph w (Section IV-C, Eq. 10): (block_of, n_blocks, Q)."""
+    import numpy as np
+
+    wa = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    n = wa.shape[0]
+    if wa.shape != (n, n):
+        raise GvqeError(GVQE_EINVAL, "gvqe_partition", "w must be square")
+    lab = np.zeros(n, dtype=np.int32)
+    nb = ctypes.c_int()
+    q = ctypes.c_double()
+    _check(load().gvqe_partition(n, wa.ctypes.data, float(resolution), int(min_block), lab.ctypes.data,
+                                 ctypes.byref(nb), ctypes.byref(q)), "gvqe_partition")
+    return [int(v) for v in lab], nb.value, q.value
 
 
 def gvqe_hamiltonian_stats(ham: int) -> dict:

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgvqe.so")
-SOURCES = ["gvqe_api.cu", "gvqe_kernels.cu", "gvqe_static.cu", "gvqe_batch.cu", "gvqe_grad_l0.cu", "gvqe_readout.cu"]
+SOURCES = ["gvqe_api.cu", "gvqe_kernels.cu", "gvqe_static.cu", "gvqe_batch.cu", "gvqe_grad_l0.cu", "gvqe_readout.cu",
+           "gvqe_graph.cu"]
 # gvqe_inst.cu is compiled once per (amplitude type, tile bits) pair
 INSTANCES = [("float", tb) for tb in (10, 11, 12, 13)] + [("double", tb) for tb in (10, 11, 12)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
