@@ -56,6 +56,8 @@ def parse_args():
                     help="run only the readout leg on the workload and print its JSON object")
     ap.add_argument("--only-entanglers", action="store_true",
                     help="run only the entangler leg on the workload and print its JSON object")
+    ap.add_argument("--only-driver", action="store_true",
+                    help="run only the Graph-VQE driver leg (one epoch at n=20) and print its JSON object")
     return ap.parse_args()
 
 
@@ -296,6 +298,31 @@ def entangler_leg(n: int, reps: int, ham, steps: int):
     return out
 
 
+def driver_leg(n: int = 20, reps: int = 4, n_terms: int = 2000):
+    """One Graph-VQE epoch (Section IV-C to IV-E) on a sequence-local synthetic H:
+    Louvain blocks, lock-step block L-BFGS-B with batched GPU evaluations, global
+    refinement.  Reports wall time and evaluation throughput inside the loop."""
+    from paper_2607_02749_gb300 import workloads as wl
+    from paper_2607_02749_gb300.driver import GraphVQE, GraphVQEConfig
+
+    ham = wl.chain_z_hamiltonian(n, n_terms, seed=0)
+    cfg = GraphVQEConfig(reps=reps, max_epochs=1, block_maxiter=60, global_maxiter=30)
+    g = GraphVQE(ham, cfg)
+    th0 = wl.thetas(n, reps, 1, seed=1)[0]
+    g.energy(th0)  # plans and workspaces
+    t0 = time.perf_counter()
+    r = g.run(th0)
+    dt = time.perf_counter() - t0
+    ev = g.evaluator
+    out = {"workload": f"chain_z n={n} reps={reps} terms={n_terms}", "wall_s": dt, "blocks": r["n_blocks"],
+           "modularity": r["modularity"], "E_start": r["E_start"], "E": r["E"],
+           "evaluations": r["evaluations"], "gpu_calls": ev.calls, "gpu_rows": ev.rows,
+           "rows_per_s": ev.rows / dt, "block_batches": getattr(g, "block_batches", None),
+           "timing": "wall clock around GraphVQE.run (host L-BFGS-B, H2D/D2H per call included)"}
+    ev.close()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -350,6 +377,10 @@ def run_gvqe(args):
         if rank == 0:
             print(json.dumps({"workload": args.workload, "readout": readout_leg(n, reps, ham, max(1, args.steps))}),
                   flush=True)
+        return 0
+    if args.only_driver:
+        if rank == 0:
+            print(json.dumps({"driver": driver_leg()}), flush=True)
         return 0
     if args.only_entanglers:
         if rank == 0:
@@ -489,6 +520,7 @@ def run_gvqe(args):
         out["cluster_batch"] = cluster_leg(args.steps)
         out["readout"] = readout_leg(n, reps, ham, max(1, min(args.steps, 3)))
         out["entanglers"] = entangler_leg(n, reps, ham, max(1, min(args.steps, 3)))
+        out["driver"] = driver_leg()
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:

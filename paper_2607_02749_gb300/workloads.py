@@ -81,6 +81,27 @@ def z_hamiltonian(n: int, n_terms: int, seed: int = 0, contact_fraction: float =
     return Hamiltonian(n, strings, coeffs)
 
 
+def chain_z_hamiltonian(n: int, n_terms: int, seed: int = 0, reach: int = 4, contact_fraction: float = 0.75,
+                        max_weight: int = 4) -> Hamiltonian:
+    """Z-only Hamiltonian with the sequence locality of Section IV-C: qubits
+    2i, 2i+1 encode turn i, and most strings act on a few nearby turns.  Each
+    string's support is drawn inside a window of `reach` consecutive qubits
+    starting at a uniform position; coefficients as in z_hamiltonian."""
+    rng = _rng(seed)
+    n_contact = int(round(contact_fraction * n_terms))
+    reach = max(1, min(reach, n))
+    strings: List[str] = []
+    coeffs = np.empty(n_terms, dtype=np.float64)
+    for k in range(n_terms):
+        start = int(rng.integers(0, n - reach + 1))
+        letters = ["I"] * n
+        for q in _support(rng, reach, max_weight):
+            letters[start + int(q)] = "Z"
+        strings.append("".join(letters))
+        coeffs[k] = rng.uniform(-7.5, -0.1) if k < n_contact else 10.0
+    return Hamiltonian(n, strings, coeffs)
+
+
 def pauli_hamiltonian(n: int, n_terms: int, seed: int = 0, xy_fraction: float = 0.4,
                       max_weight: int = 4) -> Hamiltonian:
     """General Pauli-sum Hamiltonian with X/Y letters on about xy_fraction of the strings.
