@@ -82,6 +82,27 @@ def test_energy_and_adjoint_gradient_diagonal(n, reps, tb, batch, fp64):
     _check(e, g, e_ref, g_ref, scale, fp64, "energy_grad")
 
 
+@pytest.mark.parametrize("n,reps,tb", [(12, 2, 0), (14, 3, 0), (17, 2, 0), (16, 2, 10), (21, 1, 12)])
+@pytest.mark.parametrize("fp64", [True, False])
+def test_angles_at_and_near_pi(n, reps, tb, fp64):
+    """Rotations whose cos(theta/2) is tiny or zero (theta at or near +-pi, and
+    beyond the principal range) run the backward pass's two half-angle steps;
+    several per pass, mixed with ordinary angles."""
+    if fp64 and tb > 12:
+        pytest.skip("FP64 tiles are at most 2^12 amplitudes")
+    rng = np.random.default_rng(n + 17 * reps)
+    th = wl.thetas(n, reps, 2, seed=5 + n)
+    special = np.array([np.pi, -np.pi, np.pi - 1e-3, -np.pi + 3e-3, 3 * np.pi, np.pi + 1e-9, 2.9, -3.1])
+    pick = rng.uniform(size=th.shape) < 0.4
+    th[pick] = rng.choice(special, size=int(pick.sum()))
+    ham = wl.z_hamiltonian(n, 6 * n + 5, seed=2 * n)
+    e_ref, g_ref = _oracle_eg(n, reps, th, ham)
+    a = gv.Ansatz(n, reps, tile_bits=tb)
+    h = gv.Hamiltonian.from_workload(ham)
+    e, g = gv.energy_grad(a, h, _dev(th), fp64=fp64)
+    _check(e.cpu().numpy(), g.cpu().numpy(), e_ref, g_ref, ham.abs_sum(), fp64, "near pi")
+
+
 @pytest.mark.parametrize("n,reps,tb", [(6, 2, 0), (10, 1, 0), (12, 2, 0), (14, 2, 10), (16, 1, 12), (9, 0, 0), (13, 0, 10)])
 @pytest.mark.parametrize("fp64", [True, False])
 def test_energy_and_gradient_with_xy_strings(n, reps, tb, fp64):
