@@ -59,6 +59,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         lib.oracle_set_threads.argtypes = [i]
         lib.oracle_set_entangler.argtypes = [i]
         lib.oracle_set_entangler.restype = i
+        lib.oracle_set_gates.argtypes = [i]
+        lib.oracle_set_gates.restype = i
         for f in ("oracle_state", "oracle_apply_hamiltonian", "oracle_energy",
                   "oracle_energy_grad", "oracle_param_shift_grad", "oracle_partial_work",
                   "oracle_sweep_times"):
@@ -128,15 +130,46 @@ class entangler:
         return False
 
 
+GATES_RY, GATES_RY_RZ = 1, 2
+_gates = GATES_RY
+
+
+class gates:
+    """Context manager selecting the oracle's rotation layer: GATES_RY (default,
+    P = n (D+1)) or GATES_RY_RZ, the full EfficientSU2 layer of Eq. 8 (RY then RZ
+    on every qubit, P = 2 n (D+1); layer r's RY angles at 2 r n + q, RZ angles at
+    2 r n + n + q)."""
+
+    def __init__(self, g: int, lib: Optional[ctypes.CDLL] = None):
+        self.g = int(g)
+        self.lib = lib
+
+    def __enter__(self):
+        global _gates
+        _check((self.lib or load()).oracle_set_gates(self.g), "set_gates")
+        _gates = self.g
+        return self
+
+    def __exit__(self, *exc):
+        global _gates
+        (self.lib or load()).oracle_set_gates(GATES_RY)
+        _gates = GATES_RY
+        return False
+
+
+def n_params(n: int, reps: int) -> int:
+    return _gates * n * (reps + 1)
+
+
 def max_threads() -> int:
     return int(load().oracle_max_threads())
 
 
 def state(n: int, reps: int, theta, lib: Optional[ctypes.CDLL] = None) -> np.ndarray:
-    """|psi(theta)> as complex128 [2^n] (Section IV-B ansatz, RY+CX)."""
+    """|psi(theta)> as complex128 [2^n] (Section IV-B ansatz)."""
     lib = lib or load()
     th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
-    assert th.size == n * (reps + 1)
+    assert th.size == n_params(n, reps)
     out = np.empty(2 << n, dtype=np.float64)
     _check(lib.oracle_state(n, reps, _ptr(th), _ptr(out)), "state")
     return out.view(np.complex128)

@@ -5,7 +5,8 @@ IV-B, Eq. 7) and of Pauli sums (Eq. 6) without simulating a state vector:
 
 * product_state_*:  reps = 0.  The state is a product of single-qubit states
   cos(t/2)|0> + sin(t/2)|1>, so <P> factorises: I -> 1, Z -> cos t, X -> sin t,
-  Y -> 0.  Cost O(M n).
+  Y -> 0.  Cost O(M n).  su2_product_state_energy: the same with RZ(p) after
+  each RY(t): X -> sin t cos p, Y -> sin t sin p.
 * heisenberg_reps1_energy: reps = 1 with Z-only strings.  RY(t)^dagger Z RY(t)
   = cos t Z - sin t X; conjugating X^a Z^c by the CNOT-chain permutation
   |x> -> |A x> (A = prefix XOR) gives X^(A^-1 a) Z^(A^T c) with no phase; the
@@ -44,6 +45,26 @@ def product_state_energy(theta0: Sequence[float], strings, coeffs) -> float:
                 v *= math.sin(th[q])
             else:  # Y
                 v = 0.0
+        tot += v
+    return tot
+
+
+def su2_product_state_energy(theta_y: Sequence[float], theta_z: Sequence[float], strings, coeffs) -> float:
+    """reps = 0 with the full EfficientSU2 layer (RY then RZ): each qubit's Bloch
+    vector (sin t cos p, sin t sin p, cos t) for t = theta_y, p = theta_z, so
+    I -> 1, X -> sin t cos p, Y -> sin t sin p, Z -> cos t."""
+    ty = np.asarray(theta_y, dtype=np.float64)
+    tz = np.asarray(theta_z, dtype=np.float64)
+    tot = 0.0
+    for s, c in zip(strings, coeffs):
+        v = float(c)
+        for q, ch in _letters(s):
+            if ch == "Z":
+                v *= math.cos(ty[q])
+            elif ch == "X":
+                v *= math.sin(ty[q]) * math.cos(tz[q])
+            else:
+                v *= math.sin(ty[q]) * math.sin(tz[q])
         tot += v
     return tot
 

@@ -38,6 +38,11 @@ def ry(theta: float) -> np.ndarray:
     return np.array([[c, -s], [s, c]], dtype=np.complex128)
 
 
+def rz(theta: float) -> np.ndarray:
+    """The RZ of the EfficientSU2 layer (Eq. 8): exp(-i theta Z / 2)."""
+    return np.array([[np.exp(-0.5j * theta), 0], [0, np.exp(0.5j * theta)]], dtype=np.complex128)
+
+
 def embed(ops: Dict[int, np.ndarray], n: int) -> np.ndarray:
     """Kronecker product with ops[q] on qubit q and identity elsewhere."""
     factors = [ops.get(q, I2) for q in reversed(range(n))]
@@ -87,30 +92,37 @@ def entangler_pairs(n: int, ent: int = 0, layer: int = 1):
     return pairs
 
 
-def circuit(n: int, reps: int, theta, ent: int = 0) -> np.ndarray:
-    """U(theta): RY layer, then reps x [entangler; RY layer] as explicit matrices."""
+def circuit(n: int, reps: int, theta, ent: int = 0, gates: int = 1) -> np.ndarray:
+    """U(theta): rotation layer, then reps x [entangler; rotation layer] as explicit
+    matrices.  A rotation layer is RY on every qubit, then (gates = 2) RZ on every
+    qubit; layer r's angles start at r * gates * n."""
     assert n <= MAX_QUBITS
     th = np.asarray(theta, dtype=np.float64).reshape(-1)
+    assert th.size == gates * n * (reps + 1)
     u = np.eye(1 << n, dtype=np.complex128)
     for r in range(reps + 1):
         if r > 0:
             for c, t in entangler_pairs(n, ent, r):
                 u = cnot(c, t, n) @ u
+        base = r * gates * n
         for q in range(n):
-            u = embed({q: ry(th[r * n + q])}, n) @ u
+            u = embed({q: ry(th[base + q])}, n) @ u
+        if gates == 2:
+            for q in range(n):
+                u = embed({q: rz(th[base + n + q])}, n) @ u
     return u
 
 
-def state(n: int, reps: int, theta, ent: int = 0) -> np.ndarray:
-    return circuit(n, reps, theta, ent)[:, 0]
+def state(n: int, reps: int, theta, ent: int = 0, gates: int = 1) -> np.ndarray:
+    return circuit(n, reps, theta, ent, gates)[:, 0]
 
 
-def energy(n: int, reps: int, theta, strings, coeffs, ent: int = 0) -> float:
-    psi = state(n, reps, theta, ent)
+def energy(n: int, reps: int, theta, strings, coeffs, ent: int = 0, gates: int = 1) -> float:
+    psi = state(n, reps, theta, ent, gates)
     return float(np.real(np.vdot(psi, hamiltonian(strings, coeffs) @ psi)))
 
 
-def param_shift_grad(n: int, reps: int, theta, strings, coeffs, ent: int = 0) -> np.ndarray:
+def param_shift_grad(n: int, reps: int, theta, strings, coeffs, ent: int = 0, gates: int = 1) -> np.ndarray:
     th = np.asarray(theta, dtype=np.float64).reshape(-1)
     h = hamiltonian(strings, coeffs)
     g = np.zeros_like(th)
@@ -119,7 +131,7 @@ def param_shift_grad(n: int, reps: int, theta, strings, coeffs, ent: int = 0) ->
         for sh in (+math.pi / 2, -math.pi / 2):
             t = th.copy()
             t[p] += sh
-            psi = circuit(n, reps, t, ent)[:, 0]
+            psi = circuit(n, reps, t, ent, gates)[:, 0]
             vals.append(float(np.real(np.vdot(psi, h @ psi))))
         g[p] = 0.5 * (vals[0] - vals[1])
     return g

@@ -8,9 +8,10 @@
  *
  * What it computes (all in complex128, accumulation in double):
  *   - the ansatz state |psi(theta)> = U(theta)|0...0> of Section IV-B: an
- *     initial RY rotation layer followed by D repetitions of [linear CNOT
- *     chain, RY rotation layer] (Eq. 7 gate matrix, Eq. 8 parameter count
- *     with the RY-only gate set, flattened index p = r*n + q);
+ *     initial rotation layer followed by D repetitions of [CNOT entangler,
+ *     rotation layer] (Eq. 7 gate matrix, Eq. 8 parameter count); a rotation
+ *     layer is RY on every qubit (flattened index p = r*n + q) or, with gate
+ *     set 2, the full EfficientSU2 layer RY then RZ on every qubit;
  *   - the Pauli-sum Hamiltonian applied term by term, H = sum_k c_k P_k
  *     (Eq. 6), each P_k applied letter by letter with the standard matrices;
  *   - the energy E = <psi|H|psi> (Eq. 4);
@@ -75,6 +76,31 @@ static void apply_ry(cplx *psi, int n, int q, double theta) {
         psi[x] = c * a - s * b;
         psi[x | bit] = s * a + c * b;
     }
+}
+
+/* RZ(theta) on qubit q, the RZ of Eq. 7-8's EfficientSU2 layers:
+ * diag(exp(-i theta/2), exp(+i theta/2)). */
+static void apply_rz(cplx *psi, int n, int q, double theta) {
+    const cplx p0 = cos(0.5 * theta) - I * sin(0.5 * theta);
+    const cplx p1 = cos(0.5 * theta) + I * sin(0.5 * theta);
+    const int64_t dim = (int64_t)1 << n;
+    const int64_t bit = (int64_t)1 << q;
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < dim; ++x) psi[x] *= (x & bit) ? p1 : p0;
+}
+
+/*
+ * Gate set of a rotation layer.  1: RY on every qubit (P = n (D+1)).  2: the
+ * full EfficientSU2 layer of Eq. 8, RY on every qubit and then RZ on every
+ * qubit (P = 2 n (D+1)); layer r's RY angles are theta[2 r n + q] and its RZ
+ * angles theta[2 r n + n + q].  A process-wide setting of this test oracle.
+ */
+static int g_gates = 1;
+
+int oracle_set_gates(int gates) {
+    if (gates != 1 && gates != 2) return ORACLE_EINVAL;
+    g_gates = gates;
+    return ORACLE_OK;
 }
 
 /* CNOT with control qubit `ctl` and target qubit `tgt`: |x> -> |x xor (x_ctl << tgt)>. */
@@ -180,14 +206,22 @@ static void apply_entangler_inverse(cplx *psi, int n, int layer) {
 }
 
 /* U(theta)|0> for the RY+CX ansatz (Section IV-B, Eq. 7-8). */
+/* Rotation layer r: RY on every qubit, then (gate set 2) RZ on every qubit. */
+static void apply_rotation_layer(cplx *psi, int n, int r, const double *theta) {
+    const int base = r * g_gates * n;
+    for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[base + q]);
+    if (g_gates == 2)
+        for (int q = 0; q < n; ++q) apply_rz(psi, n, q, theta[base + n + q]);
+}
+
 static void prepare_state(cplx *psi, int n, int reps, const double *theta) {
     const int64_t dim = (int64_t)1 << n;
     memset(psi, 0, sizeof(cplx) * (size_t)dim);
     psi[0] = 1.0;
-    for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[q]);
+    apply_rotation_layer(psi, n, 0, theta);
     for (int r = 1; r <= reps; ++r) {
         apply_entangler(psi, n, r);
-        for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[r * n + q]);
+        apply_rotation_layer(psi, n, r, theta);
     }
 }
 
@@ -271,6 +305,19 @@ static double im_lam_y_psi(const cplx *lam, const cplx *psi, int n, int q) {
     return acc;
 }
 
+/* Im <lam| Z_q |psi>, the RZ derivative 2 Re <lam| (-i/2) Z_q |psi>. */
+static double im_lam_z_psi(const cplx *lam, const cplx *psi, int n, int q) {
+    const int64_t dim = (int64_t)1 << n;
+    const int64_t bit = (int64_t)1 << q;
+    double acc = 0.0;
+#pragma omp parallel for reduction(+ : acc) schedule(static)
+    for (int64_t x = 0; x < dim; ++x) {
+        const cplx zpsi = (x & bit) ? -psi[x] : psi[x];
+        acc += cimag(conj(lam[x]) * zpsi);
+    }
+    return acc;
+}
+
 static int check_args(int n, int reps) {
     if (n < 1 || n > ORACLE_MAX_QUBITS || reps < 0) return ORACLE_EINVAL;
     return ORACLE_OK;
@@ -318,8 +365,9 @@ int oracle_energy(int n, int reps, const double *theta, int n_terms, const char 
  * Energy and its full gradient by the adjoint method: lam = H psi at the end of
  * the circuit, then the gates are walked in reverse order.  At each RY gate the
  * derivative is 2 Re <lam| dU/dtheta |psi> = Im <lam| Y_q |psi> (RY = exp(-i t Y/2)),
- * evaluated with psi and lam taken right after that gate; then RY(-theta) is
- * applied to both.  CNOTs are their own inverse.
+ * at each RZ gate Im <lam| Z_q |psi>, evaluated with psi and lam taken right
+ * after that gate; then the gate's inverse is applied to both.  CNOTs are their
+ * own inverse.
  */
 int oracle_energy_grad(int n, int reps, const double *theta, int n_terms, const char *pauli,
                        const double *coeffs, double *E, double *grad) {
@@ -333,8 +381,17 @@ int oracle_energy_grad(int n, int reps, const double *theta, int n_terms, const 
     if (rc) { free(psi); free(lam); return rc; }
     *E = creal(inner(psi, lam, n));
     for (int r = reps; r >= 0; --r) {
+        const int base = r * g_gates * n;
+        if (g_gates == 2) {
+            for (int q = n - 1; q >= 0; --q) {
+                const int p = base + n + q;
+                grad[p] = im_lam_z_psi(lam, psi, n, q);
+                apply_rz(psi, n, q, -theta[p]);
+                apply_rz(lam, n, q, -theta[p]);
+            }
+        }
         for (int q = n - 1; q >= 0; --q) {
-            const int p = r * n + q;
+            const int p = base + q;
             grad[p] = im_lam_y_psi(lam, psi, n, q);
             apply_ry(psi, n, q, -theta[p]);
             apply_ry(lam, n, q, -theta[p]);
@@ -358,7 +415,7 @@ int oracle_param_shift_grad(int n, int reps, const double *theta, int n_terms,
                             const char *pauli, const double *coeffs,
                             const unsigned char *mask, double *grad) {
     if (check_args(n, reps) || !theta || !grad || n_terms < 0) return ORACLE_EINVAL;
-    const int P = n * (reps + 1);
+    const int P = g_gates * n * (reps + 1);
     double *shifted = (double *)malloc(sizeof(double) * (size_t)P);
     if (!shifted) return ORACLE_ENOMEM;
     const double half_pi = 2.0 * atan(1.0);

@@ -43,11 +43,23 @@ MUTANTS = {
     "sca_offset_from_layer": ("const int o = (layer - 1) % k;", "const int o = layer % k;"),
     "adjoint_wrong_layer_entangler": ("apply_entangler_inverse(psi, n, r);\n            apply_entangler_inverse(lam, n, r);",
                                       "apply_entangler_inverse(psi, n, 1);\n            apply_entangler_inverse(lam, n, 1);"),
+    "rz_phase_sign": ("const cplx p0 = cos(0.5 * theta) - I * sin(0.5 * theta);",
+                      "const cplx p0 = cos(0.5 * theta) + I * sin(0.5 * theta);"),
+    "rz_before_ry": ("    for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[base + q]);\n    if (g_gates == 2)\n"
+                     "        for (int q = 0; q < n; ++q) apply_rz(psi, n, q, theta[base + n + q]);",
+                     "    if (g_gates == 2)\n        for (int q = 0; q < n; ++q) apply_rz(psi, n, q, theta[base + n + q]);\n"
+                     "    for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[base + q]);"),
+    "rz_grad_sign": ("const cplx zpsi = (x & bit) ? -psi[x] : psi[x];", "const cplx zpsi = (x & bit) ? psi[x] : -psi[x];"),
+    "rz_param_index": ("const int p = base + n + q;", "const int p = base + q;"),
+    "rz_not_unapplied": ("apply_rz(lam, n, q, -theta[p]);", "(void)0;"),
     "y_phase": ("phase *= b ? -I : I;", "phase *= b ? I : -I;"),
     "z_sign_dropped": ("if (b) phase = -phase;", "(void)b;"),
     "last_term_dropped": ("for (int k = 0; k < n_terms; ++k) {", "for (int k = 0; k + 1 < n_terms; ++k) {"),
     "grad_sign": ("acc += cimag(conj(lam[x]) * ypsi);", "acc -= cimag(conj(lam[x]) * ypsi);"),
-    "theta_index": ("apply_ry(psi, n, q, theta[r * n + q]);", "apply_ry(psi, n, q, theta[q * (reps + 1) + r]);"),
+    "theta_index": ("for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[base + q]);",
+                    "for (int q = 0; q < n; ++q) apply_ry(psi, n, q, theta[base + n - 1 - q]);"),
+    "layer_stride_ignores_rz": ("const int base = r * g_gates * n;\n    for (int q = 0; q < n; ++q) apply_ry",
+                                "const int base = r * n;\n    for (int q = 0; q < n; ++q) apply_ry"),
     "shift_half": ("grad[p] = 0.5 * (ep - em);", "grad[p] = (ep - em);"),
     "unapply_skipped": ("apply_ry(lam, n, q, -theta[p]);", "(void)0;"),
 }
@@ -100,6 +112,16 @@ def _pins_pass(lib) -> bool:
                 e, g = oracle.energy_grad(n, reps, th, strings, coeffs, lib=lib)
                 if np.max(np.abs(g - dense.param_shift_grad(n, reps, th, strings, coeffs, ent))) > 1e-11 * scale:
                     return False
+        # the full EfficientSU2 layer (RY then RZ): the dense model and its gradient
+        th2 = np.random.default_rng(9).uniform(-3, 3, 2 * n * (reps + 1))
+        with oracle.gates(oracle.GATES_RY_RZ, lib=lib):
+            if np.max(np.abs(oracle.state(n, reps, th2, lib=lib) - dense.state(n, reps, th2, 0, 2))) > 1e-12:
+                return False
+            e, g = oracle.energy_grad(n, reps, th2, strings, coeffs, lib=lib)
+        if abs(e - dense.energy(n, reps, th2, strings, coeffs, 0, 2)) > 1e-12 * scale:
+            return False
+        if np.max(np.abs(g - dense.param_shift_grad(n, reps, th2, strings, coeffs, 0, 2))) > 1e-11 * scale:
+            return False
         return True
     except RuntimeError:
         return False

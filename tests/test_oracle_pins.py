@@ -293,3 +293,57 @@ def test_sca_is_the_shifted_circular_entangler_alternating_direction():
             if o % 2:
                 want = hn @ want @ hn
             assert np.allclose(_entangler_unitary(n, oracle.ENT_SCA, layer), want, atol=1e-12), (n, layer)
+
+
+# ---------------------------------------------------------- EfficientSU2 --
+# The full rotation layer of Eq. 8: RY then RZ on every qubit, P = 2 n (D+1).
+
+@pytest.mark.parametrize("ent", [oracle.ENT_LINEAR, oracle.ENT_CIRCULAR, oracle.ENT_SCA])
+def test_su2_oracle_matches_the_dense_model(ent):
+    rng = np.random.default_rng(31 + ent)
+    for n, reps in ((1, 2), (2, 1), (3, 2), (5, 1), (6, 2)):
+        th = rng.uniform(-np.pi, np.pi, 2 * n * (reps + 1))
+        ham = wl.pauli_hamiltonian(n, 12, seed=n + 3)
+        with oracle.entangler(ent), oracle.gates(oracle.GATES_RY_RZ):
+            psi = oracle.state(n, reps, th)
+            e, g = oracle.energy_grad(n, reps, th, ham.strings, ham.coeffs)
+            gs = oracle.param_shift_grad(n, reps, th, ham.strings, ham.coeffs)
+        assert np.max(np.abs(psi - dense.state(n, reps, th, ent, 2))) < 1e-12
+        scale = ham.abs_sum()
+        assert abs(e - dense.energy(n, reps, th, ham.strings, ham.coeffs, ent, 2)) < 1e-12 * scale
+        gd = dense.param_shift_grad(n, reps, th, ham.strings, ham.coeffs, ent, 2)
+        assert np.max(np.abs(g - gd)) < 1e-11 * scale
+        assert np.max(np.abs(gs - g)) < 1e-11 * scale  # Eq. 13 is exact for RZ too
+
+
+def test_su2_product_state_closed_form():
+    rng = np.random.default_rng(5)
+    for n in (1, 4, 9, 12):
+        ty, tz = rng.uniform(-np.pi, np.pi, n), rng.uniform(-np.pi, np.pi, n)
+        ham = wl.pauli_hamiltonian(n, 40, seed=n)
+        with oracle.gates(oracle.GATES_RY_RZ):
+            e = oracle.energy(n, 0, np.concatenate([ty, tz]), ham.strings, ham.coeffs)
+        want = closed_form.su2_product_state_energy(ty, tz, ham.strings, ham.coeffs)
+        assert e == pytest.approx(want, abs=1e-12 * ham.abs_sum())
+
+
+def test_su2_with_zero_rz_angles_is_the_ry_circuit_and_phases_keep_basis_states():
+    n, reps = 6, 2
+    rng = np.random.default_rng(8)
+    ty = rng.uniform(-np.pi, np.pi, (reps + 1, n))
+    th2 = np.concatenate([np.concatenate([ty[r], np.zeros(n)]) for r in range(reps + 1)])
+    with oracle.gates(oracle.GATES_RY_RZ):
+        psi2 = oracle.state(n, reps, th2)
+    assert np.max(np.abs(psi2 - oracle.state(n, reps, ty.reshape(-1)))) < 1e-13
+    # RY angles in {0, pi} with arbitrary RZ angles: a basis state up to a phase
+    flips = rng.integers(0, 2, size=(reps + 1, n))
+    th3 = np.concatenate([np.concatenate([np.pi * flips[r], rng.uniform(-3, 3, n)]) for r in range(reps + 1)])
+    with oracle.gates(oracle.GATES_RY_RZ):
+        psi3 = oracle.state(n, reps, th3)
+    y = closed_form.basis_state_index(n, reps, flips.reshape(-1))
+    assert abs(abs(psi3[y]) - 1.0) < 1e-12
+    ham = wl.z_hamiltonian(n, 30, seed=1)
+    with oracle.gates(oracle.GATES_RY_RZ):
+        e = oracle.energy(n, reps, th3, ham.strings, ham.coeffs)
+    want = closed_form.basis_state_energy(n, reps, flips.reshape(-1), ham.strings, ham.coeffs)
+    assert e == pytest.approx(want, abs=1e-12 * ham.abs_sum())
