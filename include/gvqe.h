@@ -7,12 +7,14 @@
  *   - Qubit q is bit q of the basis index x (little-endian).
  *   - A Pauli string has one character per qubit over {I, X, Y, Z};
  *     character i acts on qubit i.
- *   - The ansatz (Section IV-B, Eq. 7): an initial RY layer on every qubit,
- *     then `reps` repetitions of [entangler, RY layer].  The linear entangler
- *     is CX(0,1), CX(1,2), ..., CX(n-2,n-1) in that order (others below).
+ *   - The ansatz (Section IV-B, Eq. 7): an initial rotation layer, then
+ *     `reps` repetitions of [entangler, rotation layer].  The linear entangler
+ *     is CX(0,1), CX(1,2), ..., CX(n-2,n-1) in that order (others below).  A
+ *     rotation layer is RY on every qubit (default) or the full EfficientSU2
+ *     layer RY then RZ on every qubit (GVQE_OPT_GATES, below).
  *   - Parameters are flattened layer-major: theta[p] with p = r*n + q is the
  *     RY angle of layer r (0..reps) on qubit q; P = n*(reps+1) (Eq. 8 for the
- *     RY-only gate set).
+ *     RY-only gate set; see GVQE_GATES_RY_RZ for the full one).
  *   - RY(t) = [[cos t/2, -sin t/2], [sin t/2, cos t/2]] (Eq. 7).
  *
  * Ownership: *_create copies every input; the caller owns the parameter,
@@ -67,6 +69,19 @@ extern "C" {
 
 /* options for gvqe_ansatz_set_option */
 #define GVQE_OPT_TILE_BITS 1 /* log2 amplitudes per on-chip tile, 10..13 (FP64: 10..12); 0 = auto (13 FP32, 12 FP64) */
+#define GVQE_OPT_GATES 2     /* rotation layer: GVQE_GATES_RY (default) or GVQE_GATES_RY_RZ */
+
+/* gate sets of a rotation layer (Eq. 8).
+ * RY:    RY on every qubit; P = n (reps+1), theta[r*n + q]; real amplitudes.
+ * RY_RZ: the full EfficientSU2 layer, RY on every qubit, then RZ on every
+ *        qubit, RZ(t) = diag(exp(-i t/2), exp(+i t/2)); P = 2 n (reps+1), layer
+ *        r's RY angle of qubit q at theta[2 r n + q] and its RZ angle at
+ *        theta[2 r n + n + q].  Complex amplitudes (twice the memory and
+ *        bandwidth); gvqe_energy and gvqe_energy_grad with a diagonal (I/Z)
+ *        Hamiltonian and n >= 9; readout, batches and gvqe_energy_static
+ *        return GVQE_EUNSUPPORTED. */
+#define GVQE_GATES_RY 1
+#define GVQE_GATES_RY_RZ 2
 
 #define GVQE_MAX_QUBITS 30
 

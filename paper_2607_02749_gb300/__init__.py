@@ -11,7 +11,7 @@ from __future__ import annotations
 from typing import Optional, Sequence
 
 from . import _lib
-from ._lib import (GVQE_ENT_CIRCULAR, GVQE_ENT_FULL, GVQE_ENT_LINEAR, GVQE_ENT_PAIRWISE, GVQE_ENT_REVERSE_LINEAR,
+from ._lib import (GVQE_GATES_RY, GVQE_GATES_RY_RZ, GVQE_ENT_CIRCULAR, GVQE_ENT_FULL, GVQE_ENT_LINEAR, GVQE_ENT_PAIRWISE, GVQE_ENT_REVERSE_LINEAR,
                    GVQE_ENT_SCA, GVQE_FP32, GVQE_FP64, GVQE_GRAD_ADJOINT, GVQE_GRAD_PARAM_SHIFT,
                    GVQE_OPT_TILE_BITS, GvqeError, gvqe_ansatz_create, gvqe_ansatz_set_option, gvqe_batch_create,
                    gvqe_batch_run, gvqe_destroy, gvqe_energy, gvqe_energy_grad, gvqe_hamiltonian_create,
@@ -22,6 +22,7 @@ __all__ = [
     "Hamiltonian", "Ansatz", "Batch", "GvqeEnergy", "energy", "energy_grad", "readout", "Readout", "GvqeError",
     "GVQE_FP32", "GVQE_FP64", "GVQE_GRAD_ADJOINT", "GVQE_GRAD_PARAM_SHIFT", "GVQE_ENT_LINEAR",
     "GVQE_ENT_CIRCULAR", "GVQE_ENT_FULL", "GVQE_ENT_REVERSE_LINEAR", "GVQE_ENT_PAIRWISE", "GVQE_ENT_SCA",
+    "GVQE_GATES_RY", "GVQE_GATES_RY_RZ",
     "gvqe_hamiltonian_create", "gvqe_ansatz_create", "gvqe_ansatz_set_option", "gvqe_energy",
     "gvqe_energy_grad", "gvqe_batch_create", "gvqe_batch_run", "gvqe_destroy", "gvqe_last_error",
     "gvqe_plan_describe", "gvqe_hamiltonian_stats", "gvqe_readout", "gvqe_version", "gvqe_entangler_inverse",
@@ -60,16 +61,22 @@ class Hamiltonian(_Handle):
 
 
 class Ansatz(_Handle):
-    """RY layer + reps x [entangler, RY layer] (Section IV-B); P = n (reps + 1).
+    """Rotation layer + reps x [entangler, rotation layer] (Section IV-B); a rotation
+    layer is RY on every qubit (gates=GVQE_GATES_RY, P = n (reps + 1)) or the full
+    EfficientSU2 layer RY then RZ (gates=GVQE_GATES_RY_RZ, P = 2 n (reps + 1)).
     entangler: GVQE_ENT_LINEAR (default), GVQE_ENT_CIRCULAR, GVQE_ENT_FULL, GVQE_ENT_REVERSE_LINEAR,
     GVQE_ENT_PAIRWISE or GVQE_ENT_SCA (Section IV-B, Table 2)."""
 
-    def __init__(self, n_qubits: int, reps: int, entangler: int = GVQE_ENT_LINEAR, tile_bits: int = 0):
+    def __init__(self, n_qubits: int, reps: int, entangler: int = GVQE_ENT_LINEAR, tile_bits: int = 0,
+                 gates: int = _lib.GVQE_GATES_RY):
         self.n_qubits = n_qubits
         self.reps = reps
         self.entangler = entangler
-        self.n_params = n_qubits * (reps + 1)
+        self.gates = gates
+        self.n_params = gates * n_qubits * (reps + 1)
         self.handle = gvqe_ansatz_create(n_qubits, reps, entangler)
+        if gates != _lib.GVQE_GATES_RY:
+            gvqe_ansatz_set_option(self.handle, _lib.GVQE_OPT_GATES, gates)
         if tile_bits:
             gvqe_ansatz_set_option(self.handle, GVQE_OPT_TILE_BITS, tile_bits)
 

@@ -32,6 +32,9 @@ GVQE_ENT_REVERSE_LINEAR = 3
 GVQE_ENT_PAIRWISE = 4
 GVQE_ENT_SCA = 5
 GVQE_OPT_TILE_BITS = 1
+GVQE_OPT_GATES = 2
+GVQE_GATES_RY = 1
+GVQE_GATES_RY_RZ = 2
 GVQE_MAX_QUBITS = 30
 GVQE_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 GVQE_PROF_FWD = 0

@@ -317,9 +317,141 @@ bool ent_l0_split(const EntMap &e, int n, int tb, int *kbit, uint32_t *hflip) {
 
 static long long tiles_of(int n, int tb) { return 1LL << (n - tb); }
 
+// The complex path (full EfficientSU2 layers, RY then RZ on every qubit): the
+// state is 2^(n+1) reals with the re/im channel as index bit 0, so the passes
+// run over nb = n + 1 index bits with no gate on bit 0.  Layer 0 starts from
+// |0...0> as ordinary passes (no analytic product state), every layer's passes
+// store their outputs for the backward sweep, and each backward pass writes
+// RY partial rows [0, tb) and RZ rows [tb, 2 tb).  Diagonal H only.
+static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_grad, int ent) {
+  Plan pl;
+  const int nb = n + 1;
+  pl.n = nb;
+  pl.reps = reps;
+  pl.prec = prec;
+  pl.P = 2 * n * (reps + 1);
+  pl.lp = layer_passes(nb, prec, tile_bits);
+  for (LayerPass &lp : pl.lp) lp.gmask &= ~1u;  // index bit 0 is the channel
+  const int p = (int)pl.lp.size();
+  const long long S = 1LL << nb;
+  pl.state_elems = S;
+  long long poff = 0;
+  auto base_args = [&](int kind, const LayerPass &lp, int r) {
+    PassArgs A;
+    memset(&A, 0, sizeof(A));
+    A.kind = kind;
+    A.n = nb;
+    A.P = pl.P;
+    A.pstride = 2 * n;
+    A.qoff = 1;
+    A.zoff = n;
+    A.flags = F_COMPLEX;
+    A.tb = lp.tb;
+    A.c = lp.c;
+    A.a = lp.a;
+    A.tiles = tiles_of(nb, lp.tb);
+    A.gate_mask = lp.gmask;
+    A.layer = r;
+    return A;
+  };
+  int nbuf = 0;
+  const int first_state = nbuf;
+  int PP0 = -1, PP1 = -1, LAM0 = -1, LAM1 = -1;
+  if (want_grad) {
+    nbuf += (reps + 1) * p;
+    LAM0 = nbuf++;
+    LAM1 = nbuf++;
+  } else {
+    PP0 = nbuf++;
+    PP1 = nbuf++;
+  }
+  pl.n_bufs = nbuf;
+  pl.n_states = want_grad ? (reps + 1) * p : 0;
+  // ---------------- forward
+  int cur = -1;
+  for (int r = 0; r <= reps; ++r) {
+    for (int j = 0; j < p; ++j) {
+      const LayerPass &lp = pl.lp[j];
+      PassStep st;
+      st.A = base_args(K_FWD, lp, r);
+      if (j == 0) {
+        st.A.load_mode = (r == 0) ? LD_ZERO : LD_GATHER;
+        if (r > 0) {
+          st.A.em = ent_map(ent, n, r);
+          st.A.em.sh = 1;
+          st.A.pair_mask = ent_pair_mask(st.A.em, nb, lp.tb);
+        }
+      } else {
+        st.A.load_mode = LD_PLAIN;
+      }
+      st.in = (r == 0 && j == 0) ? -1 : cur;
+      const int out = want_grad ? first_state + r * p + j : ((j == 0) ? (cur == PP0 ? PP1 : PP0) : cur);
+      st.A.store_mode = ST_PLAIN;
+      if (r == reps && j == p - 1 && !want_grad) {
+        st.A.store_mode = ST_NONE;
+        st.A.flags |= F_ENERGY;
+        st.epart_region = poff;
+        pl.dir.push_back({poff, (int)st.A.tiles, -1});
+        poff += st.A.tiles;
+      }
+      st.out = out;
+      pl.steps.push_back(st);
+      cur = out;
+    }
+  }
+  if (!want_grad) {
+    pl.part_stride = poff;
+    return pl;
+  }
+  // ---------------- backward (every layer, layer 0 included)
+  int lam_cur = -1;
+  for (int r = reps; r >= 0; --r) {
+    for (int j = p - 1; j >= 0; --j) {
+      const LayerPass &lp = pl.lp[j];
+      PassStep st;
+      st.A = base_args(K_BWD, lp, r);
+      st.in = first_state + r * p + j;
+      if (r == reps && j == p - 1) {
+        st.A.flags |= F_LAMBDA_INIT | F_ENERGY;
+        st.epart_region = poff;
+        pl.dir.push_back({poff, (int)st.A.tiles, -1});
+        poff += st.A.tiles;
+        st.lam = -1;
+      } else {
+        st.lam = lam_cur;
+      }
+      const int out = (lam_cur == LAM0) ? LAM1 : LAM0;
+      st.out = out;
+      if (j == 0 && r > 0) {
+        st.A.store_mode = ST_SCATTER;
+        st.A.em = ent_map(ent, n, r);
+        st.A.em.sh = 1;
+        st.A.pair_mask = ent_pair_mask(st.A.em, nb, lp.tb);
+      } else {
+        st.A.store_mode = (j == 0) ? ST_NONE : ST_PLAIN;  // nothing runs before layer 0
+      }
+      st.part_region = poff;
+      for (int i = 0; i < lp.tb; ++i) {
+        if (!((lp.gmask >> i) & 1u)) continue;
+        const int q = qubit_of(lp, i) - 1;
+        const int py = r * 2 * n + q, pz = r * 2 * n + n + q;
+        pl.param_dir[py] = {poff + (long long)i * st.A.tiles, (int)st.A.tiles, py};
+        pl.param_dir[pz] = {poff + (long long)(lp.tb + i) * st.A.tiles, (int)st.A.tiles, pz};
+      }
+      poff += 2LL * lp.tb * st.A.tiles;
+      pl.steps.push_back(st);
+      lam_cur = out;
+    }
+  }
+  pl.part_stride = poff;
+  for (auto &kv : pl.param_dir) pl.dir.push_back(kv.second);
+  return pl;
+}
+
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0,
-                bool state_only, int ent) {
+                bool state_only, int ent, int gates) {
+  if (gates == 2) return build_plan_su2(n, reps, prec, tile_bits, want_grad, ent);
   Plan pl;
   pl.n = n;
   pl.reps = reps;
@@ -337,6 +469,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
     A.kind = kind;
     A.n = n;
     A.P = pl.P;
+    A.pstride = n;
     return A;
   };
   auto set_layout = [&](PassArgs &A, const LayerPass &lp) {
@@ -678,8 +811,16 @@ static int build_table64(gvqe_hamiltonian_s *h, cudaStream_t s) {
   return GVQE_OK;
 }
 
-static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s) {
+static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s, bool cplx = false) {
   GV_TRY(build_table64(h, s));
+  if (cplx && !h->TC[prec].ptr) {
+    const size_t S = (size_t)1 << h->n;
+    GV_TRY(h->TC[prec].reserve(S * 2 * (prec ? 8 : 4)));
+    GV_CUDA(launch_expand_table((const double *)h->T64.ptr, h->TC[prec].ptr, (long long)S, prec, s));
+    GV_CUDA(cudaStreamSynchronize(s));
+    return GVQE_OK;
+  }
+  if (cplx) return GVQE_OK;
   if (!prec && !h->T32.ptr) {
     const size_t S = (size_t)1 << h->n;
     GV_TRY(h->T32.reserve(S * 4));
@@ -713,10 +854,10 @@ static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s) {
 
 // --------------------------------------------------------- plan execution --
 static Plan *get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool state_only = false) {
-  const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0) | (state_only ? 8 : 0);
+  const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0) | (state_only ? 8 : 0) | (a->gates == 2 ? 16 : 0);
   auto it = a->plans.find(key);
   if (it != a->plans.end() && it->second.tile_bits == a->tile_bits) return &it->second;
-  Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, want_grad, diag, false, state_only, a->ent);
+  Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, want_grad, diag, false, state_only, a->ent, a->gates);
   pl.tile_bits = a->tile_bits;
   a->plans[key] = std::move(pl);
   return &a->plans[key];
@@ -760,7 +901,8 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
     if (id < 0) return nullptr;
     return bufs + (size_t)id * J * S * es;  // buffer id, job slots contiguous
   };
-  const void *table = h ? (prec ? h->T64.ptr : h->T32.ptr) : nullptr;
+  const bool cplx = a->gates == 2;
+  const void *table = h ? (cplx ? h->TC[prec].ptr : (prec ? h->T64.ptr : h->T32.ptr)) : nullptr;
   const void *tc = h ? (prec ? (const void *)h->d_tc64 : (const void *)h->d_tc32) : nullptr;
   if (state) *state = buf_ptr(pl->final_buf);
   for (int j0 = 0; j0 < batch; j0 += J) {
@@ -846,7 +988,12 @@ static int check_pair(gvqe_ansatz a, gvqe_hamiltonian h) {
 static int energy_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, int batch,
                        double *E, double *grad, int prec, cudaStream_t s) {
   const bool diag = h->gm.empty();
-  GV_TRY(ensure_tables(h, prec, s));
+  const bool cplx = a->gates == 2;
+  if (cplx && !diag)
+    return fail(GVQE_EUNSUPPORTED, "the RY+RZ (complex) ansatz takes diagonal Hamiltonians (I/Z letters) only");
+  if (cplx && a->n + 1 < 10)
+    return fail(GVQE_EUNSUPPORTED, "the RY+RZ (complex) ansatz needs n >= 9 qubits");
+  GV_TRY(ensure_tables(h, prec, s, cplx));
   Plan *pl = get_plan(a, prec, grad != nullptr, diag);
   const int P = pl->P;
   // trig table and per-job lowest active layer
@@ -858,7 +1005,7 @@ static int energy_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, 
   count_launches(1);
   const int *ml = nullptr;
   if (grad) {
-    GV_CUDA(launch_minlayer(mask, batch, a->n, P, a->reps + 1, minlayer, s));
+    GV_CUDA(launch_minlayer(mask, batch, a->n * a->gates, P, a->reps + 1, minlayer, s));
     count_launches(1);
     ml = minlayer;
   }
@@ -867,7 +1014,7 @@ static int energy_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, 
 
 static int param_shift_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, int batch,
                             double *E, double *grad, int prec, cudaStream_t s) {
-  const int P = a->n * (a->reps + 1);
+  const int P = a->gates * a->n * (a->reps + 1);
   std::vector<uint8_t> hmask((size_t)batch * P, 1);
   if (mask) {
     GV_CUDA(cudaMemcpyAsync(hmask.data(), mask, hmask.size(), cudaMemcpyDeviceToHost, s));
@@ -1001,6 +1148,13 @@ int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
     a->plans.clear();
     return GVQE_OK;
   }
+  if (option == GVQE_OPT_GATES) {
+    if (value != GVQE_GATES_RY && value != GVQE_GATES_RY_RZ)
+      return fail(GVQE_EINVAL, "gate set %d is not GVQE_GATES_RY or GVQE_GATES_RY_RZ", value);
+    a->gates = value;
+    a->plans.clear();
+    return GVQE_OK;
+  }
   return fail(GVQE_EINVAL, "unknown option %d", option);
 }
 
@@ -1053,6 +1207,7 @@ int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int fl
                  const double *uniforms, int64_t *shots, double *stats, int64_t *argmax, void *stream) {
   g_err.clear();
   if (!is_ansatz(a)) return fail(GVQE_EINVAL, "invalid ansatz handle");
+  if (a->gates != 1) return fail(GVQE_EUNSUPPORTED, "gvqe_readout takes the RY ansatz (GVQE_GATES_RY) only");
   if (!params || !stats || !argmax) return fail(GVQE_EINVAL, "params, stats and argmax must be device pointers");
   if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(GVQE_EINVAL, "alpha %g is outside [0, 1]", alpha);
   if (n_shots < 0 || (n_shots > 0 && (!uniforms || !shots)))

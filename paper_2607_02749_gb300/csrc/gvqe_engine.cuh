@@ -31,6 +31,7 @@ enum LoadMode : int {
   LD_GATHER = 1,     // v = in[A^-1 y]: the linear CX chain applied on the fly
   LD_L0_GATHER = 2,  // v = psi_0(A^-1 y): analytic layer-0 product state through the CX chain
   LD_L0 = 3,         // v = psi_0(y)
+  LD_ZERO = 4,       // v = |0...0>: 1 at index 0, else 0 (the complex path's layer 0)
 };
 
 // Entanglers (Section IV-B; Table 2 adds reverse linear, pairwise and SCA).  As
@@ -70,6 +71,7 @@ struct EntMap {
   int form;
   int s;            // EF_RING*: the frame's origin qubit
   uint32_t m1, m2;  // EF_PAIRS: target masks of the odd-start and even-start halves
+  int sh;           // index bits below the qubits (1 on the complex path: the re/im channel)
 };
 
 // x = y rotated so that bit s lands on bit 0, within n bits (0 <= s < n)
@@ -115,7 +117,7 @@ __host__ __device__ inline uint32_t ent_inv_f(uint32_t y, uint32_t nmask, const 
   }
 }
 
-__host__ __device__ inline uint32_t ent_inv(uint32_t y, uint32_t nmask, const EntMap &e, int n) {
+__host__ __device__ inline uint32_t ent_inv_q(uint32_t y, uint32_t nmask, const EntMap &e, int n) {
   switch (e.form) {
     case EF_WRAP_DIFF: return ent_inv_f<EF_WRAP_DIFF>(y, nmask, e, n);
     case EF_PREFIX: return ent_inv_f<EF_PREFIX>(y, nmask, e, n);
@@ -124,6 +126,14 @@ __host__ __device__ inline uint32_t ent_inv(uint32_t y, uint32_t nmask, const En
     case EF_RING_REV: return ent_inv_f<EF_RING_REV>(y, nmask, e, n);
     default: return ent_inv_f<EF_DIFF>(y, nmask, e, n);
   }
+}
+
+// x = A^-1 y on the qubit bits of an index with e.sh channel bits below them
+// (n counts all index bits, nmask = 2^n - 1).
+__host__ __device__ inline uint32_t ent_inv(uint32_t y, uint32_t nmask, const EntMap &e, int n) {
+  if (e.sh == 0) return ent_inv_q(y, nmask, e, n);
+  const uint32_t low = (1u << e.sh) - 1u;
+  return (ent_inv_q(y >> e.sh, nmask >> e.sh, e, n - e.sh) << e.sh) | (y & low);
 }
 
 enum StoreMode : int {
@@ -138,13 +148,17 @@ enum PassFlags : int {
   // (4 unused: tile pairing is PassArgs::pair_mask)
   F_WRITE_LAMBDA = 8,  // K_LAMBDA_XY: write lambda
   F_ACCUM = 16,        // K_LAMBDA_XY: add onto lambda already written (group chunks)
+  F_COMPLEX = 64,      // the complex path (full EfficientSU2 layers: RY then RZ)
 };
 
 struct PassArgs {
   int kind, load_mode, store_mode, flags;
   int n, tb, c, a;          // register size, tile bits and bit layout (see above)
   uint32_t gate_mask;       // tile bits that carry a gate in this pass
-  int layer;                // r: the parameter of tile bit i is p = r*n + qubit(i)
+  int layer;                // r: the RY parameter of tile bit i is p = r*pstride + qubit(i) - qoff
+  int pstride;              // parameters per rotation layer (n, or 2n with RZ)
+  int qoff;                 // index bits below qubit 0 (0, or 1 on the complex path)
+  int zoff;                 // RZ parameter of qubit q: r*pstride + zoff + q (complex path)
   int P;                    // parameters per job
   long long tiles;          // tiles per job (a power of two)
   const void *in;           // psi input (per-job stride in_stride elements)
@@ -210,6 +224,7 @@ cudaError_t launch_reduce(const double *part, long long part_stride, const RedEn
 cudaError_t launch_scatter_coeffs(const uint32_t *z, const double *c, int count, double *table,
                                   cudaStream_t s);
 cudaError_t launch_convert_table(const double *src, float *dst, long long count, cudaStream_t s);
+cudaError_t launch_expand_table(const double *src, void *dst, long long count, int prec, cudaStream_t s);
 cudaError_t launch_shift_params(const double *params, int P, int jobs, const int *active,
                                 int n_active, double *out, cudaStream_t s);
 cudaError_t launch_shift_combine(const double *Es, int P, int jobs, const int *active, int n_active,

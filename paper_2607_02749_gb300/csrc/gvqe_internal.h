@@ -65,8 +65,10 @@ void count_launches(int k);
 // tile bits per partial), as the persistent batch kernel computes them,
 // instead of per warp of the standalone layer-0 gradient pass.
 // state_only: the forward passes alone, the final state kept (Plan::final_buf).
+// gates: 1 = RY layers (real amplitudes), 2 = full EfficientSU2 layers, RY then
+// RZ on every qubit (complex amplitudes; diagonal H, energy and gradient only).
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false,
-                bool state_only = false, int ent = ENT_LINEAR);
+                bool state_only = false, int ent = ENT_LINEAR, int gates = 1);
 std::string describe_plan(const Plan &pl);
 
 }  // namespace gvqe
@@ -85,6 +87,7 @@ struct gvqe_hamiltonian_s {
   int n_grouped = 0, n_dropped = 0;
   double abs_sum = 0.0;
   gvqe::DevBuf T64, T32, G;
+  gvqe::DevBuf TC[2];  // complex path: each table entry twice (re/im), FP32 and FP64
   uint32_t *d_gm = nullptr;
   int *d_gs = nullptr;
   uint32_t *d_tz = nullptr;
@@ -95,6 +98,7 @@ struct gvqe_hamiltonian_s {
 struct gvqe_ansatz_s {
   uint32_t magic = 0;
   int n = 0, reps = 0, ent = 0;
+  int gates = 1;  // 1: RY layers; 2: RY then RZ (the complex path)
   int tile_bits = 0;  // 0 = automatic
   std::map<int, gvqe::Plan> plans;
   gvqe::DevBuf ws, aux, shift, ro;

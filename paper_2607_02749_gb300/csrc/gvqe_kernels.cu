@@ -70,7 +70,7 @@ __device__ __forceinline__ void load_coeffs(const PassArgs &A, const T2 *cs, T2 
     v.y = 0;
     if (tid < A.tb && ((A.gate_mask >> tid) & 1u) && A.kind != K_WHT) {
       const int q = tid < A.c ? tid : A.a + tid - A.c;
-      v = cs[A.layer * A.n + q];
+      v = cs[A.layer * A.pstride + q - A.qoff];
     }
     gcs[tid] = v;
   }
@@ -280,6 +280,17 @@ __global__ void k_convert_table(const double *__restrict__ src, float *__restric
     dst[i] = (float)src[i];
 }
 
+// The complex path's table: dst[2x + c] = src[x] (c = re/im channel), in the amplitude precision.
+template <typename TD>
+__global__ void k_expand_table(const double *__restrict__ src, TD *__restrict__ dst, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const TD v = (TD)src[i];
+    dst[2 * i] = v;
+    dst[2 * i + 1] = v;
+  }
+}
+
 // Shifted parameter sets for Eq. 13: per job, row 0 = theta, then for each active
 // parameter a (+pi/2, -pi/2) pair.
 __global__ void k_shift_params(const double *__restrict__ params, int P, int jobs, const int *__restrict__ active,
@@ -403,6 +414,16 @@ cudaError_t launch_scatter_coeffs(const uint32_t *z, const double *c, int count,
 cudaError_t launch_convert_table(const double *src, float *dst, long long count, cudaStream_t s) {
   const long long blocks = (count + 255) / 256;
   k_convert_table<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_table(const double *src, void *dst, long long count, int prec, cudaStream_t s) {
+  const long long blocks = (count + 255) / 256;
+  const unsigned g = (unsigned)(blocks < 65536 ? blocks : 65536);
+  if (prec)
+    k_expand_table<double><<<g, 256, 0, s>>>(src, (double *)dst, count);
+  else
+    k_expand_table<float><<<g, 256, 0, s>>>(src, (float *)dst, count);
   return cudaGetLastError();
 }
 

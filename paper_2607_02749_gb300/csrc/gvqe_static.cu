@@ -66,6 +66,7 @@ extern "C" int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const doubl
   if (!a || a->magic != MAGIC_ANSATZ) return fail(GVQE_EINVAL, "invalid ansatz handle");
   if (!h || h->magic != MAGIC_HAM) return fail(GVQE_EINVAL, "invalid Hamiltonian handle");
   if (a->n != h->n) return fail(GVQE_EINVAL, "ansatz has %d qubits but the Hamiltonian %d", a->n, h->n);
+  if (a->gates != 1) return fail(GVQE_EUNSUPPORTED, "gvqe_energy_static takes the RY ansatz (GVQE_GATES_RY) only");
   if (!params || !energies) return fail(GVQE_EINVAL, "params or energies is NULL");
   if (batch < 1) return fail(GVQE_EINVAL, "batch=%d < 1", batch);
   if (flags & ~GVQE_FP64) return fail(GVQE_EINVAL, "flags 0x%x: only GVQE_FP32 / GVQE_FP64 apply", flags);

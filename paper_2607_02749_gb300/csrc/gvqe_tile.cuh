@@ -171,6 +171,21 @@ struct Reg32<float> {
       return r.x + r.y;
     }
   }
+  // complex path (a pair is one amplitude): sum over amplitude pairs along
+  // register bit JB >= 1 of Im(conj(lam0) psi1) + Im(conj(lam1) psi0) = Im <lam|X|psi>
+  template <int JB>
+  __device__ __forceinline__ float gradx(const Reg32 &lam) const {
+    static_assert(JB >= 1, "the channel bit carries no gate");
+    constexpr int B = 1 << (JB - 1);
+    float acc = 0.f;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      if (m & B) continue;
+      const float2 l0 = lam.v[m], l1 = lam.v[m | B], p0 = v[m], p1 = v[m | B];
+      acc += l0.x * p1.y - l0.y * p1.x + l1.x * p0.y - l1.y * p0.x;
+    }
+    return acc;
+  }
 };
 
 template <>
@@ -210,6 +225,18 @@ struct Reg32<double> {
     for (int k = 0; k < 32; ++k) {
       if (k & (1 << JB)) continue;
       acc += lam.v[k | (1 << JB)] * v[k] - lam.v[k] * v[k | (1 << JB)];
+    }
+    return acc;
+  }
+  template <int JB>
+  __device__ __forceinline__ double gradx(const Reg32 &lam) const {
+    static_assert(JB >= 1, "the channel bit carries no gate");
+    constexpr int J = 1 << JB;
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 32; k += 2) {
+      if (k & J) continue;
+      acc += lam.v[k] * v[k + J + 1] - lam.v[k + 1] * v[k + J] + lam.v[k + J] * v[k + 1] - lam.v[k + J + 1] * v[k];
     }
     return acc;
   }
@@ -299,15 +326,24 @@ __device__ __forceinline__ void round_gates(Reg32<T> &r, const GateTab<T2> &gt, 
 // reduced over the warp with a transposed butterfly (each exchange halves the
 // values a lane carries), then lane (j << 2) holds value j and stores it.
 // X5: also the gate of tile bit 5 on register bit 1 (round H), in slot 5.
-template <int NB, int RO = 0, bool X5 = false, typename T>
+// CPLX: the complex path's RY gradient cos(tz) Im<lam|Y|psi> - sin(tz) Im<lam|X|psi>
+// (the RZ after the RY turns Y into cos Y - sin X), zf[tile bit] = (cos tz, sin tz).
+template <int NB, int RO = 0, bool X5 = false, bool CPLX = false, typename T, typename T2 = typename V2<T>::type>
 __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> &lam, uint32_t gmask, int tbit0,
-                                            double *wred, int lane) {
+                                            double *wred, int lane, const T2 *zf = nullptr) {
   T v[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = T(0);
-  if (X5 && ((gmask >> 5) & 1u)) v[5] = psi.template grad<1>(lam);
-#define GVQE_GV(J) \
-  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) v[J] = psi.template grad<(J + RO < 5 ? J + RO : 4)>(lam);
+  if (X5 && ((gmask >> 5) & 1u)) {
+    v[5] = psi.template grad<1>(lam);
+    if constexpr (CPLX) v[5] = zf[5].x * v[5] - zf[5].y * psi.template gradx<1>(lam);
+  }
+#define GVQE_GV(J)                                                                            \
+  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) {                                              \
+    constexpr int JB_ = (J + RO < 5 ? J + RO : 4);                                            \
+    v[J] = psi.template grad<JB_>(lam);                                                       \
+    if constexpr (CPLX && JB_ > 0) v[J] = zf[tbit0 + J].x * v[J] - zf[tbit0 + J].y * psi.template gradx<JB_>(lam); \
+  }
   GVQE_GV(0)
   GVQE_GV(1)
   GVQE_GV(2)
@@ -342,6 +378,60 @@ __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> 
       wred[tbit0 + j] = (double)r;
     else if (X5 && j == 5 && ((gmask >> 5) & 1u))
       wred[5] = (double)r;
+  }
+}
+
+// Complex path, round L: RZ gradients Im<lam|Z_q|psi> = sum_x s_q(x) w(x) with
+// w = Im(conj(lam) psi) and s_q = +1 (x_q = 0) or -1, for every gate bit of the
+// tile: register bits (tile bits 6..9) give signed sums over the thread's
+// pairs, lane bits (1..5) sign the thread total, warp bits (10..) sign the warp
+// total.  The 16 per-tile-bit values go through one transposed warp butterfly;
+// wredz[tile bit] receives the warp's partial.
+template <typename T>
+__device__ __forceinline__ void rz_grads_L(const Reg32<T> &psi, const Reg32<T> &lam, uint32_t gmask, double *wredz,
+                                           int lane, int w) {
+  T tot = T(0), d[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const auto l = lam.pair(m), p = psi.pair(m);
+    const T x = l.x * p.y - l.y * p.x;
+    tot += x;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[j] += ((m >> j) & 1) ? -x : x;
+  }
+  T v[16];
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    if (b >= 1 && b <= 5)
+      v[b] = ((lane >> (b - 1)) & 1) ? -tot : tot;
+    else if (b >= 6 && b <= 9)
+      v[b] = d[b - 6];
+    else if (b >= 10)
+      v[b] = tot;
+    else
+      v[b] = T(0);
+  }
+  // transposed butterfly: each exchange halves the values a lane carries
+  T u8[8], u4[4], u2[2];
+  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    u8[j] = (b4 ? v[8 + j] : v[j]) + __shfl_xor_sync(0xffffffffu, b4 ? v[j] : v[8 + j], 16);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    u4[j] = (b3 ? u8[4 + j] : u8[j]) + __shfl_xor_sync(0xffffffffu, b3 ? u8[j] : u8[4 + j], 8);
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+    u2[j] = (b2 ? u4[2 + j] : u4[j]) + __shfl_xor_sync(0xffffffffu, b2 ? u4[j] : u4[2 + j], 4);
+  T r = (b1 ? u2[1] : u2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? u2[0] : u2[1], 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  if ((lane & 1) == 0) {
+    const int b = (b4 ? 8 : 0) + (b3 ? 4 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0);
+    if ((gmask >> b) & 1u) {
+      double g = (double)r;
+      if (b >= 10 && ((w >> (b - 10)) & 1)) g = -g;
+      wredz[b] = g;
+    }
   }
 }
 
@@ -538,14 +628,101 @@ __device__ __forceinline__ void load_gate_coeffs(const PassArgs &A, const T2 *cs
     v.y = 0;
     if (tid < A.tb && ((A.gate_mask >> tid) & 1u)) {
       const int q = tid < A.c ? tid : A.a + tid - A.c;
-      v = cs[A.layer * A.n + q];
+      v = cs[A.layer * A.pstride + q - A.qoff];
     }
     gcs[tid] = v;
   }
 }
 
+// ------------------------------------------------ EfficientSU2 (complex) --
+// With the full EfficientSU2 rotation layer (RY, then RZ on every qubit) the
+// state is complex.  It is stored as 2^(n+1) reals, u[2x] = Re psi(x) and
+// u[2x + 1] = Im psi(x): index bit 0 is the real/imaginary channel and index
+// bit q + 1 is qubit q, so a register pair (tile bit 0) is one amplitude.  RY
+// and the CX permutations act alike on both channels; RZ(theta) on qubit q
+// multiplies psi(x) by exp(-i theta/2) when x_q = 0 and exp(+i theta/2) when
+// x_q = 1.  A pass applies its qubits' RZ after their RY (they commute with the
+// other qubits' gates) as one phase per amplitude in round H: the product of
+// the thread's tile bits' factors (pthr) and of the register bits' (preg).
+
+template <typename T2>
+__device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+  T2 r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename T2>
+__device__ __forceinline__ T2 cconj(T2 a) {
+  a.y = -a.y;
+  return a;
+}
+
+template <typename T2, int TB>
+struct SU2Tab {
+  T2 zh[16];    // per tile bit: (cos, sin) of theta_z / 2, (1, 0) without an RZ
+  T2 zf[16];    // per tile bit: (cos, sin) of theta_z (the RY gradient is cos Y - sin X)
+  T2 preg[16];  // round H: the phase of register pattern m
+  // threads 0..15; the caller synchronises before use
+  __device__ __forceinline__ void build(const PassArgs &A, const T2 *cs, int tid) {
+    if (tid >= 16) return;
+    auto half = [&](int tb) {
+      T2 v;
+      v.x = 1;
+      v.y = 0;
+      if (tb < A.tb && ((A.gate_mask >> tb) & 1u)) {
+        const int g = tb < A.c ? tb : A.a + tb - A.c;
+        v = cs[A.layer * A.pstride + A.zoff + g - A.qoff];
+      }
+      return v;
+    };
+    const T2 h = half(tid);
+    zh[tid] = h;
+    T2 f;
+    f.x = h.x * h.x - h.y * h.y;
+    f.y = 2 * h.x * h.y;
+    zf[tid] = f;
+    T2 p;
+    p.x = 1;
+    p.y = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // pair-index bit j holds tile bit tbit_H(j)
+      T2 e = half(tbit_H<TB>(j));
+      if (!((tid >> j) & 1)) e.y = -e.y;  // x_q = 0: exp(-i theta/2)
+      p = cmul(p, e);
+    }
+    preg[tid] = p;
+  }
+  // phase of this thread's round-H tile bits (those not in its registers)
+  __device__ __forceinline__ T2 thread_phase(int tid) const {
+    const int base = idx_H_thread<TB>(tid);
+    T2 p;
+    p.x = 1;
+    p.y = 0;
+#pragma unroll
+    for (int b = 1; b < TB; ++b) {
+      if (b == tbit_H<TB>(0) || b == tbit_H<TB>(1) || b == tbit_H<TB>(2) || b == tbit_H<TB>(3)) continue;
+      T2 e = zh[b];
+      if (!((base >> b) & 1)) e.y = -e.y;
+      p = cmul(p, e);
+    }
+    return p;
+  }
+};
+
+// psi -> psi * phase (forward) or lambda -> lambda * conj(phase) (backward), round H
+template <bool CONJ, typename T, typename T2, int TB>
+__device__ __forceinline__ void apply_su2_phase(Reg32<T> &r, const SU2Tab<T2, TB> &zt, T2 pthr) {
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    T2 ph = cmul(pthr, zt.preg[m]);
+    if (CONJ) ph = cconj(ph);
+    r.set_pair(m, cmul(r.pair(m), ph));
+  }
+}
+
 // Layer-0 product state psi_0(x) = prod_q f_q(x_q), f(0) = cos(t/2), f(1) = sin(t/2), tabulated
-// per tile: bits 0..6 (lo), bits 7..TB-1 (mid), bit TB together with the tile's bits above (hi).
+// per tile: bits 0..6 (lo), bits 7..TB (mid), the tile's bits above TB (hi, two values).
 template <typename T, typename T2, int TB>
 struct L0Tables {
   T lo[128];   // x bits 0..6
@@ -582,18 +759,20 @@ struct L0Tables {
 // One tile of a forward pass: tile block index tb_idx of job `job` (the pairing
 // of tiles H and ~H for gathering passes is applied here).  State loads go
 // through L2 (ld.global.cg), so data written by other SMs is never read stale.
-template <typename T, int TB, bool FULL, int LOAD, bool WHT, bool REUSE = true>
+template <typename T, int TB, bool FULL, int LOAD, bool WHT, bool REUSE = true, bool CPLX = false>
 __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb_idx) {
   using T2 = typename V2<T>::type;
   constexpr int NT = 1 << (TB - 5);
   constexpr int NW = NT / 32;
   constexpr int H = TB - 10;
   constexpr bool L0 = (LOAD == LD_L0 || LOAD == LD_L0_GATHER);
+  static_assert(!CPLX || (!L0 && !WHT), "the complex path starts from |0> and has no table build");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *s = reinterpret_cast<T *>(smem_raw);
   __shared__ GateTab<T2> gt;
   __shared__ double ered[NW];
   __shared__ L0Tables<T, T2, TB> tab;
+  __shared__ SU2Tab<T2, TB> zt;
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const SBase sb = sbase<TB, T>(tid);
@@ -605,6 +784,7 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   if (!WHT) {
     load_gate_coeffs(A, cs, gt.cs, tid);
   }
+  if constexpr (CPLX) zt.build(A, cs, tid);
   if constexpr (L0) {
     const uint32_t xbase = (LOAD == LD_L0_GATHER) ? ent_inv(tbase, nmask, A.em, A.n) : tbase;
     const uint32_t hflip = (LOAD == LD_L0_GATHER) ? A.l0_hflip : 0u;
@@ -638,6 +818,9 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
       T2 v;
       if constexpr (LOAD == LD_PLAIN) {
         v = __ldcg(reinterpret_cast<const T2 *>(in + y));
+      } else if constexpr (LOAD == LD_ZERO) {
+        v.x = (y == 0) ? T(1) : T(0);
+        v.y = T(0);
       } else {
         v.x = tab(y, TB);
         v.y = tab(y + 1, TB);
@@ -660,6 +843,7 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   lds_H<TB>(s, sb, r);
   round_gates<1, WHT, false, 1>(r, gt, gm, 5, false);
   round_gates<H, WHT, false, 2>(r, gt, gm, 10, false);
+  if constexpr (CPLX) apply_su2_phase<false>(r, zt, zt.thread_phase(tid));
   const T *table = reinterpret_cast<const T *>(A.table);
   const bool store = A.store_mode != ST_NONE;
   const bool energy = (A.flags & F_ENERGY) != 0;
@@ -687,10 +871,10 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   if (REUSE) __syncthreads();  // shared tile and coefficients free for the caller's next tile
 }
 
-template <typename T, int TB, bool FULL, int LOAD, bool WHT>
+template <typename T, int TB, bool FULL, int LOAD, bool WHT, bool CPLX = false>
 __global__ void __launch_bounds__(1 << (TB - 5), (TB <= 12 ? 8 : 4) / (sizeof(T) == 8 ? 2 : 1))
 k_fwd(const PassArgs A) {
-  fwd_tile<T, TB, FULL, LOAD, WHT, false>(A, blockIdx.y, blockIdx.x);
+  fwd_tile<T, TB, FULL, LOAD, WHT, false, CPLX>(A, blockIdx.y, blockIdx.x);
 }
 
 // ------------------------------------------------------ backward tile pass --
@@ -717,7 +901,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // theirs, and round L writes lambda (through the inverse CX chain for the
 // first pass of a layer, layout FULL).  Gradient and energy partials are
 // written per tile.
-template <typename T, int TB, bool FULL>
+template <typename T, int TB, bool FULL, bool CPLX = false>
 __global__ void __launch_bounds__(1 << (TB - 5), (sizeof(T) == 4) ? 2 : 1)
 k_bwd(const PassArgs A) {
   using T2 = typename V2<T>::type;
@@ -732,6 +916,8 @@ k_bwd(const PassArgs A) {
   __shared__ GateTab<T2> gt;
   __shared__ double gred[2][NW][16];  // by tile parity: a warp may start the next
   __shared__ double ered[2][NW];      // tile while warp 0 still sums this one
+  __shared__ double gredz[CPLX ? 2 : 1][CPLX ? NW : 1][16];  // complex path: RZ partials
+  __shared__ SU2Tab<T2, TB> zt;
 
   const int job = blockIdx.y;
   if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.layer < A.minlayer[A.job0 + job]) return;
@@ -744,6 +930,7 @@ k_bwd(const PassArgs A) {
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   load_gate_coeffs(A, cs, gt.cs, tid);
   if (sizeof(T) == 4) gt.pack(tid);
+  if constexpr (CPLX) zt.build(A, cs, tid);
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
   const bool init = (A.flags & F_LAMBDA_INIT) != 0;
   const T *lsrc = init ? reinterpret_cast<const T *>(A.table)
@@ -775,6 +962,12 @@ k_bwd(const PassArgs A) {
     issue(lsrc, bx, buf + L * TILE);
   }
   __syncthreads();  // gate coefficients visible
+  T2 pthr;
+  const T2 *zf = nullptr;
+  if constexpr (CPLX) {
+    pthr = zt.thread_phase(tid);
+    zf = zt.zf;
+  }
   for (; bx < tiles; bx += gridDim.x) {
     const uint32_t nbx = bx + gridDim.x;
     const bool more = nbx < tiles;
@@ -807,19 +1000,22 @@ k_bwd(const PassArgs A) {
       eacc = warp_sum(eacc);
       if (lane == 0) ered[par][w] = (double)eacc;
     }
-    round_grads<4, 1>(psi, lam, gm, 6, gred[par][w], lane);
+    round_grads<4, 1, false, CPLX>(psi, lam, gm, 6, gred[par][w], lane, zf);
+    if constexpr (CPLX) rz_grads_L(psi, lam, gm, gredz[par][w], lane, w);
     if (init) __syncwarp();  // lambda = E psi is in shared before round M reads it
     // round M (gradients only)
     if (gm & 0x1Fu) {
       lds_M(sp, tid, psi);
       lds_M(sl, tid, lam);
-      round_grads<5>(psi, lam, gm, 0, gred[par][w], lane);
+      round_grads<5, 0, false, CPLX>(psi, lam, gm, 0, gred[par][w], lane, zf);
     }
-    // round H: gradients, then RY(-theta) on lambda.  Its layout crosses warps.
+    // round H: gradients, then RY(-theta) on lambda (complex path: first
+    // RZ(-theta) on every qubit of the pass, as one phase).  Its layout crosses warps.
     __syncthreads();
     lds_H<TB>(sp, sb, psi);
     lds_H<TB>(sl, sb, lam);
-    round_grads<H, 2, true>(psi, lam, gm, 10, gred[par][w], lane);
+    round_grads<H, 2, true, CPLX>(psi, lam, gm, 10, gred[par][w], lane, zf);
+    if constexpr (CPLX) apply_su2_phase<true>(lam, zt, pthr);
     round_gates<H, false, true, 2>(lam, gt, gm, 10, true);
     round_gates<1, false, true, 1>(lam, gt, gm, 5, true);
     __syncthreads();  // psi fully read; lambda may be overwritten
@@ -838,8 +1034,12 @@ k_bwd(const PassArgs A) {
     lds_L(sl, sb, lam);
     round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
     // (the short closed forms compute each x from y: measured faster here than
-    // the XOR walk, which the other forms take)
-    if (!FULL || A.em.form <= EF_PREFIX) {
+    // the XOR walk, which the other forms take).  The complex path's layer 0
+    // (FULL, no entangler) stores plainly or not at all.
+    if (FULL && A.store_mode != ST_SCATTER) {
+      if (A.store_mode == ST_PLAIN)
+        for_L(gi, [&](int m, uint32_t y) { *reinterpret_cast<T2 *>(out + y) = lam.pair(m); });
+    } else if (!FULL || (A.em.form <= EF_PREFIX && A.em.sh == 0)) {
       const EntMap em = A.em;
       for_L(gi, [&](int m, uint32_t y) {
         const T2 v = lam.pair(m);
@@ -870,6 +1070,12 @@ k_bwd(const PassArgs A) {
 #pragma unroll
       for (int ww = 0; ww < NW; ++ww) g += gred[par][ww][tid];
       part[(size_t)tid * tiles + t] = g;
+      if constexpr (CPLX) {  // RZ rows follow the TB RY rows
+        double gz = 0.0;
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) gz += gredz[par][ww][tid];
+        part[(size_t)(TB + tid) * tiles + t] = gz;
+      }
     }
     if ((A.flags & F_ENERGY) && tid == 0) {
       double e = 0.0;
@@ -1242,6 +1448,18 @@ cudaError_t launch_tb(const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
   const bool full = A.c >= TB;
   switch (A.kind) {
     case K_FWD:
+      if (A.flags & F_COMPLEX) {
+        if (!full) {
+          if (A.load_mode != LD_PLAIN) return cudaErrorInvalidValue;
+          return launch_k(k_fwd<T, TB, false, LD_PLAIN, false, true>, grid, block, tile, s, A);
+        }
+        switch (A.load_mode) {
+          case LD_PLAIN: return launch_k(k_fwd<T, TB, true, LD_PLAIN, false, true>, grid, block, tile, s, A);
+          case LD_GATHER: return launch_k(k_fwd<T, TB, true, LD_GATHER, false, true>, grid, block, tile, s, A);
+          case LD_ZERO: return launch_k(k_fwd<T, TB, true, LD_ZERO, false, true>, grid, block, tile, s, A);
+          default: return cudaErrorInvalidValue;
+        }
+      }
       if (!full) {
         if (A.load_mode != LD_PLAIN) return cudaErrorInvalidValue;
         return launch_k(k_fwd<T, TB, false, LD_PLAIN, false>, grid, block, tile, s, A);
@@ -1257,14 +1475,21 @@ cudaError_t launch_tb(const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
       if (full) return launch_k(k_fwd<T, TB, true, LD_PLAIN, true>, grid, block, tile, s, A);
       return launch_k(k_fwd<T, TB, false, LD_PLAIN, true>, grid, block, tile, s, A);
     case K_BWD: {
-      // the first pass of a layer (layout FULL) writes lambda through the inverse CX chain
-      if (full != (A.store_mode == ST_SCATTER)) return cudaErrorInvalidValue;
+      // the first pass of a layer (layout FULL) writes lambda through the inverse CX
+      // chain; the complex path's layer 0 (no entangler) stores plainly or not at all
+      const bool cplx = (A.flags & F_COMPLEX) != 0;
+      if (!full && A.store_mode != ST_PLAIN) return cudaErrorInvalidValue;
+      if (full && !cplx && A.store_mode != ST_SCATTER) return cudaErrorInvalidValue;
       // persistent CTAs: as many as fit on the device at once, split over the jobs
       const int per_sm = (sizeof(T) == 4) ? 2 : 1;
       long long ctas = (long long)num_sms() * per_sm / jobs;
       if (ctas < 1) ctas = 1;
       if (ctas > A.tiles) ctas = A.tiles;
       const dim3 pgrid((unsigned)ctas, (unsigned)jobs);
+      if (cplx) {
+        if (full) return launch_k(k_bwd<T, TB, true, true>, pgrid, block, 3 * tile, s, A);
+        return launch_k(k_bwd<T, TB, false, true>, pgrid, block, 3 * tile, s, A);
+      }
       if (full) return launch_k(k_bwd<T, TB, true>, pgrid, block, 3 * tile, s, A);
       return launch_k(k_bwd<T, TB, false>, pgrid, block, 3 * tile, s, A);
     }

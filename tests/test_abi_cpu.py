@@ -180,3 +180,13 @@ def test_entangler_inverse_rejects_bad_arguments():
         with pytest.raises(_lib.GvqeError) as e:
             _lib.gvqe_entangler_inverse(*args)
         assert e.value.code == _lib.GVQE_EINVAL
+
+
+def test_gate_set_option():
+    a = _lib.gvqe_ansatz_create(10, 2)
+    _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_GATES, _lib.GVQE_GATES_RY_RZ)
+    _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_GATES, _lib.GVQE_GATES_RY)
+    with pytest.raises(_lib.GvqeError) as e:
+        _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_GATES, 3)
+    assert e.value.code == _lib.GVQE_EINVAL
+    _lib.gvqe_destroy(a)
