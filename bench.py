@@ -56,6 +56,8 @@ def parse_args():
                     help="run only the readout leg on the workload and print its JSON object")
     ap.add_argument("--only-entanglers", action="store_true",
                     help="run only the entangler leg on the workload and print its JSON object")
+    ap.add_argument("--only-su2", action="store_true",
+                    help="run only the EfficientSU2 (RY+RZ, complex) leg on the workload and print its JSON object")
     ap.add_argument("--only-driver", action="store_true",
                     help="run only the Graph-VQE driver leg (one epoch at n=20) and print its JSON object")
     return ap.parse_args()
@@ -298,6 +300,43 @@ def entangler_leg(n: int, reps: int, ham, steps: int):
     return out
 
 
+def su2_leg(n: int, reps: int, ham, steps: int):
+    """The full EfficientSU2 rotation layer (RY then RZ on every qubit, Eq. 8) on
+    the benchmark workload: complex amplitudes, P = 2 n (D+1), one vector per call.
+    Per-kind GB/s from the library's CUDA-event profile over the timed calls."""
+    import numpy as np
+    import torch
+
+    import paper_2607_02749_gb300 as gv
+    from paper_2607_02749_gb300 import _lib
+
+    a = gv.Ansatz(n, reps, gates=gv.GVQE_GATES_RY_RZ)
+    h = gv.Hamiltonian.from_workload(ham)
+    th = torch.as_tensor(np.random.default_rng(1).uniform(-np.pi, np.pi, (1, a.n_params)), device="cuda")
+    e, g = gv.energy_grad(a, h, th)
+    torch.cuda.synchronize()
+    _lib.gvqe_profile_reset()
+    _lib.gvqe_profile_enable(True)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e, g = gv.energy_grad(a, h, th)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    _lib.gvqe_profile_enable(False)
+    prof = {k: _lib.gvqe_profile_read(k) for k in range(2)}
+    _lib.gvqe_profile_reset()
+    names = {0: "k_fwd", 1: "k_bwd"}
+    out = {"value": 1.0 / dt, "unit": UNIT, "n_params": a.n_params, "E": float(e.item()),
+           "amplitudes": "fp32 complex (2^(n+1) reals), fp64 table and reductions",
+           "per_kind": {names[k]: {"launches": prof[k]["launches"], "ms": prof[k]["ms"],
+                                   "GBps": prof[k]["bytes"] / (prof[k]["ms"] / 1000.0) / 1e9 if prof[k]["ms"] else 0.0}
+                        for k in prof if prof[k]["launches"]},
+           "timing": "wall clock around synchronous single-vector gvqe_energy_grad calls (FP32 adjoint)"}
+    a.close()
+    h.close()
+    return out
+
+
 def driver_leg(n: int = 20, reps: int = 4, n_terms: int = 2000):
     """One Graph-VQE epoch (Section IV-C to IV-E) on a sequence-local synthetic H:
     Louvain blocks, lock-step block L-BFGS-B with batched GPU evaluations, global
@@ -376,6 +415,11 @@ def run_gvqe(args):
     if args.only_readout:
         if rank == 0:
             print(json.dumps({"workload": args.workload, "readout": readout_leg(n, reps, ham, max(1, args.steps))}),
+                  flush=True)
+        return 0
+    if args.only_su2:
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "efficient_su2": su2_leg(n, reps, ham, max(1, args.steps))}),
                   flush=True)
         return 0
     if args.only_driver:
@@ -517,10 +561,12 @@ def run_gvqe(args):
         out["speedup_fp32_adjoint_vs_fp64_param_shift"] = value / ws / (1.0 / t_grad)
 
     if rank == 0 and not args.no_comparators:
+        a.close()  # the legs below allocate their own workspaces
         out["cluster_batch"] = cluster_leg(args.steps)
         out["readout"] = readout_leg(n, reps, ham, max(1, min(args.steps, 3)))
         out["entanglers"] = entangler_leg(n, reps, ham, max(1, min(args.steps, 3)))
         out["driver"] = driver_leg()
+        out["efficient_su2"] = su2_leg(n, reps, ham, max(1, min(args.steps, 3)))
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:

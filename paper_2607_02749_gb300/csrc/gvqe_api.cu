@@ -107,7 +107,7 @@ static double pass_bytes(int prec, const PassArgs &A, int jobs) {
       if (A.flags & F_ENERGY) b += S;
       break;
     case K_BWD:
-      b = 3 * S;
+      b = (A.store_mode == ST_NONE) ? 2 * S : 3 * S;
       break;
     case K_GRAD_L0:
       b = S;
@@ -991,8 +991,6 @@ static int energy_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, 
   const bool cplx = a->gates == 2;
   if (cplx && !diag)
     return fail(GVQE_EUNSUPPORTED, "the RY+RZ (complex) ansatz takes diagonal Hamiltonians (I/Z letters) only");
-  if (cplx && a->n + 1 < 10)
-    return fail(GVQE_EUNSUPPORTED, "the RY+RZ (complex) ansatz needs n >= 9 qubits");
   GV_TRY(ensure_tables(h, prec, s, cplx));
   Plan *pl = get_plan(a, prec, grad != nullptr, diag);
   const int P = pl->P;

@@ -35,6 +35,8 @@ template <typename T, typename T2>
 __device__ __forceinline__ T load_val(int mode, const T *__restrict__ in, long long y, long long nmask,
                                       const T2 *l0, int n, const EntMap &ent) {
   switch (mode) {
+    case LD_ZERO:
+      return y == 0 ? T(1) : T(0);
     case LD_GATHER:
       return in[ent_inv((uint32_t)y, (uint32_t)nmask, ent, n)];
     case LD_L0_GATHER:
@@ -86,13 +88,35 @@ __device__ __forceinline__ void load_coeffs(const PassArgs &A, const T2 *cs, T2 
 constexpr int SMALL_NT = 128;
 constexpr int SMALL_MAXN = 9;
 
+// The complex path (F_COMPLEX): index bit 0 is the re/im channel (no gate); a
+// pass's RZ gates follow its RY gates as one phase per amplitude, the backward
+// pass takes RZ gradients Im<lam|Z|psi>, corrects the RY gradients to
+// cos(tz) Y - sin(tz) X and un-applies the phase before the RY rotations.
+template <typename T, typename T2>
+__device__ __forceinline__ T2 small_phase(int x, uint32_t gm, int n, const T2 *zcs) {
+  T2 p;
+  p.x = 1;
+  p.y = 0;
+  for (int b = 1; b < n; ++b) {
+    if (!((gm >> b) & 1u)) continue;
+    T2 e = zcs[b];
+    if (!((x >> b) & 1)) e.y = -e.y;  // x_q = 0: exp(-i theta/2)
+    const T re = p.x * e.x - p.y * e.y;
+    p.y = p.x * e.y + p.y * e.x;
+    p.x = re;
+  }
+  return p;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
   using T2 = typename V2<T>::type;
+  constexpr int ES = 2 * SMALL_MAXN;  // energy slot; RY rows 0..8, RZ rows 9..17
   __shared__ T sp[1 << SMALL_MAXN], sl[1 << SMALL_MAXN];
   __shared__ T2 gcs[16];
+  __shared__ T2 zcs[16];
   __shared__ T2 l0cs[32];
-  __shared__ double red[SMALL_NT][SMALL_MAXN + 1];
+  __shared__ double red[SMALL_NT][ES + 1];
   const int job = blockIdx.y;
   const int tid = threadIdx.x;
   const int n = A.n;
@@ -103,7 +127,15 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
     if (A.kind == K_GRAD_L0 && A.minlayer[A.job0 + job] > 0) return;
   }
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
+  const bool cplx = (A.flags & F_COMPLEX) != 0;
   if (A.kind != K_WHT) load_coeffs(A, cs, gcs, l0cs, tid);
+  if (cplx && tid < 16) {
+    T2 v;
+    v.x = 1;
+    v.y = 0;
+    if (tid < A.tb && ((A.gate_mask >> tid) & 1u)) v = cs[A.layer * A.pstride + A.zoff + tid - A.qoff];
+    zcs[tid] = v;
+  }
   __syncthreads();
   const T *in = reinterpret_cast<const T *>(A.in) + job * A.in_stride;
   const T *lin = reinterpret_cast<const T *>(A.lam_in) + job * A.lam_stride;
@@ -111,7 +143,7 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
   T *out = reinterpret_cast<T *>(A.out) + job * A.out_stride;
   double *part = A.part + job * A.part_stride;
   const uint32_t gm = A.gate_mask;
-  for (int i = 0; i <= SMALL_MAXN; ++i) red[tid][i] = 0.0;
+  for (int i = 0; i <= ES; ++i) red[tid][i] = 0.0;
 
   if (A.kind == K_FWD || A.kind == K_WHT) {
     for (int x = tid; x < N; x += SMALL_NT) sp[x] = load_val<T>(A.load_mode, in, x, nmask, l0cs, n, A.em);
@@ -133,6 +165,15 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
       }
       __syncthreads();
     }
+    if (cplx) {  // the pass's RZ gates as one phase per amplitude
+      for (int x = 2 * tid; x < N; x += 2 * SMALL_NT) {
+        const T2 ph = small_phase<T, T2>(x, gm, n, zcs);
+        const T re = sp[x], im = sp[x + 1];
+        sp[x] = re * ph.x - im * ph.y;
+        sp[x + 1] = re * ph.y + im * ph.x;
+      }
+      __syncthreads();
+    }
     for (int x = tid; x < N; x += SMALL_NT) {
       store_val(A.store_mode, out, x, nmask, sp[x], n, A.em);
       if (A.flags & F_ENERGY) red[tid][0] += (double)(sp[x] * sp[x] * table[x]);
@@ -142,7 +183,7 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
     for (int x = tid; x < N; x += SMALL_NT) {
       sp[x] = in[x];
       sl[x] = init ? table[x] * sp[x] : lin[x];
-      if (A.flags & F_ENERGY) red[tid][SMALL_MAXN] += (double)(sp[x] * sl[x]);
+      if (A.flags & F_ENERGY) red[tid][ES] += (double)(sp[x] * sl[x]);
     }
     __syncthreads();
     for (int b = 0; b < n; ++b) {
@@ -150,10 +191,34 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
       for (int pi = tid; pi < N / 2; pi += SMALL_NT) {
         const int x0 = ((pi >> b) << (b + 1)) | (pi & ((1 << b) - 1));
         const int x1 = x0 | (1 << b);
-        red[tid][b] += (double)(sl[x1] * sp[x0] - sl[x0] * sp[x1]);
+        T g = sl[x1] * sp[x0] - sl[x0] * sp[x1];
+        if (cplx) {  // cos(tz) Im<lam|Y|psi> - sin(tz) Im<lam|X|psi>, over amplitude pairs
+          g *= zcs[b].x * zcs[b].x - zcs[b].y * zcs[b].y;
+          if (!(x0 & 1)) {
+            const T gx = sl[x0] * sp[x1 + 1] - sl[x0 + 1] * sp[x1] + sl[x1] * sp[x0 + 1] - sl[x1 + 1] * sp[x0];
+            g -= 2 * zcs[b].x * zcs[b].y * gx;
+          }
+        }
+        red[tid][b] += (double)g;
+      }
+    }
+    if (cplx) {  // RZ gradients: sum_x s_q(x) Im(conj(lam) psi)
+      for (int x = 2 * tid; x < N; x += 2 * SMALL_NT) {
+        const T w = sl[x] * sp[x + 1] - sl[x + 1] * sp[x];
+        for (int b = 1; b < n; ++b)
+          if ((gm >> b) & 1u) red[tid][SMALL_MAXN + b] += (double)(((x >> b) & 1) ? -w : w);
       }
     }
     __syncthreads();
+    if (cplx) {  // RZ(-theta) on lambda before the RY(-theta) rotations
+      for (int x = 2 * tid; x < N; x += 2 * SMALL_NT) {
+        const T2 ph = small_phase<T, T2>(x, gm, n, zcs);
+        const T re = sl[x], im = sl[x + 1];
+        sl[x] = re * ph.x + im * ph.y;
+        sl[x + 1] = im * ph.x - re * ph.y;
+      }
+      __syncthreads();
+    }
     for (int b = 0; b < n; ++b) {
       if (!((gm >> b) & 1u)) continue;
       const T c = gcs[b].x, s = -gcs[b].y;
@@ -172,7 +237,7 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
     for (int x = tid; x < N; x += SMALL_NT) {
       const T psi0 = product_state<T>(x, l0cs, n);
       const T lam = init ? table[x] * psi0 : lin[x];
-      if (init) red[tid][SMALL_MAXN] += (double)(psi0 * lam);
+      if (init) red[tid][ES] += (double)(psi0 * lam);
       for (int q = 0; q < n; ++q) {
         T wq = T(1);
         for (int i = 0; i < n; ++i) {
@@ -196,21 +261,23 @@ __global__ void __launch_bounds__(SMALL_NT) k_small(const PassArgs A) {
         acc += d * pu;
       }
       if (A.flags & F_WRITE_LAMBDA) out[x] = acc;
-      red[tid][SMALL_MAXN] += (double)(p * acc);
+      red[tid][ES] += (double)(p * acc);
     }
   }
   __syncthreads();
-  if (tid <= SMALL_MAXN) {
+  if (tid <= ES) {
     double s = 0.0;
     for (int i = 0; i < SMALL_NT; ++i) s += red[i][tid];
     const int q = tid;
     if (q < SMALL_MAXN) {
       const bool want = (A.kind == K_BWD && ((gm >> q) & 1u)) || (A.kind == K_GRAD_L0 && q < n);
       if (want) part[(long long)q * A.tiles] = s;
+    } else if (q < ES && cplx && A.kind == K_BWD) {
+      const int b = q - SMALL_MAXN;  // RZ rows follow the tb RY rows
+      if ((gm >> b) & 1u) part[(long long)(A.tb + b) * A.tiles] = s;
     }
     if (A.kind == K_FWD && (A.flags & F_ENERGY) && q == 0) A.epart[job * A.part_stride] = s;
-    if (q == SMALL_MAXN && (A.flags & F_ENERGY) && A.kind != K_FWD)
-      A.epart[job * A.part_stride] = s;
+    if (q == ES && (A.flags & F_ENERGY) && A.kind != K_FWD) A.epart[job * A.part_stride] = s;
   }
 }
 

@@ -1,8 +1,9 @@
 """The full EfficientSU2 rotation layer (RY then RZ on every qubit, Eq. 8;
 complex amplitudes) on the GPU against the oracle with gate set 2: energies and
-adjoint gradients (RY and RZ entries) in FP32 and FP64, several entanglers, tile
-sizes that force strided passes, reps = 0, active masks, the parameter-shift
-comparator, and the calls that refuse the complex path."""
+adjoint gradients (RY and RZ entries) in FP32 and FP64, several entanglers, the
+whole-register kernel (n <= 8) and tile sizes that force strided passes, reps = 0,
+active masks, the parameter-shift comparator, and the calls that refuse the
+complex path."""
 import numpy as np
 import pytest
 
@@ -45,7 +46,8 @@ def _check(e, g, er, gr, scale, fp64):
 
 
 @pytest.mark.parametrize("fp64", [False, True])
-@pytest.mark.parametrize("n,reps,tb,ent", [(9, 2, 0, 0), (11, 1, 0, 1), (12, 3, 0, 0), (12, 0, 0, 0),
+@pytest.mark.parametrize("n,reps,tb,ent", [(1, 2, 0, 0), (2, 1, 0, 1), (5, 2, 0, 5), (8, 3, 0, 0), (8, 0, 0, 0),
+                                           (9, 2, 0, 0), (11, 1, 0, 1), (12, 3, 0, 0), (12, 0, 0, 0),
                                            (14, 2, 0, 5), (14, 2, 10, 0), (17, 2, 11, 2), (16, 1, 12, 4)])
 def test_energy_and_gradient_match_the_oracle(n, reps, tb, ent, fp64):
     if fp64 and tb > 12:
@@ -122,7 +124,5 @@ def test_unsupported_calls_refuse_the_complex_path():
     hz = gv.Hamiltonian.from_workload(wl.z_hamiltonian(n, 30, seed=1))
     with pytest.raises(gv.GvqeError):
         gv.readout(a, hz, t[0], alpha=0.2)
-    small = gv.Ansatz(6, 1, gates=RYRZ)
     with pytest.raises(gv.GvqeError):
-        gv.energy(small, gv.Hamiltonian.from_workload(wl.z_hamiltonian(6, 10, seed=0)),
-                  torch.zeros((1, small.n_params), dtype=torch.float64, device="cuda"))
+        gv.Batch([a], [hz])
