@@ -69,6 +69,7 @@ class GraphVQEConfig:
 
     reps: int = 4
     entangler: int = _lib.GVQE_ENT_LINEAR
+    gates: int = _lib.GVQE_GATES_RY  # or GVQE_GATES_RY_RZ: the full EfficientSU2 layer (Eq. 8)
     resolution: float = 1.0        # Louvain gamma
     min_block: int = 2             # S_min
     ftol: float = 1e-4             # L-BFGS-B ftol; gtol = 0.1 ftol; also the early-stop tolerance
@@ -89,14 +90,14 @@ class GpuEvaluator:
     C ABI: one gvqe_energy_grad call per request batch (per-row masks)."""
 
     def __init__(self, n_qubits: int, reps: int, strings: Sequence[str], coeffs, entangler: int,
-                 fp64: bool = False, grad: str = "adjoint", device=None):
+                 fp64: bool = False, grad: str = "adjoint", device=None, gates: int = _lib.GVQE_GATES_RY):
         import torch
 
         from . import Ansatz, Hamiltonian
 
         self.torch = torch
         self.device = torch.device("cuda") if device is None else torch.device(device)
-        self.ansatz = Ansatz(n_qubits, reps, entangler)
+        self.ansatz = Ansatz(n_qubits, reps, entangler, gates=gates)
         self.ham = Hamiltonian(n_qubits, list(strings), np.asarray(coeffs, dtype=np.float64))
         self.flags = ((_lib.GVQE_FP64 if fp64 else _lib.GVQE_FP32)
                       | (_lib.GVQE_GRAD_PARAM_SHIFT if grad == "param_shift" else 0))
@@ -217,7 +218,7 @@ class GraphVQE:
         self.n = int(ham.n_qubits)
         self.strings = list(ham.strings)
         self.coeffs = np.asarray(ham.coeffs, dtype=np.float64)
-        self.P = self.n * (self.cfg.reps + 1)
+        self.P = self.cfg.gates * self.n * (self.cfg.reps + 1)
         self.dist = dist
         self.rank, self.world = 0, 1
         if dist is not None and dist.is_available() and dist.is_initialized():
@@ -226,13 +227,14 @@ class GraphVQE:
             self.dist = None
         c = self.cfg
         if evaluator is None:
-            evaluator = GpuEvaluator(self.n, c.reps, self.strings, self.coeffs, c.entangler, c.fp64, c.grad)
+            evaluator = GpuEvaluator(self.n, c.reps, self.strings, self.coeffs, c.entangler, c.fp64, c.grad,
+                                     gates=c.gates)
         self.evaluator = evaluator
         if global_evaluator is None:
             if self.world > 1:
                 lo, hi = self.term_slice(self.rank)
                 global_evaluator = GpuEvaluator(self.n, c.reps, self.strings[lo:hi], self.coeffs[lo:hi],
-                                                c.entangler, c.fp64, c.grad)
+                                                c.entangler, c.fp64, c.grad, gates=c.gates)
             else:
                 global_evaluator = evaluator
         self.global_evaluator = global_evaluator
@@ -252,10 +254,14 @@ class GraphVQE:
         return _lib.gvqe_partition(w, self.cfg.resolution, self.cfg.min_block)
 
     def block_masks(self) -> np.ndarray:
+        """theta_{B_i}: every rotation angle (RY, and RZ with the full layer) of every
+        layer on the qubits of block i."""
+        g = self.cfg.gates
         m = np.zeros((self.n_blocks, self.P), dtype=np.uint8)
         for r in range(self.cfg.reps + 1):
-            for q in range(self.n):
-                m[self.labels[q], r * self.n + q] = 1
+            for k in range(g):
+                for q in range(self.n):
+                    m[self.labels[q], r * g * self.n + k * self.n + q] = 1
         return m
 
     # -- Section IV-D: block phase -----------------------------------------

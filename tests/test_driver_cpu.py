@@ -21,8 +21,9 @@ _ORACLE_THREADS = oracle.max_threads()
 class OracleEvaluator:
     """(E, masked dE/dtheta) per row from the CPU oracle (tests only)."""
 
-    def __init__(self, n, reps, strings, coeffs, ent=0):
+    def __init__(self, n, reps, strings, coeffs, ent=0, gates=1):
         self.n, self.reps, self.strings, self.coeffs, self.ent = n, reps, list(strings), np.asarray(coeffs), ent
+        self.gates = gates
         self.batch_sizes = []
 
     def __call__(self, th, masks):
@@ -30,7 +31,7 @@ class OracleEvaluator:
         g = np.empty_like(th)
         oracle.set_threads(1)  # one thread: the same point always gives the same bits
         try:
-            with oracle.entangler(self.ent):
+            with oracle.entangler(self.ent), oracle.gates(self.gates):
                 for b in range(th.shape[0]):
                     eb, gb = oracle.energy_grad(self.n, self.reps, th[b], self.strings, self.coeffs)
                     e[b] = eb
@@ -162,3 +163,22 @@ def test_two_ranks_round_robin_and_hamiltonian_batching():
     assert np.array_equal(single, f0)
     e_full, _ = ev(single[None, :], None)
     assert e0 == pytest.approx(e_full[0], abs=1e-12 * ham.abs_sum())
+
+
+def test_full_efficient_su2_layers_in_the_driver():
+    """With the RY+RZ layer every block owns the RY and RZ angles of its qubits;
+    a short run lowers the energy."""
+    n, reps = 7, 1
+    ham = wl.chain_z_hamiltonian(n, 8 * n, seed=11)
+    cfg = GraphVQEConfig(reps=reps, gates=2, max_epochs=2, block_maxiter=15, global_maxiter=15)
+    ev = OracleEvaluator(n, reps, ham.strings, ham.coeffs, gates=2)
+    g = GraphVQE(ham, cfg, evaluator=ev)
+    m = g.block_masks()
+    assert m.shape == (g.n_blocks, 2 * n * (reps + 1)) and np.array_equal(m.sum(axis=0), np.ones(m.shape[1]))
+    for b in range(g.n_blocks):
+        qs = [q for q in range(n) if g.labels[q] == b]
+        want = sorted(r * 2 * n + k * n + q for r in range(reps + 1) for k in range(2) for q in qs)
+        assert list(np.nonzero(m[b])[0]) == want
+    th0 = np.random.default_rng(3).uniform(-np.pi, np.pi, 2 * n * (reps + 1))
+    r = g.run(th0)
+    assert r["E"] < r["E_start"]
