@@ -323,7 +323,8 @@ static long long tiles_of(int n, int tb) { return 1LL << (n - tb); }
 // |0...0> as ordinary passes (no analytic product state), every layer's passes
 // store their outputs for the backward sweep, and each backward pass writes
 // RY partial rows [0, tb) and RZ rows [tb, 2 tb).  Diagonal H only.
-static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_grad, int ent) {
+static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_grad, int ent, bool state_only) {
+  if (state_only) want_grad = false;
   Plan pl;
   const int nb = n + 1;
   pl.n = nb;
@@ -387,7 +388,7 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
       st.in = (r == 0 && j == 0) ? -1 : cur;
       const int out = want_grad ? first_state + r * p + j : ((j == 0) ? (cur == PP0 ? PP1 : PP0) : cur);
       st.A.store_mode = ST_PLAIN;
-      if (r == reps && j == p - 1 && !want_grad) {
+      if (r == reps && j == p - 1 && !want_grad && !state_only) {
         st.A.store_mode = ST_NONE;
         st.A.flags |= F_ENERGY;
         st.epart_region = poff;
@@ -400,6 +401,7 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
     }
   }
   if (!want_grad) {
+    if (state_only) pl.final_buf = cur;
     pl.part_stride = poff;
     return pl;
   }
@@ -451,7 +453,7 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0,
                 bool state_only, int ent, int gates) {
-  if (gates == 2) return build_plan_su2(n, reps, prec, tile_bits, want_grad, ent);
+  if (gates == 2) return build_plan_su2(n, reps, prec, tile_bits, want_grad, ent, state_only);
   Plan pl;
   pl.n = n;
   pl.reps = reps;
@@ -1205,7 +1207,6 @@ int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int fl
                  const double *uniforms, int64_t *shots, double *stats, int64_t *argmax, void *stream) {
   g_err.clear();
   if (!is_ansatz(a)) return fail(GVQE_EINVAL, "invalid ansatz handle");
-  if (a->gates != 1) return fail(GVQE_EUNSUPPORTED, "gvqe_readout takes the RY ansatz (GVQE_GATES_RY) only");
   if (!params || !stats || !argmax) return fail(GVQE_EINVAL, "params, stats and argmax must be device pointers");
   if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(GVQE_EINVAL, "alpha %g is outside [0, 1]", alpha);
   if (n_shots < 0 || (n_shots > 0 && (!uniforms || !shots)))
@@ -1231,9 +1232,16 @@ int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int fl
   const size_t o_edges = o_cdf + up(8 * (nch + 1)), o_mass = o_edges + up(8 * (RO_BINS + 1));
   const size_t o_ext = o_mass + up(8 * RO_BINS), o_part = o_ext + up(8 * 4);
   const size_t o_es = o_part + up(8 * 3 * (size_t)nparts);  // energies at the shots
-  const size_t total_bytes = o_es + up(8 * (size_t)std::max(n_shots, 1));
+  const size_t o_mod = o_es + up(8 * (size_t)std::max(n_shots, 1));
+  // complex path: the readout only needs |psi(x)|, taken once into a real array
+  const size_t total_bytes = o_mod + (a->gates == 2 ? up(((size_t)1 << n) * (prec ? 8 : 4)) : 0);
   GV_TRY(a->ro.reserve(total_bytes));
   char *w = (char *)a->ro.ptr;
+  if (a->gates == 2) {
+    GV_CUDA(launch_ro_modulus(prec, psi, n, w + o_mod, s));
+    count_launches(1);
+    psi = w + o_mod;
+  }
   double *csum = (double *)w, *cmax = (double *)(w + o_cmax), *cdf = (double *)(w + o_cdf);
   long long *cidx = (long long *)(w + o_cidx);
   unsigned long long *edges = (unsigned long long *)(w + o_edges);

@@ -236,6 +236,7 @@ int readout_chunk_bits(int n);
 int readout_tail_parts();
 // csum/cmax/cidx: [chunks], cdf: [chunks + 1]; writes stats[0] (largest p),
 // stats[2] (total) and argmax[0].
+cudaError_t launch_ro_modulus(int prec, const void *psi, int n, void *out, cudaStream_t s);
 cudaError_t launch_ro_prob(int prec, const void *psi, int n, double *csum, double *cmax, long long *cidx,
                            double *cdf, double *stats, long long *argmax, cudaStream_t s);
 cudaError_t launch_ro_sample(int prec, const void *psi, int n, const double *cdf, const double *u, int nshots,

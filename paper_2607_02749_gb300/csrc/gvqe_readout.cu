@@ -414,6 +414,26 @@ inline int ro_grid() { return num_sms_cached() * 4; }
 int readout_chunk_bits(int n) { return n < 13 ? n : 13; }
 int readout_tail_parts() { return ro_grid(); }
 
+// Complex path: out[x] = |psi(x)| from interleaved (re, im) amplitudes.
+template <typename T>
+__global__ void k_ro_modulus(const T *__restrict__ psi, long long N, T *__restrict__ out) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < N; x += (long long)gridDim.x * blockDim.x) {
+    const T re = __ldcg(psi + 2 * x), im = __ldcg(psi + 2 * x + 1);
+    out[x] = sqrt(re * re + im * im);
+  }
+}
+
+cudaError_t launch_ro_modulus(int prec, const void *psi, int n, void *out, cudaStream_t s) {
+  const long long N = 1LL << n;
+  const long long blocks = (N + RO_NT - 1) / RO_NT;
+  const unsigned g = (unsigned)(blocks < 65536 ? blocks : 65536);
+  if (prec)
+    k_ro_modulus<double><<<g, RO_NT, 0, s>>>((const double *)psi, N, (double *)out);
+  else
+    k_ro_modulus<float><<<g, RO_NT, 0, s>>>((const float *)psi, N, (float *)out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ro_prob(int prec, const void *psi, int n, double *csum, double *cmax, long long *cidx,
                            double *cdf, double *stats, long long *argmax, cudaStream_t s) {
   const int cb = readout_chunk_bits(n);

@@ -123,6 +123,32 @@ def test_unsupported_calls_refuse_the_complex_path():
     assert e.value.code == gv._lib.GVQE_EUNSUPPORTED
     hz = gv.Hamiltonian.from_workload(wl.z_hamiltonian(n, 30, seed=1))
     with pytest.raises(gv.GvqeError):
-        gv.readout(a, hz, t[0], alpha=0.2)
-    with pytest.raises(gv.GvqeError):
         gv.Batch([a], [hz])
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("n,reps", [(6, 2), (12, 1), (15, 2)])
+def test_readout_of_the_complex_state(n, reps, fp64):
+    from oracle import readout as ro
+
+    ham = wl.chain_z_hamiltonian(n, 10 * n, seed=n)
+    th = _thetas(n, reps, 1, seed=2 * n)[0]
+    with oracle.gates(oracle.GATES_RY_RZ):
+        p = ro.probabilities(oracle.state(n, reps, th))
+    e = ro.diagonal_energies(n, ham.strings, ham.coeffs)
+    a = gv.Ansatz(n, reps, gates=RYRZ)
+    h = gv.Hamiltonian.from_workload(ham)
+    tol = 1e-12 if fp64 else 2e-6
+    u = np.random.Generator(np.random.PCG64(0)).random(2048)
+    r = gv.readout(a, h, torch.as_tensor(th, device="cuda"), alpha=0.2,
+                   uniforms=torch.as_tensor(u, device="cuda"), fp64=fp64)
+    assert abs(r.total - 1.0) <= 4 * tol * (1 << n) ** 0.5 + 4 * tol
+    xo, po = ro.most_probable(p)
+    assert p[r.argmax] >= po - 8 * tol
+    assert abs(r.cvar - ro.cvar(p, e, 0.2)) <= (1e-10 if fp64 else 2e-5) * ham.abs_sum()
+    s = r.shots.cpu().numpy()
+    cdf = np.cumsum(p)
+    t = u * cdf[-1]
+    slack = 8 * tol * (1 << n) ** 0.5
+    lo = np.where(s > 0, cdf[np.maximum(s - 1, 0)], 0.0)
+    assert np.all(lo <= t + slack) and np.all(t < cdf[s] + slack)
