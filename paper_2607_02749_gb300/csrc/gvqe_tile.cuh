@@ -941,15 +941,31 @@ k_bwd(const PassArgs A) {
   const uint32_t cm = (1u << A.c) - 1;
 
   // copy one array of tile bx into shared tile dst (one commit group); warp w
-  // copies tile amplitudes [1024 w, 1024 w + 1024), the ones its rounds L and M read
+  // copies tile amplitudes [1024 w, 1024 w + 1024), the ones its rounds L and M read.
+  // Chunk m of the thread is tile index i0 + 32 CH m; the bits of m sit above
+  // i0's, and a tile index maps bitwise to its global offset, so the offset is
+  // go(i0) plus one per-pass weight per set bit of m (computed once here).
+  constexpr int IB = (CH == 4) ? 7 : 6;  // log2(32 CH): tile bit of m's bit 0
+  constexpr int MB = (CPT == 8) ? 3 : 4;  // bits of m
+  static_assert((1 << MB) == CPT && (32 * CH) == (1 << IB), "chunk layout");
+  const uint32_t i0 = (uint32_t)(lane * CH + 1024 * w);
+  const uint32_t g0 = FULL ? i0 : (i0 & cm) + ((i0 >> A.c) << A.a);
+  uint32_t wm[MB];
+#pragma unroll
+  for (int j = 0; j < MB; ++j) {
+    const int b = IB + j;
+    wm[j] = (FULL || b < A.c) ? (1u << b) : (1u << (A.a + b - A.c));
+  }
   auto issue = [&](const T *src, uint32_t bx, T *dst) {
     const uint32_t t = tile_of_block(bx, tiles, pair);
-    const uint32_t tbase = tile_base(t, A.c, A.a, TB);
+    const T *gb = src + (tile_base(t, A.c, A.a, TB) + g0);
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
-      const uint32_t i = (uint32_t)((lane + 32 * m) * CH + 1024 * w);
-      const uint32_t go = FULL ? tbase + i : tbase + (i & cm) + ((i >> A.c) << A.a);
-      cp_async16(dst + swz<T>((int)i), src + go);
+      uint32_t off = 0;
+#pragma unroll
+      for (int j = 0; j < MB; ++j)
+        if ((m >> j) & 1) off += wm[j];
+      cp_async16(dst + swz<T>((int)(i0 + (uint32_t)(32 * CH * m))), gb + off);
     }
     cp_async_commit();
   };
