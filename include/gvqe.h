@@ -77,9 +77,9 @@ extern "C" {
  *        qubit, RZ(t) = diag(exp(-i t/2), exp(+i t/2)); P = 2 n (reps+1), layer
  *        r's RY angle of qubit q at theta[2 r n + q] and its RZ angle at
  *        theta[2 r n + n + q].  Complex amplitudes (twice the memory and
- *        bandwidth); gvqe_energy, gvqe_energy_grad (diagonal, I/Z-only
- *        Hamiltonians) and gvqe_readout; batches and gvqe_energy_static
- *        return GVQE_EUNSUPPORTED. */
+ *        bandwidth; strings with an odd number of Y letters now contribute);
+ *        gvqe_energy, gvqe_energy_grad and gvqe_readout; batches and
+ *        gvqe_energy_static return GVQE_EUNSUPPORTED. */
 #define GVQE_GATES_RY 1
 #define GVQE_GATES_RY_RZ 2
 

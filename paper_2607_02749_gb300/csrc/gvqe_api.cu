@@ -323,8 +323,10 @@ static long long tiles_of(int n, int tb) { return 1LL << (n - tb); }
 // |0...0> as ordinary passes (no analytic product state), every layer's passes
 // store their outputs for the backward sweep, and each backward pass writes
 // RY partial rows [0, tb) and RZ rows [tb, 2 tb).  Diagonal H only.
-static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_grad, int ent, bool state_only) {
+static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, int ent,
+                           bool state_only) {
   if (state_only) want_grad = false;
+  if (state_only) diag = true;
   Plan pl;
   const int nb = n + 1;
   pl.n = nb;
@@ -388,7 +390,7 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
       st.in = (r == 0 && j == 0) ? -1 : cur;
       const int out = want_grad ? first_state + r * p + j : ((j == 0) ? (cur == PP0 ? PP1 : PP0) : cur);
       st.A.store_mode = ST_PLAIN;
-      if (r == reps && j == p - 1 && !want_grad && !state_only) {
+      if (r == reps && j == p - 1 && !want_grad && !state_only && diag) {
         st.A.store_mode = ST_NONE;
         st.A.flags |= F_ENERGY;
         st.epart_region = poff;
@@ -400,20 +402,37 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
       cur = out;
     }
   }
+  // X/Y groups: lambda = H psi (and the energy) by the complex X/Y kernel
+  int lam_cur = -1;
+  if (!diag) {
+    PassStep st;
+    st.A = base_args(K_LAMBDA_XY, pl.lp[0], reps);
+    st.A.tiles = std::max<long long>(1, (1LL << n) / XYC_AMPS_PER_CTA);
+    st.A.gate_mask = 0;
+    st.A.load_mode = LD_PLAIN;
+    st.A.flags |= F_ENERGY | (want_grad ? F_WRITE_LAMBDA : 0);
+    st.in = cur;
+    st.out = want_grad ? LAM0 : (cur == PP0 ? PP1 : PP0);
+    st.epart_region = poff;
+    st.xy = true;
+    pl.dir.push_back({poff, (int)st.A.tiles, -1});
+    poff += st.A.tiles;
+    pl.steps.push_back(st);
+    lam_cur = st.out;
+  }
   if (!want_grad) {
     if (state_only) pl.final_buf = cur;
     pl.part_stride = poff;
     return pl;
   }
   // ---------------- backward (every layer, layer 0 included)
-  int lam_cur = -1;
   for (int r = reps; r >= 0; --r) {
     for (int j = p - 1; j >= 0; --j) {
       const LayerPass &lp = pl.lp[j];
       PassStep st;
       st.A = base_args(K_BWD, lp, r);
       st.in = first_state + r * p + j;
-      if (r == reps && j == p - 1) {
+      if (r == reps && j == p - 1 && diag) {
         st.A.flags |= F_LAMBDA_INIT | F_ENERGY;
         st.epart_region = poff;
         pl.dir.push_back({poff, (int)st.A.tiles, -1});
@@ -453,7 +472,7 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0,
                 bool state_only, int ent, int gates) {
-  if (gates == 2) return build_plan_su2(n, reps, prec, tile_bits, want_grad, ent, state_only);
+  if (gates == 2) return build_plan_su2(n, reps, prec, tile_bits, want_grad, diag, ent, state_only);
   Plan pl;
   pl.n = n;
   pl.reps = reps;
@@ -711,6 +730,7 @@ using namespace gvqe;
 static int parse_hamiltonian(gvqe_hamiltonian_s *h, int n, int m, const char *pauli, const double *coeffs) {
   std::map<uint32_t, double> diag;
   std::map<uint32_t, std::map<uint32_t, double>> groups;
+  std::map<uint32_t, std::map<uint32_t, std::pair<double, double>>> cgroups;  // complex path
   h->n_dropped = 0;
   h->abs_sum = 0.0;
   for (int k = 0; k < m; ++k) {
@@ -731,6 +751,14 @@ static int parse_hamiltonian(gvqe_hamiltonian_s *h, int n, int m, const char *pa
     const double c = coeffs[k];
     if (!std::isfinite(c)) return fail(GVQE_EINVAL, "term %d: coefficient is not finite", k);
     h->abs_sum += std::fabs(c);
+    if (mx != 0) {  // i^ny = 1, i, -1, -i for ny = 0, 1, 2, 3 (mod 4)
+      auto &v = cgroups[mx][mz];
+      const int r4 = ny % 4;
+      if (r4 == 0) v.first += c;
+      if (r4 == 1) v.second += c;
+      if (r4 == 2) v.first -= c;
+      if (r4 == 3) v.second -= c;
+    }
     if (mx == 0) {
       diag[mz] += c;
     } else if (ny & 1) {
@@ -761,6 +789,21 @@ static int parse_hamiltonian(gvqe_hamiltonian_s *h, int n, int m, const char *pa
     }
   }
   h->gs.push_back((int)h->tz.size());
+  h->cgm.clear();
+  h->cgs.clear();
+  h->ctz.clear();
+  h->ctr.clear();
+  h->cti.clear();
+  for (auto &g : cgroups) {
+    h->cgm.push_back(g.first);
+    h->cgs.push_back((int)h->ctz.size());
+    for (auto &t : g.second) {
+      h->ctz.push_back(t.first);
+      h->ctr.push_back(t.second.first);
+      h->cti.push_back(t.second.second);
+    }
+  }
+  h->cgs.push_back((int)h->ctz.size());
   return GVQE_OK;
 }
 
@@ -815,14 +858,46 @@ static int build_table64(gvqe_hamiltonian_s *h, cudaStream_t s) {
 
 static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s, bool cplx = false) {
   GV_TRY(build_table64(h, s));
-  if (cplx && !h->TC[prec].ptr) {
-    const size_t S = (size_t)1 << h->n;
-    GV_TRY(h->TC[prec].reserve(S * 2 * (prec ? 8 : 4)));
-    GV_CUDA(launch_expand_table((const double *)h->T64.ptr, h->TC[prec].ptr, (long long)S, prec, s));
-    GV_CUDA(cudaStreamSynchronize(s));
+  if (cplx) {
+    if (!h->TC[prec].ptr) {
+      const size_t S = (size_t)1 << h->n;
+      GV_TRY(h->TC[prec].reserve(S * 2 * (prec ? 8 : 4)));
+      GV_CUDA(launch_expand_table((const double *)h->T64.ptr, h->TC[prec].ptr, (long long)S, prec, s));
+      GV_CUDA(cudaStreamSynchronize(s));
+    }
+    if (h->cgm.empty()) return GVQE_OK;
+    if (!prec && !h->T32.ptr) {  // the X/Y kernel reads the plain table
+      const size_t S = (size_t)1 << h->n;
+      GV_TRY(h->T32.reserve(S * 4));
+      GV_CUDA(launch_convert_table((const double *)h->T64.ptr, (float *)h->T32.ptr, (long long)S, s));
+      GV_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!h->CG.ptr) {
+      const size_t ng = h->cgm.size(), nt = h->ctz.size();
+      auto up = [](size_t b) { return (b + 15) / 16 * 16; };
+      const size_t o_gm = 0, o_gs = up(ng * 4), o_tz = o_gs + up((ng + 1) * 4);
+      const size_t o_r64 = o_tz + up(nt * 4), o_i64 = o_r64 + nt * 8, o_r32 = o_i64 + nt * 8;
+      const size_t o_i32 = o_r32 + up(nt * 4), total = o_i32 + up(nt * 4) + 16;
+      GV_TRY(h->CG.reserve(total));
+      char *b = (char *)h->CG.ptr;
+      std::vector<float> r32(h->ctr.begin(), h->ctr.end()), i32(h->cti.begin(), h->cti.end());
+      GV_CUDA(cudaMemcpy(b + o_gm, h->cgm.data(), ng * 4, cudaMemcpyHostToDevice));
+      GV_CUDA(cudaMemcpy(b + o_gs, h->cgs.data(), (ng + 1) * 4, cudaMemcpyHostToDevice));
+      GV_CUDA(cudaMemcpy(b + o_tz, h->ctz.data(), nt * 4, cudaMemcpyHostToDevice));
+      GV_CUDA(cudaMemcpy(b + o_r64, h->ctr.data(), nt * 8, cudaMemcpyHostToDevice));
+      GV_CUDA(cudaMemcpy(b + o_i64, h->cti.data(), nt * 8, cudaMemcpyHostToDevice));
+      GV_CUDA(cudaMemcpy(b + o_r32, r32.data(), nt * 4, cudaMemcpyHostToDevice));
+      GV_CUDA(cudaMemcpy(b + o_i32, i32.data(), nt * 4, cudaMemcpyHostToDevice));
+      h->d_cgm = (uint32_t *)(b + o_gm);
+      h->d_cgs = (int *)(b + o_gs);
+      h->d_ctz = (uint32_t *)(b + o_tz);
+      h->d_ctr[1] = b + o_r64;
+      h->d_cti[1] = b + o_i64;
+      h->d_ctr[0] = b + o_r32;
+      h->d_cti[0] = b + o_i32;
+    }
     return GVQE_OK;
   }
-  if (cplx) return GVQE_OK;
   if (!prec && !h->T32.ptr) {
     const size_t S = (size_t)1 << h->n;
     GV_TRY(h->T32.reserve(S * 4));
@@ -929,7 +1004,11 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
         continue;
       }
       // X-mask groups in chunks that fit in shared memory; the last chunk forms the energy.
-      const int ng = (int)h->gm.size();
+      // (the complex path uses its own groups, which keep odd-#Y strings, and the plain table)
+      if (cplx) A.table = prec ? h->T64.ptr : h->T32.ptr;
+      const std::vector<uint32_t> &gmv = cplx ? h->cgm : h->gm;
+      const std::vector<int> &gsv = cplx ? h->cgs : h->gs;
+      const int ng = (int)gmv.size();
       if (ng == 0) {
         A.ngroups = 0;
         A.gmask = nullptr;
@@ -942,17 +1021,19 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
       while (g0 < ng) {
         int g1 = g0;
         while (g1 < ng) {
-          const int nt = h->gs[g1 + 1] - h->gs[g0];
-          if (xy_smem_bytes(prec, g1 + 1 - g0, nt) > 160 * 1024) break;
+          const int nt = gsv[g1 + 1] - gsv[g0];
+          const size_t need = cplx ? xyc_smem_bytes(prec, g1 + 1 - g0, nt) : xy_smem_bytes(prec, g1 + 1 - g0, nt);
+          if (need > 160 * 1024) break;
           ++g1;
         }
         if (g1 == g0) return fail(GVQE_EUNSUPPORTED, "X-mask group %d has too many terms", g0);
         PassArgs B = A;
-        B.gmask = h->d_gm + g0;
-        B.gstart = h->d_gs + g0;
+        B.gmask = (cplx ? h->d_cgm : h->d_gm) + g0;
+        B.gstart = (cplx ? h->d_cgs : h->d_gs) + g0;
         B.ngroups = g1 - g0;
-        B.tz = h->d_tz;
-        B.tc = tc;
+        B.tz = cplx ? h->d_ctz : h->d_tz;
+        B.tc = cplx ? h->d_ctr[prec] : tc;
+        B.tci = cplx ? h->d_cti[prec] : nullptr;
         const bool last = (g1 == ng);
         B.flags = A.flags & ~(F_ENERGY | F_WRITE_LAMBDA | F_ACCUM);
         if (!first) B.flags |= F_ACCUM;
@@ -962,7 +1043,7 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
           if (!B.out) return fail(GVQE_EUNSUPPORTED, "chunked X-mask groups need a lambda buffer");
         }
         B.lam_in = B.out;  // chunks after the first accumulate onto lambda
-        const int nt = h->gs[g1] - h->gs[g0];
+        const int nt = gsv[g1] - gsv[g0];
         GV_CUDA(launch_step(prec, B, jobs, nt, s));
         first = false;
         g0 = g1;
@@ -989,10 +1070,8 @@ static int check_pair(gvqe_ansatz a, gvqe_hamiltonian h) {
 // energies (and optionally adjoint gradients) for a batch
 static int energy_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, int batch,
                        double *E, double *grad, int prec, cudaStream_t s) {
-  const bool diag = h->gm.empty();
   const bool cplx = a->gates == 2;
-  if (cplx && !diag)
-    return fail(GVQE_EUNSUPPORTED, "the RY+RZ (complex) ansatz takes diagonal Hamiltonians (I/Z letters) only");
+  const bool diag = cplx ? h->cgm.empty() : h->gm.empty();
   GV_TRY(ensure_tables(h, prec, s, cplx));
   Plan *pl = get_plan(a, prec, grad != nullptr, diag);
   const int P = pl->P;

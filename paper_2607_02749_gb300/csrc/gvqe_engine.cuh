@@ -185,6 +185,7 @@ struct PassArgs {
   int ngroups;
   const uint32_t *tz;
   const void *tc;
+  const void *tci;  // complex path: imaginary coefficient parts (i^#Y folded in)
 };
 
 // One output of the final reduction: the sum of `count` partials starting at
@@ -213,6 +214,9 @@ __host__ __device__ inline XyLayout xy_layout(int ngroups, int nterm, int elem) 
 // Host-side launchers (gvqe_kernels.cu).  prec: 0 = float, 1 = double.
 // nterm: number of terms of the X-mask group chunk (K_LAMBDA_XY only).
 cudaError_t launch_pass(int prec, const PassArgs &A, int jobs, int nterm, cudaStream_t s);
+// shared memory of one complex-path X/Y chunk (gvqe_kernels.cu); 1024 amplitudes per CTA
+size_t xyc_smem_bytes(int prec, int ngroups, int nterm);
+constexpr int XYC_AMPS_PER_CTA = 1024;
 // Shared memory of one K_LAMBDA_XY launch; at most ~200 KiB is accepted.
 size_t xy_smem_bytes(int prec, int ngroups, int nterm);
 cudaError_t launch_trig(int prec, const double *params, long long count, void *cs, cudaStream_t s);

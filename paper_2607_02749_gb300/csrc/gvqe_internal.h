@@ -85,6 +85,17 @@ struct gvqe_hamiltonian_s {
   std::vector<uint32_t> tz;
   std::vector<double> tc;
   int n_grouped = 0, n_dropped = 0;
+  // the complex path's X-mask groups: every string with X/Y letters, odd #Y
+  // included, with real and imaginary coefficient parts (i^#Y folded in)
+  std::vector<uint32_t> cgm;
+  std::vector<int> cgs;
+  std::vector<uint32_t> ctz;
+  std::vector<double> ctr, cti;
+  gvqe::DevBuf CG;
+  uint32_t *d_cgm = nullptr;
+  int *d_cgs = nullptr;
+  uint32_t *d_ctz = nullptr;
+  void *d_ctr[2] = {nullptr, nullptr}, *d_cti[2] = {nullptr, nullptr};  // FP32, FP64
   double abs_sum = 0.0;
   gvqe::DevBuf T64, T32, G;
   gvqe::DevBuf TC[2];  // complex path: each table entry twice (re/im), FP32 and FP64

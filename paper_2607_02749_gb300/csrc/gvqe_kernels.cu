@@ -439,8 +439,105 @@ int num_sms_cached() {
   return n;
 }
 
+// lambda = H psi for the X-mask groups on the complex path (amplitude y at
+// u[2y], u[2y + 1]; A.n counts the index bits, n + 1).  Group g flips mask
+// gmask[g]; each of its terms adds (tr + i ti) (-1)^popcount(u & tz) psi(u),
+// u = y ^ gmask[g], with i^#Y folded into (tr, ti).  The diagonal part comes
+// from the plain table E(y) (or lambda already written, F_ACCUM).  One CTA per
+// XYC_PER_CTA amplitudes; the energy partial Re sum conj(psi) lambda per CTA.
+constexpr int XYC_NT = 256;
+constexpr int XYC_PER_CTA = XYC_AMPS_PER_CTA;
+
+size_t xyc_smem_bytes(int prec, int ngroups, int nterm) {
+  const size_t es = prec ? 8 : 4;
+  auto up = [](size_t b) { return (b + 15) / 16 * 16; };
+  return up((size_t)ngroups * 4) + up((size_t)(ngroups + 1) * 4) + up((size_t)nterm * 4) + 2 * up((size_t)nterm * es);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(XYC_NT) k_lambda_xy_c(const PassArgs A) {
+  using T2 = typename V2<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double ered[XYC_NT / 32];
+  const int ng = A.ngroups;
+  const int t0 = ng > 0 ? A.gstart[0] : 0;
+  const int nterm = ng > 0 ? A.gstart[ng] - t0 : 0;
+  auto up = [](size_t b) { return (b + 15) / 16 * 16; };
+  uint32_t *sgm = reinterpret_cast<uint32_t *>(smem_raw);
+  int *sgs = reinterpret_cast<int *>(smem_raw + up((size_t)ng * 4));
+  uint32_t *stz = reinterpret_cast<uint32_t *>(smem_raw + up((size_t)ng * 4) + up((size_t)(ng + 1) * 4));
+  T *str = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(stz) + up((size_t)nterm * 4));
+  T *sti = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(str) + up((size_t)nterm * sizeof(T)));
+  const int tid = threadIdx.x;
+  for (int i = tid; i < ng; i += XYC_NT) sgm[i] = A.gmask[i];
+  for (int i = tid; i <= ng; i += XYC_NT) sgs[i] = A.gstart[i] - t0;
+  for (int i = tid; i < nterm; i += XYC_NT) {
+    stz[i] = A.tz[t0 + i];
+    str[i] = reinterpret_cast<const T *>(A.tc)[t0 + i];
+    sti[i] = reinterpret_cast<const T *>(A.tci)[t0 + i];
+  }
+  __syncthreads();
+  const int job = blockIdx.y;
+  const long long NQ = 1LL << (A.n - 1);
+  const T2 *in = reinterpret_cast<const T2 *>(A.in) + (size_t)job * (A.in_stride / 2);
+  const T2 *lin = reinterpret_cast<const T2 *>(A.lam_in) + (size_t)job * (A.lam_stride / 2);
+  T2 *out = reinterpret_cast<T2 *>(A.out) + (size_t)job * (A.out_stride / 2);
+  const T *table = reinterpret_cast<const T *>(A.table);
+  T eacc = T(0);
+  for (int k = 0; k < XYC_PER_CTA / XYC_NT; ++k) {
+    const long long y = (long long)blockIdx.x * XYC_PER_CTA + k * XYC_NT + tid;
+    if (y >= NQ) break;
+    const T2 p = __ldcg(in + y);
+    T2 acc;
+    if (A.flags & F_ACCUM) {
+      acc = lin[y];
+    } else {
+      const T e = table[y];
+      acc.x = e * p.x;
+      acc.y = e * p.y;
+    }
+    for (int g = 0; g < ng; ++g) {
+      const uint32_t u = (uint32_t)y ^ sgm[g];
+      const T2 pu = __ldcg(in + u);
+      T dr = T(0), di = T(0);
+      for (int j = sgs[g]; j < sgs[g + 1]; ++j) {
+        const bool neg = __popc(u & stz[j]) & 1;
+        dr += neg ? -str[j] : str[j];
+        di += neg ? -sti[j] : sti[j];
+      }
+      acc.x += dr * pu.x - di * pu.y;
+      acc.y += dr * pu.y + di * pu.x;
+    }
+    if (A.flags & F_WRITE_LAMBDA) out[y] = acc;
+    eacc += p.x * acc.x + p.y * acc.y;
+  }
+  if (A.flags & F_ENERGY) {
+    for (int o = 16; o > 0; o >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+    if ((tid & 31) == 0) ered[tid >> 5] = (double)eacc;
+    __syncthreads();
+    if (tid == 0) {
+      double e = 0.0;
+      for (int w = 0; w < XYC_NT / 32; ++w) e += ered[w];
+      A.epart[(size_t)job * A.part_stride + blockIdx.x] = e;
+    }
+  }
+}
+
 cudaError_t launch_pass(int prec, const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
   if (jobs < 1 || A.tiles < 1) return cudaErrorInvalidValue;
+  if (A.kind == K_LAMBDA_XY && (A.flags & F_COMPLEX)) {
+    const size_t smem = xyc_smem_bytes(prec, A.ngroups, nterm);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)A.tiles, (unsigned)jobs);
+    if (prec) {
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k_lambda_xy_c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_lambda_xy_c<double><<<grid, XYC_NT, smem, s>>>(A);
+    } else {
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k_lambda_xy_c<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_lambda_xy_c<float><<<grid, XYC_NT, smem, s>>>(A);
+    }
+    return cudaGetLastError();
+  }
   if (A.kind == K_GRAD_L0 && A.n > SMALL_MAXN) return launch_grad_l0(prec, A, jobs, s);
   return prec ? launch_typed<double>(A, jobs, nterm, s) : launch_typed<float>(A, jobs, nterm, s);
 }
