@@ -78,8 +78,8 @@ extern "C" {
  *        r's RY angle of qubit q at theta[2 r n + q] and its RZ angle at
  *        theta[2 r n + n + q].  Complex amplitudes (twice the memory and
  *        bandwidth; strings with an odd number of Y letters now contribute);
- *        gvqe_energy, gvqe_energy_grad and gvqe_readout; batches and
- *        gvqe_energy_static return GVQE_EUNSUPPORTED. */
+ *        every call but gvqe_energy_static (GVQE_EUNSUPPORTED); batches of
+ *        such instances run instance by instance. */
 #define GVQE_GATES_RY 1
 #define GVQE_GATES_RY_RZ 2
 

@@ -508,9 +508,9 @@ int gvqe_batch_create(int n_inst, const gvqe_ansatz *ansatze, const gvqe_hamilto
     if (!a || a->magic != MAGIC_ANSATZ) return fail(GVQE_EINVAL, "instance %d: invalid ansatz handle", i);
     if (!h || h->magic != MAGIC_HAM) return fail(GVQE_EINVAL, "instance %d: invalid Hamiltonian handle", i);
     if (a->n != h->n) return fail(GVQE_EINVAL, "instance %d: ansatz has %d qubits, Hamiltonian %d", i, a->n, h->n);
-    if (a->gates != 1) return fail(GVQE_EUNSUPPORTED, "instance %d: batches take the RY ansatz only", i);
-    // the persistent kernel runs one tile size and diagonal Hamiltonians
-    if (a->n < tile_bits_for(prec) || !h->gm.empty()) persistent = false;
+    // the persistent kernel runs one tile size, RY layers and diagonal Hamiltonians;
+    // other batches run instance by instance through the regular path
+    if (a->n < tile_bits_for(prec) || !h->gm.empty() || a->gates != 1) persistent = false;
   }
   for (int i = 0; i < n_inst; ++i) {
     const int rc = prepare_tables(hams[i], prec, nullptr);

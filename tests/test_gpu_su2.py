@@ -137,8 +137,23 @@ def test_unsupported_calls_refuse_the_complex_path():
     a = gv.Ansatz(n, 1, gates=RYRZ)
     t = torch.zeros((1, a.n_params), dtype=torch.float64, device="cuda")
     hz = gv.Hamiltonian.from_workload(wl.z_hamiltonian(n, 30, seed=1))
-    with pytest.raises(gv.GvqeError):
-        gv.Batch([a], [hz])
+    with pytest.raises(gv.GvqeError) as e:
+        gv._lib.gvqe_energy_static(a.handle, hz.handle, t, torch.empty(1, dtype=torch.float64, device="cuda"), 0, None)
+    assert e.value.code == gv._lib.GVQE_EUNSUPPORTED
+
+
+def test_batch_of_complex_instances():
+    insts = wl.cluster_batch(4, qubit_range=(10, 13), reps_range=(1, 2), terms_per_qubit=15)
+    ans = [gv.Ansatz(i.n_qubits, i.reps, gates=RYRZ) for i in insts]
+    hams = [gv.Hamiltonian.from_workload(i.ham) for i in insts]
+    b = gv.Batch(ans, hams, fp64=True)
+    params = [torch.as_tensor(_thetas(i.n_qubits, i.reps, 1, seed=k)[0], device="cuda") for k, i in enumerate(insts)]
+    grads = [torch.empty_like(p) for p in params]
+    e = b.run(params, grads=grads).cpu().numpy()
+    for k, i in enumerate(insts):
+        er, gr = _ref(i.n_qubits, i.reps, params[k].cpu().numpy()[None, :], i.ham)
+        assert abs(e[k] - er[0]) <= 1e-10 * i.ham.abs_sum()
+        assert np.max(np.abs(grads[k].cpu().numpy() - gr[0])) <= 1e-9 * i.ham.abs_sum()
 
 
 @pytest.mark.parametrize("fp64", [False, True])
