@@ -242,6 +242,18 @@ int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int fl
  * device work the handle enqueued before freeing its memory. */
 int gvqe_destroy(void *handle);
 
+/*
+ * gvqe_set_device_memory_limit -- a budget for the device memory this library
+ * holds in its workspaces (all handles of the process together); 0 removes it.
+ * A call that would exceed it fails with GVQE_ENOMEM and leaves every handle
+ * usable (a call over several parameter vectors first runs fewer of them per
+ * launch to fit).  Host only.
+ * gvqe_device_memory_in_use -- bytes held now.
+ * Errors: GVQE_EINVAL (bytes < 0).
+ */
+int gvqe_set_device_memory_limit(long long bytes);
+long long gvqe_device_memory_in_use(void);
+
 /* gvqe_last_error -- message of the last failing call on this thread ("" if none). */
 const char *gvqe_last_error(void);
 

@@ -78,6 +78,7 @@ _SIGS = {
     "gvqe_destroy": [_VP],
     "gvqe_plan_describe": [_I, _I, _I, _I, ctypes.c_char_p, _I],
     "gvqe_entangler_inverse": [_I, _I, _I, _VP, _VP, ctypes.c_longlong],
+    "gvqe_set_device_memory_limit": [ctypes.c_longlong],
     "gvqe_interaction_graph": [_I, _I, ctypes.c_char_p, _VP, _VP],
     "gvqe_partition": [_I, _VP, ctypes.c_double, _I, _VP, _VP, _VP],
     "gvqe_hamiltonian_stats": [_VP, _VP, _VP, _VP, _VP],
@@ -266,6 +267,18 @@ def gvqe_entangler_inverse(entangler: int, n_qubits: int, layer: int, y) -> "np.
     _check(load().gvqe_entangler_inverse(entangler, n_qubits, layer, ya.ctypes.data, xa.ctypes.data, ya.size),
            "gvqe_entangler_inverse")
     return xa
+
+
+def gvqe_set_device_memory_limit(limit_bytes: int) -> None:
+    """Budget for the library's device workspaces (0 = none); over it calls fail with GVQE_ENOMEM."""
+    _check(load().gvqe_set_device_memory_limit(int(limit_bytes)), "gvqe_set_device_memory_limit")
+
+
+def gvqe_device_memory_in_use() -> int:
+    lib = load()
+    lib.gvqe_device_memory_in_use.restype = ctypes.c_longlong
+    lib.gvqe_device_memory_in_use.argtypes = []
+    return int(lib.gvqe_device_memory_in_use())
 
 
 def gvqe_interaction_graph(n_qubits: int, strings, coeffs) -> "np.ndarray":

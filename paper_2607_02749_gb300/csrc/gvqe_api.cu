@@ -54,9 +54,23 @@ int fail(int code, const char *fmt, ...) {
   } while (0)
 
 // ------------------------------------------------------------ device memory --
+// Device bytes held by all workspaces of this process, and an optional budget
+// (gvqe_set_device_memory_limit) that reservations may not exceed.
+static std::atomic<long long> g_mem_used{0};
+static std::atomic<long long> g_mem_limit{0};
+
+static long long budget_left() {
+  const long long lim = g_mem_limit.load();
+  return lim > 0 ? std::max(0LL, lim - g_mem_used.load()) : -1;
+}
+
 int DevBuf::reserve(size_t need) {
   if (need <= bytes) return GVQE_OK;
   release();
+  const long long left = budget_left();
+  if (left >= 0 && (long long)need > left)
+    return fail(GVQE_ENOMEM, "device workspace of %.3f GiB exceeds the %.3f GiB left of the memory limit",
+                need / 1073741824.0, left / 1073741824.0);
   size_t freeb = 0, total = 0;
   GV_CUDA(cudaMemGetInfo(&freeb, &total));
   if (need > freeb)
@@ -69,11 +83,15 @@ int DevBuf::reserve(size_t need) {
     return fail(GVQE_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
   }
   bytes = need;
+  g_mem_used += (long long)need;
   return GVQE_OK;
 }
 
 void DevBuf::release() {
-  if (ptr) cudaFree(ptr);
+  if (ptr) {
+    cudaFree(ptr);
+    g_mem_used -= (long long)bytes;
+  }
   ptr = nullptr;
   bytes = 0;
 }
@@ -809,14 +827,28 @@ static int parse_hamiltonian(gvqe_hamiltonian_s *h, int n, int m, const char *pa
 
 // Build the FP64 diagonal table E(x) = sum_z chat[z] (-1)^popcount(x & z): scatter
 // the merged coefficients, then Walsh-Hadamard passes on the device.
+// A table built in steps: its buffer is released again unless the build
+// completes, so a failed call (say, over the memory limit) leaves no half-built
+// table behind for the next call to trust.
+struct PendingBuf {
+  DevBuf &b;
+  bool done = false;
+  explicit PendingBuf(DevBuf &x) : b(x) {}
+  ~PendingBuf() {
+    if (!done) b.release();
+  }
+};
+
 static int build_table64(gvqe_hamiltonian_s *h, cudaStream_t s) {
   if (h->T64.ptr) return GVQE_OK;
   const int n = h->n;
   const size_t S = (size_t)1 << n;
+  PendingBuf guard(h->T64);
   GV_TRY(h->T64.reserve(S * 8));
   GV_CUDA(cudaMemsetAsync(h->T64.ptr, 0, S * 8, s));
   if (!h->dz.empty()) {
     DevBuf tmp;
+    PendingBuf tmp_guard(tmp);  // always released
     const size_t cnt = h->dz.size();
     GV_TRY(tmp.reserve(cnt * (4 + 8)));
     uint32_t *dz = (uint32_t *)tmp.ptr;
@@ -849,10 +881,10 @@ static int build_table64(gvqe_hamiltonian_s *h, cudaStream_t s) {
       GV_CUDA(launch_step(1, A, 1, 0, s));
     }
     GV_CUDA(cudaStreamSynchronize(s));
-    tmp.release();
   } else {
     GV_CUDA(cudaStreamSynchronize(s));
   }
+  guard.done = true;
   return GVQE_OK;
 }
 
@@ -861,18 +893,23 @@ static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s, bool c
   if (cplx) {
     if (!h->TC[prec].ptr) {
       const size_t S = (size_t)1 << h->n;
+      PendingBuf guard(h->TC[prec]);
       GV_TRY(h->TC[prec].reserve(S * 2 * (prec ? 8 : 4)));
       GV_CUDA(launch_expand_table((const double *)h->T64.ptr, h->TC[prec].ptr, (long long)S, prec, s));
       GV_CUDA(cudaStreamSynchronize(s));
+      guard.done = true;
     }
     if (h->cgm.empty()) return GVQE_OK;
     if (!prec && !h->T32.ptr) {  // the X/Y kernel reads the plain table
       const size_t S = (size_t)1 << h->n;
+      PendingBuf guard(h->T32);
       GV_TRY(h->T32.reserve(S * 4));
       GV_CUDA(launch_convert_table((const double *)h->T64.ptr, (float *)h->T32.ptr, (long long)S, s));
       GV_CUDA(cudaStreamSynchronize(s));
+      guard.done = true;
     }
     if (!h->CG.ptr) {
+      PendingBuf guard(h->CG);
       const size_t ng = h->cgm.size(), nt = h->ctz.size();
       auto up = [](size_t b) { return (b + 15) / 16 * 16; };
       const size_t o_gm = 0, o_gs = up(ng * 4), o_tz = o_gs + up((ng + 1) * 4);
@@ -895,17 +932,21 @@ static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s, bool c
       h->d_cti[1] = b + o_i64;
       h->d_ctr[0] = b + o_r32;
       h->d_cti[0] = b + o_i32;
+      guard.done = true;
     }
     return GVQE_OK;
   }
   if (!prec && !h->T32.ptr) {
     const size_t S = (size_t)1 << h->n;
+    PendingBuf guard(h->T32);
     GV_TRY(h->T32.reserve(S * 4));
     GV_CUDA(launch_convert_table((const double *)h->T64.ptr, (float *)h->T32.ptr, (long long)S, s));
     GV_CUDA(cudaStreamSynchronize(s));
+    guard.done = true;
   }
   // X-mask group tables
   if (!h->gm.empty() && !h->G.ptr) {
+    PendingBuf guard(h->G);
     const size_t ng = h->gm.size(), nt = h->tz.size();
     const size_t o_gm = 0, o_gs = ((ng * 4 + 15) / 16) * 16;
     const size_t o_tz = o_gs + (((ng + 1) * 4 + 15) / 16) * 16;
@@ -925,6 +966,7 @@ static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s, bool c
     h->d_tz = (uint32_t *)(b + o_tz);
     h->d_tc64 = (double *)(b + o_t64);
     h->d_tc32 = (float *)(b + o_t32);
+    guard.done = true;
   }
   return GVQE_OK;
 }
@@ -963,7 +1005,9 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
   const size_t per_job = (size_t)pl->n_bufs * S * es + (size_t)pl->part_stride * 8;
   size_t freeb = 0, total = 0;
   GV_CUDA(cudaMemGetInfo(&freeb, &total));
-  const size_t have = freeb + a->ws.bytes;
+  size_t have = freeb + a->ws.bytes;
+  const long long left = budget_left();
+  if (left >= 0) have = std::min(have, (size_t)left + a->ws.bytes + ((size_t)512 << 20));
   const size_t budget = have > (size_t)512 << 20 ? have - ((size_t)512 << 20) : 0;
   if (per_job > budget)
     return fail(GVQE_ENOMEM, "one evaluation needs %.3f GiB of workspace, %.3f GiB available", per_job / 1073741824.0,
@@ -1153,6 +1197,15 @@ int gvqe_profile_reset(void) {
   }
   return GVQE_OK;
 }
+
+int gvqe_set_device_memory_limit(long long bytes) {
+  g_err.clear();
+  if (bytes < 0) return fail(GVQE_EINVAL, "limit %lld < 0", bytes);
+  g_mem_limit = bytes;
+  return GVQE_OK;
+}
+
+long long gvqe_device_memory_in_use(void) { return g_mem_used.load(); }
 
 int gvqe_version(void) { return 10000 * GVQE_VERSION_MAJOR + 100 * GVQE_VERSION_MINOR + GVQE_VERSION_PATCH; }
 

@@ -190,3 +190,12 @@ def test_gate_set_option():
         _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_GATES, 3)
     assert e.value.code == _lib.GVQE_EINVAL
     _lib.gvqe_destroy(a)
+
+
+def test_device_memory_limit_setter():
+    _lib.gvqe_set_device_memory_limit(1 << 30)
+    _lib.gvqe_set_device_memory_limit(0)
+    assert _lib.gvqe_device_memory_in_use() >= 0
+    with pytest.raises(_lib.GvqeError) as e:
+        _lib.gvqe_set_device_memory_limit(-1)
+    assert e.value.code == _lib.GVQE_EINVAL
