@@ -326,11 +326,17 @@ def su2_leg(n: int, reps: int, ham, steps: int):
     prof = {k: _lib.gvqe_profile_read(k) for k in range(2)}
     _lib.gvqe_profile_reset()
     names = {0: "k_fwd", 1: "k_bwd"}
+    peak, peak_src = measured_peaks()
+    per_kind = {}
+    for k in prof:
+        if not prof[k]["launches"]:
+            continue
+        gbps = prof[k]["bytes"] / (prof[k]["ms"] / 1000.0) / 1e9 if prof[k]["ms"] else 0.0
+        per_kind[names[k]] = {"launches": prof[k]["launches"], "ms": prof[k]["ms"], "GBps": gbps,
+                              "frac": gbps / peak if peak else None}
     out = {"value": 1.0 / dt, "unit": UNIT, "n_params": a.n_params, "E": float(e.item()),
            "amplitudes": "fp32 complex (2^(n+1) reals), fp64 table and reductions",
-           "per_kind": {names[k]: {"launches": prof[k]["launches"], "ms": prof[k]["ms"],
-                                   "GBps": prof[k]["bytes"] / (prof[k]["ms"] / 1000.0) / 1e9 if prof[k]["ms"] else 0.0}
-                        for k in prof if prof[k]["launches"]},
+           "per_kind": per_kind, "peak_GBps": peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
            "timing": "wall clock around synchronous single-vector gvqe_energy_grad calls (FP32 adjoint)"}
     a.close()
     h.close()

@@ -23,6 +23,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gvqe.h"
 #include "gvqe_engine.cuh"
 #include "gvqe_internal.h"
@@ -827,6 +829,12 @@ static int parse_hamiltonian(gvqe_hamiltonian_s *h, int n, int m, const char *pa
 
 // Build the FP64 diagonal table E(x) = sum_z chat[z] (-1)^popcount(x & z): scatter
 // the merged coefficients, then Walsh-Hadamard passes on the device.
+// An NVTX range around one public call (visible to Nsight tools; free otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 // A table built in steps: its buffer is released again unless the build
 // completes, so a failed call (say, over the memory limit) leaves no half-built
 // table behind for the next call to trust.
@@ -1305,6 +1313,7 @@ static int common_checks(gvqe_ansatz a, gvqe_hamiltonian h, const void *params, 
 int gvqe_energy(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int batch, double *energies, int flags,
                 void *stream) {
   g_err.clear();
+  NvtxRange range("gvqe_energy");
   GV_TRY(common_checks(a, h, params, batch, energies, flags));
   if (flags & GVQE_GRAD_PARAM_SHIFT) return fail(GVQE_EINVAL, "GVQE_GRAD_PARAM_SHIFT is a gradient flag");
   return energy_impl(a, h, params, nullptr, batch, energies, nullptr, flags & GVQE_FP64 ? 1 : 0,
@@ -1314,6 +1323,7 @@ int gvqe_energy(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int bat
 int gvqe_energy_grad(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, int batch,
                      double *energies, double *grad, int flags, void *stream) {
   g_err.clear();
+  NvtxRange range("gvqe_energy_grad");
   GV_TRY(common_checks(a, h, params, batch, energies, flags));
   if (!grad) return fail(GVQE_EINVAL, "grad is NULL");
   const int prec = flags & GVQE_FP64 ? 1 : 0;
@@ -1338,6 +1348,7 @@ static double key_to_double(unsigned long long k) {
 int gvqe_readout(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int flags, double alpha, int n_shots,
                  const double *uniforms, int64_t *shots, double *stats, int64_t *argmax, void *stream) {
   g_err.clear();
+  NvtxRange range("gvqe_readout");
   if (!is_ansatz(a)) return fail(GVQE_EINVAL, "invalid ansatz handle");
   if (!params || !stats || !argmax) return fail(GVQE_EINVAL, "params, stats and argmax must be device pointers");
   if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(GVQE_EINVAL, "alpha %g is outside [0, 1]", alpha);
