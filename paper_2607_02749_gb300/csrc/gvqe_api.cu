@@ -181,7 +181,7 @@ static void prof_drain() {
 
 // ---------------------------------------------------------------- planner --
 // 2^13 FP32 / 2^12 FP64 amplitudes per tile: a backward tile (psi + lambda) is
-// 64 KiB, so two CTAs share an SM, and n = 30 still takes three passes per layer.
+// 64 KiB, so three CTAs share an SM, and n = 30 still takes three passes per layer.
 int auto_tile_bits(int prec) { return prec ? 12 : 13; }
 
 std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits) {

@@ -397,14 +397,14 @@ __global__ void k_shift_combine(const double *__restrict__ Es, int P, int jobs, 
 }  // namespace
 
 // --------------------------------------------------------------- launchers --
-// The backward pass holds 3 rotating tiles in shared memory (227 KiB max):
-// 2^13 FP32 (96 KiB, two CTAs per SM) or 2^12 FP64 (96 KiB).
+// The backward pass holds two tiles in shared memory (psi and lambda), and three
+// CTAs share an SM: 2^13 FP32 or 2^12 FP64 amplitudes (64 KiB per CTA).
 int max_tile_bits(int prec) { return prec ? 12 : 13; }
 
 size_t pass_smem_bytes(int prec, int kind, int tb) {
   const size_t es = prec ? 8 : 4;
   if (tb < 10) return 0;
-  if (kind == K_BWD) return 3 * (es << tb);
+  if (kind == K_BWD) return 2 * (es << tb);
   if (kind == K_FWD || kind == K_WHT) return es << tb;
   return 0;
 }

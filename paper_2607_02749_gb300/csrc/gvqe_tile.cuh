@@ -23,6 +23,8 @@
 // FP64 in a fixed order (deterministic).
 #pragma once
 #include <cstdint>
+#include <mutex>
+#include <unordered_map>
 
 #include "gvqe_engine.cuh"
 
@@ -890,10 +892,13 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Persistent CTAs walk the tiles blockIdx.x, +gridDim.x, ...  Each CTA owns
-// three tile-sized shared buffers that rotate: tile k reads psi from P and
-// lambda from L while the next tile's psi streams into the free buffer F
-// (issued when tile k starts) and its lambda into P (issued once round H is
-// done with psi).  Two CTAs share an SM.
+// two tile-sized shared buffers, one for psi and one for lambda.  The next
+// tile's psi streams into the psi buffer once round H has read this tile's psi
+// (it overlaps the rest of the lambda rounds and the store), and each warp
+// refills its own part of the lambda buffer once its final round L has read it.
+// Three CTAs share an SM: against three buffers at two CTAs per SM the extra
+// warps hide more of the shared-memory round latency than the shorter lambda
+// prefetch exposes.
 //
 // lambda and psi are both at the point right after this pass's gates.  Rounds
 // L, M, H read both and form the gradients (all at that same point); round H
@@ -902,7 +907,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // first pass of a layer, layout FULL).  Gradient and energy partials are
 // written per tile.
 template <typename T, int TB, bool FULL, bool CPLX = false>
-__global__ void __launch_bounds__(1 << (TB - 5), (sizeof(T) == 4) ? 2 : 1)
+__global__ void __launch_bounds__(1 << (TB - 5), 3)
 k_bwd(const PassArgs A) {
   using T2 = typename V2<T>::type;
   constexpr int NT = 1 << (TB - 5);
@@ -912,7 +917,7 @@ k_bwd(const PassArgs A) {
   constexpr int CH = 16 / (int)sizeof(T);  // amplitudes per 16-byte chunk
   constexpr int CPT = TILE / CH / NT;      // chunks per thread per array
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *buf = reinterpret_cast<T *>(smem_raw);  // three rotating tiles
+  T *buf = reinterpret_cast<T *>(smem_raw);  // psi tile, lambda tile
   __shared__ GateTab<T2> gt;
   __shared__ double gred[2][NW][16];  // by tile parity: a warp may start the next
   __shared__ double ered[2][NW];      // tile while warp 0 still sums this one
@@ -971,11 +976,12 @@ k_bwd(const PassArgs A) {
   };
 
   uint32_t bx = blockIdx.x;
-  int P = 0, L = 1, F = 2;  // buffer roles
   int par = 0;              // tile parity (gred / ered)
+  T *const sp = buf;
+  T *const sl = buf + TILE;
   if (bx < tiles) {
-    issue(in, bx, buf + P * TILE);
-    issue(lsrc, bx, buf + L * TILE);
+    issue(in, bx, sp);
+    issue(lsrc, bx, sl);
   }
   __syncthreads();  // gate coefficients visible
   T2 pthr;
@@ -987,14 +993,8 @@ k_bwd(const PassArgs A) {
   for (; bx < tiles; bx += gridDim.x) {
     const uint32_t nbx = bx + gridDim.x;
     const bool more = nbx < tiles;
-    if (more)
-      issue(in, nbx, buf + F * TILE);  // next psi into the free buffer
-    else
-      cp_async_commit();
-    cp_async_wait<1>();  // this tile's psi and lambda have landed (this warp's part)
+    cp_async_wait<0>();  // this tile's psi and lambda have landed (this warp's part)
     __syncwarp();
-    T *sp = buf + P * TILE;
-    T *sl = buf + L * TILE;
     const uint32_t t = tile_of_block(bx, tiles, pair);
     GIdx<TB, FULL> gi;
     gi.init(tile_base(t, A.c, A.a, TB), A.c, A.a, lane, w, tid);
@@ -1035,10 +1035,7 @@ k_bwd(const PassArgs A) {
     round_gates<H, false, true, 2>(lam, gt, gm, 10, true);
     round_gates<1, false, true, 1>(lam, gt, gm, 5, true);
     __syncthreads();  // psi fully read; lambda may be overwritten
-    if (more)
-      issue(lsrc, nbx, sp);  // next lambda into the psi buffer
-    else
-      cp_async_commit();
+    if (more) issue(in, nbx, sp);  // next psi into the psi buffer
     sts_H<TB>(sl, sb, lam);
     __syncthreads();
     if (gm & 0x1Fu) {
@@ -1048,6 +1045,8 @@ k_bwd(const PassArgs A) {
       __syncwarp();  // M -> L stays inside the warp's 1024 amplitudes
     }
     lds_L(sl, sb, lam);
+    __syncwarp();  // every lane has read its lambda: only this warp reads its part
+    if (more) issue(lsrc, nbx, sl);  // next lambda into this warp's part of the lambda buffer
     round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
     // (the short closed forms compute each x from y: measured faster here than
     // the XOR walk, which the other forms take).  The complex path's layer 0
@@ -1099,15 +1098,9 @@ k_bwd(const PassArgs A) {
       for (int ww = 0; ww < NW; ++ww) e += ered[par][ww];
       A.epart[(size_t)job * A.part_stride + t] = e;
     }
-    // rotate: next psi is in F, next lambda in P, the lambda buffer becomes
-    // free.  Warp w refills only its own part of it, which only it still
-    // reads; gred / ered of this parity are rewritten two tiles later, after
-    // the next tile's round-H barrier, which warp 0 passes only after the sums above.
+    // gred / ered of this parity are rewritten two tiles later, after the next
+    // tile's round-H barrier, which warp 0 passes only after the sums above.
     par ^= 1;
-    const int nP = F, nL = P, nF = L;
-    P = nP;
-    L = nL;
-    F = nF;
   }
   cp_async_wait<0>();
 }
@@ -1456,6 +1449,35 @@ static cudaError_t launch_k(K k, dim3 grid, dim3 block, size_t smem, cudaStream_
   return cudaGetLastError();
 }
 
+// A persistent kernel: as many CTAs as are resident on the device at once
+// (the occupancy calculator's count per SM, cached per kernel), split over the
+// jobs, and never more than the tiles of one job.
+static cudaError_t launch_persistent(void (*k)(const PassArgs), int jobs, long long tiles, dim3 block, size_t smem,
+                                     cudaStream_t s, const PassArgs &A) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, int> per_sm_of;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = per_sm_of.find((const void *)k);
+    if (it != per_sm_of.end()) {
+      per_sm = it->second;
+    } else {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)block.x, smem);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      per_sm_of[(const void *)k] = per_sm;
+    }
+  }
+  long long ctas = (long long)num_sms() * per_sm / jobs;
+  if (ctas < 1) ctas = 1;
+  if (ctas > tiles) ctas = tiles;
+  k<<<dim3((unsigned)ctas, (unsigned)jobs), block, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
 template <typename T, int TB>
 cudaError_t launch_tb(const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
   const dim3 grid((unsigned)A.tiles, (unsigned)jobs);
@@ -1496,18 +1518,9 @@ cudaError_t launch_tb(const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
       const bool cplx = (A.flags & F_COMPLEX) != 0;
       if (!full && A.store_mode != ST_PLAIN) return cudaErrorInvalidValue;
       if (full && !cplx && A.store_mode != ST_SCATTER) return cudaErrorInvalidValue;
-      // persistent CTAs: as many as fit on the device at once, split over the jobs
-      const int per_sm = (sizeof(T) == 4) ? 2 : 1;
-      long long ctas = (long long)num_sms() * per_sm / jobs;
-      if (ctas < 1) ctas = 1;
-      if (ctas > A.tiles) ctas = A.tiles;
-      const dim3 pgrid((unsigned)ctas, (unsigned)jobs);
-      if (cplx) {
-        if (full) return launch_k(k_bwd<T, TB, true, true>, pgrid, block, 3 * tile, s, A);
-        return launch_k(k_bwd<T, TB, false, true>, pgrid, block, 3 * tile, s, A);
-      }
-      if (full) return launch_k(k_bwd<T, TB, true>, pgrid, block, 3 * tile, s, A);
-      return launch_k(k_bwd<T, TB, false>, pgrid, block, 3 * tile, s, A);
+      void (*k)(const PassArgs) = cplx ? (full ? k_bwd<T, TB, true, true> : k_bwd<T, TB, false, true>)
+                                       : (full ? k_bwd<T, TB, true> : k_bwd<T, TB, false>);
+      return launch_persistent(k, jobs, A.tiles, block, 2 * tile, s, A);
     }
     case K_LAMBDA_XY: {
       const size_t smem = xy_layout(A.ngroups, nterm, (int)sizeof(T)).total;
