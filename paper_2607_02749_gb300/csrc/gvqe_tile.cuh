@@ -1034,10 +1034,9 @@ k_bwd(const PassArgs A) {
     if constexpr (CPLX) apply_su2_phase<true>(lam, zt, pthr);
     round_gates<H, false, true, 2>(lam, gt, gm, 10, true);
     round_gates<1, false, true, 1>(lam, gt, gm, 5, true);
-    __syncthreads();  // psi fully read; lambda may be overwritten
+    sts_H<TB>(sl, sb, lam);  // the places this thread read
+    __syncthreads();  // psi fully read; lambda in round-H order written
     if (more) issue(in, nbx, sp);  // next psi into the psi buffer
-    sts_H<TB>(sl, sb, lam);
-    __syncthreads();
     if (gm & 0x1Fu) {
       lds_M(sl, tid, lam);
       round_gates<5, false>(lam, gt, gm, 0, true);
@@ -1163,25 +1162,25 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
     eacc = warp_sum(eacc);
     if (lane == 0) ered[w] = (double)eacc;
   }
-  __syncthreads();
+  __syncwarp();  // L -> M stays inside the warp's 1024 amplitudes
   if (gm & 0x1Fu) {
     lds_M(sp, tid, psi);
     lds_M(sl, tid, lam);
     round_grads<5>(psi, lam, gm, 0, gred[w], lane);
   }
+  __syncthreads();  // round H reads across warps, after every warp's round M
   lds_H<TB>(sp, sb, psi);
   lds_H<TB>(sl, sb, lam);
   round_grads<H, 2, true>(psi, lam, gm, 10, gred[w], lane);
   round_gates<H, false, true, 2>(lam, gt, gm, 10, true);
   round_gates<1, false, true, 1>(lam, gt, gm, 5, true);
-  __syncthreads();
-  sts_H<TB>(sl, sb, lam);
+  sts_H<TB>(sl, sb, lam);  // the places this thread read
   __syncthreads();
   if (gm & 0x1Fu) {
     lds_M(sl, tid, lam);
     round_gates<5, false>(lam, gt, gm, 0, true);
     sts_M(sl, tid, lam);
-    __syncthreads();
+    __syncwarp();  // M -> L stays inside the warp's 1024 amplitudes
   }
   lds_L(sl, sb, lam);
   round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
