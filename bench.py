@@ -100,14 +100,14 @@ def workload_sweeps(n: int, reps: int, n_terms: int):
     return gate_sweeps, n_terms
 
 
-def oracle_sample(n: int, reps: int, ham, n_gates: int = 2, n_terms: int = 2):
+def oracle_sample(n: int, reps: int, ham, n_gates: int = 2, n_terms: int = 2, single_thread: bool = False):
     """Time a bounded sample of the oracle on the full-size state and scale to one E+grad."""
     import oracle
 
     t_gate, t_term = oracle.sweep_times(n, n_gates, ham.strings[:n_terms], ham.coeffs[:n_terms])
     gs, ts = workload_sweeps(n, reps, ham.n_terms)
     sec = gs * t_gate + ts * t_term
-    return {
+    out = {
         "value": 1.0 / sec,
         "unit": UNIT,
         "cores": oracle.max_threads(),
@@ -116,6 +116,18 @@ def oracle_sample(n: int, reps: int, ham, n_gates: int = 2, n_terms: int = 2):
                    f"Pauli-term sweeps ({t_term:.3f} s each), scaled to one E+grad = {gs} gate sweeps + "
                    f"{ts} term sweeps = {sec:.0f} s"),
     }
+    if single_thread:  # the plain oracle on one core, same scaling
+        threads = oracle.max_threads()
+        oracle.set_threads(1)
+        try:
+            g1, t1 = oracle.sweep_times(n, 1, ham.strings[:1], ham.coeffs[:1])
+        finally:
+            oracle.set_threads(threads)
+        sec1 = gs * g1 + ts * t1
+        out["single_thread"] = {"value": 1.0 / sec1, "unit": UNIT, "cores": 1,
+                                "sample": f"1 RY sweep ({g1:.3f} s) and 1 Pauli-term sweep ({t1:.3f} s) on one "
+                                          f"core, scaled the same way = {sec1:.0f} s"}
+    return out
 
 
 class ClockSampler:
@@ -576,7 +588,7 @@ def run_gvqe(args):
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
-            out["cpu_baseline"] = oracle_sample(n, reps, ham)
+            out["cpu_baseline"] = oracle_sample(n, reps, ham, single_thread=True)
         except Exception as exc:  # pragma: no cover - host out of memory
             out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                                    "sample": f"failed: {exc}"}

@@ -70,6 +70,10 @@ extern "C" {
 /* options for gvqe_ansatz_set_option */
 #define GVQE_OPT_TILE_BITS 1 /* log2 amplitudes per on-chip tile, 10..13 (FP64: 10..12); 0 = auto (13 FP32, 12 FP64) */
 #define GVQE_OPT_GATES 2     /* rotation layer: GVQE_GATES_RY (default) or GVQE_GATES_RY_RZ */
+#define GVQE_OPT_SPLIT_PASSES 3 /* strided-pass bit layout: 0 auto, 1 never split, 2 always split (when a layer
+                                   takes two strided passes).  A split pass covers two runs of qubits, the low
+                                   and the top ones, so that no pass's tile spans more 2 MiB pages than needed;
+                                   results are the same up to the order of FP32/FP64 additions. */
 
 /* gate sets of a rotation layer (Eq. 8).
  * RY:    RY on every qubit; P = n (reps+1), theta[r*n + q]; real amplitudes.
@@ -264,6 +268,15 @@ const char *gvqe_last_error(void);
  * buflen).  Returns the number of passes per rotation layer, or a negative code.
  */
 int gvqe_plan_describe(int n_qubits, int reps, int flags, int tile_bits, char *buf, int buflen);
+
+/*
+ * gvqe_ansatz_describe -- the same text for the energy+gradient plan of an
+ * ansatz handle with its options (entangler, gate set, tile bits, split
+ * layout) at precision flags (GVQE_FP32 / GVQE_FP64).  Host only: builds (and
+ * caches) the plan, touches no device memory.  Returns the passes per rotation
+ * layer, or a negative code (GVQE_EINVAL for a bad handle or flags).
+ */
+int gvqe_ansatz_describe(gvqe_ansatz a, int flags, char *buf, int buflen);
 
 /*
  * gvqe_entangler_inverse -- basis-index map of one entangler layer (Section

@@ -13,7 +13,8 @@ from typing import Optional, Sequence
 from . import _lib
 from ._lib import (GVQE_GATES_RY, GVQE_GATES_RY_RZ, GVQE_ENT_CIRCULAR, GVQE_ENT_FULL, GVQE_ENT_LINEAR, GVQE_ENT_PAIRWISE, GVQE_ENT_REVERSE_LINEAR,
                    GVQE_ENT_SCA, GVQE_FP32, GVQE_FP64, GVQE_GRAD_ADJOINT, GVQE_GRAD_PARAM_SHIFT,
-                   GVQE_OPT_TILE_BITS, GvqeError, gvqe_ansatz_create, gvqe_ansatz_set_option, gvqe_batch_create,
+                   GVQE_OPT_SPLIT_PASSES, GVQE_OPT_TILE_BITS, GvqeError, gvqe_ansatz_create, gvqe_ansatz_describe,
+                   gvqe_ansatz_set_option, gvqe_batch_create,
                    gvqe_batch_run, gvqe_destroy, gvqe_energy, gvqe_energy_grad, gvqe_hamiltonian_create,
                    gvqe_entangler_inverse, gvqe_hamiltonian_stats, gvqe_interaction_graph, gvqe_last_error,
                    gvqe_partition, gvqe_plan_describe, gvqe_readout, gvqe_version)
@@ -26,7 +27,7 @@ __all__ = [
     "gvqe_hamiltonian_create", "gvqe_ansatz_create", "gvqe_ansatz_set_option", "gvqe_energy",
     "gvqe_energy_grad", "gvqe_batch_create", "gvqe_batch_run", "gvqe_destroy", "gvqe_last_error",
     "gvqe_plan_describe", "gvqe_hamiltonian_stats", "gvqe_readout", "gvqe_version", "gvqe_entangler_inverse",
-    "gvqe_interaction_graph", "gvqe_partition",
+    "gvqe_interaction_graph", "gvqe_partition", "gvqe_ansatz_describe", "GVQE_OPT_SPLIT_PASSES",
 ]
 
 
@@ -68,7 +69,7 @@ class Ansatz(_Handle):
     GVQE_ENT_PAIRWISE or GVQE_ENT_SCA (Section IV-B, Table 2)."""
 
     def __init__(self, n_qubits: int, reps: int, entangler: int = GVQE_ENT_LINEAR, tile_bits: int = 0,
-                 gates: int = _lib.GVQE_GATES_RY):
+                 gates: int = _lib.GVQE_GATES_RY, split: int = 0):
         self.n_qubits = n_qubits
         self.reps = reps
         self.entangler = entangler
@@ -79,9 +80,15 @@ class Ansatz(_Handle):
             gvqe_ansatz_set_option(self.handle, _lib.GVQE_OPT_GATES, gates)
         if tile_bits:
             gvqe_ansatz_set_option(self.handle, GVQE_OPT_TILE_BITS, tile_bits)
+        if split:
+            gvqe_ansatz_set_option(self.handle, GVQE_OPT_SPLIT_PASSES, split)
 
     def set_tile_bits(self, bits: int) -> None:
         gvqe_ansatz_set_option(self.handle, GVQE_OPT_TILE_BITS, bits)
+
+    def describe(self, fp64: bool = False) -> str:
+        """The tile-pass plan of this ansatz (host only)."""
+        return gvqe_ansatz_describe(self.handle, GVQE_FP64 if fp64 else GVQE_FP32)
 
 
 def _flags(fp64: bool, param_shift: bool = False) -> int:

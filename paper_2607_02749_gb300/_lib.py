@@ -33,6 +33,7 @@ GVQE_ENT_PAIRWISE = 4
 GVQE_ENT_SCA = 5
 GVQE_OPT_TILE_BITS = 1
 GVQE_OPT_GATES = 2
+GVQE_OPT_SPLIT_PASSES = 3
 GVQE_GATES_RY = 1
 GVQE_GATES_RY_RZ = 2
 GVQE_MAX_QUBITS = 30
@@ -77,6 +78,7 @@ _SIGS = {
     "gvqe_readout": [_VP, _VP, _VP, _I, ctypes.c_double, _I, _VP, _VP, _VP, _VP, _VP],
     "gvqe_destroy": [_VP],
     "gvqe_plan_describe": [_I, _I, _I, _I, ctypes.c_char_p, _I],
+    "gvqe_ansatz_describe": [_VP, _I, ctypes.c_char_p, _I],
     "gvqe_entangler_inverse": [_I, _I, _I, _VP, _VP, ctypes.c_longlong],
     "gvqe_set_device_memory_limit": [ctypes.c_longlong],
     "gvqe_interaction_graph": [_I, _I, ctypes.c_char_p, _VP, _VP],
@@ -255,6 +257,12 @@ def gvqe_destroy(handle: Optional[int]) -> None:
 def gvqe_plan_describe(n_qubits: int, reps: int, flags: int = GVQE_FP32, tile_bits: int = 0) -> str:
     buf = ctypes.create_string_buffer(1 << 16)
     _check(load().gvqe_plan_describe(n_qubits, reps, flags, tile_bits, buf, len(buf)), "gvqe_plan_describe")
+    return buf.value.decode()
+
+
+def gvqe_ansatz_describe(a: int, flags: int = GVQE_FP32) -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().gvqe_ansatz_describe(a, flags, buf, len(buf)), "gvqe_ansatz_describe")
     return buf.value.decode()
 
 

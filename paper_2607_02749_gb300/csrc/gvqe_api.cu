@@ -184,7 +184,7 @@ static void prof_drain() {
 // 64 KiB, so three CTAs share an SM, and n = 30 still takes three passes per layer.
 int auto_tile_bits(int prec) { return prec ? 12 : 13; }
 
-std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits) {
+std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits, int split) {
   std::vector<LayerPass> out;
   const int tbmax = tile_bits > 0 ? tile_bits : auto_tile_bits(prec);
   if (n <= tbmax) {
@@ -210,10 +210,50 @@ std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits) {
     out.push_back({c, a, tb, (uint32_t)(((1ull << g) - 1) << c)});
     a += g;
   }
+  // Two strided passes over [tb, n): the first takes [tb, tb + gA), the second
+  // the top bits.  A tile of the top pass touches one 2 MiB page per combination
+  // of its gate bits at or above index bit pb (stride >= 2 MiB); measured on
+  // GB300, a pass whose 64-byte runs spread over 512 such pages ran 1.8x slower
+  // than one over 8.  The split layout gives the first pass [tb, tb + x) and
+  // [n - y, n) and the second pass [tb + x, n - y), y chosen to balance the
+  // page bits of the two (auto: only when the top pass has more than 8).
+  if (chunks == 2 && split != SPLIT_NEVER) {
+    LayerPass &pa = out[1], &pb_ = out[2];
+    const int gA = tb - pa.c;
+    const int pb = prec ? 18 : 19;
+    auto pages = [&](int lo, int hi) { return std::max(0, hi - std::max(lo, pb)); };
+    const int top = pages(tb + gA, n);
+    int best_y = 0, best = std::max(pages(tb, tb + gA), top);
+    if (split == SPLIT_ALWAYS || top > 8) {
+      for (int y = 1; y < gA; ++y) {
+        const int x = gA - y;
+        const int m = std::max(pages(tb, tb + x) + pages(n - y, n), pages(tb + x, n - y));
+        if (m < best) {
+          best = m;
+          best_y = y;
+        }
+      }
+      if (best_y == 0 && split == SPLIT_ALWAYS && gA >= 2) best_y = gA / 2;
+    }
+    if (best_y > 0) {
+      const int x = gA - best_y;
+      pa.k1 = x;
+      pa.gap = (n - best_y) - (tb + x);
+      pb_.a = tb + x;
+    }
+  }
   return out;
 }
 
-static int qubit_of(const LayerPass &lp, int i) { return i < lp.c ? i : lp.a + i - lp.c; }
+static int qubit_of(const LayerPass &lp, int i) { return tile_gbit(i, lp.c, lp.a, lp.k1, lp.gap); }
+
+void set_pass_layout(PassArgs &A, const LayerPass &lp) {
+  A.tb = lp.tb;
+  A.c = lp.c;
+  A.a = lp.a;
+  A.k1 = lp.k1;
+  A.gap = lp.gap;
+}
 
 // ------------------------------------------------------------- entanglers --
 // The closed form of A^-1 for the entangler of layer r (1 .. reps).
@@ -344,7 +384,7 @@ static long long tiles_of(int n, int tb) { return 1LL << (n - tb); }
 // store their outputs for the backward sweep, and each backward pass writes
 // RY partial rows [0, tb) and RZ rows [tb, 2 tb).  Diagonal H only.
 static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, int ent,
-                           bool state_only) {
+                           bool state_only, int split) {
   if (state_only) want_grad = false;
   if (state_only) diag = true;
   Plan pl;
@@ -353,7 +393,7 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
   pl.reps = reps;
   pl.prec = prec;
   pl.P = 2 * n * (reps + 1);
-  pl.lp = layer_passes(nb, prec, tile_bits);
+  pl.lp = layer_passes(nb, prec, tile_bits, split);
   for (LayerPass &lp : pl.lp) lp.gmask &= ~1u;  // index bit 0 is the channel
   const int p = (int)pl.lp.size();
   const long long S = 1LL << nb;
@@ -369,9 +409,7 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
     A.qoff = 1;
     A.zoff = n;
     A.flags = F_COMPLEX;
-    A.tb = lp.tb;
-    A.c = lp.c;
-    A.a = lp.a;
+    set_pass_layout(A, lp);
     A.tiles = tiles_of(nb, lp.tb);
     A.gate_mask = lp.gmask;
     A.layer = r;
@@ -491,14 +529,14 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
 
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0,
-                bool state_only, int ent, int gates) {
-  if (gates == 2) return build_plan_su2(n, reps, prec, tile_bits, want_grad, diag, ent, state_only);
+                bool state_only, int ent, int gates, int split) {
+  if (gates == 2) return build_plan_su2(n, reps, prec, tile_bits, want_grad, diag, ent, state_only, split);
   Plan pl;
   pl.n = n;
   pl.reps = reps;
   pl.prec = prec;
   pl.P = n * (reps + 1);
-  pl.lp = layer_passes(n, prec, tile_bits);
+  pl.lp = layer_passes(n, prec, tile_bits, split);
   const int p = (int)pl.lp.size();
   const int tbA = pl.lp[0].tb;
   const long long S = 1LL << n;
@@ -514,9 +552,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
     return A;
   };
   auto set_layout = [&](PassArgs &A, const LayerPass &lp) {
-    A.tb = lp.tb;
-    A.c = lp.c;
-    A.a = lp.a;
+    set_pass_layout(A, lp);
     A.tiles = tiles_of(n, lp.tb);
   };
   // Buffer ids: stored pass outputs (gradient path) or a forward ping-pong
@@ -721,15 +757,22 @@ std::string describe_plan(const Plan &pl) {
   s += buf;
   for (size_t j = 0; j < pl.lp.size(); ++j) {
     const LayerPass &lp = pl.lp[j];
-    int qlo = -1, qhi = -1;
-    for (int i = 0; i < lp.tb; ++i)
-      if ((lp.gmask >> i) & 1u) {
-        const int q = qubit_of(lp, i);
-        if (qlo < 0) qlo = q;
-        qhi = q;
+    // gate bits as runs of consecutive index bits: [lo,hi] or [lo,hi]+[lo2,hi2] (split)
+    std::string runs;
+    int lo = -1, prev = -2;
+    for (int i = 0; i <= lp.tb; ++i) {
+      const int q = (i < lp.tb && ((lp.gmask >> i) & 1u)) ? qubit_of(lp, i) : -1;
+      if (lo >= 0 && q != prev + 1) {
+        snprintf(buf, sizeof(buf), "%s[%d,%d]", runs.empty() ? "" : "+", lo, prev);
+        runs += buf;
+        lo = -1;
       }
-    snprintf(buf, sizeof(buf), "  layer pass %zu: tile_bits=%d carry=%d high_start=%d qubits=[%d,%d] tiles=%lld\n", j,
-             lp.tb, lp.c, lp.a, qlo, qhi, tiles_of(pl.n, lp.tb));
+      if (q >= 0 && lo < 0) lo = q;
+      prev = q;
+    }
+    if (runs.empty()) runs = "[-1,-1]";
+    snprintf(buf, sizeof(buf), "  layer pass %zu: tile_bits=%d carry=%d high_start=%d qubits=%s split=%d,%d tiles=%lld\n",
+             j, lp.tb, lp.c, lp.a, runs.c_str(), lp.k1, lp.gap, tiles_of(pl.n, lp.tb));
     s += buf;
   }
   static const char *kinds[] = {"fwd", "bwd", "grad_l0", "lambda_xy", "wht"};
@@ -878,9 +921,7 @@ static int build_table64(gvqe_hamiltonian_s *h, cudaStream_t s) {
       A.load_mode = LD_PLAIN;
       A.store_mode = ST_PLAIN;
       A.n = n;
-      A.tb = lp.tb;
-      A.c = lp.c;
-      A.a = lp.a;
+      set_pass_layout(A, lp);
       A.tiles = 1LL << (n - lp.tb);
       A.gate_mask = lp.gmask;
       A.in = h->T64.ptr;
@@ -984,7 +1025,8 @@ static Plan *get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, boo
   const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0) | (state_only ? 8 : 0) | (a->gates == 2 ? 16 : 0);
   auto it = a->plans.find(key);
   if (it != a->plans.end() && it->second.tile_bits == a->tile_bits) return &it->second;
-  Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, want_grad, diag, false, state_only, a->ent, a->gates);
+  Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, want_grad, diag, false, state_only, a->ent, a->gates,
+                       a->split);
   pl.tile_bits = a->tile_bits;
   a->plans[key] = std::move(pl);
   return &a->plans[key];
@@ -1288,6 +1330,13 @@ int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
     a->plans.clear();
     return GVQE_OK;
   }
+  if (option == GVQE_OPT_SPLIT_PASSES) {
+    if (value < SPLIT_AUTO || value > SPLIT_ALWAYS)
+      return fail(GVQE_EINVAL, "split mode %d is not 0 (auto), 1 (never) or 2 (always)", value);
+    a->split = value;
+    a->plans.clear();
+    return GVQE_OK;
+  }
   if (option == GVQE_OPT_GATES) {
     if (value != GVQE_GATES_RY && value != GVQE_GATES_RY_RZ)
       return fail(GVQE_EINVAL, "gate set %d is not GVQE_GATES_RY or GVQE_GATES_RY_RZ", value);
@@ -1556,6 +1605,22 @@ int gvqe_plan_describe(int n_qubits, int reps, int flags, int tile_bits, char *b
     buf[m] = 0;
   }
   return (int)pl.lp.size();
+}
+
+int gvqe_ansatz_describe(gvqe_ansatz a, int flags, char *buf, int buflen) {
+  g_err.clear();
+  if (!is_ansatz(a)) return fail(GVQE_EINVAL, "invalid ansatz handle");
+  if (flags & ~GVQE_FP64) return fail(GVQE_EINVAL, "flags 0x%x: only GVQE_FP32 / GVQE_FP64 apply", flags);
+  const int prec = flags & GVQE_FP64 ? 1 : 0;
+  if (a->tile_bits > max_tile_bits(prec)) return fail(GVQE_EINVAL, "tile bits %d too large", a->tile_bits);
+  const Plan *pl = get_plan(a, prec, true, true);
+  const std::string s = describe_plan(*pl);
+  if (buf && buflen > 0) {
+    const size_t m = std::min<size_t>((size_t)buflen - 1, s.size());
+    memcpy(buf, s.data(), m);
+    buf[m] = 0;
+  }
+  return (int)pl->lp.size();
 }
 
 int gvqe_destroy(void *handle) {

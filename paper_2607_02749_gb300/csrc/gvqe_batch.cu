@@ -272,7 +272,8 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   const int ni = (int)b->a.size();
   sc.plans.clear();
   sc.plans.reserve(ni);
-  for (int i = 0; i < ni; ++i) sc.plans.push_back(build_plan(b->a[i]->n, b->a[i]->reps, prec, TB, want_grad != 0, true, true, false, b->a[i]->ent));
+  for (int i = 0; i < ni; ++i) sc.plans.push_back(build_plan(b->a[i]->n, b->a[i]->reps, prec, TB, want_grad != 0, true, true, false, b->a[i]->ent, 1,
+                                                 b->a[i]->split));
 
   // device layout: [steps][seg_start][seg_step][counters][io][per-instance workspace]
   std::vector<BatchStep> steps;

@@ -8,10 +8,12 @@
 // Work is organised in "tile passes".  A tile is 2^tb amplitudes whose index
 // bits are tile-local bits [0, c) -> global bits [0, c) (contiguous runs that
 // keep global accesses coalesced) and tile-local bits [c, tb) -> global bits
-// [a, a + tb - c).  The remaining global bits enumerate the tiles.  A pass
-// applies the RY gates of one layer on the qubits of its gate bits while the
-// tile sits on chip; an RY layer on n qubits takes one pass over bits
-// [0, tb) plus passes over the higher qubits.
+// [a, a + tb - c), or, split in two runs, [c, c + k1) -> [a, a + k1) and
+// [c + k1, tb) -> [a + k1 + gap, a + gap + tb - c) (gap = 0: one run).  The
+// remaining global bits enumerate the tiles.  A pass applies the RY gates of
+// one layer on the qubits of its gate bits while the tile sits on chip; an RY
+// layer on n qubits takes one pass over bits [0, tb) plus passes over the
+// higher qubits.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -136,6 +138,12 @@ __host__ __device__ inline uint32_t ent_inv(uint32_t y, uint32_t nmask, const En
   return (ent_inv_q(y >> e.sh, nmask >> e.sh, e, n - e.sh) << e.sh) | (y & low);
 }
 
+// Global bit of tile bit t under the (possibly split) strided layout; the
+// FULL layout is c = tb.
+__host__ __device__ inline int tile_gbit(int t, int c, int a, int k1, int gap) {
+  return t < c ? t : (t - c < k1 ? a + t - c : a + gap + t - c);
+}
+
 enum StoreMode : int {
   ST_PLAIN = 0,    // out[y] = v
   ST_SCATTER = 1,  // out[A^-1 y] = v: the inverse CX chain (adjoint of LD_GATHER)
@@ -154,6 +162,7 @@ enum PassFlags : int {
 struct PassArgs {
   int kind, load_mode, store_mode, flags;
   int n, tb, c, a;          // register size, tile bits and bit layout (see above)
+  int k1, gap;              // split layout: first-run length and the global bits skipped (0, 0: one run)
   uint32_t gate_mask;       // tile bits that carry a gate in this pass
   int layer;                // r: the RY parameter of tile bit i is p = r*pstride + qubit(i) - qoff
   int pstride;              // parameters per rotation layer (n, or 2n with RZ)

@@ -30,12 +30,17 @@ struct DevBuf {
   void release();
 };
 
-// One pass of an RY layer: tile bits [0,c) -> global [0,c), [c,tb) -> global [a, a+tb-c);
+// One pass of an RY layer: tile bits [0,c) -> global [0,c), [c,tb) -> global [a, a+tb-c)
+// or, split, [c, c+k1) -> [a, a+k1) and [c+k1, tb) -> [a+k1+gap, a+gap+tb-c);
 // gates on the tile bits in gmask.
 struct LayerPass {
   int c, a, tb;
   uint32_t gmask;
+  int k1 = 0, gap = 0;
 };
+
+// Strided-pass layout choice (GVQE_OPT_SPLIT_PASSES).
+enum SplitMode : int { SPLIT_AUTO = 0, SPLIT_NEVER = 1, SPLIT_ALWAYS = 2 };
 
 // One launch of a plan.  Buffer ids index the plan's state buffers (-1 = none).
 struct PassStep {
@@ -59,7 +64,8 @@ struct Plan {
   int d_dir_count = 0;
 };
 
-std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits);
+std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits, int split = SPLIT_AUTO);
+void set_pass_layout(PassArgs &A, const LayerPass &lp);
 void count_launches(int k);
 // tile_grad_l0: lay the layer-0 gradient partials out per tile (one CTA of
 // tile bits per partial), as the persistent batch kernel computes them,
@@ -68,7 +74,7 @@ void count_launches(int k);
 // gates: 1 = RY layers (real amplitudes), 2 = full EfficientSU2 layers, RY then
 // RZ on every qubit (complex amplitudes; diagonal H, energy and gradient only).
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false,
-                bool state_only = false, int ent = ENT_LINEAR, int gates = 1);
+                bool state_only = false, int ent = ENT_LINEAR, int gates = 1, int split = SPLIT_AUTO);
 std::string describe_plan(const Plan &pl);
 
 }  // namespace gvqe
@@ -111,6 +117,7 @@ struct gvqe_ansatz_s {
   int n = 0, reps = 0, ent = 0;
   int gates = 1;  // 1: RY layers; 2: RY then RZ (the complex path)
   int tile_bits = 0;  // 0 = automatic
+  int split = 0;      // gvqe::SplitMode
   std::map<int, gvqe::Plan> plans;
   gvqe::DevBuf ws, aux, shift, ro;
 };

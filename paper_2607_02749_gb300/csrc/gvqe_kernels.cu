@@ -71,7 +71,7 @@ __device__ __forceinline__ void load_coeffs(const PassArgs &A, const T2 *cs, T2 
     v.x = 1;
     v.y = 0;
     if (tid < A.tb && ((A.gate_mask >> tid) & 1u) && A.kind != K_WHT) {
-      const int q = tid < A.c ? tid : A.a + tid - A.c;
+      const int q = tile_gbit(tid, A.c, A.a, A.k1, A.gap);
       v = cs[A.layer * A.pstride + q - A.qoff];
     }
     gcs[tid] = v;

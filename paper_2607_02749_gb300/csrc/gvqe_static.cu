@@ -77,7 +77,7 @@ extern "C" int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const doubl
   cudaStream_t s = (cudaStream_t)stream;
 
   // The energy plan: forward passes with the energy fused into the last one.
-  const Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, false, true, false, false, a->ent);
+  const Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, false, true, false, false, a->ent, 1, a->split);
   const int n = a->n, P = pl.P;
   const size_t S = (size_t)1 << n;
   const size_t es = prec ? 8 : 4;
@@ -133,9 +133,7 @@ extern "C" int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const doubl
       A.load_mode = LD_PLAIN;
       A.store_mode = ST_PLAIN;
       A.n = n;
-      A.tb = lp.tb;
-      A.c = lp.c;
-      A.a = lp.a;
+      set_pass_layout(A, lp);
       A.tiles = 1LL << (n - lp.tb);
       A.gate_mask = lp.gmask;
       A.in = t64;

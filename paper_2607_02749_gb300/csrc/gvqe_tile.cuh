@@ -263,11 +263,15 @@ __device__ __forceinline__ uint32_t tile_of_block(uint32_t bx, uint32_t tiles, u
   return (bx & 1) ? (u ^ pair_mask) : u;
 }
 
-__device__ __forceinline__ uint32_t tile_base(uint32_t t, int c, int a, int tb) {
-  const int lo = a - c;
-  const uint32_t tlo = t & ((1u << lo) - 1);
-  const uint32_t thi = t >> lo;
-  return (tlo << c) | (thi << (a + tb - c));
+// Global offset of tile t: its index bits fill the global bits outside the
+// tile in increasing order, [c, a), then [a + k1, a + k1 + gap) (split layout),
+// then [a + gap + tb - c, n).
+__device__ __forceinline__ uint32_t tile_base(uint32_t t, const PassArgs &A, int tb) {
+  const int lo = A.a - A.c;
+  const uint32_t t0 = t & ((1u << lo) - 1);
+  const uint32_t tm = (t >> lo) & ((1u << A.gap) - 1);
+  const uint32_t th = t >> (lo + A.gap);
+  return (t0 << A.c) | (tm << (A.a + A.k1)) | (th << (A.a + A.gap + tb - A.c));
 }
 
 
@@ -279,7 +283,12 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // Global offset of a tile bit under the STRIDED layout.
-__device__ __forceinline__ uint32_t gbit(int t, int c, int a) { return 1u << (t < c ? t : a + t - c); }
+__device__ __forceinline__ uint32_t gbit(int t, const PassArgs &A) { return 1u << tile_gbit(t, A.c, A.a, A.k1, A.gap); }
+// Global offset (within its tile) of tile index i under the STRIDED layout.
+__device__ __forceinline__ uint32_t tile_goff(uint32_t i, const PassArgs &A) {
+  const uint32_t hi = i >> A.c;
+  return (i & ((1u << A.c) - 1)) + ((hi & ((1u << A.k1) - 1)) << A.a) + ((hi >> A.k1) << (A.a + A.k1 + A.gap));
+}
 
 // Gate coefficients of one pass, per tile bit: (cos, sin) and, for FP32, the
 // packed pairs (c,c), (s,s), (-s,-s) the f32x2 rotations take, built once per CTA.
@@ -563,22 +572,14 @@ struct GIdx {
   uint32_t SL[4];  // offset of pair-index bit j in round L (tile bit 6 + j)
   uint32_t baseH;  // offset of pair 0 in round H
   uint32_t SH[4];  // offset of pair-index bit j in round H (tile bit tbit_H(j))
-  uint32_t cm;
-  int c, a;
-  uint32_t tbase;
-  __device__ __forceinline__ uint32_t g(uint32_t i) const { return tbase + (i & cm) + ((i >> c) << a); }
-  __device__ __forceinline__ void init(uint32_t tb_, int c_, int a_, int lane, int w, int tid) {
-    tbase = tb_;
-    c = c_;
-    a = a_;
-    cm = (1u << c) - 1;
+  __device__ __forceinline__ void init(uint32_t tbase, const PassArgs &A, int lane, int w, int tid) {
     const uint32_t iL = (uint32_t)idx_L(lane, w, 0), iH = (uint32_t)idx_H_thread<TB>(tid);
-    baseL = FULL ? tbase + iL : g(iL);
-    baseH = FULL ? tbase + iH : g(iH);
+    baseL = tbase + (FULL ? iL : tile_goff(iL, A));
+    baseH = tbase + (FULL ? iH : tile_goff(iH, A));
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      SL[j] = FULL ? (1u << (6 + j)) : gbit(6 + j, c, a);
-      SH[j] = FULL ? (1u << tbit_H<TB>(j)) : gbit(tbit_H<TB>(j), c, a);
+      SL[j] = FULL ? (1u << (6 + j)) : gbit(6 + j, A);
+      SH[j] = FULL ? (1u << tbit_H<TB>(j)) : gbit(tbit_H<TB>(j), A);
     }
   }
 };
@@ -629,7 +630,7 @@ __device__ __forceinline__ void load_gate_coeffs(const PassArgs &A, const T2 *cs
     v.x = 1;
     v.y = 0;
     if (tid < A.tb && ((A.gate_mask >> tid) & 1u)) {
-      const int q = tid < A.c ? tid : A.a + tid - A.c;
+      const int q = tile_gbit(tid, A.c, A.a, A.k1, A.gap);
       v = cs[A.layer * A.pstride + q - A.qoff];
     }
     gcs[tid] = v;
@@ -673,7 +674,7 @@ struct SU2Tab {
       v.x = 1;
       v.y = 0;
       if (tb < A.tb && ((A.gate_mask >> tb) & 1u)) {
-        const int g = tb < A.c ? tb : A.a + tb - A.c;
+        const int g = tile_gbit(tb, A.c, A.a, A.k1, A.gap);
         v = cs[A.layer * A.pstride + A.zoff + g - A.qoff];
       }
       return v;
@@ -779,7 +780,7 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const SBase sb = sbase<TB, T>(tid);
   const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, A.pair_mask);
-  const uint32_t tbase = tile_base(t, A.c, A.a, TB);
+  const uint32_t tbase = tile_base(t, A, TB);
   const uint32_t nmask = (A.n >= 32) ? 0xffffffffu : ((1u << A.n) - 1);
   const uint32_t d1 = ent_inv(1u, nmask, A.em, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
@@ -797,7 +798,7 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
   const uint32_t gm = A.gate_mask;
   GIdx<TB, FULL> gi;
-  gi.init(tbase, A.c, A.a, lane, w, tid);
+  gi.init(tbase, A, lane, w, tid);
 
   Reg32<T> r;
   // round L: global -> registers (tile bits 6..9) -> gates -> shared.  The
@@ -943,7 +944,6 @@ k_bwd(const PassArgs A) {
   T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
   double *part = A.part + (size_t)job * A.part_stride;
   const uint32_t gm = A.gate_mask;
-  const uint32_t cm = (1u << A.c) - 1;
 
   // copy one array of tile bx into shared tile dst (one commit group); warp w
   // copies tile amplitudes [1024 w, 1024 w + 1024), the ones its rounds L and M read.
@@ -954,16 +954,15 @@ k_bwd(const PassArgs A) {
   constexpr int MB = (CPT == 8) ? 3 : 4;  // bits of m
   static_assert((1 << MB) == CPT && (32 * CH) == (1 << IB), "chunk layout");
   const uint32_t i0 = (uint32_t)(lane * CH + 1024 * w);
-  const uint32_t g0 = FULL ? i0 : (i0 & cm) + ((i0 >> A.c) << A.a);
+  const uint32_t g0 = FULL ? i0 : tile_goff(i0, A);
   uint32_t wm[MB];
 #pragma unroll
   for (int j = 0; j < MB; ++j) {
     const int b = IB + j;
-    wm[j] = (FULL || b < A.c) ? (1u << b) : (1u << (A.a + b - A.c));
+    wm[j] = FULL ? (1u << b) : gbit(b, A);
   }
-  auto issue = [&](const T *src, uint32_t bx, T *dst) {
-    const uint32_t t = tile_of_block(bx, tiles, pair);
-    const T *gb = src + (tile_base(t, A.c, A.a, TB) + g0);
+  auto issue = [&](const T *src, uint32_t base, T *dst) {
+    const T *gb = src + (base + g0);
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
       uint32_t off = 0;
@@ -979,10 +978,16 @@ k_bwd(const PassArgs A) {
   int par = 0;              // tile parity (gred / ered)
   T *const sp = buf;
   T *const sl = buf + TILE;
+  // this tile's index and global base; a thread's global offsets relative to
+  // the base are the same for every tile
+  uint32_t t = bx < tiles ? tile_of_block(bx, tiles, pair) : 0u;
+  uint32_t base = tile_base(t, A, TB);
   if (bx < tiles) {
-    issue(in, bx, sp);
-    issue(lsrc, bx, sl);
+    issue(in, base, sp);
+    issue(lsrc, base, sl);
   }
+  GIdx<TB, FULL> grel;
+  grel.init(0u, A, lane, w, tid);
   __syncthreads();  // gate coefficients visible
   T2 pthr;
   const T2 *zf = nullptr;
@@ -993,11 +998,13 @@ k_bwd(const PassArgs A) {
   for (; bx < tiles; bx += gridDim.x) {
     const uint32_t nbx = bx + gridDim.x;
     const bool more = nbx < tiles;
+    const uint32_t nt = more ? tile_of_block(nbx, tiles, pair) : 0u;
+    const uint32_t nbase = more ? tile_base(nt, A, TB) : 0u;
     cp_async_wait<0>();  // this tile's psi and lambda have landed (this warp's part)
     __syncwarp();
-    const uint32_t t = tile_of_block(bx, tiles, pair);
-    GIdx<TB, FULL> gi;
-    gi.init(tile_base(t, A.c, A.a, TB), A.c, A.a, lane, w, tid);
+    GIdx<TB, FULL> gi = grel;
+    gi.baseL += base;
+    gi.baseH += base;
 
     Reg32<T> psi, lam;
     // round L (from shared)
@@ -1036,7 +1043,7 @@ k_bwd(const PassArgs A) {
     round_gates<1, false, true, 1>(lam, gt, gm, 5, true);
     sts_H<TB>(sl, sb, lam);  // the places this thread read
     __syncthreads();  // psi fully read; lambda in round-H order written
-    if (more) issue(in, nbx, sp);  // next psi into the psi buffer
+    if (more) issue(in, nbase, sp);  // next psi into the psi buffer
     if (gm & 0x1Fu) {
       lds_M(sl, tid, lam);
       round_gates<5, false>(lam, gt, gm, 0, true);
@@ -1045,7 +1052,7 @@ k_bwd(const PassArgs A) {
     }
     lds_L(sl, sb, lam);
     __syncwarp();  // every lane has read its lambda: only this warp reads its part
-    if (more) issue(lsrc, nbx, sl);  // next lambda into this warp's part of the lambda buffer
+    if (more) issue(lsrc, nbase, sl);  // next lambda into this warp's part of the lambda buffer
     round_gates<4, false, true, 1>(lam, gt, gm, 6, true);
     // (the short closed forms compute each x from y: measured faster here than
     // the XOR walk, which the other forms take).  The complex path's layer 0
@@ -1100,6 +1107,8 @@ k_bwd(const PassArgs A) {
     // gred / ered of this parity are rewritten two tiles later, after the next
     // tile's round-H barrier, which warp 0 passes only after the sums above.
     par ^= 1;
+    t = nt;
+    base = nbase;
   }
   cp_async_wait<0>();
 }
@@ -1124,7 +1133,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const SBase sb = sbase<TB, T>(tid);
   const uint32_t t = tile_of_block(tb_idx, (uint32_t)A.tiles, A.pair_mask);
-  const uint32_t tbase = tile_base(t, A.c, A.a, TB);
+  const uint32_t tbase = tile_base(t, A, TB);
   const uint32_t nmask = (1u << A.n) - 1;
   const uint32_t d1 = ent_inv(1u, nmask, A.em, A.n);  // the pair (y, y + 1) maps to (x, x ^ d1)
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
@@ -1138,7 +1147,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   const uint32_t gm = A.gate_mask;
   const bool init = (A.flags & F_LAMBDA_INIT) != 0;
   GIdx<TB, FULL> gi;
-  gi.init(tbase, A.c, A.a, lane, w, tid);
+  gi.init(tbase, A, lane, w, tid);
 
   Reg32<T> psi, lam;
   T eacc = T(0);

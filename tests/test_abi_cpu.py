@@ -99,9 +99,13 @@ def test_tile_bits_option_validation():
 
 
 def _layer_passes(text):
+    """(tile bits, carry, high start, [qubits of the pass's gates]) per layer pass."""
     out = []
-    for m in re.finditer(r"layer pass \d+: tile_bits=(\d+) carry=(\d+) high_start=(\d+) qubits=\[(\d+),(\d+)\]", text):
-        out.append(tuple(int(x) for x in m.groups()))
+    for m in re.finditer(r"layer pass \d+: tile_bits=(\d+) carry=(\d+) high_start=(\d+) qubits=(\S+)", text):
+        qs = []
+        for lo, hi in re.findall(r"\[(-?\d+),(-?\d+)\]", m.group(4)):
+            qs.extend(range(int(lo), int(hi) + 1))
+        out.append((int(m.group(1)), int(m.group(2)), int(m.group(3)), qs))
     return out
 
 
@@ -114,8 +118,8 @@ def test_plan_covers_every_qubit_once(n, flags, tb, expect):
     passes = _layer_passes(text)
     assert len(passes) == expect
     covered = []
-    for tbits, carry, start, qlo, qhi in passes:
-        covered.extend(range(qlo, qhi + 1))
+    for tbits, carry, start, qs in passes:
+        covered.extend(qs)
         assert carry >= min(3 if flags else 4, tbits) or carry == tbits
     assert sorted(covered) == list(range(n))
 
@@ -199,3 +203,43 @@ def test_device_memory_limit_setter():
     with pytest.raises(_lib.GvqeError) as e:
         _lib.gvqe_set_device_memory_limit(-1)
     assert e.value.code == _lib.GVQE_EINVAL
+
+
+def test_split_layout_option_and_plans():
+    """GVQE_OPT_SPLIT_PASSES: auto splits only where the top strided pass would
+    span more than 2^8 large pages (n = 30 RY+RZ in FP32, n = 30 RY in FP64), never
+    keeps one run per pass, always splits any layer with two strided passes; the
+    split qubit runs still cover every qubit once."""
+    import re
+
+    import paper_2607_02749_gb300 as gv
+
+    def runs(a, fp64=False):
+        d = a.describe(fp64=fp64)
+        out = []
+        for m in re.finditer(r"carry=(\d+) high_start=(\d+) qubits=\S+ split=(\d+),(\d+)", d):
+            out.append(tuple(map(int, m.groups())))
+        return d, out
+
+    _, r = runs(gv.Ansatz(30, 6))
+    assert all(k1 == 0 and gap == 0 for _, _, k1, gap in r)  # FP32 RY: top pass spans 2^8 pages
+    _, r = runs(gv.Ansatz(30, 6), fp64=True)
+    assert r[1][2:] == (3, 9) and r[2][1] == 15
+    _, r = runs(gv.Ansatz(30, 6, gates=gv.GVQE_GATES_RY_RZ))
+    assert r[1][2:] == (3, 9) and r[2][1] == 16
+    _, r = runs(gv.Ansatz(30, 6, gates=gv.GVQE_GATES_RY_RZ, split=1))
+    assert all(k1 == 0 and gap == 0 for _, _, k1, gap in r)
+    d, r = runs(gv.Ansatz(17, 2, tile_bits=10, split=2))
+    assert r[1][2] > 0
+    # every qubit is a gate bit of exactly one pass of the layer
+    c1, a1, k1, gap = r[1]
+    first = list(range(a1, a1 + k1)) + list(range(a1 + k1 + gap, a1 + gap + 10 - c1))
+    c2, a2, _, _ = r[2]
+    second = list(range(a2, a2 + 10 - c2))
+    assert sorted(list(range(10)) + first + second) == list(range(17))
+    assert [p[3] for p in _layer_passes(d)] == [list(range(10)), first, second]
+    a = gv.Ansatz(12, 1)
+    for bad in (-1, 3):
+        with pytest.raises(gv.GvqeError) as e:
+            gv.gvqe_ansatz_set_option(a.handle, gv.GVQE_OPT_SPLIT_PASSES, bad)
+        assert e.value.code == gv._lib.GVQE_EINVAL
