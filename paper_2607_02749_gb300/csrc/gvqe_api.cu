@@ -212,29 +212,25 @@ std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits, int split) {
   }
   // Two strided passes over [tb, n): the first takes [tb, tb + gA), the second
   // the top bits.  A tile of the top pass touches one 2 MiB page per combination
-  // of its gate bits at or above index bit pb (stride >= 2 MiB); measured on
-  // GB300, a pass whose 64-byte runs spread over 512 such pages ran 1.8x slower
-  // than one over 8.  The split layout gives the first pass [tb, tb + x) and
-  // [n - y, n) and the second pass [tb + x, n - y), y chosen to balance the
-  // page bits of the two (auto: only when the top pass has more than 8).
+  // of its gate bits at or above index bit pb (stride >= 2 MiB).  Measured on
+  // GB300: with 64-byte runs, a top pass over 2^9 such pages ran 1.8x slower than
+  // a pass over the middle qubits, while 2^8 pages at the top ran at full speed.
+  // The split layout gives the first pass [tb, tb + x) and [n - y, n) and the
+  // second pass [tb + x, n - y).  Auto, when the top pass would span more than
+  // 2^8 pages: the fewest top qubits y that bring the second pass down to 2^8
+  // (at n = 30 RY+RZ, y = 4 and 5 measured best, 6 and 3 about 4% slower).
   if (chunks == 2 && split != SPLIT_NEVER) {
     LayerPass &pa = out[1], &pb_ = out[2];
     const int gA = tb - pa.c;
     const int pb = prec ? 18 : 19;
     auto pages = [&](int lo, int hi) { return std::max(0, hi - std::max(lo, pb)); };
     const int top = pages(tb + gA, n);
-    int best_y = 0, best = std::max(pages(tb, tb + gA), top);
-    if (split == SPLIT_ALWAYS || top > 8) {
-      for (int y = 1; y < gA; ++y) {
-        const int x = gA - y;
-        const int m = std::max(pages(tb, tb + x) + pages(n - y, n), pages(tb + x, n - y));
-        if (m < best) {
-          best = m;
-          best_y = y;
-        }
-      }
-      if (best_y == 0 && split == SPLIT_ALWAYS && gA >= 2) best_y = gA / 2;
+    int best_y = 0;
+    if (top > 8) {
+      for (int y = 1; y < gA && best_y == 0; ++y)
+        if (pages(tb + gA - y, n - y) <= 8) best_y = y;
     }
+    if (best_y == 0 && split == SPLIT_ALWAYS && gA >= 2) best_y = gA / 2;
     if (best_y > 0) {
       const int x = gA - best_y;
       pa.k1 = x;

@@ -224,9 +224,9 @@ def test_split_layout_option_and_plans():
     _, r = runs(gv.Ansatz(30, 6))
     assert all(k1 == 0 and gap == 0 for _, _, k1, gap in r)  # FP32 RY: top pass spans 2^8 pages
     _, r = runs(gv.Ansatz(30, 6), fp64=True)
-    assert r[1][2:] == (3, 9) and r[2][1] == 15
+    assert r[1][2:] == (5, 9) and r[2][1] == 17  # [12,17) + [26,30), then [17,26)
     _, r = runs(gv.Ansatz(30, 6, gates=gv.GVQE_GATES_RY_RZ))
-    assert r[1][2:] == (3, 9) and r[2][1] == 16
+    assert r[1][2:] == (5, 9) and r[2][1] == 18  # [13,18) + [27,31), then [18,27)
     _, r = runs(gv.Ansatz(30, 6, gates=gv.GVQE_GATES_RY_RZ, split=1))
     assert all(k1 == 0 and gap == 0 for _, _, k1, gap in r)
     d, r = runs(gv.Ansatz(17, 2, tile_bits=10, split=2))
