@@ -1,5 +1,5 @@
 """Full-size checks at n = 30 (the benchmark's launch configuration: three
-2^14-amplitude tile passes per layer), where the CPU oracle cannot run.
+2^13-amplitude tile passes per layer), where the CPU oracle cannot run.
 
 Pinned by properties that hold at any size:
   * reps = 0: product-state closed form (energy and every gradient entry);
@@ -122,3 +122,62 @@ def test_fp32_matches_fp64_at_benchmark_size(ham20k):
     gps = gps[0].cpu().numpy()
     for p in (17, P - 5):
         assert abs(gps[p] - g64[p]) <= 1e-9 * scale
+
+
+def _split_first_strided_pass(a, fp64=False):
+    import re
+
+    runs = re.findall(r"split=(\d+),(\d+)", a.describe(fp64=fp64))
+    return int(runs[1][0]) > 0
+
+
+def test_su2_split_layout_at_n30_with_zero_rz_is_the_ry_ansatz(ham20k):
+    """n = 30 RY+RZ takes the split strided layout (31 index bits); with every
+    RZ angle 0 it must reproduce the RY ansatz (one run per pass) exactly in
+    structure: the same energy and RY gradients within the FP32 bound, RZ
+    gradients 0 (the amplitudes stay real, so Im<lam|Z|psi> vanishes)."""
+    reps = 2
+    h = gv.Hamiltonian.from_workload(ham20k)
+    ty = wl.thetas(N, reps, 1, seed=3)[0].reshape(reps + 1, N)
+    a1 = gv.Ansatz(N, reps)
+    assert not _split_first_strided_pass(a1)
+    e1, g1 = gv.energy_grad(a1, h, _dev(ty.reshape(1, -1)))
+    e1, g1 = e1.item(), g1[0].cpu().numpy().reshape(reps + 1, N)
+    a1.close()
+    a2 = gv.Ansatz(N, reps, gates=gv.GVQE_GATES_RY_RZ)
+    assert _split_first_strided_pass(a2)
+    th2 = np.concatenate([np.concatenate([ty[r], np.zeros(N)]) for r in range(reps + 1)])[None, :]
+    e2, g2 = gv.energy_grad(a2, h, _dev(th2))
+    e2, g2 = e2.item(), g2[0].cpu().numpy().reshape(reps + 1, 2, N)
+    a2.close()
+    scale = ham20k.abs_sum()
+    assert abs(e2 - e1) <= 2e-5 * scale
+    assert np.linalg.norm(g2[:, 0, :] - g1) <= 1e-4 * np.linalg.norm(g1)
+    assert np.max(np.abs(g2[:, 1, :])) <= 1e-9 * scale
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_su2_reps0_closed_form_at_n30(ham20k, fp64):
+    """reps = 0 RY+RZ at n = 30 (FP32: split layout; FP64: three strided passes
+    of 2^12 tiles): the Bloch-vector product form gives the energy, and its
+    central differences sampled gradient entries."""
+    a = gv.Ansatz(N, 0, gates=gv.GVQE_GATES_RY_RZ)
+    assert _split_first_strided_pass(a, fp64) == (not fp64)
+    h = gv.Hamiltonian.from_workload(ham20k)
+    th = np.random.default_rng(5).uniform(-np.pi, np.pi, 2 * N)
+    e, g = gv.energy_grad(a, h, _dev(th[None, :]), fp64=fp64)
+    e, g = e.item(), g[0].cpu().numpy()
+    a.close()
+    scale = ham20k.abs_sum()
+
+    def ef(t):
+        return closed_form.su2_product_state_energy(t[:N], t[N:], ham20k.strings, ham20k.coeffs)
+
+    assert abs(e - ef(th)) <= (1e-10 if fp64 else 2e-5) * scale
+    hstep = 1e-5
+    for p in (0, 13, 17, 29, N + 2, N + 16, N + 27):
+        tp, tm = th.copy(), th.copy()
+        tp[p] += hstep
+        tm[p] -= hstep
+        fd = (ef(tp) - ef(tm)) / (2 * hstep)
+        assert abs(g[p] - fd) <= (1e-8 if fp64 else 2e-5) * scale, p
