@@ -807,7 +807,10 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
     const int kbit = A.l0_kbit;
     for_L_ent(gi, nmask, A.em, A.n, [&](int m, uint32_t x) {
       T2 v;
-      if constexpr (LOAD == LD_GATHER) {
+      if constexpr (LOAD == LD_GATHER && CPLX) {
+        // the map keeps the channel bit: (re, im) of x stay neighbours
+        v = __ldcg(reinterpret_cast<const T2 *>(in + x));
+      } else if constexpr (LOAD == LD_GATHER) {
         v.x = __ldcg(in + x);
         v.y = __ldcg(in + (x ^ d1));
       } else {
@@ -1081,8 +1084,12 @@ k_bwd(const PassArgs A) {
     } else if constexpr (FULL) {
       for_L_ent(gi, nmask, A.em, A.n, [&](int m, uint32_t x) {
         const T2 v = lam.pair(m);
-        out[x] = v.x;
-        out[x ^ d1] = v.y;
+        if constexpr (CPLX) {
+          *reinterpret_cast<T2 *>(out + x) = v;  // the map keeps the channel bit
+        } else {
+          out[x] = v.x;
+          out[x ^ d1] = v.y;
+        }
       });
     }
     // gred / ered of this tile were written before the round-H barriers
