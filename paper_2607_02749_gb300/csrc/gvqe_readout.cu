@@ -251,12 +251,30 @@ __global__ void __launch_bounds__(RO_NT) k_ro_minmax(const double *E, long long 
 // are the keys of evenly spaced energies.  With `below` set, the masses under
 // and above the range are summed too (ext[0], ext[3]); otherwise only x inside
 // the range read their amplitude (the mass below is known from earlier passes).
+//
+// A key's bin: the range is cut into RO_LUT equal key intervals, lut[j] holds
+// the bin of interval j's first key, so a key of interval j lies in a bin of
+// [lut[j], lut[j+1]], found by a binary search over that (usually one- or
+// two-bin) span instead of over all RO_BINS edges.
+constexpr int RO_LUT_BITS = 11;
+constexpr int RO_LUT = 1 << RO_LUT_BITS;
+__device__ __forceinline__ int ro_bin_search(const unsigned long long *se, unsigned long long k, int b0, int b1) {
+  while (b0 < b1) {  // largest b in [b0, b1] with se[b] <= k (se[b0] <= k holds)
+    const int mid = (b0 + b1 + 1) >> 1;
+    if (se[mid] <= k)
+      b0 = mid;
+    else
+      b1 = mid - 1;
+  }
+  return b0;
+}
 template <typename T>
 __global__ void __launch_bounds__(RO_NT) k_ro_hist(const T *psi, const double *E, long long N,
                                                    const unsigned long long *edges, unsigned long long *gmass,
                                                    unsigned long long *ext, int below) {
   __shared__ unsigned long long se[RO_BINS + 1];
   __shared__ unsigned long long sm[RO_BINS];
+  __shared__ unsigned short lut[RO_LUT + 1];
   __shared__ unsigned long long smin, smax;
   for (int i = threadIdx.x; i <= RO_BINS; i += RO_NT) {
     se[i] = edges[i];
@@ -268,6 +286,13 @@ __global__ void __launch_bounds__(RO_NT) k_ro_hist(const T *psi, const double *E
   }
   __syncthreads();
   const unsigned long long lo = se[0], hi = se[RO_BINS];
+  const unsigned long long span = hi - lo;
+  const int lsh = (span == 0ull) ? 0 : max(0, 64 - __clzll((long long)span) - RO_LUT_BITS);
+  for (int j = threadIdx.x; j <= RO_LUT; j += RO_NT) {
+    const unsigned long long kj = lo + ((unsigned long long)j << lsh);
+    lut[j] = (unsigned short)((j == RO_LUT || kj >= hi || kj < lo) ? RO_BINS - 1 : ro_bin_search(se, kj, 0, RO_BINS - 1));
+  }
+  __syncthreads();
   const unsigned long long lo_read = below ? 0ull : lo;   // keys in [lo_read, hi_read) read psi
   const unsigned long long hi_read = below ? ~0ull : hi;
   unsigned long long kmin = ~0ull, kmax = 0ull, qbelow = 0ull, qabove = 0ull;
@@ -281,10 +306,8 @@ __global__ void __launch_bounds__(RO_NT) k_ro_hist(const T *psi, const double *E
       return;
     }
     const unsigned long long q = qmass(v);
-    int b = 0;  // largest b with edges[b] <= k
-#pragma unroll
-    for (int step = RO_BINS / 2; step > 0; step >>= 1)
-      if (se[b + step] <= k) b += step;
+    const int j = (int)((k - lo) >> lsh);  // < RO_LUT
+    const int b = ro_bin_search(se, k, lut[j], lut[j + 1]);  // largest b with edges[b] <= k
     if (q) atomicAdd(&sm[b], q);
     kmin = k < kmin ? k : kmin;
     kmax = k > kmax ? k : kmax;
