@@ -42,6 +42,7 @@ extern "C" {
 #define GVQE_ECUDA (-3)        /* a CUDA runtime call failed (message has the CUDA error) */
 #define GVQE_ETIMEOUT (-4)     /* a bounded device-side wait ran out (persistent batch kernel) */
 #define GVQE_EUNSUPPORTED (-5) /* a valid request this build does not implement */
+#define GVQE_ECORRUPT (-6)     /* debug build: a device write landed outside its workspace */
 
 /* flags for gvqe_energy / gvqe_energy_grad / gvqe_batch_create */
 #define GVQE_FP32 0x0             /* FP32 amplitudes, FP64 table and FP64 reductions (default) */
@@ -257,6 +258,26 @@ int gvqe_destroy(void *handle);
  */
 int gvqe_set_device_memory_limit(long long bytes);
 long long gvqe_device_memory_in_use(void);
+
+/*
+ * gvqe_debug_check -- debug builds (compiled with GVQE_DEBUG, libgvqe_debug.so):
+ * every device workspace is allocated with a 4 KiB guard zone on each side,
+ * filled with a known byte.  This call synchronises the device and checks every
+ * live workspace's guards; a kernel that wrote past either end of its buffer
+ * makes it fail with GVQE_ECORRUPT, the message naming the buffer's size, the
+ * side and the first overwritten byte.  The guards cost two memsets per
+ * allocation and leave every result bit-identical to the regular build.
+ * Regular builds return GVQE_EUNSUPPORTED.
+ */
+int gvqe_debug_check(void);
+
+/*
+ * gvqe_debug_poke_guard -- debug builds, for testing gvqe_debug_check: from the
+ * host (cudaMemset, no kernel), set (restore = 0) or reset (restore = 1) the
+ * first byte above the largest live workspace, as an overrun by one byte would.
+ * Errors: GVQE_EINVAL (no live workspace); regular builds GVQE_EUNSUPPORTED.
+ */
+int gvqe_debug_poke_guard(int restore);
 
 /* gvqe_last_error -- message of the last failing call on this thread ("" if none). */
 const char *gvqe_last_error(void);

@@ -14,6 +14,8 @@ from typing import Optional, Sequence
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgvqe.so")
+# GVQE_DEBUG=1 in the environment loads the debug build (guarded workspaces)
+DEBUG = os.environ.get("GVQE_DEBUG", "0") not in ("", "0")
 
 GVQE_OK = 0
 GVQE_EINVAL = -1
@@ -21,6 +23,7 @@ GVQE_ENOMEM = -2
 GVQE_ECUDA = -3
 GVQE_ETIMEOUT = -4
 GVQE_EUNSUPPORTED = -5
+GVQE_ECORRUPT = -6
 GVQE_FP32 = 0x0
 GVQE_FP64 = 0x1
 GVQE_GRAD_ADJOINT = 0x0
@@ -50,6 +53,7 @@ _ERRNAMES = {
     GVQE_ECUDA: "GVQE_ECUDA",
     GVQE_ETIMEOUT: "GVQE_ETIMEOUT",
     GVQE_EUNSUPPORTED: "GVQE_EUNSUPPORTED",
+    GVQE_ECORRUPT: "GVQE_ECORRUPT",
 }
 
 
@@ -88,6 +92,8 @@ _SIGS = {
     "gvqe_profile_enable": [_I],
     "gvqe_profile_read": [_I, _VP, _VP, _VP],
     "gvqe_profile_reset": [],
+    "gvqe_debug_check": [],
+    "gvqe_debug_poke_guard": [_I],
 }
 
 
@@ -97,11 +103,11 @@ def load(path: Optional[str] = None, build_if_missing: bool = True) -> ctypes.CD
     with _lock:
         if _lib is not None and path is None:
             return _lib
-        p = path or LIB_PATH
+        p = path or (os.path.join(HERE, "libgvqe_debug.so") if DEBUG else LIB_PATH)
         if path is None and build_if_missing:
             from . import build as _build
 
-            p = _build.build()
+            p = _build.build(debug=DEBUG)
         if not os.path.exists(p):
             raise RuntimeError(f"gvqe CUDA library not found at {p}; run paper_2607_02749_gb300.build.build()")
         lib = ctypes.CDLL(p)
@@ -258,6 +264,17 @@ def gvqe_plan_describe(n_qubits: int, reps: int, flags: int = GVQE_FP32, tile_bi
     buf = ctypes.create_string_buffer(1 << 16)
     _check(load().gvqe_plan_describe(n_qubits, reps, flags, tile_bits, buf, len(buf)), "gvqe_plan_describe")
     return buf.value.decode()
+
+
+def gvqe_debug_check() -> None:
+    """Debug build: raise GvqeError (GVQE_ECORRUPT) if a device write landed in a
+    workspace guard; regular builds raise GVQE_EUNSUPPORTED."""
+    _check(load().gvqe_debug_check(), "gvqe_debug_check")
+
+
+def gvqe_debug_poke_guard(restore: bool = False) -> None:
+    """Debug build, tests only: overwrite (or restore) the first guard byte above the largest workspace."""
+    _check(load().gvqe_debug_poke_guard(1 if restore else 0), "gvqe_debug_poke_guard")
 
 
 def gvqe_ansatz_describe(a: int, flags: int = GVQE_FP32) -> str:

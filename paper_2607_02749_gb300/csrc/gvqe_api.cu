@@ -66,6 +66,15 @@ static long long budget_left() {
   return lim > 0 ? std::max(0LL, lim - g_mem_used.load()) : -1;
 }
 
+#ifdef GVQE_DEBUG
+// Debug builds: a guard zone of kGuard bytes of kGuardByte on each side of every
+// workspace (ptr points past the lower one); gvqe_debug_check verifies them.
+constexpr size_t kGuard = 4096;
+constexpr unsigned char kGuardByte = 0xA5;
+static std::mutex g_guard_mu;
+static std::map<char *, size_t> g_guarded;  // workspace pointer -> its bytes
+#endif
+
 int DevBuf::reserve(size_t need) {
   if (need <= bytes) return GVQE_OK;
   release();
@@ -78,12 +87,34 @@ int DevBuf::reserve(size_t need) {
   if (need > freeb)
     return fail(GVQE_ENOMEM, "device workspace of %.3f GiB does not fit in %.3f GiB free", need / 1073741824.0,
                 freeb / 1073741824.0);
+#ifdef GVQE_DEBUG
+  void *base = nullptr;
+  cudaError_t e = cudaMalloc(&base, need + 2 * kGuard);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    cudaGetLastError();
+    return fail(GVQE_ENOMEM, "cudaMalloc(%zu): %s", need + 2 * kGuard, cudaGetErrorString(e));
+  }
+  e = cudaMemset(base, kGuardByte, kGuard);
+  if (e == cudaSuccess) e = cudaMemset((char *)base + kGuard + need, kGuardByte, kGuard);
+  if (e != cudaSuccess) {
+    cudaFree(base);
+    ptr = nullptr;
+    return fail(GVQE_ECUDA, "guard fill: %s", cudaGetErrorString(e));
+  }
+  ptr = (char *)base + kGuard;
+  {
+    std::lock_guard<std::mutex> lk(g_guard_mu);
+    g_guarded[(char *)ptr] = need;
+  }
+#else
   cudaError_t e = cudaMalloc(&ptr, need);
   if (e != cudaSuccess) {
     ptr = nullptr;
     cudaGetLastError();
     return fail(GVQE_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
   }
+#endif
   bytes = need;
   g_mem_used += (long long)need;
   return GVQE_OK;
@@ -91,7 +122,15 @@ int DevBuf::reserve(size_t need) {
 
 void DevBuf::release() {
   if (ptr) {
+#ifdef GVQE_DEBUG
+    {
+      std::lock_guard<std::mutex> lk(g_guard_mu);
+      g_guarded.erase((char *)ptr);
+    }
+    cudaFree((char *)ptr - kGuard);
+#else
     cudaFree(ptr);
+#endif
     g_mem_used -= (long long)bytes;
   }
   ptr = nullptr;
@@ -1601,6 +1640,45 @@ int gvqe_plan_describe(int n_qubits, int reps, int flags, int tile_bits, char *b
     buf[m] = 0;
   }
   return (int)pl.lp.size();
+}
+
+int gvqe_debug_check(void) {
+  g_err.clear();
+#ifndef GVQE_DEBUG
+  return fail(GVQE_EUNSUPPORTED, "built without GVQE_DEBUG: no workspace guards to check");
+#else
+  GV_CUDA(cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> lk(g_guard_mu);
+  std::vector<unsigned char> h(kGuard);
+  for (const auto &kv : g_guarded) {
+    for (int side = 0; side < 2; ++side) {
+      const char *g = side ? kv.first + kv.second : kv.first - kGuard;
+      GV_CUDA(cudaMemcpy(h.data(), g, kGuard, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < kGuard; ++i)
+        if (h[i] != kGuardByte)
+          return fail(GVQE_ECORRUPT, "the guard %s a %zu-byte workspace was overwritten at byte %zu %s it", 
+                      side ? "above" : "below", kv.second, side ? i : kGuard - i, side ? "past the end of" : "before");
+    }
+  }
+  return GVQE_OK;
+#endif
+}
+
+int gvqe_debug_poke_guard(int restore) {
+  g_err.clear();
+#ifndef GVQE_DEBUG
+  (void)restore;
+  return fail(GVQE_EUNSUPPORTED, "built without GVQE_DEBUG: no workspace guards");
+#else
+  std::lock_guard<std::mutex> lk(g_guard_mu);
+  const std::pair<char *const, size_t> *big = nullptr;
+  for (const auto &kv : g_guarded)
+    if (!big || kv.second > big->second) big = &kv;
+  if (!big) return fail(GVQE_EINVAL, "no live workspace");
+  GV_CUDA(cudaMemset(big->first + big->second, restore ? kGuardByte : 0, 1));
+  GV_CUDA(cudaDeviceSynchronize());
+  return GVQE_OK;
+#endif
 }
 
 int gvqe_ansatz_describe(gvqe_ansatz a, int flags, char *buf, int buflen) {

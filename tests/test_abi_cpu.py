@@ -243,3 +243,12 @@ def test_split_layout_option_and_plans():
         with pytest.raises(gv.GvqeError) as e:
             gv.gvqe_ansatz_set_option(a.handle, gv.GVQE_OPT_SPLIT_PASSES, bad)
         assert e.value.code == gv._lib.GVQE_EINVAL
+
+
+def test_debug_entry_points_refuse_in_the_regular_build():
+    if _lib.DEBUG:
+        pytest.skip("the debug library is loaded")
+    for f in (_lib.gvqe_debug_check, _lib.gvqe_debug_poke_guard):
+        with pytest.raises(_lib.GvqeError) as e:
+            f()
+        assert e.value.code == _lib.GVQE_EUNSUPPORTED
