@@ -239,9 +239,21 @@ def cluster_leg(steps: int):
     torch.cuda.synchronize()
     dt_loop = time.perf_counter() - t0
     amps = sum(2 ** i.n_qubits for i in insts)
+    # algorithmic bytes of one run (FP32, every layer's passes): per amplitude 4 (layer 1's
+    # first pass writes only) + 8 per other forward pass + 12 per backward pass + 4 (layer 0)
+    lib = _lib.load()
+    nbytes = 0
+    for i in insts:
+        p = lib.gvqe_plan_describe(i.n_qubits, i.reps, _lib.GVQE_FP32, 0, None, 0)
+        nbytes += 2 ** i.n_qubits * (4 + 8 * (i.reps * p - 1) + 12 * i.reps * p + 4)
+    peak, peak_src = measured_peaks()
+    gbps = nbytes / dt / 1e9
     return {"value": len(insts) / dt, "unit": "E+grad/s", "instances": len(insts), "ms_per_run": dt * 1e3,
             "launches_per_run": launches, "per_instance_calls_ms": dt_loop * 1e3,
-            "total_amplitudes": amps, "timing": "wall clock around synchronous gvqe_batch_run calls"}
+            "total_amplitudes": amps, "algorithmic_GB_per_run": nbytes / 1e9, "GBps": gbps,
+            "frac_of_hbm_peak": gbps / peak if peak else None,
+            "note": "states of 2^14..2^20 amplitudes stay in L2, so the rate can pass the HBM copy peak",
+            "timing": "wall clock around synchronous gvqe_batch_run calls"}
 
 
 def readout_leg(n: int, reps: int, ham, steps: int):
