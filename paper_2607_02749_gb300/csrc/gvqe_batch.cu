@@ -146,7 +146,7 @@ __device__ void batch_pass(const PassArgs &A, uint32_t tile) {
 }
 
 template <typename T, int TB>
-__global__ void __launch_bounds__(1 << (TB - 5), (TB == 12 && sizeof(T) == 4) ? 4 : 2) k_batch(const BatchArgs B) {
+__global__ void __launch_bounds__(1 << (TB - 5), (TB == 12 && sizeof(T) == 4) ? 5 : 2) k_batch(const BatchArgs B) {
   __shared__ unsigned s_item;
   __shared__ int s_ok;
   for (;;) {
@@ -249,9 +249,10 @@ namespace {
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// 2^12-amplitude tiles in both precisions: an item is one tile, and in FP32 four
-// 128-thread CTAs per SM keep more items in flight than two 256-thread CTAs on
-// 2^13 tiles (measured 4.97 -> 4.78 ms for the 256-instance cluster batch).
+// 2^12-amplitude tiles in both precisions: an item is one tile, and in FP32 five
+// 128-thread CTAs per SM (96 registers) keep more items in flight than two
+// 256-thread CTAs on 2^13 tiles (measured for the 256-instance cluster batch:
+// 4.97 ms on 2^13 tiles, 4.78 ms at four CTAs of 2^12, 4.48 ms at five).
 int tile_bits_for(int prec) {
   (void)prec;
   return 12;
