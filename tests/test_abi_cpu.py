@@ -252,3 +252,44 @@ def test_debug_entry_points_refuse_in_the_regular_build():
         with pytest.raises(_lib.GvqeError) as e:
             f()
         assert e.value.code == _lib.GVQE_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("gates", [1, 2])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_split_rule_over_register_sizes(gates, fp64):
+    """For every size with two strided passes per layer: auto mode splits exactly
+    when the top pass would span more than 2^8 large pages (gate index bits whose
+    stride is at least 2 MiB), and then moves the fewest top qubits that leave the
+    other pass at 2^8; every index bit of the layer is covered once."""
+    import re
+
+    import paper_2607_02749_gb300 as gv
+
+    pb = 18 if fp64 else 19  # index bits with a stride of at least 2 MiB
+    seen_split = False
+    for n in range(14, 31):
+        a = gv.Ansatz(n, 1, gates=gates)
+        d = a.describe(fp64=fp64)
+        nb = int(re.search(r"n=(\d+)", d).group(1))
+        passes = _layer_passes(d)
+        runs = [tuple(map(int, m)) for m in re.findall(r"split=(\d+),(\d+)", d)]
+        covered = sorted(q for p in passes for q in p[3])
+        first = 1 if gates == 2 else 0  # index bit 0 is the channel on the complex path
+        assert covered == list(range(first, nb)), (n, d)
+        if len(passes) != 3:
+            assert all(r == (0, 0) for r in runs)
+            continue
+        tb = passes[0][0]
+        ga = tb - passes[1][1]
+        top_unsplit = max(0, nb - max(tb + ga, pb))
+        split = runs[1][0] > 0
+        assert split == (top_unsplit > 8), (n, fp64, gates, d)
+        pages_second = sum(1 for q in passes[2][3] if q >= pb)
+        if split:
+            seen_split = True
+            assert pages_second <= 8
+            y = ga - runs[1][0]
+            # one fewer top qubit would leave the second pass above 2^8 pages
+            lo, hi = tb + ga - (y - 1), nb - (y - 1)
+            assert y == 1 or max(0, hi - max(lo, pb)) > 8
+    assert seen_split == (gates == 2 or fp64)
