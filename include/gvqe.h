@@ -160,8 +160,12 @@ int gvqe_energy_grad(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, co
 /*
  * gvqe_batch_create -- a fixed set of independent restricted-update problems
  * (Section IV-D, Eq. 11): instance i pairs ansatze[i] with hams[i] (equal n)
- * and evaluates one parameter vector with its own active mask per run.  All
- * instances run in one persistent kernel launch, captured in a CUDA graph.
+ * and evaluates one parameter vector with its own active mask per run.  When
+ * every instance has n >= 12, RY layers and a diagonal (I/Z-only) Hamiltonian,
+ * all instances run in one persistent kernel launch on 2^12-amplitude tiles,
+ * captured in a CUDA graph; otherwise they run one after another through
+ * gvqe_energy_grad.  The tile size fixes the summation order, so results agree
+ * with single calls within the precision bounds, not bit for bit.
  *   n_inst: >= 1.  ansatze, hams: host arrays of n_inst handles (borrowed: they
  *   must outlive the batch).  flags: GVQE_FP32 or GVQE_FP64.
  * Errors: GVQE_EINVAL, GVQE_ENOMEM, GVQE_ECUDA, GVQE_EUNSUPPORTED.
