@@ -2,16 +2,22 @@
 //
 // A CTA owns one tile of 2^TB real amplitudes; each of its 2^(TB-5) threads
 // holds 32 amplitudes in registers at a time, and the tile moves through
-// register "rounds":
-//   round L: registers <-> tile bits 5..9, lanes <-> bits 0..4, warps <-> bits 10..
-//            (global loads/stores here are coalesced warp accesses)
-//   round M: registers <-> tile bits 0..4 (one 32-amplitude group per thread,
-//            16-byte vector shared-memory accesses)
-//   round H: registers <-> tile bits 10..TB-1
-// RY gates on the bits held in registers are applied in registers (FP32:
-// packed f32x2 FMAs on amplitude pairs); shared memory only transposes the
-// tile between rounds.  The shared tile is swizzled (16-byte chunk index XOR
-// the 32-amplitude group index) so both access shapes are conflict-free.
+// register "rounds".  In every round register bit 0 is tile bit 0, so a
+// thread's elements 2m and 2m+1 are neighbours in shared and global memory and
+// move as one 8-byte (FP32) or 16-byte (FP64) access:
+//   round L: registers <-> tile bits 0, 6..9; lanes <-> bits 1..5; warps <->
+//            bits 10..TB-1 (global loads/stores here are coalesced warp accesses)
+//   round M: registers <-> tile bits 0..4 (16-byte vector shared-memory
+//            accesses); lanes <-> bits 5..9
+//   round H: registers <-> tile bits 0, 5, 10..TB-1 (and, for TB < 13, gate-free
+//            group bits below 10); threads <-> bits 1..4, 6..9
+// Rounds L and M of one warp cover the same 1024 tile amplitudes, so the L<->M
+// transition only synchronises the warp; round H crosses warps.  RY gates on the
+// bits held in registers are applied in registers (FP32: packed f32x2 FMAs on
+// amplitude pairs, every gate but the one on tile bit 0); shared memory only
+// transposes the tile between rounds.  The shared tile is swizzled (16-byte
+// chunk index XOR the 128-byte row index) so all three access shapes are
+// conflict-free.
 //
 // Global indices are 32-bit element offsets inside one state (n <= 30).
 // Layout FULL: tile bits == global bits [0, TB) (the first pass of a layer,
