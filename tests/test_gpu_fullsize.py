@@ -69,14 +69,22 @@ def test_reps1_heisenberg_closed_form(fp64):
     e_ref = fn(th)
     tol_e = 1e-10 if fp64 else 2e-5
     assert abs(e - e_ref) <= tol_e * scale
-    for p in (0, 13, 14, 21, 22, 29, 30, 44, 52, 59):
+    picks = (0, 13, 14, 21, 22, 29, 30, 44, 52, 59)
+    g_ref = []
+    for p in picks:
         tp = th.copy()
         tp[p] += math.pi / 2
         tm = th.copy()
         tm[p] -= math.pi / 2
-        g_ref = 0.5 * (fn(tp) - fn(tm))
-        tol_g = 1e-9 * scale if fp64 else 1e-4 * max(abs(g_ref), 1e-3 * scale) + 2e-5 * scale
-        assert abs(g[p] - g_ref) <= tol_g, (p, g[p], g_ref)
+        g_ref.append(0.5 * (fn(tp) - fn(tm)))  # Eq. 13, exact for a degree-one angle
+    g_ref = np.array(g_ref)
+    g_s = g[list(picks)]
+    if fp64:
+        assert np.max(np.abs(g_s - g_ref)) <= 1e-9 * scale, (g_s, g_ref)
+    else:  # the FP32 bound: relative L2 over the sampled entries
+        rel = np.linalg.norm(g_s - g_ref) / np.linalg.norm(g_ref)
+        print(f"n=30 reps=1 fp32: sampled grad rel L2 = {rel:.3e}")
+        assert rel <= 1e-4, (g_s, g_ref)
 
 
 def test_zero_and_basis_angles_at_reps6(ham20k):
