@@ -205,18 +205,23 @@ struct RedEntry {
   int param;
 };
 
-// Shared-memory layout of one chunk of X-mask groups: [gmask][gstart][tz][tc], 16-byte aligned parts.
+// Shared-memory layout of one chunk of X-mask groups: [gmask][gstart][tz][tc]
+// [run starts][per-term slot masks][two partner tiles of 2^tb amplitudes],
+// 16-byte aligned parts (tb = 0: the group tables alone).
 struct XyLayout {
-  size_t gm, gs, tz, tc, total;
+  size_t gm, gs, tz, tc, runs, km, buf, total;
 };
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-__host__ __device__ inline XyLayout xy_layout(int ngroups, int nterm, int elem) {
+__host__ __device__ inline XyLayout xy_layout(int ngroups, int nterm, int elem, int tb = 0) {
   XyLayout l;
   l.gm = 0;
   l.gs = align16((size_t)ngroups * 4);
   l.tz = align16(l.gs + (size_t)(ngroups + 1) * 4);
   l.tc = align16(l.tz + (size_t)nterm * 4);
-  l.total = align16(l.tc + (size_t)nterm * elem);
+  l.runs = align16(l.tc + (size_t)nterm * elem);
+  l.km = align16(l.runs + (size_t)(ngroups + 1) * 4);
+  l.buf = align16(l.km + (size_t)nterm * 4);
+  l.total = l.buf + (tb > 0 ? ((size_t)2 * elem << tb) : 0);
   return l;
 }
 
@@ -226,7 +231,8 @@ cudaError_t launch_pass(int prec, const PassArgs &A, int jobs, int nterm, cudaSt
 // shared memory of one complex-path X/Y chunk (gvqe_kernels.cu); 1024 amplitudes per CTA
 size_t xyc_smem_bytes(int prec, int ngroups, int nterm);
 constexpr int XYC_AMPS_PER_CTA = 1024;
-// Shared memory of one K_LAMBDA_XY launch; at most ~200 KiB is accepted.
+// Shared memory of the group tables of one K_LAMBDA_XY launch (the two partner
+// tiles come on top: at most ~200 KiB in all is accepted).
 size_t xy_smem_bytes(int prec, int ngroups, int nterm);
 cudaError_t launch_trig(int prec, const double *params, long long count, void *cs, cudaStream_t s);
 cudaError_t launch_minlayer(const uint8_t *mask, int jobs, int n, int P, int none_value, int *out,

@@ -409,7 +409,7 @@ size_t pass_smem_bytes(int prec, int kind, int tb) {
   return 0;
 }
 
-size_t xy_smem_bytes(int prec, int ngroups, int nterm) { return xy_layout(ngroups, nterm, prec ? 8 : 4).total; }
+size_t xy_smem_bytes(int prec, int ngroups, int nterm) { return xy_layout(ngroups, nterm, prec ? 8 : 4).buf; }
 
 template <typename T>
 static cudaError_t launch_typed(const PassArgs &A, int jobs, int nterm, cudaStream_t s) {

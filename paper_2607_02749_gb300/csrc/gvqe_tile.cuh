@@ -288,6 +288,14 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// c, negated when bit is 1 (a sign-bit flip, no branch).
+__device__ __forceinline__ float flip_sign(float c, uint32_t bit) {
+  return __int_as_float(__float_as_int(c) ^ (int)(bit << 31));
+}
+__device__ __forceinline__ double flip_sign(double c, uint32_t bit) {
+  return __longlong_as_double(__double_as_longlong(c) ^ ((long long)bit << 63));
+}
+
 // Global offset of a tile bit under the STRIDED layout.
 __device__ __forceinline__ uint32_t gbit(int t, const PassArgs &A) { return 1u << tile_gbit(t, A.c, A.a, A.k1, A.gap); }
 // Global offset (within its tile) of tile index i under the STRIDED layout.
@@ -1394,10 +1402,40 @@ __device__ __forceinline__ void grad_l0_tile(const PassArgs &A, int job, uint32_
 // ----------------------------------------- lambda = H psi with X-mask groups --
 // lambda[x] = E(x) psi[x] + sum_groups D_m(x ^ m) psi[x ^ m] with
 // D_m(u) = sum_{k in group} c_k (-1)^popcount(u & z_k) (c_k carries the i^#Y sign).
+//
+// A CTA owns the output tile t (2^TB amplitudes, 32 per thread in registers).
+// The groups come sorted by X-mask m, so groups whose mask agrees above the
+// tile bits (the same high part h = m >> TB) form consecutive runs; a run needs
+// one partner tile, psi over tile t ^ h, which is streamed into shared memory
+// with cp.async, the next run's partner landing in the other buffer while this
+// run's groups are applied.  For element e of the tile (u = x ^ m has tile part
+// e ^ m_lo), the sign (-1)^popcount(u & z) splits into a part constant over the
+// CTA (the tile index bits of u), one constant per thread (its thread bits of
+// e ^ m_lo) and one that depends only on the register slot k, read from a
+// 32-bit mask per term built once per CTA: no population count per element.
+// Bytes: psi and the table of tile t, one partner tile per run, lambda written.
+// One X-mask group applied to a thread's 32 elements: element k (tile index
+// e = k NT + tid) gains D(u) psi[u] with u's tile part k NT ^ tm read from the
+// partner tile; D(u) = sum_j c[j] (-1)^(bit k of km[j]), the signs of u's other
+// bits already folded into c[j].  NTERM terms (unused ones have c = 0).
+template <typename T, int TB, int NTERM>
+__device__ __forceinline__ void xy_group(T (&acc)[ROUND], const T *buf, uint32_t tm, const T (&c)[4],
+                                         const uint32_t (&km)[4]) {
+  constexpr int NT = 1 << (TB - 5);
+#pragma unroll
+  for (int k = 0; k < ROUND; ++k) {
+    T d = flip_sign(c[0], (km[0] >> k) & 1u);
+#pragma unroll
+    for (int j = 1; j < NTERM; ++j) d += flip_sign(c[j], (km[j] >> k) & 1u);
+    acc[k] += d * buf[((uint32_t)(k * NT)) ^ tm];
+  }
+}
+
 template <typename T, int TB>
 __global__ void __launch_bounds__(1 << (TB - 5)) k_lambda_xy(const PassArgs A) {
   constexpr int NT = 1 << (TB - 5);
   constexpr int NW = NT / 32;
+  constexpr uint32_t LOW = (1u << TB) - 1u;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nterm = A.ngroups > 0 ? A.gstart[A.ngroups] - A.gstart[0] : 0;
   const XyLayout lay = xy_layout(A.ngroups, nterm, (int)sizeof(T));
@@ -1405,37 +1443,115 @@ __global__ void __launch_bounds__(1 << (TB - 5)) k_lambda_xy(const PassArgs A) {
   int *sgs = reinterpret_cast<int *>(smem_raw + lay.gs);
   uint32_t *stz = reinterpret_cast<uint32_t *>(smem_raw + lay.tz);
   T *stc = reinterpret_cast<T *>(smem_raw + lay.tc);
+  int *srun = reinterpret_cast<int *>(smem_raw + lay.runs);
+  uint32_t *skm = reinterpret_cast<uint32_t *>(smem_raw + lay.km);
+  T *sbuf = reinterpret_cast<T *>(smem_raw + lay.buf);
   __shared__ double ered[NW];
+  __shared__ int s_nruns;
   const int job = blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint32_t t = blockIdx.x;
   const int t0 = A.ngroups > 0 ? A.gstart[0] : 0;
   for (int i = tid; i < A.ngroups; i += NT) sgm[i] = A.gmask[i];
-  for (int i = tid; i <= A.ngroups; i += NT) sgs[i] = A.gstart[i] - t0;
+  if (A.ngroups > 0)
+    for (int i = tid; i <= A.ngroups; i += NT) sgs[i] = A.gstart[i] - t0;
   for (int i = tid; i < nterm; i += NT) {
-    stz[i] = A.tz[t0 + i];
+    const uint32_t z = A.tz[t0 + i];
+    stz[i] = z;
     stc[i] = reinterpret_cast<const T *>(A.tc)[t0 + i];
+    // bit k: parity of k * NT & z (the register-slot bits, tile bits TB-5 .. TB-1)
+    const uint32_t zk = (z >> (TB - 5)) & 31u;
+    uint32_t km = 0;
+    for (int k = 0; k < 32; ++k) km |= (uint32_t)(__popc((uint32_t)k & zk) & 1) << k;
+    skm[i] = km;
   }
   __syncthreads();
+  if (tid == 0) {  // runs of equal high part (groups arrive sorted by mask)
+    int nr = 0;
+    for (int g = 0; g < A.ngroups; ++g)
+      if (g == 0 || (sgm[g] >> TB) != (sgm[g - 1] >> TB)) srun[nr++] = g;
+    srun[nr] = A.ngroups;
+    s_nruns = nr;
+  }
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
   const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
   const T *table = reinterpret_cast<const T *>(A.table);
   T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
   const uint32_t tbase = t << TB;
-  T eacc = T(0);
+  T acc[ROUND];
+#pragma unroll
   for (int k = 0; k < ROUND; ++k) {
-    const uint32_t x = tbase + lane + 32 * k + 1024 * w;
-    const T p = in[x];
-    T acc = (A.flags & F_ACCUM) ? lin[x] : table[x] * p;
-    for (int g = 0; g < A.ngroups; ++g) {
-      const uint32_t u = x ^ sgm[g];
-      const T pu = in[u];
-      T d = T(0);
-      for (int j = sgs[g]; j < sgs[g + 1]; ++j) d += (__popc(u & stz[j]) & 1) ? -stc[j] : stc[j];
-      acc += d * pu;
+    const uint32_t x = tbase + (uint32_t)(k * NT + tid);
+    acc[k] = (A.flags & F_ACCUM) ? lin[x] : table[x] * in[x];
+  }
+  __syncthreads();
+  const int nruns = s_nruns;
+  constexpr int CHUNKS = (int)((sizeof(T) << TB) / 16);  // 16-byte pieces of one tile
+  auto load_partner = [&](int r, int b) {
+    const uint32_t pt = t ^ (sgm[srun[r]] >> TB);
+    const char *src = reinterpret_cast<const char *>(in + ((size_t)pt << TB));
+    char *dst = reinterpret_cast<char *>(sbuf + ((size_t)b << TB));
+    for (int i = tid; i < CHUNKS; i += NT) cp_async16(dst + 16 * i, src + 16 * (size_t)i);
+    cp_async_commit();
+  };
+  if (nruns > 0) load_partner(0, 0);
+  for (int r = 0; r < nruns; ++r) {
+    if (r + 1 < nruns) {
+      load_partner(r + 1, (r + 1) & 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
-    if (A.flags & F_WRITE_LAMBDA) out[x] = acc;
-    eacc += p * acc;
+    __syncthreads();
+    const T *buf = sbuf + ((size_t)(r & 1) << TB);
+    const uint32_t hi_bits = (t ^ (sgm[srun[r]] >> TB)) << TB;  // tile-index bits of u
+    for (int g = srun[r]; g < srun[r + 1]; ++g) {
+      const uint32_t tm = (uint32_t)tid ^ (sgm[g] & LOW);  // e ^ m_lo = k * NT ^ tm
+      const int j0 = sgs[g], nt = sgs[g + 1] - j0;
+      // per term: its coefficient with the sign of every bit of u but the slot bits
+      // folded in, and its slot mask (bit k: the sign the slot bits of k add)
+      T c[4];
+      uint32_t km[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j < nt) {
+          c[j] = flip_sign(stc[j0 + j], __popc(stz[j0 + j] & (hi_bits | tm)) & 1);
+          km[j] = skm[j0 + j];
+        } else {
+          c[j] = T(0);
+          km[j] = 0;
+        }
+      }
+      if (nt == 1) {
+        xy_group<T, TB, 1>(acc, buf, tm, c, km);
+      } else if (nt == 2) {
+        xy_group<T, TB, 2>(acc, buf, tm, c, km);
+      } else if (nt <= 4) {
+        xy_group<T, TB, 4>(acc, buf, tm, c, km);
+      } else {
+        for (int j4 = 0; j4 < nt; j4 += 4) {  // more than four terms: four at a time
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (j4 + j < nt) {
+              c[j] = flip_sign(stc[j0 + j4 + j], __popc(stz[j0 + j4 + j] & (hi_bits | tm)) & 1);
+              km[j] = skm[j0 + j4 + j];
+            } else {
+              c[j] = T(0);
+              km[j] = 0;
+            }
+          }
+          xy_group<T, TB, 4>(acc, buf, tm, c, km);
+        }
+      }
+    }
+    __syncthreads();  // every thread is done with this buffer before it is refilled
+  }
+  T eacc = T(0);
+#pragma unroll
+  for (int k = 0; k < ROUND; ++k) {
+    const uint32_t x = tbase + (uint32_t)(k * NT + tid);
+    if (A.flags & F_WRITE_LAMBDA) out[x] = acc[k];
+    eacc += in[x] * acc[k];
   }
   if (A.flags & F_ENERGY) {
     eacc = warp_sum(eacc);
@@ -1544,7 +1660,7 @@ cudaError_t launch_tb(const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
       return launch_persistent(k, jobs, A.tiles, block, 2 * tile, s, A);
     }
     case K_LAMBDA_XY: {
-      const size_t smem = xy_layout(A.ngroups, nterm, (int)sizeof(T)).total;
+      const size_t smem = xy_layout(A.ngroups, nterm, (int)sizeof(T), TB).total;
       if (smem > 200 * 1024) return cudaErrorInvalidValue;
       return launch_k(k_lambda_xy<T, TB>, grid, block, smem, s, A);
     }

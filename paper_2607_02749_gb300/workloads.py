@@ -200,6 +200,9 @@ WORKLOADS = {
     "n27_reps2_z2000": dict(n=27, reps=2, terms=2000, batch=1, kind="z"),
     # n=28, reps=5, FP32: 5,000 strings over {I,X,Y,Z}, 8 thetas.
     "n28_reps5_pauli5000": dict(n=28, reps=5, terms=5000, batch=8, kind="pauli"),
+    # n=26, reps=2, FP32: the same term mix, 1 theta: a profiling-size case of the
+    # non-diagonal path (256 MiB state, a few GiB on the device in total).
+    "n26_reps2_pauli5000": dict(n=26, reps=2, terms=5000, batch=1, kind="pauli"),
 }
 
 
