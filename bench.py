@@ -61,7 +61,12 @@ def parse_args():
     ap.add_argument("--only-driver", action="store_true",
                     help="run only the Graph-VQE driver leg (one epoch at n=20) and print its JSON object")
     ap.add_argument("--only-xy", action="store_true",
-                    help="run only the non-diagonal leg (n=28, 5,000 mixed strings, 8 vectors) and print its JSON object")
+                    help="run only the non-diagonal leg (default n=28, 5,000 mixed strings, 8 vectors; "
+                         "--xy-workload picks another) and print its JSON object")
+    ap.add_argument("--xy-workload", default="n28_reps5_pauli5000")
+    ap.add_argument("--only-cluster", action="store_true",
+                    help="run only the 256-instance cluster batch leg and print its JSON object")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default tile plan (skip the autotuner)")
     ap.add_argument("--cpu-single-core", action="store_true",
                     help="also time one full oracle E+grad at n=24 on one core (about 3-4 minutes)")
     return ap.parse_args()
@@ -251,6 +256,7 @@ def cluster_leg(steps: int):
     masks = [torch.as_tensor(i.mask[0], dtype=torch.uint8, device="cuda") for i in insts]
     grads = [torch.empty_like(p) for p in params]
     energies = torch.empty(len(insts), dtype=torch.float64, device="cuda")
+    tune = b.autotune(params, masks=masks, grads=grads, energies=energies)
     for _ in range(3):
         b.run(params, masks=masks, grads=grads, energies=energies)
     torch.cuda.synchronize()
@@ -283,7 +289,8 @@ def cluster_leg(steps: int):
             "launches_per_run": launches, "per_instance_calls_ms": dt_loop * 1e3,
             "total_amplitudes": amps, "algorithmic_GB_per_run": nbytes / 1e9, "GBps": gbps,
             "frac_of_hbm_peak": gbps / peak if peak else None,
-            "note": "states of 2^14..2^20 amplitudes stay in L2, so the rate can pass the HBM copy peak",
+            "schedule": tune.strip().splitlines(),
+            "note": "states of 2^14..2^20 amplitudes partly stay in L2, so the rate can pass the HBM copy peak",
             "timing": "wall clock around synchronous gvqe_batch_run calls"}
 
 
@@ -574,7 +581,11 @@ def run_gvqe(args):
         return 0
     if args.only_xy:
         if rank == 0:
-            print(json.dumps({"non_diagonal": xy_leg(max(1, args.steps))}), flush=True)
+            print(json.dumps({"non_diagonal": xy_leg(max(1, args.steps), args.xy_workload)}), flush=True)
+        return 0
+    if args.only_cluster:
+        if rank == 0:
+            print(json.dumps({"cluster_batch": cluster_leg(max(1, args.steps))}), flush=True)
         return 0
     if args.only_entanglers:
         if rank == 0:
@@ -590,6 +601,12 @@ def run_gvqe(args):
     E = torch.empty(B, dtype=torch.float64, device=dev)
     G = torch.empty(B, P, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
+
+    # the tile plan: measured by the library's autotuner on this workload (cached per key)
+    tune_cache = os.environ.get("GVQE_TUNE_CACHE", os.path.join("/tmp", "gvqe_tune.json"))
+    t0 = time.perf_counter()
+    tune_report = a.autotune(h, th, cache=tune_cache, stream=stream) if not args.no_tune else "not tuned"
+    tune_s = time.perf_counter() - t0
 
     def step():
         _lib.gvqe_energy_grad(a.handle, h.handle, th, None, E, G, _lib.GVQE_FP32, stream)
@@ -706,6 +723,8 @@ def run_gvqe(args):
                    "amplitudes": "fp32 (real: RY+CX keeps the state real), fp64 table and reductions",
                    "l2": "inputs larger than L2 (4 GiB state per pass)", "parallelism": f"replicas x{ws}"},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
+        "plan": {"autotune": tune_report.strip().splitlines(), "tune_seconds": tune_s, "cache": tune_cache,
+                 "layer_passes": [ln.strip() for ln in a.describe().splitlines() if "layer pass" in ln]},
     }
 
     if rank == 0 and not args.no_comparators:

@@ -188,12 +188,38 @@ int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *con
                    double *energies, double *const *grads, void *stream);
 
 /*
+ * gvqe_batch_set_option -- schedule option of a batch (Section IV-D, Eq. 11:
+ * the paper runs its blocks concurrently; the schedule of the one persistent
+ * launch is this library's own).
+ *   GVQE_BATCH_OPT_WAVE_BYTES: the persistent launch takes the instances,
+ *     larger first, in waves whose live bytes (three states of each instance:
+ *     a pass's input, output and stored state or table) add up to at most this
+ *     many bytes (0: one wave), each wave stage-major (every instance's pass s
+ *     before any instance's pass s + 1), so a wave's states can stay in L2
+ *     between their passes.  Default 0 (one wave).  The schedule is rebuilt on
+ *     the next run.
+ * Results do not depend on the option (each instance's passes and reductions
+ * are the same).  Errors: GVQE_EINVAL.
+ *
+ * gvqe_batch_autotune -- run the batch under each of the wave budgets 0, 64,
+ * 96, 128, 192 and 256 MiB (one warm-up run and three timed runs under CUDA
+ * events on `stream` each, with the caller's params / masks / outputs as in
+ * gvqe_batch_run) and keep the fastest.  report (host, report_len bytes, or
+ * NULL) receives the choice and the sweep.  A batch that runs instance by
+ * instance has nothing to tune.  Errors: those of gvqe_batch_run.
+ */
+#define GVQE_BATCH_OPT_WAVE_BYTES 1
+int gvqe_batch_set_option(gvqe_batch b, int option, long long value);
+int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t *const *masks, double *energies,
+                        double *const *grads, char *report, int report_len, void *stream);
+
+/*
  * gvqe_energy_static -- the energies of gvqe_energy, computed without any
  * device allocation.  The paper has no counterpart: this is for callers that
- * cannot allocate device memory when they need an energy (inside a stream
- * capture that must not allocate, under a runtime that owns every device
- * allocation of the process or enforces a fixed memory budget, or in a loop
- * that cannot afford the first-call workspace allocation of gvqe_energy).
+ * cannot allocate device memory when they need an energy (under a runtime
+ * that owns every device allocation of the process or enforces a fixed memory
+ * budget this library may not draw on, or in a loop that cannot afford the
+ * first-call workspace allocation of gvqe_energy).
  *   a, h:     handles as for gvqe_energy; h must be diagonal (I/Z letters only,
  *             else GVQE_EUNSUPPORTED).
  *   params:   device, batch x P doubles.  energies: device, batch doubles.
@@ -204,12 +230,64 @@ int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *con
  * (about n <= 19 at batch 1) return GVQE_EINVAL with the required size.  The
  * first call on each device looks up the array's device address (make it
  * before any stream capture).  Every call reuses the same array and clears what
- * must start at zero; calls whose GPU work overlaps in time race on it.
+ * must start at zero; calls whose GPU work overlaps in time race on it.  Its
+ * host-to-device copies read only memory owned by the handles (the merged
+ * diagonal terms of h, the cached energy plan of a).  Its launches count in
+ * gvqe_launch_count and the event profiler like those of gvqe_energy.
  * Errors: GVQE_EINVAL, GVQE_EUNSUPPORTED, GVQE_ECUDA.
  */
 #define GVQE_STATIC_SCRATCH_BYTES (16 * 1024 * 1024)
 int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int batch,
                        double *energies, int flags, void *stream);
+
+/*
+ * gvqe_autotune -- choose the ansatz's tile plan by measurement.  The paper has
+ * no counterpart (it names no kernel layout); the plan decides how the RY
+ * layers of Section IV-B are cut into tile passes for the evaluations of Eq. 4
+ * and Eq. 13.  Every distinct plan among tile bits 10 .. 13 (FP64: 10 .. 12)
+ * and the two strided layouts (one run of qubits per pass, or a low and a top
+ * run) runs the requested evaluation once to warm up and three times under
+ * CUDA events on `stream`; the fastest is kept on the ansatz as if set with
+ * GVQE_OPT_TILE_BITS and GVQE_OPT_SPLIT_PASSES.  Candidates that do not fit in
+ * device memory are skipped.  Results of the tuned plan equal those of any
+ * other plan up to the order of FP32/FP64 additions.
+ *   a, h:       handles with equal n.
+ *   params:     device, batch x P doubles (the evaluation that is timed).
+ *   flags:      GVQE_FP32 or GVQE_FP64, plus GVQE_TUNE_ENERGY to tune the
+ *               energy-only path (default: energy and adjoint gradient).
+ *   cache_path: host path of a JSON file of earlier winners, or NULL.  The
+ *               entry for this call's key (gvqe_tune_key) is used without any
+ *               timing when present; otherwise the sweep runs and its winner is
+ *               stored.  A missing, unreadable or malformed file counts as
+ *               empty and is rewritten whole; deleting it is always safe.
+ *   report:     host buffer of report_len bytes (or NULL): the choice and the
+ *               sweep, one "tb=<bits>/<layout>: <ms> ms" item per candidate.
+ *               The same text is appended to gvqe_ansatz_describe.
+ * Synchronises `stream`.  Errors: GVQE_EINVAL, GVQE_ENOMEM (no candidate fits),
+ * GVQE_ECUDA.
+ */
+#define GVQE_TUNE_ENERGY 0x4
+int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int batch, int flags,
+                  const char *cache_path, char *report, int report_len, void *stream);
+
+/*
+ * gvqe_tune_key -- the cache key gvqe_autotune uses for (a, h, batch, flags):
+ * GPU name (or "no-gpu"), n, reps, entangler, gate set, precision, gradient or
+ * energy only, diagonal H or not, batch.  Host only.  Errors: GVQE_EINVAL.
+ *
+ * gvqe_tune_cache_get -- look `key` up in the JSON cache at `path` (host only):
+ * returns 1 and fills tile_bits, split (0 auto, 1 one run, 2 split) and ms (may
+ * be NULL) when present, 0 when the file is missing, unreadable, malformed or
+ * has no such key, GVQE_EINVAL on NULL arguments.
+ *
+ * gvqe_tune_cache_put -- store or replace the entry for `key` (host only); an
+ * invalid existing file is replaced by one holding this entry.  The file is
+ * written to <path>.tmp and renamed over <path>.  Errors: GVQE_EINVAL (bad
+ * arguments, or the file cannot be written).
+ */
+int gvqe_tune_key(gvqe_ansatz a, gvqe_hamiltonian h, int batch, int flags, char *buf, int buflen);
+int gvqe_tune_cache_get(const char *path, const char *key, int *tile_bits, int *split, double *ms);
+int gvqe_tune_cache_put(const char *path, const char *key, int tile_bits, int split, double ms, const char *sweep);
 
 /*
  * gvqe_readout -- read out the prepared state |psi(theta)> (Section IV-F:

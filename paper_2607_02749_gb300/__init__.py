@@ -87,8 +87,20 @@ class Ansatz(_Handle):
         gvqe_ansatz_set_option(self.handle, GVQE_OPT_TILE_BITS, bits)
 
     def describe(self, fp64: bool = False) -> str:
-        """The tile-pass plan of this ansatz (host only)."""
+        """The tile-pass plan of this ansatz (host only), with the last autotune report."""
         return gvqe_ansatz_describe(self.handle, GVQE_FP64 if fp64 else GVQE_FP32)
+
+    def autotune(self, ham: "Hamiltonian", theta, fp64: bool = False, energy_only: bool = False,
+                 cache: Optional[str] = None, stream=None) -> str:
+        """Time every distinct tile plan on theta (CUDA float64 [B, P]) and keep the
+        fastest; `cache` is a JSON file of earlier winners (default: $GVQE_TUNE_CACHE,
+        none if unset).  Returns the report."""
+        import os
+
+        flags = (GVQE_FP64 if fp64 else GVQE_FP32) | (_lib.GVQE_TUNE_ENERGY if energy_only else 0)
+        th = theta.reshape(-1, self.n_params).contiguous()
+        path = cache if cache is not None else os.environ.get("GVQE_TUNE_CACHE")
+        return _lib.gvqe_autotune(self.handle, ham.handle, th, flags, path, stream)
 
 
 def _flags(fp64: bool, param_shift: bool = False) -> int:
@@ -171,6 +183,19 @@ class Batch(_Handle):
             energies = torch.empty(len(params), dtype=torch.float64, device=params[0].device)
         gvqe_batch_run(self.handle, params, masks, energies, grads, stream)
         return energies
+
+    def set_wave_bytes(self, nbytes: int) -> None:
+        """Workspace bytes per wave of the persistent schedule (0: one wave)."""
+        _lib.gvqe_batch_set_option(self.handle, _lib.GVQE_BATCH_OPT_WAVE_BYTES, nbytes)
+
+    def autotune(self, params: Sequence, masks: Optional[Sequence] = None, grads: Optional[Sequence] = None,
+                 energies=None, stream=None) -> str:
+        """Time the batch under each wave budget and keep the fastest; returns the report."""
+        import torch
+
+        if energies is None:
+            energies = torch.empty(len(params), dtype=torch.float64, device=params[0].device)
+        return _lib.gvqe_batch_autotune(self.handle, params, masks, energies, grads, stream)
 
 
 def _make_function():

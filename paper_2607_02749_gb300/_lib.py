@@ -41,6 +41,8 @@ GVQE_GATES_RY = 1
 GVQE_GATES_RY_RZ = 2
 GVQE_MAX_QUBITS = 30
 GVQE_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
+GVQE_TUNE_ENERGY = 0x4
+GVQE_BATCH_OPT_WAVE_BYTES = 1
 GVQE_PROF_FWD = 0
 GVQE_PROF_BWD = 1
 GVQE_PROF_GRAD_L0 = 2
@@ -94,6 +96,12 @@ _SIGS = {
     "gvqe_profile_reset": [],
     "gvqe_debug_check": [],
     "gvqe_debug_poke_guard": [_I],
+    "gvqe_batch_set_option": [_VP, _I, ctypes.c_longlong],
+    "gvqe_batch_autotune": [_VP, _VP, _VP, _VP, _VP, ctypes.c_char_p, _I, _VP],
+    "gvqe_autotune": [_VP, _VP, _VP, _I, _I, ctypes.c_char_p, ctypes.c_char_p, _I, _VP],
+    "gvqe_tune_key": [_VP, _VP, _I, _I, ctypes.c_char_p, _I],
+    "gvqe_tune_cache_get": [ctypes.c_char_p, ctypes.c_char_p, _VP, _VP, _VP],
+    "gvqe_tune_cache_put": [ctypes.c_char_p, ctypes.c_char_p, _I, _I, ctypes.c_double, ctypes.c_char_p],
 }
 
 
@@ -256,6 +264,23 @@ def gvqe_batch_run(batch: int, params: Sequence, masks: Optional[Sequence], ener
     _check(load().gvqe_batch_run(batch, pa, ma, _ptr(energies), ga, _stream(stream)), "gvqe_batch_run")
 
 
+def gvqe_batch_set_option(batch: int, option: int, value: int) -> None:
+    _check(load().gvqe_batch_set_option(batch, option, int(value)), "gvqe_batch_set_option")
+
+
+def gvqe_batch_autotune(batch: int, params: Sequence, masks: Optional[Sequence], energies,
+                        grads: Optional[Sequence], stream=None) -> str:
+    """Time the batch under each wave budget and keep the fastest; returns the report."""
+    n = len(params)
+    pa = (_VP * n)(*[_ptr(p) for p in params])
+    ma = (_VP * n)(*[_ptr(m) for m in masks]) if masks is not None else None
+    ga = (_VP * n)(*[_ptr(g) for g in grads]) if grads is not None else None
+    buf = ctypes.create_string_buffer(1 << 12)
+    _check(load().gvqe_batch_autotune(batch, pa, ma, _ptr(energies), ga, buf, len(buf), _stream(stream)),
+           "gvqe_batch_autotune")
+    return buf.value.decode()
+
+
 def gvqe_destroy(handle: Optional[int]) -> None:
     _check(load().gvqe_destroy(handle), "gvqe_destroy")
 
@@ -275,6 +300,38 @@ def gvqe_debug_check() -> None:
 def gvqe_debug_poke_guard(restore: bool = False) -> None:
     """Debug build, tests only: overwrite (or restore) the first guard byte above the largest workspace."""
     _check(load().gvqe_debug_poke_guard(1 if restore else 0), "gvqe_debug_poke_guard")
+
+
+def gvqe_autotune(ansatz: int, ham: int, params, flags: int = GVQE_FP32, cache_path: Optional[str] = None,
+                  stream=None) -> str:
+    """Pick the ansatz's tile plan by timing every distinct candidate on `params`
+    (CUDA float64 [B, P]); returns the report (choice and sweep)."""
+    _require_cuda(params)
+    batch = params.shape[0] if params.dim() > 1 else 1
+    buf = ctypes.create_string_buffer(1 << 14)
+    path = cache_path.encode() if cache_path else None
+    _check(load().gvqe_autotune(ansatz, ham, _ptr(params), batch, flags, path, buf, len(buf), _stream(stream)),
+           "gvqe_autotune")
+    return buf.value.decode()
+
+
+def gvqe_tune_key(ansatz: int, ham: int, batch: int, flags: int = GVQE_FP32) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    _check(load().gvqe_tune_key(ansatz, ham, batch, flags, buf, len(buf)), "gvqe_tune_key")
+    return buf.value.decode()
+
+
+def gvqe_tune_cache_get(path: str, key: str):
+    """(tile_bits, split, ms) of the cached entry for key, or None (host only)."""
+    tb, sp, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    rc = _check(load().gvqe_tune_cache_get(path.encode(), key.encode(), ctypes.byref(tb), ctypes.byref(sp),
+                                           ctypes.byref(ms)), "gvqe_tune_cache_get")
+    return (tb.value, sp.value, ms.value) if rc == 1 else None
+
+
+def gvqe_tune_cache_put(path: str, key: str, tile_bits: int, split: int, ms: float = 0.0, sweep: str = "") -> None:
+    _check(load().gvqe_tune_cache_put(path.encode(), key.encode(), tile_bits, split, ms, sweep.encode()),
+           "gvqe_tune_cache_put")
 
 
 def gvqe_ansatz_describe(a: int, flags: int = GVQE_FP32) -> str:

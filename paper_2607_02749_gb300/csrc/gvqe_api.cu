@@ -178,7 +178,7 @@ static double pass_bytes(int prec, const PassArgs &A, int jobs) {
   return b;
 }
 
-static cudaError_t launch_step(int prec, const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
+cudaError_t launch_step(int prec, const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
   ProfRec rec{};
   bool prof;
   {
@@ -1056,7 +1056,7 @@ static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s, bool c
 }
 
 // --------------------------------------------------------- plan execution --
-static Plan *get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool state_only = false) {
+Plan *gvqe::get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool state_only) {
   const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0) | (state_only ? 8 : 0) | (a->gates == 2 ? 16 : 0);
   auto it = a->plans.find(key);
   if (it != a->plans.end() && it->second.tile_bits == a->tile_bits) return &it->second;
@@ -1151,8 +1151,9 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
         int g1 = g0;
         while (g1 < ng) {
           const int nt = gsv[g1 + 1] - gsv[g0];
+          // real path: the group tables share the CTA with two 32 KiB (FP32 2^13 / FP64 2^12) partner tiles
           const size_t need = cplx ? xyc_smem_bytes(prec, g1 + 1 - g0, nt) : xy_smem_bytes(prec, g1 + 1 - g0, nt);
-          if (need > 160 * 1024) break;
+          if (need > (cplx ? 160 : 120) * 1024) break;
           ++g1;
         }
         if (g1 == g0) return fail(GVQE_EUNSUPPORTED, "X-mask group %d has too many terms", g0);
@@ -1197,8 +1198,8 @@ static int check_pair(gvqe_ansatz a, gvqe_hamiltonian h) {
 }
 
 // energies (and optionally adjoint gradients) for a batch
-static int energy_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, int batch,
-                       double *E, double *grad, int prec, cudaStream_t s) {
+int gvqe::energy_impl(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const uint8_t *mask, int batch,
+                      double *E, double *grad, int prec, cudaStream_t s) {
   const bool cplx = a->gates == 2;
   const bool diag = cplx ? h->cgm.empty() : h->gm.empty();
   GV_TRY(ensure_tables(h, prec, s, cplx));
@@ -1688,7 +1689,8 @@ int gvqe_ansatz_describe(gvqe_ansatz a, int flags, char *buf, int buflen) {
   const int prec = flags & GVQE_FP64 ? 1 : 0;
   if (a->tile_bits > max_tile_bits(prec)) return fail(GVQE_EINVAL, "tile bits %d too large", a->tile_bits);
   const Plan *pl = get_plan(a, prec, true, true);
-  const std::string s = describe_plan(*pl);
+  std::string s = describe_plan(*pl);
+  if (!a->tune_report.empty()) s += a->tune_report;
   if (buf && buflen > 0) {
     const size_t m = std::min<size_t>((size_t)buflen - 1, s.size());
     memcpy(buf, s.data(), m);
@@ -1718,6 +1720,7 @@ int gvqe_destroy(void *handle) {
     a->aux.release();
     a->shift.release();
     a->ro.release();
+    a->tune.release();
     for (auto &kv : a->plans) kv.second.d_dir.release();
     a->magic = 0;
     delete a;

@@ -20,6 +20,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "gvqe.h"
@@ -29,6 +30,7 @@
 namespace gvqe {
 
 enum StepKind : int { S_PREP = 0, S_PASS = 1, S_REDUCE = 2 };
+constexpr int SEG_BLK_BITS = 6;  // tickets per entry of the segment index: 64
 
 struct BatchStep {
   PassArgs A;        // pass arguments with this instance's buffers (job 0 of one)
@@ -53,6 +55,7 @@ struct BatchArgs {
   const BatchStep *steps;
   const unsigned *seg_start;  // first ticket of each step in schedule order
   const int *seg_step;        // step index of each segment
+  const int *blk_seg;         // segment holding ticket (b << SEG_BLK_BITS), per block b of tickets
   int nseg;
   unsigned total;
   unsigned *ticket;
@@ -145,43 +148,51 @@ __device__ void batch_pass(const PassArgs &A, uint32_t tile) {
   }
 }
 
+// Thread 0 of each CTA claims its next ticket while the current item runs (the
+// atomic's latency hides behind the item's work).  A CTA then holds two tickets
+// and always finishes the smaller first, so the smallest unfinished item is
+// always being run by the CTA that claimed it and its dependencies (smaller
+// tickets) are finished: the schedule still cannot deadlock.
 template <typename T, int TB>
 __global__ void __launch_bounds__(1 << (TB - 5), (TB == 12 && sizeof(T) == 4) ? 5 : 2) k_batch(const BatchArgs B) {
-  __shared__ unsigned s_item;
-  __shared__ int s_ok;
+  __shared__ unsigned s_tile;
+  __shared__ int s_si, s_ok;
+  unsigned next = 0;
+  if (threadIdx.x == 0) next = atomicAdd(B.ticket, 1u);
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(B.ticket, 1u);
-    __syncthreads();
-    const unsigned item = s_item;
-    if (item >= B.total) break;
-    // segment of this ticket: the last one whose start is <= item
-    int lo = 0, hi = B.nseg - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (B.seg_start[mid] <= item)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    const int si = B.seg_step[lo];
-    const unsigned tile = item - B.seg_start[lo];
-    const BatchStep &st = B.steps[si];
     if (threadIdx.x == 0) {
-      int ok = 1;
-      if (st.dep >= 0 && ld_acquire(B.done + st.dep) < st.dep_need) {
-        const long long t0 = clock64();
-        while (ld_acquire(B.done + st.dep) < st.dep_need) {
-          if (clock64() - t0 > B.timeout_cycles) {
-            atomicOr(B.err, 1);
-            ok = 0;
-            break;
+      const unsigned item = next;
+      if (item < B.total) {
+        next = atomicAdd(B.ticket, 1u);
+        // segment of this ticket: from the index entry of its block of tickets, forward
+        int lo = B.blk_seg[item >> SEG_BLK_BITS];
+        while (lo + 1 < B.nseg && B.seg_start[lo + 1] <= item) ++lo;
+        const int si = B.seg_step[lo];
+        const BatchStep &st = B.steps[si];
+        int ok = 1;
+        if (st.dep >= 0 && ld_acquire(B.done + st.dep) < st.dep_need) {
+          const long long t0 = clock64();
+          while (ld_acquire(B.done + st.dep) < st.dep_need) {
+            if (clock64() - t0 > B.timeout_cycles) {
+              atomicOr(B.err, 1);
+              ok = 0;
+              break;
+            }
+            __nanosleep(128);
           }
-          __nanosleep(128);
         }
+        s_si = si;
+        s_tile = item - B.seg_start[lo];
+        s_ok = ok;
+      } else {
+        s_si = -1;
       }
-      s_ok = ok;
     }
     __syncthreads();
+    const int si = s_si;
+    if (si < 0) break;
+    const unsigned tile = s_tile;
+    const BatchStep &st = B.steps[si];
     if (s_ok) {
       const BatchIO io = B.io[st.inst];
       if (st.kind == S_PREP)
@@ -220,6 +231,11 @@ static int batch_occupancy(size_t smem) {
 
 using namespace gvqe;
 
+// Live bytes per wave of the batch schedule (GVQE_BATCH_OPT_WAVE_BYTES, 0: one
+// wave); gvqe_batch_autotune picks among 0 and budgets sized so that a wave's
+// pass inputs and outputs fit the 129 MB L2.
+constexpr long long kDefaultWaveBytes = 0;
+
 // One compiled schedule (energy-only or energy + gradient).
 struct BatchSchedule {
   bool built = false;
@@ -232,12 +248,15 @@ struct BatchSchedule {
   cudaGraphExec_t exec = nullptr;
   int nsteps = 0;
   int counters = 0;
+  int waves = 0;
 };
 
 struct gvqe_batch_s {
   uint32_t magic = 0;
   int prec = 0;
   bool persistent = false;
+  long long wave_bytes = kDefaultWaveBytes;  // GVQE_BATCH_OPT_WAVE_BYTES
+  std::string tune_report;
   std::vector<gvqe_ansatz> a;
   std::vector<gvqe_hamiltonian> h;
   BatchSchedule sched[2];  // [0] energies only, [1] energies + gradients
@@ -326,25 +345,57 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
     st.dep = nsteps;  // a spare counter
     st.dep_need = 1;
   }
-  // stage-major schedule; within a stage the larger instances first
+  // Ticket order: the instances, larger first, cut into waves whose live bytes
+  // add up to at most wave_bytes (one wave when 0), and inside each wave
+  // stage-major (every instance's step s before any instance's step s + 1).  A
+  // wave's states are written and read again while they are still in L2; the
+  // next wave's first items need nothing from it and fill the GPU as it drains.
   std::vector<int> order(ni);
   for (int i = 0; i < ni; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->a[x]->n > b->a[y]->n; });
+  // an instance's live bytes while one of its passes runs: the pass input, its
+  // output and (backward) the stored forward state or the table
+  auto inst_bytes = [&](int i) { return (size_t)3 * sc.plans[i].state_elems * es; };
+  std::vector<std::vector<int>> waves;
+  size_t wave_sum = 0;
+  for (int i : order) {
+    const size_t bi = inst_bytes(i);
+    if (waves.empty() || (b->wave_bytes > 0 && wave_sum + bi > (size_t)b->wave_bytes && !waves.back().empty())) {
+      waves.emplace_back();
+      wave_sum = 0;
+    }
+    waves.back().push_back(i);
+    wave_sum += bi;
+  }
   std::vector<unsigned> seg_start;
   std::vector<int> seg_step;
   unsigned tick = 0;
-  size_t max_stage = 0;
-  for (int i = 0; i < ni; ++i) max_stage = std::max(max_stage, inst_steps[i].size());
-  for (size_t s = 0; s < max_stage; ++s)
-    for (int i : order) {
-      if (s >= inst_steps[i].size()) continue;
-      const int si = inst_steps[i][s];
-      seg_start.push_back(tick);
-      seg_step.push_back(si);
-      tick += steps[si].items;
-    }
+  for (const std::vector<int> &wv : waves) {
+    size_t max_stage = 0;
+    for (int i : wv) max_stage = std::max(max_stage, inst_steps[i].size());
+    for (size_t s = 0; s < max_stage; ++s)
+      for (int i : wv) {
+        if (s >= inst_steps[i].size()) continue;
+        const int si = inst_steps[i][s];
+        seg_start.push_back(tick);
+        seg_step.push_back(si);
+        tick += steps[si].items;
+      }
+  }
+  sc.waves = (int)waves.size();
   const int nseg = (int)seg_start.size();
   const int counters = nsteps + 1;
+  // segment index: for each block of 2^SEG_BLK_BITS tickets, the segment holding its first ticket
+  const unsigned nblk = (tick >> SEG_BLK_BITS) + 1;
+  std::vector<int> blk_seg(nblk);
+  {
+    int sg = 0;
+    for (unsigned bk = 0; bk < nblk; ++bk) {
+      const unsigned first = bk << SEG_BLK_BITS;
+      while (sg + 1 < nseg && seg_start[sg + 1] <= first) ++sg;
+      blk_seg[bk] = sg;
+    }
+  }
 
   // workspace offsets
   size_t off = 0;
@@ -354,6 +405,8 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   off = up256(off + sizeof(unsigned) * nseg);
   const size_t o_segstep = off;
   off = up256(off + sizeof(int) * nseg);
+  const size_t o_blkseg = off;
+  off = up256(off + sizeof(int) * nblk);
   const size_t o_ctr = off;  // ticket, err, done[counters]
   off = up256(off + sizeof(unsigned) * (2 + counters));
   const size_t o_io = off;
@@ -422,12 +475,14 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   GB_CUDA(cudaMemcpy(base + o_steps, steps.data(), sizeof(BatchStep) * nsteps, cudaMemcpyHostToDevice));
   GB_CUDA(cudaMemcpy(base + o_segs, seg_start.data(), sizeof(unsigned) * nseg, cudaMemcpyHostToDevice));
   GB_CUDA(cudaMemcpy(base + o_segstep, seg_step.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice));
+  GB_CUDA(cudaMemcpy(base + o_blkseg, blk_seg.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice));
   if (!dirs.empty()) GB_CUDA(cudaMemcpy(base + o_dir, dirs.data(), sizeof(RedEntry) * dirs.size(), cudaMemcpyHostToDevice));
 
   BatchArgs &B = sc.args;
   B.steps = (const BatchStep *)(base + o_steps);
   B.seg_start = (const unsigned *)(base + o_segs);
   B.seg_step = (const int *)(base + o_segstep);
+  B.blk_seg = (const int *)(base + o_blkseg);
   B.nseg = nseg;
   B.total = tick;
   B.ticket = (unsigned *)(base + o_ctr);
@@ -531,6 +586,95 @@ int gvqe_batch_create(int n_inst, const gvqe_ansatz *ansatze, const gvqe_hamilto
   b->a.assign(ansatze, ansatze + n_inst);
   b->h.assign(hams, hams + n_inst);
   *out = b;
+  return GVQE_OK;
+}
+
+int gvqe_batch_set_option(gvqe_batch b, int option, long long value) {
+  g_err.clear();
+  if (!b || b->magic != MAGIC_BATCH) return fail(GVQE_EINVAL, "invalid batch handle");
+  if (option != GVQE_BATCH_OPT_WAVE_BYTES) return fail(GVQE_EINVAL, "unknown batch option %d", option);
+  if (value < 0) return fail(GVQE_EINVAL, "wave bytes %lld < 0", value);
+  if (value == b->wave_bytes) return GVQE_OK;
+  cudaDeviceSynchronize();
+  b->wave_bytes = value;
+  for (BatchSchedule &sc : b->sched) {  // rebuilt (and recaptured) on the next run
+    if (sc.exec) cudaGraphExecDestroy(sc.exec);
+    if (sc.graph) cudaGraphDestroy(sc.graph);
+    sc.exec = nullptr;
+    sc.graph = nullptr;
+    sc.built = false;
+  }
+  b->io_valid[0] = b->io_valid[1] = false;
+  return GVQE_OK;
+}
+
+int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *const *masks, double *energies,
+                   double *const *grads, void *stream);
+
+int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t *const *masks, double *energies,
+                        double *const *grads, char *report, int report_len, void *stream) {
+  g_err.clear();
+  if (!b || b->magic != MAGIC_BATCH) return fail(GVQE_EINVAL, "invalid batch handle");
+  std::string rep;
+  auto put = [&]() {
+    if (report && report_len > 0) {
+      const size_t m = std::min<size_t>((size_t)report_len - 1, rep.size());
+      memcpy(report, rep.data(), m);
+      report[m] = 0;
+    }
+  };
+  if (!b->persistent) {
+    rep = "batch autotune: instance by instance (no persistent schedule to tune)\n";
+    put();
+    return GVQE_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long cands[] = {0, 64ll << 20, 96ll << 20, 128ll << 20, 192ll << 20, 256ll << 20};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GB_CUDA(cudaEventCreate(&e0));
+  GB_CUDA(cudaEventCreate(&e1));
+  const long long keep = b->wave_bytes;
+  long long best = -1;
+  double best_ms = 0.0;
+  std::string sweep;
+  int rc = GVQE_OK;
+  for (long long wb : cands) {
+    rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_WAVE_BYTES, wb);
+    if (rc == GVQE_OK) rc = gvqe_batch_run(b, params, masks, energies, grads, stream);  // build + warm
+    if (rc != GVQE_OK) break;
+    const int timed = 3;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < timed && rc == GVQE_OK; ++r) rc = gvqe_batch_run(b, params, masks, energies, grads, stream);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    if (rc != GVQE_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = ms / timed;
+    const int g = grads ? 1 : 0;
+    char line[160];
+    snprintf(line, sizeof(line), "%swave=%lldMiB (%d waves): %.3f ms", sweep.empty() ? "" : "; ", wb >> 20,
+             b->sched[g].waves, per);
+    sweep += line;
+    if (best < 0 || per < best_ms) {
+      best = wb;
+      best_ms = per;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != GVQE_OK) {
+    gvqe_batch_set_option(b, GVQE_BATCH_OPT_WAVE_BYTES, keep);
+    return rc;
+  }
+  rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_WAVE_BYTES, best);
+  if (rc != GVQE_OK) return rc;
+  char line[200];
+  snprintf(line, sizeof(line), "batch autotune: wave bytes %lld MiB (%s), %.3f ms per run\n", best >> 20,
+           best == 0 ? "one wave" : "waves", best_ms);
+  rep = std::string(line) + "batch autotune sweep: " + sweep + "\n";
+  b->tune_report = rep;
+  put();
   return GVQE_OK;
 }
 

@@ -76,6 +76,9 @@ void count_launches(int k);
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false,
                 bool state_only = false, int ent = ENT_LINEAR, int gates = 1, int split = SPLIT_AUTO);
 std::string describe_plan(const Plan &pl);
+// One tile-pass launch, counted by gvqe_launch_count and timed by the event
+// profiler when it is on.
+cudaError_t launch_step(int prec, const PassArgs &A, int jobs, int nterm, cudaStream_t s);
 
 }  // namespace gvqe
 
@@ -119,8 +122,20 @@ struct gvqe_ansatz_s {
   int tile_bits = 0;  // 0 = automatic
   int split = 0;      // gvqe::SplitMode
   std::map<int, gvqe::Plan> plans;
-  gvqe::DevBuf ws, aux, shift, ro;
+  gvqe::DevBuf ws, aux, shift, ro, tune;
+  std::string tune_report;  // the last gvqe_autotune sweep and its choice (empty: not tuned)
 };
 
 struct gvqe_batch_s;
 int batch_destroy(gvqe_batch_s *b);
+
+namespace gvqe {
+// The ansatz's cached plan for (precision, gradient or not, diagonal H or not,
+// state only); it and its host-side reduction directory live until the
+// ansatz is destroyed or one of its options changes.
+Plan *get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool state_only = false);
+// Energies (and adjoint gradients when grad != NULL) of a batch: the body of
+// gvqe_energy / gvqe_energy_grad after their argument checks.
+int energy_impl(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, const double *params, const uint8_t *mask, int batch,
+                double *E, double *grad, int prec, cudaStream_t s);
+}  // namespace gvqe

@@ -1,14 +1,14 @@
 // gvqe_static.cu -- gvqe_energy_static: energies without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need an
-// energy: code running inside a CUDA stream capture that must not create
-// allocations, an embedding runtime that owns every cudaMalloc of the process
-// (a custom allocator or a fixed memory budget), or a latency-critical loop
-// where the first-call allocation of the regular workspaces is not acceptable.
-// For them this entry point evaluates the same energies as gvqe_energy for
-// small registers with every scratch buffer (diagonal table, trig table,
-// state vectors, partial sums, reduction directory) carved out of one
-// file-scope device array of fixed size, GVQE_STATIC_SCRATCH_BYTES.
+// energy: an embedding runtime that owns every cudaMalloc of the process (a
+// custom allocator or a fixed memory budget that this library may not draw
+// on), or a latency-critical loop where the first-call allocation of the
+// regular workspaces is not acceptable.  For them this entry point evaluates
+// the same energies as gvqe_energy for small registers with every scratch
+// buffer (diagonal table, trig table, state vectors, partial sums, reduction
+// directory) carved out of one file-scope device array of fixed size,
+// GVQE_STATIC_SCRATCH_BYTES.
 //
 // The array lives in every GPU that loads this library until the process
 // exits.  Host code cannot use the array's symbol as a device address, so the
@@ -17,7 +17,9 @@
 // stream capture.  All calls share the one array and the last call's contents
 // stay in it: everything that must start at zero is cleared by each call, and
 // two calls whose GPU work overlaps (different streams, or different host
-// threads on one device) race on the array.
+// threads on one device) race on the array.  Every host-to-device copy reads
+// host memory owned by the two handles (the Hamiltonian's merged Z-masks and
+// coefficients, the ansatz's cached energy plan), never a local of this call.
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -76,8 +78,9 @@ extern "C" int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const doubl
   if (a->tile_bits > max_tile_bits(prec)) return fail(GVQE_EINVAL, "tile bits %d too large", a->tile_bits);
   cudaStream_t s = (cudaStream_t)stream;
 
-  // The energy plan: forward passes with the energy fused into the last one.
-  const Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, false, true, false, false, a->ent, 1, a->split);
+  // The energy plan (forward passes with the energy fused into the last one),
+  // cached on the ansatz so that its reduction directory outlives this call.
+  const Plan &pl = *get_plan(a, prec, false, true);
   const int n = a->n, P = pl.P;
   const size_t S = (size_t)1 << n;
   const size_t es = prec ? 8 : 4;
@@ -126,6 +129,7 @@ extern "C" int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const doubl
     GS_CUDA(cudaMemcpyAsync(b + o_dz, h->dz.data(), ndz * 4, cudaMemcpyHostToDevice, s));
     GS_CUDA(cudaMemcpyAsync(b + o_dc, h->dc.data(), ndz * 8, cudaMemcpyHostToDevice, s));
     GS_CUDA(launch_scatter_coeffs((const uint32_t *)(b + o_dz), (const double *)(b + o_dc), (int)ndz, t64, s));
+    count_launches(1);
     for (const LayerPass &lp : layer_passes(n, 1, 0)) {
       PassArgs A;
       memset(&A, 0, sizeof(A));
@@ -139,14 +143,18 @@ extern "C" int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const doubl
       A.in = t64;
       A.out = t64;
       A.P = 1;
-      GS_CUDA(launch_pass(1, A, 1, 0, s));
+      GS_CUDA(launch_step(1, A, 1, 0, s));
     }
   }
-  if (!prec) GS_CUDA(launch_convert_table(t64, t32, (long long)S, s));
+  if (!prec) {
+    GS_CUDA(launch_convert_table(t64, t32, (long long)S, s));
+    count_launches(1);
+  }
 
   // trig table and reduction directory
   void *cs = b + o_cs;
   GS_CUDA(launch_trig(prec, params, (long long)batch * P, cs, s));
+  count_launches(1);
   GS_CUDA(cudaMemcpyAsync(b + o_dir, pl.dir.data(), pl.dir.size() * sizeof(RedEntry), cudaMemcpyHostToDevice, s));
 
   double *part = (double *)(b + o_part);
@@ -170,12 +178,11 @@ extern "C" int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const doubl
     A.epart = part + (st.epart_region >= 0 ? st.epart_region : 0);
     A.part_stride = pl.part_stride;
     A.minlayer = nullptr;
-    GS_CUDA(launch_pass(prec, A, batch, 0, s));
+    GS_CUDA(launch_step(prec, A, batch, 0, s));
   }
   GS_CUDA(launch_reduce(part, pl.part_stride, (const RedEntry *)(b + o_dir), (int)pl.dir.size(), nullptr, P,
                         energies, nullptr, batch, s));
-  // The host -> device copies above read pageable host memory, so each returned
-  // only after its source was staged; the local plan may go out of scope.
+  count_launches(1);
 #undef GS_CUDA
   return GVQE_OK;
 }

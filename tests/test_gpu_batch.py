@@ -51,12 +51,15 @@ def test_persistent_batch_matches_single_calls_and_oracle(fp64):
             if fp64:
                 assert np.max(np.abs(g - g1)) <= 1e-9 * scale
             else:
-                assert np.linalg.norm(g - g1) <= 1e-4 * max(np.linalg.norm(g1), 1e-3 * scale)
+                assert np.linalg.norm(g - g1) <= 1e-4 * np.linalg.norm(g1)
             if rep == 0 and k < 3:
                 e_ref, g_ref = oracle.energy_grad(i.n_qubits, i.reps, i.theta[0], i.ham.strings, i.ham.coeffs)
                 g_ref = np.where(i.mask[0] == 1, g_ref, 0.0)
                 assert abs(e[k] - e_ref) <= tol_e
-                assert np.linalg.norm(g - g_ref) <= (1e-9 if fp64 else 1e-4) * max(np.linalg.norm(g_ref), scale * 1e-3)
+                if fp64:
+                    assert np.max(np.abs(g - g_ref)) <= 1e-9 * scale
+                else:
+                    assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
 
 
 def test_persistent_batch_energies_only_and_pointer_change():
@@ -83,7 +86,29 @@ def test_cluster_workload_256_instances():
         scale = i.ham.abs_sum()
         assert abs(e[k] - e1.item()) <= 2e-5 * scale
         g1 = g1.cpu().numpy()[0]
-        assert np.linalg.norm(grads[k].cpu().numpy() - g1) <= 1e-4 * max(np.linalg.norm(g1), 1e-3 * scale)
+        assert np.linalg.norm(grads[k].cpu().numpy() - g1) <= 1e-4 * np.linalg.norm(g1)
+
+
+def test_wave_schedules_give_identical_results_and_autotune_keeps_them():
+    """The wave budget only reorders independent items: every budget gives the
+    same bits; the batch autotuner times each budget and keeps one."""
+    insts = wl.cluster_batch(40, qubit_range=(13, 18), reps_range=(1, 3), terms_per_qubit=10)
+    ans, hams, b, params, masks = _setup(insts)
+    outs = []
+    for wb in (0, 1 << 20, 8 << 20, 48 << 20):
+        b.set_wave_bytes(wb)
+        grads = [torch.full_like(p, float("nan")) for p in params]
+        e = b.run(params, masks=masks, grads=grads).cpu().numpy()
+        outs.append((e, [g.cpu().numpy() for g in grads]))
+    for e, gs in outs[1:]:
+        assert np.array_equal(e, outs[0][0])
+        for g, g0 in zip(gs, outs[0][1]):
+            assert np.array_equal(g, g0)
+    grads = [torch.empty_like(p) for p in params]
+    rep = b.autotune(params, masks=masks, grads=grads)
+    assert "batch autotune: wave bytes" in rep and rep.count("ms") >= 6, rep
+    e = b.run(params, masks=masks, grads=grads).cpu().numpy()
+    assert np.array_equal(e, outs[0][0])
 
 
 def test_bounded_wait_returns_timeout_and_context_survives():

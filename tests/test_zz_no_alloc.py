@@ -1,10 +1,12 @@
 """gvqe_energy_static: energies for callers that cannot allocate device memory.
 
 The entry point computes the same energies as gvqe_energy but takes every
-scratch buffer from a fixed device array inside the library, so it works where
-a device allocation is not allowed (inside a stream capture, under an allocator
-or memory budget the caller does not control).  These tests call it through the
-C ABI twice in a row and compare each result with gvqe_energy within the parity
+scratch buffer from a fixed device array inside the library, so it serves
+callers whose runtime owns every device allocation or holds the process to a
+memory budget this library may not draw on.  These tests call it through the C
+ABI twice in a row, on handles whose tables gvqe_energy never built, check that
+the library's device memory does not change across those calls, and compare
+each result with gvqe_energy (on a second pair of handles) within the parity
 tolerances; the file is collected last so a failure here leaves every other
 test already run.
 """
@@ -28,15 +30,23 @@ from paper_2607_02749_gb300 import _lib  # noqa: E402
 def test_static_energy_matches_gvqe_energy_on_two_calls(n, reps, tb, batch, fp64):
     ham = wl.z_hamiltonian(n, 8 * n, seed=n)
     th = torch.as_tensor(wl.thetas(n, reps, batch, seed=2 * n), dtype=torch.float64, device="cuda")
+    flags = _lib.GVQE_FP64 if fp64 else _lib.GVQE_FP32
+    tol = (1e-10 if fp64 else 2e-5) * ham.abs_sum()
+    # handles only the static entry point ever sees: no table, plan or workspace
+    # of gvqe_energy exists for them
     a = gv.Ansatz(n, reps, tile_bits=tb)
     h = gv.Hamiltonian.from_workload(ham)
-    flags = _lib.GVQE_FP64 if fp64 else _lib.GVQE_FP32
-    e_ref = gv.energy(a, h, th, fp64=fp64).cpu().numpy()
-    tol = (1e-10 if fp64 else 2e-5) * ham.abs_sum()
-    for _ in range(2):
-        e = torch.full((batch,), float("nan"), dtype=torch.float64, device="cuda")
+    outs = [torch.full((batch,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    held = _lib.gvqe_device_memory_in_use()
+    for e in outs:
         _lib.gvqe_energy_static(a.handle, h.handle, th, e, flags)
         torch.cuda.synchronize()
+    assert _lib.gvqe_device_memory_in_use() == held
+    a_ref = gv.Ansatz(n, reps, tile_bits=tb)
+    h_ref = gv.Hamiltonian.from_workload(ham)
+    e_ref = gv.energy(a_ref, h_ref, th, fp64=fp64).cpu().numpy()
+    for e in outs:
         e = e.cpu().numpy()
         assert np.all(np.isfinite(e))
         assert np.max(np.abs(e - e_ref)) <= tol
