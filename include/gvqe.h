@@ -160,12 +160,15 @@ int gvqe_energy_grad(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, co
 /*
  * gvqe_batch_create -- a fixed set of independent restricted-update problems
  * (Section IV-D, Eq. 11): instance i pairs ansatze[i] with hams[i] (equal n)
- * and evaluates one parameter vector with its own active mask per run.  When
- * every instance has n >= 12, RY layers and a diagonal (I/Z-only) Hamiltonian,
- * all instances run in one persistent kernel launch on 2^12-amplitude tiles,
- * captured in a CUDA graph; otherwise they run one after another through
- * gvqe_energy_grad.  The tile size fixes the summation order, so results agree
- * with single calls within the precision bounds, not bit for bit.
+ * and evaluates one parameter vector with its own active mask per run.  The
+ * same pair of handles may appear in several slots (several parameter vectors
+ * of one subproblem per run).  Instances with n >= 12, RY layers and a
+ * diagonal (I/Z-only) Hamiltonian run together in one persistent kernel
+ * launch on 2^12-amplitude tiles, captured in a CUDA graph; the others (n <
+ * 12, X/Y strings, RY+RZ layers) are evaluated by single gvqe_energy_grad
+ * calls on the same stream in the same gvqe_batch_run, after that launch.
+ * The tile size fixes the summation order, so persistent results agree with
+ * single calls within the precision bounds, not bit for bit.
  *   n_inst: >= 1.  ansatze, hams: host arrays of n_inst handles (borrowed: they
  *   must outlive the batch).  flags: GVQE_FP32 or GVQE_FP64.
  * Errors: GVQE_EINVAL, GVQE_ENOMEM, GVQE_ECUDA, GVQE_EUNSUPPORTED.
@@ -196,19 +199,35 @@ int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *con
  *     a pass's input, output and stored state or table) add up to at most this
  *     many bytes (0: one wave), each wave stage-major (every instance's pass s
  *     before any instance's pass s + 1), so a wave's states can stay in L2
- *     between their passes.  Default 0 (one wave).  The schedule is rebuilt on
- *     the next run.
+ *     between their passes.  Default 0 (one wave).
+ *   GVQE_BATCH_OPT_SCHEDULE: GVQE_BATCH_PERSISTENT (default): one persistent
+ *     launch whose CTAs claim items in ticket order and wait (bounded) for the
+ *     previous step of the item's instance; GVQE_BATCH_STAGED: one launch per
+ *     stage (every instance's step s), each CTA one item, the stream order
+ *     between the launches in place of the waits.  Both are captured in the
+ *     batch's CUDA graph.
+ *   GVQE_BATCH_OPT_TILE_BITS: 10, 11 or 12 (default), the log2 amplitudes of
+ *     one work item of the persistent launch (FP32; FP64 batches take 12 only,
+ *     else GVQE_EUNSUPPORTED).  2^10 makes every CTA one warp.  Instances with
+ *     fewer qubits than this are evaluated by single calls in the same run.
+ * The schedule is rebuilt on the next run.
  * Results do not depend on the option (each instance's passes and reductions
  * are the same).  Errors: GVQE_EINVAL.
  *
- * gvqe_batch_autotune -- run the batch under each of the wave budgets 0, 64,
- * 96, 128, 192 and 256 MiB (one warm-up run and three timed runs under CUDA
+ * gvqe_batch_autotune -- run the batch under both schedules and each tile size
+ * 2^12, 2^11, 2^10 (FP64: 2^12), one wave, and persistent 2^12 with 256 MiB
+ * waves (one warm-up run and three
+ * timed runs under CUDA
  * events on `stream` each, with the caller's params / masks / outputs as in
  * gvqe_batch_run) and keep the fastest.  report (host, report_len bytes, or
  * NULL) receives the choice and the sweep.  A batch that runs instance by
  * instance has nothing to tune.  Errors: those of gvqe_batch_run.
  */
 #define GVQE_BATCH_OPT_WAVE_BYTES 1
+#define GVQE_BATCH_OPT_TILE_BITS 2
+#define GVQE_BATCH_OPT_SCHEDULE 3
+#define GVQE_BATCH_PERSISTENT 0
+#define GVQE_BATCH_STAGED 1
 int gvqe_batch_set_option(gvqe_batch b, int option, long long value);
 int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t *const *masks, double *energies,
                         double *const *grads, char *report, int report_len, void *stream);
@@ -247,8 +266,9 @@ int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, 
  * and Eq. 13.  Every distinct plan among tile bits 10 .. 13 (FP64: 10 .. 12)
  * and the two strided layouts (one run of qubits per pass, or a low and a top
  * run) runs the requested evaluation once to warm up and three times under
- * CUDA events on `stream`; the fastest is kept on the ansatz as if set with
- * GVQE_OPT_TILE_BITS and GVQE_OPT_SPLIT_PASSES.  Candidates that do not fit in
+ * CUDA events on `stream`; the fastest becomes the ansatz's plan in that
+ * precision (the other precision keeps its own; setting GVQE_OPT_TILE_BITS or
+ * GVQE_OPT_SPLIT_PASSES later replaces both).  Candidates that do not fit in
  * device memory are skipped.  Results of the tuned plan equal those of any
  * other plan up to the order of FP32/FP64 additions.
  *   a, h:       handles with equal n.
@@ -282,8 +302,10 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
  *
  * gvqe_tune_cache_put -- store or replace the entry for `key` (host only); an
  * invalid existing file is replaced by one holding this entry.  The file is
- * written to <path>.tmp and renamed over <path>.  Errors: GVQE_EINVAL (bad
- * arguments, or the file cannot be written).
+ * written to <path>.tmp<pid> and renamed over <path>.  Errors: GVQE_EINVAL (bad
+ * arguments, or the file cannot be written).  Several processes may tune into
+ * one file: each writes its own temporary and renames it over the file, so the
+ * file is always whole (the last writer's entries win).
  */
 int gvqe_tune_key(gvqe_ansatz a, gvqe_hamiltonian h, int batch, int flags, char *buf, int buflen);
 int gvqe_tune_cache_get(const char *path, const char *key, int *tile_bits, int *split, double *ms);

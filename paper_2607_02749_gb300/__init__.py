@@ -83,6 +83,11 @@ class Ansatz(_Handle):
         if split:
             gvqe_ansatz_set_option(self.handle, GVQE_OPT_SPLIT_PASSES, split)
 
+    def set_schedule(self, staged: bool) -> None:
+        """One launch per stage (True) or one persistent launch (False, the default)."""
+        _lib.gvqe_batch_set_option(self.handle, _lib.GVQE_BATCH_OPT_SCHEDULE,
+                                   _lib.GVQE_BATCH_STAGED if staged else _lib.GVQE_BATCH_PERSISTENT)
+
     def set_tile_bits(self, bits: int) -> None:
         gvqe_ansatz_set_option(self.handle, GVQE_OPT_TILE_BITS, bits)
 
@@ -183,6 +188,15 @@ class Batch(_Handle):
             energies = torch.empty(len(params), dtype=torch.float64, device=params[0].device)
         gvqe_batch_run(self.handle, params, masks, energies, grads, stream)
         return energies
+
+    def set_schedule(self, staged: bool) -> None:
+        """One launch per stage (True) or one persistent launch (False, the default)."""
+        _lib.gvqe_batch_set_option(self.handle, _lib.GVQE_BATCH_OPT_SCHEDULE,
+                                   _lib.GVQE_BATCH_STAGED if staged else _lib.GVQE_BATCH_PERSISTENT)
+
+    def set_tile_bits(self, bits: int) -> None:
+        """log2 amplitudes of one work item of the persistent launch (10, 11 or 12)."""
+        _lib.gvqe_batch_set_option(self.handle, _lib.GVQE_BATCH_OPT_TILE_BITS, bits)
 
     def set_wave_bytes(self, nbytes: int) -> None:
         """Workspace bytes per wave of the persistent schedule (0: one wave)."""

@@ -43,6 +43,10 @@ GVQE_MAX_QUBITS = 30
 GVQE_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 GVQE_TUNE_ENERGY = 0x4
 GVQE_BATCH_OPT_WAVE_BYTES = 1
+GVQE_BATCH_OPT_TILE_BITS = 2
+GVQE_BATCH_OPT_SCHEDULE = 3
+GVQE_BATCH_PERSISTENT = 0
+GVQE_BATCH_STAGED = 1
 GVQE_PROF_FWD = 0
 GVQE_PROF_BWD = 1
 GVQE_PROF_GRAD_L0 = 2

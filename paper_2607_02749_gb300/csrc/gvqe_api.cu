@@ -1059,10 +1059,11 @@ static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s, bool c
 Plan *gvqe::get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool state_only) {
   const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0) | (state_only ? 8 : 0) | (a->gates == 2 ? 16 : 0);
   auto it = a->plans.find(key);
-  if (it != a->plans.end() && it->second.tile_bits == a->tile_bits) return &it->second;
-  Plan pl = build_plan(a->n, a->reps, prec, a->tile_bits, want_grad, diag, false, state_only, a->ent, a->gates,
-                       a->split);
-  pl.tile_bits = a->tile_bits;
+  const int tb = eff_tile_bits(a, prec);
+  if (it != a->plans.end() && it->second.tile_bits == tb) return &it->second;
+  Plan pl = build_plan(a->n, a->reps, prec, tb, want_grad, diag, false, state_only, a->ent, a->gates,
+                       eff_split(a, prec));
+  pl.tile_bits = tb;
   a->plans[key] = std::move(pl);
   return &a->plans[key];
 }
@@ -1363,6 +1364,9 @@ int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
     if (value != 0 && (value < 10 || value > 13))
       return fail(GVQE_EINVAL, "tile bits %d outside [10, 13] (0 = auto)", value);
     a->tile_bits = value;
+    a->tuned_tb[0] = a->tuned_tb[1] = 0;  // an explicit choice replaces a tuned one
+    a->tuned_split[0] = a->tuned_split[1] = -1;
+    a->tune_report.clear();
     a->plans.clear();
     return GVQE_OK;
   }
@@ -1370,6 +1374,9 @@ int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
     if (value < SPLIT_AUTO || value > SPLIT_ALWAYS)
       return fail(GVQE_EINVAL, "split mode %d is not 0 (auto), 1 (never) or 2 (always)", value);
     a->split = value;
+    a->tuned_tb[0] = a->tuned_tb[1] = 0;
+    a->tuned_split[0] = a->tuned_split[1] = -1;
+    a->tune_report.clear();
     a->plans.clear();
     return GVQE_OK;
   }
@@ -1389,8 +1396,8 @@ static int common_checks(gvqe_ansatz a, gvqe_hamiltonian h, const void *params, 
   if (batch < 1) return fail(GVQE_EINVAL, "batch=%d < 1", batch);
   if (flags & ~(GVQE_FP64 | GVQE_GRAD_PARAM_SHIFT)) return fail(GVQE_EINVAL, "unknown flags 0x%x", flags);
   const int prec = flags & GVQE_FP64 ? 1 : 0;
-  if (a->tile_bits > max_tile_bits(prec))
-    return fail(GVQE_EINVAL, "tile bits %d above the %s maximum %d", a->tile_bits, prec ? "FP64" : "FP32",
+  if (eff_tile_bits(a, prec) > max_tile_bits(prec))
+    return fail(GVQE_EINVAL, "tile bits %d above the %s maximum %d", eff_tile_bits(a, prec), prec ? "FP64" : "FP32",
                 max_tile_bits(prec));
   return GVQE_OK;
 }
@@ -1687,7 +1694,8 @@ int gvqe_ansatz_describe(gvqe_ansatz a, int flags, char *buf, int buflen) {
   if (!is_ansatz(a)) return fail(GVQE_EINVAL, "invalid ansatz handle");
   if (flags & ~GVQE_FP64) return fail(GVQE_EINVAL, "flags 0x%x: only GVQE_FP32 / GVQE_FP64 apply", flags);
   const int prec = flags & GVQE_FP64 ? 1 : 0;
-  if (a->tile_bits > max_tile_bits(prec)) return fail(GVQE_EINVAL, "tile bits %d too large", a->tile_bits);
+  if (eff_tile_bits(a, prec) > max_tile_bits(prec))
+    return fail(GVQE_EINVAL, "tile bits %d too large", eff_tile_bits(a, prec));
   const Plan *pl = get_plan(a, prec, true, true);
   std::string s = describe_plan(*pl);
   if (!a->tune_report.empty()) s += a->tune_report;

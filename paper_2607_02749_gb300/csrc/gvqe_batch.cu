@@ -148,27 +148,79 @@ __device__ void batch_pass(const PassArgs &A, uint32_t tile) {
   }
 }
 
-// Thread 0 of each CTA claims its next ticket while the current item runs (the
-// atomic's latency hides behind the item's work).  A CTA then holds two tickets
-// and always finishes the smaller first, so the smallest unfinished item is
-// always being run by the CTA that claimed it and its dependencies (smaller
-// tickets) are finished: the schedule still cannot deadlock.
+// Bring the inputs of one future item into L2 (a hint: no data is waited for or
+// kept).  Forward passes that gather through the entangler or start from the
+// analytic product state are left out; the others read their tile as rows of
+// 2^c contiguous amplitudes (a whole 2^TB run in layout FULL).
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 template <typename T, int TB>
-__global__ void __launch_bounds__(1 << (TB - 5), (TB == 12 && sizeof(T) == 4) ? 5 : 2) k_batch(const BatchArgs B) {
-  __shared__ unsigned s_tile;
-  __shared__ int s_si, s_ok;
-  unsigned next = 0;
-  if (threadIdx.x == 0) next = atomicAdd(B.ticket, 1u);
+__device__ void batch_prefetch(const BatchStep &st, unsigned tile) {
+  if (st.kind != S_PASS) return;
+  const PassArgs &A = st.A;
+  if (A.kind == K_FWD && A.load_mode != LD_PLAIN) return;
+  const T *src[2] = {nullptr, nullptr};
+  if (A.kind == K_FWD) {
+    src[0] = reinterpret_cast<const T *>(A.in);
+  } else if (A.kind == K_BWD) {
+    src[0] = reinterpret_cast<const T *>(A.in);
+    src[1] = reinterpret_cast<const T *>((A.flags & F_LAMBDA_INIT) ? A.table : A.lam_in);
+  } else if (A.kind == K_GRAD_L0) {
+    src[0] = reinterpret_cast<const T *>(A.lam_in);
+  } else {
+    return;
+  }
+  const bool full = A.c >= TB;
+  const uint32_t base = (A.kind == K_GRAD_L0) ? (tile << TB) : tile_base(tile_of_block(tile, (uint32_t)A.tiles, A.pair_mask), A, TB);
+  constexpr int LINE = 128 / (int)sizeof(T);  // amplitudes per 128-byte line
+  const int run = full ? (1 << TB) : (1 << A.c);
+  const int lines_per_run = run > LINE ? run / LINE : 1;
+  const int step = run > LINE ? LINE : run;
+  const int nlines = (1 << TB) / step;
+  for (int i = threadIdx.x; i < nlines; i += blockDim.x) {
+    const uint32_t r = (uint32_t)(i / lines_per_run), l = (uint32_t)(i % lines_per_run);
+    const uint32_t off = full ? base + (uint32_t)i * LINE : base + tile_goff(r << A.c, A) + l * LINE;
+    prefetch_l2(src[0] + off);
+    if (src[1]) prefetch_l2(src[1] + off);
+  }
+}
+
+// Thread 0 of each CTA holds two claimed tickets besides the current item: the
+// next item's inputs are prefetched into L2 while the current one runs, and the
+// ticket after it is claimed then (the atomic's latency hides behind the item's
+// work).  A CTA always finishes the smallest ticket it holds first, so the
+// smallest unfinished item is always being run by the CTA that claimed it and
+// its dependencies (smaller tickets) are finished: the schedule still cannot
+// deadlock.
+template <typename T, int TB>
+__global__ void __launch_bounds__(1 << (TB - 5), sizeof(T) == 8 ? 2 : (TB == 12 ? 5 : (TB == 11 ? 8 : 16)))
+k_batch(const BatchArgs B) {
+  __shared__ unsigned s_tile, s_ntile;
+  __shared__ int s_si, s_nsi, s_ok;
+  // thread 0: seg lookup of a ticket (segment index, from the block index, forward)
+  auto lookup = [&](unsigned item, int *si, unsigned *tile) {
+    int lo = B.blk_seg[item >> SEG_BLK_BITS];
+    while (lo + 1 < B.nseg && B.seg_start[lo + 1] <= item) ++lo;
+    *si = B.seg_step[lo];
+    *tile = item - B.seg_start[lo];
+  };
+  unsigned nxt = 0, nxt2 = 0;  // claimed tickets after the current one (thread 0)
+  int cur_si = -1, nxt_si = -1;
+  unsigned cur_tile = 0, nxt_tile = 0;
+  if (threadIdx.x == 0) {
+    const unsigned first = atomicAdd(B.ticket, 1u);
+    nxt = atomicAdd(B.ticket, 1u);
+    if (first < B.total) lookup(first, &cur_si, &cur_tile);
+  }
   for (;;) {
     if (threadIdx.x == 0) {
-      const unsigned item = next;
-      if (item < B.total) {
-        next = atomicAdd(B.ticket, 1u);
-        // segment of this ticket: from the index entry of its block of tickets, forward
-        int lo = B.blk_seg[item >> SEG_BLK_BITS];
-        while (lo + 1 < B.nseg && B.seg_start[lo + 1] <= item) ++lo;
-        const int si = B.seg_step[lo];
-        const BatchStep &st = B.steps[si];
+      if (cur_si >= 0) {
+        nxt_si = -1;
+        if (nxt < B.total) {
+          nxt2 = atomicAdd(B.ticket, 1u);
+          lookup(nxt, &nxt_si, &nxt_tile);
+        }
+        const BatchStep &st = B.steps[cur_si];
         int ok = 1;
         if (st.dep >= 0 && ld_acquire(B.done + st.dep) < st.dep_need) {
           const long long t0 = clock64();
@@ -181,18 +233,19 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB == 12 && sizeof(T) == 4) ? 
             __nanosleep(128);
           }
         }
-        s_si = si;
-        s_tile = item - B.seg_start[lo];
         s_ok = ok;
-      } else {
-        s_si = -1;
+        s_tile = cur_tile;
+        s_nsi = nxt_si;
+        s_ntile = nxt_tile;
       }
+      s_si = cur_si;
     }
     __syncthreads();
     const int si = s_si;
     if (si < 0) break;
     const unsigned tile = s_tile;
     const BatchStep &st = B.steps[si];
+    if (s_nsi >= 0) batch_prefetch<T, TB>(B.steps[s_nsi], s_ntile);
     if (s_ok) {
       const BatchIO io = B.io[st.inst];
       if (st.kind == S_PREP)
@@ -206,8 +259,36 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB == 12 && sizeof(T) == 4) ? 
     if (threadIdx.x == 0) {
       __threadfence();
       atomicAdd(B.done + (si), 1u);
+      cur_si = nxt_si;
+      cur_tile = nxt_tile;
+      nxt = nxt2;
     }
   }
+}
+
+// The staged schedule: one launch per stage (every instance's step s), the
+// stream order in place of the persistent kernel's waits.  A CTA runs the one
+// item of this stage's ticket range that its block index names.
+template <typename T, int TB>
+__global__ void __launch_bounds__(1 << (TB - 5), sizeof(T) == 8 ? 2 : 5) k_stage(const BatchArgs B, unsigned first) {
+  __shared__ int s_si;
+  __shared__ unsigned s_tile;
+  if (threadIdx.x == 0) {
+    const unsigned item = first + blockIdx.x;
+    int lo = B.blk_seg[item >> SEG_BLK_BITS];
+    while (lo + 1 < B.nseg && B.seg_start[lo + 1] <= item) ++lo;
+    s_si = B.seg_step[lo];
+    s_tile = item - B.seg_start[lo];
+  }
+  __syncthreads();
+  const BatchStep &st = B.steps[s_si];
+  const BatchIO io = B.io[st.inst];
+  if (st.kind == S_PREP)
+    batch_prep<T>(st, io);
+  else if (st.kind == S_REDUCE)
+    batch_reduce(st, io);
+  else
+    batch_pass<T, TB>(st.A, s_tile);
 }
 
 // ------------------------------------------------------------------- host --
@@ -215,6 +296,14 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB == 12 && sizeof(T) == 4) ? 
 template <typename T, int TB>
 static cudaError_t launch_batch(const BatchArgs &B, int ctas, size_t smem, cudaStream_t s) {
   k_batch<T, TB><<<ctas, 1 << (TB - 5), smem, s>>>(B);
+  return cudaGetLastError();
+}
+
+template <typename T, int TB>
+static cudaError_t launch_stage(const BatchArgs &B, unsigned first, unsigned count, size_t smem, cudaStream_t s) {
+  const cudaError_t e = cudaFuncSetAttribute(k_stage<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_stage<T, TB><<<count, 1 << (TB - 5), smem, s>>>(B, first);
   return cudaGetLastError();
 }
 
@@ -249,6 +338,7 @@ struct BatchSchedule {
   int nsteps = 0;
   int counters = 0;
   int waves = 0;
+  std::vector<unsigned> stage_first;  // ticket ranges of the stages (staged schedule), plus the end
 };
 
 struct gvqe_batch_s {
@@ -256,7 +346,12 @@ struct gvqe_batch_s {
   int prec = 0;
   bool persistent = false;
   long long wave_bytes = kDefaultWaveBytes;  // GVQE_BATCH_OPT_WAVE_BYTES
+  int schedule = GVQE_BATCH_PERSISTENT;     // GVQE_BATCH_OPT_SCHEDULE
+  int tile_bits = 12;                        // GVQE_BATCH_OPT_TILE_BITS (FP64: always 12)
   std::string tune_report;
+  // instances of the persistent launch (slot k -> instance pidx[k]) and the
+  // ones evaluated by single calls in the same run (n < 12, X/Y strings, RY+RZ)
+  std::vector<int> pidx, sidx;
   std::vector<gvqe_ansatz> a;
   std::vector<gvqe_hamiltonian> h;
   BatchSchedule sched[2];  // [0] energies only, [1] energies + gradients
@@ -272,9 +367,35 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 // 128-thread CTAs per SM (96 registers) keep more items in flight than two
 // 256-thread CTAs on 2^13 tiles (measured for the 256-instance cluster batch:
 // 4.97 ms on 2^13 tiles, 4.78 ms at four CTAs of 2^12, 4.48 ms at five).
-int tile_bits_for(int prec) {
-  (void)prec;
-  return 12;
+int tile_bits_for(const gvqe_batch_s *b) { return b->tile_bits; }
+
+// Launch of the persistent kernel for the batch's tile size: 2^12 (four warps
+// per CTA), 2^11 (two) or 2^10 (one warp per CTA, so every block barrier of
+// the tile rounds is a warp barrier and each warp claims its own items).
+cudaError_t launch_batch_tb(int prec, int tb, const BatchArgs &B, int ctas, size_t smem, cudaStream_t s) {
+  if (prec) return launch_batch<double, 12>(B, ctas, smem, s);
+  switch (tb) {
+    case 10: return launch_batch<float, 10>(B, ctas, smem, s);
+    case 11: return launch_batch<float, 11>(B, ctas, smem, s);
+    default: return launch_batch<float, 12>(B, ctas, smem, s);
+  }
+}
+cudaError_t launch_stage_tb(int prec, int tb, const BatchArgs &B, unsigned first, unsigned count, size_t smem,
+                            cudaStream_t s) {
+  if (prec) return launch_stage<double, 12>(B, first, count, smem, s);
+  switch (tb) {
+    case 10: return launch_stage<float, 10>(B, first, count, smem, s);
+    case 11: return launch_stage<float, 11>(B, first, count, smem, s);
+    default: return launch_stage<float, 12>(B, first, count, smem, s);
+  }
+}
+int batch_occupancy_tb(int prec, int tb, size_t smem) {
+  if (prec) return batch_occupancy<double, 12>(smem);
+  switch (tb) {
+    case 10: return batch_occupancy<float, 10>(smem);
+    case 11: return batch_occupancy<float, 11>(smem);
+    default: return batch_occupancy<float, 12>(smem);
+  }
 }
 
 long long wait_budget_cycles() {
@@ -293,13 +414,16 @@ long long wait_budget_cycles() {
 int build_schedule(gvqe_batch_s *b, int want_grad) {
   BatchSchedule &sc = b->sched[want_grad];
   const int prec = b->prec;
-  const int TB = tile_bits_for(prec);
+  const int TB = tile_bits_for(b);
   const size_t es = prec ? 8 : 4;
-  const int ni = (int)b->a.size();
+  const int ni = (int)b->pidx.size();  // slots of the persistent launch
+  auto A_of = [&](int k) { return b->a[b->pidx[k]]; };
+  auto H_of = [&](int k) { return b->h[b->pidx[k]]; };
   sc.plans.clear();
   sc.plans.reserve(ni);
-  for (int i = 0; i < ni; ++i) sc.plans.push_back(build_plan(b->a[i]->n, b->a[i]->reps, prec, TB, want_grad != 0, true, true, false, b->a[i]->ent, 1,
-                                                 b->a[i]->split));
+  for (int i = 0; i < ni; ++i)
+    sc.plans.push_back(build_plan(A_of(i)->n, A_of(i)->reps, prec, TB, want_grad != 0, true, true, false, A_of(i)->ent, 1,
+                                  eff_split(A_of(i), prec)));
 
   // device layout: [steps][seg_start][seg_step][counters][io][per-instance workspace]
   std::vector<BatchStep> steps;
@@ -352,7 +476,7 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   // next wave's first items need nothing from it and fill the GPU as it drains.
   std::vector<int> order(ni);
   for (int i = 0; i < ni; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->a[x]->n > b->a[y]->n; });
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return A_of(x)->n > A_of(y)->n; });
   // an instance's live bytes while one of its passes runs: the pass input, its
   // output and (backward) the stored forward state or the table
   auto inst_bytes = [&](int i) { return (size_t)3 * sc.plans[i].state_elems * es; };
@@ -370,10 +494,12 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   std::vector<unsigned> seg_start;
   std::vector<int> seg_step;
   unsigned tick = 0;
+  sc.stage_first.clear();
   for (const std::vector<int> &wv : waves) {
     size_t max_stage = 0;
     for (int i : wv) max_stage = std::max(max_stage, inst_steps[i].size());
-    for (size_t s = 0; s < max_stage; ++s)
+    for (size_t s = 0; s < max_stage; ++s) {
+      sc.stage_first.push_back(tick);
       for (int i : wv) {
         if (s >= inst_steps[i].size()) continue;
         const int si = inst_steps[i][s];
@@ -381,7 +507,9 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
         seg_step.push_back(si);
         tick += steps[si].items;
       }
+    }
   }
+  sc.stage_first.push_back(tick);
   sc.waves = (int)waves.size();
   const int nseg = (int)seg_start.size();
   const int counters = nsteps + 1;
@@ -442,7 +570,7 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
     p += up256((size_t)pl.part_stride * 8);
     char *bufs = p;
     auto buf = [&](int id) -> void * { return id < 0 ? nullptr : bufs + (size_t)id * pl.state_elems * es; };
-    const void *table = prec ? b->h[i]->T64.ptr : b->h[i]->T32.ptr;
+    const void *table = prec ? H_of(i)->T64.ptr : H_of(i)->T32.ptr;
     const RedEntry *dir = (const RedEntry *)(base + o_dir) + dir_off;
     for (size_t k = 0; k < inst_steps[i].size(); ++k) {
       BatchStep &st = steps[inst_steps[i][k]];
@@ -497,7 +625,7 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   int sms = 1, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per = prec ? batch_occupancy<double, 12>(sc.smem) : batch_occupancy<float, 12>(sc.smem);
+  const int per = batch_occupancy_tb(prec, TB, sc.smem);
   sc.ctas = std::max(1, sms * per);
 
   // the graph: clear ticket, error word and counters, then the persistent launch
@@ -506,11 +634,15 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(base + o_ctr, 0, sizeof(unsigned) * (2 + counters), cap);
-    if (prec)
-      launch_batch<double, 12>(B, sc.ctas, sc.smem, cap);
-    else
-      launch_batch<float, 12>(B, sc.ctas, sc.smem, cap);
+    cudaError_t le = cudaSuccess;
+    if (b->schedule == GVQE_BATCH_STAGED) {
+      for (size_t k = 0; k + 1 < sc.stage_first.size() && le == cudaSuccess; ++k)
+        le = launch_stage_tb(prec, TB, B, sc.stage_first[k], sc.stage_first[k + 1] - sc.stage_first[k], sc.smem, cap);
+    } else {
+      le = launch_batch_tb(prec, TB, B, sc.ctas, sc.smem, cap);
+    }
     e = cudaStreamEndCapture(cap, &sc.graph);
+    if (e == cudaSuccess) e = le;
   }
   cudaStreamDestroy(cap);
   if (e != cudaSuccess) return fail(GVQE_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
@@ -543,9 +675,25 @@ int energy_one(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, const ui
 int prepare_tables(gvqe_hamiltonian h, int prec, cudaStream_t s);
 
 namespace {
+// Which instances the persistent kernel takes: RY layers, a diagonal Hamiltonian
+// and n at least the batch tile bits; the others are evaluated by single calls.
+void classify(gvqe_batch_s *b) {
+  b->pidx.clear();
+  b->sidx.clear();
+  for (size_t i = 0; i < b->a.size(); ++i) {
+    const gvqe_ansatz a = b->a[i];
+    const gvqe_hamiltonian h = b->h[i];
+    if (a->n < tile_bits_for(b) || !h->gm.empty() || a->gates != 1)
+      b->sidx.push_back((int)i);
+    else
+      b->pidx.push_back((int)i);
+  }
+  b->persistent = !b->pidx.empty();
+}
+
 int batch_loop(gvqe_batch_s *b, const double *const *params, const uint8_t *const *masks, double *energies,
                double *const *grads, cudaStream_t s) {
-  for (size_t i = 0; i < b->a.size(); ++i) {
+  for (int i : b->sidx) {
     const int rc = energy_one(b->a[i], b->h[i], params[i], masks ? masks[i] : nullptr, energies + i,
                               grads ? grads[i] : nullptr, b->prec, s);
     if (rc != GVQE_OK) return rc;
@@ -564,16 +712,12 @@ int gvqe_batch_create(int n_inst, const gvqe_ansatz *ansatze, const gvqe_hamilto
   if (n_inst < 1 || !ansatze || !hams) return fail(GVQE_EINVAL, "n_inst=%d or NULL instance arrays", n_inst);
   if (flags & ~GVQE_FP64) return fail(GVQE_EINVAL, "unknown flags 0x%x", flags);
   const int prec = flags & GVQE_FP64 ? 1 : 0;
-  bool persistent = true;
   for (int i = 0; i < n_inst; ++i) {
     gvqe_ansatz a = ansatze[i];
     gvqe_hamiltonian h = hams[i];
     if (!a || a->magic != MAGIC_ANSATZ) return fail(GVQE_EINVAL, "instance %d: invalid ansatz handle", i);
     if (!h || h->magic != MAGIC_HAM) return fail(GVQE_EINVAL, "instance %d: invalid Hamiltonian handle", i);
     if (a->n != h->n) return fail(GVQE_EINVAL, "instance %d: ansatz has %d qubits, Hamiltonian %d", i, a->n, h->n);
-    // the persistent kernel runs one tile size, RY layers and diagonal Hamiltonians;
-    // other batches run instance by instance through the regular path
-    if (a->n < tile_bits_for(prec) || !h->gm.empty() || a->gates != 1) persistent = false;
   }
   for (int i = 0; i < n_inst; ++i) {
     const int rc = prepare_tables(hams[i], prec, nullptr);
@@ -582,9 +726,9 @@ int gvqe_batch_create(int n_inst, const gvqe_ansatz *ansatze, const gvqe_hamilto
   gvqe_batch_s *b = new gvqe_batch_s();
   b->magic = MAGIC_BATCH;
   b->prec = prec;
-  b->persistent = persistent;
   b->a.assign(ansatze, ansatze + n_inst);
   b->h.assign(hams, hams + n_inst);
+  classify(b);
   *out = b;
   return GVQE_OK;
 }
@@ -592,11 +736,29 @@ int gvqe_batch_create(int n_inst, const gvqe_ansatz *ansatze, const gvqe_hamilto
 int gvqe_batch_set_option(gvqe_batch b, int option, long long value) {
   g_err.clear();
   if (!b || b->magic != MAGIC_BATCH) return fail(GVQE_EINVAL, "invalid batch handle");
-  if (option != GVQE_BATCH_OPT_WAVE_BYTES) return fail(GVQE_EINVAL, "unknown batch option %d", option);
-  if (value < 0) return fail(GVQE_EINVAL, "wave bytes %lld < 0", value);
-  if (value == b->wave_bytes) return GVQE_OK;
+  if (option == GVQE_BATCH_OPT_WAVE_BYTES) {
+    if (value < 0) return fail(GVQE_EINVAL, "wave bytes %lld < 0", value);
+    if (value == b->wave_bytes) return GVQE_OK;
+  } else if (option == GVQE_BATCH_OPT_SCHEDULE) {
+    if (value != GVQE_BATCH_PERSISTENT && value != GVQE_BATCH_STAGED)
+      return fail(GVQE_EINVAL, "batch schedule %lld is not GVQE_BATCH_PERSISTENT or GVQE_BATCH_STAGED", value);
+    if (value == b->schedule) return GVQE_OK;
+  } else if (option == GVQE_BATCH_OPT_TILE_BITS) {
+    if (value < 10 || value > 12) return fail(GVQE_EINVAL, "batch tile bits %lld outside [10, 12]", value);
+    if (b->prec && value != 12) return fail(GVQE_EUNSUPPORTED, "FP64 batches run 2^12-amplitude tiles only");
+    if (value == b->tile_bits) return GVQE_OK;
+  } else {
+    return fail(GVQE_EINVAL, "unknown batch option %d", option);
+  }
   cudaDeviceSynchronize();
-  b->wave_bytes = value;
+  if (option == GVQE_BATCH_OPT_WAVE_BYTES) {
+    b->wave_bytes = value;
+  } else if (option == GVQE_BATCH_OPT_SCHEDULE) {
+    b->schedule = (int)value;
+  } else {
+    b->tile_bits = (int)value;
+    classify(b);
+  }
   for (BatchSchedule &sc : b->sched) {  // rebuilt (and recaptured) on the next run
     if (sc.exec) cudaGraphExecDestroy(sc.exec);
     if (sc.graph) cudaGraphDestroy(sc.graph);
@@ -629,17 +791,30 @@ int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t
     return GVQE_OK;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const long long cands[] = {0, 64ll << 20, 96ll << 20, 128ll << 20, 192ll << 20, 256ll << 20};
+  struct Cand {
+    int sched, tb;
+    long long wb;
+  };
+  std::vector<Cand> cands;
+  for (int sch : {(int)GVQE_BATCH_PERSISTENT, (int)GVQE_BATCH_STAGED})
+    for (int tb : {12, 11, 10}) {
+      if (b->prec && tb != 12) continue;
+      cands.push_back({sch, tb, 0});
+    }
+  cands.push_back({GVQE_BATCH_PERSISTENT, 12, 256ll << 20});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   GB_CUDA(cudaEventCreate(&e0));
   GB_CUDA(cudaEventCreate(&e1));
   const long long keep = b->wave_bytes;
-  long long best = -1;
+  const int keep_tb = b->tile_bits, keep_sched = b->schedule;
+  Cand best{-1, -1, 0};
   double best_ms = 0.0;
   std::string sweep;
   int rc = GVQE_OK;
-  for (long long wb : cands) {
-    rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_WAVE_BYTES, wb);
+  for (const Cand &cd : cands) {
+    rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_SCHEDULE, cd.sched);
+    if (rc == GVQE_OK) rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_TILE_BITS, cd.tb);
+    if (rc == GVQE_OK) rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_WAVE_BYTES, cd.wb);
     if (rc == GVQE_OK) rc = gvqe_batch_run(b, params, masks, energies, grads, stream);  // build + warm
     if (rc != GVQE_OK) break;
     const int timed = 3;
@@ -652,26 +827,32 @@ int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t
     cudaEventElapsedTime(&ms, e0, e1);
     const double per = ms / timed;
     const int g = grads ? 1 : 0;
-    char line[160];
-    snprintf(line, sizeof(line), "%swave=%lldMiB (%d waves): %.3f ms", sweep.empty() ? "" : "; ", wb >> 20,
-             b->sched[g].waves, per);
+    char line[200];
+    snprintf(line, sizeof(line), "%s%s tiles=2^%d wave=%lldMiB (%d waves, %zu of %zu instances in it): %.3f ms",
+             sweep.empty() ? "" : "; ", cd.sched == GVQE_BATCH_STAGED ? "staged" : "persistent", cd.tb, cd.wb >> 20,
+             b->sched[g].waves, b->pidx.size(), b->a.size(), per);
     sweep += line;
-    if (best < 0 || per < best_ms) {
-      best = wb;
+    if (best.tb < 0 || per < best_ms) {
+      best = cd;
       best_ms = per;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != GVQE_OK) {
+    gvqe_batch_set_option(b, GVQE_BATCH_OPT_SCHEDULE, keep_sched);
+    gvqe_batch_set_option(b, GVQE_BATCH_OPT_TILE_BITS, keep_tb);
     gvqe_batch_set_option(b, GVQE_BATCH_OPT_WAVE_BYTES, keep);
     return rc;
   }
-  rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_WAVE_BYTES, best);
+  rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_SCHEDULE, best.sched);
+  if (rc == GVQE_OK) rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_TILE_BITS, best.tb);
+  if (rc == GVQE_OK) rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_WAVE_BYTES, best.wb);
   if (rc != GVQE_OK) return rc;
   char line[200];
-  snprintf(line, sizeof(line), "batch autotune: wave bytes %lld MiB (%s), %.3f ms per run\n", best >> 20,
-           best == 0 ? "one wave" : "waves", best_ms);
+  snprintf(line, sizeof(line), "batch autotune: %s schedule, tiles 2^%d, wave bytes %lld MiB (%s), %.3f ms per run\n",
+           best.sched == GVQE_BATCH_STAGED ? "staged" : "persistent", best.tb, best.wb >> 20,
+           best.wb == 0 ? "one wave" : "waves", best_ms);
   rep = std::string(line) + "batch autotune sweep: " + sweep + "\n";
   b->tune_report = rep;
   put();
@@ -696,21 +877,28 @@ int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *con
     const int rc = build_schedule(b, g);
     if (rc != GVQE_OK) return rc;
   }
-  std::vector<BatchIO> io(ni);
-  for (size_t i = 0; i < ni; ++i) {
-    io[i].params = params[i];
-    io[i].mask = masks ? masks[i] : nullptr;
-    io[i].grad = grads ? grads[i] : nullptr;
-    io[i].energy = energies + i;
+  const size_t np = b->pidx.size();
+  std::vector<BatchIO> io(np);
+  for (size_t k = 0; k < np; ++k) {
+    const int i = b->pidx[k];
+    io[k].params = params[i];
+    io[k].mask = masks ? masks[i] : nullptr;
+    io[k].grad = grads ? grads[i] : nullptr;
+    io[k].energy = energies + i;
   }
-  if (!b->io_valid[g] || b->io_host.size() != ni || memcmp(io.data(), b->io_host.data(), sizeof(BatchIO) * ni) != 0) {
-    GB_CUDA(cudaMemcpyAsync((void *)sc.args.io, io.data(), sizeof(BatchIO) * ni, cudaMemcpyHostToDevice, s));
+  if (!b->io_valid[g] || b->io_host.size() != np || memcmp(io.data(), b->io_host.data(), sizeof(BatchIO) * np) != 0) {
+    GB_CUDA(cudaMemcpyAsync((void *)sc.args.io, io.data(), sizeof(BatchIO) * np, cudaMemcpyHostToDevice, s));
     b->io_host = io;
     b->io_valid[g] = true;
     b->io_valid[1 - g] = false;
   }
   GB_CUDA(cudaGraphLaunch(sc.exec, s));
   count_launches(1);
+  // the instances outside the persistent launch, on the same stream after it
+  if (!b->sidx.empty()) {
+    const int rc = batch_loop(b, params, masks, energies, grads, s);
+    if (rc != GVQE_OK) return rc;
+  }
   GB_CUDA(cudaStreamSynchronize(s));
   int err = 0;
   GB_CUDA(cudaMemcpy(&err, sc.args.err, sizeof(int), cudaMemcpyDeviceToHost));

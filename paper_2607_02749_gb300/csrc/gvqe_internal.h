@@ -119,8 +119,12 @@ struct gvqe_ansatz_s {
   uint32_t magic = 0;
   int n = 0, reps = 0, ent = 0;
   int gates = 1;  // 1: RY layers; 2: RY then RZ (the complex path)
-  int tile_bits = 0;  // 0 = automatic
-  int split = 0;      // gvqe::SplitMode
+  int tile_bits = 0;  // 0 = automatic (GVQE_OPT_TILE_BITS, both precisions)
+  int split = 0;      // gvqe::SplitMode (GVQE_OPT_SPLIT_PASSES, both precisions)
+  // per precision (FP32, FP64): the plan gvqe_autotune chose (0 / -1: none), which
+  // takes the place of tile_bits / split for that precision until an option is set
+  int tuned_tb[2] = {0, 0};
+  int tuned_split[2] = {-1, -1};
   std::map<int, gvqe::Plan> plans;
   gvqe::DevBuf ws, aux, shift, ro, tune;
   std::string tune_report;  // the last gvqe_autotune sweep and its choice (empty: not tuned)
@@ -130,6 +134,9 @@ struct gvqe_batch_s;
 int batch_destroy(gvqe_batch_s *b);
 
 namespace gvqe {
+// The tile bits and strided layout an ansatz's plans take in one precision.
+inline int eff_tile_bits(const gvqe_ansatz_s *a, int prec) { return a->tuned_tb[prec] ? a->tuned_tb[prec] : a->tile_bits; }
+inline int eff_split(const gvqe_ansatz_s *a, int prec) { return a->tuned_split[prec] >= 0 ? a->tuned_split[prec] : a->split; }
 // The ansatz's cached plan for (precision, gradient or not, diagonal H or not,
 // state only); it and its host-side reduction directory live until the
 // ansatz is destroyed or one of its options changes.

@@ -75,7 +75,8 @@ extern "C" int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const doubl
   if (!h->gm.empty())
     return fail(GVQE_EUNSUPPORTED, "gvqe_energy_static takes diagonal (I/Z-only) Hamiltonians");
   const int prec = flags & GVQE_FP64 ? 1 : 0;
-  if (a->tile_bits > max_tile_bits(prec)) return fail(GVQE_EINVAL, "tile bits %d too large", a->tile_bits);
+  if (eff_tile_bits(a, prec) > max_tile_bits(prec))
+    return fail(GVQE_EINVAL, "tile bits %d too large", eff_tile_bits(a, prec));
   cudaStream_t s = (cudaStream_t)stream;
 
   // The energy plan (forward passes with the energy fused into the last one),

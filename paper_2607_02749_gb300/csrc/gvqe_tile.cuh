@@ -1403,7 +1403,8 @@ __device__ __forceinline__ void grad_l0_tile(const PassArgs &A, int job, uint32_
 // lambda[x] = E(x) psi[x] + sum_groups D_m(x ^ m) psi[x ^ m] with
 // D_m(u) = sum_{k in group} c_k (-1)^popcount(u & z_k) (c_k carries the i^#Y sign).
 //
-// A CTA owns the output tile t (2^TB amplitudes, 32 per thread in registers).
+// A CTA owns the output tile t (2^TB amplitudes, 32 per thread in registers:
+// FP32 as 16 packed pairs of neighbouring elements, see xy_group_pk).
 // The groups come sorted by X-mask m, so groups whose mask agrees above the
 // tile bits (the same high part h = m >> TB) form consecutive runs; a run needs
 // one partner tile, psi over tile t ^ h, which is streamed into shared memory
@@ -1414,10 +1415,10 @@ __device__ __forceinline__ void grad_l0_tile(const PassArgs &A, int job, uint32_
 // e ^ m_lo) and one that depends only on the register slot k, read from a
 // 32-bit mask per term built once per CTA: no population count per element.
 // Bytes: psi and the table of tile t, one partner tile per run, lambda written.
-// One X-mask group applied to a thread's 32 elements: element k (tile index
-// e = k NT + tid) gains D(u) psi[u] with u's tile part k NT ^ tm read from the
-// partner tile; D(u) = sum_j c[j] (-1)^(bit k of km[j]), the signs of u's other
-// bits already folded into c[j].  NTERM terms (unused ones have c = 0).
+// One X-mask group applied to a thread's 32 elements (FP64): element k (tile
+// index e = k NT + tid) gains D(u) psi[u] with u's tile part k NT ^ tm read from
+// the partner tile; D(u) = sum_j c[j] (-1)^(bit k of km[j]), the signs of u's
+// other bits already folded into c[j].  NTERM terms (unused ones have c = 0).
 template <typename T, int TB, int NTERM>
 __device__ __forceinline__ void xy_group(T (&acc)[ROUND], const T *buf, uint32_t tm, const T (&c)[4],
                                          const uint32_t (&km)[4]) {
@@ -1431,11 +1432,37 @@ __device__ __forceinline__ void xy_group(T (&acc)[ROUND], const T *buf, uint32_t
   }
 }
 
+// The FP32 form: a thread owns 16 pairs of neighbouring elements, pair j holding
+// tile indices e = j 2^(TB-4) + 2 tid and e + 1; their partners e ^ m_lo and
+// e ^ m_lo ^ 1 share one 8-byte word (in swapped order when bit 0 of m_lo is
+// set), and a term's two signs differ by bit 0 of z, so each pair takes one
+// 8-byte shared load and packed f32x2 arithmetic.  c2[t] holds the term's pair
+// of signed coefficients, km[t] bit j the sign pair j's slot bits add.
+template <int TB, int NTERM, bool SWAP>
+__device__ __forceinline__ void xy_group_pk(unsigned long long (&acc)[ROUND / 2], const float *buf, uint32_t tm,
+                                            const unsigned long long (&c2)[4], const uint32_t (&km)[4]) {
+  const float2 *b2 = reinterpret_cast<const float2 *>(buf);
+#pragma unroll
+  for (int j = 0; j < ROUND / 2; ++j) {
+    const float2 p = b2[(((uint32_t)j << (TB - 4)) ^ tm) >> 1];
+    const unsigned long long p2 = SWAP ? pk(p.y, p.x) : pk(p.x, p.y);
+    auto signed_c = [&](int t) {
+      const uint32_t sb = (km[t] << (31 - j)) & 0x80000000u;
+      return c2[t] ^ (((unsigned long long)sb << 32) | sb);
+    };
+    unsigned long long d2 = signed_c(0);
+#pragma unroll
+    for (int t = 1; t < NTERM; ++t) d2 = add2(d2, signed_c(t));
+    acc[j] = fma2(d2, p2, acc[j]);
+  }
+}
+
 template <typename T, int TB>
 __global__ void __launch_bounds__(1 << (TB - 5)) k_lambda_xy(const PassArgs A) {
   constexpr int NT = 1 << (TB - 5);
   constexpr int NW = NT / 32;
   constexpr uint32_t LOW = (1u << TB) - 1u;
+  constexpr bool PAIRS = sizeof(T) == 4;  // FP32: packed pairs of neighbouring elements
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nterm = A.ngroups > 0 ? A.gstart[A.ngroups] - A.gstart[0] : 0;
   const XyLayout lay = xy_layout(A.ngroups, nterm, (int)sizeof(T));
@@ -1459,10 +1486,12 @@ __global__ void __launch_bounds__(1 << (TB - 5)) k_lambda_xy(const PassArgs A) {
     const uint32_t z = A.tz[t0 + i];
     stz[i] = z;
     stc[i] = reinterpret_cast<const T *>(A.tc)[t0 + i];
-    // bit k: parity of k * NT & z (the register-slot bits, tile bits TB-5 .. TB-1)
-    const uint32_t zk = (z >> (TB - 5)) & 31u;
+    // bit k: the parity of z over the slot bits of register slot k (FP64: slot
+    // k is tile bits TB-5.. of k NT; FP32: pair k is tile bits TB-4.. of k 2^(TB-4))
+    const int sbits = PAIRS ? 4 : 5;
+    const uint32_t zk = (z >> (TB - sbits)) & ((1u << sbits) - 1u);
     uint32_t km = 0;
-    for (int k = 0; k < 32; ++k) km |= (uint32_t)(__popc((uint32_t)k & zk) & 1) << k;
+    for (int k = 0; k < (1 << sbits); ++k) km |= (uint32_t)(__popc((uint32_t)k & zk) & 1) << k;
     skm[i] = km;
   }
   __syncthreads();
@@ -1478,11 +1507,30 @@ __global__ void __launch_bounds__(1 << (TB - 5)) k_lambda_xy(const PassArgs A) {
   const T *table = reinterpret_cast<const T *>(A.table);
   T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
   const uint32_t tbase = t << TB;
-  T acc[ROUND];
+  // the thread's elements: FP64 e = k NT + tid; FP32 pairs (j 2^(TB-4) + 2 tid, + 1)
+  const uint32_t tpart = PAIRS ? (uint32_t)tid << 1 : (uint32_t)tid;
+  T acc[PAIRS ? 1 : ROUND];
+  unsigned long long acc2[PAIRS ? ROUND / 2 : 1];
+  if constexpr (PAIRS) {
 #pragma unroll
-  for (int k = 0; k < ROUND; ++k) {
-    const uint32_t x = tbase + (uint32_t)(k * NT + tid);
-    acc[k] = (A.flags & F_ACCUM) ? lin[x] : table[x] * in[x];
+    for (int j = 0; j < ROUND / 2; ++j) {
+      const uint32_t x = tbase + ((uint32_t)j << (TB - 4)) + tpart;
+      float2 v;
+      if (A.flags & F_ACCUM) {
+        v = *reinterpret_cast<const float2 *>(lin + x);
+      } else {
+        const float2 p = *reinterpret_cast<const float2 *>(in + x);
+        const float2 e = *reinterpret_cast<const float2 *>(table + x);
+        v = make_float2(e.x * p.x, e.y * p.y);
+      }
+      acc2[j] = pk(v);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < ROUND; ++k) {
+      const uint32_t x = tbase + (uint32_t)(k * NT) + tpart;
+      acc[k] = (A.flags & F_ACCUM) ? lin[x] : table[x] * in[x];
+    }
   }
   __syncthreads();
   const int nruns = s_nruns;
@@ -1506,52 +1554,86 @@ __global__ void __launch_bounds__(1 << (TB - 5)) k_lambda_xy(const PassArgs A) {
     const T *buf = sbuf + ((size_t)(r & 1) << TB);
     const uint32_t hi_bits = (t ^ (sgm[srun[r]] >> TB)) << TB;  // tile-index bits of u
     for (int g = srun[r]; g < srun[r + 1]; ++g) {
-      const uint32_t tm = (uint32_t)tid ^ (sgm[g] & LOW);  // e ^ m_lo = k * NT ^ tm
+      const uint32_t mlo = sgm[g] & LOW;
+      const uint32_t tm = tpart ^ mlo;  // the partner of the thread's (first) element, less the slot bits
       const int j0 = sgs[g], nt = sgs[g + 1] - j0;
-      // per term: its coefficient with the sign of every bit of u but the slot bits
-      // folded in, and its slot mask (bit k: the sign the slot bits of k add)
-      T c[4];
-      uint32_t km[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (j < nt) {
-          c[j] = flip_sign(stc[j0 + j], __popc(stz[j0 + j] & (hi_bits | tm)) & 1);
-          km[j] = skm[j0 + j];
-        } else {
-          c[j] = T(0);
-          km[j] = 0;
-        }
-      }
-      if (nt == 1) {
-        xy_group<T, TB, 1>(acc, buf, tm, c, km);
-      } else if (nt == 2) {
-        xy_group<T, TB, 2>(acc, buf, tm, c, km);
-      } else if (nt <= 4) {
-        xy_group<T, TB, 4>(acc, buf, tm, c, km);
-      } else {
-        for (int j4 = 0; j4 < nt; j4 += 4) {  // more than four terms: four at a time
+      if constexpr (PAIRS) {
+        // per term: the pair of coefficients with the signs of every bit of u but
+        // the slot bits folded in (the pair's second element adds bit 0 of z)
+        auto load_terms = [&](int jb, unsigned long long (&c2)[4], uint32_t (&km)[4]) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            if (j4 + j < nt) {
-              c[j] = flip_sign(stc[j0 + j4 + j], __popc(stz[j0 + j4 + j] & (hi_bits | tm)) & 1);
-              km[j] = skm[j0 + j4 + j];
+            if (jb + j < j0 + nt) {
+              const uint32_t z = stz[jb + j];
+              const float c0 = flip_sign(stc[jb + j], __popc(z & (hi_bits | tm)) & 1);
+              c2[j] = pk(c0, flip_sign(c0, z & 1u));
+              km[j] = skm[jb + j];
+            } else {
+              c2[j] = 0ull;
+              km[j] = 0;
+            }
+          }
+        };
+        unsigned long long c2[4];
+        uint32_t km[4];
+        const bool swap = (mlo & 1u) != 0;
+        const float *f = reinterpret_cast<const float *>(buf);
+        for (int jb = j0; jb < j0 + nt; jb += 4) {
+          load_terms(jb, c2, km);
+          const int left = j0 + nt - jb;
+          if (left == 1) {
+            swap ? xy_group_pk<TB, 1, true>(acc2, f, tm, c2, km) : xy_group_pk<TB, 1, false>(acc2, f, tm, c2, km);
+          } else if (left == 2) {
+            swap ? xy_group_pk<TB, 2, true>(acc2, f, tm, c2, km) : xy_group_pk<TB, 2, false>(acc2, f, tm, c2, km);
+          } else {
+            swap ? xy_group_pk<TB, 4, true>(acc2, f, tm, c2, km) : xy_group_pk<TB, 4, false>(acc2, f, tm, c2, km);
+          }
+        }
+      } else {
+        // per term: its coefficient with the sign of every bit of u but the slot bits
+        // folded in, and its slot mask (bit k: the sign the slot bits of k add)
+        T c[4];
+        uint32_t km[4];
+        for (int jb = j0; jb < j0 + nt; jb += 4) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (jb + j < j0 + nt) {
+              c[j] = flip_sign(stc[jb + j], __popc(stz[jb + j] & (hi_bits | tm)) & 1);
+              km[j] = skm[jb + j];
             } else {
               c[j] = T(0);
               km[j] = 0;
             }
           }
-          xy_group<T, TB, 4>(acc, buf, tm, c, km);
+          const int left = j0 + nt - jb;
+          if (left == 1)
+            xy_group<T, TB, 1>(acc, buf, tm, c, km);
+          else if (left == 2)
+            xy_group<T, TB, 2>(acc, buf, tm, c, km);
+          else
+            xy_group<T, TB, 4>(acc, buf, tm, c, km);
         }
       }
     }
     __syncthreads();  // every thread is done with this buffer before it is refilled
   }
   T eacc = T(0);
+  if constexpr (PAIRS) {
 #pragma unroll
-  for (int k = 0; k < ROUND; ++k) {
-    const uint32_t x = tbase + (uint32_t)(k * NT + tid);
-    if (A.flags & F_WRITE_LAMBDA) out[x] = acc[k];
-    eacc += in[x] * acc[k];
+    for (int j = 0; j < ROUND / 2; ++j) {
+      const uint32_t x = tbase + ((uint32_t)j << (TB - 4)) + tpart;
+      const float2 v = upk(acc2[j]);
+      if (A.flags & F_WRITE_LAMBDA) *reinterpret_cast<float2 *>(out + x) = v;
+      const float2 p = *reinterpret_cast<const float2 *>(in + x);
+      eacc += p.x * v.x + p.y * v.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < ROUND; ++k) {
+      const uint32_t x = tbase + (uint32_t)(k * NT) + tpart;
+      if (A.flags & F_WRITE_LAMBDA) out[x] = acc[k];
+      eacc += in[x] * acc[k];
+    }
   }
   if (A.flags & F_ENERGY) {
     eacc = warp_sum(eacc);

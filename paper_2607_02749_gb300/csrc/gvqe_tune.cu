@@ -27,6 +27,8 @@
 #include <string>
 #include <vector>
 
+#include <unistd.h>
+
 #include "gvqe.h"
 #include "gvqe_engine.cuh"
 #include "gvqe_internal.h"
@@ -212,7 +214,8 @@ int cache_store(const char *path, const std::string &key, const TuneEntry &t) {
   if (read_file(path, &text) && !parse_cache(text, &m)) m.clear();  // an invalid file is rewritten
   m[key] = t;
   const std::string out = write_cache(m);
-  const std::string tmp = std::string(path) + ".tmp";
+  // a writer-private temporary (processes tuning at once each rename a whole file)
+  const std::string tmp = std::string(path) + ".tmp" + std::to_string((long long)getpid());
   FILE *f = fopen(tmp.c_str(), "wb");
   if (!f) return fail(GVQE_EINVAL, "cannot write the tuning cache %s", tmp.c_str());
   const bool ok = fwrite(out.data(), 1, out.size(), f) == out.size();
@@ -328,8 +331,8 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
     TuneEntry t;
     if (cache_lookup(cache_path, key, &t) && t.tile_bits >= 10 && t.tile_bits <= tb_max && t.split >= SPLIT_AUTO &&
         t.split <= SPLIT_ALWAYS) {
-      a->tile_bits = t.tile_bits;
-      a->split = t.split;
+      a->tuned_tb[prec] = t.tile_bits;
+      a->tuned_split[prec] = t.split;
       a->plans.clear();
       char line[256];
       snprintf(line, sizeof(line), "autotune: cached (%s): tile_bits=%d strided=%s %.3f ms\n", cache_path,
@@ -361,14 +364,19 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
   EventPair ev;
   GT_CUDA(cudaEventCreate(&ev.a));
   GT_CUDA(cudaEventCreate(&ev.b));
-  const int keep_tb = a->tile_bits, keep_split = a->split;
+  const int keep_tb = a->tuned_tb[prec], keep_split = a->tuned_split[prec];
+  auto restore = [&]() {
+    a->tuned_tb[prec] = keep_tb;
+    a->tuned_split[prec] = keep_split;
+    a->plans.clear();
+  };
   std::string sweep;
   int best = -1;
   double best_ms = 0.0;
   const int timed = 3;
   for (size_t c = 0; c < cands.size(); ++c) {
-    a->tile_bits = cands[c].tb;
-    a->split = cands[c].split;
+    a->tuned_tb[prec] = cands[c].tb;
+    a->tuned_split[prec] = cands[c].split;
     a->plans.clear();
     char line[160];
     // warm-up call: plan, tables and workspaces
@@ -376,9 +384,7 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
     if (rc == GVQE_OK) {
       cudaError_t e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) {
-        a->tile_bits = keep_tb;
-        a->split = keep_split;
-        a->plans.clear();
+        restore();
         return fail(GVQE_ECUDA, "autotune candidate tile_bits=%d: %s", cands[c].tb, cudaGetErrorString(e));
       }
     }
@@ -389,9 +395,7 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
       continue;
     }
     if (rc != GVQE_OK) {
-      a->tile_bits = keep_tb;
-      a->split = keep_split;
-      a->plans.clear();
+      restore();
       return rc;
     }
     GT_CUDA(cudaEventRecord(ev.a, s));
@@ -399,9 +403,7 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
     GT_CUDA(cudaEventRecord(ev.b, s));
     GT_CUDA(cudaEventSynchronize(ev.b));
     if (rc != GVQE_OK) {
-      a->tile_bits = keep_tb;
-      a->split = keep_split;
-      a->plans.clear();
+      restore();
       return rc;
     }
     float ms = 0.f;
@@ -417,22 +419,21 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
   }
   a->ws.release();  // the chosen plan sizes its own workspace on the next call
   if (best < 0) {
-    a->tile_bits = keep_tb;
-    a->split = keep_split;
-    a->plans.clear();
+    restore();
     return fail(GVQE_ENOMEM, "autotune: no candidate plan fits in device memory (%s)", sweep.c_str());
   }
-  a->tile_bits = cands[best].tb;
-  a->split = cands[best].split;
+  a->tuned_tb[prec] = cands[best].tb;
+  a->tuned_split[prec] = cands[best].split;
   a->plans.clear();
   char line[256];
-  snprintf(line, sizeof(line), "autotune: measured: tile_bits=%d strided=%s %.3f ms per call (batch %d, %s)\n",
-           a->tile_bits, split_name(a->split), best_ms, batch, want_grad ? "energy+gradient" : "energy");
+  snprintf(line, sizeof(line), "autotune: measured: tile_bits=%d strided=%s %.3f ms per call (batch %d, %s, %s)\n",
+           cands[best].tb, split_name(cands[best].split), best_ms, batch, want_grad ? "energy+gradient" : "energy",
+           prec ? "fp64" : "fp32");
   a->tune_report = std::string(line) + "autotune sweep: " + sweep + "\n";
   if (cache_path && cache_path[0]) {
     TuneEntry t;
-    t.tile_bits = a->tile_bits;
-    t.split = a->split;
+    t.tile_bits = cands[best].tb;
+    t.split = cands[best].split;
     t.ms = best_ms;
     t.sweep = sweep;
     rc = cache_store(cache_path, key, t);

@@ -62,6 +62,11 @@ def test_tuned_plan_matches_oracle_and_is_cached(tmp_path, n, reps, fp64):
     assert _lib.gvqe_tune_cache_get(cache, key)[0] == best_tb
     e2, g2 = gv.energy_grad(a2, h2, _dev(th), fp64=fp64)
     assert np.array_equal(e2.cpu().numpy(), e) and np.array_equal(g2.cpu().numpy(), g)
+    # the other precision keeps its own plan on the tuned ansatz
+    e3, _ = gv.energy_grad(a, h, _dev(th), fp64=not fp64)
+    tol = (2e-5 if fp64 else 1e-10) * scale
+    for b in range(2):
+        assert abs(e3[b].item() - oracle.energy(n, reps, th[b], ham.strings, ham.coeffs)) <= tol
 
 
 def test_energy_only_tuning_with_xy_strings(tmp_path):

@@ -104,11 +104,31 @@ def test_wave_schedules_give_identical_results_and_autotune_keeps_them():
         assert np.array_equal(e, outs[0][0])
         for g, g0 in zip(gs, outs[0][1]):
             assert np.array_equal(g, g0)
-    grads = [torch.empty_like(p) for p in params]
-    rep = b.autotune(params, masks=masks, grads=grads)
-    assert "batch autotune: wave bytes" in rep and rep.count("ms") >= 6, rep
+    # the staged schedule (one launch per stage) runs the same items: the same bits
+    b.set_schedule(True)
+    grads = [torch.full_like(p, float("nan")) for p in params]
     e = b.run(params, masks=masks, grads=grads).cpu().numpy()
     assert np.array_equal(e, outs[0][0])
+    for g, g0 in zip(grads, outs[0][1]):
+        assert np.array_equal(g.cpu().numpy(), g0)
+    b.set_schedule(False)
+    # smaller work items (2^11, 2^10 amplitudes) change the summation order only
+    for tb in (11, 10):
+        b.set_tile_bits(tb)
+        b.set_wave_bytes(0)
+        grads = [torch.full_like(p, float("nan")) for p in params]
+        e = b.run(params, masks=masks, grads=grads).cpu().numpy()
+        for k, i in enumerate(insts):
+            scale = i.ham.abs_sum()
+            assert abs(e[k] - outs[0][0][k]) <= 2e-5 * scale
+            g0 = outs[0][1][k]
+            assert np.linalg.norm(grads[k].cpu().numpy() - g0) <= 1e-4 * np.linalg.norm(g0)
+    grads = [torch.empty_like(p) for p in params]
+    rep = b.autotune(params, masks=masks, grads=grads)
+    assert "schedule, tiles 2^" in rep and rep.count(" ms") >= 8, rep
+    e = b.run(params, masks=masks, grads=grads).cpu().numpy()
+    if "tiles 2^12" in rep.splitlines()[0]:
+        assert np.array_equal(e, outs[0][0])
 
 
 def test_bounded_wait_returns_timeout_and_context_survives():
@@ -128,3 +148,42 @@ def test_bounded_wait_returns_timeout_and_context_survives():
     e = b.run(params).cpu().numpy()
     for k in range(len(insts)):
         assert abs(e[k] - gv.energy(ans[k], hams[k], params[k]).item()) <= 2e-5 * insts[k].ham.abs_sum()
+
+
+def test_mixed_batch_small_xy_and_repeated_subproblems():
+    """One run over instances the persistent launch takes (n >= 12, diagonal H),
+    instances it does not (n < 12, X/Y strings) and one subproblem listed three
+    times with different parameter vectors; every slot matches its single call
+    and the oracle."""
+    insts = wl.cluster_batch(6, qubit_range=(12, 15), reps_range=(1, 2), terms_per_qubit=10)
+    small = wl.cluster_batch(3, qubit_range=(6, 11), reps_range=(1, 2), terms_per_qubit=10, base_seed=7000)
+    xy_n, xy_reps = 13, 2
+    xy_ham = wl.pauli_hamiltonian(xy_n, 60, seed=11)
+    ans = [gv.Ansatz(i.n_qubits, i.reps) for i in insts + small]
+    hams = [gv.Hamiltonian.from_workload(i.ham) for i in insts + small]
+    xa, xh = gv.Ansatz(xy_n, xy_reps), gv.Hamiltonian.from_workload(xy_ham)
+    ans.append(xa)
+    hams.append(xh)
+    rep_a, rep_h = ans[0], hams[0]
+    ans += [rep_a, rep_a]
+    hams += [rep_h, rep_h]
+    thetas = [i.theta[0] for i in insts + small]
+    thetas.append(wl.thetas(xy_n, xy_reps, 1, seed=12)[0])
+    thetas += [wl.thetas(insts[0].n_qubits, insts[0].reps, 2, seed=13)[k] for k in range(2)]
+    b = gv.Batch(ans, hams)
+    params = [_dev(t) for t in thetas]
+    grads = [torch.full_like(p, float("nan")) for p in params]
+    e = b.run(params, grads=grads).cpu().numpy()
+    refs = [(i.n_qubits, i.reps, i.ham) for i in insts + small] + [(xy_n, xy_reps, xy_ham)]
+    refs += [refs[0], refs[0]]
+    for k, (n, reps, ham) in enumerate(refs):
+        e1, g1 = gv.energy_grad(ans[k], hams[k], params[k])
+        g = grads[k].cpu().numpy()
+        scale = ham.abs_sum()
+        assert abs(e[k] - e1.item()) <= 2e-5 * scale
+        assert np.linalg.norm(g - g1.cpu().numpy()[0]) <= 1e-4 * np.linalg.norm(g1.cpu().numpy()[0])
+        e_ref, g_ref = oracle.energy_grad(n, reps, thetas[k], ham.strings, ham.coeffs)
+        assert abs(e[k] - e_ref) <= 2e-5 * scale, k
+        assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref), k
+    # the repeated subproblem: three different vectors, three different results
+    assert len({float(e[0]), float(e[-2]), float(e[-1])}) == 3

@@ -182,8 +182,13 @@ def test_batch_api_matches_single_calls():
     e = b.run(params, masks=masks, grads=grads).cpu().numpy()
     for k, i in enumerate(insts):
         e1, g1 = gv.energy_grad(ans[k], hams[k], params[k], mask=masks[k])
-        assert e[k] == e1.item()
-        assert np.array_equal(grads[k].cpu().numpy(), g1.cpu().numpy()[0])
+        if i.n_qubits < 12:  # evaluated by a single call inside the run: the same bits
+            assert e[k] == e1.item()
+            assert np.array_equal(grads[k].cpu().numpy(), g1.cpu().numpy()[0])
+        else:  # the persistent launch's 2^12-amplitude tiles sum in another order
+            assert abs(e[k] - e1.item()) <= FP32_E * i.ham.abs_sum()
+            g1 = g1.cpu().numpy()[0]
+            assert np.linalg.norm(grads[k].cpu().numpy() - g1) <= FP32_G * np.linalg.norm(g1)
         e_ref, g_ref = oracle.energy_grad(i.n_qubits, i.reps, i.theta[0], i.ham.strings, i.ham.coeffs)
         g_ref = np.where(i.mask[0] == 1, g_ref, 0.0)
         _check(np.array([e[k]]), grads[k].cpu().numpy()[None], np.array([e_ref]), g_ref[None],

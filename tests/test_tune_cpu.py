@@ -56,7 +56,7 @@ def test_round_trip_and_replace(tmp_path):
     _lib.gvqe_tune_cache_put(p, "k1", 12, 0, 9.0, "")
     assert _lib.gvqe_tune_cache_get(p, "k1") == (12, 0, 9.0)
     assert _lib.gvqe_tune_cache_get(p, "stale-key") is None
-    assert not os.path.exists(p + ".tmp")
+    assert not any(f.startswith("tune.json.tmp") for f in os.listdir(tmp_path))
 
 
 @pytest.mark.parametrize("text", ["", "{", "not json", '{"k1": {"tile_bits": 13}}', '{"k1": [1, 2]}',
