@@ -290,8 +290,18 @@ def cluster_leg(steps: int):
             "total_amplitudes": amps, "algorithmic_GB_per_run": nbytes / 1e9, "GBps": gbps,
             "frac_of_hbm_peak": gbps / peak if peak else None,
             "schedule": tune.strip().splitlines(),
-            "note": "states of 2^14..2^20 amplitudes partly stay in L2, so the rate can pass the HBM copy peak",
-            "timing": "wall clock around synchronous gvqe_batch_run calls"}
+            "tuned_ms_per_run": _tuned_ms(tune),
+            "note": "algorithmic bytes: per amplitude 4 + 8 per further forward pass + 12 per backward pass + 4 "
+                    "(every pass of the 2^12-tile plans); some states stay in L2 between passes",
+            "timing": "wall clock around synchronous gvqe_batch_run calls (tuned_ms_per_run: CUDA events)"}
+
+
+def _tuned_ms(report: str):
+    """The chosen schedule's CUDA-event time per run from the batch autotuner's report."""
+    import re
+
+    m = re.search(r"([0-9.]+) ms per run", report)
+    return float(m.group(1)) if m else None
 
 
 def readout_leg(n: int, reps: int, ham, steps: int):

@@ -162,13 +162,14 @@ int gvqe_energy_grad(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, co
  * (Section IV-D, Eq. 11): instance i pairs ansatze[i] with hams[i] (equal n)
  * and evaluates one parameter vector with its own active mask per run.  The
  * same pair of handles may appear in several slots (several parameter vectors
- * of one subproblem per run).  Instances with n >= 12, RY layers and a
- * diagonal (I/Z-only) Hamiltonian run together in one persistent kernel
- * launch on 2^12-amplitude tiles, captured in a CUDA graph; the others (n <
- * 12, X/Y strings, RY+RZ layers) are evaluated by single gvqe_energy_grad
- * calls on the same stream in the same gvqe_batch_run, after that launch.
- * The tile size fixes the summation order, so persistent results agree with
- * single calls within the precision bounds, not bit for bit.
+ * of one subproblem per run).  Instances with RY layers and a diagonal (I/Z-
+ * only) Hamiltonian run together in the batch's CUDA graph under its schedule
+ * (gvqe_batch_set_option: staged by default, or one persistent kernel
+ * launch); the others (X/Y strings, RY+RZ layers) are evaluated by single
+ * gvqe_energy_grad calls on the same stream in the same gvqe_batch_run, after
+ * the graph.  Staged results equal single calls bit for bit; the persistent
+ * kernel's 2^12-amplitude tiles fix another summation order, so its results
+ * agree with single calls within the precision bounds.
  *   n_inst: >= 1.  ansatze, hams: host arrays of n_inst handles (borrowed: they
  *   must outlive the batch).  flags: GVQE_FP32 or GVQE_FP64.
  * Errors: GVQE_EINVAL, GVQE_ENOMEM, GVQE_ECUDA, GVQE_EUNSUPPORTED.
@@ -200,23 +201,30 @@ int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *con
  *     many bytes (0: one wave), each wave stage-major (every instance's pass s
  *     before any instance's pass s + 1), so a wave's states can stay in L2
  *     between their passes.  Default 0 (one wave).
- *   GVQE_BATCH_OPT_SCHEDULE: GVQE_BATCH_PERSISTENT (default): one persistent
- *     launch whose CTAs claim items in ticket order and wait (bounded) for the
- *     previous step of the item's instance; GVQE_BATCH_STAGED: one launch per
- *     stage (every instance's step s), each CTA one item, the stream order
- *     between the launches in place of the waits.  Both are captured in the
- *     batch's CUDA graph.
+ *   GVQE_BATCH_OPT_SCHEDULE: GVQE_BATCH_STAGED (default): the instances with
+ *     the same plan (n, reps, entangler, strided layout) form a group whose
+ *     states, partial sums and diagonal tables sit job after job, and each
+ *     group runs its plan's passes as launches of the regular pass kernels over
+ *     all its jobs (as gvqe_energy_grad runs a batch of vectors), on its own
+ *     branch of the graph; the branches run side by side.  Results equal those
+ *     of single gvqe_energy_grad calls bit for bit, and every instance with RY
+ *     layers and a diagonal H takes part, whatever its n.
+ *     GVQE_BATCH_PERSISTENT: one persistent launch whose CTAs claim items
+ *     (one 2^tile-bits tile of one pass) in ticket order and wait, with a
+ *     bounded spin, for the previous step of the item's instance.  Both are
+ *     captured in the batch's CUDA graph.
  *   GVQE_BATCH_OPT_TILE_BITS: 10, 11 or 12 (default), the log2 amplitudes of
  *     one work item of the persistent launch (FP32; FP64 batches take 12 only,
- *     else GVQE_EUNSUPPORTED).  2^10 makes every CTA one warp.  Instances with
- *     fewer qubits than this are evaluated by single calls in the same run.
+ *     else GVQE_EUNSUPPORTED).  2^10 makes every CTA one warp.  Under the
+ *     persistent schedule, instances with fewer qubits than this are evaluated
+ *     by single calls in the same run.
  * The schedule is rebuilt on the next run.
  * Results do not depend on the option (each instance's passes and reductions
  * are the same).  Errors: GVQE_EINVAL.
  *
- * gvqe_batch_autotune -- run the batch under both schedules and each tile size
- * 2^12, 2^11, 2^10 (FP64: 2^12), one wave, and persistent 2^12 with 256 MiB
- * waves (one warm-up run and three
+ * gvqe_batch_autotune -- run the batch under the persistent schedule with
+ * tiles of 2^12, 2^11, 2^10 (FP64: 2^12) in one wave and 2^12 in 256 MiB
+ * waves, and under the staged schedule (one warm-up run and three
  * timed runs under CUDA
  * events on `stream` each, with the caller's params / masks / outputs as in
  * gvqe_batch_run) and keep the fastest.  report (host, report_len bytes, or

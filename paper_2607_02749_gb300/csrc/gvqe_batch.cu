@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -266,29 +267,23 @@ k_batch(const BatchArgs B) {
   }
 }
 
-// The staged schedule: one launch per stage (every instance's step s), the
-// stream order in place of the persistent kernel's waits.  A CTA runs the one
-// item of this stage's ticket range that its block index names.
+// The staged schedule: instances with the same plan (n, reps, entangler,
+// layout) form a group, and a group runs its plan's steps as launches in order
+// on a stream of its own (one branch of the batch's graph; the branches run
+// side by side).  A launch covers one step of every instance of the group: CTA
+// (x, y) runs tile x of the step of the group's y-th instance.  The stream order
+// takes the place of the persistent kernel's waits, and no CTA searches for its
+// work item.
 template <typename T, int TB>
-__global__ void __launch_bounds__(1 << (TB - 5), sizeof(T) == 8 ? 2 : 5) k_stage(const BatchArgs B, unsigned first) {
-  __shared__ int s_si;
-  __shared__ unsigned s_tile;
-  if (threadIdx.x == 0) {
-    const unsigned item = first + blockIdx.x;
-    int lo = B.blk_seg[item >> SEG_BLK_BITS];
-    while (lo + 1 < B.nseg && B.seg_start[lo + 1] <= item) ++lo;
-    s_si = B.seg_step[lo];
-    s_tile = item - B.seg_start[lo];
+__global__ void __launch_bounds__(1 << (TB - 5), sizeof(T) == 8 ? 2 : 5) k_stage(const BatchArgs B, const int *ids) {
+  const BatchStep &st = B.steps[ids[blockIdx.y]];
+  if (st.kind == S_PREP) {
+    batch_prep<T>(st, B.io[st.inst]);
+  } else if (st.kind == S_REDUCE) {
+    batch_reduce(st, B.io[st.inst]);
+  } else {
+    batch_pass<T, TB>(st.A, blockIdx.x);
   }
-  __syncthreads();
-  const BatchStep &st = B.steps[s_si];
-  const BatchIO io = B.io[st.inst];
-  if (st.kind == S_PREP)
-    batch_prep<T>(st, io);
-  else if (st.kind == S_REDUCE)
-    batch_reduce(st, io);
-  else
-    batch_pass<T, TB>(st.A, s_tile);
 }
 
 // ------------------------------------------------------------------- host --
@@ -300,10 +295,11 @@ static cudaError_t launch_batch(const BatchArgs &B, int ctas, size_t smem, cudaS
 }
 
 template <typename T, int TB>
-static cudaError_t launch_stage(const BatchArgs &B, unsigned first, unsigned count, size_t smem, cudaStream_t s) {
+static cudaError_t launch_stage(const BatchArgs &B, const int *ids, unsigned tiles, unsigned insts, size_t smem,
+                                cudaStream_t s) {
   const cudaError_t e = cudaFuncSetAttribute(k_stage<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_stage<T, TB><<<count, 1 << (TB - 5), smem, s>>>(B, first);
+  k_stage<T, TB><<<dim3(tiles, insts), 1 << (TB - 5), smem, s>>>(B, ids);
   return cudaGetLastError();
 }
 
@@ -338,7 +334,7 @@ struct BatchSchedule {
   int nsteps = 0;
   int counters = 0;
   int waves = 0;
-  std::vector<unsigned> stage_first;  // ticket ranges of the stages (staged schedule), plus the end
+  int groups = 0;  // staged schedule: groups of instances that share one plan
 };
 
 struct gvqe_batch_s {
@@ -346,7 +342,7 @@ struct gvqe_batch_s {
   int prec = 0;
   bool persistent = false;
   long long wave_bytes = kDefaultWaveBytes;  // GVQE_BATCH_OPT_WAVE_BYTES
-  int schedule = GVQE_BATCH_PERSISTENT;     // GVQE_BATCH_OPT_SCHEDULE
+  int schedule = GVQE_BATCH_STAGED;         // GVQE_BATCH_OPT_SCHEDULE
   int tile_bits = 12;                        // GVQE_BATCH_OPT_TILE_BITS (FP64: always 12)
   std::string tune_report;
   // instances of the persistent launch (slot k -> instance pidx[k]) and the
@@ -380,13 +376,13 @@ cudaError_t launch_batch_tb(int prec, int tb, const BatchArgs &B, int ctas, size
     default: return launch_batch<float, 12>(B, ctas, smem, s);
   }
 }
-cudaError_t launch_stage_tb(int prec, int tb, const BatchArgs &B, unsigned first, unsigned count, size_t smem,
-                            cudaStream_t s) {
-  if (prec) return launch_stage<double, 12>(B, first, count, smem, s);
+cudaError_t launch_stage_tb(int prec, int tb, const BatchArgs &B, const int *ids, unsigned tiles, unsigned insts,
+                            size_t smem, cudaStream_t s) {
+  if (prec) return launch_stage<double, 12>(B, ids, tiles, insts, smem, s);
   switch (tb) {
-    case 10: return launch_stage<float, 10>(B, first, count, smem, s);
-    case 11: return launch_stage<float, 11>(B, first, count, smem, s);
-    default: return launch_stage<float, 12>(B, first, count, smem, s);
+    case 10: return launch_stage<float, 10>(B, ids, tiles, insts, smem, s);
+    case 11: return launch_stage<float, 11>(B, ids, tiles, insts, smem, s);
+    default: return launch_stage<float, 12>(B, ids, tiles, insts, smem, s);
   }
 }
 int batch_occupancy_tb(int prec, int tb, size_t smem) {
@@ -411,7 +407,10 @@ long long wait_budget_cycles() {
     if (e_ != cudaSuccess) return fail(GVQE_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));  \
   } while (0)
 
+int build_grouped(gvqe_batch_s *b, int want_grad);
+
 int build_schedule(gvqe_batch_s *b, int want_grad) {
+  if (b->schedule == GVQE_BATCH_STAGED) return build_grouped(b, want_grad);
   BatchSchedule &sc = b->sched[want_grad];
   const int prec = b->prec;
   const int TB = tile_bits_for(b);
@@ -494,12 +493,10 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   std::vector<unsigned> seg_start;
   std::vector<int> seg_step;
   unsigned tick = 0;
-  sc.stage_first.clear();
   for (const std::vector<int> &wv : waves) {
     size_t max_stage = 0;
     for (int i : wv) max_stage = std::max(max_stage, inst_steps[i].size());
     for (size_t s = 0; s < max_stage; ++s) {
-      sc.stage_first.push_back(tick);
       for (int i : wv) {
         if (s >= inst_steps[i].size()) continue;
         const int si = inst_steps[i][s];
@@ -509,7 +506,6 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
       }
     }
   }
-  sc.stage_first.push_back(tick);
   sc.waves = (int)waves.size();
   const int nseg = (int)seg_start.size();
   const int counters = nsteps + 1;
@@ -535,6 +531,7 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   off = up256(off + sizeof(int) * nseg);
   const size_t o_blkseg = off;
   off = up256(off + sizeof(int) * nblk);
+
   const size_t o_ctr = off;  // ticket, err, done[counters]
   off = up256(off + sizeof(unsigned) * (2 + counters));
   const size_t o_io = off;
@@ -604,6 +601,7 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   GB_CUDA(cudaMemcpy(base + o_segs, seg_start.data(), sizeof(unsigned) * nseg, cudaMemcpyHostToDevice));
   GB_CUDA(cudaMemcpy(base + o_segstep, seg_step.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice));
   GB_CUDA(cudaMemcpy(base + o_blkseg, blk_seg.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice));
+
   if (!dirs.empty()) GB_CUDA(cudaMemcpy(base + o_dir, dirs.data(), sizeof(RedEntry) * dirs.size(), cudaMemcpyHostToDevice));
 
   BatchArgs &B = sc.args;
@@ -634,13 +632,7 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(base + o_ctr, 0, sizeof(unsigned) * (2 + counters), cap);
-    cudaError_t le = cudaSuccess;
-    if (b->schedule == GVQE_BATCH_STAGED) {
-      for (size_t k = 0; k + 1 < sc.stage_first.size() && le == cudaSuccess; ++k)
-        le = launch_stage_tb(prec, TB, B, sc.stage_first[k], sc.stage_first[k + 1] - sc.stage_first[k], sc.smem, cap);
-    } else {
-      le = launch_batch_tb(prec, TB, B, sc.ctas, sc.smem, cap);
-    }
+    const cudaError_t le = launch_batch_tb(prec, TB, B, sc.ctas, sc.smem, cap);
     e = cudaStreamEndCapture(cap, &sc.graph);
     if (e == cudaSuccess) e = le;
   }
@@ -654,6 +646,190 @@ int build_schedule(gvqe_batch_s *b, int want_grad) {
 
 int batch_loop(gvqe_batch_s *b, const double *const *params, const uint8_t *const *masks, double *energies,
                double *const *grads, cudaStream_t s);
+
+// The staged schedule.  Instances with the same plan (n, reps, entangler, strided
+// layout) form a group of J jobs whose states, partial sums, trig tables and
+// diagonal tables (copied from each Hamiltonian) sit job after job, so each of
+// the plan's passes runs as ONE launch of the regular pass kernels over all J
+// jobs (the persistent, prefetching backward included), as gvqe_energy_grad
+// runs a batch of parameter vectors.  Per group, on a branch of its own of the
+// graph: a PREP launch (one CTA per job: its cos/sin table and lowest active
+// layer), the plan's passes, and a REDUCE launch (one CTA per job: its energy
+// and gradient into the caller's buffers).  The branches run side by side.
+int build_grouped(gvqe_batch_s *b, int want_grad) {
+  BatchSchedule &sc = b->sched[want_grad];
+  const int prec = b->prec;
+  const size_t es = prec ? 8 : 4;
+  const int tbg = max_tile_bits(prec);
+  const int ni = (int)b->pidx.size();
+  auto A_of = [&](int k) { return b->a[b->pidx[k]]; };
+  auto H_of = [&](int k) { return b->h[b->pidx[k]]; };
+  std::map<std::vector<int>, std::vector<int>> by_plan;  // plan key -> slots
+  for (int k = 0; k < ni; ++k)
+    by_plan[{A_of(k)->n, A_of(k)->reps, A_of(k)->ent, eff_split(A_of(k), prec)}].push_back(k);
+  struct Group {
+    std::vector<int> slots;
+    Plan plan;
+    size_t o_cs, o_ml, o_part, o_tab, o_bufs, o_dir;
+  };
+  std::vector<Group> groups;
+  std::vector<BatchStep> steps;  // PREP then REDUCE per slot
+  size_t off = 0;
+  const size_t o_steps = off;
+  off = up256(off + sizeof(BatchStep) * 2 * (size_t)ni);
+  const size_t o_ids = off;
+  off = up256(off + sizeof(int) * 2 * (size_t)ni);
+  const size_t o_ctr = off;  // ticket, err (unused here, kept zero for the error check)
+  off = up256(off + sizeof(unsigned) * 2);
+  const size_t o_io = off;
+  off = up256(off + sizeof(BatchIO) * ni);
+  for (auto &kv : by_plan) {
+    Group g;
+    g.slots = kv.second;
+    const gvqe_ansatz a0 = A_of(g.slots[0]);
+    g.plan = build_plan(a0->n, a0->reps, prec, tbg, want_grad != 0, true, false, false, a0->ent, 1,
+                        eff_split(a0, prec));
+    const size_t J = g.slots.size(), S = (size_t)g.plan.state_elems;
+    g.o_cs = off;
+    off = up256(off + J * g.plan.P * 2 * es);
+    g.o_ml = off;
+    off = up256(off + J * 4);
+    g.o_part = off;
+    off = up256(off + J * (size_t)g.plan.part_stride * 8);
+    g.o_tab = off;
+    off = up256(off + J * S * es);
+    g.o_bufs = off;
+    off = up256(off + (size_t)g.plan.n_bufs * J * S * es);
+    g.o_dir = off;
+    off = up256(off + sizeof(RedEntry) * std::max<size_t>(1, g.plan.dir.size()));
+    groups.push_back(std::move(g));
+  }
+  {
+    const int rc = sc.dev.reserve(off);
+    if (rc != GVQE_OK) return rc;
+  }
+  char *base = (char *)sc.dev.ptr;
+  std::vector<int> prep_ids(ni), red_ids(ni);
+  steps.resize(2 * (size_t)ni);
+  for (const Group &g : groups) {
+    const size_t S = (size_t)g.plan.state_elems;
+    for (size_t j = 0; j < g.slots.size(); ++j) {
+      const int k = g.slots[j];
+      BatchStep &pr = steps[2 * (size_t)k];
+      pr = BatchStep{};
+      pr.kind = S_PREP;
+      pr.inst = k;
+      pr.items = 1;
+      pr.dep = -1;
+      pr.n = g.plan.n;
+      pr.reps = g.plan.reps;
+      pr.A.P = g.plan.P;
+      pr.A.cs = base + g.o_cs + j * g.plan.P * 2 * es;
+      pr.A.minlayer = (const int *)(base + g.o_ml) + j;
+      BatchStep &rd = steps[2 * (size_t)k + 1];
+      rd = BatchStep{};
+      rd.kind = S_REDUCE;
+      rd.inst = k;
+      rd.items = 1;
+      rd.dep = -1;
+      rd.A.part = (double *)(base + g.o_part) + j * (size_t)g.plan.part_stride;
+      rd.dir = (const RedEntry *)(base + g.o_dir);
+      rd.ndir = (int)g.plan.dir.size();
+      // this job's diagonal table
+      const gvqe_hamiltonian h = H_of(k);
+      GB_CUDA(cudaMemcpy(base + g.o_tab + j * S * es, prec ? h->T64.ptr : h->T32.ptr, S * es, cudaMemcpyDeviceToDevice));
+    }
+    if (!g.plan.dir.empty())
+      GB_CUDA(cudaMemcpy(base + g.o_dir, g.plan.dir.data(), sizeof(RedEntry) * g.plan.dir.size(), cudaMemcpyHostToDevice));
+  }
+  // PREP and REDUCE ids in group order (a launch covers one group's contiguous range)
+  std::vector<int> ids;
+  for (const Group &g : groups)
+    for (int k : g.slots) ids.push_back(2 * k);
+  for (const Group &g : groups)
+    for (int k : g.slots) ids.push_back(2 * k + 1);
+  GB_CUDA(cudaMemcpy(base + o_steps, steps.data(), sizeof(BatchStep) * steps.size(), cudaMemcpyHostToDevice));
+  GB_CUDA(cudaMemcpy(base + o_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
+  GB_CUDA(cudaMemset(base + o_ctr, 0, sizeof(unsigned) * 2));
+
+  BatchArgs &B = sc.args;
+  B = BatchArgs{};
+  B.steps = (const BatchStep *)(base + o_steps);
+  B.ticket = (unsigned *)(base + o_ctr);
+  B.err = (int *)(base + o_ctr + sizeof(unsigned));
+  B.io = (const BatchIO *)(base + o_io);
+  sc.smem = 0;
+  sc.groups = (int)groups.size();
+  sc.waves = 1;
+  const int *d_ids = (const int *)(base + o_ids);
+
+  cudaStream_t cap;
+  GB_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  cudaError_t le = cudaSuccess;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> evs;
+  if (e == cudaSuccess) {
+    cudaEvent_t fork = nullptr;
+    le = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (le == cudaSuccess) {
+      evs.push_back(fork);
+      le = cudaEventRecord(fork, cap);
+    }
+    size_t first = 0;
+    for (size_t gi = 0; gi < groups.size() && le == cudaSuccess; ++gi) {
+      const Group &g = groups[gi];
+      const int J = (int)g.slots.size();
+      const size_t S = (size_t)g.plan.state_elems;
+      cudaStream_t gs = nullptr;
+      le = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+      if (le != cudaSuccess) break;
+      streams.push_back(gs);
+      le = cudaStreamWaitEvent(gs, fork, 0);
+      if (le == cudaSuccess) le = launch_stage_tb(prec, 12, B, d_ids + first, 1, (unsigned)J, 0, gs);
+      char *bufs = base + g.o_bufs;
+      for (const PassStep &st : g.plan.steps) {
+        if (le != cudaSuccess) break;
+        PassArgs A = st.A;
+        A.job0 = 0;
+        A.cs = base + g.o_cs;
+        A.table = base + g.o_tab;
+        A.table_stride = (long long)S;
+        A.in = st.in < 0 ? nullptr : bufs + (size_t)st.in * J * S * es;
+        A.in_stride = (long long)S;
+        A.lam_in = st.lam < 0 ? nullptr : bufs + (size_t)st.lam * J * S * es;
+        A.lam_stride = (long long)S;
+        A.out = st.out < 0 ? nullptr : bufs + (size_t)st.out * J * S * es;
+        A.out_stride = (long long)S;
+        double *part = (double *)(base + g.o_part);
+        A.part = part + (st.part_region >= 0 ? st.part_region : 0);
+        A.epart = part + (st.epart_region >= 0 ? st.epart_region : 0);
+        A.part_stride = g.plan.part_stride;
+        A.minlayer = (const int *)(base + g.o_ml);
+        le = launch_pass(prec, A, J, 0, gs);
+      }
+      if (le == cudaSuccess) le = launch_stage_tb(prec, 12, B, d_ids + ni + first, 1, (unsigned)J, 0, gs);
+      cudaEvent_t join = nullptr;
+      if (le == cudaSuccess) le = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+      if (le == cudaSuccess) {
+        evs.push_back(join);
+        le = cudaEventRecord(join, gs);
+      }
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(cap, join, 0);
+      first += (size_t)J;
+    }
+    e = cudaStreamEndCapture(cap, &sc.graph);
+    if (e == cudaSuccess) e = le;
+  }
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+  for (cudaStream_t gs : streams) cudaStreamDestroy(gs);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return fail(GVQE_ECUDA, "batch graph capture (staged): %s", cudaGetErrorString(e));
+  GB_CUDA(cudaGraphInstantiate(&sc.exec, sc.graph, 0));
+  sc.built = true;
+  b->io_valid[want_grad] = false;
+  return GVQE_OK;
+}
 
 }  // namespace
 
@@ -683,7 +859,8 @@ void classify(gvqe_batch_s *b) {
   for (size_t i = 0; i < b->a.size(); ++i) {
     const gvqe_ansatz a = b->a[i];
     const gvqe_hamiltonian h = b->h[i];
-    if (a->n < tile_bits_for(b) || !h->gm.empty() || a->gates != 1)
+    const bool small = b->schedule != GVQE_BATCH_STAGED && a->n < tile_bits_for(b);
+    if (small || !h->gm.empty() || a->gates != 1)
       b->sidx.push_back((int)i);
     else
       b->pidx.push_back((int)i);
@@ -755,6 +932,7 @@ int gvqe_batch_set_option(gvqe_batch b, int option, long long value) {
     b->wave_bytes = value;
   } else if (option == GVQE_BATCH_OPT_SCHEDULE) {
     b->schedule = (int)value;
+    classify(b);
   } else {
     b->tile_bits = (int)value;
     classify(b);
@@ -796,12 +974,12 @@ int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t
     long long wb;
   };
   std::vector<Cand> cands;
-  for (int sch : {(int)GVQE_BATCH_PERSISTENT, (int)GVQE_BATCH_STAGED})
-    for (int tb : {12, 11, 10}) {
-      if (b->prec && tb != 12) continue;
-      cands.push_back({sch, tb, 0});
-    }
+  for (int tb : {12, 11, 10}) {
+    if (b->prec && tb != 12) continue;
+    cands.push_back({GVQE_BATCH_PERSISTENT, tb, 0});
+  }
   cands.push_back({GVQE_BATCH_PERSISTENT, 12, 256ll << 20});
+  cands.push_back({GVQE_BATCH_STAGED, 12, 0});  // the regular plans' tiles (2^13 FP32, 2^12 FP64)
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   GB_CUDA(cudaEventCreate(&e0));
   GB_CUDA(cudaEventCreate(&e1));
@@ -828,9 +1006,12 @@ int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t
     const double per = ms / timed;
     const int g = grads ? 1 : 0;
     char line[200];
-    snprintf(line, sizeof(line), "%s%s tiles=2^%d wave=%lldMiB (%d waves, %zu of %zu instances in it): %.3f ms",
-             sweep.empty() ? "" : "; ", cd.sched == GVQE_BATCH_STAGED ? "staged" : "persistent", cd.tb, cd.wb >> 20,
-             b->sched[g].waves, b->pidx.size(), b->a.size(), per);
+    if (cd.sched == GVQE_BATCH_STAGED)
+      snprintf(line, sizeof(line), "%sstaged (%d plan groups, %zu of %zu instances in it): %.3f ms",
+               sweep.empty() ? "" : "; ", b->sched[g].groups, b->pidx.size(), b->a.size(), per);
+    else
+      snprintf(line, sizeof(line), "%spersistent tiles=2^%d wave=%lldMiB (%d waves, %zu of %zu instances in it): %.3f ms",
+               sweep.empty() ? "" : "; ", cd.tb, cd.wb >> 20, b->sched[g].waves, b->pidx.size(), b->a.size(), per);
     sweep += line;
     if (best.tb < 0 || per < best_ms) {
       best = cd;
@@ -850,9 +1031,13 @@ int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t
   if (rc == GVQE_OK) rc = gvqe_batch_set_option(b, GVQE_BATCH_OPT_WAVE_BYTES, best.wb);
   if (rc != GVQE_OK) return rc;
   char line[200];
-  snprintf(line, sizeof(line), "batch autotune: %s schedule, tiles 2^%d, wave bytes %lld MiB (%s), %.3f ms per run\n",
-           best.sched == GVQE_BATCH_STAGED ? "staged" : "persistent", best.tb, best.wb >> 20,
-           best.wb == 0 ? "one wave" : "waves", best_ms);
+  if (best.sched == GVQE_BATCH_STAGED)
+    snprintf(line, sizeof(line), "batch autotune: staged schedule (plan groups, regular pass kernels), %.3f ms per run\n",
+             best_ms);
+  else
+    snprintf(line, sizeof(line),
+             "batch autotune: persistent schedule, tiles 2^%d, wave bytes %lld MiB (%s), %.3f ms per run\n", best.tb,
+             best.wb >> 20, best.wb == 0 ? "one wave" : "waves", best_ms);
   rep = std::string(line) + "batch autotune sweep: " + sweep + "\n";
   b->tune_report = rep;
   put();

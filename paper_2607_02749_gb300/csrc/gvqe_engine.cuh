@@ -177,6 +177,7 @@ struct PassArgs {
   void *out;                // psi or lambda output
   long long out_stride;
   const void *table;        // diagonal table E(x) in amplitude precision
+  long long table_stride;   // elements between the tables of consecutive jobs (0: one table for all)
   const void *cs;           // (cos(theta/2), sin(theta/2)) per job and parameter
   int job0;                 // global index of job 0 of this launch (cs, minlayer)
   EntMap em;                // this layer's entangler, x = A^-1 y (LD_GATHER, LD_L0_GATHER, ST_SCATTER)

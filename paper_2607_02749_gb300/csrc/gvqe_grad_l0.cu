@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(GL_NT, sizeof(T) == 4 ? 2 : 1) k_grad_l0w(cons
   }
   const int src = 2 * slot_of(lane, mb);
 
-  const T *base = INIT ? reinterpret_cast<const T *>(A.table)
+  const T *base = INIT ? reinterpret_cast<const T *>(A.table) + (size_t)job * A.table_stride
                        : reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
   const int lofs = 4 * lane;
   auto chunk_ptr = [&](long long s) -> const T * {

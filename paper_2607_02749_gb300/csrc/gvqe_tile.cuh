@@ -864,7 +864,7 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   round_gates<1, WHT, false, 1>(r, gt, gm, 5, false);
   round_gates<H, WHT, false, 2>(r, gt, gm, 10, false);
   if constexpr (CPLX) apply_su2_phase<false>(r, zt, zt.thread_phase(tid));
-  const T *table = reinterpret_cast<const T *>(A.table);
+  const T *table = reinterpret_cast<const T *>(A.table) + (size_t)job * A.table_stride;
   const bool store = A.store_mode != ST_NONE;
   const bool energy = (A.flags & F_ENERGY) != 0;
   T eacc = T(0);
@@ -956,7 +956,7 @@ k_bwd(const PassArgs A) {
   if constexpr (CPLX) zt.build(A, cs, tid);
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
   const bool init = (A.flags & F_LAMBDA_INIT) != 0;
-  const T *lsrc = init ? reinterpret_cast<const T *>(A.table)
+  const T *lsrc = init ? reinterpret_cast<const T *>(A.table) + (size_t)job * A.table_stride
                        : reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
   T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
   double *part = A.part + (size_t)job * A.part_stride;
@@ -1163,7 +1163,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   __syncthreads();
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
   const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
-  const T *table = reinterpret_cast<const T *>(A.table);
+  const T *table = reinterpret_cast<const T *>(A.table) + (size_t)job * A.table_stride;
   T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
   const uint32_t gm = A.gate_mask;
   const bool init = (A.flags & F_LAMBDA_INIT) != 0;
@@ -1328,7 +1328,7 @@ __device__ __forceinline__ void grad_l0_tile(const PassArgs &A, int job, uint32_
 
   const bool init = (A.flags & F_LAMBDA_INIT) != 0;
   const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
-  const T *table = reinterpret_cast<const T *>(A.table);
+  const T *table = reinterpret_cast<const T *>(A.table) + (size_t)job * A.table_stride;
   const uint32_t tbase = t << TB;
   const T fhi_t = (T)fhi_all;
   T S = T(0), Sj[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -1504,7 +1504,7 @@ __global__ void __launch_bounds__(1 << (TB - 5)) k_lambda_xy(const PassArgs A) {
   }
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
   const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
-  const T *table = reinterpret_cast<const T *>(A.table);
+  const T *table = reinterpret_cast<const T *>(A.table) + (size_t)job * A.table_stride;
   T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
   const uint32_t tbase = t << TB;
   // the thread's elements: FP64 e = k NT + tid; FP32 pairs (j 2^(TB-4) + 2 tid, + 1)

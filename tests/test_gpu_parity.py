@@ -176,6 +176,7 @@ def test_batch_api_matches_single_calls():
     ans = [gv.Ansatz(i.n_qubits, i.reps) for i in insts]
     hams = [gv.Hamiltonian.from_workload(i.ham) for i in insts]
     b = gv.Batch(ans, hams)
+    b.set_schedule(False)  # the persistent kernel (the staged default is checked in test_gpu_batch.py)
     params = [_dev(i.theta[0]) for i in insts]
     masks = [_dev(i.mask[0], torch.uint8) for i in insts]
     grads = [torch.empty_like(p) for p in params]
