@@ -385,6 +385,7 @@ def su2_leg(n: int, reps: int, ham, steps: int):
     a = gv.Ansatz(n, reps, gates=gv.GVQE_GATES_RY_RZ)
     h = gv.Hamiltonian.from_workload(ham)
     th = torch.as_tensor(np.random.default_rng(1).uniform(-np.pi, np.pi, (1, a.n_params)), device="cuda")
+    tune = a.autotune(h, th, cache=os.environ.get("GVQE_TUNE_CACHE", os.path.join("/tmp", "gvqe_tune.json")))
     e, g = gv.energy_grad(a, h, th)
     torch.cuda.synchronize()
     _lib.gvqe_profile_reset()
@@ -407,6 +408,7 @@ def su2_leg(n: int, reps: int, ham, steps: int):
         per_kind[names[k]] = {"launches": prof[k]["launches"], "ms": prof[k]["ms"], "GBps": gbps,
                               "frac": gbps / peak if peak else None}
     out = {"value": 1.0 / dt, "unit": UNIT, "n_params": a.n_params, "E": float(e.item()),
+           "plan": tune.strip().splitlines(),
            "amplitudes": "fp32 complex (2^(n+1) reals), fp64 table and reductions",
            "per_kind": per_kind, "peak_GBps": peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
            "timing": "wall clock around synchronous single-vector gvqe_energy_grad calls (FP32 adjoint)"}
@@ -475,6 +477,7 @@ def xy_leg(steps: int, workload: str = "n28_reps5_pauli5000"):
     h = gv.Hamiltonian.from_workload(ham)
     st = h.stats()
     base = torch.as_tensor(th, dtype=torch.float64, device="cuda")
+    tune = a.autotune(h, base, cache=os.environ.get("GVQE_TUNE_CACHE", os.path.join("/tmp", "gvqe_tune.json")))
 
     def step():
         t = base.clone().requires_grad_(True)
@@ -495,14 +498,19 @@ def xy_leg(steps: int, workload: str = "n28_reps5_pauli5000"):
     prof = {k: _lib.gvqe_profile_read(k) for k in range(5)}
     _lib.gvqe_profile_reset()
     names = {0: "k_fwd", 1: "k_bwd", 2: "k_grad_l0", 3: "k_lambda_xy", 4: "k_wht"}
-    d_all, d_hi = xy_masks(ham, 13)
+    import re
+
+    m = re.search(r"tile_bits=(\d+)", tune)
+    tb_sel = int(m.group(1)) if m else 13
+    d_all, d_hi = xy_masks(ham, tb_sel)
     S = 4 * 2 ** n
     T = 8 * 2 ** n
     xy = prof[3]
     lam_ms = xy["ms"] / (steps * B) if xy["launches"] else None
     lam_alg = (2 + d_hi) * S + T  # energy and lambda with the X-mask groups (one partner sweep per high part)
     out = {"value": B / dt, "unit": UNIT, "workload": workload, "n_qubits": n, "reps": reps, "batch": B,
-           "n_terms": ham.n_terms, "x_masks": d_all, "D_hi": d_hi, "tile_bits": 13,
+           "n_terms": ham.n_terms, "x_masks": d_all, "D_hi": d_hi, "tile_bits": tb_sel,
+           "plan": tune.strip().splitlines(),
            "groups": st["groups"], "grouped_terms": st["grouped"], "dropped_odd_y": st["dropped_odd_y"],
            "ms_per_step": dt * 1e3,
            "per_kind_ms_per_step": {names[k]: prof[k]["ms"] / steps for k in prof if prof[k]["launches"]},

@@ -72,9 +72,10 @@ extern "C" {
 #define GVQE_OPT_TILE_BITS 1 /* log2 amplitudes per on-chip tile, 10..13 (FP64: 10..12); 0 = auto (13 FP32, 12 FP64) */
 #define GVQE_OPT_GATES 2     /* rotation layer: GVQE_GATES_RY (default) or GVQE_GATES_RY_RZ */
 #define GVQE_OPT_SPLIT_PASSES 3 /* strided-pass bit layout: 0 auto, 1 never split, 2 always split (when a layer
-                                   takes two strided passes).  A split pass covers two runs of qubits, the low
-                                   and the top ones, so that no pass's tile spans more 2 MiB pages than needed;
-                                   results are the same up to the order of FP32/FP64 additions. */
+                                   takes two strided passes), 2 + y: split with y top qubits.  A split pass
+                                   covers two runs of qubits, the low and the top ones, so that no pass's tile
+                                   spans more 2 MiB pages than needed; results are the same up to the order of
+                                   FP32/FP64 additions. */
 
 /* gate sets of a rotation layer (Eq. 8).
  * RY:    RY on every qubit; P = n (reps+1), theta[r*n + q]; real amplitudes.
@@ -272,8 +273,9 @@ int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, 
  * no counterpart (it names no kernel layout); the plan decides how the RY
  * layers of Section IV-B are cut into tile passes for the evaluations of Eq. 4
  * and Eq. 13.  Every distinct plan among tile bits 10 .. 13 (FP64: 10 .. 12)
- * and the two strided layouts (one run of qubits per pass, or a low and a top
- * run) runs the requested evaluation once to warm up and three times under
+ * and the strided layouts (one run of qubits per pass, or a low and a top run
+ * of y = 1 .. 8 top qubits) runs the requested evaluation once to warm up and
+ * three times under
  * CUDA events on `stream`; the fastest becomes the ansatz's plan in that
  * precision (the other precision keeps its own; setting GVQE_OPT_TILE_BITS or
  * GVQE_OPT_SPLIT_PASSES later replaces both).  Candidates that do not fit in
@@ -304,7 +306,7 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
  * energy only, diagonal H or not, batch.  Host only.  Errors: GVQE_EINVAL.
  *
  * gvqe_tune_cache_get -- look `key` up in the JSON cache at `path` (host only):
- * returns 1 and fills tile_bits, split (0 auto, 1 one run, 2 split) and ms (may
+ * returns 1 and fills tile_bits, split (a GVQE_OPT_SPLIT_PASSES value) and ms (may
  * be NULL) when present, 0 when the file is missing, unreadable, malformed or
  * has no such key, GVQE_EINVAL on NULL arguments.
  *

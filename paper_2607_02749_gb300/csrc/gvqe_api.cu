@@ -258,6 +258,7 @@ std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits, int split) {
   // second pass [tb + x, n - y).  Auto, when the top pass would span more than
   // 2^8 pages: the fewest top qubits y that bring the second pass down to 2^8
   // (at n = 30 RY+RZ, y = 4 and 5 measured best, 6 and 3 about 4% slower).
+  // Split modes above SPLIT_ALWAYS name y itself: split = SPLIT_ALWAYS + y.
   if (chunks == 2 && split != SPLIT_NEVER) {
     LayerPass &pa = out[1], &pb_ = out[2];
     const int gA = tb - pa.c;
@@ -265,7 +266,9 @@ std::vector<LayerPass> layer_passes(int n, int prec, int tile_bits, int split) {
     auto pages = [&](int lo, int hi) { return std::max(0, hi - std::max(lo, pb)); };
     const int top = pages(tb + gA, n);
     int best_y = 0;
-    if (top > 8) {
+    if (split > SPLIT_ALWAYS) {
+      best_y = std::min(split - SPLIT_ALWAYS, gA - 1);
+    } else if (top > 8) {
       for (int y = 1; y < gA && best_y == 0; ++y)
         if (pages(tb + gA - y, n - y) <= 8) best_y = y;
     }
@@ -1371,8 +1374,8 @@ int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
     return GVQE_OK;
   }
   if (option == GVQE_OPT_SPLIT_PASSES) {
-    if (value < SPLIT_AUTO || value > SPLIT_ALWAYS)
-      return fail(GVQE_EINVAL, "split mode %d is not 0 (auto), 1 (never) or 2 (always)", value);
+    if (value < SPLIT_AUTO || value > SPLIT_ALWAYS + GVQE_MAX_QUBITS)
+      return fail(GVQE_EINVAL, "split mode %d is not 0 (auto), 1 (never), 2 (always) or 2 + y (y top qubits)", value);
     a->split = value;
     a->tuned_tb[0] = a->tuned_tb[1] = 0;
     a->tuned_split[0] = a->tuned_split[1] = -1;

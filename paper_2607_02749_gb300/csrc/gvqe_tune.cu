@@ -227,7 +227,12 @@ int cache_store(const char *path, const std::string &key, const TuneEntry &t) {
   return GVQE_OK;
 }
 
-const char *split_name(int s) { return s == SPLIT_NEVER ? "one run" : (s == SPLIT_ALWAYS ? "split" : "auto"); }
+std::string split_name(int s) {
+  if (s == SPLIT_NEVER) return "one run";
+  if (s == SPLIT_ALWAYS) return "split";
+  if (s > SPLIT_ALWAYS) return "split y=" + std::to_string(s - SPLIT_ALWAYS);
+  return "auto";
+}
 
 }  // namespace
 }  // namespace gvqe
@@ -278,7 +283,7 @@ int gvqe_tune_cache_put(const char *path, const char *key, int tile_bits, int sp
   g_err.clear();
   if (!path || !key) return fail(GVQE_EINVAL, "path or key is NULL");
   if (tile_bits < 10 || tile_bits > 13) return fail(GVQE_EINVAL, "tile bits %d outside [10, 13]", tile_bits);
-  if (split < SPLIT_AUTO || split > SPLIT_ALWAYS) return fail(GVQE_EINVAL, "split mode %d", split);
+  if (split < SPLIT_AUTO || split > SPLIT_ALWAYS + GVQE_MAX_QUBITS) return fail(GVQE_EINVAL, "split mode %d", split);
   TuneEntry t;
   t.tile_bits = tile_bits;
   t.split = split;
@@ -330,13 +335,13 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
   if (cache_path && cache_path[0]) {
     TuneEntry t;
     if (cache_lookup(cache_path, key, &t) && t.tile_bits >= 10 && t.tile_bits <= tb_max && t.split >= SPLIT_AUTO &&
-        t.split <= SPLIT_ALWAYS) {
+        t.split <= SPLIT_ALWAYS + GVQE_MAX_QUBITS) {
       a->tuned_tb[prec] = t.tile_bits;
       a->tuned_split[prec] = t.split;
       a->plans.clear();
       char line[256];
       snprintf(line, sizeof(line), "autotune: cached (%s): tile_bits=%d strided=%s %.3f ms\n", cache_path,
-               t.tile_bits, split_name(t.split), t.ms);
+               t.tile_bits, split_name(t.split).c_str(), t.ms);
       a->tune_report = std::string(line) + "autotune sweep (cached): " + t.sweep + "\n";
       put_report(a->tune_report, report, report_len);
       return GVQE_OK;
@@ -349,12 +354,16 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
   };
   std::vector<Cand> cands;
   std::set<std::string> seen;
-  for (int tb = tb_max; tb >= 10; --tb)
-    for (int sp : {(int)SPLIT_NEVER, (int)SPLIT_ALWAYS}) {
+  // one run per strided pass, or a split first strided pass with y = 1 .. 8 top qubits
+  for (int tb = tb_max; tb >= 10; --tb) {
+    std::vector<int> modes = {(int)SPLIT_NEVER};
+    for (int y = 1; y <= 8; ++y) modes.push_back((int)SPLIT_ALWAYS + y);
+    for (int sp : modes) {
       const Plan pl = build_plan(a->n, a->reps, prec, tb, want_grad, true, false, false, a->ent, a->gates, sp);
       std::string d = describe_plan(pl);
       if (seen.insert(d).second) cands.push_back({tb, sp});
     }
+  }
   const int P = a->gates * a->n * (a->reps + 1);
   const size_t out_bytes = ((size_t)batch * 8 + 255) / 256 * 256 + (size_t)batch * P * 8;
   rc = a->tune.reserve(out_bytes);
@@ -390,7 +399,7 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
     }
     if (rc == GVQE_ENOMEM) {
       snprintf(line, sizeof(line), "%stb=%d/%s: no memory", sweep.empty() ? "" : "; ", cands[c].tb,
-               split_name(cands[c].split));
+               split_name(cands[c].split).c_str());
       sweep += line;
       continue;
     }
@@ -410,7 +419,7 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
     GT_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
     const double per = ms / timed;
     snprintf(line, sizeof(line), "%stb=%d/%s: %.3f ms", sweep.empty() ? "" : "; ", cands[c].tb,
-             split_name(cands[c].split), per);
+             split_name(cands[c].split).c_str(), per);
     sweep += line;
     if (best < 0 || per < best_ms) {
       best = (int)c;
@@ -427,7 +436,7 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
   a->plans.clear();
   char line[256];
   snprintf(line, sizeof(line), "autotune: measured: tile_bits=%d strided=%s %.3f ms per call (batch %d, %s, %s)\n",
-           cands[best].tb, split_name(cands[best].split), best_ms, batch, want_grad ? "energy+gradient" : "energy",
+           cands[best].tb, split_name(cands[best].split).c_str(), best_ms, batch, want_grad ? "energy+gradient" : "energy",
            prec ? "fp64" : "fp32");
   a->tune_report = std::string(line) + "autotune sweep: " + sweep + "\n";
   if (cache_path && cache_path[0]) {

@@ -239,10 +239,17 @@ def test_split_layout_option_and_plans():
     assert sorted(list(range(10)) + first + second) == list(range(17))
     assert [p[3] for p in _layer_passes(d)] == [list(range(10)), first, second]
     a = gv.Ansatz(12, 1)
-    for bad in (-1, 3):
+    for bad in (-1, 33):
         with pytest.raises(gv.GvqeError) as e:
             gv.gvqe_ansatz_set_option(a.handle, gv.GVQE_OPT_SPLIT_PASSES, bad)
         assert e.value.code == gv._lib.GVQE_EINVAL
+    # 2 + y: the first strided pass takes y top qubits (capped below its gate count)
+    for y in (1, 3, 6):
+        _, r = runs(gv.Ansatz(30, 6, split=2 + y))
+        c1, a1, k1, gap = r[1]
+        g1 = 13 - c1
+        ye = min(y, g1 - 1)
+        assert k1 == g1 - ye and a1 + k1 + gap == 30 - ye  # low run [13, 13 + k1), top run [30 - y, 30)
 
 
 def test_debug_entry_points_refuse_in_the_regular_build():

@@ -72,9 +72,16 @@ def test_corrupt_file_reads_as_empty_and_is_rewritten(tmp_path, text):
     assert list(json.load(open(p))) == ["k2"]
 
 
+def test_split_depths_round_trip(tmp_path):
+    p = str(tmp_path / "tune.json")
+    for y in (1, 4, 8):  # GVQE_OPT_SPLIT_PASSES = 2 + y: a split pass with y top qubits
+        _lib.gvqe_tune_cache_put(p, f"k{y}", 13, 2 + y, 1.0, "")
+        assert _lib.gvqe_tune_cache_get(p, f"k{y}") == (13, 2 + y, 1.0)
+
+
 def test_put_rejects_bad_entries(tmp_path):
     p = str(tmp_path / "tune.json")
-    for tb, sp in ((9, 0), (14, 0), (12, 3), (12, -1)):
+    for tb, sp in ((9, 0), (14, 0), (12, 33), (12, -1)):
         with pytest.raises(_lib.GvqeError) as e:
             _lib.gvqe_tune_cache_put(p, "k", tb, sp, 1.0, "")
         assert e.value.code == _lib.GVQE_EINVAL
