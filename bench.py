@@ -64,6 +64,8 @@ def parse_args():
                     help="run only the non-diagonal leg (default n=28, 5,000 mixed strings, 8 vectors; "
                          "--xy-workload picks another) and print its JSON object")
     ap.add_argument("--xy-workload", default="n28_reps5_pauli5000")
+    ap.add_argument("--only-configs", action="store_true",
+                    help="run only the small named workloads (C1 n=12 FP64, C2 n=24 FP32) and print their JSON object")
     ap.add_argument("--only-cluster", action="store_true",
                     help="run only the 256-instance cluster batch leg and print its JSON object")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile plan (skip the autotuner)")
@@ -527,6 +529,72 @@ def xy_leg(steps: int, workload: str = "n28_reps5_pauli5000"):
     return out
 
 
+def configs_leg(steps: int):
+    """The two small named workloads, on the GPU:
+    C1: n = 12, reps = 2, FP64, 200 Z-strings: energies of 64 parameter vectors in one call
+        plus the FP64 parameter-shift gradient (Eq. 13) of one vector (2P + 1 = 73 energies);
+    C2: n = 24, reps = 4, FP32 adjoint E+grad of 16 vectors (2,000 Z-strings), plan tuned."""
+    import torch
+
+    import paper_2607_02749_gb300 as gv
+    from paper_2607_02749_gb300 import workloads as wl
+
+    cache = os.environ.get("GVQE_TUNE_CACHE", os.path.join("/tmp", "gvqe_tune.json"))
+    out = {}
+    # C1
+    ham, th = wl.make_workload("n12_reps2_z200", batch=64)
+    a = gv.Ansatz(12, 2)
+    h = gv.Hamiltonian.from_workload(ham)
+    t = torch.as_tensor(th, device="cuda")
+
+    def c1():
+        e = gv.energy(a, h, t, fp64=True)
+        _, g = gv.energy_grad(a, h, t[:1], fp64=True, param_shift=True)
+        return e, g
+
+    for _ in range(3):
+        c1()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        c1()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    P = a.n_params
+    out["C1_n12_reps2_z200_fp64"] = {"value": (64 + 2 * P + 1) / dt, "unit": "energy evals/s",
+                                     "ms_per_step": dt * 1e3,
+                                     "step": f"64 energies + parameter-shift gradient of one vector ({2 * P + 1} energies)",
+                                     "timing": "wall clock around synchronous calls (FP64)"}
+    a.close()
+    h.close()
+    # C2
+    ham, th = wl.make_workload("n24_reps4_z2000")
+    a = gv.Ansatz(24, 4)
+    h = gv.Hamiltonian.from_workload(ham)
+    t = torch.as_tensor(th, device="cuda")
+    tune = a.autotune(h, t, cache=cache)
+    res = {}
+    for fp64 in (False, True):
+        for _ in range(2):
+            gv.energy_grad(a, h, t, fp64=fp64)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(steps):
+            gv.energy_grad(a, h, t, fp64=fp64)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        res["fp64" if fp64 else "fp32"] = {"value": th.shape[0] / (ms / 1e3), "unit": UNIT, "ms_per_16": ms}
+    out["C2_n24_reps4_z2000"] = {"fp32_adjoint": res["fp32"], "fp64_adjoint": res["fp64"],
+                                 "plan": tune.strip().splitlines(),
+                                 "timing": "CUDA events around 16-vector gvqe_energy_grad calls"}
+    a.close()
+    h.close()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -600,6 +668,10 @@ def run_gvqe(args):
     if args.only_xy:
         if rank == 0:
             print(json.dumps({"non_diagonal": xy_leg(max(1, args.steps), args.xy_workload)}), flush=True)
+        return 0
+    if args.only_configs:
+        if rank == 0:
+            print(json.dumps({"configs": configs_leg(max(1, args.steps))}), flush=True)
         return 0
     if args.only_cluster:
         if rank == 0:
@@ -782,6 +854,7 @@ def run_gvqe(args):
         out["driver"] = driver_leg()
         out["efficient_su2"] = su2_leg(n, reps, ham, max(1, min(args.steps, 3)))
         out["non_diagonal"] = xy_leg(max(1, min(args.steps, 3)))
+        out["configs"] = configs_leg(max(1, min(args.steps, 3)))
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
