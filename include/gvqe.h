@@ -196,12 +196,13 @@ int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *con
  * gvqe_batch_set_option -- schedule option of a batch (Section IV-D, Eq. 11:
  * the paper runs its blocks concurrently; the schedule of the one persistent
  * launch is this library's own).
- *   GVQE_BATCH_OPT_WAVE_BYTES: the persistent launch takes the instances,
- *     larger first, in waves whose live bytes (three states of each instance:
- *     a pass's input, output and stored state or table) add up to at most this
- *     many bytes (0: one wave), each wave stage-major (every instance's pass s
- *     before any instance's pass s + 1), so a wave's states can stay in L2
- *     between their passes.  Default 0 (one wave).
+ *   GVQE_BATCH_OPT_WAVE_BYTES: waves whose live bytes (three states of each
+ *     instance: a pass's input, output and stored state or table) add up to at
+ *     most this many bytes (0: one wave), so a wave's states can stay in L2
+ *     between their passes.  Persistent: the instances, larger first, each
+ *     wave stage-major (every instance's pass s before any instance's pass
+ *     s + 1).  Staged: the plan groups, larger first, the groups of a wave side
+ *     by side and a wave after the previous one.  Default 0 (one wave).
  *   GVQE_BATCH_OPT_SCHEDULE: GVQE_BATCH_STAGED (default): the instances with
  *     the same plan (n, reps, entangler, strided layout) form a group whose
  *     states, partial sums and diagonal tables sit job after job, and each
@@ -225,7 +226,8 @@ int gvqe_batch_run(gvqe_batch b, const double *const *params, const uint8_t *con
  *
  * gvqe_batch_autotune -- run the batch under the persistent schedule with
  * tiles of 2^12, 2^11, 2^10 (FP64: 2^12) in one wave and 2^12 in 256 MiB
- * waves, and under the staged schedule (one warm-up run and three
+ * waves, and under the staged schedule in one wave and in 128 and 256 MiB
+ * waves (one warm-up run and three
  * timed runs under CUDA
  * events on `stream` each, with the caller's params / masks / outputs as in
  * gvqe_batch_run) and keep the fastest.  report (host, report_len bytes, or

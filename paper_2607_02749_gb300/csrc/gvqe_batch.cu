@@ -704,6 +704,11 @@ int build_grouped(gvqe_batch_s *b, int want_grad) {
     off = up256(off + sizeof(RedEntry) * std::max<size_t>(1, g.plan.dir.size()));
     groups.push_back(std::move(g));
   }
+  // larger groups first: their longer chains of passes start early
+  std::stable_sort(groups.begin(), groups.end(), [](const Group &x, const Group &y) {
+    return x.slots.size() * (size_t)x.plan.state_elems * x.plan.steps.size() >
+           y.slots.size() * (size_t)y.plan.state_elems * y.plan.steps.size();
+  });
   {
     const int rc = sc.dev.reserve(off);
     if (rc != GVQE_OK) return rc;
@@ -760,7 +765,6 @@ int build_grouped(gvqe_batch_s *b, int want_grad) {
   B.io = (const BatchIO *)(base + o_io);
   sc.smem = 0;
   sc.groups = (int)groups.size();
-  sc.waves = 1;
   const int *d_ids = (const int *)(base + o_ids);
 
   cudaStream_t cap;
@@ -769,15 +773,34 @@ int build_grouped(gvqe_batch_s *b, int want_grad) {
   cudaError_t le = cudaSuccess;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> evs;
+  // waves of groups (GVQE_BATCH_OPT_WAVE_BYTES: live bytes, three states per job):
+  // the groups of a wave run side by side, a wave starts when the previous ends
+  std::vector<size_t> wave_start = {0};
+  {
+    size_t sum = 0;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      const size_t live = (size_t)3 * groups[gi].slots.size() * (size_t)groups[gi].plan.state_elems * es;
+      if (b->wave_bytes > 0 && gi > wave_start.back() && sum + live > (size_t)b->wave_bytes) {
+        wave_start.push_back(gi);
+        sum = 0;
+      }
+      sum += live;
+    }
+    wave_start.push_back(groups.size());
+  }
+  sc.waves = (int)wave_start.size() - 1;
   if (e == cudaSuccess) {
     cudaEvent_t fork = nullptr;
-    le = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    if (le == cudaSuccess) {
-      evs.push_back(fork);
-      le = cudaEventRecord(fork, cap);
-    }
     size_t first = 0;
     for (size_t gi = 0; gi < groups.size() && le == cudaSuccess; ++gi) {
+      if (std::find(wave_start.begin(), wave_start.end(), gi) != wave_start.end()) {
+        fork = nullptr;  // a new wave forks from the capture stream after the last one joined
+        le = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (le != cudaSuccess) break;
+        evs.push_back(fork);
+        le = cudaEventRecord(fork, cap);
+        if (le != cudaSuccess) break;
+      }
       const Group &g = groups[gi];
       const int J = (int)g.slots.size();
       const size_t S = (size_t)g.plan.state_elems;
@@ -979,7 +1002,8 @@ int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t
     cands.push_back({GVQE_BATCH_PERSISTENT, tb, 0});
   }
   cands.push_back({GVQE_BATCH_PERSISTENT, 12, 256ll << 20});
-  cands.push_back({GVQE_BATCH_STAGED, 12, 0});  // the regular plans' tiles (2^13 FP32, 2^12 FP64)
+  for (long long wb : {0ll, 128ll << 20, 256ll << 20})  // the regular plans' tiles (2^13 FP32, 2^12 FP64)
+    cands.push_back({GVQE_BATCH_STAGED, 12, wb});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   GB_CUDA(cudaEventCreate(&e0));
   GB_CUDA(cudaEventCreate(&e1));
@@ -1007,8 +1031,9 @@ int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t
     const int g = grads ? 1 : 0;
     char line[200];
     if (cd.sched == GVQE_BATCH_STAGED)
-      snprintf(line, sizeof(line), "%sstaged (%d plan groups, %zu of %zu instances in it): %.3f ms",
-               sweep.empty() ? "" : "; ", b->sched[g].groups, b->pidx.size(), b->a.size(), per);
+      snprintf(line, sizeof(line), "%sstaged wave=%lldMiB (%d plan groups in %d waves, %zu of %zu instances in it): %.3f ms",
+               sweep.empty() ? "" : "; ", cd.wb >> 20, b->sched[g].groups, b->sched[g].waves, b->pidx.size(),
+               b->a.size(), per);
     else
       snprintf(line, sizeof(line), "%spersistent tiles=2^%d wave=%lldMiB (%d waves, %zu of %zu instances in it): %.3f ms",
                sweep.empty() ? "" : "; ", cd.tb, cd.wb >> 20, b->sched[g].waves, b->pidx.size(), b->a.size(), per);
@@ -1032,8 +1057,9 @@ int gvqe_batch_autotune(gvqe_batch b, const double *const *params, const uint8_t
   if (rc != GVQE_OK) return rc;
   char line[200];
   if (best.sched == GVQE_BATCH_STAGED)
-    snprintf(line, sizeof(line), "batch autotune: staged schedule (plan groups, regular pass kernels), %.3f ms per run\n",
-             best_ms);
+    snprintf(line, sizeof(line),
+             "batch autotune: staged schedule (plan groups, regular pass kernels), wave bytes %lld MiB, %.3f ms per run\n",
+             best.wb >> 20, best_ms);
   else
     snprintf(line, sizeof(line),
              "batch autotune: persistent schedule, tiles 2^%d, wave bytes %lld MiB (%s), %.3f ms per run\n", best.tb,
