@@ -277,7 +277,7 @@ int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, 
  * and Eq. 13.  Every distinct plan among tile bits 10 .. 13 (FP64: 10 .. 12)
  * and the strided layouts (one run of qubits per pass, or a low and a top run
  * of y = 1 .. 8 top qubits) runs the requested evaluation once to warm up and
- * three times under
+ * then once (three times when a call takes under 50 ms, averaged) under
  * CUDA events on `stream`; the fastest becomes the ansatz's plan in that
  * precision (the other precision keeps its own; setting GVQE_OPT_TILE_BITS or
  * GVQE_OPT_SPLIT_PASSES later replaces both).  Candidates that do not fit in
