@@ -530,8 +530,8 @@ def xy_leg(steps: int, workload: str = "n28_reps5_pauli5000"):
     names = {0: "k_fwd", 1: "k_bwd", 2: "k_grad_l0", 3: "k_lambda_xy", 4: "k_wht"}
     import re
 
-    m = re.search(r"tile_bits=(\d+)", tune)
-    tb_sel = int(m.group(1)) if m else 13
+    m = re.search(r"xy_tile_bits=(\d+)", tune) or re.search(r"tile_bits=(\d+)", tune)
+    tb_sel = int(m.group(1)) if m else 13  # the X-mask pass's tile bits
     d_all, d_hi = xy_masks(ham, tb_sel)
     S = 4 * 2 ** n
     T = 8 * 2 ** n

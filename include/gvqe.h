@@ -77,6 +77,9 @@ extern "C" {
                                    spans more 2 MiB pages than needed; results are the same up to the order of
                                    FP32/FP64 additions. */
 
+#define GVQE_OPT_XY_TILE_BITS 4 /* log2 amplitudes per tile of the X-mask pass (strings with X/Y letters, RY
+                                   layers), 10..13 (FP64: at most 12), 0 = those of the first pass */
+
 /* gate sets of a rotation layer (Eq. 8).
  * RY:    RY on every qubit; P = n (reps+1), theta[r*n + q]; real amplitudes.
  * RY_RZ: the full EfficientSU2 layer, RY on every qubit, then RZ on every
@@ -280,8 +283,10 @@ int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, 
  * then once (three times when a call takes under 50 ms, averaged) under
  * CUDA events on `stream`; the fastest becomes the ansatz's plan in that
  * precision (the other precision keeps its own; setting GVQE_OPT_TILE_BITS or
- * GVQE_OPT_SPLIT_PASSES later replaces both).  Candidates that do not fit in
- * device memory are skipped.  Results of the tuned plan equal those of any
+ * GVQE_OPT_SPLIT_PASSES later replaces both).  With X/Y strings (RY layers),
+ * the X-mask pass's own tile size (GVQE_OPT_XY_TILE_BITS) is swept first, on
+ * the default plan, and the plans are then timed with the fastest.
+ * Candidates that do not fit in device memory are skipped.  Results of the tuned plan equal those of any
  * other plan up to the order of FP32/FP64 additions.
  *   a, h:       handles with equal n.
  *   params:     device, batch x P doubles (the evaluation that is timed).

@@ -567,7 +567,7 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
 
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0,
-                bool state_only, int ent, int gates, int split) {
+                bool state_only, int ent, int gates, int split, int xy_tb) {
   if (gates == 2) return build_plan_su2(n, reps, prec, tile_bits, want_grad, diag, ent, state_only, split);
   Plan pl;
   pl.n = n;
@@ -697,10 +697,12 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
   if (!diag) {
     PassStep st;
     st.A = base_args(K_LAMBDA_XY);
-    st.A.tb = tbA;
-    st.A.c = tbA;
-    st.A.a = tbA;
-    st.A.tiles = tiles_of(n, tbA);
+    // the X-mask pass may take its own tile size (fewer qubits than n: the whole register)
+    const int tbx = xy_tb > 0 ? std::min(std::min(xy_tb, max_tile_bits(prec)), n) : tbA;
+    st.A.tb = tbx;
+    st.A.c = tbx;
+    st.A.a = tbx;
+    st.A.tiles = tiles_of(n, tbx);
     st.A.load_mode = LD_PLAIN;
     st.A.flags = F_ENERGY | (want_grad ? F_WRITE_LAMBDA : 0);
     st.in = last_state;
@@ -1065,7 +1067,7 @@ Plan *gvqe::get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool
   const int tb = eff_tile_bits(a, prec);
   if (it != a->plans.end() && it->second.tile_bits == tb) return &it->second;
   Plan pl = build_plan(a->n, a->reps, prec, tb, want_grad, diag, false, state_only, a->ent, a->gates,
-                       eff_split(a, prec));
+                       eff_split(a, prec), eff_xy_tb(a, prec));
   pl.tile_bits = tb;
   a->plans[key] = std::move(pl);
   return &a->plans[key];
@@ -1369,6 +1371,7 @@ int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
     a->tile_bits = value;
     a->tuned_tb[0] = a->tuned_tb[1] = 0;  // an explicit choice replaces a tuned one
     a->tuned_split[0] = a->tuned_split[1] = -1;
+    a->tuned_xy_tb[0] = a->tuned_xy_tb[1] = 0;
     a->tune_report.clear();
     a->plans.clear();
     return GVQE_OK;
@@ -1379,6 +1382,16 @@ int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
     a->split = value;
     a->tuned_tb[0] = a->tuned_tb[1] = 0;
     a->tuned_split[0] = a->tuned_split[1] = -1;
+    a->tuned_xy_tb[0] = a->tuned_xy_tb[1] = 0;
+    a->tune_report.clear();
+    a->plans.clear();
+    return GVQE_OK;
+  }
+  if (option == GVQE_OPT_XY_TILE_BITS) {
+    if (value != 0 && (value < 10 || value > 13))
+      return fail(GVQE_EINVAL, "X-mask tile bits %d outside [10, 13] (0 = those of the first pass)", value);
+    a->xy_tb = value;
+    a->tuned_xy_tb[0] = a->tuned_xy_tb[1] = 0;
     a->tune_report.clear();
     a->plans.clear();
     return GVQE_OK;

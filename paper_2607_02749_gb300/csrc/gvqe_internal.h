@@ -73,8 +73,9 @@ void count_launches(int k);
 // state_only: the forward passes alone, the final state kept (Plan::final_buf).
 // gates: 1 = RY layers (real amplitudes), 2 = full EfficientSU2 layers, RY then
 // RZ on every qubit (complex amplitudes; diagonal H, energy and gradient only).
+// xy_tb: tile bits of the X-mask pass (0: those of the layer's first pass).
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false,
-                bool state_only = false, int ent = ENT_LINEAR, int gates = 1, int split = SPLIT_AUTO);
+                bool state_only = false, int ent = ENT_LINEAR, int gates = 1, int split = SPLIT_AUTO, int xy_tb = 0);
 std::string describe_plan(const Plan &pl);
 // One tile-pass launch, counted by gvqe_launch_count and timed by the event
 // profiler when it is on.
@@ -125,6 +126,8 @@ struct gvqe_ansatz_s {
   // takes the place of tile_bits / split for that precision until an option is set
   int tuned_tb[2] = {0, 0};
   int tuned_split[2] = {-1, -1};
+  int xy_tb = 0;                 // GVQE_OPT_XY_TILE_BITS (0: the first pass's tile bits)
+  int tuned_xy_tb[2] = {0, 0};   // per precision, chosen by gvqe_autotune (0: none)
   std::map<int, gvqe::Plan> plans;
   gvqe::DevBuf ws, aux, shift, ro, tune;
   std::string tune_report;  // the last gvqe_autotune sweep and its choice (empty: not tuned)
@@ -137,6 +140,7 @@ namespace gvqe {
 // The tile bits and strided layout an ansatz's plans take in one precision.
 inline int eff_tile_bits(const gvqe_ansatz_s *a, int prec) { return a->tuned_tb[prec] ? a->tuned_tb[prec] : a->tile_bits; }
 inline int eff_split(const gvqe_ansatz_s *a, int prec) { return a->tuned_split[prec] >= 0 ? a->tuned_split[prec] : a->split; }
+inline int eff_xy_tb(const gvqe_ansatz_s *a, int prec) { return a->tuned_xy_tb[prec] ? a->tuned_xy_tb[prec] : a->xy_tb; }
 // The ansatz's cached plan for (precision, gradient or not, diagonal H or not,
 // state only); it and its host-side reduction directory live until the
 // ansatz is destroyed or one of its options changes.

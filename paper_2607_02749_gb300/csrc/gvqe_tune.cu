@@ -39,6 +39,7 @@ namespace {
 struct TuneEntry {
   int tile_bits = 0;
   int split = 0;
+  int xy_tb = 0;  // X-mask pass tile bits (0: the first pass's); optional in the file
   double ms = 0.0;
   std::string sweep;
 };
@@ -123,6 +124,8 @@ bool parse_entry(JsonIn &in, TuneEntry *t) {
         have_split = true;
       } else if (k == "ms") {
         t->ms = v;
+      } else if (k == "xy_tile_bits") {
+        t->xy_tb = (int)v;
       }
     }
     if (in.eat(',')) continue;
@@ -178,7 +181,9 @@ std::string write_cache(const std::map<std::string, TuneEntry> &m) {
     first = false;
     snprintf(num, sizeof(num), "%.6g", kv.second.ms);
     o += "  " + json_str(kv.first) + ": {\"tile_bits\": " + std::to_string(kv.second.tile_bits) +
-         ", \"split\": " + std::to_string(kv.second.split) + ", \"ms\": " + num +
+         ", \"split\": " + std::to_string(kv.second.split) +
+         (kv.second.xy_tb ? ", \"xy_tile_bits\": " + std::to_string(kv.second.xy_tb) : std::string()) +
+         ", \"ms\": " + num +
          ", \"sweep\": " + json_str(kv.second.sweep) + "}";
   }
   return o + "\n}\n";
@@ -338,10 +343,12 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
         t.split <= SPLIT_ALWAYS + GVQE_MAX_QUBITS) {
       a->tuned_tb[prec] = t.tile_bits;
       a->tuned_split[prec] = t.split;
+      a->tuned_xy_tb[prec] = (t.xy_tb >= 10 && t.xy_tb <= tb_max) ? t.xy_tb : 0;
       a->plans.clear();
       char line[256];
-      snprintf(line, sizeof(line), "autotune: cached (%s): tile_bits=%d strided=%s %.3f ms\n", cache_path,
-               t.tile_bits, split_name(t.split).c_str(), t.ms);
+      snprintf(line, sizeof(line), "autotune: cached (%s): tile_bits=%d strided=%s%s %.3f ms\n", cache_path,
+               t.tile_bits, split_name(t.split).c_str(),
+               a->tuned_xy_tb[prec] ? (" xy_tile_bits=" + std::to_string(a->tuned_xy_tb[prec])).c_str() : "", t.ms);
       a->tune_report = std::string(line) + "autotune sweep (cached): " + t.sweep + "\n";
       put_report(a->tune_report, report, report_len);
       return GVQE_OK;
@@ -373,84 +380,116 @@ int gvqe_autotune(gvqe_ansatz a, gvqe_hamiltonian h, const double *params, int b
   EventPair ev;
   GT_CUDA(cudaEventCreate(&ev.a));
   GT_CUDA(cudaEventCreate(&ev.b));
-  const int keep_tb = a->tuned_tb[prec], keep_split = a->tuned_split[prec];
+  const int keep_tb = a->tuned_tb[prec], keep_split = a->tuned_split[prec], keep_xy = a->tuned_xy_tb[prec];
   auto restore = [&]() {
     a->tuned_tb[prec] = keep_tb;
     a->tuned_split[prec] = keep_split;
+    a->tuned_xy_tb[prec] = keep_xy;
     a->plans.clear();
   };
-  std::string sweep;
-  int best = -1;
-  double best_ms = 0.0;
+  // One candidate: a warm-up call (plan, tables, workspaces), then one timed call,
+  // two more when a call is short (under 50 ms), averaged.  *per < 0: no memory.
   const int timed = 3;
-  for (size_t c = 0; c < cands.size(); ++c) {
-    a->tuned_tb[prec] = cands[c].tb;
-    a->tuned_split[prec] = cands[c].split;
+  auto time_candidate = [&](int tb, int sp, int xtb, double *per) -> int {
+    a->tuned_tb[prec] = tb;
+    a->tuned_split[prec] = sp;
+    a->tuned_xy_tb[prec] = xtb;
     a->plans.clear();
-    char line[160];
-    // warm-up call: plan, tables and workspaces
-    rc = energy_impl(a, h, params, nullptr, batch, E, G, prec, s);
-    if (rc == GVQE_OK) {
-      cudaError_t e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) {
-        restore();
-        return fail(GVQE_ECUDA, "autotune candidate tile_bits=%d: %s", cands[c].tb, cudaGetErrorString(e));
-      }
+    int r = energy_impl(a, h, params, nullptr, batch, E, G, prec, s);
+    if (r == GVQE_ENOMEM) {
+      *per = -1.0;
+      return GVQE_OK;
     }
-    if (rc == GVQE_ENOMEM) {
-      snprintf(line, sizeof(line), "%stb=%d/%s: no memory", sweep.empty() ? "" : "; ", cands[c].tb,
-               split_name(cands[c].split).c_str());
-      sweep += line;
-      continue;
-    }
-    if (rc != GVQE_OK) {
-      restore();
-      return rc;
-    }
-    // one timed call; two more when a call is short (under 50 ms), averaged
+    if (r != GVQE_OK) return r;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(GVQE_ECUDA, "autotune candidate tile_bits=%d: %s", tb, cudaGetErrorString(e));
     double total_ms = 0.0;
     int calls = 0;
     while (calls < timed) {
       GT_CUDA(cudaEventRecord(ev.a, s));
-      rc = energy_impl(a, h, params, nullptr, batch, E, G, prec, s);
+      r = energy_impl(a, h, params, nullptr, batch, E, G, prec, s);
       GT_CUDA(cudaEventRecord(ev.b, s));
       GT_CUDA(cudaEventSynchronize(ev.b));
-      if (rc != GVQE_OK) {
-        restore();
-        return rc;
-      }
+      if (r != GVQE_OK) return r;
       float ms = 0.f;
       GT_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
       total_ms += ms;
       ++calls;
       if (calls == 1 && ms >= 50.f) break;
     }
-    const double per = total_ms / calls;
-    snprintf(line, sizeof(line), "%stb=%d/%s: %.3f ms", sweep.empty() ? "" : "; ", cands[c].tb,
-             split_name(cands[c].split).c_str(), per);
+    *per = total_ms / calls;
+    return GVQE_OK;
+  };
+  std::string sweep;
+  // With X/Y strings (RY layers) the X-mask pass's own tile size comes first, on
+  // the default plan (its best size hardly depends on the RY passes' layout);
+  // the plans are then timed with it.
+  const bool cplx = a->gates == 2;
+  const bool diag = cplx ? h->cgm.empty() : h->gm.empty();
+  int best_xy = 0;
+  if (!diag && !cplx) {
+    double xy_ms = -1.0;
+    for (int xtb = std::min(tb_max, a->n); xtb >= 10; --xtb) {
+      double per = 0.0;
+      rc = time_candidate(tb_max, SPLIT_AUTO, xtb, &per);
+      if (rc != GVQE_OK) {
+        restore();
+        return rc;
+      }
+      char line[160];
+      snprintf(line, sizeof(line), "%sX-mask tiles 2^%d: %s%.3f ms", sweep.empty() ? "" : "; ", xtb,
+               per < 0 ? "no memory " : "", per < 0 ? 0.0 : per);
+      sweep += line;
+      if (per >= 0 && (xy_ms < 0 || per < xy_ms)) {
+        xy_ms = per;
+        best_xy = xtb;
+      }
+    }
+  }
+  int best = -1;
+  double best_ms = 0.0;
+  for (size_t c = 0; c < cands.size(); ++c) {
+    double per = 0.0;
+    rc = time_candidate(cands[c].tb, cands[c].split, best_xy, &per);
+    if (rc != GVQE_OK) {
+      restore();
+      return rc;
+    }
+    char line[160];
+    if (per < 0)
+      snprintf(line, sizeof(line), "%stb=%d/%s: no memory", sweep.empty() ? "" : "; ", cands[c].tb,
+               split_name(cands[c].split).c_str());
+    else
+      snprintf(line, sizeof(line), "%stb=%d/%s: %.3f ms", sweep.empty() ? "" : "; ", cands[c].tb,
+               split_name(cands[c].split).c_str(), per);
     sweep += line;
-    if (best < 0 || per < best_ms) {
+    if (per >= 0 && (best < 0 || per < best_ms)) {
       best = (int)c;
       best_ms = per;
     }
   }
-  a->ws.release();  // the chosen plan sizes its own workspace on the next call
   if (best < 0) {
+    a->ws.release();
     restore();
     return fail(GVQE_ENOMEM, "autotune: no candidate plan fits in device memory (%s)", sweep.c_str());
   }
+  a->ws.release();  // the chosen plan sizes its own workspace on the next call
   a->tuned_tb[prec] = cands[best].tb;
   a->tuned_split[prec] = cands[best].split;
+  a->tuned_xy_tb[prec] = best_xy;
   a->plans.clear();
   char line[256];
-  snprintf(line, sizeof(line), "autotune: measured: tile_bits=%d strided=%s %.3f ms per call (batch %d, %s, %s)\n",
-           cands[best].tb, split_name(cands[best].split).c_str(), best_ms, batch, want_grad ? "energy+gradient" : "energy",
-           prec ? "fp64" : "fp32");
+  snprintf(line, sizeof(line),
+           "autotune: measured: tile_bits=%d strided=%s%s %.3f ms per call (batch %d, %s, %s)\n", cands[best].tb,
+           split_name(cands[best].split).c_str(),
+           best_xy ? (" xy_tile_bits=" + std::to_string(best_xy)).c_str() : "", best_ms, batch,
+           want_grad ? "energy+gradient" : "energy", prec ? "fp64" : "fp32");
   a->tune_report = std::string(line) + "autotune sweep: " + sweep + "\n";
   if (cache_path && cache_path[0]) {
     TuneEntry t;
     t.tile_bits = cands[best].tb;
     t.split = cands[best].split;
+    t.xy_tb = best_xy;
     t.ms = best_ms;
     t.sweep = sweep;
     rc = cache_store(cache_path, key, t);

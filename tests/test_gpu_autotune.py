@@ -77,6 +77,7 @@ def test_energy_only_tuning_with_xy_strings(tmp_path):
     a = gv.Ansatz(n, reps)
     rep = a.autotune(h, _dev(th), energy_only=True, cache=str(tmp_path / "t.json"))
     assert "(batch 1, energy, fp32)" in rep, rep
+    assert "X-mask tiles 2^" in rep, rep  # the X-mask pass's own tile size was swept too
     e = gv.energy(a, h, _dev(th)).item()
     e_ref = oracle.energy(n, reps, th[0], ham.strings, ham.coeffs)
     assert abs(e - e_ref) <= 2e-5 * ham.abs_sum()

@@ -119,6 +119,26 @@ def test_energy_and_gradient_with_xy_strings(n, reps, tb, fp64):
     _check(e.cpu().numpy(), g.cpu().numpy(), e_ref, g_ref, scale, fp64, "energy_grad xy")
 
 
+@pytest.mark.parametrize("xtb", [10, 11, 12, 13])
+@pytest.mark.parametrize("fp64", [True, False])
+def test_xy_pass_with_its_own_tile_size(xtb, fp64):
+    """GVQE_OPT_XY_TILE_BITS: the X-mask pass on 2^10..2^13-amplitude tiles (FP64
+    clamps 13 to 12) while the RY passes keep theirs; against the oracle."""
+    n, reps = 15, 2
+    ham = wl.pauli_hamiltonian(n, 8 * n, seed=21)
+    th = wl.thetas(n, reps, 2, seed=22)
+    e_ref, g_ref = _oracle_eg(n, reps, th, ham)
+    a = gv.Ansatz(n, reps)
+    gv.gvqe_ansatz_set_option(a.handle, gv._lib.GVQE_OPT_XY_TILE_BITS, xtb)
+    h = gv.Hamiltonian.from_workload(ham)
+    t = _dev(th)
+    e_only = gv.energy(a, h, t, fp64=fp64).cpu().numpy()
+    e, g = gv.energy_grad(a, h, t, fp64=fp64)
+    scale = ham.abs_sum()
+    _check(e_only, None, e_ref, None, scale, fp64, f"xy tiles {xtb} energy")
+    _check(e.cpu().numpy(), g.cpu().numpy(), e_ref, g_ref, scale, fp64, f"xy tiles {xtb} energy_grad")
+
+
 @pytest.mark.parametrize("n,reps,tb", [(8, 2, 0), (12, 3, 0), (16, 2, 10)])
 def test_masks_zero_inactive_and_keep_active(n, reps, tb):
     ham = wl.z_hamiltonian(n, 50, seed=2)
