@@ -179,21 +179,6 @@ struct Reg32<float> {
       return r.x + r.y;
     }
   }
-  // complex path (a pair is one amplitude): sum over amplitude pairs along
-  // register bit JB >= 1 of Im(conj(lam0) psi1) + Im(conj(lam1) psi0) = Im <lam|X|psi>
-  template <int JB>
-  __device__ __forceinline__ float gradx(const Reg32 &lam) const {
-    static_assert(JB >= 1, "the channel bit carries no gate");
-    constexpr int B = 1 << (JB - 1);
-    float acc = 0.f;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      if (m & B) continue;
-      const float2 l0 = lam.v[m], l1 = lam.v[m | B], p0 = v[m], p1 = v[m | B];
-      acc += l0.x * p1.y - l0.y * p1.x + l1.x * p0.y - l1.y * p0.x;
-    }
-    return acc;
-  }
 };
 
 template <>
@@ -233,18 +218,6 @@ struct Reg32<double> {
     for (int k = 0; k < 32; ++k) {
       if (k & (1 << JB)) continue;
       acc += lam.v[k | (1 << JB)] * v[k] - lam.v[k] * v[k | (1 << JB)];
-    }
-    return acc;
-  }
-  template <int JB>
-  __device__ __forceinline__ double gradx(const Reg32 &lam) const {
-    static_assert(JB >= 1, "the channel bit carries no gate");
-    constexpr int J = 1 << JB;
-    double acc = 0.0;
-#pragma unroll
-    for (int k = 0; k < 32; k += 2) {
-      if (k & J) continue;
-      acc += lam.v[k] * v[k + J + 1] - lam.v[k + 1] * v[k + J] + lam.v[k + J] * v[k + 1] - lam.v[k + J + 1] * v[k];
     }
     return acc;
   }
@@ -351,23 +324,17 @@ __device__ __forceinline__ void round_gates(Reg32<T> &r, const GateTab<T2> &gt, 
 // reduced over the warp with a transposed butterfly (each exchange halves the
 // values a lane carries), then lane (j << 2) holds value j and stores it.
 // X5: also the gate of tile bit 5 on register bit 1 (round H), in slot 5.
-// CPLX: the complex path's RY gradient cos(tz) Im<lam|Y|psi> - sin(tz) Im<lam|X|psi>
-// (the RZ after the RY turns Y into cos Y - sin X), zf[tile bit] = (cos tz, sin tz).
-template <int NB, int RO = 0, bool X5 = false, bool CPLX = false, typename T, typename T2 = typename V2<T>::type>
+template <int NB, int RO = 0, bool X5 = false, typename T>
 __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> &lam, uint32_t gmask, int tbit0,
-                                            double *wred, int lane, const T2 *zf = nullptr) {
+                                            double *wred, int lane) {
   T v[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = T(0);
-  if (X5 && ((gmask >> 5) & 1u)) {
-    v[5] = psi.template grad<1>(lam);
-    if constexpr (CPLX) v[5] = zf[5].x * v[5] - zf[5].y * psi.template gradx<1>(lam);
-  }
-#define GVQE_GV(J)                                                                            \
-  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) {                                              \
-    constexpr int JB_ = (J + RO < 5 ? J + RO : 4);                                            \
-    v[J] = psi.template grad<JB_>(lam);                                                       \
-    if constexpr (CPLX && JB_ > 0) v[J] = zf[tbit0 + J].x * v[J] - zf[tbit0 + J].y * psi.template gradx<JB_>(lam); \
+  if (X5 && ((gmask >> 5) & 1u)) v[5] = psi.template grad<1>(lam);
+#define GVQE_GV(J)                                          \
+  if (NB > J && ((gmask >> (tbit0 + J)) & 1u)) {            \
+    constexpr int JB_ = (J + RO < 5 ? J + RO : 4);          \
+    v[J] = psi.template grad<JB_>(lam);                     \
   }
   GVQE_GV(0)
   GVQE_GV(1)
@@ -659,8 +626,10 @@ __device__ __forceinline__ void load_gate_coeffs(const PassArgs &A, const T2 *cs
 // and the CX permutations act alike on both channels; RZ(theta) on qubit q
 // multiplies psi(x) by exp(-i theta/2) when x_q = 0 and exp(+i theta/2) when
 // x_q = 1.  A pass applies its qubits' RZ after their RY (they commute with the
-// other qubits' gates) as one phase per amplitude in round H: the product of
-// the thread's tile bits' factors (pthr) and of the register bits' (preg).
+// other qubits' gates) as one phase per amplitude: the product of the thread's
+// tile bits' factors and of the register bits' factors.  The forward pass applies
+// it in round H (preg), the backward pass takes it off psi and lambda in round L
+// (pregL), before the RY gradients and RY(-theta).
 
 template <typename T2>
 __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
@@ -678,8 +647,8 @@ __device__ __forceinline__ T2 cconj(T2 a) {
 template <typename T2, int TB>
 struct SU2Tab {
   T2 zh[16];    // per tile bit: (cos, sin) of theta_z / 2, (1, 0) without an RZ
-  T2 zf[16];    // per tile bit: (cos, sin) of theta_z (the RY gradient is cos Y - sin X)
   T2 preg[16];  // round H: the phase of register pattern m
+  T2 pregL[16]; // round L: the phase of register pattern m (tile bits 6..9)
   // threads 0..15; the caller synchronises before use
   __device__ __forceinline__ void build(const PassArgs &A, const T2 *cs, int tid) {
     if (tid >= 16) return;
@@ -695,10 +664,6 @@ struct SU2Tab {
     };
     const T2 h = half(tid);
     zh[tid] = h;
-    T2 f;
-    f.x = h.x * h.x - h.y * h.y;
-    f.y = 2 * h.x * h.y;
-    zf[tid] = f;
     T2 p;
     p.x = 1;
     p.y = 0;
@@ -709,6 +674,31 @@ struct SU2Tab {
       p = cmul(p, e);
     }
     preg[tid] = p;
+    T2 q;
+    q.x = 1;
+    q.y = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // round L: pair-index bit j holds tile bit 6 + j
+      T2 e = half(6 + j);
+      if (!((tid >> j) & 1)) e.y = -e.y;
+      q = cmul(q, e);
+    }
+    pregL[tid] = q;
+  }
+  // phase of this thread's round-L tile bits (lanes: 1..5, warps: 10..)
+  __device__ __forceinline__ T2 thread_phase_L(int lane, int w) const {
+    T2 p;
+    p.x = 1;
+    p.y = 0;
+#pragma unroll
+    for (int b = 1; b < TB; ++b) {
+      if (b >= 6 && b <= 9) continue;
+      const int bit = b <= 5 ? ((lane >> (b - 1)) & 1) : ((w >> (b - 10)) & 1);
+      T2 e = zh[b];
+      if (!bit) e.y = -e.y;
+      p = cmul(p, e);
+    }
+    return p;
   }
   // phase of this thread's round-H tile bits (those not in its registers)
   __device__ __forceinline__ T2 thread_phase(int tid) const {
@@ -1006,12 +996,8 @@ k_bwd(const PassArgs A) {
   GIdx<TB, FULL> grel;
   grel.init(0u, A, lane, w, tid);
   __syncthreads();  // gate coefficients visible
-  T2 pthr;
-  const T2 *zf = nullptr;
-  if constexpr (CPLX) {
-    pthr = zt.thread_phase(tid);
-    zf = zt.zf;
-  }
+  T2 pthrL;
+  if constexpr (CPLX) pthrL = zt.thread_phase_L(lane, w);
   for (; bx < tiles; bx += gridDim.x) {
     const uint32_t nbx = bx + gridDim.x;
     const bool more = nbx < tiles;
@@ -1036,26 +1022,39 @@ k_bwd(const PassArgs A) {
         lam.set(k, l);
         eacc += p * l;
       }
-      sts_L(sl, sb, lam);
+      if (!CPLX) sts_L(sl, sb, lam);
       eacc = warp_sum(eacc);
       if (lane == 0) ered[par][w] = (double)eacc;
     }
-    round_grads<4, 1, false, CPLX>(psi, lam, gm, 6, gred[par][w], lane, zf);
+    if constexpr (CPLX) {
+      // RZ(-theta) of every qubit of the pass on psi and lambda: both then sit
+      // between the pass's RY and RZ gates, where the RY gradients are the plain
+      // Im<lam|Y_q|psi> (the other RY gates commute with Y_q) and from where
+      // lambda continues through RY(-theta).  The RZ gradients Im<lam|Z_q|psi>
+      // are the same on either side of the common phase.
+#pragma unroll
+      for (int m = 0; m < ROUND / 2; ++m) {
+        const T2 ph = cconj(cmul(pthrL, zt.pregL[m]));
+        psi.set_pair(m, cmul(psi.pair(m), ph));
+        lam.set_pair(m, cmul(lam.pair(m), ph));
+      }
+      sts_L(sp, sb, psi);
+      sts_L(sl, sb, lam);
+    }
+    round_grads<4, 1, false>(psi, lam, gm, 6, gred[par][w], lane);
     if constexpr (CPLX) rz_grads_L(psi, lam, gm, gredz[par][w], lane, w);
-    if (init) __syncwarp();  // lambda = E psi is in shared before round M reads it
+    if (init || CPLX) __syncwarp();  // the rewritten lambda (and psi) are in shared before round M reads them
     // round M (gradients only)
     if (gm & 0x1Fu) {
       lds_M(sp, tid, psi);
       lds_M(sl, tid, lam);
-      round_grads<5, 0, false, CPLX>(psi, lam, gm, 0, gred[par][w], lane, zf);
+      round_grads<5, 0, false>(psi, lam, gm, 0, gred[par][w], lane);
     }
-    // round H: gradients, then RY(-theta) on lambda (complex path: first
-    // RZ(-theta) on every qubit of the pass, as one phase).  Its layout crosses warps.
+    // round H: gradients, then RY(-theta) on lambda.  Its layout crosses warps.
     __syncthreads();
     lds_H<TB>(sp, sb, psi);
     lds_H<TB>(sl, sb, lam);
-    round_grads<H, 2, true, CPLX>(psi, lam, gm, 10, gred[par][w], lane, zf);
-    if constexpr (CPLX) apply_su2_phase<true>(lam, zt, pthr);
+    round_grads<H, 2, true>(psi, lam, gm, 10, gred[par][w], lane);
     round_gates<H, false, true, 2>(lam, gt, gm, 10, true);
     round_gates<1, false, true, 1>(lam, gt, gm, 5, true);
     sts_H<TB>(sl, sb, lam);  // the places this thread read

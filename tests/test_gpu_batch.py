@@ -229,3 +229,32 @@ def test_staged_schedule_takes_every_diagonal_instance(fp64):
         else:
             assert abs(e[k] - e_ref) <= 2e-5 * scale
             assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+
+
+def test_staged_schedule_edge_instances():
+    """Degenerate instances in one staged batch: n = 1 and 2, reps = 0, n at a
+    tile boundary, all-inactive and single-parameter masks; each equals its
+    single call bit for bit."""
+    specs = [(1, 0), (1, 2), (2, 1), (9, 0), (13, 0), (13, 2), (14, 1), (10, 3)]
+    ans, hams, params, masks = [], [], [], []
+    for k, (n, reps) in enumerate(specs):
+        ham = wl.z_hamiltonian(n, 5 * n + 3, seed=50 + k)
+        ans.append(gv.Ansatz(n, reps))
+        hams.append(gv.Hamiltonian.from_workload(ham))
+        params.append(_dev(wl.thetas(n, reps, 1, seed=60 + k)[0]))
+        P = n * (reps + 1)
+        m = np.ones(P, dtype=np.uint8)
+        if k == 2:
+            m[:] = 0  # nothing active
+        if k == 5:
+            m[:] = 0
+            m[P - 1] = 1  # only the last parameter
+        masks.append(_dev(m, torch.uint8))
+    b = gv.Batch(ans, hams)
+    grads = [torch.full_like(p, float("nan")) for p in params]
+    e = b.run(params, masks=masks, grads=grads).cpu().numpy()
+    for k in range(len(specs)):
+        e1, g1 = gv.energy_grad(ans[k], hams[k], params[k], mask=masks[k])
+        assert e[k] == e1.item(), specs[k]
+        assert np.array_equal(grads[k].cpu().numpy(), g1.cpu().numpy()[0]), specs[k]
+    assert np.all(grads[2].cpu().numpy() == 0.0)
