@@ -324,9 +324,13 @@ __device__ __forceinline__ void round_gates(Reg32<T> &r, const GateTab<T2> &gt, 
 // reduced over the warp with a transposed butterfly (each exchange halves the
 // values a lane carries), then lane (j << 2) holds value j and stores it.
 // X5: also the gate of tile bit 5 on register bit 1 (round H), in slot 5.
+// The warp partial is stored in the working precision T; the tile epilogue
+// converts it to FP64 (exactly) and sums the warps in FP64, so the narrow FP64
+// pipe sees one warp's adds per tile instead of a conversion in every warp
+// after every round.
 template <int NB, int RO = 0, bool X5 = false, typename T>
 __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> &lam, uint32_t gmask, int tbit0,
-                                            double *wred, int lane) {
+                                            T *wred, int lane) {
   T v[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = T(0);
@@ -367,9 +371,9 @@ __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> 
   if ((lane & 3) == 0) {
     const int j = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     if (j < NB && ((gmask >> (tbit0 + j)) & 1u))
-      wred[tbit0 + j] = (double)r;
+      wred[tbit0 + j] = r;
     else if (X5 && j == 5 && ((gmask >> 5) & 1u))
-      wred[5] = (double)r;
+      wred[5] = r;
   }
 }
 
@@ -380,7 +384,7 @@ __device__ __forceinline__ void round_grads(const Reg32<T> &psi, const Reg32<T> 
 // total.  The 16 per-tile-bit values go through one transposed warp butterfly;
 // wredz[tile bit] receives the warp's partial.
 template <typename T>
-__device__ __forceinline__ void rz_grads_L(const Reg32<T> &psi, const Reg32<T> &lam, uint32_t gmask, double *wredz,
+__device__ __forceinline__ void rz_grads_L(const Reg32<T> &psi, const Reg32<T> &lam, uint32_t gmask, T *wredz,
                                            int lane, int w) {
   T tot = T(0), d[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
@@ -420,9 +424,7 @@ __device__ __forceinline__ void rz_grads_L(const Reg32<T> &psi, const Reg32<T> &
   if ((lane & 1) == 0) {
     const int b = (b4 ? 8 : 0) + (b3 ? 4 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0);
     if ((gmask >> b) & 1u) {
-      double g = (double)r;
-      if (b >= 10 && ((w >> (b - 10)) & 1)) g = -g;
-      wredz[b] = g;
+      wredz[b] = (b >= 10 && ((w >> (b - 10)) & 1)) ? -r : r;
     }
   }
 }
@@ -927,9 +929,9 @@ k_bwd(const PassArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *buf = reinterpret_cast<T *>(smem_raw);  // psi tile, lambda tile
   __shared__ GateTab<T2> gt;
-  __shared__ double gred[2][NW][16];  // by tile parity: a warp may start the next
-  __shared__ double ered[2][NW];      // tile while warp 0 still sums this one
-  __shared__ double gredz[CPLX ? 2 : 1][CPLX ? NW : 1][16];  // complex path: RZ partials
+  __shared__ T gred[2][NW][16];   // by tile parity: a warp may start the next
+  __shared__ double ered[2][NW];  // tile while warp 0 still sums this one
+  __shared__ T gredz[CPLX ? 2 : 1][CPLX ? NW : 1][16];  // complex path: RZ partials
   __shared__ SU2Tab<T2, TB> zt;
 
   const int job = blockIdx.y;
@@ -1109,12 +1111,12 @@ k_bwd(const PassArgs A) {
     if (tid < TB && ((gm >> tid) & 1u)) {
       double g = 0.0;
 #pragma unroll
-      for (int ww = 0; ww < NW; ++ww) g += gred[par][ww][tid];
+      for (int ww = 0; ww < NW; ++ww) g += (double)gred[par][ww][tid];
       part[(size_t)tid * tiles + t] = g;
       if constexpr (CPLX) {  // RZ rows follow the TB RY rows
         double gz = 0.0;
 #pragma unroll
-        for (int ww = 0; ww < NW; ++ww) gz += gredz[par][ww][tid];
+        for (int ww = 0; ww < NW; ++ww) gz += (double)gredz[par][ww][tid];
         part[(size_t)(TB + tid) * tiles + t] = gz;
       }
     }
@@ -1146,7 +1148,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   T *sp = reinterpret_cast<T *>(smem_raw);
   T *sl = sp + (1 << TB);
   __shared__ GateTab<T2> gt;
-  __shared__ double gred[NW][16];
+  __shared__ T gred[NW][16];
   __shared__ double ered[NW];
 
   if (A.minlayer != nullptr && !(A.flags & F_ENERGY) && A.layer < A.minlayer[A.job0 + job]) return;
@@ -1227,7 +1229,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   if (tid < TB && ((gm >> tid) & 1u)) {
     double g = 0.0;
 #pragma unroll
-    for (int ww = 0; ww < NW; ++ww) g += gred[ww][tid];
+    for (int ww = 0; ww < NW; ++ww) g += (double)gred[ww][tid];
     part[(size_t)tid * A.tiles + t] = g;
   }
   if ((A.flags & F_ENERGY) && tid == 0) {
