@@ -799,7 +799,6 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
     const uint32_t hflip = (LOAD == LD_L0_GATHER) ? A.l0_hflip : 0u;
     tab.build(cs, A.n, xbase, A.l0_kbit, hflip, tid, NT);
   }
-  __syncthreads();
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
   T *out = reinterpret_cast<T *>(A.out) + (size_t)job * A.out_stride;
   const uint32_t gm = A.gate_mask;
@@ -809,37 +808,46 @@ __device__ __forceinline__ void fwd_tile(const PassArgs &A, int job, uint32_t tb
   Reg32<T> r;
   // round L: global -> registers (tile bits 6..9) -> gates -> shared.  The
   // inverse CX chain maps the pair (y, y + 1) to (x, x ^ 3), x = A^-1 y.
-  if constexpr (FULL && (LOAD == LD_GATHER || LOAD == LD_L0_GATHER)) {
-    const int kbit = A.l0_kbit;
-    for_L_ent(gi, nmask, A.em, A.n, [&](int m, uint32_t x) {
-      T2 v;
-      if constexpr (LOAD == LD_GATHER && CPLX) {
-        // the map keeps the channel bit: (re, im) of x stay neighbours
-        v = __ldcg(reinterpret_cast<const T2 *>(in + x));
-      } else if constexpr (LOAD == LD_GATHER) {
-        v.x = __ldcg(in + x);
-        v.y = __ldcg(in + (x ^ d1));
-      } else {
-        v.x = tab(x, kbit);
-        v.y = tab(x ^ d1, kbit);
-      }
-      r.set_pair(m, v);
-    });
-  } else {
-    for_L(gi, [&](int m, uint32_t y) {
-      T2 v;
-      if constexpr (LOAD == LD_PLAIN) {
-        v = __ldcg(reinterpret_cast<const T2 *>(in + y));
-      } else if constexpr (LOAD == LD_ZERO) {
-        v.x = (y == 0) ? T(1) : T(0);
-        v.y = T(0);
-      } else {
-        v.x = tab(y, TB);
-        v.y = tab(y + 1, TB);
-      }
-      r.set_pair(m, v);
-    });
-  }
+  // State loads do not depend on the gate coefficients, so they are issued
+  // before the barrier that publishes them and are in flight while the
+  // coefficient loads complete; the layer-0 forms read the tables built above
+  // and come after it.
+  auto load_L = [&]() {
+    if constexpr (FULL && (LOAD == LD_GATHER || LOAD == LD_L0_GATHER)) {
+      const int kbit = A.l0_kbit;
+      for_L_ent(gi, nmask, A.em, A.n, [&](int m, uint32_t x) {
+        T2 v;
+        if constexpr (LOAD == LD_GATHER && CPLX) {
+          // the map keeps the channel bit: (re, im) of x stay neighbours
+          v = __ldcg(reinterpret_cast<const T2 *>(in + x));
+        } else if constexpr (LOAD == LD_GATHER) {
+          v.x = __ldcg(in + x);
+          v.y = __ldcg(in + (x ^ d1));
+        } else {
+          v.x = tab(x, kbit);
+          v.y = tab(x ^ d1, kbit);
+        }
+        r.set_pair(m, v);
+      });
+    } else {
+      for_L(gi, [&](int m, uint32_t y) {
+        T2 v;
+        if constexpr (LOAD == LD_PLAIN) {
+          v = __ldcg(reinterpret_cast<const T2 *>(in + y));
+        } else if constexpr (LOAD == LD_ZERO) {
+          v.x = (y == 0) ? T(1) : T(0);
+          v.y = T(0);
+        } else {
+          v.x = tab(y, TB);
+          v.y = tab(y + 1, TB);
+        }
+        r.set_pair(m, v);
+      });
+    }
+  };
+  if constexpr (!L0) load_L();
+  __syncthreads();
+  if constexpr (L0) load_L();
   round_gates<4, WHT, false, 1>(r, gt, gm, 6, false);
   sts_L(s, sb, r);
   // round M: tile bits 0..4.  Layouts L and M of warp w both cover tile
