@@ -1169,7 +1169,6 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   const T2 *cs = reinterpret_cast<const T2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   load_gate_coeffs(A, cs, gt.cs, tid);
   if (sizeof(T) == 4) gt.pack(tid);
-  __syncthreads();
   const T *in = reinterpret_cast<const T *>(A.in) + (size_t)job * A.in_stride;
   const T *lin = reinterpret_cast<const T *>(A.lam_in) + (size_t)job * A.lam_stride;
   const T *table = reinterpret_cast<const T *>(A.table) + (size_t)job * A.table_stride;
@@ -1179,6 +1178,9 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
   GIdx<TB, FULL> gi;
   gi.init(tbase, A, lane, w, tid);
 
+  // round L loads go out before the barrier that publishes the gate
+  // coefficients (they do not depend on them); the shared partials and tiles
+  // are written after it, once the previous item's epilogue has read them
   Reg32<T> psi, lam;
   T eacc = T(0);
   for_L(gi, [&](int m, uint32_t y) {
@@ -1194,6 +1196,7 @@ __device__ __forceinline__ void bwd_tile(const PassArgs &A, int job, uint32_t tb
     lam.set_pair(m, l);
     eacc += p.x * l.x + p.y * l.y;
   });
+  __syncthreads();
   round_grads<4, 1>(psi, lam, gm, 6, gred[w], lane);
   sts_L(sp, sb, psi);
   sts_L(sl, sb, lam);
