@@ -773,8 +773,9 @@ def run_gvqe(args):
     # Each kind's share over its measured time is its algorithmic GB/s; the
     # implementation's own per-pass bytes (every tile pass reads and writes the
     # whole state) give the per-pass figure beside it.
-    prof = {k: _lib.gvqe_profile_read(k) for k in range(5)}
-    names = {0: "k_fwd", 1: "k_bwd", 2: "k_grad_l0", 3: "k_lambda_xy", 4: "k_wht"}
+    prof = {k: _lib.gvqe_profile_read(k) for k in range(7)}
+    names = {0: "k_fwd", 1: "k_bwd", 2: "k_grad_l0", 3: "k_lambda_xy", 4: "k_wht", 5: "k_mps_write",
+             6: "k_mps_tab"}
     dom = max(prof, key=lambda k: prof[k]["ms"])
     pk = prof[dom]
     peak, peak_src = measured_peaks()
@@ -795,11 +796,12 @@ def run_gvqe(args):
         "traffic": ncu_traffic(names[dom], amps_per_launch),
         "kernel": names[dom], "launches": pk["launches"], "avg_launch_ms": pk["ms"] / launches_dom,
         "algorithmic_bytes_per_launch": alg_share.get(dom, 0.0) * evals / launches_dom,
-        "bytes_rule": ("algorithmic: (6D+2) S + T per E+grad, one sweep per layer (k_fwd S + 2DS, k_bwd "
+        "bytes_rule": ("algorithmic: (6D+2) S + T per E+grad, one sweep per layer (forward S + 2DS, k_bwd "
                        "(4D-1) S + T, k_grad_l0 2S); S = 4 B x 2^n real FP32 state, T = 8 B x 2^n FP64 table. "
-                       "Layer 0 is an analytic product state here, so k_fwd never writes it and k_grad_l0 reads "
-                       "only lambda: their algorithmic rates count bytes the method's plain form moves and "
-                       "these kernels do not"),
+                       "Layer 0 is an analytic product state here, so the forward never writes it and k_grad_l0 "
+                       "reads only lambda; the forward's stored states of layers 1..3 are written in closed "
+                       "form (k_mps_tab + k_mps_write, write-only) and the rest by k_fwd tile passes, so the "
+                       "forward's algorithmic rate is given for the three kinds together (per_kind.forward)"),
         "per_pass": {"achieved": pass_gbps, "frac": pass_gbps / peak,
                      "bytes_per_launch": pk["bytes"] / launches_dom,
                      "rule": "every tile pass reads and writes the whole state (3 passes per layer at n=30)"},
@@ -809,9 +811,14 @@ def run_gvqe(args):
         "per_kind": {names[k]: {"launches": prof[k]["launches"], "ms": prof[k]["ms"],
                                 "GBps_per_pass": (prof[k]["bytes"] / (prof[k]["ms"] / 1000.0) / 1e9)
                                 if prof[k]["ms"] else 0.0,
-                                "GBps_algorithmic": kind_alg(k)}
+                                "GBps_algorithmic": kind_alg(k) if k != 0 else None}
                      for k in prof if prof[k]["launches"]},
     }
+    fwd_ms = sum(prof[k]["ms"] for k in (0, 5, 6))
+    if fwd_ms > 0:
+        roofline["per_kind"]["forward"] = {
+            "kinds": "k_fwd + k_mps_write + k_mps_tab", "ms": fwd_ms,
+            "GBps_algorithmic": alg_share[0] * evals / (fwd_ms / 1000.0) / 1e9}
     _lib.gvqe_profile_reset()
 
     # e2e through the public API: pinned host inputs in, results out, every step

@@ -83,13 +83,12 @@ class Ansatz(_Handle):
         if split:
             gvqe_ansatz_set_option(self.handle, GVQE_OPT_SPLIT_PASSES, split)
 
-    def set_schedule(self, staged: bool) -> None:
-        """One launch per stage (True) or one persistent launch (False, the default)."""
-        _lib.gvqe_batch_set_option(self.handle, _lib.GVQE_BATCH_OPT_SCHEDULE,
-                                   _lib.GVQE_BATCH_STAGED if staged else _lib.GVQE_BATCH_PERSISTENT)
-
     def set_tile_bits(self, bits: int) -> None:
         gvqe_ansatz_set_option(self.handle, GVQE_OPT_TILE_BITS, bits)
+
+    def set_mps_layers(self, layers: int) -> None:
+        """Leading layers written in closed form (GVQE_OPT_MPS_LAYERS): 0 auto, -1 none, 1..3."""
+        gvqe_ansatz_set_option(self.handle, _lib.GVQE_OPT_MPS_LAYERS, layers)
 
     def describe(self, fp64: bool = False) -> str:
         """The tile-pass plan of this ansatz (host only), with the last autotune report."""

@@ -22,7 +22,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgvqe.so")
 LIB_DEBUG = os.path.join(HERE, "libgvqe_debug.so")
 SOURCES = ["gvqe_api.cu", "gvqe_kernels.cu", "gvqe_static.cu", "gvqe_batch.cu", "gvqe_grad_l0.cu", "gvqe_readout.cu",
-           "gvqe_graph.cu", "gvqe_tune.cu"]
+           "gvqe_graph.cu", "gvqe_tune.cu", "gvqe_mps.cu"]
 # gvqe_inst.cu is compiled once per (amplitude type, tile bits) pair
 INSTANCES = [("float", tb) for tb in (10, 11, 12, 13)] + [("double", tb) for tb in (10, 11, 12)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -148,9 +148,10 @@ struct ProfRec {
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
 static std::vector<ProfRec> g_prof_pending;
-static long long g_prof_n[5] = {0, 0, 0, 0, 0};
-static double g_prof_ms[5] = {0, 0, 0, 0, 0};
-static double g_prof_bytes[5] = {0, 0, 0, 0, 0};
+constexpr int PROF_KINDS = 7;  // PassKind values
+static long long g_prof_n[PROF_KINDS] = {};
+static double g_prof_ms[PROF_KINDS] = {};
+static double g_prof_bytes[PROF_KINDS] = {};
 
 void count_launches(int k) { g_launches += k; }
 
@@ -173,6 +174,12 @@ static double pass_bytes(int prec, const PassArgs &A, int jobs) {
       break;
     case K_LAMBDA_XY:
       b = 2 * S + ((A.flags & F_WRITE_LAMBDA) ? S : 0);
+      break;
+    case K_MPS:
+      b = S;  // write-only
+      break;
+    case K_MPS_TAB:
+      b = (double)mps_dims(A.n, A.layer).total * 4 * jobs;
       break;
   }
   return b;
@@ -207,7 +214,7 @@ static void prof_drain() {
   for (ProfRec &r : g_prof_pending) {
     float ms = 0.f;
     cudaEventSynchronize(r.b);
-    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess && r.kind >= 0 && r.kind < 5) {
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess && r.kind >= 0 && r.kind < PROF_KINDS) {
       g_prof_n[r.kind] += 1;
       g_prof_ms[r.kind] += ms;
       g_prof_bytes[r.kind] += r.bytes;
@@ -566,8 +573,19 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
 }
 
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
+int mps_layers_for(int n, int reps, int prec, int ent, int gates, int want) {
+  if (want < 0 || prec != 0 || gates != 1 || n < MPS_MIN_QUBITS || reps < 2) return 0;
+  int R = std::min(MPS_MAX_LAYERS, reps - 1);
+  if (want > 0) R = std::min(R, want);
+  for (int r = 1; r <= R; ++r) {
+    const EntMap e = ent_map(ent, n, r);
+    if (e.sh != 0 || (e.form != EF_DIFF && e.form != EF_PREFIX)) return 0;
+  }
+  return R;
+}
+
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0,
-                bool state_only, int ent, int gates, int split, int xy_tb) {
+                bool state_only, int ent, int gates, int split, int xy_tb, int mps_layers) {
   if (gates == 2) return build_plan_su2(n, reps, prec, tile_bits, want_grad, diag, ent, state_only, split);
   Plan pl;
   pl.n = n;
@@ -648,7 +666,35 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
       pl.steps.push_back(st);
     }
   }
-  for (int r = 1; r <= reps; ++r) {
+  // closed-form leading layers: every stored state of layers 1..R (gradient
+  // path), or layer R's final state alone (energy path)
+  const int R = (mps_layers > 0 && reps >= 2) ? std::min(mps_layers, reps - 1) : 0;
+  pl.mps_layers = R;
+  for (int r = 1; r <= R; ++r) {
+    pl.mps_elems = std::max(pl.mps_elems, (mps_dims(n, r).total + 63) / 64 * 64);
+    uint32_t rot = 0;
+    for (int j = 0; j < p; ++j) {
+      const LayerPass &lp = pl.lp[j];
+      for (int i = 0; i < lp.tb; ++i)
+        if ((lp.gmask >> i) & 1u) rot |= 1u << qubit_of(lp, i);
+      if (!want_grad && !(r == R && j == p - 1)) continue;
+      PassStep tab;
+      tab.A = base_args(K_MPS_TAB);
+      tab.A.layer = r;
+      tab.A.gate_mask = rot;
+      tab.A.em = ent_map(ent, n, r);
+      tab.A.tiles = 1;
+      pl.steps.push_back(tab);
+      PassStep st = tab;
+      st.A.kind = K_MPS;
+      st.A.tiles = 1LL << (n - MPS_CHUNK_BITS);
+      st.A.store_mode = ST_PLAIN;
+      st.out = want_grad ? first_state + (r - 1) * p + j : PP0;
+      pl.steps.push_back(st);
+      cur = st.out;
+    }
+  }
+  for (int r = R + 1; r <= reps; ++r) {
     for (int j = 0; j < p; ++j) {
       const LayerPass &lp = pl.lp[j];
       PassStep st;
@@ -815,7 +861,12 @@ std::string describe_plan(const Plan &pl) {
              j, lp.tb, lp.c, lp.a, runs.c_str(), lp.k1, lp.gap, tiles_of(pl.n, lp.tb));
     s += buf;
   }
-  static const char *kinds[] = {"fwd", "bwd", "grad_l0", "lambda_xy", "wht"};
+  if (pl.mps_layers > 0) {
+    snprintf(buf, sizeof(buf), "  closed-form layers 1..%d (bond dimension up to %d), %lld table floats per job\n",
+             pl.mps_layers, 1 << pl.mps_layers, pl.mps_elems);
+    s += buf;
+  }
+  static const char *kinds[] = {"fwd", "bwd", "grad_l0", "lambda_xy", "wht", "mps", "mps_tab"};
   for (const PassStep &st : pl.steps) {
     snprintf(buf, sizeof(buf), "  %-9s layer=%d tb=%d c=%d a=%d gates=0x%x load=%d store=%d flags=0x%x in=%d lam=%d out=%d\n",
              kinds[st.A.kind], st.A.layer, st.A.tb, st.A.c, st.A.a, st.A.gate_mask, st.A.load_mode, st.A.store_mode,
@@ -1061,13 +1112,15 @@ static int ensure_tables(gvqe_hamiltonian_s *h, int prec, cudaStream_t s, bool c
 }
 
 // --------------------------------------------------------- plan execution --
-Plan *gvqe::get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool state_only) {
-  const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0) | (state_only ? 8 : 0) | (a->gates == 2 ? 16 : 0);
+Plan *gvqe::get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool state_only, bool allow_mps) {
+  const int key = prec | (want_grad ? 2 : 0) | (diag ? 4 : 0) | (state_only ? 8 : 0) | (a->gates == 2 ? 16 : 0) |
+                  (allow_mps ? 0 : 32);
   auto it = a->plans.find(key);
   const int tb = eff_tile_bits(a, prec);
   if (it != a->plans.end() && it->second.tile_bits == tb) return &it->second;
+  const int mps = allow_mps ? mps_layers_for(a->n, a->reps, prec, a->ent, a->gates, a->mps) : 0;
   Plan pl = build_plan(a->n, a->reps, prec, tb, want_grad, diag, false, state_only, a->ent, a->gates,
-                       eff_split(a, prec), eff_xy_tb(a, prec));
+                       eff_split(a, prec), eff_xy_tb(a, prec), mps);
   pl.tile_bits = tb;
   a->plans[key] = std::move(pl);
   return &a->plans[key];
@@ -1093,7 +1146,7 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
   // jobs per launch: enough tiles to fill the GPU, bounded by memory
   const long long tilesA = 1LL << (pl->n - pl->lp[0].tb);
   int J = (int)std::min<long long>(batch, std::max<long long>(1, 4096 / tilesA));
-  const size_t per_job = (size_t)pl->n_bufs * S * es + (size_t)pl->part_stride * 8;
+  const size_t per_job = (size_t)pl->n_bufs * S * es + (size_t)pl->part_stride * 8 + (size_t)pl->mps_elems * 4;
   size_t freeb = 0, total = 0;
   GV_CUDA(cudaMemGetInfo(&freeb, &total));
   size_t have = freeb + a->ws.bytes;
@@ -1113,6 +1166,8 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
     if (id < 0) return nullptr;
     return bufs + (size_t)id * J * S * es;  // buffer id, job slots contiguous
   };
+  // closed-form layer tables after the state buffers (a multiple of 64 floats per job)
+  float *mps_tab = (float *)(bufs + (size_t)pl->n_bufs * J * S * es);
   const bool cplx = a->gates == 2;
   const void *table = h ? (cplx ? h->TC[prec].ptr : (prec ? h->T64.ptr : h->T32.ptr)) : nullptr;
   const void *tc = h ? (prec ? (const void *)h->d_tc64 : (const void *)h->d_tc32) : nullptr;
@@ -1134,6 +1189,13 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
       A.epart = part + (st.epart_region >= 0 ? st.epart_region : 0);
       A.part_stride = pl->part_stride;
       A.minlayer = minlayer;
+      if (A.kind == K_MPS_TAB) {
+        A.out = mps_tab;
+        A.out_stride = pl->mps_elems;
+      } else if (A.kind == K_MPS) {
+        A.in = mps_tab;
+        A.in_stride = pl->mps_elems;
+      }
       if (!st.xy) {
         GV_CUDA(launch_step(prec, A, jobs, 0, s));
         continue;
@@ -1269,7 +1331,7 @@ int gvqe_profile_enable(int on) {
 
 int gvqe_profile_read(int kind, int64_t *launches, double *ms, double *bytes) {
   g_err.clear();
-  if (kind < 0 || kind > 4) return fail(GVQE_EINVAL, "profile kind %d", kind);
+  if (kind < 0 || kind >= PROF_KINDS) return fail(GVQE_EINVAL, "profile kind %d", kind);
   prof_drain();
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (launches) *launches = g_prof_n[kind];
@@ -1282,7 +1344,7 @@ int gvqe_profile_reset(void) {
   g_err.clear();
   prof_drain();
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < PROF_KINDS; ++k) {
     g_prof_n[k] = 0;
     g_prof_ms[k] = 0;
     g_prof_bytes[k] = 0;
@@ -1393,6 +1455,13 @@ int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
     a->xy_tb = value;
     a->tuned_xy_tb[0] = a->tuned_xy_tb[1] = 0;
     a->tune_report.clear();
+    a->plans.clear();
+    return GVQE_OK;
+  }
+  if (option == GVQE_OPT_MPS_LAYERS) {
+    if (value < -1 || value > MPS_MAX_LAYERS)
+      return fail(GVQE_EINVAL, "closed-form layers %d outside [-1, %d] (0 = auto, -1 = none)", value, MPS_MAX_LAYERS);
+    a->mps = value;
     a->plans.clear();
     return GVQE_OK;
   }

@@ -26,6 +26,8 @@ enum PassKind : int {
   K_GRAD_L0 = 2,    // layer-0 gradients against the analytic product state
   K_LAMBDA_XY = 3,  // lambda = H psi with X-mask groups; energy
   K_WHT = 4,        // unnormalised Walsh-Hadamard butterflies (diagonal table build)
+  K_MPS = 5,        // a leading layer's state written in closed form (gvqe_mps.cu)
+  K_MPS_TAB = 6,    // the contracted site-tensor tables K_MPS reads
 };
 
 enum LoadMode : int {
@@ -198,6 +200,33 @@ struct PassArgs {
   const void *tci;  // complex path: imaginary coefficient parts (i^#Y folded in)
 };
 
+// Closed-form leading layers (gvqe_mps.cu).  After r layers the state is a
+// product of D x D site matrices, D = 2^r, evaluated per amplitude from four
+// tables of contracted site ranges: qubits [0, 7) (a row vector per pattern,
+// stored transposed [D][128]), [7, 13) (a matrix per pattern, [64][D][D]),
+// [13, 13 + h1) ([2^h1][D][D]) and [13 + h1, n) (a column vector, [2^h2][D]),
+// h1 = min(9, n - 13).  Offsets in floats inside one job's table region.
+constexpr int MPS_MAX_LAYERS = 3;
+constexpr int MPS_MIN_QUBITS = 14;
+constexpr int MPS_CHUNK_BITS = 13;
+struct MpsDims {
+  int D, h1, h2;
+  long long lo, mid, m1, r2, total;
+};
+__host__ __device__ inline MpsDims mps_dims(int n, int r) {
+  MpsDims d;
+  d.D = 1 << r;
+  d.h1 = (n - MPS_CHUNK_BITS) < 9 ? (n - MPS_CHUNK_BITS) : 9;
+  d.h2 = n - MPS_CHUNK_BITS - d.h1;
+  const long long D = d.D;
+  d.lo = 0;
+  d.mid = d.lo + 128 * D;
+  d.m1 = d.mid + 64 * D * D;
+  d.r2 = d.m1 + (1LL << d.h1) * D * D;
+  d.total = d.r2 + (1LL << d.h2) * D;
+  return d;
+}
+
 // One output of the final reduction: the sum of `count` partials starting at
 // `off` inside a job's partial buffer becomes E (param < 0) or grad[param].
 struct RedEntry {
@@ -236,6 +265,11 @@ constexpr int XYC_AMPS_PER_CTA = 1024;
 // tiles come on top: at most ~200 KiB in all is accepted).
 size_t xy_smem_bytes(int prec, int ngroups, int nterm);
 cudaError_t launch_trig(int prec, const double *params, long long count, void *cs, cudaStream_t s);
+// K_MPS_TAB / K_MPS launches (gvqe_mps.cu, FP32 only).  K_MPS_TAB: layer = r,
+// gate_mask = the qubits layer r has rotated at this stage, em = the entangler
+// (EF_DIFF or EF_PREFIX), out = table region (out_stride floats per job).
+// K_MPS: in = that region (in_stride), out = the state, tiles = 2^(n - 13) chunks.
+cudaError_t launch_mps(int prec, const PassArgs &A, int jobs, cudaStream_t s);
 cudaError_t launch_minlayer(const uint8_t *mask, int jobs, int n, int P, int none_value, int *out,
                             cudaStream_t s);
 cudaError_t launch_reduce(const double *part, long long part_stride, const RedEntry *dir, int ndir,

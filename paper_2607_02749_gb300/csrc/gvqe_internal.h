@@ -60,6 +60,8 @@ struct Plan {
   std::map<int, RedEntry> param_dir;
   std::vector<RedEntry> dir;  // energy entry first, then one per parameter
   int final_buf = -1;         // state-only plans: buffer of the final state
+  int mps_layers = 0;         // leading layers written in closed form (K_MPS steps)
+  long long mps_elems = 0;    // floats of closed-form tables per job (one stage at a time)
   DevBuf d_dir;
   int d_dir_count = 0;
 };
@@ -74,8 +76,17 @@ void count_launches(int k);
 // gates: 1 = RY layers (real amplitudes), 2 = full EfficientSU2 layers, RY then
 // RZ on every qubit (complex amplitudes; diagonal H, energy and gradient only).
 // xy_tb: tile bits of the X-mask pass (0: those of the layer's first pass).
+// mps_layers: the leading layers after layer 0 whose states K_MPS steps write
+// in closed form (0: none; see mps_layers_for).
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false,
-                bool state_only = false, int ent = ENT_LINEAR, int gates = 1, int split = SPLIT_AUTO, int xy_tb = 0);
+                bool state_only = false, int ent = ENT_LINEAR, int gates = 1, int split = SPLIT_AUTO, int xy_tb = 0,
+                int mps_layers = 0);
+// How many leading layers a plan may write in closed form: FP32, RY layers,
+// an entangler whose index map ties each qubit only to the one below it
+// (linear, full, reverse linear), n >= MPS_MIN_QUBITS, and never the last
+// layer (which carries the energy epilogue); `want` is GVQE_OPT_MPS_LAYERS
+// (0 = up to MPS_MAX_LAYERS, -1 = none, 1..3 = at most that many).
+int mps_layers_for(int n, int reps, int prec, int ent, int gates, int want);
 std::string describe_plan(const Plan &pl);
 // One tile-pass launch, counted by gvqe_launch_count and timed by the event
 // profiler when it is on.
@@ -128,6 +139,7 @@ struct gvqe_ansatz_s {
   int tuned_split[2] = {-1, -1};
   int xy_tb = 0;                 // GVQE_OPT_XY_TILE_BITS (0: the first pass's tile bits)
   int tuned_xy_tb[2] = {0, 0};   // per precision, chosen by gvqe_autotune (0: none)
+  int mps = 0;                   // GVQE_OPT_MPS_LAYERS (0 auto, -1 none, 1..3 at most that many)
   std::map<int, gvqe::Plan> plans;
   gvqe::DevBuf ws, aux, shift, ro, tune;
   std::string tune_report;  // the last gvqe_autotune sweep and its choice (empty: not tuned)
@@ -144,7 +156,8 @@ inline int eff_xy_tb(const gvqe_ansatz_s *a, int prec) { return a->tuned_xy_tb[p
 // The ansatz's cached plan for (precision, gradient or not, diagonal H or not,
 // state only); it and its host-side reduction directory live until the
 // ansatz is destroyed or one of its options changes.
-Plan *get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool state_only = false);
+// allow_mps = false: no closed-form layers (callers without a table region).
+Plan *get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool state_only = false, bool allow_mps = true);
 // Energies (and adjoint gradients when grad != NULL) of a batch: the body of
 // gvqe_energy / gvqe_energy_grad after their argument checks.
 int energy_impl(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, const double *params, const uint8_t *mask, int batch,

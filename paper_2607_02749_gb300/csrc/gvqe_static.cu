@@ -81,7 +81,7 @@ extern "C" int gvqe_energy_static(gvqe_ansatz a, gvqe_hamiltonian h, const doubl
 
   // The energy plan (forward passes with the energy fused into the last one),
   // cached on the ansatz so that its reduction directory outlives this call.
-  const Plan &pl = *get_plan(a, prec, false, true);
+  const Plan &pl = *get_plan(a, prec, false, true, false, false);  // no closed-form layers: no table region here
   const int n = a->n, P = pl.P;
   const size_t S = (size_t)1 << n;
   const size_t es = prec ? 8 : 4;

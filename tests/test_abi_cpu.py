@@ -300,3 +300,44 @@ def test_split_rule_over_register_sizes(gates, fp64):
             lo, hi = tb + ga - (y - 1), nb - (y - 1)
             assert y == 1 or max(0, hi - max(lo, pb)) > 8
     assert seen_split == (gates == 2 or fp64)
+
+
+def test_closed_form_layer_option_and_plans():
+    """GVQE_OPT_MPS_LAYERS: FP32 plans with n >= 14, reps >= 2 and a linear,
+    full or reverse-linear entangler write layers 1..min(3, reps - 1) in closed
+    form (one table build and one write per stored state); everything else keeps
+    every layer as tile passes."""
+    def desc(n, reps, ent=_lib.GVQE_ENT_LINEAR, mps=None, flags=_lib.GVQE_FP32):
+        a = _lib.gvqe_ansatz_create(n, reps, ent)
+        try:
+            if mps is not None:
+                _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_MPS_LAYERS, mps)
+            return _lib.gvqe_ansatz_describe(a, flags)
+        finally:
+            _lib.gvqe_destroy(a)
+
+    d = desc(30, 6)
+    assert "closed-form layers 1..3 (bond dimension up to 8), 39936 table floats per job" in d
+    steps = [ln.split()[0] for ln in d.splitlines()[1:] if ln.startswith("  ") and not ln.startswith("  layer pass")
+             and not ln.startswith("  closed-form")]
+    # three stored states per layer for layers 1..3: a table build and a write each, then tile passes
+    assert steps[:18] == ["mps_tab", "mps"] * 9
+    assert steps[18:21] == ["fwd"] * 3 and "mps" not in steps[18:]
+    assert steps.count("fwd") == 9 and steps.count("bwd") == 18
+    for ent in (_lib.GVQE_ENT_FULL, _lib.GVQE_ENT_REVERSE_LINEAR):
+        assert "closed-form layers 1..3 " in desc(20, 5, ent)
+    assert "closed-form layers 1..1 " in desc(14, 2)
+    assert "closed-form layers 1..2 " in desc(14, 6, mps=2)
+    for args in [dict(n=13, reps=4), dict(n=20, reps=1), dict(n=20, reps=4, mps=-1),
+                 dict(n=20, reps=4, flags=_lib.GVQE_FP64), dict(n=20, reps=4, ent=_lib.GVQE_ENT_CIRCULAR),
+                 dict(n=20, reps=4, ent=_lib.GVQE_ENT_PAIRWISE), dict(n=20, reps=4, ent=_lib.GVQE_ENT_SCA)]:
+        assert "closed-form" not in desc(**args), args
+    a = _lib.gvqe_ansatz_create(16, 3)
+    try:
+        for v in (-1, 0, 1, 2, 3):
+            _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_MPS_LAYERS, v)
+        for v in (-2, 4):
+            with pytest.raises(_lib.GvqeError):
+                _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_MPS_LAYERS, v)
+    finally:
+        _lib.gvqe_destroy(a)

@@ -1,0 +1,169 @@
+"""Closed-form leading layers (GVQE_OPT_MPS_LAYERS) on the GPU.
+
+From the layer-0 product state, r layers of [linear / full / reverse-linear
+CX chain, RY] leave a product of 2^r x 2^r site matrices along the qubits;
+FP32 plans with n >= 14 and reps >= 2 write the stored states of layers
+1..min(3, reps - 1) from contracted tables of them (gvqe_mps.cu) instead of
+running tile passes.  Checked here against the oracle (energies, adjoint
+gradients, masks, X/Y strings, readout) and against the same plans with every
+layer as tile passes.  Tolerances as in test_gpu_parity.py (FP32 mode):
+|dE| <= 2e-5 sum|c|, gradient relative L2 <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import readout as ro
+from paper_2607_02749_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2607_02749_gb300 as gv  # noqa: E402
+
+FP32_E, FP32_G = 2e-5, 1e-4
+ENTS = [gv.GVQE_ENT_LINEAR, gv.GVQE_ENT_FULL, gv.GVQE_ENT_REVERSE_LINEAR]
+
+
+def _ref(n, reps, th, ham, ent):
+    with oracle.entangler(ent):
+        return oracle.energy_grad(n, reps, th, ham.strings, ham.coeffs)
+
+
+def _run(n, reps, ham, th, ent, mps, tb=0, mask=None):
+    a = gv.Ansatz(n, reps, entangler=ent, tile_bits=tb)
+    a.set_mps_layers(mps)
+    h = gv.Hamiltonian.from_workload(ham)
+    t = torch.as_tensor(th, device="cuda")
+    m = None if mask is None else torch.as_tensor(mask, dtype=torch.uint8, device="cuda")
+    e_only = gv.energy(a, h, t).cpu().numpy()
+    e, g = gv.energy_grad(a, h, t, mask=m)
+    desc = a.describe()
+    a.close()
+    h.close()
+    return e_only, e.cpu().numpy(), g.cpu().numpy(), desc
+
+
+def _check_oracle(e, g, n, reps, th, ham, ent, what):
+    scale = ham.abs_sum()
+    for b in range(th.shape[0]):
+        er, gr = _ref(n, reps, th[b], ham, ent)
+        de = abs(e[b] - er)
+        assert de <= FP32_E * scale, f"{what} b={b} |dE|={de:.3e}"
+        if g is not None:
+            rel = np.linalg.norm(g[b] - gr) / max(np.linalg.norm(gr), 1e-300)
+            assert rel <= FP32_G, f"{what} b={b} grad rel L2={rel:.3e}"
+
+
+# (n, reps, tile bits): one to three closed-form layers, one run per strided
+# pass and split layouts (forced small tiles give more passes per layer, so
+# the stored states between passes rotate different qubit subsets)
+CASES = [(14, 2, 0), (14, 4, 0), (15, 3, 10), (17, 5, 11), (19, 4, 0), (20, 3, 12), (22, 4, 0)]
+
+
+@pytest.mark.parametrize("ent", ENTS)
+@pytest.mark.parametrize("n,reps,tb", CASES)
+def test_closed_form_layers_match_oracle_and_tile_passes(n, reps, tb, ent):
+    ham = wl.z_hamiltonian(n, 6 * n + 5, seed=n + reps)
+    th = wl.thetas(n, reps, 2, seed=200 + n + ent)
+    e_only, e, g, desc = _run(n, reps, ham, th, ent, 0, tb)
+    R = min(3, reps - 1)
+    assert f"closed-form layers 1..{R} " in desc, desc
+    _check_oracle(e_only, None, n, reps, th, ham, ent, "energy")
+    _check_oracle(e, g, n, reps, th, ham, ent, "energy_grad")
+    e0_only, e0, g0, desc0 = _run(n, reps, ham, th, ent, -1, tb)
+    assert "closed-form" not in desc0
+    scale = ham.abs_sum()
+    assert np.max(np.abs(e_only - e0_only)) <= FP32_E * scale
+    for b in range(th.shape[0]):
+        rel = np.linalg.norm(g[b] - g0[b]) / np.linalg.norm(g0[b])
+        print(f"n={n} reps={reps} tb={tb} ent={ent} b={b}: closed form vs tile passes grad rel L2 {rel:.2e}")
+        assert rel <= FP32_G
+
+
+@pytest.mark.parametrize("layers", [1, 2, 3])
+def test_explicit_layer_counts(layers):
+    n, reps = 16, 5
+    ham = wl.z_hamiltonian(n, 90, seed=4)
+    th = wl.thetas(n, reps, 3, seed=5)
+    e_only, e, g, desc = _run(n, reps, ham, th, gv.GVQE_ENT_LINEAR, layers)
+    assert f"closed-form layers 1..{layers} " in desc
+    _check_oracle(e, g, n, reps, th, ham, gv.GVQE_ENT_LINEAR, f"layers={layers}")
+
+
+def test_many_vectors_per_launch():
+    # n = 14: two tiles per state, so one launch covers every vector (per-job table regions)
+    n, reps = 14, 3
+    ham = wl.z_hamiltonian(n, 70, seed=6)
+    th = wl.thetas(n, reps, 7, seed=7)
+    e_only, e, g, desc = _run(n, reps, ham, th, gv.GVQE_ENT_LINEAR, 0)
+    assert "closed-form layers 1..2 " in desc
+    _check_oracle(e_only, None, n, reps, th, ham, gv.GVQE_ENT_LINEAR, "energy")
+    _check_oracle(e, g, n, reps, th, ham, gv.GVQE_ENT_LINEAR, "energy_grad")
+
+
+def test_masks_with_closed_form_layers():
+    n, reps = 16, 4
+    P = n * (reps + 1)
+    ham = wl.z_hamiltonian(n, 80, seed=8)
+    th = wl.thetas(n, reps, 4, seed=9)
+    mask = wl.active_mask(P, 4, seed=10)
+    mask[1, :] = 0
+    mask[2, : 2 * n] = 0  # layers 0 and 1 (closed form) inactive
+    mask[3, :] = 0
+    mask[3, n + 3] = 1    # only one parameter of a closed-form layer
+    _, e, g, desc = _run(n, reps, ham, th, gv.GVQE_ENT_LINEAR, 0, mask=mask)
+    assert "closed-form layers 1..3 " in desc
+    assert np.all(g[mask == 0] == 0.0)
+    scale = ham.abs_sum()
+    for b in range(4):
+        er, gr = _ref(n, reps, th[b], ham, gv.GVQE_ENT_LINEAR)
+        assert abs(e[b] - er) <= FP32_E * scale
+        act = mask[b] != 0
+        if act.any():
+            rel = np.linalg.norm(g[b][act] - gr[act]) / max(np.linalg.norm(gr[act]), 1e-3 * scale)
+            assert rel <= FP32_G, (b, rel)
+
+
+def test_xy_strings_with_closed_form_layers():
+    n, reps = 16, 3
+    ham = wl.pauli_hamiltonian(n, 300, seed=11)
+    th = wl.thetas(n, reps, 2, seed=12)
+    e_only, e, g, desc = _run(n, reps, ham, th, gv.GVQE_ENT_LINEAR, 0)
+    assert "closed-form layers 1..2 " in desc
+    _check_oracle(e_only, None, n, reps, th, ham, gv.GVQE_ENT_LINEAR, "energy")
+    _check_oracle(e, g, n, reps, th, ham, gv.GVQE_ENT_LINEAR, "energy_grad")
+
+
+def test_readout_with_closed_form_layers():
+    n, reps = 15, 3
+    ham = wl.z_hamiltonian(n, 60, seed=13)
+    th = wl.thetas(n, reps, 1, seed=14)[0]
+    p = ro.probabilities(oracle.state(n, reps, th))
+    e = ro.diagonal_energies(n, ham.strings, ham.coeffs)
+    a = gv.Ansatz(n, reps)
+    assert "closed-form layers 1..2 " in a.describe()
+    h = gv.Hamiltonian.from_workload(ham)
+    r = gv.readout(a, h, torch.as_tensor(th, device="cuda"), alpha=0.2, shots=0)
+    assert abs(r.total - p.sum()) <= 8e-6
+    xo, po = ro.most_probable(p)
+    assert abs(r.p_max - po) <= 8e-6
+    assert p[r.argmax] >= po - 8e-6
+    assert abs(r.cvar - ro.cvar(p, e, 0.2)) <= FP32_E * ham.abs_sum()
+    a.close()
+    h.close()
+
+
+def test_plans_without_closed_form_layers():
+    # FP64, other entanglers, n < 14 and reps < 2 keep every layer as tile passes
+    assert "closed-form" not in gv.Ansatz(16, 4).describe(fp64=True)
+    for ent in (gv.GVQE_ENT_CIRCULAR, gv.GVQE_ENT_PAIRWISE, gv.GVQE_ENT_SCA):
+        assert "closed-form" not in gv.Ansatz(16, 4, entangler=ent).describe()
+    assert "closed-form" not in gv.Ansatz(13, 4).describe()
+    assert "closed-form" not in gv.Ansatz(16, 1).describe()
+    a = gv.Ansatz(16, 4)
+    a.set_mps_layers(-1)
+    assert "closed-form" not in a.describe()
