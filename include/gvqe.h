@@ -79,7 +79,7 @@ extern "C" {
 
 #define GVQE_OPT_XY_TILE_BITS 4 /* log2 amplitudes per tile of the X-mask pass (strings with X/Y letters, RY
                                    layers), 10..13 (FP64: at most 12), 0 = those of the first pass */
-#define GVQE_OPT_MPS_LAYERS 5 /* leading layers written in closed form: 0 = auto (up to 3), -1 = none, 1..3 =
+#define GVQE_OPT_MPS_LAYERS 5 /* leading layers written in closed form: 0 = auto (up to 3), -1 = none, 1..4 =
                                  at most that many.  After r entangler + RY layers on the analytic layer-0
                                  product state, the linear, full and reverse-linear entanglers leave a state
                                  that is a product of 2^r x 2^r matrices along the qubits; FP32 plans with

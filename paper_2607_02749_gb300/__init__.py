@@ -87,7 +87,7 @@ class Ansatz(_Handle):
         gvqe_ansatz_set_option(self.handle, GVQE_OPT_TILE_BITS, bits)
 
     def set_mps_layers(self, layers: int) -> None:
-        """Leading layers written in closed form (GVQE_OPT_MPS_LAYERS): 0 auto, -1 none, 1..3."""
+        """Leading layers written in closed form (GVQE_OPT_MPS_LAYERS): 0 auto, -1 none, 1..4."""
         gvqe_ansatz_set_option(self.handle, _lib.GVQE_OPT_MPS_LAYERS, layers)
 
     def describe(self, fp64: bool = False) -> str:

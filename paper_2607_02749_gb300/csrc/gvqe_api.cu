@@ -575,8 +575,7 @@ static Plan build_plan_su2(int n, int reps, int prec, int tile_bits, bool want_g
 // Build the ordered pass list for one (n, reps, precision) and what is requested.
 int mps_layers_for(int n, int reps, int prec, int ent, int gates, int want) {
   if (want < 0 || prec != 0 || gates != 1 || n < MPS_MIN_QUBITS || reps < 2) return 0;
-  int R = std::min(MPS_MAX_LAYERS, reps - 1);
-  if (want > 0) R = std::min(R, want);
+  int R = std::min(want > 0 ? std::min(want, MPS_MAX_LAYERS) : MPS_AUTO_LAYERS, reps - 1);
   for (int r = 1; r <= R; ++r) {
     const EntMap e = ent_map(ent, n, r);
     if (e.sh != 0 || (e.form != EF_DIFF && e.form != EF_PREFIX)) return 0;

@@ -85,7 +85,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
 // an entangler whose index map ties each qubit only to the one below it
 // (linear, full, reverse linear), n >= MPS_MIN_QUBITS, and never the last
 // layer (which carries the energy epilogue); `want` is GVQE_OPT_MPS_LAYERS
-// (0 = up to MPS_MAX_LAYERS, -1 = none, 1..3 = at most that many).
+// (0 = up to MPS_AUTO_LAYERS, -1 = none, 1..MPS_MAX_LAYERS = at most that many).
 int mps_layers_for(int n, int reps, int prec, int ent, int gates, int want);
 std::string describe_plan(const Plan &pl);
 // One tile-pass launch, counted by gvqe_launch_count and timed by the event
@@ -139,7 +139,7 @@ struct gvqe_ansatz_s {
   int tuned_split[2] = {-1, -1};
   int xy_tb = 0;                 // GVQE_OPT_XY_TILE_BITS (0: the first pass's tile bits)
   int tuned_xy_tb[2] = {0, 0};   // per precision, chosen by gvqe_autotune (0: none)
-  int mps = 0;                   // GVQE_OPT_MPS_LAYERS (0 auto, -1 none, 1..3 at most that many)
+  int mps = 0;                   // GVQE_OPT_MPS_LAYERS (0 auto, -1 none, 1..4 at most that many)
   std::map<int, gvqe::Plan> plans;
   gvqe::DevBuf ws, aux, shift, ro, tune;
   std::string tune_report;  // the last gvqe_autotune sweep and its choice (empty: not tuned)

@@ -88,9 +88,30 @@ __host__ __device__ inline MpsItems mps_items(const MpsDims &d) {
 }
 constexpr int TAB_NT = 64;
 
+// The qubits a table section's items contract over.
+__host__ __device__ inline int mps_q_first(const MpsItems &its, const MpsDims &d, long long i) {
+  return i < its.lo ? 0 : (i < its.mid ? 7 : (i < its.m1 ? 13 : 13 + d.h1));
+}
+__host__ __device__ inline int mps_q_last(const MpsItems &its, const MpsDims &d, int n, long long i) {
+  return i < its.lo ? 6 : (i < its.mid ? 12 : (i < its.m1 ? 12 + d.h1 : n - 1));
+}
+// Site matrices one CTA of k_mps_tab holds: the widest qubit span of any CTA's items.
+inline int mps_tab_span(int n, int r) {
+  const MpsDims d = mps_dims(n, r);
+  const MpsItems its = mps_items(d);
+  int span = 1;
+  for (long long i0 = 0; i0 < its.total; i0 += TAB_NT) {
+    const long long i1 = (i0 + TAB_NT < its.total) ? i0 + TAB_NT : its.total;
+    const int w = mps_q_last(its, d, n, i1 - 1) - mps_q_first(its, d, i0) + 1;
+    if (w > span) span = w;
+  }
+  return span;
+}
+
 // One CTA of TAB_NT threads takes items [blockIdx.x TAB_NT, +TAB_NT): it
 // builds the site matrices of the qubits those items span in shared memory
-// (FP64, [q][y][a][b]) and contracts one table row (or column) per thread.
+// (FP64, [q - first qubit][y][a][b]; the host sizes it by mps_tab_span) and
+// contracts one table row (or column) per thread.
 template <int D, int FORM>
 __global__ void __launch_bounds__(TAB_NT) k_mps_tab(const PassArgs A) {
   extern __shared__ double site[];
@@ -101,14 +122,11 @@ __global__ void __launch_bounds__(TAB_NT) k_mps_tab(const PassArgs A) {
   const float2 *cs = reinterpret_cast<const float2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
   const long long i0 = (long long)blockIdx.x * TAB_NT;
   const long long i1 = (i0 + TAB_NT < its.total) ? i0 + TAB_NT : its.total;
-  // qubit range of a section
-  auto q_first = [&](long long i) { return i < its.lo ? 0 : (i < its.mid ? 7 : (i < its.m1 ? 13 : 13 + d.h1)); };
-  auto q_last = [&](long long i) { return i < its.lo ? 6 : (i < its.mid ? 12 : (i < its.m1 ? 12 + d.h1 : n - 1)); };
-  const int qa = q_first(i0), qb = q_last(i1 - 1);
+  const int qa = mps_q_first(its, d, i0), qb = mps_q_last(its, d, n, i1 - 1);
   const int ne = (qb - qa + 1) * 2 * DD;
   for (int e = tid; e < ne; e += TAB_NT) {
     const int b = e % D, a = (e / D) % D, y = (e / DD) & 1, q = qa + e / (2 * DD);
-    site[(size_t)q * 2 * DD + y * DD + a * D + b] =
+    site[(size_t)(q - qa) * 2 * DD + y * DD + a * D + b] =
         (FORM == EF_PREFIX) ? site_entry<EF_PREFIX>(cs, A.pstride, q, y, a, b, r, (A.gate_mask >> q) & 1u)
                             : site_entry<EF_DIFF>(cs, A.pstride, q, y, a, b, r, (A.gate_mask >> q) & 1u);
   }
@@ -116,7 +134,7 @@ __global__ void __launch_bounds__(TAB_NT) k_mps_tab(const PassArgs A) {
   const long long it = i0 + tid;
   if (it >= i1) return;
   float *tab = reinterpret_cast<float *>(A.out) + (size_t)job * A.out_stride;
-  auto mat = [&](int q, int y) { return site + (size_t)q * 2 * DD + y * DD; };
+  auto mat = [&](int q, int y) { return site + (size_t)(q - qa) * 2 * DD + y * DD; };
   double v[D];
   // v <- v A (row vector)
   auto vecmat = [&](const double *M) {
@@ -184,18 +202,41 @@ constexpr int WR_NT = 256;  // 8 warps; warp w writes the rows w, w + 8, ... of 
 // Persistent CTAs walk the 2^13-amplitude chunks.  Lane l of every warp owns
 // amplitudes 4l .. 4l + 3 of each 128-amplitude row (qubits 0..6), so its four
 // row vectors of [0, 7) stay in registers; a row of the chunk (qubits 7..12)
-// is one shared vector m, read as a broadcast.
+// is one shared vector m, read as a broadcast.  For D >= 4 the next chunk's
+// matrix of [13, 13 + h1) and vector of [13 + h1, n) stream into a second
+// shared buffer (cp.async) while this chunk is written, so no chunk waits on
+// their loads.
 template <int D>
 __global__ void __launch_bounds__(WR_NT) k_mps_write(const PassArgs A) {
-  __shared__ __align__(16) float sM[64 * D * D];
-  __shared__ __align__(16) float sm[64 * D];
+  extern __shared__ __align__(16) float sM[];  // [64][b][a] (transposed), dynamic (64 KiB at D = 16)
+  __shared__ __align__(16) float sm[64 * 2 * D];  // m per row, each value twice: (m_a, m_a) pairs
+  __shared__ __align__(16) float sb[2][D * D + D];  // staged [D][D] matrix and [D] vector, by chunk parity
   __shared__ float sr[D];
-  const int r = (D == 2) ? 1 : (D == 4 ? 2 : 3);
+  constexpr bool STAGE = D >= 4;
+  constexpr int NCH = (D * D + D) / 4;  // 16-byte copies per staged chunk
+  const int r = (D == 2) ? 1 : (D == 4 ? 2 : (D == 8 ? 3 : 4));
   const MpsDims d = mps_dims(A.n, r);
   const int job = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const float *tab = reinterpret_cast<const float *>(A.in) + (size_t)job * A.in_stride;
   float *out = reinterpret_cast<float *>(A.out) + (size_t)job * A.out_stride;
-  for (int i = tid; i < 64 * D * D; i += WR_NT) sM[i] = tab[d.mid + i];
+  const long long chunks = A.tiles;
+  const long long mask1 = (1LL << d.h1) - 1;
+  // one 16-byte piece of chunk c's matrix (pieces 0 .. D D / 4 - 1) or vector
+  auto stage = [&](long long c, int buf) {
+    if (tid < NCH) {
+      const float *src = (tid < D * D / 4) ? tab + d.m1 + (c & mask1) * D * D + 4 * tid
+                                           : tab + d.r2 + (c >> d.h1) * D + 4 * (tid - D * D / 4);
+      cp_async16(&sb[buf][4 * tid], src);
+    }
+    cp_async_commit();
+  };
+  if constexpr (STAGE) stage(blockIdx.x, 0);
+  // the matrices of [7, 13) transposed, so that the threads of m = M r (consecutive a)
+  // read consecutive words for every b
+  for (int i = tid; i < 64 * D * D; i += WR_NT) {
+    const int ym = i / (D * D), b = (i / D) % D, a = i % D;
+    sM[i] = tab[d.mid + (ym * D + a) * D + b];
+  }
   unsigned long long L01[D], L23[D];  // (L[4l], L[4l+1]) and (L[4l+2], L[4l+3]) per bond index
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -203,43 +244,66 @@ __global__ void __launch_bounds__(WR_NT) k_mps_write(const PassArgs A) {
     L01[a] = pk(l.x, l.y);
     L23[a] = pk(l.z, l.w);
   }
-  const long long chunks = A.tiles;
-  const long long mask1 = (1LL << d.h1) - 1;
-  for (long long c = blockIdx.x; c < chunks; c += gridDim.x) {
-    __syncthreads();  // the previous chunk's vectors are read (and sM is loaded)
-    if (tid < D) {
-      const float *m1 = tab + d.m1 + ((c & mask1) * D + tid) * D;
-      const float *r2 = tab + d.r2 + (c >> d.h1) * D;
-      float acc = 0.f;
+  int par = 0;
+  for (long long c = blockIdx.x; c < chunks; c += gridDim.x, par ^= 1) {
+    if constexpr (STAGE) cp_async_wait<0>();
+    __syncthreads();  // staged data visible; the previous chunk's vectors are read (and sM is loaded)
+    if constexpr (STAGE) {
+      if (c + gridDim.x < chunks) stage(c + gridDim.x, par ^ 1);
+      if (tid < D) {
+        const float *m1 = &sb[par][tid * D];
+        const float *r2 = &sb[par][D * D];
+        float acc = 0.f;
 #pragma unroll
-      for (int b = 0; b < D; ++b) acc = fmaf(m1[b], r2[b], acc);
-      sr[tid] = acc;
+        for (int b = 0; b < D; ++b) acc = fmaf(m1[b], r2[b], acc);
+        sr[tid] = acc;
+      }
+    } else {
+      if (tid < D) {
+        const float *m1 = tab + d.m1 + ((c & mask1) * D + tid) * D;
+        const float *r2 = tab + d.r2 + (c >> d.h1) * D;
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) acc = fmaf(m1[b], r2[b], acc);
+        sr[tid] = acc;
+      }
     }
     __syncthreads();
-    for (int i = tid; i < 64 * D; i += WR_NT) {
-      const float *mrow = sM + i * D;
-      float acc = 0.f;
+    constexpr int NM = (64 * D + WR_NT - 1) / WR_NT;  // outputs per thread
+    // (unrolled only at D = 16, where independent outputs pay; at D <= 8 it would
+    // cost the registers of a fourth CTA per SM)
+#pragma unroll(D >= 16 ? NM : 1)
+    for (int k = 0; k < NM; ++k) {
+      const int i = tid + k * WR_NT;  // i = ym D + a
+      if (i < 64 * D) {
+        const float *mcol = sM + (i / D) * D * D + (i % D);
+        float acc = 0.f;
 #pragma unroll
-      for (int b = 0; b < D; ++b) acc = fmaf(mrow[b], sr[b], acc);
-      sm[i] = acc;
+        for (int b = 0; b < D; ++b) acc = fmaf(mcol[b * D], sr[b], acc);
+        *reinterpret_cast<float2 *>(&sm[2 * i]) = make_float2(acc, acc);
+      }
     }
     __syncthreads();
     float *oc = out + (c << MPS_CHUNK_BITS) + 4 * lane;
 #pragma unroll 2
     for (int ym = w; ym < 64; ym += WR_NT / 32) {
-      const float *mv = sm + ym * D;
-      unsigned long long p01 = 0ull, p23 = 0ull;
+      // one 16-byte broadcast load gives (m_a, m_a) and (m_{a+1}, m_{a+1});
+      // even and odd a accumulate separately (shorter dependency chains)
+      const ulonglong2 *mv = reinterpret_cast<const ulonglong2 *>(sm + ym * 2 * D);
+      unsigned long long p01 = 0ull, p23 = 0ull, q01 = 0ull, q23 = 0ull;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const float m = mv[a];
-        const unsigned long long m2 = pk(m, m);
-        p01 = fma2(L01[a], m2, p01);
-        p23 = fma2(L23[a], m2, p23);
+      for (int a = 0; a < D; a += 2) {
+        const ulonglong2 m = mv[a / 2];
+        p01 = fma2(L01[a], m.x, p01);
+        p23 = fma2(L23[a], m.x, p23);
+        q01 = fma2(L01[a + 1], m.y, q01);
+        q23 = fma2(L23[a + 1], m.y, q23);
       }
-      const float2 v01 = upk(p01), v23 = upk(p23);
+      const float2 v01 = upk(add2(p01, q01)), v23 = upk(add2(p23, q23));
       *reinterpret_cast<float4 *>(oc + ym * 128) = make_float4(v01.x, v01.y, v23.x, v23.y);
     }
   }
+  if constexpr (STAGE) cp_async_wait<0>();
 }
 
 template <int D>
@@ -248,7 +312,7 @@ cudaError_t launch_mps_d(const PassArgs &A, int jobs, cudaStream_t s) {
     const MpsDims d = mps_dims(A.n, A.layer);
     const MpsItems its = mps_items(d);
     const dim3 grid((unsigned)((its.total + TAB_NT - 1) / TAB_NT), (unsigned)jobs);
-    const size_t smem = (size_t)A.n * 2 * D * D * sizeof(double);
+    const size_t smem = (size_t)mps_tab_span(A.n, A.layer) * 2 * D * D * sizeof(double);
     if (A.em.form == EF_PREFIX) {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_mps_tab<D, EF_PREFIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -260,9 +324,11 @@ cudaError_t launch_mps_d(const PassArgs &A, int jobs, cudaStream_t s) {
     }
     return cudaGetLastError();
   }
-  const long long cap = (long long)num_sms_cached() * 4;
+  const long long cap = (long long)num_sms_cached() * (D >= 16 ? 2 : 4);
   const dim3 grid((unsigned)(A.tiles < cap ? A.tiles : cap), (unsigned)jobs);
-  k_mps_write<D><<<grid, WR_NT, 0, s>>>(A);
+  const size_t smem = (size_t)64 * D * D * sizeof(float);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_mps_write<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_mps_write<D><<<grid, WR_NT, smem, s>>>(A);
   return cudaGetLastError();
 }
 
@@ -276,7 +342,8 @@ cudaError_t launch_mps(int prec, const PassArgs &A, int jobs, cudaStream_t s) {
   switch (A.layer) {
     case 1: return launch_mps_d<2>(A, jobs, s);
     case 2: return launch_mps_d<4>(A, jobs, s);
-    default: return launch_mps_d<8>(A, jobs, s);
+    case 3: return launch_mps_d<8>(A, jobs, s);
+    default: return launch_mps_d<16>(A, jobs, s);
   }
 }
 

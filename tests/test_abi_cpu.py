@@ -324,8 +324,11 @@ def test_closed_form_layer_option_and_plans():
     assert steps[:18] == ["mps_tab", "mps"] * 9
     assert steps[18:21] == ["fwd"] * 3 and "mps" not in steps[18:]
     assert steps.count("fwd") == 9 and steps.count("bwd") == 18
+    # a fourth layer (bond dimension 16) on request
+    assert "closed-form layers 1..4 (bond dimension up to 16), 153600 table floats per job" in desc(30, 6, mps=4)
     for ent in (_lib.GVQE_ENT_FULL, _lib.GVQE_ENT_REVERSE_LINEAR):
         assert "closed-form layers 1..3 " in desc(20, 5, ent)
+        assert "closed-form layers 1..2 " in desc(20, 3, ent)
     assert "closed-form layers 1..1 " in desc(14, 2)
     assert "closed-form layers 1..2 " in desc(14, 6, mps=2)
     for args in [dict(n=13, reps=4), dict(n=20, reps=1), dict(n=20, reps=4, mps=-1),
@@ -334,9 +337,9 @@ def test_closed_form_layer_option_and_plans():
         assert "closed-form" not in desc(**args), args
     a = _lib.gvqe_ansatz_create(16, 3)
     try:
-        for v in (-1, 0, 1, 2, 3):
+        for v in (-1, 0, 1, 2, 3, 4):
             _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_MPS_LAYERS, v)
-        for v in (-2, 4):
+        for v in (-2, 5):
             with pytest.raises(_lib.GvqeError):
                 _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_MPS_LAYERS, v)
     finally:

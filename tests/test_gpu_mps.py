@@ -3,7 +3,7 @@
 From the layer-0 product state, r layers of [linear / full / reverse-linear
 CX chain, RY] leave a product of 2^r x 2^r site matrices along the qubits;
 FP32 plans with n >= 14 and reps >= 2 write the stored states of layers
-1..min(3, reps - 1) from contracted tables of them (gvqe_mps.cu) instead of
+1..min(3, reps - 1) (on request up to 4) from contracted tables of them (gvqe_mps.cu) instead of
 running tile passes.  Checked here against the oracle (energies, adjoint
 gradients, masks, X/Y strings, readout) and against the same plans with every
 layer as tile passes.  Tolerances as in test_gpu_parity.py (FP32 mode):
@@ -84,7 +84,7 @@ def test_closed_form_layers_match_oracle_and_tile_passes(n, reps, tb, ent):
         assert rel <= FP32_G
 
 
-@pytest.mark.parametrize("layers", [1, 2, 3])
+@pytest.mark.parametrize("layers", [1, 2, 3, 4])
 def test_explicit_layer_counts(layers):
     n, reps = 16, 5
     ham = wl.z_hamiltonian(n, 90, seed=4)
