@@ -148,7 +148,7 @@ struct ProfRec {
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
 static std::vector<ProfRec> g_prof_pending;
-constexpr int PROF_KINDS = 7;  // PassKind values
+constexpr int PROF_KINDS = 11;  // PassKind values
 static long long g_prof_n[PROF_KINDS] = {};
 static double g_prof_ms[PROF_KINDS] = {};
 static double g_prof_bytes[PROF_KINDS] = {};
@@ -180,6 +180,9 @@ static double pass_bytes(int prec, const PassArgs &A, int jobs) {
       break;
     case K_MPS_TAB:
       b = (double)mps_dims(A.n, A.layer).total * 4 * jobs;
+      break;
+    case K_MPS_GRAD:
+      b = S;  // read lambda once
       break;
   }
   return b;
@@ -612,9 +615,19 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
   };
   // Buffer ids: stored pass outputs (gradient path) or a forward ping-pong
   // pair (energy path), the lambda ping-pong pair, and psi_0 for X/Y terms at reps = 0.
+  // closed-form leading layers 1..R; with gradients and bond dimension up to 8
+  // (R <= 3) their gradients come from lambda_R and the matrix product
+  // (mgrad), so only layer R's final state is stored for them
+  const int R = (mps_layers > 0 && reps >= 2) ? std::min(mps_layers, reps - 1) : 0;
+  const bool mgrad = want_grad && !state_only && R >= 1 && R <= 3;
   int nb = 0;
   const int first_state = nb;
-  if (want_grad) nb += reps * p;
+  if (want_grad) nb += mgrad ? 1 + (reps - R) * p : reps * p;
+  // buffer of the stored state after pass j of layer r (gradient path)
+  auto state_id = [&](int r, int j) {
+    if (!mgrad) return first_state + (r - 1) * p + j;
+    return (r == R) ? first_state : first_state + 1 + (r - R - 1) * p + j;
+  };
   int PP0 = -1, PP1 = -1;
   if (!want_grad && reps > 0) {
     PP0 = nb++;
@@ -630,7 +643,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
   int XYB = -1;
   if (reps == 0 && !diag) XYB = nb++;
   pl.n_bufs = nb;
-  pl.n_states = want_grad ? reps * p : 0;
+  pl.n_states = want_grad ? (mgrad ? 1 + (reps - R) * p : reps * p) : 0;
 
   auto add_E_region = [&](long long tiles) {
     pl.dir.push_back({poff, (int)tiles, -1});
@@ -666,29 +679,33 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
     }
   }
   // closed-form leading layers: every stored state of layers 1..R (gradient
-  // path), or layer R's final state alone (energy path)
-  const int R = (mps_layers > 0 && reps >= 2) ? std::min(mps_layers, reps - 1) : 0;
+  // path without mgrad), or layer R's final state alone (energy path; mgrad,
+  // whose table region then also keeps the site matrices for the gradients)
   pl.mps_layers = R;
+  pl.mps_grad = mgrad;
   for (int r = 1; r <= R; ++r) {
-    pl.mps_elems = std::max(pl.mps_elems, (mps_dims(n, r).total + 63) / 64 * 64);
     uint32_t rot = 0;
     for (int j = 0; j < p; ++j) {
       const LayerPass &lp = pl.lp[j];
       for (int i = 0; i < lp.tb; ++i)
         if ((lp.gmask >> i) & 1u) rot |= 1u << qubit_of(lp, i);
-      if (!want_grad && !(r == R && j == p - 1)) continue;
+      if ((!want_grad || mgrad) && !(r == R && j == p - 1)) continue;
+      const MpsDims md = mps_dims(n, r);
+      pl.mps_elems = std::max(pl.mps_elems, ((mgrad ? md.total_grad : md.total) + 63) / 64 * 64);
       PassStep tab;
       tab.A = base_args(K_MPS_TAB);
       tab.A.layer = r;
       tab.A.gate_mask = rot;
       tab.A.em = ent_map(ent, n, r);
       tab.A.tiles = 1;
+      if (mgrad) tab.A.flags |= F_MPS_SITES;
       pl.steps.push_back(tab);
       PassStep st = tab;
       st.A.kind = K_MPS;
+      st.A.flags = 0;
       st.A.tiles = 1LL << (n - MPS_CHUNK_BITS);
       st.A.store_mode = ST_PLAIN;
-      st.out = want_grad ? first_state + (r - 1) * p + j : PP0;
+      st.out = want_grad ? state_id(r, j) : PP0;
       pl.steps.push_back(st);
       cur = st.out;
     }
@@ -712,7 +729,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
       st.in = (r == 1 && j == 0) ? -1 : cur;
       int out;
       if (want_grad) {
-        out = first_state + (r - 1) * p + j;
+        out = state_id(r, j);
       } else {
         // the gathering first pass writes the other buffer; later passes run in place
         out = (j == 0) ? (cur == PP0 ? PP1 : PP0) : cur;
@@ -761,7 +778,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
 
   if (want_grad) {
     // ---------------- backward
-    for (int r = reps; r >= 1; --r) {
+    for (int r = reps; r >= (mgrad ? R + 1 : 1); --r) {
       for (int j = p - 1; j >= 0; --j) {
         const LayerPass &lp = pl.lp[j];
         PassStep st;
@@ -769,7 +786,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
         set_layout(st.A, lp);
         st.A.gate_mask = lp.gmask;
         st.A.layer = r;
-        st.in = first_state + (r - 1) * p + j;
+        st.in = state_id(r, j);
         const bool first = (r == reps && j == p - 1);
         if (first && diag) {
           st.A.flags |= F_LAMBDA_INIT | F_ENERGY;
@@ -799,6 +816,27 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
         pl.steps.push_back(st);
         lam_cur = out;
       }
+    }
+    if (mgrad) {
+      // ---------------- gradients of layers 0..R from lambda_R (closed form)
+      const MpsGradRegions g = mps_grad_regions(n, R);
+      const long long base = poff;
+      poff += g.total;
+      for (int kind : {K_MPS_GRAD, K_MPS_GHIGH, K_MPS_GRED, K_MPS_GENV}) {
+        PassStep st;
+        st.A = base_args(kind);
+        st.A.layer = R;
+        st.A.tiles = 1LL << (n - MPS_CHUNK_BITS);
+        st.A.em = ent_map(ent, n, R);
+        st.lam = (kind == K_MPS_GRAD) ? lam_cur : -1;
+        st.part_region = base;
+        pl.steps.push_back(st);
+      }
+      for (int k = 0; k <= R; ++k)
+        for (int q = 0; q < n; ++q) pl.param_dir[k * n + q] = {base + g.fin + (long long)k * n + q, 1, k * n + q};
+      pl.part_stride = poff;
+      for (auto &kv : pl.param_dir) pl.dir.push_back(kv.second);
+      return pl;
     }
     // ---------------- layer-0 gradients
     PassStep st;
@@ -861,11 +899,13 @@ std::string describe_plan(const Plan &pl) {
     s += buf;
   }
   if (pl.mps_layers > 0) {
-    snprintf(buf, sizeof(buf), "  closed-form layers 1..%d (bond dimension up to %d), %lld table floats per job\n",
-             pl.mps_layers, 1 << pl.mps_layers, pl.mps_elems);
+    snprintf(buf, sizeof(buf), "  closed-form layers 1..%d (bond dimension up to %d), %lld table floats per job%s\n",
+             pl.mps_layers, 1 << pl.mps_layers, pl.mps_elems,
+             pl.mps_grad ? "; their gradients from lambda and the matrix product" : "");
     s += buf;
   }
-  static const char *kinds[] = {"fwd", "bwd", "grad_l0", "lambda_xy", "wht", "mps", "mps_tab"};
+  static const char *kinds[] = {"fwd",     "bwd",       "grad_l0",   "lambda_xy", "wht",     "mps",
+                                "mps_tab", "mps_grad", "mps_ghigh", "mps_gred", "mps_genv"};
   for (const PassStep &st : pl.steps) {
     snprintf(buf, sizeof(buf), "  %-9s layer=%d tb=%d c=%d a=%d gates=0x%x load=%d store=%d flags=0x%x in=%d lam=%d out=%d\n",
              kinds[st.A.kind], st.A.layer, st.A.tb, st.A.c, st.A.a, st.A.gate_mask, st.A.load_mode, st.A.store_mode,
@@ -1191,9 +1231,21 @@ static int run_plan(gvqe_ansatz_s *a, gvqe_hamiltonian_s *h, Plan *pl, const voi
       if (A.kind == K_MPS_TAB) {
         A.out = mps_tab;
         A.out_stride = pl->mps_elems;
-      } else if (A.kind == K_MPS) {
+      } else if (A.kind >= K_MPS) {
         A.in = mps_tab;
         A.in_stride = pl->mps_elems;
+        if (A.kind >= K_MPS_GRAD) {
+          // the chunk vectors (floats) inside this step's partial region
+          const MpsGradRegions g = mps_grad_regions(A.n, A.layer);
+          float *lall = reinterpret_cast<float *>(A.part + g.lall);
+          if (A.kind == K_MPS_GRAD) {
+            A.out = lall;
+            A.out_stride = pl->part_stride * 2;
+          } else if (A.kind == K_MPS_GHIGH) {
+            A.lam_in = lall;
+            A.lam_stride = pl->part_stride * 2;
+          }
+        }
       }
       if (!st.xy) {
         GV_CUDA(launch_step(prec, A, jobs, 0, s));

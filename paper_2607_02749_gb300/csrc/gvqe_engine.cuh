@@ -28,6 +28,10 @@ enum PassKind : int {
   K_WHT = 4,        // unnormalised Walsh-Hadamard butterflies (diagonal table build)
   K_MPS = 5,        // a leading layer's state written in closed form (gvqe_mps.cu)
   K_MPS_TAB = 6,    // the contracted site-tensor tables K_MPS reads
+  K_MPS_GRAD = 7,   // gradients of the closed-form layers: one pass over lambda (environments)
+  K_MPS_GHIGH = 8,  // ... the qubits above the 2^13-amplitude chunk, per chunk and qubit
+  K_MPS_GRED = 9,   // ... fixed-order FP64 sums of the per-CTA partials
+  K_MPS_GENV = 10,  // ... the qubits inside the chunk, from the summed environments
 };
 
 enum LoadMode : int {
@@ -159,6 +163,7 @@ enum PassFlags : int {
   F_WRITE_LAMBDA = 8,  // K_LAMBDA_XY: write lambda
   F_ACCUM = 16,        // K_LAMBDA_XY: add onto lambda already written (group chunks)
   F_COMPLEX = 64,      // the complex path (full EfficientSU2 layers: RY then RZ)
+  F_MPS_SITES = 128,   // K_MPS_TAB: also write the site matrices and their derivatives
 };
 
 struct PassArgs {
@@ -210,9 +215,13 @@ constexpr int MPS_MAX_LAYERS = 4;   // bond dimension up to 16 (GVQE_OPT_MPS_LAY
 constexpr int MPS_AUTO_LAYERS = 3;  // the default: a bond-16 stage costs about a tile pass
 constexpr int MPS_MIN_QUBITS = 14;
 constexpr int MPS_CHUNK_BITS = 13;
+// With gradients (K_MPS_TAB flag F_MPS_SITES) the region also holds the site
+// matrices themselves, [q][y][a][b], and their derivatives by each layer's
+// angle, [k][q][y][a][b] for k = 0..r (FP32, rounded from FP64).
 struct MpsDims {
   int D, h1, h2;
   long long lo, mid, m1, r2, total;
+  long long sites, dsites, total_grad;
 };
 __host__ __device__ inline MpsDims mps_dims(int n, int r) {
   MpsDims d;
@@ -225,7 +234,34 @@ __host__ __device__ inline MpsDims mps_dims(int n, int r) {
   d.m1 = d.mid + 64 * D * D;
   d.r2 = d.m1 + (1LL << d.h1) * D * D;
   d.total = d.r2 + (1LL << d.h2) * D;
+  d.sites = (d.total + 3) / 4 * 4;
+  d.dsites = d.sites + (long long)n * 2 * D * D;
+  d.total_grad = d.dsites + (long long)(r + 1) * n * 2 * D * D;
   return d;
+}
+// Gradient scratch of one job (doubles), for layer r's stage at n qubits:
+// per-CTA partials of the pass over lambda (mu: [128][D], P: [64][D][D]), the
+// left-contracted vector of every chunk (floats), per-block partials of the
+// high qubits, their fixed-order sums, and the final gradients [k][q].
+constexpr int MPS_GRAD_CTAS = 256;
+struct MpsGradRegions {
+  long long gc, nb3, v1, k;
+  long long part1, lall, part3, red, fin, total;
+};
+__host__ __device__ inline MpsGradRegions mps_grad_regions(int n, int r) {
+  MpsGradRegions g;
+  const long long D = 1LL << r, chunks = 1LL << (n - MPS_CHUNK_BITS);
+  g.gc = chunks < MPS_GRAD_CTAS ? chunks : MPS_GRAD_CTAS;
+  g.nb3 = (chunks + 255) / 256;
+  g.v1 = 128 * D + 64 * D * D;
+  g.k = n - MPS_CHUNK_BITS;
+  g.part1 = 0;
+  g.lall = g.part1 + g.gc * g.v1;
+  g.part3 = g.lall + (chunks * D + 1) / 2;
+  g.red = g.part3 + g.k * (r + 1) * g.nb3;
+  g.fin = g.red + g.v1 + g.k * (r + 1);
+  g.total = g.fin + (long long)n * (r + 1);
+  return g;
 }
 
 // One output of the final reduction: the sum of `count` partials starting at
@@ -270,6 +306,14 @@ cudaError_t launch_trig(int prec, const double *params, long long count, void *c
 // gate_mask = the qubits layer r has rotated at this stage, em = the entangler
 // (EF_DIFF or EF_PREFIX), out = table region (out_stride floats per job).
 // K_MPS: in = that region (in_stride), out = the state, tiles = 2^(n - 13) chunks.
+// Gradient steps (layer = r, tiles = chunks; regions of mps_grad_regions inside
+// the partial buffer, part_stride doubles per job):
+//   K_MPS_GRAD:  in = tables, lam_in = lambda_r (lam_stride), part = per-CTA partials,
+//                out = chunk vectors (floats, out_stride floats per job)
+//   K_MPS_GHIGH: in = tables, lam_in = chunk vectors (lam_stride floats), part = block partials
+//   K_MPS_GRED:  part = per-CTA partials, lam_in = block partials (lam_stride doubles),
+//                epart = sums
+//   K_MPS_GENV:  in = tables, epart = sums, out = gradients [k][q] (out_stride doubles)
 cudaError_t launch_mps(int prec, const PassArgs &A, int jobs, cudaStream_t s);
 cudaError_t launch_minlayer(const uint8_t *mask, int jobs, int n, int P, int none_value, int *out,
                             cudaStream_t s);

@@ -61,6 +61,7 @@ struct Plan {
   std::vector<RedEntry> dir;  // energy entry first, then one per parameter
   int final_buf = -1;         // state-only plans: buffer of the final state
   int mps_layers = 0;         // leading layers written in closed form (K_MPS steps)
+  bool mps_grad = false;      // ... and their gradients from lambda and the matrix product
   long long mps_elems = 0;    // floats of closed-form tables per job (one stage at a time)
   DevBuf d_dir;
   int d_dir_count = 0;

@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(XYC_NT) k_lambda_xy_c(const PassArgs A) {
 
 cudaError_t launch_pass(int prec, const PassArgs &A, int jobs, int nterm, cudaStream_t s) {
   if (jobs < 1 || A.tiles < 1) return cudaErrorInvalidValue;
-  if (A.kind == K_MPS || A.kind == K_MPS_TAB) return launch_mps(prec, A, jobs, s);
+  if (A.kind >= K_MPS) return launch_mps(prec, A, jobs, s);
   if (A.kind == K_LAMBDA_XY && (A.flags & F_COMPLEX)) {
     const size_t smem = xyc_smem_bytes(prec, A.ngroups, nterm);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;

@@ -46,14 +46,17 @@ __device__ __forceinline__ double ry_entry(float2 g, int out, int in) {
   return out == in ? (double)g.x : (out ? (double)g.y : -(double)g.y);
 }
 
-// Site matrix entry A_q[y](a, b) of the stage (layer r, layer r's rotated qubits rot).
+// Site matrix entry A_q[y](a, b) of the stage (layer r, layer r's rotated qubits
+// rot), or, for dr >= 0, its derivative by layer dr's angle of qubit q: that
+// layer's factor becomes d cos(t/2)/dt = -sin(t/2)/2, d sin(t/2)/dt = cos(t/2)/2.
 template <int FORM>
-__device__ double site_entry(const float2 *cs, int pstride, int q, int y, int a, int b, int r, bool rot) {
+__device__ double site_entry(const float2 *cs, int pstride, int q, int y, int a, int b, int r, bool rot,
+                             int dr = -1) {
   if (q == 0 && a != 0) return 0.0;  // the left end's bond is 0
   auto bit = [](int v, int k) { return (v >> (k - 1)) & 1; };
   const float2 f = cs[q];
   const int x0 = (FORM == EF_PREFIX) ? bit(b, 1) : (bit(b, 1) ^ bit(a, 1));
-  double v = x0 ? (double)f.y : (double)f.x;
+  double v = (dr == 0) ? (x0 ? 0.5 * (double)f.x : -0.5 * (double)f.y) : (x0 ? (double)f.y : (double)f.x);
   for (int k = 1; k <= r; ++k) {
     int out, in;
     if (FORM == EF_PREFIX) {
@@ -67,7 +70,11 @@ __device__ double site_entry(const float2 *cs, int pstride, int q, int y, int a,
       if (out != in) return 0.0;
       continue;
     }
-    v *= ry_entry(cs[(size_t)k * pstride + q], out, in);
+    const float2 g = cs[(size_t)k * pstride + q];
+    if (k == dr)
+      v *= (out == in) ? -0.5 * (double)g.y : (out ? 0.5 * (double)g.x : -0.5 * (double)g.x);
+    else
+      v *= ry_entry(g, out, in);
   }
   return v;
 }
@@ -120,6 +127,22 @@ __global__ void __launch_bounds__(TAB_NT) k_mps_tab(const PassArgs A) {
   const MpsDims d = mps_dims(n, r);
   const MpsItems its = mps_items(d);
   const float2 *cs = reinterpret_cast<const float2 *>(A.cs) + (size_t)(A.job0 + job) * A.P;
+  const long long row_blocks = (its.total + TAB_NT - 1) / TAB_NT;
+  if (blockIdx.x >= row_blocks) {
+    // the site matrices [q][y][a][b] and their derivatives [k][q][y][a][b], one entry per thread
+    const long long e = (blockIdx.x - row_blocks) * TAB_NT + tid;
+    const long long ns = (long long)n * 2 * DD;
+    if (e >= ns * (r + 2)) return;
+    const int k = (int)(e / ns) - 1;  // -1: the matrices themselves
+    const long long w = e % ns;
+    const int b = (int)(w % D), a = (int)((w / D) % D), y = (int)((w / DD) & 1), q = (int)(w / (2 * DD));
+    const bool rot = (A.gate_mask >> q) & 1u;
+    const double v = (FORM == EF_PREFIX) ? site_entry<EF_PREFIX>(cs, A.pstride, q, y, a, b, r, rot, k)
+                                         : site_entry<EF_DIFF>(cs, A.pstride, q, y, a, b, r, rot, k);
+    float *tab = reinterpret_cast<float *>(A.out) + (size_t)job * A.out_stride;
+    tab[d.sites + e] = (float)v;  // d.dsites = d.sites + ns
+    return;
+  }
   const long long i0 = (long long)blockIdx.x * TAB_NT;
   const long long i1 = (i0 + TAB_NT < its.total) ? i0 + TAB_NT : its.total;
   const int qa = mps_q_first(its, d, i0), qb = mps_q_last(its, d, n, i1 - 1);
@@ -306,12 +329,457 @@ __global__ void __launch_bounds__(WR_NT) k_mps_write(const PassArgs A) {
   if constexpr (STAGE) cp_async_wait<0>();
 }
 
+// ------------------------------------------------- closed-form gradients --
+// For the angles of layers 0..r (the closed-form ones), with lambda_r the
+// adjoint state at the output of layer r (the backward passes of layers
+// D..r+1 bring it there),
+//
+//   dE/dtheta_{k,q} = 2 <lambda_r | d psi_r / d theta_{k,q}>,
+//
+// and d psi_r / d theta_{k,q} is the same matrix product with site q's matrix
+// replaced by its derivative dA_q^k.  Split psi_r(y) = L(y_0..6) M(y_7..12) R_c
+// (R_c = the column vector of the chunk's high qubits), and contract lambda
+// once, chunk by chunk (k_mps_grad):
+//   mu(y_0..6)  = sum over chunks and y_7..12 of lambda(y) M(y_7..12) R_c  (row-side qubits 0..6)
+//   P(y_7..12)  = sum over chunks of [sum_{y_0..6} lambda(y) L(y_0..6)] (x) R_c  (qubits 7..12)
+//   l_c         = sum_{y_0..12} lambda(y) L(y_0..6) M(y_7..12)  (one row vector per chunk)
+// Then qubits 0..12 take their gradients from mu and P (k_mps_genv), and the
+// high qubits from l_c, per chunk: l_c A_13 .. dA_q .. A_{n-1} 1 (k_mps_ghigh).
+// Sums run in FP32 inside a chunk (a warp's lanes, a thread's rows) and in
+// FP64 across chunks and CTAs, in a fixed order.
+
+// Sum of D values over the 32 lanes: after log2(D) halving exchanges a lane
+// holds one value (its index from the lane's top bits), then plain sums.
+template <int D>
+__device__ __forceinline__ float warp_tsum(const float (&v)[D], int lane, int &idx) {
+  float cur[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) cur[j] = v[j];
+  idx = 0;
+  int sh = 16;
+#pragma unroll
+  for (int cnt = D; cnt > 1; cnt >>= 1, sh >>= 1) {
+    const int half = cnt / 2;
+    const bool hi = (lane & sh) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const float keep = hi ? cur[half + j] : cur[j];
+      const float send = hi ? cur[j] : cur[half + j];
+      cur[j] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+    }
+    idx = 2 * idx + (hi ? 1 : 0);
+  }
+  float r = cur[0];
+  for (; sh >= 1; sh >>= 1) r += __shfl_xor_sync(0xffffffffu, r, sh);
+  return r;
+}
+
+constexpr int GR_NT = 256;
+
+// One pass over lambda_r.  The chunk set-up (R_c staged with cp.async, the
+// row vectors m = M R_c) is the writer's; then warp w takes rows w, w + 8, ..:
+// lane l's four amplitudes 4l..4l+3 of a row add lambda * m into its mu
+// accumulators and lambda * L into the row's sum, reduced over the warp.
+// Every 8 chunks the mu and P accumulators (FP32) are added into this CTA's
+// FP64 partials.
+template <int D>
+__global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
+  extern __shared__ __align__(16) float dyn[];  // [64][b][a] transposed mid matrices, then [8][D][128] scratch
+  float *sM = dyn;
+  float *scr = dyn + 64 * D * D;
+  __shared__ __align__(16) float sm[64 * 2 * D];
+  __shared__ __align__(16) float sb[2][D * D + D];
+  __shared__ float sr[D];
+  __shared__ float sL1[64 * D];
+  __shared__ float sLc[GR_NT / 32][D];
+  constexpr bool STAGE = D >= 4;
+  constexpr int NCH = (D * D + D) / 4;
+  constexpr int NP = (64 * D * D) / GR_NT;  // P entries per thread
+  constexpr int NMU = (128 * D) / GR_NT;    // mu sums per thread in a flush
+  constexpr int FLUSH = 8;
+  const int r = (D == 2) ? 1 : (D == 4 ? 2 : 3);
+  const MpsDims d = mps_dims(A.n, r);
+  const MpsGradRegions gr = mps_grad_regions(A.n, r);
+  const int job = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const float *tab = reinterpret_cast<const float *>(A.in) + (size_t)job * A.in_stride;
+  const float *lam = reinterpret_cast<const float *>(A.lam_in) + (size_t)job * A.lam_stride;
+  double *part = A.part + (size_t)job * A.part_stride + (size_t)blockIdx.x * gr.v1;
+  float *lall = reinterpret_cast<float *>(A.out) + (size_t)job * A.out_stride;
+  const long long chunks = A.tiles;
+  const long long mask1 = (1LL << d.h1) - 1;
+#pragma unroll
+  for (int k = 0; k < NMU; ++k) part[tid + GR_NT * k] = 0.0;  // mu^T [a][128]
+#pragma unroll
+  for (int k = 0; k < NP; ++k) part[128 * D + tid + GR_NT * k] = 0.0;  // P [64][D][D]
+  auto stage = [&](long long c, int buf) {
+    if (tid < NCH) {
+      const float *src = (tid < D * D / 4) ? tab + d.m1 + (c & mask1) * D * D + 4 * tid
+                                           : tab + d.r2 + (c >> d.h1) * D + 4 * (tid - D * D / 4);
+      cp_async16(&sb[buf][4 * tid], src);
+    }
+    cp_async_commit();
+  };
+  if constexpr (STAGE) stage(blockIdx.x, 0);
+  for (int i = tid; i < 64 * D * D; i += GR_NT) {
+    const int ym = i / (D * D), b = (i / D) % D, a = i % D;
+    sM[i] = tab[d.mid + (ym * D + a) * D + b];
+  }
+  unsigned long long L01[D], L23[D], mu01[D], mu23[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const float4 l = *reinterpret_cast<const float4 *>(tab + d.lo + a * 128 + 4 * lane);
+    L01[a] = pk(l.x, l.y);
+    L23[a] = pk(l.z, l.w);
+    mu01[a] = mu23[a] = 0ull;
+  }
+  float Pacc[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) Pacc[k] = 0.f;
+  auto flush = [&]() {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const float2 m01 = upk(mu01[a]), m23 = upk(mu23[a]);
+      *reinterpret_cast<float4 *>(&scr[(w * D + a) * 128 + 4 * lane]) = make_float4(m01.x, m01.y, m23.x, m23.y);
+      mu01[a] = mu23[a] = 0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NMU; ++k) {
+      const int v = tid + GR_NT * k;
+      float t = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < GR_NT / 32; ++ww) t += scr[ww * D * 128 + v];
+      part[v] += (double)t;
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      part[128 * D + tid + GR_NT * k] += (double)Pacc[k];
+      Pacc[k] = 0.f;
+    }
+  };
+  int par = 0, since = 0;
+  for (long long c = blockIdx.x; c < chunks; c += gridDim.x, par ^= 1) {
+    if constexpr (STAGE) cp_async_wait<0>();
+    __syncthreads();
+    if constexpr (STAGE) {
+      if (c + gridDim.x < chunks) stage(c + gridDim.x, par ^ 1);
+      if (tid < D) {
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) acc = fmaf(sb[par][tid * D + b], sb[par][D * D + b], acc);
+        sr[tid] = acc;
+      }
+    } else {
+      if (tid < D) {
+        const float *m1 = tab + d.m1 + ((c & mask1) * D + tid) * D;
+        const float *r2 = tab + d.r2 + (c >> d.h1) * D;
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) acc = fmaf(m1[b], r2[b], acc);
+        sr[tid] = acc;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < 64 * D; i += GR_NT) {
+      const float *mcol = sM + (i / D) * D * D + (i % D);
+      float acc = 0.f;
+#pragma unroll
+      for (int b = 0; b < D; ++b) acc = fmaf(mcol[b * D], sr[b], acc);
+      *reinterpret_cast<float2 *>(&sm[2 * i]) = make_float2(acc, acc);
+    }
+    __syncthreads();
+    const float *lc = lam + (c << MPS_CHUNK_BITS) + 4 * lane;
+#pragma unroll 2
+    for (int ym = w; ym < 64; ym += GR_NT / 32) {
+      const float4 lv = __ldcs(reinterpret_cast<const float4 *>(lc + ym * 128));
+      const unsigned long long l01 = pk(lv.x, lv.y), l23 = pk(lv.z, lv.w);
+      const ulonglong2 *mv = reinterpret_cast<const ulonglong2 *>(sm + ym * 2 * D);
+#pragma unroll
+      for (int a = 0; a < D; a += 2) {
+        const ulonglong2 m = mv[a / 2];
+        mu01[a] = fma2(l01, m.x, mu01[a]);
+        mu23[a] = fma2(l23, m.x, mu23[a]);
+        mu01[a + 1] = fma2(l01, m.y, mu01[a + 1]);
+        mu23[a + 1] = fma2(l23, m.y, mu23[a + 1]);
+      }
+      float sv[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const float2 t = upk(fma2(L23[a], l23, mul2(L01[a], l01)));
+        sv[a] = t.x + t.y;
+      }
+      int idx;
+      const float tot = warp_tsum<D>(sv, lane, idx);
+      if ((lane & (32 / D - 1)) == 0) sL1[ym * D + idx] = tot;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int e = tid + GR_NT * k;  // (ym D + a) D + b
+      Pacc[k] = fmaf(sL1[e / D], sr[e % D], Pacc[k]);
+    }
+    {
+      // l_c(b) = sum over (ym, a) of sL1[ym][a] M(ym)(a, b): thread (g, b) takes every
+      // (GR_NT / D)-th (ym, a), then the warp and the CTA sum over g
+      const int b = tid % D, g = tid / D;
+      float x = 0.f;
+      for (int i = g; i < 64 * D; i += GR_NT / D) x = fmaf(sL1[i], sM[((i / D) * D + b) * D + (i % D)], x);
+#pragma unroll
+      for (int off = D; off < 32; off <<= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      if (lane < D) sLc[w][lane] = x;
+    }
+    __syncthreads();
+    if (tid < D) {
+      float t = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < GR_NT / 32; ++ww) t += sLc[ww][tid];
+      lall[c * D + tid] = t;
+    }
+    if (++since == FLUSH) {
+      flush();
+      since = 0;
+    }
+  }
+  if (since > 0) flush();
+  if constexpr (STAGE) cp_async_wait<0>();
+}
+
+// High qubits: block (x, q - 13) takes chunks 256 x .. 256 x + 255 and qubit q.
+// Thread c forms u = l_c A_13 .. A_{q-1} and s = A_{q+1} .. A_{n-1} 1 and adds
+// u dA_q^k s for every layer k <= r; the block's FP64 sums go to its partials.
+template <int D>
+__global__ void __launch_bounds__(256) k_mps_ghigh(const PassArgs A) {
+  constexpr int DD = D * D;
+  constexpr int RMAX = 3;
+  __shared__ float sA[17 * 2 * DD];
+  __shared__ float sdA[(RMAX + 1) * 2 * DD];
+  __shared__ double red[8][RMAX + 1];
+  const int r = (D == 2) ? 1 : (D == 4 ? 2 : 3);
+  const int n = A.n, K = n - MPS_CHUNK_BITS, q = MPS_CHUNK_BITS + blockIdx.y, job = blockIdx.z;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const MpsDims d = mps_dims(n, r);
+  const MpsGradRegions gr = mps_grad_regions(n, r);
+  const float *tab = reinterpret_cast<const float *>(A.in) + (size_t)job * A.in_stride;
+  const float *lall = reinterpret_cast<const float *>(A.lam_in) + (size_t)job * A.lam_stride;
+  double *part = A.part + (size_t)job * A.part_stride;
+  for (int i = tid; i < K * 2 * DD; i += 256) sA[i] = tab[d.sites + (long long)MPS_CHUNK_BITS * 2 * DD + i];
+  for (int i = tid; i < (r + 1) * 2 * DD; i += 256) {
+    const int k = i / (2 * DD), e = i % (2 * DD);
+    sdA[i] = tab[d.dsites + ((long long)k * n + q) * 2 * DD + e];
+  }
+  __syncthreads();
+  const long long c = (long long)blockIdx.x * 256 + tid;
+  float val[RMAX + 1] = {0.f, 0.f, 0.f, 0.f};
+  if (c < A.tiles) {
+    float u[D], sv[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      u[a] = lall[c * D + a];
+      sv[a] = 1.f;
+    }
+    for (int j = MPS_CHUNK_BITS; j < q; ++j) {
+      const float *M = sA + ((j - MPS_CHUNK_BITS) * 2 + (int)((c >> (j - MPS_CHUNK_BITS)) & 1)) * DD;
+      float t[D];
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc = fmaf(u[a], M[a * D + b], acc);
+        t[b] = acc;
+      }
+#pragma unroll
+      for (int b = 0; b < D; ++b) u[b] = t[b];
+    }
+    for (int j = n - 1; j > q; --j) {
+      const float *M = sA + ((j - MPS_CHUNK_BITS) * 2 + (int)((c >> (j - MPS_CHUNK_BITS)) & 1)) * DD;
+      float t[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) acc = fmaf(M[a * D + b], sv[b], acc);
+        t[a] = acc;
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) sv[a] = t[a];
+    }
+    const int yq = (int)((c >> (q - MPS_CHUNK_BITS)) & 1);
+    for (int k = 0; k <= r; ++k) {
+      const float *M = sdA + (k * 2 + yq) * DD;
+      float acc = 0.f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float ra = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) ra = fmaf(M[a * D + b], sv[b], ra);
+        acc = fmaf(u[a], ra, acc);
+      }
+      val[k] = acc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k <= RMAX; ++k) {
+    float x = val[k];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) red[w][k] = (double)x;
+  }
+  __syncthreads();
+  if (tid <= r) {
+    double t = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) t += red[ww][tid];
+    part[gr.part3 + ((long long)(q - MPS_CHUNK_BITS) * (r + 1) + tid) * gr.nb3 + blockIdx.x] = t;
+  }
+}
+
+// Fixed-order FP64 sums: value v < v1 over the CTAs of k_mps_grad, the rest
+// (high qubit, layer) over the blocks of k_mps_ghigh.
+__global__ void __launch_bounds__(128) k_mps_gred(const PassArgs A) {
+  const int r = A.layer, job = blockIdx.y;
+  const MpsGradRegions gr = mps_grad_regions(A.n, r);
+  const long long v = (long long)blockIdx.x * 128 + threadIdx.x;
+  if (v >= gr.v1 + gr.k * (r + 1)) return;
+  const double *p = A.part + (size_t)job * A.part_stride;
+  double t = 0.0;
+  if (v < gr.v1) {
+    for (long long c = 0; c < gr.gc; ++c) t += p[gr.part1 + c * gr.v1 + v];
+  } else {
+    const long long i = v - gr.v1;
+    for (long long b = 0; b < gr.nb3; ++b) t += p[gr.part3 + i * gr.nb3 + b];
+  }
+  A.part[(size_t)job * A.part_stride + gr.red + v] = t;
+}
+
+// Gradients of qubits 0..12 (block q) from the summed mu and P, and the high
+// qubits' sums copied (block 13).  Qubit q in 0..6: thread y (a pattern of
+// qubits 0..6) forms x = e_0 A_0 .. A_{q-1} and s = A_{q+1} .. A_6 mu(y);
+// qubit q in 7..12: thread (y, a) (a pattern of qubits 7..12 and a row) forms
+// x = e_a A_7 .. A_{q-1} and s = A_{q+1} .. A_12 P(y)(a, :); each adds
+// x dA_q^k s, summed in FP64.
+template <int D>
+__global__ void __launch_bounds__(256) k_mps_genv(const PassArgs A) {
+  constexpr int DD = D * D;
+  constexpr int RMAX = 3;
+  __shared__ double red[8][RMAX + 1];
+  const int r = (D == 2) ? 1 : (D == 4 ? 2 : 3);
+  const int n = A.n, q = blockIdx.x, job = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const MpsDims d = mps_dims(n, r);
+  const MpsGradRegions gr = mps_grad_regions(n, r);
+  const float *tab = reinterpret_cast<const float *>(A.in) + (size_t)job * A.in_stride;
+  const double *sums = A.part + (size_t)job * A.part_stride + gr.red;
+  double *fin = A.part + (size_t)job * A.part_stride + gr.fin;
+  if (q == MPS_CHUNK_BITS) {
+    for (int i = tid; i < gr.k * (r + 1); i += 256) {
+      const int qq = MPS_CHUNK_BITS + i / (r + 1), k = i % (r + 1);
+      fin[(long long)k * n + qq] = 2.0 * sums[gr.v1 + i];
+    }
+    return;
+  }
+  auto site = [&](int j, int y) { return tab + d.sites + ((long long)j * 2 + y) * DD; };
+  const bool lo = q < 7;
+  const int nitems = lo ? 128 : 64 * D;
+  double acc[RMAX + 1] = {0.0, 0.0, 0.0, 0.0};
+  for (int it = tid; it < nitems; it += 256) {
+    const int pat = lo ? it : it / D, a0 = lo ? 0 : it % D;
+    const int q0 = lo ? 0 : 7, q1 = lo ? 7 : 13;
+    float x[D], sv[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      x[a] = (a == a0) ? 1.f : 0.f;
+      sv[a] = lo ? (float)sums[(long long)a * 128 + pat] : (float)sums[128 * D + ((long long)pat * D + a0) * D + a];
+    }
+    for (int j = q0; j < q; ++j) {
+      const float *M = site(j, (pat >> (j - q0)) & 1);
+      float t[D];
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        float s = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) s = fmaf(x[a], M[a * D + b], s);
+        t[b] = s;
+      }
+#pragma unroll
+      for (int b = 0; b < D; ++b) x[b] = t[b];
+    }
+    for (int j = q1 - 1; j > q; --j) {
+      const float *M = site(j, (pat >> (j - q0)) & 1);
+      float t[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float s = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) s = fmaf(M[a * D + b], sv[b], s);
+        t[a] = s;
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) sv[a] = t[a];
+    }
+    const int yq = (pat >> (q - q0)) & 1;
+    for (int k = 0; k <= r; ++k) {
+      const float *M = tab + d.dsites + (((long long)k * n + q) * 2 + yq) * DD;
+      double s = 0.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float ra = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) ra = fmaf(M[a * D + b], sv[b], ra);
+        s += (double)x[a] * (double)ra;
+      }
+      acc[k] += s;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k <= RMAX; ++k) {
+    double x = acc[k];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) red[w][k] = x;
+  }
+  __syncthreads();
+  if (tid <= r) {
+    double t = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) t += red[ww][tid];
+    fin[(long long)tid * n + q] = 2.0 * t;
+  }
+}
+
+template <int D>
+cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
+  const MpsGradRegions gr = mps_grad_regions(A.n, A.layer);
+  switch (A.kind) {
+    case K_MPS_GRAD: {
+      const size_t smem = (size_t)(64 * D * D + (GR_NT / 32) * D * 128) * sizeof(float);
+      cudaFuncSetAttribute(k_mps_grad<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_mps_grad<D><<<dim3((unsigned)gr.gc, (unsigned)jobs), GR_NT, smem, s>>>(A);
+      break;
+    }
+    case K_MPS_GHIGH:
+      k_mps_ghigh<D><<<dim3((unsigned)gr.nb3, (unsigned)gr.k, (unsigned)jobs), 256, 0, s>>>(A);
+      break;
+    case K_MPS_GRED:
+      k_mps_gred<<<dim3((unsigned)((gr.v1 + gr.k * (A.layer + 1) + 127) / 128), (unsigned)jobs), 128, 0, s>>>(A);
+      break;
+    default:  // K_MPS_GENV
+      k_mps_genv<D><<<dim3(MPS_CHUNK_BITS + 1, (unsigned)jobs), 256, 0, s>>>(A);
+      break;
+  }
+  return cudaGetLastError();
+}
+
 template <int D>
 cudaError_t launch_mps_d(const PassArgs &A, int jobs, cudaStream_t s) {
+  if (A.kind >= K_MPS_GRAD) {
+    if constexpr (D <= 8) return launch_mps_grad_d<D>(A, jobs, s);
+    return cudaErrorInvalidValue;
+  }
   if (A.kind == K_MPS_TAB) {
     const MpsDims d = mps_dims(A.n, A.layer);
     const MpsItems its = mps_items(d);
-    const dim3 grid((unsigned)((its.total + TAB_NT - 1) / TAB_NT), (unsigned)jobs);
+    long long blocks = (its.total + TAB_NT - 1) / TAB_NT;
+    if (A.flags & F_MPS_SITES) blocks += ((long long)A.n * 2 * D * D * (A.layer + 2) + TAB_NT - 1) / TAB_NT;
+    const dim3 grid((unsigned)blocks, (unsigned)jobs);
     const size_t smem = (size_t)mps_tab_span(A.n, A.layer) * 2 * D * D * sizeof(double);
     if (A.em.form == EF_PREFIX) {
       if (smem > 48 * 1024)

@@ -316,16 +316,24 @@ def test_closed_form_layer_option_and_plans():
         finally:
             _lib.gvqe_destroy(a)
 
+    def steps_of(d):
+        return [ln.split()[0] for ln in d.splitlines()[1:] if ln.startswith("  ")
+                and not ln.startswith("  layer pass") and not ln.startswith("  closed-form")]
+
     d = desc(30, 6)
-    assert "closed-form layers 1..3 (bond dimension up to 8), 39936 table floats per job" in d
-    steps = [ln.split()[0] for ln in d.splitlines()[1:] if ln.startswith("  ") and not ln.startswith("  layer pass")
-             and not ln.startswith("  closed-form")]
-    # three stored states per layer for layers 1..3: a table build and a write each, then tile passes
-    assert steps[:18] == ["mps_tab", "mps"] * 9
-    assert steps[18:21] == ["fwd"] * 3 and "mps" not in steps[18:]
-    assert steps.count("fwd") == 9 and steps.count("bwd") == 18
-    # a fourth layer (bond dimension 16) on request
-    assert "closed-form layers 1..4 (bond dimension up to 16), 153600 table floats per job" in desc(30, 6, mps=4)
+    assert ("closed-form layers 1..3 (bond dimension up to 8), 59136 table floats per job; their gradients "
+            "from lambda and the matrix product") in d
+    # layer 3's final state in closed form, layers 4..6 as tile passes and their backward, then the
+    # gradients of layers 0..3 from lambda_3 (no backward passes and no layer-0 pass below layer 4)
+    assert steps_of(d) == (["mps_tab", "mps"] + ["fwd"] * 9 + ["bwd"] * 9
+                           + ["mps_grad", "mps_ghigh", "mps_gred", "mps_genv"])
+    # a fourth layer (bond dimension 16) on request: every stored state of layers 1..4 in closed form,
+    # the backward through every layer
+    d4 = desc(30, 6, mps=4)
+    assert "closed-form layers 1..4 (bond dimension up to 16), 153600 table floats per job\n" in d4
+    s4 = steps_of(d4)
+    assert s4[:24] == ["mps_tab", "mps"] * 12 and s4.count("fwd") == 6 and s4.count("bwd") == 18
+    assert s4[-1] == "grad_l0"
     for ent in (_lib.GVQE_ENT_FULL, _lib.GVQE_ENT_REVERSE_LINEAR):
         assert "closed-form layers 1..3 " in desc(20, 5, ent)
         assert "closed-form layers 1..2 " in desc(20, 3, ent)
