@@ -27,6 +27,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import os
 import statistics
@@ -773,15 +774,20 @@ def run_gvqe(args):
     # Each kind's share over its measured time is its algorithmic GB/s; the
     # implementation's own per-pass bytes (every tile pass reads and writes the
     # whole state) give the per-pass figure beside it.
-    prof = {k: _lib.gvqe_profile_read(k) for k in range(7)}
+    prof = {k: _lib.gvqe_profile_read(k) for k in range(11)}
     names = {0: "k_fwd", 1: "k_bwd", 2: "k_grad_l0", 3: "k_lambda_xy", 4: "k_wht", 5: "k_mps_write",
-             6: "k_mps_tab"}
+             6: "k_mps_tab", 7: "k_mps_grad", 8: "k_mps_ghigh", 9: "k_mps_gred", 10: "k_mps_genv"}
     dom = max(prof, key=lambda k: prof[k]["ms"])
     pk = prof[dom]
     peak, peak_src = measured_peaks()
     S_b, T_b = 4.0 * 2 ** n, 8.0 * 2 ** n
     evals = B * args.steps  # E+grad evaluations in the timed region (this rank)
-    alg_share = {0: (1 + 2 * reps) * S_b, 1: (4 * reps - 1) * S_b + T_b, 2: 2 * S_b}
+    # layers 1..R in closed form: with their gradients taken from lambda_R, k_bwd
+    # sweeps layers D..R+1 only, and the closed-form gradient kernels stand in for
+    # the backward of layers R..1 and layer 0 (4 R S + 2 S of the algorithmic count)
+    m = re.search(r"closed-form layers 1\.\.(\d+) .*their gradients", a.describe())
+    R_cf = int(m.group(1)) if m else 0
+    alg_share = {0: (1 + 2 * reps) * S_b, 1: (4 * (reps - R_cf) - 1) * S_b + T_b, 2: 2 * S_b}
     alg_step = ((6 * reps + 2) * S_b + T_b) * B
     def kind_alg(k):
         if not prof[k]["ms"] or k not in alg_share:
@@ -797,7 +803,9 @@ def run_gvqe(args):
         "kernel": names[dom], "launches": pk["launches"], "avg_launch_ms": pk["ms"] / launches_dom,
         "algorithmic_bytes_per_launch": alg_share.get(dom, 0.0) * evals / launches_dom,
         "bytes_rule": ("algorithmic: (6D+2) S + T per E+grad, one sweep per layer (forward S + 2DS, k_bwd "
-                       "(4D-1) S + T, k_grad_l0 2S); S = 4 B x 2^n real FP32 state, T = 8 B x 2^n FP64 table. "
+                       "(4D-1) S + T, k_grad_l0 2S; with layers 1..R in closed form and their gradients from "
+                       "lambda_R, k_bwd's share is (4(D-R)-1) S + T and the closed-form gradient kernels' "
+                       "(4R+2) S); S = 4 B x 2^n real FP32 state, T = 8 B x 2^n FP64 table. "
                        "Layer 0 is an analytic product state here, so the forward never writes it and k_grad_l0 "
                        "reads only lambda; the forward's stored states of layers 1..3 are written in closed "
                        "form (k_mps_tab + k_mps_write, write-only) and the rest by k_fwd tile passes, so the "
@@ -819,6 +827,12 @@ def run_gvqe(args):
         roofline["per_kind"]["forward"] = {
             "kinds": "k_fwd + k_mps_write + k_mps_tab", "ms": fwd_ms,
             "GBps_algorithmic": alg_share[0] * evals / (fwd_ms / 1000.0) / 1e9}
+    cfg_ms = sum(prof[k]["ms"] for k in (7, 8, 9, 10))
+    if R_cf and cfg_ms > 0:
+        roofline["per_kind"]["closed_form_gradients"] = {
+            "kinds": "k_mps_grad + k_mps_ghigh + k_mps_gred + k_mps_genv", "ms": cfg_ms, "layers": R_cf,
+            "GBps_algorithmic": (4 * R_cf + 2) * S_b * evals / (cfg_ms / 1000.0) / 1e9,
+            "rule": "stand-in for the backward of layers R..1 and layer 0: (4R + 2) S of the algorithmic count"}
     _lib.gvqe_profile_reset()
 
     # e2e through the public API: pinned host inputs in, results out, every step

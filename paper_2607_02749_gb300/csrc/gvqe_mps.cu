@@ -345,57 +345,43 @@ __global__ void __launch_bounds__(WR_NT) k_mps_write(const PassArgs A) {
 //   l_c         = sum_{y_0..12} lambda(y) L(y_0..6) M(y_7..12)  (one row vector per chunk)
 // Then qubits 0..12 take their gradients from mu and P (k_mps_genv), and the
 // high qubits from l_c, per chunk: l_c A_13 .. dA_q .. A_{n-1} 1 (k_mps_ghigh).
-// Sums run in FP32 inside a chunk (a warp's lanes, a thread's rows) and in
-// FP64 across chunks and CTAs, in a fixed order.
-
-// Sum of D values over the 32 lanes: after log2(D) halving exchanges a lane
-// holds one value (its index from the lane's top bits), then plain sums.
-template <int D>
-__device__ __forceinline__ float warp_tsum(const float (&v)[D], int lane, int &idx) {
-  float cur[D];
-#pragma unroll
-  for (int j = 0; j < D; ++j) cur[j] = v[j];
-  idx = 0;
-  int sh = 16;
-#pragma unroll
-  for (int cnt = D; cnt > 1; cnt >>= 1, sh >>= 1) {
-    const int half = cnt / 2;
-    const bool hi = (lane & sh) != 0;
-#pragma unroll
-    for (int j = 0; j < half; ++j) {
-      const float keep = hi ? cur[half + j] : cur[j];
-      const float send = hi ? cur[j] : cur[half + j];
-      cur[j] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
-    }
-    idx = 2 * idx + (hi ? 1 : 0);
-  }
-  float r = cur[0];
-  for (; sh >= 1; sh >>= 1) r += __shfl_xor_sync(0xffffffffu, r, sh);
-  return r;
-}
+// Sums run in FP32 inside a chunk (a thread's 32 rows or columns, the four
+// column quarters) and over 8 chunks, then in FP64 across chunks and CTAs, in
+// a fixed order.
 
 constexpr int GR_NT = 256;
+constexpr int LAM_LD = 132;  // floats per staged lambda row (128 + 4: 16-byte aligned, see k_mps_grad)
 
-// One pass over lambda_r.  The chunk set-up (R_c staged with cp.async, the
-// row vectors m = M R_c) is the writer's; then warp w takes rows w, w + 8, ..:
-// lane l's four amplitudes 4l..4l+3 of a row add lambda * m into its mu
-// accumulators and lambda * L into the row's sum, reduced over the warp.
-// Every 8 chunks the mu and P accumulators (FP32) are added into this CTA's
-// FP64 partials.
+// One pass over lambda_r, chunk by chunk, each chunk's 64 x 128 lambda block
+// (rows: qubits 7..12, columns: qubits 0..6) staged in shared memory by
+// cp.async while the previous chunk is contracted.  Per chunk, with m = M R_c
+// as in the writer:
+//   Lambda1 = lambda_c L     (64 x D; thread (k-quarter, row) keeps one row's D sums
+//                             over 32 columns, the quarters are added in shared memory)
+//   mu     += lambda_c^T m   (128 x D; thread (half, column) keeps one column's D sums
+//                             over 32 rows, in registers across chunks)
+//   P      += Lambda1 (x) R_c,  l_c = sum_rows Lambda1(row) M(row)
+// Both products read the block conflict-free: rows are 132 floats apart and the
+// k order of the Lambda1 product is rotated per lane (lane 8i + j starts at
+// column offset i, so bank 4j + i + k differs across the warp).  Every 8 chunks
+// the FP32 accumulators are added into this CTA's FP64 partials.
 template <int D>
 __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
-  extern __shared__ __align__(16) float dyn[];  // [64][b][a] transposed mid matrices, then [8][D][128] scratch
-  float *sM = dyn;
-  float *scr = dyn + 64 * D * D;
-  __shared__ __align__(16) float sm[64 * 2 * D];
+  // dynamic: two staged lambda blocks, the transposed mid matrices [64][b][a],
+  // the row vectors of qubits 0..6 [128][D], quarter partials [4][64][D]
+  extern __shared__ __align__(16) float dyn[];
+  float *slam = dyn;                        // [2][64][LAM_LD]
+  float *sM = slam + 2 * 64 * LAM_LD;       // [64][D][D]
+  float *sLo = sM + 64 * D * D;             // [128][D]
+  float *sQ = sLo + 128 * D;                // [4][64][D]
+  __shared__ __align__(16) float sm[64 * D];  // m per row (8-byte pairs read as f32x2)
   __shared__ __align__(16) float sb[2][D * D + D];
   __shared__ float sr[D];
   __shared__ float sL1[64 * D];
   __shared__ float sLc[GR_NT / 32][D];
-  constexpr bool STAGE = D >= 4;
+  constexpr bool STAGE = D >= 4;  // the chunk's matrix and vector by cp.async (16-byte pieces)
   constexpr int NCH = (D * D + D) / 4;
   constexpr int NP = (64 * D * D) / GR_NT;  // P entries per thread
-  constexpr int NMU = (128 * D) / GR_NT;    // mu sums per thread in a flush
   constexpr int FLUSH = 8;
   const int r = (D == 2) ? 1 : (D == 4 ? 2 : 3);
   const MpsDims d = mps_dims(A.n, r);
@@ -407,77 +393,90 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
   float *lall = reinterpret_cast<float *>(A.out) + (size_t)job * A.out_stride;
   const long long chunks = A.tiles;
   const long long mask1 = (1LL << d.h1) - 1;
+  // mu: thread (half h, column u) sums rows [32 h, 32 h + 32) of column u; partial layout [a][128]
+  const int mh = tid >> 7, mu_col = tid & 127;
+  // Lambda1: thread (quarter qt, row ym) sums columns [32 qt, 32 qt + 32) of row ym
+  const int qt = tid >> 6, l1_row = tid & 63, rot = (l1_row >> 3) & 3;
+  if (mh == 0) {
 #pragma unroll
-  for (int k = 0; k < NMU; ++k) part[tid + GR_NT * k] = 0.0;  // mu^T [a][128]
+    for (int a = 0; a < D; ++a) part[(size_t)a * 128 + mu_col] = 0.0;
+  }
 #pragma unroll
-  for (int k = 0; k < NP; ++k) part[128 * D + tid + GR_NT * k] = 0.0;  // P [64][D][D]
+  for (int k = 0; k < NP; ++k) part[128 * D + tid + GR_NT * k] = 0.0;
+  // chunk c's staged data into buffer buf: its matrix of [13, 13 + h1) and vector
+  // of [13 + h1, n), and its 64 x 128 lambda block
   auto stage = [&](long long c, int buf) {
-    if (tid < NCH) {
+    if (STAGE && tid < NCH) {
       const float *src = (tid < D * D / 4) ? tab + d.m1 + (c & mask1) * D * D + 4 * tid
                                            : tab + d.r2 + (c >> d.h1) * D + 4 * (tid - D * D / 4);
       cp_async16(&sb[buf][4 * tid], src);
     }
+    const float *lc = lam + (c << MPS_CHUNK_BITS);
+    float *dst = slam + buf * 64 * LAM_LD;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = tid + GR_NT * j, row = i >> 5, col = (i & 31) * 4;
+      cp_async16(dst + row * LAM_LD + col, lc + row * 128 + col);
+    }
     cp_async_commit();
   };
-  if constexpr (STAGE) stage(blockIdx.x, 0);
+  stage(blockIdx.x, 0);
   for (int i = tid; i < 64 * D * D; i += GR_NT) {
     const int ym = i / (D * D), b = (i / D) % D, a = i % D;
     sM[i] = tab[d.mid + (ym * D + a) * D + b];
   }
-  unsigned long long L01[D], L23[D], mu01[D], mu23[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const float4 l = *reinterpret_cast<const float4 *>(tab + d.lo + a * 128 + 4 * lane);
-    L01[a] = pk(l.x, l.y);
-    L23[a] = pk(l.z, l.w);
-    mu01[a] = mu23[a] = 0ull;
-  }
+  for (int i = tid; i < 128 * D; i += GR_NT) sLo[i] = tab[d.lo + (i % D) * 128 + i / D];  // [yl][a]
+  unsigned long long mu2[D / 2];  // (mu[2a], mu[2a+1])
   float Pacc[NP];
+#pragma unroll
+  for (int a = 0; a < D / 2; ++a) mu2[a] = 0ull;
 #pragma unroll
   for (int k = 0; k < NP; ++k) Pacc[k] = 0.f;
   auto flush = [&]() {
+    // the two row halves of each column meet in sQ (free at this point)
+    if (mh == 1) {
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const float2 m01 = upk(mu01[a]), m23 = upk(mu23[a]);
-      *reinterpret_cast<float4 *>(&scr[(w * D + a) * 128 + 4 * lane]) = make_float4(m01.x, m01.y, m23.x, m23.y);
-      mu01[a] = mu23[a] = 0ull;
+      for (int a = 0; a < D / 2; ++a) {
+        const float2 m = upk(mu2[a]);
+        sQ[(2 * a) * 128 + mu_col] = m.x;
+        sQ[(2 * a + 1) * 128 + mu_col] = m.y;
+      }
     }
     __syncthreads();
+    if (mh == 0) {
 #pragma unroll
-    for (int k = 0; k < NMU; ++k) {
-      const int v = tid + GR_NT * k;
-      float t = 0.f;
-#pragma unroll
-      for (int ww = 0; ww < GR_NT / 32; ++ww) t += scr[ww * D * 128 + v];
-      part[v] += (double)t;
+      for (int a = 0; a < D / 2; ++a) {
+        const float2 m = upk(mu2[a]);
+        part[(size_t)(2 * a) * 128 + mu_col] += (double)(m.x + sQ[(2 * a) * 128 + mu_col]);
+        part[(size_t)(2 * a + 1) * 128 + mu_col] += (double)(m.y + sQ[(2 * a + 1) * 128 + mu_col]);
+      }
     }
+#pragma unroll
+    for (int a = 0; a < D / 2; ++a) mu2[a] = 0ull;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       part[128 * D + tid + GR_NT * k] += (double)Pacc[k];
       Pacc[k] = 0.f;
     }
+    __syncthreads();  // sQ free again
   };
   int par = 0, since = 0;
   for (long long c = blockIdx.x; c < chunks; c += gridDim.x, par ^= 1) {
-    if constexpr (STAGE) cp_async_wait<0>();
-    __syncthreads();
-    if constexpr (STAGE) {
-      if (c + gridDim.x < chunks) stage(c + gridDim.x, par ^ 1);
-      if (tid < D) {
-        float acc = 0.f;
+    cp_async_wait<0>();
+    __syncthreads();  // chunk c staged; the previous chunk's shared vectors are read
+    if (c + gridDim.x < chunks) stage(c + gridDim.x, par ^ 1);
+    if (tid < D) {
+      float acc = 0.f;
+      if constexpr (STAGE) {
 #pragma unroll
         for (int b = 0; b < D; ++b) acc = fmaf(sb[par][tid * D + b], sb[par][D * D + b], acc);
-        sr[tid] = acc;
-      }
-    } else {
-      if (tid < D) {
+      } else {
         const float *m1 = tab + d.m1 + ((c & mask1) * D + tid) * D;
         const float *r2 = tab + d.r2 + (c >> d.h1) * D;
-        float acc = 0.f;
 #pragma unroll
         for (int b = 0; b < D; ++b) acc = fmaf(m1[b], r2[b], acc);
-        sr[tid] = acc;
       }
+      sr[tid] = acc;
     }
     __syncthreads();
     for (int i = tid; i < 64 * D; i += GR_NT) {
@@ -485,33 +484,45 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
       float acc = 0.f;
 #pragma unroll
       for (int b = 0; b < D; ++b) acc = fmaf(mcol[b * D], sr[b], acc);
-      *reinterpret_cast<float2 *>(&sm[2 * i]) = make_float2(acc, acc);
+      sm[i] = acc;
     }
     __syncthreads();
-    const float *lc = lam + (c << MPS_CHUNK_BITS) + 4 * lane;
-#pragma unroll 2
-    for (int ym = w; ym < 64; ym += GR_NT / 32) {
-      const float4 lv = __ldcs(reinterpret_cast<const float4 *>(lc + ym * 128));
-      const unsigned long long l01 = pk(lv.x, lv.y), l23 = pk(lv.z, lv.w);
-      const ulonglong2 *mv = reinterpret_cast<const ulonglong2 *>(sm + ym * 2 * D);
+    const float *blk = slam + par * 64 * LAM_LD;
+    {
+      // mu += lambda^T m over this thread's 32 rows (packed pairs of bond indices)
+      const float *col = blk + mu_col;
+#pragma unroll 4
+      for (int k = 0; k < 32; ++k) {
+        const int ym = 32 * mh + k;
+        const float l = col[ym * LAM_LD];
+        const unsigned long long l2 = pk(l, l);
+        const unsigned long long *mv = reinterpret_cast<const unsigned long long *>(sm + ym * D);
 #pragma unroll
-      for (int a = 0; a < D; a += 2) {
-        const ulonglong2 m = mv[a / 2];
-        mu01[a] = fma2(l01, m.x, mu01[a]);
-        mu23[a] = fma2(l23, m.x, mu23[a]);
-        mu01[a + 1] = fma2(l01, m.y, mu01[a + 1]);
-        mu23[a + 1] = fma2(l23, m.y, mu23[a + 1]);
+        for (int a = 0; a < D / 2; ++a) mu2[a] = fma2(l2, mv[a], mu2[a]);
       }
-      float sv[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const float2 t = upk(fma2(L23[a], l23, mul2(L01[a], l01)));
-        sv[a] = t.x + t.y;
-      }
-      int idx;
-      const float tot = warp_tsum<D>(sv, lane, idx);
-      if ((lane & (32 / D - 1)) == 0) sL1[ym * D + idx] = tot;
     }
+    {
+      // Lambda1 quarter sums: row l1_row, columns 32 qt + (k + rot) mod 32
+      unsigned long long acc[D / 2];
+#pragma unroll
+      for (int a = 0; a < D / 2; ++a) acc[a] = 0ull;
+      const float *row = blk + l1_row * LAM_LD + 32 * qt;
+      const float *lo = sLo + 32 * qt * D;
+#pragma unroll 4
+      for (int k = 0; k < 32; ++k) {
+        const int yl = (k + rot) & 31;
+        const float l = row[yl];
+        const unsigned long long l2 = pk(l, l);
+        const unsigned long long *lv = reinterpret_cast<const unsigned long long *>(lo + yl * D);
+#pragma unroll
+        for (int a = 0; a < D / 2; ++a) acc[a] = fma2(l2, lv[a], acc[a]);
+      }
+#pragma unroll
+      for (int a = 0; a < D / 2; ++a)
+        *reinterpret_cast<float2 *>(&sQ[(qt * 64 + l1_row) * D + 2 * a]) = upk(acc[a]);
+    }
+    __syncthreads();
+    for (int i = tid; i < 64 * D; i += GR_NT) sL1[i] = sQ[i] + sQ[64 * D + i] + sQ[128 * D + i] + sQ[192 * D + i];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -541,7 +552,7 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
     }
   }
   if (since > 0) flush();
-  if constexpr (STAGE) cp_async_wait<0>();
+  cp_async_wait<0>();
 }
 
 // High qubits: block (x, q - 13) takes chunks 256 x .. 256 x + 255 and qubit q.
@@ -750,7 +761,7 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
   const MpsGradRegions gr = mps_grad_regions(A.n, A.layer);
   switch (A.kind) {
     case K_MPS_GRAD: {
-      const size_t smem = (size_t)(64 * D * D + (GR_NT / 32) * D * 128) * sizeof(float);
+      const size_t smem = (size_t)(2 * 64 * LAM_LD + 64 * D * D + 128 * D + 4 * 64 * D) * sizeof(float);
       cudaFuncSetAttribute(k_mps_grad<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_mps_grad<D><<<dim3((unsigned)gr.gc, (unsigned)jobs), GR_NT, smem, s>>>(A);
       break;
