@@ -79,11 +79,11 @@ extern "C" {
 
 #define GVQE_OPT_XY_TILE_BITS 4 /* log2 amplitudes per tile of the X-mask pass (strings with X/Y letters, RY
                                    layers), 10..13 (FP64: at most 12), 0 = those of the first pass */
-#define GVQE_OPT_MPS_LAYERS 5 /* leading layers written in closed form: 0 = auto (up to 3), -1 = none, 1..4 =
+#define GVQE_OPT_MPS_LAYERS 5 /* leading layers written in closed form: 0 = auto (up to 4), -1 = none, 1..4 =
                                  at most that many.  After r entangler + RY layers on the analytic layer-0
                                  product state, the linear, full and reverse-linear entanglers leave a state
                                  that is a product of 2^r x 2^r matrices along the qubits; FP32 plans with
-                                 n >= 14 and reps >= 2 write the stored states of layers 1..min(3, reps - 1)
+                                 n >= 14 and reps >= 2 write layers 1..min(4, reps - 1)
                                  from contracted tables of those matrices (a write-only pass per state)
                                  instead of running their tile passes.  Same results up to FP32 rounding;
                                  the last layer always runs as tile passes. */

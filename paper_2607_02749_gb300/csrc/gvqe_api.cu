@@ -615,11 +615,10 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
   };
   // Buffer ids: stored pass outputs (gradient path) or a forward ping-pong
   // pair (energy path), the lambda ping-pong pair, and psi_0 for X/Y terms at reps = 0.
-  // closed-form leading layers 1..R; with gradients and bond dimension up to 8
-  // (R <= 3) their gradients come from lambda_R and the matrix product
-  // (mgrad), so only layer R's final state is stored for them
+  // closed-form leading layers 1..R; with gradients, theirs come from lambda_R
+  // and the matrix product (mgrad), so only layer R's final state is stored
   const int R = (mps_layers > 0 && reps >= 2) ? std::min(mps_layers, reps - 1) : 0;
-  const bool mgrad = want_grad && !state_only && R >= 1 && R <= 3;
+  const bool mgrad = want_grad && !state_only && R >= 1 && R <= MPS_MAX_LAYERS;
   int nb = 0;
   const int first_state = nb;
   if (want_grad) nb += mgrad ? 1 + (reps - R) * p : reps * p;

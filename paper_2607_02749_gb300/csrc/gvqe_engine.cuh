@@ -211,8 +211,8 @@ struct PassArgs {
 // stored transposed [D][128]), [7, 13) (a matrix per pattern, [64][D][D]),
 // [13, 13 + h1) ([2^h1][D][D]) and [13 + h1, n) (a column vector, [2^h2][D]),
 // h1 = min(9, n - 13).  Offsets in floats inside one job's table region.
-constexpr int MPS_MAX_LAYERS = 4;   // bond dimension up to 16 (GVQE_OPT_MPS_LAYERS = 4)
-constexpr int MPS_AUTO_LAYERS = 3;  // the default: a bond-16 stage costs about a tile pass
+constexpr int MPS_MAX_LAYERS = 4;   // bond dimension up to 16
+constexpr int MPS_AUTO_LAYERS = 4;  // the default
 constexpr int MPS_MIN_QUBITS = 14;
 constexpr int MPS_CHUNK_BITS = 13;
 // With gradients (K_MPS_TAB flag F_MPS_SITES) the region also holds the site

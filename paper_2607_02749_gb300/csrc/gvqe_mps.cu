@@ -368,12 +368,15 @@ constexpr int LAM_LD = 132;  // floats per staged lambda row (128 + 4: 16-byte a
 template <int D>
 __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
   // dynamic: two staged lambda blocks, the transposed mid matrices [64][b][a],
-  // the row vectors of qubits 0..6 [128][D], quarter partials [4][64][D]
+  // the row vectors of qubits 0..6 [128][D], then quarter partials [4][64][D]
+  // (D <= 8) or the P accumulators [64][D][D] (D = 16, too many for registers)
   extern __shared__ __align__(16) float dyn[];
+  constexpr bool BIG = D >= 16;
   float *slam = dyn;                        // [2][64][LAM_LD]
   float *sM = slam + 2 * 64 * LAM_LD;       // [64][D][D]
   float *sLo = sM + 64 * D * D;             // [128][D]
-  float *sQ = sLo + 128 * D;                // [4][64][D]
+  float *sQ = sLo + 128 * D;                // [4][64][D] (D <= 8)
+  float *sP = sLo + 128 * D;                // [64][D][D] (D = 16)
   __shared__ __align__(16) float sm[64 * D];  // m per row (8-byte pairs read as f32x2)
   __shared__ __align__(16) float sb[2][D * D + D];
   __shared__ float sr[D];
@@ -382,8 +385,9 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
   constexpr bool STAGE = D >= 4;  // the chunk's matrix and vector by cp.async (16-byte pieces)
   constexpr int NCH = (D * D + D) / 4;
   constexpr int NP = (64 * D * D) / GR_NT;  // P entries per thread
+  constexpr int NPR = BIG ? 1 : NP;         // ... held in registers (D <= 8)
   constexpr int FLUSH = 8;
-  const int r = (D == 2) ? 1 : (D == 4 ? 2 : 3);
+  const int r = (D == 2) ? 1 : (D == 4 ? 2 : (D == 8 ? 3 : 4));
   const MpsDims d = mps_dims(A.n, r);
   const MpsGradRegions gr = mps_grad_regions(A.n, r);
   const int job = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -393,16 +397,27 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
   float *lall = reinterpret_cast<float *>(A.out) + (size_t)job * A.out_stride;
   const long long chunks = A.tiles;
   const long long mask1 = (1LL << d.h1) - 1;
-  // mu: thread (half h, column u) sums rows [32 h, 32 h + 32) of column u; partial layout [a][128]
+  // mu (partial layout [a][128]): D <= 8, thread (half h, column u) sums rows
+  // [32 h, 32 h + 32) of column u for every a; D = 16, thread (a-half h, column u)
+  // sums every row for a in [8 h, 8 h + 8)
   const int mh = tid >> 7, mu_col = tid & 127;
-  // Lambda1: thread (quarter qt, row ym) sums columns [32 qt, 32 qt + 32) of row ym
+  // Lambda1: D <= 8, thread (quarter qt, row ym) sums columns [32 qt, 32 qt + 32)
+  // of row ym; D = 16, thread (row, a-quarter) sums every column for 4 of the a
   const int qt = tid >> 6, l1_row = tid & 63, rot = (l1_row >> 3) & 3;
-  if (mh == 0) {
+  const int b_row = tid >> 2, b_aq = tid & 3;
+  if constexpr (BIG) {
+#pragma unroll
+    for (int j = 0; j < D / 2; ++j) part[(size_t)(mh * (D / 2) + j) * 128 + mu_col] = 0.0;
+  } else if (mh == 0) {
 #pragma unroll
     for (int a = 0; a < D; ++a) part[(size_t)a * 128 + mu_col] = 0.0;
   }
 #pragma unroll
   for (int k = 0; k < NP; ++k) part[128 * D + tid + GR_NT * k] = 0.0;
+  if constexpr (BIG) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) sP[tid + GR_NT * k] = 0.f;
+  }
   // chunk c's staged data into buffer buf: its matrix of [13, 13 + h1) and vector
   // of [13 + h1, n), and its 64 x 128 lambda block
   auto stage = [&](long long c, int buf) {
@@ -426,12 +441,27 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
     sM[i] = tab[d.mid + (ym * D + a) * D + b];
   }
   for (int i = tid; i < 128 * D; i += GR_NT) sLo[i] = tab[d.lo + (i % D) * 128 + i / D];  // [yl][a]
-  unsigned long long mu2[D / 2];  // (mu[2a], mu[2a+1])
-  float Pacc[NP];
+  constexpr int NMU2 = BIG ? D / 4 : D / 2;
+  unsigned long long mu2[NMU2];  // packed pairs of this thread's mu values
+  float Pacc[NPR];
 #pragma unroll
-  for (int a = 0; a < D / 2; ++a) mu2[a] = 0ull;
+  for (int a = 0; a < NMU2; ++a) mu2[a] = 0ull;
 #pragma unroll
-  for (int k = 0; k < NP; ++k) Pacc[k] = 0.f;
+  for (int k = 0; k < NPR; ++k) Pacc[k] = 0.f;
+  auto flush_big = [&]() {
+#pragma unroll
+    for (int j = 0; j < NMU2; ++j) {
+      const float2 m = upk(mu2[j]);
+      part[(size_t)(mh * (D / 2) + 2 * j) * 128 + mu_col] += (double)m.x;
+      part[(size_t)(mh * (D / 2) + 2 * j + 1) * 128 + mu_col] += (double)m.y;
+      mu2[j] = 0ull;
+    }
+#pragma unroll 8
+    for (int k = 0; k < NP; ++k) {
+      part[128 * D + tid + GR_NT * k] += (double)sP[tid + GR_NT * k];
+      sP[tid + GR_NT * k] = 0.f;
+    }
+  };
   auto flush = [&]() {
     // the two row halves of each column meet in sQ (free at this point)
     if (mh == 1) {
@@ -488,6 +518,33 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
     }
     __syncthreads();
     const float *blk = slam + par * 64 * LAM_LD;
+    if constexpr (BIG) {
+      // mu += lambda^T m: column mu_col, every row, a in [8 mh, 8 mh + 8)
+      const float *col = blk + mu_col;
+#pragma unroll 4
+      for (int ym = 0; ym < 64; ++ym) {
+        const float l = col[ym * LAM_LD];
+        const unsigned long long l2 = pk(l, l);
+        const unsigned long long *mv = reinterpret_cast<const unsigned long long *>(sm + ym * D + mh * (D / 2));
+#pragma unroll
+        for (int j = 0; j < NMU2; ++j) mu2[j] = fma2(l2, mv[j], mu2[j]);
+      }
+      // Lambda1 row b_row, a in [4 b_aq, 4 b_aq + 4), every column (rows 132 floats
+      // apart: the warp's 8 rows fall in distinct banks)
+      unsigned long long acc[2] = {0ull, 0ull};
+      const float *row = blk + b_row * LAM_LD;
+#pragma unroll 4
+      for (int k = 0; k < 128; ++k) {
+        const float l = row[k];
+        const unsigned long long l2 = pk(l, l);
+        const unsigned long long *lv = reinterpret_cast<const unsigned long long *>(sLo + k * D + 4 * b_aq);
+        acc[0] = fma2(l2, lv[0], acc[0]);
+        acc[1] = fma2(l2, lv[1], acc[1]);
+      }
+      *reinterpret_cast<float2 *>(&sL1[b_row * D + 4 * b_aq]) = upk(acc[0]);
+      *reinterpret_cast<float2 *>(&sL1[b_row * D + 4 * b_aq + 2]) = upk(acc[1]);
+      __syncthreads();
+    } else {
     {
       // mu += lambda^T m over this thread's 32 rows (packed pairs of bond indices)
       const float *col = blk + mu_col;
@@ -524,10 +581,19 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
     __syncthreads();
     for (int i = tid; i < 64 * D; i += GR_NT) sL1[i] = sQ[i] + sQ[64 * D + i] + sQ[128 * D + i] + sQ[192 * D + i];
     __syncthreads();
+    }
+    if constexpr (BIG) {
+#pragma unroll 8
+      for (int k = 0; k < NP; ++k) {
+        const int e = tid + GR_NT * k;  // (ym D + a) D + b
+        sP[e] = fmaf(sL1[e / D], sr[e % D], sP[e]);
+      }
+    } else {
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      const int e = tid + GR_NT * k;  // (ym D + a) D + b
-      Pacc[k] = fmaf(sL1[e / D], sr[e % D], Pacc[k]);
+      for (int k = 0; k < NP; ++k) {
+        const int e = tid + GR_NT * k;  // (ym D + a) D + b
+        Pacc[k] = fmaf(sL1[e / D], sr[e % D], Pacc[k]);
+      }
     }
     {
       // l_c(b) = sum over (ym, a) of sL1[ym][a] M(ym)(a, b): thread (g, b) takes every
@@ -547,11 +613,19 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
       lall[c * D + tid] = t;
     }
     if (++since == FLUSH) {
-      flush();
+      if constexpr (BIG)
+        flush_big();
+      else
+        flush();
       since = 0;
     }
   }
-  if (since > 0) flush();
+  if (since > 0) {
+    if constexpr (BIG)
+      flush_big();
+    else
+      flush();
+  }
   cp_async_wait<0>();
 }
 
@@ -561,11 +635,11 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
 template <int D>
 __global__ void __launch_bounds__(256) k_mps_ghigh(const PassArgs A) {
   constexpr int DD = D * D;
-  constexpr int RMAX = 3;
+  constexpr int RMAX = 4;
   __shared__ float sA[17 * 2 * DD];
   __shared__ float sdA[(RMAX + 1) * 2 * DD];
   __shared__ double red[8][RMAX + 1];
-  const int r = (D == 2) ? 1 : (D == 4 ? 2 : 3);
+  const int r = (D == 2) ? 1 : (D == 4 ? 2 : (D == 8 ? 3 : 4));
   const int n = A.n, K = n - MPS_CHUNK_BITS, q = MPS_CHUNK_BITS + blockIdx.y, job = blockIdx.z;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const MpsDims d = mps_dims(n, r);
@@ -580,7 +654,7 @@ __global__ void __launch_bounds__(256) k_mps_ghigh(const PassArgs A) {
   }
   __syncthreads();
   const long long c = (long long)blockIdx.x * 256 + tid;
-  float val[RMAX + 1] = {0.f, 0.f, 0.f, 0.f};
+  float val[RMAX + 1] = {0.f, 0.f, 0.f, 0.f, 0.f};
   if (c < A.tiles) {
     float u[D], sv[D];
 #pragma unroll
@@ -671,9 +745,9 @@ __global__ void __launch_bounds__(128) k_mps_gred(const PassArgs A) {
 template <int D>
 __global__ void __launch_bounds__(256) k_mps_genv(const PassArgs A) {
   constexpr int DD = D * D;
-  constexpr int RMAX = 3;
+  constexpr int RMAX = 4;
   __shared__ double red[8][RMAX + 1];
-  const int r = (D == 2) ? 1 : (D == 4 ? 2 : 3);
+  const int r = (D == 2) ? 1 : (D == 4 ? 2 : (D == 8 ? 3 : 4));
   const int n = A.n, q = blockIdx.x, job = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const MpsDims d = mps_dims(n, r);
   const MpsGradRegions gr = mps_grad_regions(n, r);
@@ -690,7 +764,7 @@ __global__ void __launch_bounds__(256) k_mps_genv(const PassArgs A) {
   auto site = [&](int j, int y) { return tab + d.sites + ((long long)j * 2 + y) * DD; };
   const bool lo = q < 7;
   const int nitems = lo ? 128 : 64 * D;
-  double acc[RMAX + 1] = {0.0, 0.0, 0.0, 0.0};
+  double acc[RMAX + 1] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int it = tid; it < nitems; it += 256) {
     const int pat = lo ? it : it / D, a0 = lo ? 0 : it % D;
     const int q0 = lo ? 0 : 7, q1 = lo ? 7 : 13;
@@ -761,7 +835,8 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
   const MpsGradRegions gr = mps_grad_regions(A.n, A.layer);
   switch (A.kind) {
     case K_MPS_GRAD: {
-      const size_t smem = (size_t)(2 * 64 * LAM_LD + 64 * D * D + 128 * D + 4 * 64 * D) * sizeof(float);
+      const size_t smem =
+          (size_t)(2 * 64 * LAM_LD + 64 * D * D + 128 * D + (D >= 16 ? 64 * D * D : 4 * 64 * D)) * sizeof(float);
       cudaFuncSetAttribute(k_mps_grad<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_mps_grad<D><<<dim3((unsigned)gr.gc, (unsigned)jobs), GR_NT, smem, s>>>(A);
       break;
@@ -781,10 +856,7 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
 
 template <int D>
 cudaError_t launch_mps_d(const PassArgs &A, int jobs, cudaStream_t s) {
-  if (A.kind >= K_MPS_GRAD) {
-    if constexpr (D <= 8) return launch_mps_grad_d<D>(A, jobs, s);
-    return cudaErrorInvalidValue;
-  }
+  if (A.kind >= K_MPS_GRAD) return launch_mps_grad_d<D>(A, jobs, s);
   if (A.kind == K_MPS_TAB) {
     const MpsDims d = mps_dims(A.n, A.layer);
     const MpsItems its = mps_items(d);

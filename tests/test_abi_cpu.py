@@ -304,7 +304,7 @@ def test_split_rule_over_register_sizes(gates, fp64):
 
 def test_closed_form_layer_option_and_plans():
     """GVQE_OPT_MPS_LAYERS: FP32 plans with n >= 14, reps >= 2 and a linear,
-    full or reverse-linear entangler write layers 1..min(3, reps - 1) in closed
+    full or reverse-linear entangler write layers 1..min(4, reps - 1) in closed
     form (one table build and one write per stored state); everything else keeps
     every layer as tile passes."""
     def desc(n, reps, ent=_lib.GVQE_ENT_LINEAR, mps=None, flags=_lib.GVQE_FP32):
@@ -321,21 +321,18 @@ def test_closed_form_layer_option_and_plans():
                 and not ln.startswith("  layer pass") and not ln.startswith("  closed-form")]
 
     d = desc(30, 6)
-    assert ("closed-form layers 1..3 (bond dimension up to 8), 59136 table floats per job; their gradients "
+    assert ("closed-form layers 1..4 (bond dimension up to 16), 245760 table floats per job; their gradients "
             "from lambda and the matrix product") in d
-    # layer 3's final state in closed form, layers 4..6 as tile passes and their backward, then the
-    # gradients of layers 0..3 from lambda_3 (no backward passes and no layer-0 pass below layer 4)
-    assert steps_of(d) == (["mps_tab", "mps"] + ["fwd"] * 9 + ["bwd"] * 9
+    # layer 4's final state in closed form, layers 5..6 as tile passes and their backward, then the
+    # gradients of layers 0..4 from lambda_4 (no backward passes and no layer-0 pass below layer 5)
+    assert steps_of(d) == (["mps_tab", "mps"] + ["fwd"] * 6 + ["bwd"] * 6
                            + ["mps_grad", "mps_ghigh", "mps_gred", "mps_genv"])
-    # a fourth layer (bond dimension 16) on request: every stored state of layers 1..4 in closed form,
-    # the backward through every layer
-    d4 = desc(30, 6, mps=4)
-    assert "closed-form layers 1..4 (bond dimension up to 16), 153600 table floats per job\n" in d4
-    s4 = steps_of(d4)
-    assert s4[:24] == ["mps_tab", "mps"] * 12 and s4.count("fwd") == 6 and s4.count("bwd") == 18
-    assert s4[-1] == "grad_l0"
+    d3 = desc(30, 6, mps=3)
+    assert ("closed-form layers 1..3 (bond dimension up to 8), 59136 table floats per job; their gradients "
+            "from lambda and the matrix product") in d3
+    assert steps_of(d3).count("fwd") == 9 and steps_of(d3).count("bwd") == 9
     for ent in (_lib.GVQE_ENT_FULL, _lib.GVQE_ENT_REVERSE_LINEAR):
-        assert "closed-form layers 1..3 " in desc(20, 5, ent)
+        assert "closed-form layers 1..4 " in desc(20, 5, ent)
         assert "closed-form layers 1..2 " in desc(20, 3, ent)
     assert "closed-form layers 1..1 " in desc(14, 2)
     assert "closed-form layers 1..2 " in desc(14, 6, mps=2)

@@ -3,7 +3,7 @@
 From the layer-0 product state, r layers of [linear / full / reverse-linear
 CX chain, RY] leave a product of 2^r x 2^r site matrices along the qubits;
 FP32 plans with n >= 14 and reps >= 2 write the stored states of layers
-1..min(3, reps - 1) (on request up to 4) from contracted tables of them (gvqe_mps.cu) instead of
+1..min(4, reps - 1) from contracted tables of them (gvqe_mps.cu) instead of
 running tile passes.  Checked here against the oracle (energies, adjoint
 gradients, masks, X/Y strings, readout) and against the same plans with every
 layer as tile passes.  Tolerances as in test_gpu_parity.py (FP32 mode):
@@ -58,7 +58,7 @@ def _check_oracle(e, g, n, reps, th, ham, ent, what):
             assert rel <= FP32_G, f"{what} b={b} grad rel L2={rel:.3e}"
 
 
-# (n, reps, tile bits): one to three closed-form layers, one run per strided
+# (n, reps, tile bits): one to four closed-form layers, one run per strided
 # pass and split layouts (forced small tiles give more passes per layer, so
 # the stored states between passes rotate different qubit subsets)
 CASES = [(14, 2, 0), (14, 4, 0), (15, 3, 10), (17, 5, 11), (19, 4, 0), (20, 3, 12), (22, 4, 0)]
@@ -70,7 +70,7 @@ def test_closed_form_layers_match_oracle_and_tile_passes(n, reps, tb, ent):
     ham = wl.z_hamiltonian(n, 6 * n + 5, seed=n + reps)
     th = wl.thetas(n, reps, 2, seed=200 + n + ent)
     e_only, e, g, desc = _run(n, reps, ham, th, ent, 0, tb)
-    R = min(3, reps - 1)
+    R = min(4, reps - 1)
     assert f"closed-form layers 1..{R} " in desc, desc
     _check_oracle(e_only, None, n, reps, th, ham, ent, "energy")
     _check_oracle(e, g, n, reps, th, ham, ent, "energy_grad")
