@@ -629,6 +629,193 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
   cp_async_wait<0>();
 }
 
+// Bond dimension 16: the same pass, 16 warps per CTA and one CTA per SM.
+// Warps 0..7 form Lambda1 (thread: one row, 4 of the a, every column) while
+// warps 8..15 form mu (thread: one column, 8 of the a, every row); P lives in
+// registers (thread: two (row, a) pairs x 16 b), and the mid matrices are kept
+// twice, transposed [64][b][a] for m = M R_c and as stored [64][a][b] for l_c,
+// so that both read consecutive words across the lanes.  FP32 accumulators are
+// added into the FP64 partials every 16 chunks.
+constexpr int G16_NT = 512;
+__global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
+  constexpr int D = 16, DD = 256;
+  extern __shared__ __align__(16) float dyn[];
+  float *slam = dyn;                   // [2][64][LAM_LD]
+  float *sM = slam + 2 * 64 * LAM_LD;  // [64][b][a]
+  float *sMn = sM + 64 * DD;           // [64][a][b]
+  float *sLo = sMn + 64 * DD;          // [128][D]
+  __shared__ __align__(16) float sm[64 * D];
+  __shared__ __align__(16) float sb[2][DD + D];
+  __shared__ __align__(16) float sr[D];
+  __shared__ __align__(16) float sL1[64 * D];
+  __shared__ float sLc[2 * G16_NT / 32][D];
+  constexpr int NCH = (DD + D) / 4;
+  constexpr int FLUSH = 16;
+  const MpsDims d = mps_dims(A.n, 4);
+  const MpsGradRegions gr = mps_grad_regions(A.n, 4);
+  const int job = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const float *tab = reinterpret_cast<const float *>(A.in) + (size_t)job * A.in_stride;
+  const float *lam = reinterpret_cast<const float *>(A.lam_in) + (size_t)job * A.lam_stride;
+  double *part = A.part + (size_t)job * A.part_stride + (size_t)blockIdx.x * gr.v1;
+  float *lall = reinterpret_cast<float *>(A.out) + (size_t)job * A.out_stride;
+  const long long chunks = A.tiles;
+  const long long mask1 = (1LL << d.h1) - 1;
+  const bool l1w = tid < 256;
+  const int t2 = tid & 255;
+  const int b_row = t2 >> 2, b_aq = t2 & 3;   // Lambda1 warps
+  const int mu_col = t2 & 127, mh = t2 >> 7;  // mu warps: a in [8 mh, 8 mh + 8)
+  if (!l1w) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) part[(size_t)(8 * mh + j) * 128 + mu_col] = 0.0;
+  }
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int b = 0; b < D; ++b) part[128 * D + (size_t)(tid + G16_NT * p) * D + b] = 0.0;
+  auto stage = [&](long long c, int buf) {
+    if (tid < NCH) {
+      const float *src = (tid < DD / 4) ? tab + d.m1 + (c & mask1) * DD + 4 * tid
+                                        : tab + d.r2 + (c >> d.h1) * D + 4 * (tid - DD / 4);
+      cp_async16(&sb[buf][4 * tid], src);
+    }
+    const float *lc = lam + (c << MPS_CHUNK_BITS);
+    float *dst = slam + buf * 64 * LAM_LD;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = tid + G16_NT * j, row = i >> 5, col = (i & 31) * 4;
+      cp_async16(dst + row * LAM_LD + col, lc + row * 128 + col);
+    }
+    cp_async_commit();
+  };
+  stage(blockIdx.x, 0);
+  for (int i = tid; i < 64 * DD; i += G16_NT) {
+    const int ym = i / DD, b = (i / D) % D, a = i % D;
+    sM[i] = tab[d.mid + (ym * D + a) * D + b];
+    sMn[i] = tab[d.mid + i];
+  }
+  for (int i = tid; i < 128 * D; i += G16_NT) sLo[i] = tab[d.lo + (i % D) * 128 + i / D];  // [yl][a]
+  unsigned long long mu2[4], P2[2][8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) mu2[j] = 0ull;
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) P2[p][j] = 0ull;
+  auto flush = [&]() {
+    if (!l1w) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 m = upk(mu2[j]);
+        part[(size_t)(8 * mh + 2 * j) * 128 + mu_col] += (double)m.x;
+        part[(size_t)(8 * mh + 2 * j + 1) * 128 + mu_col] += (double)m.y;
+        mu2[j] = 0ull;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float2 v = upk(P2[p][j]);
+        double *dst = part + 128 * D + (size_t)(tid + G16_NT * p) * D + 2 * j;
+        dst[0] += (double)v.x;
+        dst[1] += (double)v.y;
+        P2[p][j] = 0ull;
+      }
+  };
+  int par = 0, since = 0;
+  for (long long c = blockIdx.x; c < chunks; c += gridDim.x, par ^= 1) {
+    cp_async_wait<0>();
+    __syncthreads();
+    if (c + gridDim.x < chunks) stage(c + gridDim.x, par ^ 1);
+    if (tid < D) {
+      float acc = 0.f;
+#pragma unroll
+      for (int b = 0; b < D; ++b) acc = fmaf(sb[par][tid * D + b], sb[par][DD + b], acc);
+      sr[tid] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int i = tid + G16_NT * k;  // i = ym D + a
+      const float *mcol = sM + (i / D) * DD + (i % D);
+      float acc = 0.f;
+#pragma unroll
+      for (int b = 0; b < D; ++b) acc = fmaf(mcol[b * D], sr[b], acc);
+      sm[i] = acc;
+    }
+    __syncthreads();
+    const float *blk = slam + par * 64 * LAM_LD;
+    if (l1w) {
+      unsigned long long acc[2] = {0ull, 0ull};
+      const float *row = blk + b_row * LAM_LD;
+#pragma unroll 8
+      for (int k = 0; k < 128; ++k) {
+        const float l = row[k];
+        const unsigned long long l2 = pk(l, l);
+        const ulonglong2 lv = *reinterpret_cast<const ulonglong2 *>(sLo + k * D + 4 * b_aq);
+        acc[0] = fma2(l2, lv.x, acc[0]);
+        acc[1] = fma2(l2, lv.y, acc[1]);
+      }
+      const float2 v0 = upk(acc[0]), v1 = upk(acc[1]);
+      *reinterpret_cast<float4 *>(&sL1[b_row * D + 4 * b_aq]) = make_float4(v0.x, v0.y, v1.x, v1.y);
+    } else {
+      const float *col = blk + mu_col;
+#pragma unroll 8
+      for (int ym = 0; ym < 64; ++ym) {
+        const float l = col[ym * LAM_LD];
+        const unsigned long long l2 = pk(l, l);
+        const ulonglong2 *mv = reinterpret_cast<const ulonglong2 *>(sm + ym * D + 8 * mh);
+        const ulonglong2 m0 = mv[0], m1 = mv[1];
+        mu2[0] = fma2(l2, m0.x, mu2[0]);
+        mu2[1] = fma2(l2, m0.y, mu2[1]);
+        mu2[2] = fma2(l2, m1.x, mu2[2]);
+        mu2[3] = fma2(l2, m1.y, mu2[3]);
+      }
+    }
+    __syncthreads();
+    {
+      // P(pair, :) += Lambda1(pair) R_c for this thread's two (row, a) pairs
+      const ulonglong2 *rv = reinterpret_cast<const ulonglong2 *>(sr);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const float L = sL1[tid + G16_NT * p];
+        const unsigned long long L2 = pk(L, L);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const ulonglong2 rr = rv[j];
+          P2[p][2 * j] = fma2(L2, rr.x, P2[p][2 * j]);
+          P2[p][2 * j + 1] = fma2(L2, rr.y, P2[p][2 * j + 1]);
+        }
+      }
+      // l_c(b) = sum over ym of sum_a Lambda1(ym, a) M(ym)(a, b): thread (ym, b) for two ym
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int e = tid + G16_NT * k, ym = e / D, b = e % D;
+        const float *lr = sL1 + ym * D;
+        const float *mr = sMn + ym * DD + b;
+        float x = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) x = fmaf(lr[a], mr[a * D], x);
+        x += __shfl_xor_sync(0xffffffffu, x, 16);
+        if (lane < D) sLc[2 * w + k][lane] = x;
+      }
+    }
+    __syncthreads();
+    if (tid < D) {
+      float t = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < 2 * G16_NT / 32; ++ww) t += sLc[ww][tid];
+      lall[c * D + tid] = t;
+    }
+    if (++since == FLUSH) {
+      flush();
+      since = 0;
+    }
+  }
+  if (since > 0) flush();
+  cp_async_wait<0>();
+}
+
 // High qubits: block (x, q - 13) takes chunks 256 x .. 256 x + 255 and qubit q.
 // Thread c forms u = l_c A_13 .. A_{q-1} and s = A_{q+1} .. A_{n-1} 1 and adds
 // u dA_q^k s for every layer k <= r; the block's FP64 sums go to its partials.
@@ -835,10 +1022,15 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
   const MpsGradRegions gr = mps_grad_regions(A.n, A.layer);
   switch (A.kind) {
     case K_MPS_GRAD: {
-      const size_t smem =
-          (size_t)(2 * 64 * LAM_LD + 64 * D * D + 128 * D + (D >= 16 ? 64 * D * D : 4 * 64 * D)) * sizeof(float);
-      cudaFuncSetAttribute(k_mps_grad<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_mps_grad<D><<<dim3((unsigned)gr.gc, (unsigned)jobs), GR_NT, smem, s>>>(A);
+      if constexpr (D >= 16) {
+        const size_t smem = (size_t)(2 * 64 * LAM_LD + 2 * 64 * D * D + 128 * D) * sizeof(float);
+        cudaFuncSetAttribute(k_mps_grad16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_mps_grad16<<<dim3((unsigned)gr.gc, (unsigned)jobs), G16_NT, smem, s>>>(A);
+      } else {
+        const size_t smem = (size_t)(2 * 64 * LAM_LD + 64 * D * D + 128 * D + 4 * 64 * D) * sizeof(float);
+        cudaFuncSetAttribute(k_mps_grad<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_mps_grad<D><<<dim3((unsigned)gr.gc, (unsigned)jobs), GR_NT, smem, s>>>(A);
+      }
       break;
     }
     case K_MPS_GHIGH:
