@@ -243,7 +243,8 @@ __host__ __device__ inline MpsDims mps_dims(int n, int r) {
 // per-CTA partials of the pass over lambda (mu: [128][D], P: [64][D][D]), the
 // left-contracted vector of every chunk (floats), per-block partials of the
 // high qubits, their fixed-order sums, and the final gradients [k][q].
-constexpr int MPS_GRAD_CTAS = 256;
+constexpr int MPS_GRAD_CTAS = 256;     // CTAs of the pass over lambda (two per SM fit at D <= 8)
+constexpr int MPS_GRAD_CTAS_16 = 152;  // at D = 16 one CTA per SM fits: one wave on 152 SMs
 struct MpsGradRegions {
   long long gc, nb3, v1, k;
   long long part1, lall, part3, red, fin, total;
@@ -251,7 +252,8 @@ struct MpsGradRegions {
 __host__ __device__ inline MpsGradRegions mps_grad_regions(int n, int r) {
   MpsGradRegions g;
   const long long D = 1LL << r, chunks = 1LL << (n - MPS_CHUNK_BITS);
-  g.gc = chunks < MPS_GRAD_CTAS ? chunks : MPS_GRAD_CTAS;
+  const long long cap = (r >= 4) ? MPS_GRAD_CTAS_16 : MPS_GRAD_CTAS;
+  g.gc = chunks < cap ? chunks : cap;
   g.nb3 = (chunks + 255) / 256;
   g.v1 = 128 * D + 64 * D * D;
   g.k = n - MPS_CHUNK_BITS;

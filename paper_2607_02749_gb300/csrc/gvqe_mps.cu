@@ -630,25 +630,28 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
 }
 
 // Bond dimension 16: the same pass, 16 warps per CTA and one CTA per SM.
-// Warps 0..7 form Lambda1 (thread: one row, 4 of the a, every column) while
-// warps 8..15 form mu (thread: one column, 8 of the a, every row); P lives in
-// registers (thread: two (row, a) pairs x 16 b), and the mid matrices are kept
-// twice, transposed [64][b][a] for m = M R_c and as stored [64][a][b] for l_c,
-// so that both read consecutive words across the lanes.  FP32 accumulators are
-// added into the FP64 partials every 16 chunks.
+// Warps 0..7 form Lambda1: thread (row, column quarter) over 32 columns for
+// all 16 a, four columns per 16-byte load (rows 132 floats apart keep a
+// quarter-warp's rows in distinct banks), the quarters added in shared memory.  Warps 8..15 form
+// mu: thread (column pair, a-half, row half) over 32 rows, two columns per
+// 8-byte load.  P lives in registers (thread: two (row, a) pairs x 16 b), and
+// l_c is summed with it from the same Lambda1 values and rows of the mid
+// matrices.  The shared loads are 16-byte vectors wherever the lanes allow, so
+// the shared-memory pipe, not the FMA pipe, sets the pace.  FP32 accumulators
+// are added into the FP64 partials every 16 chunks.
 constexpr int G16_NT = 512;
 __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
   constexpr int D = 16, DD = 256;
   extern __shared__ __align__(16) float dyn[];
   float *slam = dyn;                   // [2][64][LAM_LD]
-  float *sM = slam + 2 * 64 * LAM_LD;  // [64][b][a]
-  float *sMn = sM + 64 * DD;           // [64][a][b]
+  float *sMn = slam + 2 * 64 * LAM_LD; // [64][a][b]
   float *sLo = sMn + 64 * DD;          // [128][D]
+  float *sQ = sLo + 128 * D;           // [4][64][D]: Lambda1 quarters; mu row halves at a flush
   __shared__ __align__(16) float sm[64 * D];
   __shared__ __align__(16) float sb[2][DD + D];
   __shared__ __align__(16) float sr[D];
   __shared__ __align__(16) float sL1[64 * D];
-  __shared__ float sLc[2 * G16_NT / 32][D];
+  __shared__ float sLc[G16_NT / 32][D];
   constexpr int NCH = (DD + D) / 4;
   constexpr int FLUSH = 16;
   const MpsDims d = mps_dims(A.n, 4);
@@ -662,11 +665,17 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
   const long long mask1 = (1LL << d.h1) - 1;
   const bool l1w = tid < 256;
   const int t2 = tid & 255;
-  const int b_row = t2 >> 2, b_aq = t2 & 3;   // Lambda1 warps
-  const int mu_col = t2 & 127, mh = t2 >> 7;  // mu warps: a in [8 mh, 8 mh + 8)
-  if (!l1w) {
+  // Lambda1 warps: thread (row l_row, column quarter l_q) sums columns
+  // [32 l_q, 32 l_q + 32) for all 16 a; a warp's lanes take 32 consecutive rows
+  const int l_row = t2 & 63, l_q = t2 >> 6;
+  // mu warps: column pair (t2 & 63), a-half ((t2 >> 6) & 1), row half (t2 >> 7)
+  const int m_cp = t2 & 63, m_ah = (t2 >> 6) & 1, m_rh = t2 >> 7;
+  if (!l1w && m_rh == 0) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) part[(size_t)(8 * mh + j) * 128 + mu_col] = 0.0;
+    for (int j = 0; j < 8; ++j) {
+      part[(size_t)(8 * m_ah + j) * 128 + 2 * m_cp] = 0.0;
+      part[(size_t)(8 * m_ah + j) * 128 + 2 * m_cp + 1] = 0.0;
+    }
   }
 #pragma unroll
   for (int p = 0; p < 2; ++p)
@@ -688,29 +697,42 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
     cp_async_commit();
   };
   stage(blockIdx.x, 0);
-  for (int i = tid; i < 64 * DD; i += G16_NT) {
-    const int ym = i / DD, b = (i / D) % D, a = i % D;
-    sM[i] = tab[d.mid + (ym * D + a) * D + b];
-    sMn[i] = tab[d.mid + i];
-  }
+  for (int i = tid; i < 64 * DD; i += G16_NT) sMn[i] = tab[d.mid + i];
   for (int i = tid; i < 128 * D; i += G16_NT) sLo[i] = tab[d.lo + (i % D) * 128 + i / D];  // [yl][a]
-  unsigned long long mu2[4], P2[2][8];
+  // mu: 2 columns x 8 a (packed pairs over a); P: 2 pairs x 16 b (packed pairs over b)
+  unsigned long long mu2[2][4], P2[2][8];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) mu2[j] = 0ull;
+  for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mu2[c2][j] = 0ull;
 #pragma unroll
   for (int p = 0; p < 2; ++p)
 #pragma unroll
     for (int j = 0; j < 8; ++j) P2[p][j] = 0ull;
   auto flush = [&]() {
-    if (!l1w) {
+    // mu: the row-half-1 threads park their sums in sQ, the row-half-0 threads add both
+    if (!l1w && m_rh == 1) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float2 m = upk(mu2[j]);
-        part[(size_t)(8 * mh + 2 * j) * 128 + mu_col] += (double)m.x;
-        part[(size_t)(8 * mh + 2 * j + 1) * 128 + mu_col] += (double)m.y;
-        mu2[j] = 0ull;
-      }
+      for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) *reinterpret_cast<float2 *>(&sQ[((c2 * 64 + m_cp) * 2 + m_ah) * 8 + 2 * j]) = upk(mu2[c2][j]);
     }
+    __syncthreads();
+    if (!l1w && m_rh == 0) {
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 m = upk(mu2[c2][j]);
+          const float2 o = *reinterpret_cast<const float2 *>(&sQ[((c2 * 64 + m_cp) * 2 + m_ah) * 8 + 2 * j]);
+          part[(size_t)(8 * m_ah + 2 * j) * 128 + 2 * m_cp + c2] += (double)(m.x + o.x);
+          part[(size_t)(8 * m_ah + 2 * j + 1) * 128 + 2 * m_cp + c2] += (double)(m.y + o.y);
+        }
+    }
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) mu2[c2][j] = 0ull;
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
@@ -721,6 +743,7 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
         dst[1] += (double)v.y;
         P2[p][j] = 0ull;
       }
+    __syncthreads();  // sQ free for the next chunk's quarters
   };
   int par = 0, since = 0;
   for (long long c = blockIdx.x; c < chunks; c += gridDim.x, par ^= 1) {
@@ -734,77 +757,137 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
       sr[tid] = acc;
     }
     __syncthreads();
+    {
+      // m(ym)(a) = M(ym)(a, :) R_c: thread (ym, a) for two rows, 16-byte row loads
+      const float4 *r4 = reinterpret_cast<const float4 *>(sr);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int i = tid + G16_NT * k;  // i = ym D + a
-      const float *mcol = sM + (i / D) * DD + (i % D);
-      float acc = 0.f;
+      for (int k = 0; k < 2; ++k) {
+        const int i = tid + G16_NT * k;  // ym D + a
+        const float4 *mrow = reinterpret_cast<const float4 *>(sMn + (size_t)i * D);
+        float acc = 0.f;
 #pragma unroll
-      for (int b = 0; b < D; ++b) acc = fmaf(mcol[b * D], sr[b], acc);
-      sm[i] = acc;
+        for (int j = 0; j < 4; ++j) {
+          const float4 m = mrow[j], rr = r4[j];
+          acc = fmaf(m.x, rr.x, fmaf(m.y, rr.y, fmaf(m.z, rr.z, fmaf(m.w, rr.w, acc))));
+        }
+        sm[i] = acc;
+      }
     }
     __syncthreads();
     const float *blk = slam + par * 64 * LAM_LD;
     if (l1w) {
-      unsigned long long acc[2] = {0ull, 0ull};
-      const float *row = blk + b_row * LAM_LD;
-#pragma unroll 8
-      for (int k = 0; k < 128; ++k) {
-        const float l = row[k];
-        const unsigned long long l2 = pk(l, l);
-        const ulonglong2 lv = *reinterpret_cast<const ulonglong2 *>(sLo + k * D + 4 * b_aq);
-        acc[0] = fma2(l2, lv.x, acc[0]);
-        acc[1] = fma2(l2, lv.y, acc[1]);
+      // Lambda1 quarter: row l_row, columns [32 l_q, 32 l_q + 32), all 16 a
+      unsigned long long acc[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = 0ull;
+      const float4 *row4 = reinterpret_cast<const float4 *>(blk + l_row * LAM_LD + 32 * l_q);
+      const ulonglong2 *lo2 = reinterpret_cast<const ulonglong2 *>(sLo + 32 * l_q * D);
+#pragma unroll 2
+      for (int k4 = 0; k4 < 8; ++k4) {
+        const float4 l4 = row4[k4];
+        const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const unsigned long long l2 = pk(lv[e], lv[e]);
+          const ulonglong2 *lr = lo2 + (4 * k4 + e) * (D / 4);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const ulonglong2 v = lr[j];
+            acc[2 * j] = fma2(l2, v.x, acc[2 * j]);
+            acc[2 * j + 1] = fma2(l2, v.y, acc[2 * j + 1]);
+          }
+        }
       }
-      const float2 v0 = upk(acc[0]), v1 = upk(acc[1]);
-      *reinterpret_cast<float4 *>(&sL1[b_row * D + 4 * b_aq]) = make_float4(v0.x, v0.y, v1.x, v1.y);
+      float4 *q4 = reinterpret_cast<float4 *>(sQ + (l_q * 64 + l_row) * D);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 x = upk(acc[2 * j]), y = upk(acc[2 * j + 1]);
+        q4[j] = make_float4(x.x, x.y, y.x, y.y);
+      }
     } else {
-      const float *col = blk + mu_col;
-#pragma unroll 8
-      for (int ym = 0; ym < 64; ++ym) {
-        const float l = col[ym * LAM_LD];
-        const unsigned long long l2 = pk(l, l);
-        const ulonglong2 *mv = reinterpret_cast<const ulonglong2 *>(sm + ym * D + 8 * mh);
+      // mu: columns 2 m_cp, 2 m_cp + 1; rows [32 m_rh, 32 m_rh + 32); a in [8 m_ah, 8 m_ah + 8)
+      const float *colp = blk + 2 * m_cp;
+#pragma unroll 4
+      for (int k = 0; k < 32; ++k) {
+        const int ym = 32 * m_rh + k;
+        const float2 l = *reinterpret_cast<const float2 *>(colp + ym * LAM_LD);
+        const unsigned long long lx = pk(l.x, l.x), ly = pk(l.y, l.y);
+        const ulonglong2 *mv = reinterpret_cast<const ulonglong2 *>(sm + ym * D + 8 * m_ah);
         const ulonglong2 m0 = mv[0], m1 = mv[1];
-        mu2[0] = fma2(l2, m0.x, mu2[0]);
-        mu2[1] = fma2(l2, m0.y, mu2[1]);
-        mu2[2] = fma2(l2, m1.x, mu2[2]);
-        mu2[3] = fma2(l2, m1.y, mu2[3]);
+        mu2[0][0] = fma2(lx, m0.x, mu2[0][0]);
+        mu2[0][1] = fma2(lx, m0.y, mu2[0][1]);
+        mu2[0][2] = fma2(lx, m1.x, mu2[0][2]);
+        mu2[0][3] = fma2(lx, m1.y, mu2[0][3]);
+        mu2[1][0] = fma2(ly, m0.x, mu2[1][0]);
+        mu2[1][1] = fma2(ly, m0.y, mu2[1][1]);
+        mu2[1][2] = fma2(ly, m1.x, mu2[1][2]);
+        mu2[1][3] = fma2(ly, m1.y, mu2[1][3]);
       }
     }
     __syncthreads();
+    // Lambda1 = the sum of the four column quarters
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int i = tid + G16_NT * k;
+      sL1[i] = sQ[i] + sQ[64 * D + i] + sQ[128 * D + i] + sQ[192 * D + i];
+    }
+    __syncthreads();
     {
-      // P(pair, :) += Lambda1(pair) R_c for this thread's two (row, a) pairs
+      // P(pair, :) += Lambda1(pair) R_c and l_c(:) += Lambda1(pair) M(pair)(:), for two pairs
       const ulonglong2 *rv = reinterpret_cast<const ulonglong2 *>(sr);
+      unsigned long long lc2[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) lc2[j] = 0ull;
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        const float L = sL1[tid + G16_NT * p];
+        const int pair = tid + G16_NT * p;  // ym D + a
+        const float L = sL1[pair];
         const unsigned long long L2 = pk(L, L);
+        const ulonglong2 *mr = reinterpret_cast<const ulonglong2 *>(sMn + (size_t)pair * D);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const ulonglong2 rr = rv[j];
+          const ulonglong2 rr = rv[j], mm = mr[j];
           P2[p][2 * j] = fma2(L2, rr.x, P2[p][2 * j]);
           P2[p][2 * j + 1] = fma2(L2, rr.y, P2[p][2 * j + 1]);
+          lc2[2 * j] = fma2(L2, mm.x, lc2[2 * j]);
+          lc2[2 * j + 1] = fma2(L2, mm.y, lc2[2 * j + 1]);
         }
       }
-      // l_c(b) = sum over ym of sum_a Lambda1(ym, a) M(ym)(a, b): thread (ym, b) for two ym
+      // sum the 16 values of l_c over the warp (transposed halving: 8 + 4 + 2 + 1 exchanges)
+      float v[16];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int e = tid + G16_NT * k, ym = e / D, b = e % D;
-        const float *lr = sL1 + ym * D;
-        const float *mr = sMn + ym * DD + b;
-        float x = 0.f;
+      for (int j = 0; j < 8; ++j) {
+        const float2 t = upk(lc2[j]);
+        v[2 * j] = t.x;
+        v[2 * j + 1] = t.y;
+      }
+      int cnt = 16;
 #pragma unroll
-        for (int a = 0; a < D; ++a) x = fmaf(lr[a], mr[a * D], x);
-        x += __shfl_xor_sync(0xffffffffu, x, 16);
-        if (lane < D) sLc[2 * w + k][lane] = x;
+      for (int sh = 16; sh >= 2; sh >>= 1) {
+        const int half = cnt / 2;
+        const bool hi = (lane & sh) != 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j < half) {
+            const float keep = hi ? v[half + j] : v[j];
+            const float send = hi ? v[j] : v[half + j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+          }
+        }
+        cnt = half;
+      }
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+      // lane bits 4..1 name the value: b = 8 b4 + 4 b3 + 2 b2 + b1
+      if ((lane & 1) == 0) {
+        const int b = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+        sLc[w][b] = v[0];
       }
     }
     __syncthreads();
     if (tid < D) {
       float t = 0.f;
 #pragma unroll
-      for (int ww = 0; ww < 2 * G16_NT / 32; ++ww) t += sLc[ww][tid];
+      for (int ww = 0; ww < G16_NT / 32; ++ww) t += sLc[ww][tid];
       lall[c * D + tid] = t;
     }
     if (++since == FLUSH) {
@@ -1023,7 +1106,7 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
   switch (A.kind) {
     case K_MPS_GRAD: {
       if constexpr (D >= 16) {
-        const size_t smem = (size_t)(2 * 64 * LAM_LD + 2 * 64 * D * D + 128 * D) * sizeof(float);
+        const size_t smem = (size_t)(2 * 64 * LAM_LD + 64 * D * D + 128 * D + 4 * 64 * D) * sizeof(float);
         cudaFuncSetAttribute(k_mps_grad16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_mps_grad16<<<dim3((unsigned)gr.gc, (unsigned)jobs), G16_NT, smem, s>>>(A);
       } else {
