@@ -26,6 +26,10 @@ def _dev(a, dtype=torch.float64):
 
 def _setup(insts, fp64=False, persistent=True):
     ans = [gv.Ansatz(i.n_qubits, i.reps) for i in insts]
+    # the batch runs every layer as tile passes; the single calls these tests compare
+    # with bit for bit do the same (no closed-form leading layers)
+    for a in ans:
+        a.set_mps_layers(-1)
     hams = [gv.Hamiltonian.from_workload(i.ham) for i in insts]
     b = gv.Batch(ans, hams, fp64=fp64)
     if persistent:  # most tests here exercise the persistent kernel; the staged one has its own
