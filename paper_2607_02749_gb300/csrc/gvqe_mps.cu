@@ -640,13 +640,16 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
 // the shared-memory pipe, not the FMA pipe, sets the pace.  FP32 accumulators
 // are added into the FP64 partials every 16 chunks.
 constexpr int G16_NT = 512;
+constexpr int G16_RS = 20;  // floats per 16-float row of the mid matrices and the quarters (16 + 4)
 __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
   constexpr int D = 16, DD = 256;
+  // 16-float rows read or written by consecutive lanes sit G16_RS floats apart:
+  // eight lanes' 16-byte accesses then fall in eight distinct bank groups
   extern __shared__ __align__(16) float dyn[];
-  float *slam = dyn;                   // [2][64][LAM_LD]
-  float *sMn = slam + 2 * 64 * LAM_LD; // [64][a][b]
-  float *sLo = sMn + 64 * DD;          // [128][D]
-  float *sQ = sLo + 128 * D;           // [4][64][D]: Lambda1 quarters; mu row halves at a flush
+  float *slam = dyn;                    // [2][64][LAM_LD]
+  float *sMn = slam + 2 * 64 * LAM_LD;  // [64 D rows (ym, a)][G16_RS]: M(ym)(a, b)
+  float *sLo = sMn + 64 * D * G16_RS;   // [128][D]
+  float *sQ = sLo + 128 * D;            // [4 x 64 rows][G16_RS]: Lambda1 quarters; mu row halves at a flush
   __shared__ __align__(16) float sm[64 * D];
   __shared__ __align__(16) float sb[2][DD + D];
   __shared__ __align__(16) float sr[D];
@@ -697,7 +700,7 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
     cp_async_commit();
   };
   stage(blockIdx.x, 0);
-  for (int i = tid; i < 64 * DD; i += G16_NT) sMn[i] = tab[d.mid + i];
+  for (int i = tid; i < 64 * DD; i += G16_NT) sMn[(i / D) * G16_RS + i % D] = tab[d.mid + i];
   for (int i = tid; i < 128 * D; i += G16_NT) sLo[i] = tab[d.lo + (i % D) * 128 + i / D];  // [yl][a]
   // mu: 2 columns x 8 a (packed pairs over a); P: 2 pairs x 16 b (packed pairs over b)
   unsigned long long mu2[2][4], P2[2][8];
@@ -711,11 +714,17 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
     for (int j = 0; j < 8; ++j) P2[p][j] = 0ull;
   auto flush = [&]() {
     // mu: the row-half-1 threads park their sums in sQ, the row-half-0 threads add both
+    // parked as [a (8)][column of the pair][a-half][column pair]: consecutive lanes, consecutive words
+    auto park = [&](int jj, int c2) { return ((jj * 2 + c2) * 2 + m_ah) * 64 + m_cp; };
     if (!l1w && m_rh == 1) {
 #pragma unroll
       for (int c2 = 0; c2 < 2; ++c2)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) *reinterpret_cast<float2 *>(&sQ[((c2 * 64 + m_cp) * 2 + m_ah) * 8 + 2 * j]) = upk(mu2[c2][j]);
+        for (int j = 0; j < 4; ++j) {
+          const float2 m = upk(mu2[c2][j]);
+          sQ[park(2 * j, c2)] = m.x;
+          sQ[park(2 * j + 1, c2)] = m.y;
+        }
     }
     __syncthreads();
     if (!l1w && m_rh == 0) {
@@ -724,9 +733,8 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float2 m = upk(mu2[c2][j]);
-          const float2 o = *reinterpret_cast<const float2 *>(&sQ[((c2 * 64 + m_cp) * 2 + m_ah) * 8 + 2 * j]);
-          part[(size_t)(8 * m_ah + 2 * j) * 128 + 2 * m_cp + c2] += (double)(m.x + o.x);
-          part[(size_t)(8 * m_ah + 2 * j + 1) * 128 + 2 * m_cp + c2] += (double)(m.y + o.y);
+          part[(size_t)(8 * m_ah + 2 * j) * 128 + 2 * m_cp + c2] += (double)(m.x + sQ[park(2 * j, c2)]);
+          part[(size_t)(8 * m_ah + 2 * j + 1) * 128 + 2 * m_cp + c2] += (double)(m.y + sQ[park(2 * j + 1, c2)]);
         }
     }
 #pragma unroll
@@ -763,7 +771,7 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int i = tid + G16_NT * k;  // ym D + a
-        const float4 *mrow = reinterpret_cast<const float4 *>(sMn + (size_t)i * D);
+        const float4 *mrow = reinterpret_cast<const float4 *>(sMn + (size_t)i * G16_RS);
         float acc = 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -798,7 +806,7 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
           }
         }
       }
-      float4 *q4 = reinterpret_cast<float4 *>(sQ + (l_q * 64 + l_row) * D);
+      float4 *q4 = reinterpret_cast<float4 *>(sQ + (l_q * 64 + l_row) * G16_RS);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float2 x = upk(acc[2 * j]), y = upk(acc[2 * j + 1]);
@@ -828,8 +836,8 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
     // Lambda1 = the sum of the four column quarters
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const int i = tid + G16_NT * k;
-      sL1[i] = sQ[i] + sQ[64 * D + i] + sQ[128 * D + i] + sQ[192 * D + i];
+      const int i = tid + G16_NT * k, o = (i / D) * G16_RS + i % D;  // row ym = i / D, a = i % D
+      sL1[i] = sQ[o] + sQ[64 * G16_RS + o] + sQ[128 * G16_RS + o] + sQ[192 * G16_RS + o];
     }
     __syncthreads();
     {
@@ -843,7 +851,7 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
         const int pair = tid + G16_NT * p;  // ym D + a
         const float L = sL1[pair];
         const unsigned long long L2 = pk(L, L);
-        const ulonglong2 *mr = reinterpret_cast<const ulonglong2 *>(sMn + (size_t)pair * D);
+        const ulonglong2 *mr = reinterpret_cast<const ulonglong2 *>(sMn + (size_t)pair * G16_RS);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const ulonglong2 rr = rv[j], mm = mr[j];
@@ -1106,7 +1114,7 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
   switch (A.kind) {
     case K_MPS_GRAD: {
       if constexpr (D >= 16) {
-        const size_t smem = (size_t)(2 * 64 * LAM_LD + 64 * D * D + 128 * D + 4 * 64 * D) * sizeof(float);
+        const size_t smem = (size_t)(2 * 64 * LAM_LD + 64 * D * G16_RS + 128 * D + 4 * 64 * G16_RS) * sizeof(float);
         cudaFuncSetAttribute(k_mps_grad16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_mps_grad16<<<dim3((unsigned)gr.gc, (unsigned)jobs), G16_NT, smem, s>>>(A);
       } else {
