@@ -231,7 +231,8 @@ constexpr int WR_NT = 256;  // 8 warps; warp w writes the rows w, w + 8, ... of 
 // their loads.
 template <int D>
 __global__ void __launch_bounds__(WR_NT) k_mps_write(const PassArgs A) {
-  extern __shared__ __align__(16) float sM[];  // [64][b][a] (transposed), dynamic (64 KiB at D = 16)
+  constexpr int MS_LD = D * D + D;  // per-ym stride: the lanes of m = M R_c cross ym on distinct banks
+  extern __shared__ __align__(16) float sM[];  // [64][b][a] (transposed), MS_LD floats per ym, dynamic
   __shared__ __align__(16) float sm[64 * 2 * D];  // m per row, each value twice: (m_a, m_a) pairs
   __shared__ __align__(16) float sb[2][D * D + D];  // staged [D][D] matrix and [D] vector, by chunk parity
   __shared__ float sr[D];
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(WR_NT) k_mps_write(const PassArgs A) {
   // read consecutive words for every b
   for (int i = tid; i < 64 * D * D; i += WR_NT) {
     const int ym = i / (D * D), b = (i / D) % D, a = i % D;
-    sM[i] = tab[d.mid + (ym * D + a) * D + b];
+    sM[ym * MS_LD + b * D + a] = tab[d.mid + (ym * D + a) * D + b];
   }
   unsigned long long L01[D], L23[D];  // (L[4l], L[4l+1]) and (L[4l+2], L[4l+3]) per bond index
 #pragma unroll
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(WR_NT) k_mps_write(const PassArgs A) {
     for (int k = 0; k < NM; ++k) {
       const int i = tid + k * WR_NT;  // i = ym D + a
       if (i < 64 * D) {
-        const float *mcol = sM + (i / D) * D * D + (i % D);
+        const float *mcol = sM + (i / D) * MS_LD + (i % D);
         float acc = 0.f;
 #pragma unroll
         for (int b = 0; b < D; ++b) acc = fmaf(mcol[b * D], sr[b], acc);
@@ -373,8 +374,9 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
   extern __shared__ __align__(16) float dyn[];
   constexpr bool BIG = D >= 16;
   float *slam = dyn;                        // [2][64][LAM_LD]
-  float *sM = slam + 2 * 64 * LAM_LD;       // [64][D][D]
-  float *sLo = sM + 64 * D * D;             // [128][D]
+  constexpr int MS_LD = D * D + D;          // per-ym stride of the transposed mid matrices
+  float *sM = slam + 2 * 64 * LAM_LD;       // [64][MS_LD]: [b][a]
+  float *sLo = sM + 64 * MS_LD;             // [128][D]
   float *sQ = sLo + 128 * D;                // [4][64][D] (D <= 8)
   float *sP = sLo + 128 * D;                // [64][D][D] (D = 16)
   __shared__ __align__(16) float sm[64 * D];  // m per row (8-byte pairs read as f32x2)
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
   stage(blockIdx.x, 0);
   for (int i = tid; i < 64 * D * D; i += GR_NT) {
     const int ym = i / (D * D), b = (i / D) % D, a = i % D;
-    sM[i] = tab[d.mid + (ym * D + a) * D + b];
+    sM[ym * MS_LD + b * D + a] = tab[d.mid + (ym * D + a) * D + b];
   }
   for (int i = tid; i < 128 * D; i += GR_NT) sLo[i] = tab[d.lo + (i % D) * 128 + i / D];  // [yl][a]
   constexpr int NMU2 = BIG ? D / 4 : D / 2;
@@ -510,7 +512,7 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
     }
     __syncthreads();
     for (int i = tid; i < 64 * D; i += GR_NT) {
-      const float *mcol = sM + (i / D) * D * D + (i % D);
+      const float *mcol = sM + (i / D) * MS_LD + (i % D);
       float acc = 0.f;
 #pragma unroll
       for (int b = 0; b < D; ++b) acc = fmaf(mcol[b * D], sr[b], acc);
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(GR_NT, 2) k_mps_grad(const PassArgs A) {
       // (GR_NT / D)-th (ym, a), then the warp and the CTA sum over g
       const int b = tid % D, g = tid / D;
       float x = 0.f;
-      for (int i = g; i < 64 * D; i += GR_NT / D) x = fmaf(sL1[i], sM[((i / D) * D + b) * D + (i % D)], x);
+      for (int i = g; i < 64 * D; i += GR_NT / D) x = fmaf(sL1[i], sM[(i / D) * MS_LD + b * D + (i % D)], x);
 #pragma unroll
       for (int off = D; off < 32; off <<= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
       if (lane < D) sLc[w][lane] = x;
@@ -913,9 +915,10 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
 template <int D>
 __global__ void __launch_bounds__(256) k_mps_ghigh(const PassArgs A) {
   constexpr int DD = D * D;
+  constexpr int ML = DD + 4;  // per-matrix stride: a warp's two matrices (y = 0, 1) on distinct banks
   constexpr int RMAX = 4;
-  __shared__ float sA[17 * 2 * DD];
-  __shared__ float sdA[(RMAX + 1) * 2 * DD];
+  __shared__ float sA[17 * 2 * ML];
+  __shared__ float sdA[(RMAX + 1) * 2 * ML];
   __shared__ double red[8][RMAX + 1];
   const int r = (D == 2) ? 1 : (D == 4 ? 2 : (D == 8 ? 3 : 4));
   const int n = A.n, K = n - MPS_CHUNK_BITS, q = MPS_CHUNK_BITS + blockIdx.y, job = blockIdx.z;
@@ -925,10 +928,10 @@ __global__ void __launch_bounds__(256) k_mps_ghigh(const PassArgs A) {
   const float *tab = reinterpret_cast<const float *>(A.in) + (size_t)job * A.in_stride;
   const float *lall = reinterpret_cast<const float *>(A.lam_in) + (size_t)job * A.lam_stride;
   double *part = A.part + (size_t)job * A.part_stride;
-  for (int i = tid; i < K * 2 * DD; i += 256) sA[i] = tab[d.sites + (long long)MPS_CHUNK_BITS * 2 * DD + i];
+  for (int i = tid; i < K * 2 * DD; i += 256) sA[(i / DD) * ML + i % DD] = tab[d.sites + (long long)MPS_CHUNK_BITS * 2 * DD + i];
   for (int i = tid; i < (r + 1) * 2 * DD; i += 256) {
     const int k = i / (2 * DD), e = i % (2 * DD);
-    sdA[i] = tab[d.dsites + ((long long)k * n + q) * 2 * DD + e];
+    sdA[(i / DD) * ML + i % DD] = tab[d.dsites + ((long long)k * n + q) * 2 * DD + e];
   }
   __syncthreads();
   const long long c = (long long)blockIdx.x * 256 + tid;
@@ -941,7 +944,7 @@ __global__ void __launch_bounds__(256) k_mps_ghigh(const PassArgs A) {
       sv[a] = 1.f;
     }
     for (int j = MPS_CHUNK_BITS; j < q; ++j) {
-      const float *M = sA + ((j - MPS_CHUNK_BITS) * 2 + (int)((c >> (j - MPS_CHUNK_BITS)) & 1)) * DD;
+      const float *M = sA + ((j - MPS_CHUNK_BITS) * 2 + (int)((c >> (j - MPS_CHUNK_BITS)) & 1)) * ML;
       float t[D];
 #pragma unroll
       for (int b = 0; b < D; ++b) {
@@ -954,7 +957,7 @@ __global__ void __launch_bounds__(256) k_mps_ghigh(const PassArgs A) {
       for (int b = 0; b < D; ++b) u[b] = t[b];
     }
     for (int j = n - 1; j > q; --j) {
-      const float *M = sA + ((j - MPS_CHUNK_BITS) * 2 + (int)((c >> (j - MPS_CHUNK_BITS)) & 1)) * DD;
+      const float *M = sA + ((j - MPS_CHUNK_BITS) * 2 + (int)((c >> (j - MPS_CHUNK_BITS)) & 1)) * ML;
       float t[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -968,7 +971,7 @@ __global__ void __launch_bounds__(256) k_mps_ghigh(const PassArgs A) {
     }
     const int yq = (int)((c >> (q - MPS_CHUNK_BITS)) & 1);
     for (int k = 0; k <= r; ++k) {
-      const float *M = sdA + (k * 2 + yq) * DD;
+      const float *M = sdA + (k * 2 + yq) * ML;
       float acc = 0.f;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -1118,7 +1121,7 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
         cudaFuncSetAttribute(k_mps_grad16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_mps_grad16<<<dim3((unsigned)gr.gc, (unsigned)jobs), G16_NT, smem, s>>>(A);
       } else {
-        const size_t smem = (size_t)(2 * 64 * LAM_LD + 64 * D * D + 128 * D + 4 * 64 * D) * sizeof(float);
+        const size_t smem = (size_t)(2 * 64 * LAM_LD + 64 * (D * D + D) + 128 * D + 4 * 64 * D) * sizeof(float);
         cudaFuncSetAttribute(k_mps_grad<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_mps_grad<D><<<dim3((unsigned)gr.gc, (unsigned)jobs), GR_NT, smem, s>>>(A);
       }
@@ -1160,7 +1163,7 @@ cudaError_t launch_mps_d(const PassArgs &A, int jobs, cudaStream_t s) {
   }
   const long long cap = (long long)num_sms_cached() * (D >= 16 ? 2 : 4);
   const dim3 grid((unsigned)(A.tiles < cap ? A.tiles : cap), (unsigned)jobs);
-  const size_t smem = (size_t)64 * D * D * sizeof(float);
+  const size_t smem = (size_t)64 * (D * D + D) * sizeof(float);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_mps_write<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_mps_write<D><<<grid, WR_NT, smem, s>>>(A);
   return cudaGetLastError();
