@@ -70,6 +70,8 @@ def parse_args():
     ap.add_argument("--only-cluster", action="store_true",
                     help="run only the 256-instance cluster batch leg and print its JSON object")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile plan (skip the autotuner)")
+    ap.add_argument("--mps-layers", type=int, default=0,
+                    help="closed-form leading layers (GVQE_OPT_MPS_LAYERS: 0 auto, -1 none, 1..4)")
     ap.add_argument("--cpu-single-core", action="store_true",
                     help="also time one full oracle E+grad at n=24 on one core (about 3-4 minutes)")
     return ap.parse_args()
@@ -716,6 +718,8 @@ def run_gvqe(args):
     dev = torch.device("cuda", local)
     h = gv.Hamiltonian.from_workload(ham)
     a = gv.Ansatz(n, reps)
+    if args.mps_layers:
+        a.set_mps_layers(args.mps_layers)
     th = torch.as_tensor(theta, dtype=torch.float64, device=dev)
     E = torch.empty(B, dtype=torch.float64, device=dev)
     G = torch.empty(B, P, dtype=torch.float64, device=dev)

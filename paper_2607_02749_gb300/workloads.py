@@ -198,6 +198,9 @@ WORKLOADS = {
     # n=27, reps=2, FP32: 2,000 Z-strings, 1 theta: a profiling-size case (512 MiB state,
     # larger than L2, a few GiB on the device in total).
     "n27_reps2_z2000": dict(n=27, reps=2, terms=2000, batch=1, kind="z"),
+    # n=27, reps=6, FP32: the same, with the benchmark's depth (closed-form layers 1..4
+    # and two tile-pass layers): the profiling-size case of the closed-form kernels.
+    "n27_reps6_z2000": dict(n=27, reps=6, terms=2000, batch=1, kind="z"),
     # n=28, reps=5, FP32: 5,000 strings over {I,X,Y,Z}, 8 thetas.
     "n28_reps5_pauli5000": dict(n=28, reps=5, terms=5000, batch=8, kind="pauli"),
     # n=26, reps=2, FP32: the same term mix, 1 theta: a profiling-size case of the
