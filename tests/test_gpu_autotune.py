@@ -33,7 +33,7 @@ def test_tuned_plan_matches_oracle_and_is_cached(tmp_path, n, reps, fp64):
     a = gv.Ansatz(n, reps)
     rep = a.autotune(h, _dev(th), fp64=fp64, cache=cache)
     print(rep)
-    items = re.findall(r"tb=(\d+)/([a-z ]+): ([0-9.]+) ms", rep)
+    items = re.findall(r"tb=(\d+)/(one run|split y=\d+): ([0-9.]+) ms", rep)
     assert len(items) >= 2, rep  # several distinct plans were timed
     m = re.search(r"measured: tile_bits=(\d+)", rep)
     assert m, rep
