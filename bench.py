@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile plan (skip the autotuner)")
     ap.add_argument("--mps-layers", type=int, default=0,
                     help="closed-form leading layers (GVQE_OPT_MPS_LAYERS: 0 auto, -1 none, 1..4)")
+    ap.add_argument("--mps-tensor", type=int, default=0,
+                    help="bond-16 closed-form gradient pass (GVQE_OPT_MPS_TENSOR: 0 tensor cores, -1 FP32 pipe)")
     ap.add_argument("--cpu-single-core", action="store_true",
                     help="also time one full oracle E+grad at n=24 on one core (about 3-4 minutes)")
     return ap.parse_args()
@@ -720,6 +722,8 @@ def run_gvqe(args):
     a = gv.Ansatz(n, reps)
     if args.mps_layers:
         a.set_mps_layers(args.mps_layers)
+    if args.mps_tensor:
+        a.set_mps_tensor(args.mps_tensor)
     th = torch.as_tensor(theta, dtype=torch.float64, device=dev)
     E = torch.empty(B, dtype=torch.float64, device=dev)
     G = torch.empty(B, P, dtype=torch.float64, device=dev)

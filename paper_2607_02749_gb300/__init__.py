@@ -90,6 +90,10 @@ class Ansatz(_Handle):
         """Leading layers written in closed form (GVQE_OPT_MPS_LAYERS): 0 auto, -1 none, 1..4."""
         gvqe_ansatz_set_option(self.handle, _lib.GVQE_OPT_MPS_LAYERS, layers)
 
+    def set_mps_tensor(self, mode: int) -> None:
+        """Bond-16 closed-form gradient pass (GVQE_OPT_MPS_TENSOR): 0 tensor cores (auto), -1 FP32 pipe."""
+        gvqe_ansatz_set_option(self.handle, _lib.GVQE_OPT_MPS_TENSOR, mode)
+
     def describe(self, fp64: bool = False) -> str:
         """The tile-pass plan of this ansatz (host only), with the last autotune report."""
         return gvqe_ansatz_describe(self.handle, GVQE_FP64 if fp64 else GVQE_FP32)

@@ -39,6 +39,7 @@ GVQE_OPT_GATES = 2
 GVQE_OPT_SPLIT_PASSES = 3
 GVQE_OPT_XY_TILE_BITS = 4
 GVQE_OPT_MPS_LAYERS = 5
+GVQE_OPT_MPS_TENSOR = 6
 GVQE_GATES_RY = 1
 GVQE_GATES_RY_RZ = 2
 GVQE_MAX_QUBITS = 30

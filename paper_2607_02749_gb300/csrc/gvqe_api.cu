@@ -587,7 +587,7 @@ int mps_layers_for(int n, int reps, int prec, int ent, int gates, int want) {
 }
 
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0,
-                bool state_only, int ent, int gates, int split, int xy_tb, int mps_layers) {
+                bool state_only, int ent, int gates, int split, int xy_tb, int mps_layers, bool mps_tc) {
   if (gates == 2) return build_plan_su2(n, reps, prec, tile_bits, want_grad, diag, ent, state_only, split);
   Plan pl;
   pl.n = n;
@@ -682,6 +682,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
   // whose table region then also keeps the site matrices for the gradients)
   pl.mps_layers = R;
   pl.mps_grad = mgrad;
+  pl.mps_tc = mgrad && R == MPS_MAX_LAYERS && mps_tc;
   for (int r = 1; r <= R; ++r) {
     uint32_t rot = 0;
     for (int j = 0; j < p; ++j) {
@@ -828,6 +829,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
         st.A.tiles = 1LL << (n - MPS_CHUNK_BITS);
         st.A.em = ent_map(ent, n, R);
         st.lam = (kind == K_MPS_GRAD) ? lam_cur : -1;
+        if (kind == K_MPS_GRAD && R == MPS_MAX_LAYERS && mps_tc) st.A.flags |= F_MPS_TC;
         st.part_region = base;
         pl.steps.push_back(st);
       }
@@ -900,7 +902,9 @@ std::string describe_plan(const Plan &pl) {
   if (pl.mps_layers > 0) {
     snprintf(buf, sizeof(buf), "  closed-form layers 1..%d (bond dimension up to %d), %lld table floats per job%s\n",
              pl.mps_layers, 1 << pl.mps_layers, pl.mps_elems,
-             pl.mps_grad ? "; their gradients from lambda and the matrix product" : "");
+             !pl.mps_grad ? ""
+             : pl.mps_tc  ? "; their gradients from lambda and the matrix product (tensor cores, TF32 split)"
+                          : "; their gradients from lambda and the matrix product");
     s += buf;
   }
   static const char *kinds[] = {"fwd",     "bwd",       "grad_l0",   "lambda_xy", "wht",     "mps",
@@ -1158,7 +1162,7 @@ Plan *gvqe::get_plan(gvqe_ansatz_s *a, int prec, bool want_grad, bool diag, bool
   if (it != a->plans.end() && it->second.tile_bits == tb) return &it->second;
   const int mps = allow_mps ? mps_layers_for(a->n, a->reps, prec, a->ent, a->gates, a->mps) : 0;
   Plan pl = build_plan(a->n, a->reps, prec, tb, want_grad, diag, false, state_only, a->ent, a->gates,
-                       eff_split(a, prec), eff_xy_tb(a, prec), mps);
+                       eff_split(a, prec), eff_xy_tb(a, prec), mps, a->mps_tc >= 0);
   pl.tile_bits = tb;
   a->plans[key] = std::move(pl);
   return &a->plans[key];
@@ -1512,6 +1516,13 @@ int gvqe_ansatz_set_option(gvqe_ansatz a, int option, int value) {
     if (value < -1 || value > MPS_MAX_LAYERS)
       return fail(GVQE_EINVAL, "closed-form layers %d outside [-1, %d] (0 = auto, -1 = none)", value, MPS_MAX_LAYERS);
     a->mps = value;
+    a->plans.clear();
+    return GVQE_OK;
+  }
+  if (option == GVQE_OPT_MPS_TENSOR) {
+    if (value < -1 || value > 0)
+      return fail(GVQE_EINVAL, "closed-form tensor-core mode %d is not 0 (auto) or -1 (FP32 pipe)", value);
+    a->mps_tc = value;
     a->plans.clear();
     return GVQE_OK;
   }

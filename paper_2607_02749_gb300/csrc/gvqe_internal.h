@@ -62,6 +62,7 @@ struct Plan {
   int final_buf = -1;         // state-only plans: buffer of the final state
   int mps_layers = 0;         // leading layers written in closed form (K_MPS steps)
   bool mps_grad = false;      // ... and their gradients from lambda and the matrix product
+  bool mps_tc = false;        // ... with the bond-16 lambda contractions on the tensor cores
   long long mps_elems = 0;    // floats of closed-form tables per job (one stage at a time)
   DevBuf d_dir;
   int d_dir_count = 0;
@@ -78,10 +79,11 @@ void count_launches(int k);
 // RZ on every qubit (complex amplitudes; diagonal H, energy and gradient only).
 // xy_tb: tile bits of the X-mask pass (0: those of the layer's first pass).
 // mps_layers: the leading layers after layer 0 whose states K_MPS steps write
-// in closed form (0: none; see mps_layers_for).
+// in closed form (0: none; see mps_layers_for).  mps_tc: at bond dimension 16
+// the gradient pass over lambda contracts on the tensor cores (F_MPS_TC).
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false,
                 bool state_only = false, int ent = ENT_LINEAR, int gates = 1, int split = SPLIT_AUTO, int xy_tb = 0,
-                int mps_layers = 0);
+                int mps_layers = 0, bool mps_tc = true);
 // How many leading layers a plan may write in closed form: FP32, RY layers,
 // an entangler whose index map ties each qubit only to the one below it
 // (linear, full, reverse linear), n >= MPS_MIN_QUBITS, and never the last
@@ -141,6 +143,7 @@ struct gvqe_ansatz_s {
   int xy_tb = 0;                 // GVQE_OPT_XY_TILE_BITS (0: the first pass's tile bits)
   int tuned_xy_tb[2] = {0, 0};   // per precision, chosen by gvqe_autotune (0: none)
   int mps = 0;                   // GVQE_OPT_MPS_LAYERS (0 auto, -1 none, 1..4 at most that many)
+  int mps_tc = 0;                // GVQE_OPT_MPS_TENSOR (0 auto = tensor cores, -1 = FP32 pipe)
   std::map<int, gvqe::Plan> plans;
   gvqe::DevBuf ws, aux, shift, ro, tune;
   std::string tune_report;  // the last gvqe_autotune sweep and its choice (empty: not tuned)

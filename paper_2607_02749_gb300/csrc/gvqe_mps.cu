@@ -909,6 +909,385 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
   cp_async_wait<0>();
 }
 
+// ------------------------------------------------ bond 16 on the tensor cores --
+// The two contractions of the bond-16 pass that grow with the chunk,
+// Lambda1 = lambda_c L (64 x 128 by 128 x 16) and mu += lambda_c^T m
+// (128 x 64 by 64 x 16), run as tcgen05.mma kind::tf32 with FP32 accumulators
+// in tensor memory.  TF32 keeps 10 mantissa bits, so every operand x is split
+// into x_hi (x with its low 13 mantissa bits cleared) and x_lo = x - x_hi
+// (four-term split products, relative error about 2^-21 per product, the level
+// of the FP32 SIMT pass): Lambda1 takes A = [lambda_hi; lambda_lo] (128 rows)
+// against B = [L_hi | L_lo] (N = 32) in one 128 x 32 accumulator, whose four
+// 64 x 16 blocks add up to Lambda1; mu takes A = lambda_hi^T, then lambda_lo^T,
+// against B = [m_hi | m_lo] into a 128 x 32 accumulator, whose two column halves
+// add up to mu: 16 + 16 MMAs (M = 128, N = 32, K = 8) per chunk.  Both contractions read lambda
+// with K-major operands (the tensor cores' MN-major form came out zero for
+// TF32 on this part), so each chunk's split lambda is written twice: rows ym
+// with runs of yl for Lambda1, rows yl with runs of ym for mu.  Operand
+// layout: no swizzle, core matrices of 8 rows x 16 bytes; LBO steps along K,
+// SBO along the rows.  The K strides are padded (144 bytes between the
+// Lambda1 core matrices along yl, 2064 bytes between 8-row groups of the mu
+// copy) so that the split writes, one 4 x 4 block per thread, are free of
+// bank conflicts.
+//
+// The rest stays on the FP32 pipe: R_c, m = M R_c and, for the previous chunk
+// while the tensor cores work on this one, P += Lambda1 (x) R_c and
+// l_c = sum Lambda1 M (each thread keeps its two rows of the mid matrices in
+// registers for the whole pass).  mu stays in tensor memory for FLUSH chunks,
+// then both mu and P are added into the FP64 partials.
+//
+// One thread issues the MMAs and commits them to an mbarrier; every thread
+// waits on it with a bounded spin.  A wait that runs out (not expected: the
+// MMAs always complete) writes NaN into the CTA's partials, so the job's
+// gradients come out NaN, and frees tensor memory only once the MMAs are done.
+constexpr int TC_NT = 512;
+constexpr int TC_FLUSH = 16;
+// float offsets of the shared-memory regions
+constexpr int TC_A1 = 0;                   // lambda for Lambda1: 16 groups of 8 rows x 4608 bytes
+constexpr int TC_AT = TC_A1 + 16 * 1152;   // lambda^T for mu: hi, lo, 16 groups x 2064 bytes each
+constexpr int TC_LH = TC_AT + 2 * 8256;    // L_hi (B of Lambda1: 16 a-rows x 128 yl), 8 KB
+constexpr int TC_LL = TC_LH + 2048;        // L_lo
+constexpr int TC_MH = TC_LL + 2048;        // m_hi (B of mu: 16 a-rows x 64 ym), 4 KB
+constexpr int TC_ML = TC_MH + 1024;        // m_lo
+constexpr int TC_RAW = TC_ML + 1024;       // the next chunk of lambda as read: [64][128]
+constexpr int TC_Q = TC_RAW + 64 * 128;    // Lambda1 rows from tensor memory: 128 x 20
+constexpr int TC_SB = TC_Q + 128 * 20;     // staged M_h1 and r_h2: [2][272]
+constexpr int TC_SR = TC_SB + 2 * 272;     // R_c: [2][16]
+constexpr int TC_LC = TC_SR + 32;          // l_c per warp: [16][16]
+constexpr int TC_BAR = TC_LC + 256;        // mbarrier (8 bytes) and the tensor-memory address
+constexpr size_t TC_SMEM = (size_t)(TC_BAR + 4) * sizeof(float);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// shared-memory matrix descriptor: start address, LBO and SBO in 16-byte units,
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, M = 128, N = 32
+constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// the two parts of x: hi keeps the sign, exponent and top 10 mantissa bits (a TF32
+// value), lo = x - hi exactly; the tensor cores read lo's top 19 bits, so lo loses
+// under 2^-11 of itself, about 2^-21 of x
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc));
+}
+__device__ __forceinline__ void tc_ld16(uint32_t ta, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
+  constexpr int D = 16, DD = 256;
+  extern __shared__ __align__(16) float dyn[];
+  float *sA1 = dyn + TC_A1, *sAT = dyn + TC_AT, *sQ = dyn + TC_Q, *sb = dyn + TC_SB, *sr = dyn + TC_SR;
+  float *sraw = dyn + TC_RAW;
+  float *sLc = dyn + TC_LC;
+  const uint32_t bar = smem_u32(dyn + TC_BAR);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(dyn + TC_BAR + 2);
+  const MpsDims d = mps_dims(A.n, 4);
+  const MpsGradRegions gr = mps_grad_regions(A.n, 4);
+  const int job = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const float *tab = reinterpret_cast<const float *>(A.in) + (size_t)job * A.in_stride;
+  const float *lam = reinterpret_cast<const float *>(A.lam_in) + (size_t)job * A.lam_stride;
+  double *part = A.part + (size_t)job * A.part_stride + (size_t)blockIdx.x * gr.v1;
+  float *lall = reinterpret_cast<float *>(A.out) + (size_t)job * A.out_stride;
+  const long long chunks = A.tiles;
+  const long long mask1 = (1LL << d.h1) - 1;
+  // rows of the mid matrices (pairs (ym, a), index 16 ym + a) owned by this thread:
+  // lanes of warp w sit in tensor-memory lanes 32 (w % 4) .. + 31
+  const int pr0 = 128 * (w >> 2) + 32 * (w & 3) + lane;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) part[tid + TC_NT * k] = 0.0;  // mu: [a][yl]
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int b = 0; b < D; ++b) part[128 * D + (size_t)(pr0 + 512 * p) * D + b] = 0.0;
+  // L split into its B operand (rows a, runs of 4 yl): L(yl, a) = tab[lo + 128 a + yl]
+  for (int i = tid; i < 128 * D; i += TC_NT) {
+    const int a = i >> 7, yl = i & 127;
+    const float x = tab[d.lo + i], h = tf32_hi(x);
+    const int o = (a >> 3) * 1024 + (yl >> 2) * 32 + (a & 7) * 4 + (yl & 3);
+    dyn[TC_LH + o] = h;
+    dyn[TC_LL + o] = x - h;
+  }
+  unsigned long long Mr[2][8];  // M(ym)(a, b) for this thread's two pairs, packed over b
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const float4 *src = reinterpret_cast<const float4 *>(tab + d.mid + (size_t)(pr0 + 512 * p) * D);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 v = src[j];
+      Mr[p][2 * j] = pk(v.x, v.y);
+      Mr[p][2 * j + 1] = pk(v.z, v.w);
+    }
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  auto stage = [&](long long c, int buf) {
+    if (tid < 68) {
+      const float *src = (tid < DD / 4) ? tab + d.m1 + (c & mask1) * DD + 4 * tid
+                                        : tab + d.r2 + (c >> d.h1) * D + 4 * (tid - DD / 4);
+      cp_async16(sb + buf * 272 + 4 * tid, src);
+    }
+    // this thread's 4 x 4 block of lambda: rows ym = 4 w + i, columns yl = 4 lane + j
+    // (each thread copies, and later reads, only its own block)
+    const float *lc = lam + (c << MPS_CHUNK_BITS) + 4 * lane;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cp_async16(sraw + (4 * w + i) * 128 + 4 * lane, lc + (4 * w + i) * 128);
+    cp_async_commit();
+  };
+  stage(blockIdx.x, 0);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot, tL = tmem, tM = tmem + 32;
+  const uint32_t tw = tmem + ((uint32_t)(32 * (w & 3)) << 16);  // this warp's lane quarter
+  unsigned long long P2[2][8];
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) P2[p][j] = 0ull;
+  bool ok = true, mu_acc = false;
+  int since = 0, par = 0;
+  uint32_t phase = 0;
+  long long cprev = -1;
+
+  // P and l_c of chunk cp from the Lambda1 rows in sQ and R_c in sr[rb]
+  auto update_prev = [&](long long cp, int rb) {
+    unsigned long long L2[2], lc2[8];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int pr = pr0 + 512 * p, ym = pr >> 4, a = pr & 15;
+      const float L = sQ[ym * 20 + a] + sQ[(64 + ym) * 20 + a];
+      L2[p] = pk(L, L);
+    }
+    const ulonglong2 *r2 = reinterpret_cast<const ulonglong2 *>(sr + 16 * rb);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const ulonglong2 t = r2[j];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        P2[p][2 * j] = fma2(L2[p], t.x, P2[p][2 * j]);
+        P2[p][2 * j + 1] = fma2(L2[p], t.y, P2[p][2 * j + 1]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) lc2[j] = fma2(L2[1], Mr[1][j], mul2(L2[0], Mr[0][j]));
+    // the 16 values of l_c summed over the warp (transposed halving)
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float2 t = upk(lc2[j]);
+      v[2 * j] = t.x;
+      v[2 * j + 1] = t.y;
+    }
+    int cnt = 16;
+#pragma unroll
+    for (int sh = 16; sh >= 2; sh >>= 1) {
+      const int half = cnt / 2;
+      const bool hi = (lane & sh) != 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (j < half) {
+          const float keep = hi ? v[half + j] : v[j];
+          const float send = hi ? v[j] : v[half + j];
+          v[j] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+        }
+      }
+      cnt = half;
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    if ((lane & 1) == 0) {
+      const int b = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+      sLc[w * 16 + b] = v[0];
+    }
+    __syncthreads();
+    if (tid < D) {
+      float t = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < TC_NT / 32; ++ww) t += sLc[ww * 16 + tid];
+      lall[cp * D + tid] = t;
+    }
+  };
+  auto flush_mu = [&]() {
+    if (w < 4) {
+      float v[16], u[16];
+      tc_ld16(tw + 32, v);  // mu rows yl = 32 w + lane: lambda^T m_hi and lambda^T m_lo
+      tc_ld16(tw + 48, u);
+#pragma unroll
+      for (int a = 0; a < D; ++a) part[a * 128 + 32 * w + lane] += (double)(v[a] + u[a]);
+    }
+  };
+  auto flush_p = [&]() {
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float2 v = upk(P2[p][j]);
+        double *dst = part + 128 * D + (size_t)(pr0 + 512 * p) * D + 2 * j;
+        dst[0] += (double)v.x;
+        dst[1] += (double)v.y;
+        P2[p][j] = 0ull;
+      }
+  };
+
+  for (long long c = blockIdx.x; c < chunks; c += gridDim.x, par ^= 1) {
+    cp_async_wait<0>();
+    __syncthreads();  // S1: sb[par] staged, the previous Lambda1 rows in sQ
+    if (tid < D) {
+      float acc = 0.f;
+#pragma unroll
+      for (int b = 0; b < D; ++b) acc = fmaf(sb[par * 272 + tid * D + b], sb[par * 272 + DD + b], acc);
+      sr[16 * par + tid] = acc;
+    }
+    const bool more = c + gridDim.x < chunks;
+    {
+      // split this chunk's block into both operand copies (the previous MMAs are complete)
+      float h[4][4], l[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 v = *reinterpret_cast<const float4 *>(sraw + (4 * w + i) * 128 + 4 * lane);
+        const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          h[i][j] = tf32_hi(x[j]);
+          l[i][j] = x[j] - h[i][j];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = 4 * w + i;
+        const int o = (row >> 3) * 1152 + lane * 36 + (row & 7) * 4;
+        *reinterpret_cast<float4 *>(sA1 + o) = make_float4(h[i][0], h[i][1], h[i][2], h[i][3]);
+        *reinterpret_cast<float4 *>(sA1 + 8 * 1152 + o) = make_float4(l[i][0], l[i][1], l[i][2], l[i][3]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int yl = 4 * lane + j;
+        const int o = (yl >> 3) * 516 + w * 32 + (yl & 7) * 4;
+        *reinterpret_cast<float4 *>(sAT + o) = make_float4(h[0][j], h[1][j], h[2][j], h[3][j]);
+        *reinterpret_cast<float4 *>(sAT + 8256 + o) = make_float4(l[0][j], l[1][j], l[2][j], l[3][j]);
+      }
+    }
+    if (more) stage(c + gridDim.x, par ^ 1);  // sb[par ^ 1] was read a chunk ago; this thread's block is split
+    __syncthreads();  // S2: R_c in sr[par]
+    {
+      // m(ym)(a) = M(ym)(a, :) R_c for this thread's pairs, split into the B operand of mu
+      const ulonglong2 *r2 = reinterpret_cast<const ulonglong2 *>(sr + 16 * par);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        unsigned long long acc = 0ull;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const ulonglong2 t = r2[j];
+          acc = fma2(Mr[p][2 * j], t.x, acc);
+          acc = fma2(Mr[p][2 * j + 1], t.y, acc);
+        }
+        const float2 s2 = upk(acc);
+        const float m = s2.x + s2.y, hm = tf32_hi(m);
+        const int pr = pr0 + 512 * p, ym = pr >> 4, a = pr & 15;
+        const int o = (a >> 3) * 512 + (ym >> 2) * 32 + (a & 7) * 4 + (ym & 3);
+        dyn[TC_MH + o] = hm;
+        dyn[TC_ML + o] = m - hm;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();  // S3: operands in shared memory
+    tc_fence_after();
+    if (tid == 0) {
+      // B operands [L_hi | L_lo] and [m_hi | m_lo]: N = 32 rows, the lo rows two 8-row groups on
+      const uint64_t a1 = tc_desc(smem_u32(sA1), 144, 4608);
+      const uint64_t lb = tc_desc(smem_u32(dyn + TC_LH), 128, 4096);
+      const uint64_t th = tc_desc(smem_u32(sAT), 128, 2064), tl = tc_desc(smem_u32(sAT + 8256), 128, 2064);
+      const uint64_t mb = tc_desc(smem_u32(dyn + TC_MH), 128, 2048);
+      // K steps of 8: 288 bytes (two core matrices at LBO 144) along yl, 256 bytes along ym
+#pragma unroll 1
+      for (int s = 0; s < 16; ++s) tc_mma(tL, a1 + 18 * s, lb + 16 * s, s > 0);
+#pragma unroll 1
+      for (int s = 0; s < 8; ++s) {
+        tc_mma(tM, th + 16 * s, mb + 16 * s, (s > 0 || mu_acc) ? 1 : 0);
+        tc_mma(tM, tl + 16 * s, mb + 16 * s, 1);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                   : "memory");
+    }
+    mu_acc = true;
+    if (cprev >= 0) update_prev(cprev, par ^ 1);  // overlaps this chunk's MMAs; ends with a barrier
+    if (!__syncthreads_and(mbar_wait_bounded(bar, phase) ? 1 : 0)) {
+      ok = false;
+      break;
+    }
+    phase ^= 1;
+    tc_fence_after();
+    if (w < 4) {
+      float v[16], u[16];
+      tc_ld16(tw, v);  // row 32 w + lane of [lambda_hi; lambda_lo] L_hi, then of ... L_lo
+      tc_ld16(tw + 16, u);
+      float4 *q4 = reinterpret_cast<float4 *>(sQ + (32 * w + lane) * 20);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        q4[k] = make_float4(v[4 * k] + u[4 * k], v[4 * k + 1] + u[4 * k + 1], v[4 * k + 2] + u[4 * k + 2],
+                            v[4 * k + 3] + u[4 * k + 3]);
+    }
+    if (++since == TC_FLUSH) {
+      flush_mu();
+      flush_p();
+      since = 0;
+      mu_acc = false;
+    }
+    tc_fence_before();
+    cprev = c;
+  }
+  if (ok) {
+    __syncthreads();
+    if (cprev >= 0) update_prev(cprev, par ^ 1);
+    if (since > 0) flush_mu();
+    flush_p();
+  }
+  cp_async_wait<0>();
+  if (!ok) {
+    // a wait ran out: poison this CTA's partials, give the MMAs another bounded wait
+    for (int i = tid; i < gr.v1; i += TC_NT) part[i] = __longlong_as_double(0x7ff8000000000000LL);
+    ok = __syncthreads_and(mbar_wait_bounded(bar, phase) ? 1 : 0) != 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (w == 0 && ok) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+}
+
 // High qubits: block (x, q - 13) takes chunks 256 x .. 256 x + 255 and qubit q.
 // Thread c forms u = l_c A_13 .. A_{q-1} and s = A_{q+1} .. A_{n-1} 1 and adds
 // u dA_q^k s for every layer k <= r; the block's FP64 sums go to its partials.
@@ -1117,6 +1496,11 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
   switch (A.kind) {
     case K_MPS_GRAD: {
       if constexpr (D >= 16) {
+        if (A.flags & F_MPS_TC) {
+          cudaFuncSetAttribute(k_mps_grad16tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+          k_mps_grad16tc<<<dim3((unsigned)gr.gc, (unsigned)jobs), TC_NT, TC_SMEM, s>>>(A);
+          break;
+        }
         const size_t smem = (size_t)(2 * 64 * LAM_LD + 64 * D * G16_RS + 128 * D + 4 * 64 * G16_RS) * sizeof(float);
         cudaFuncSetAttribute(k_mps_grad16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_mps_grad16<<<dim3((unsigned)gr.gc, (unsigned)jobs), G16_NT, smem, s>>>(A);

@@ -322,14 +322,28 @@ def test_closed_form_layer_option_and_plans():
 
     d = desc(30, 6)
     assert ("closed-form layers 1..4 (bond dimension up to 16), 245760 table floats per job; their gradients "
-            "from lambda and the matrix product") in d
+            "from lambda and the matrix product (tensor cores, TF32 split)") in d
     # layer 4's final state in closed form, layers 5..6 as tile passes and their backward, then the
     # gradients of layers 0..4 from lambda_4 (no backward passes and no layer-0 pass below layer 5)
     assert steps_of(d) == (["mps_tab", "mps"] + ["fwd"] * 6 + ["bwd"] * 6
                            + ["mps_grad", "mps_ghigh", "mps_gred", "mps_genv"])
     d3 = desc(30, 6, mps=3)
     assert ("closed-form layers 1..3 (bond dimension up to 8), 59136 table floats per job; their gradients "
-            "from lambda and the matrix product") in d3
+            "from lambda and the matrix product\n") in d3  # bond 8: FP32 pipe
+    # GVQE_OPT_MPS_TENSOR: -1 keeps the bond-16 gradient pass on the FP32 pipe; same steps
+    a = _lib.gvqe_ansatz_create(30, 6)
+    try:
+        _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_MPS_TENSOR, -1)
+        d_fp32 = _lib.gvqe_ansatz_describe(a, _lib.GVQE_FP32)
+        assert "matrix product\n" in d_fp32 and "tensor cores" not in d_fp32
+        assert steps_of(d_fp32) == steps_of(d)
+        _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_MPS_TENSOR, 0)
+        assert "(tensor cores, TF32 split)" in _lib.gvqe_ansatz_describe(a, _lib.GVQE_FP32)
+        for bad in (-2, 1):
+            with pytest.raises(_lib.GvqeError):
+                _lib.gvqe_ansatz_set_option(a, _lib.GVQE_OPT_MPS_TENSOR, bad)
+    finally:
+        _lib.gvqe_destroy(a)
     assert steps_of(d3).count("fwd") == 9 and steps_of(d3).count("bwd") == 9
     for ent in (_lib.GVQE_ENT_FULL, _lib.GVQE_ENT_REVERSE_LINEAR):
         assert "closed-form layers 1..4 " in desc(20, 5, ent)

@@ -167,3 +167,48 @@ def test_plans_without_closed_form_layers():
     a = gv.Ansatz(16, 4)
     a.set_mps_layers(-1)
     assert "closed-form" not in a.describe()
+
+
+def _run_opts(n, reps, ham, th, ent, mps, tensor):
+    a = gv.Ansatz(n, reps, entangler=ent)
+    a.set_mps_layers(mps)
+    a.set_mps_tensor(tensor)
+    h = gv.Hamiltonian.from_workload(ham)
+    e, g = gv.energy_grad(a, h, torch.as_tensor(th, device="cuda"))
+    desc = a.describe()
+    a.close()
+    h.close()
+    return e.cpu().numpy(), g.cpu().numpy(), desc
+
+
+# bond dimension 16 (four closed-form layers): the tensor-core gradient pass
+# (TF32 split operands) against the FP32-pipe pass and against plans with every
+# layer as tile passes; n = 25 gives 4096 chunks, 27 per CTA (the FP64 flush of
+# the tensor-memory accumulators inside the loop), batch 3 three CTA waves
+@pytest.mark.parametrize("n,reps,batch,ent", [(17, 5, 2, gv.GVQE_ENT_LINEAR), (21, 6, 3, gv.GVQE_ENT_FULL),
+                                              (25, 5, 3, gv.GVQE_ENT_LINEAR),
+                                              (23, 5, 1, gv.GVQE_ENT_REVERSE_LINEAR)])
+def test_tensor_core_gradient_pass(n, reps, batch, ent):
+    ham = wl.z_hamiltonian(n, 4 * n, seed=n)
+    th = wl.thetas(n, reps, batch, seed=300 + n)
+    e_tc, g_tc, d_tc = _run_opts(n, reps, ham, th, ent, 0, 0)
+    assert "closed-form layers 1..4 " in d_tc and "(tensor cores, TF32 split)" in d_tc, d_tc
+    e_f, g_f, d_f = _run_opts(n, reps, ham, th, ent, 0, -1)
+    assert "closed-form layers 1..4 " in d_f and "tensor cores" not in d_f
+    e_t, g_t, d_t = _run_opts(n, reps, ham, th, ent, -1, 0)
+    assert "closed-form" not in d_t
+    assert np.all(np.isfinite(g_tc))
+    scale = ham.abs_sum()
+    assert np.max(np.abs(e_tc - e_t)) <= FP32_E * scale
+    for b in range(batch):
+        r_f = np.linalg.norm(g_tc[b] - g_f[b]) / np.linalg.norm(g_f[b])
+        r_t = np.linalg.norm(g_tc[b] - g_t[b]) / np.linalg.norm(g_t[b])
+        r_ft = np.linalg.norm(g_f[b] - g_t[b]) / np.linalg.norm(g_t[b])
+        # the closed-form layers' own gradients (layers 0..4), where the pass differs
+        lo = slice(0, 5 * n)
+        r_lo = np.linalg.norm(g_tc[b][lo] - g_t[b][lo]) / np.linalg.norm(g_t[b][lo])
+        print(f"n={n} reps={reps} b={b}: tensor vs FP32 pipe {r_f:.2e}, tensor vs tile passes {r_t:.2e} "
+              f"(layers 0..4 {r_lo:.2e}), FP32 pipe vs tile passes {r_ft:.2e}")
+        assert r_t <= FP32_G and r_f <= FP32_G and r_lo <= FP32_G
+    if n <= 17:
+        _check_oracle(e_tc, g_tc, n, reps, th, ham, ent, "tensor-core pass")
