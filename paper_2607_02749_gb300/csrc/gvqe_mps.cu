@@ -936,26 +936,36 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
 // registers for the whole pass).  mu stays in tensor memory for FLUSH chunks,
 // then both mu and P are added into the FP64 partials.
 //
-// One thread issues the MMAs and commits them to an mbarrier; every thread
-// waits on it with a bounded spin.  A wait that runs out (not expected: the
-// MMAs always complete) writes NaN into the CTA's partials, so the job's
-// gradients come out NaN, and frees tensor memory only once the MMAs are done.
+// Pipeline.  lambda is copied (cp.async) straight into the Lambda1 operand
+// layout: those FP32 values are lambda_hi as the tensor cores read them (the
+// top 19 bits), so only lambda_lo and the mu copy are written by the threads.
+// The copy buffer is double: [hi 0 | lo | hi 1], and chunk parity 0 stacks
+// [hi 0; lo], parity 1 [lo; hi 1] (either way Lambda1 is the sum of the two
+// 64-row halves).  Lambda1's accumulator is double too.  One thread issues
+// each chunk's MMAs in two commits, Lambda1 (mbarrier barL) and mu (barM), so
+// that lambda_lo of chunk c + 1 is written while mu(c) runs and the mu copy of
+// c + 1 while Lambda1(c + 1) runs; the previous chunk's Lambda1 rows are read
+// out and its P and l_c formed meanwhile.  Three CTA barriers per chunk.
+//
+// Every thread waits on the mbarriers with a bounded spin.  A wait that runs
+// out (not expected: the MMAs always complete) writes NaN into the CTA's
+// partials, so the job's gradients come out NaN, and frees tensor memory only
+// once both mbarriers report their last commit complete.
 constexpr int TC_NT = 512;
 constexpr int TC_FLUSH = 16;
 // float offsets of the shared-memory regions
-constexpr int TC_A1 = 0;                   // lambda for Lambda1: 16 groups of 8 rows x 4608 bytes
-constexpr int TC_AT = TC_A1 + 16 * 1152;   // lambda^T for mu: hi, lo, 16 groups x 2064 bytes each
-constexpr int TC_LH = TC_AT + 2 * 8256;    // L_hi (B of Lambda1: 16 a-rows x 128 yl), 8 KB
-constexpr int TC_LL = TC_LH + 2048;        // L_lo
-constexpr int TC_MH = TC_LL + 2048;        // m_hi (B of mu: 16 a-rows x 64 ym), 4 KB
-constexpr int TC_ML = TC_MH + 1024;        // m_lo
-constexpr int TC_RAW = TC_ML + 1024;       // the next chunk of lambda as read: [64][128]
-constexpr int TC_Q = TC_RAW + 64 * 128;    // Lambda1 rows from tensor memory: 128 x 20
-constexpr int TC_SB = TC_Q + 128 * 20;     // staged M_h1 and r_h2: [2][272]
-constexpr int TC_SR = TC_SB + 2 * 272;     // R_c: [2][16]
-constexpr int TC_LC = TC_SR + 32;          // l_c per warp: [16][16]
-constexpr int TC_BAR = TC_LC + 256;        // mbarrier (8 bytes) and the tensor-memory address
-constexpr size_t TC_SMEM = (size_t)(TC_BAR + 4) * sizeof(float);
+constexpr int TC_HALF = 8 * 1152;         // 64 rows of the Lambda1 operand: 8 groups x 4608 bytes
+constexpr int TC_A1 = 0;                  // lambda for Lambda1: [hi 0 | lo | hi 1]
+constexpr int TC_AT = TC_A1 + 3 * TC_HALF;  // lambda^T for mu: hi, lo, 16 groups x 2064 bytes each
+constexpr int TC_LB = TC_AT + 2 * 8256;   // [L_hi | L_lo] (B of Lambda1: 32 rows x 128 yl), 16 KB
+constexpr int TC_MB = TC_LB + 4096;       // [m_hi | m_lo] (B of mu: 32 rows x 64 ym), 8 KB
+constexpr int TC_Q = TC_MB + 2048;        // Lambda1 rows from tensor memory: 128 x 20
+constexpr int TC_SB = TC_Q + 128 * 20;    // staged M_h1 and r_h2: [2][272]
+constexpr int TC_SR = TC_SB + 2 * 272;    // R_c: [2][16]
+constexpr int TC_LC = TC_SR + 32;         // l_c per warp: [16][16]
+constexpr int TC_BAR = TC_LC + 256;       // mbarriers barL, barM (8 bytes each), the tensor-memory address
+constexpr size_t TC_SMEM = (size_t)(TC_BAR + 8) * sizeof(float);
+static_assert(TC_SMEM <= 232448, "the bond-16 tensor-core pass needs at most 227 KB of shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 // shared-memory matrix descriptor: start address, LBO and SBO in 16-byte units,
@@ -1004,11 +1014,9 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
   constexpr int D = 16, DD = 256;
   extern __shared__ __align__(16) float dyn[];
-  float *sA1 = dyn + TC_A1, *sAT = dyn + TC_AT, *sQ = dyn + TC_Q, *sb = dyn + TC_SB, *sr = dyn + TC_SR;
-  float *sraw = dyn + TC_RAW;
-  float *sLc = dyn + TC_LC;
-  const uint32_t bar = smem_u32(dyn + TC_BAR);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(dyn + TC_BAR + 2);
+  float *sAT = dyn + TC_AT, *sQ = dyn + TC_Q, *sb = dyn + TC_SB, *sr = dyn + TC_SR, *sLc = dyn + TC_LC;
+  const uint32_t barL = smem_u32(dyn + TC_BAR), barM = barL + 8;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(dyn + TC_BAR + 4);
   const MpsDims d = mps_dims(A.n, 4);
   const MpsGradRegions gr = mps_grad_regions(A.n, 4);
   const int job = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -1018,22 +1026,26 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
   float *lall = reinterpret_cast<float *>(A.out) + (size_t)job * A.out_stride;
   const long long chunks = A.tiles;
   const long long mask1 = (1LL << d.h1) - 1;
-  // rows of the mid matrices (pairs (ym, a), index 16 ym + a) owned by this thread:
-  // lanes of warp w sit in tensor-memory lanes 32 (w % 4) .. + 31
+  // rows of the mid matrices (pairs (ym, a), index 16 ym + a) owned by this thread
   const int pr0 = 128 * (w >> 2) + 32 * (w & 3) + lane;
+  // the serial jobs sit in different warps, so that no warp reaches the CTA barriers late
+  // with all of them: MMA issue (warp 0, lane 0), Lambda1 readout and mu flush (warps 4..7,
+  // one per tensor-memory lane quarter), R_c (warp 8), the l_c sums (warp 9)
+  const bool issuer = tid == 0, rw = (w >> 2) == 1;
+  const int rc_t = tid - 8 * 32, ls_t = tid - 9 * 32;
 #pragma unroll
   for (int k = 0; k < 4; ++k) part[tid + TC_NT * k] = 0.0;  // mu: [a][yl]
 #pragma unroll
   for (int p = 0; p < 2; ++p)
 #pragma unroll
     for (int b = 0; b < D; ++b) part[128 * D + (size_t)(pr0 + 512 * p) * D + b] = 0.0;
-  // L split into its B operand (rows a, runs of 4 yl): L(yl, a) = tab[lo + 128 a + yl]
+  // [L_hi | L_lo]: rows a (L_lo two 8-row groups on), runs of 4 yl; L(yl, a) = tab[lo + 128 a + yl]
   for (int i = tid; i < 128 * D; i += TC_NT) {
     const int a = i >> 7, yl = i & 127;
     const float x = tab[d.lo + i], h = tf32_hi(x);
     const int o = (a >> 3) * 1024 + (yl >> 2) * 32 + (a & 7) * 4 + (yl & 3);
-    dyn[TC_LH + o] = h;
-    dyn[TC_LL + o] = x - h;
+    dyn[TC_LB + o] = h;
+    dyn[TC_LB + 2048 + o] = x - h;
   }
   unsigned long long Mr[2][8];  // M(ym)(a, b) for this thread's two pairs, packed over b
 #pragma unroll
@@ -1047,44 +1059,70 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
     }
   }
   if (w == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(tslot)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tslot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barL));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barM));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  auto stage = [&](long long c, int buf) {
+  // this thread's 4 x 4 block of a chunk: rows ym = 4 w + i, columns yl = 4 lane + j, at
+  // float offset blk(i) of a 64-row half of the Lambda1 operand
+  auto blk = [&](int i) { return ((4 * w + i) >> 3) * 1152 + lane * 36 + ((4 * w + i) & 7) * 4; };
+  // chunk c into hi buffer b (float offset 2 TC_HALF b) and (tid < 68) its M_h1 and r_h2 into
+  // sb[b]; each thread copies,
+  // and later reads, only its own block
+  auto stage = [&](long long c, int b) {
     if (tid < 68) {
       const float *src = (tid < DD / 4) ? tab + d.m1 + (c & mask1) * DD + 4 * tid
                                         : tab + d.r2 + (c >> d.h1) * D + 4 * (tid - DD / 4);
-      cp_async16(sb + buf * 272 + 4 * tid, src);
+      cp_async16(sb + b * 272 + 4 * tid, src);
     }
-    // this thread's 4 x 4 block of lambda: rows ym = 4 w + i, columns yl = 4 lane + j
-    // (each thread copies, and later reads, only its own block)
     const float *lc = lam + (c << MPS_CHUNK_BITS) + 4 * lane;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) cp_async16(sraw + (4 * w + i) * 128 + 4 * lane, lc + (4 * w + i) * 128);
+    for (int i = 0; i < 4; ++i) cp_async16(dyn + 2 * TC_HALF * b + blk(i), lc + (4 * w + i) * 128);
     cp_async_commit();
+  };
+  auto split = [&](int b, float (&h)[4][4], float (&l)[4][4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 v = *reinterpret_cast<const float4 *>(dyn + 2 * TC_HALF * b + blk(i));
+      const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        h[i][j] = tf32_hi(x[j]);
+        l[i][j] = x[j] - h[i][j];
+      }
+    }
   };
   stage(blockIdx.x, 0);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot, tL = tmem, tM = tmem + 32;
+  const uint32_t tmem = *tslot;
   const uint32_t tw = tmem + ((uint32_t)(32 * (w & 3)) << 16);  // this warp's lane quarter
   unsigned long long P2[2][8];
 #pragma unroll
   for (int p = 0; p < 2; ++p)
 #pragma unroll
     for (int j = 0; j < 8; ++j) P2[p][j] = 0ull;
-  bool ok = true, mu_acc = false;
-  int since = 0, par = 0;
-  uint32_t phase = 0;
-  long long cprev = -1;
 
-  // P and l_c of chunk cp from the Lambda1 rows in sQ and R_c in sr[rb]
-  auto update_prev = [&](long long cp, int rb) {
+  // Lambda1 rows of accumulator buffer b into sQ (warps 0..3, lanes = rows)
+  auto readout = [&](int b) {
+    if (rw) {
+      float v[16], u[16];
+      tc_ld16(tw + 32 * b, v);  // [lambda_hi; lambda_lo] L_hi, then ... L_lo
+      tc_ld16(tw + 32 * b + 16, u);
+      float4 *q4 = reinterpret_cast<float4 *>(sQ + (32 * (w & 3) + lane) * 20);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        q4[k] = make_float4(v[4 * k] + u[4 * k], v[4 * k + 1] + u[4 * k + 1], v[4 * k + 2] + u[4 * k + 2],
+                            v[4 * k + 3] + u[4 * k + 3]);
+    }
+  };
+  // P and the warp's l_c partial of the chunk whose Lambda1 rows are in sQ and R_c in sr[rb]
+  auto update = [&](int rb) {
     unsigned long long L2[2], lc2[8];
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
@@ -1132,66 +1170,109 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
       const int b = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
       sLc[w * 16 + b] = v[0];
     }
-    __syncthreads();
-    if (tid < D) {
+  };
+  auto lall_sum = [&](long long cp) {
+    if (ls_t >= 0 && ls_t < D) {
       float t = 0.f;
 #pragma unroll
-      for (int ww = 0; ww < TC_NT / 32; ++ww) t += sLc[ww * 16 + tid];
-      lall[cp * D + tid] = t;
+      for (int ww = 0; ww < TC_NT / 32; ++ww) t += sLc[ww * 16 + ls_t];
+      lall[cp * D + ls_t] = t;
     }
   };
   auto flush_mu = [&]() {
-    if (w < 4) {
+    if (rw) {
       float v[16], u[16];
-      tc_ld16(tw + 32, v);  // mu rows yl = 32 w + lane: lambda^T m_hi and lambda^T m_lo
-      tc_ld16(tw + 48, u);
+      tc_ld16(tw + 64, v);  // mu rows yl = 32 (w % 4) + lane: lambda^T m_hi and lambda^T m_lo
+      tc_ld16(tw + 80, u);
 #pragma unroll
-      for (int a = 0; a < D; ++a) part[a * 128 + 32 * w + lane] += (double)(v[a] + u[a]);
+      for (int a = 0; a < D; ++a) part[a * 128 + 32 * (w & 3) + lane] += (double)(v[a] + u[a]);
     }
   };
+  // P into the FP64 partials [pair][b]: each warp's 32 pairs x 16 values go through its own
+  // scratch rows (20 floats apart) in the mu copy's region, which is free at every flush
+  // point, so that consecutive lanes add into consecutive doubles
   auto flush_p = [&]() {
+    float *scr = sAT + w * 32 * 20;
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 2; ++p) {
+      float4 *row = reinterpret_cast<float4 *>(scr + lane * 20);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float2 v = upk(P2[p][j]);
-        double *dst = part + 128 * D + (size_t)(pr0 + 512 * p) * D + 2 * j;
-        dst[0] += (double)v.x;
-        dst[1] += (double)v.y;
-        P2[p][j] = 0ull;
+      for (int j = 0; j < 4; ++j) {
+        const float2 x = upk(P2[p][2 * j]), y = upk(P2[p][2 * j + 1]);
+        row[j] = make_float4(x.x, x.y, y.x, y.y);
+        P2[p][2 * j] = P2[p][2 * j + 1] = 0ull;
       }
+      __syncwarp();
+      double *dst = part + 128 * D + (size_t)(pr0 - lane + 512 * p) * D;
+#pragma unroll 4
+      for (int t = 0; t < 16; ++t) {
+        const int e = 32 * t + lane;  // pair e / 16 of the warp, value e % 16
+        dst[e] += (double)scr[(e >> 4) * 20 + (e & 15)];
+      }
+      __syncwarp();
+    }
   };
 
-  for (long long c = blockIdx.x; c < chunks; c += gridDim.x, par ^= 1) {
+  bool ok = true;
+  int since = 0, k = 0, nL = 0, nM = 0;
+  long long p = -1, pp = -1;  // the previous chunk; the chunk whose l_c partials sit in sLc
+  for (long long c = blockIdx.x; c < chunks; p = c, c += gridDim.x, ++k) {
+    const int b = k & 1;
     cp_async_wait<0>();
-    __syncthreads();  // S1: sb[par] staged, the previous Lambda1 rows in sQ
-    if (tid < D) {
+    __syncthreads();  // B1: sb[b] staged; sLc holds chunk pp's l_c partials
+    if (rc_t >= 0 && rc_t < D) {
       float acc = 0.f;
 #pragma unroll
-      for (int b = 0; b < D; ++b) acc = fmaf(sb[par * 272 + tid * D + b], sb[par * 272 + DD + b], acc);
-      sr[16 * par + tid] = acc;
+      for (int j = 0; j < D; ++j) acc = fmaf(sb[b * 272 + rc_t * D + j], sb[b * 272 + DD + j], acc);
+      sr[16 * b + rc_t] = acc;
     }
-    const bool more = c + gridDim.x < chunks;
+    if (pp >= 0) lall_sum(pp);
+    bool wok = true;
+    if (p >= 0) {
+      wok = mbar_wait_bounded(barL, (k - 1) & 1);  // Lambda1(p) done: lambda_lo free, its rows ready
+      tc_fence_after();
+      readout(b ^ 1);
+    }
     {
-      // split this chunk's block into both operand copies (the previous MMAs are complete)
       float h[4][4], l[4][4];
+      split(b, h, l);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float4 v = *reinterpret_cast<const float4 *>(sraw + (4 * w + i) * 128 + 4 * lane);
-        const float x[4] = {v.x, v.y, v.z, v.w};
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4 *>(dyn + TC_HALF + blk(i)) = make_float4(l[i][0], l[i][1], l[i][2], l[i][3]);
+    }
+    if (c + gridDim.x < chunks) stage(c + gridDim.x, b ^ 1);  // hi buffer b ^ 1: Lambda1(p) has read it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    if (!__syncthreads_and(wok ? 1 : 0)) {  // B2: Lambda1 operands of chunk c in place
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    if (issuer) {
+      // A: [hi 0; lo] or [lo; hi 1], 16 groups at SBO 4608, K steps of 288 bytes (two core
+      // matrices at LBO 144); B: [L_hi | L_lo], N = 32
+      const uint64_t a1 = tc_desc(smem_u32(dyn + TC_A1 + b * TC_HALF), 144, 4608);
+      const uint64_t lb = tc_desc(smem_u32(dyn + TC_LB), 128, 4096);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          h[i][j] = tf32_hi(x[j]);
-          l[i][j] = x[j] - h[i][j];
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int row = 4 * w + i;
-        const int o = (row >> 3) * 1152 + lane * 36 + (row & 7) * 4;
-        *reinterpret_cast<float4 *>(sA1 + o) = make_float4(h[i][0], h[i][1], h[i][2], h[i][3]);
-        *reinterpret_cast<float4 *>(sA1 + 8 * 1152 + o) = make_float4(l[i][0], l[i][1], l[i][2], l[i][3]);
-      }
+      for (int s = 0; s < 16; ++s) tc_mma(tmem + 32 * b, a1 + 18 * s, lb + 16 * s, s > 0);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(barL)
+                   : "memory");
+    }
+    ++nL;
+    wok = true;
+    if (p >= 0) {
+      wok = mbar_wait_bounded(barM, (k - 1) & 1);  // mu(p) done: the mu copy and m free
+      tc_fence_after();
+    }
+    if (since == TC_FLUSH) {
+      flush_mu();
+      flush_p();
+      since = 0;
+      __syncthreads();  // every warp's scratch read before the mu copy is written
+    }
+    {
+      float h[4][4], l[4][4];
+      split(b, h, l);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int yl = 4 * lane + j;
@@ -1199,93 +1280,82 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
         *reinterpret_cast<float4 *>(sAT + o) = make_float4(h[0][j], h[1][j], h[2][j], h[3][j]);
         *reinterpret_cast<float4 *>(sAT + 8256 + o) = make_float4(l[0][j], l[1][j], l[2][j], l[3][j]);
       }
-    }
-    if (more) stage(c + gridDim.x, par ^ 1);  // sb[par ^ 1] was read a chunk ago; this thread's block is split
-    __syncthreads();  // S2: R_c in sr[par]
-    {
-      // m(ym)(a) = M(ym)(a, :) R_c for this thread's pairs, split into the B operand of mu
-      const ulonglong2 *r2 = reinterpret_cast<const ulonglong2 *>(sr + 16 * par);
+      // m(ym)(a) = M(ym)(a, :) R_c for this thread's pairs, split into [m_hi | m_lo]
+      const ulonglong2 *r2 = reinterpret_cast<const ulonglong2 *>(sr + 16 * b);
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
+      for (int q = 0; q < 2; ++q) {
         unsigned long long acc = 0ull;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const ulonglong2 t = r2[j];
-          acc = fma2(Mr[p][2 * j], t.x, acc);
-          acc = fma2(Mr[p][2 * j + 1], t.y, acc);
+          acc = fma2(Mr[q][2 * j], t.x, acc);
+          acc = fma2(Mr[q][2 * j + 1], t.y, acc);
         }
         const float2 s2 = upk(acc);
         const float m = s2.x + s2.y, hm = tf32_hi(m);
-        const int pr = pr0 + 512 * p, ym = pr >> 4, a = pr & 15;
+        const int pr = pr0 + 512 * q, ym = pr >> 4, a = pr & 15;
         const int o = (a >> 3) * 512 + (ym >> 2) * 32 + (a & 7) * 4 + (ym & 3);
-        dyn[TC_MH + o] = hm;
-        dyn[TC_ML + o] = m - hm;
+        dyn[TC_MB + o] = hm;
+        dyn[TC_MB + 1024 + o] = m - hm;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
-    __syncthreads();  // S3: operands in shared memory
-    tc_fence_after();
-    if (tid == 0) {
-      // B operands [L_hi | L_lo] and [m_hi | m_lo]: N = 32 rows, the lo rows two 8-row groups on
-      const uint64_t a1 = tc_desc(smem_u32(sA1), 144, 4608);
-      const uint64_t lb = tc_desc(smem_u32(dyn + TC_LH), 128, 4096);
-      const uint64_t th = tc_desc(smem_u32(sAT), 128, 2064), tl = tc_desc(smem_u32(sAT + 8256), 128, 2064);
-      const uint64_t mb = tc_desc(smem_u32(dyn + TC_MH), 128, 2048);
-      // K steps of 8: 288 bytes (two core matrices at LBO 144) along yl, 256 bytes along ym
-#pragma unroll 1
-      for (int s = 0; s < 16; ++s) tc_mma(tL, a1 + 18 * s, lb + 16 * s, s > 0);
-#pragma unroll 1
-      for (int s = 0; s < 8; ++s) {
-        tc_mma(tM, th + 16 * s, mb + 16 * s, (s > 0 || mu_acc) ? 1 : 0);
-        tc_mma(tM, tl + 16 * s, mb + 16 * s, 1);
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                   : "memory");
-    }
-    mu_acc = true;
-    if (cprev >= 0) update_prev(cprev, par ^ 1);  // overlaps this chunk's MMAs; ends with a barrier
-    if (!__syncthreads_and(mbar_wait_bounded(bar, phase) ? 1 : 0)) {
+    if (!__syncthreads_and(wok ? 1 : 0)) {  // B3: mu operands of chunk c in place, R_c in sr[b]
       ok = false;
       break;
     }
-    phase ^= 1;
     tc_fence_after();
-    if (w < 4) {
-      float v[16], u[16];
-      tc_ld16(tw, v);  // row 32 w + lane of [lambda_hi; lambda_lo] L_hi, then of ... L_lo
-      tc_ld16(tw + 16, u);
-      float4 *q4 = reinterpret_cast<float4 *>(sQ + (32 * w + lane) * 20);
+    if (issuer) {
+      const uint64_t th = tc_desc(smem_u32(sAT), 128, 2064), tl = tc_desc(smem_u32(sAT + 8256), 128, 2064);
+      const uint64_t mb = tc_desc(smem_u32(dyn + TC_MB), 128, 2048);
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        q4[k] = make_float4(v[4 * k] + u[4 * k], v[4 * k + 1] + u[4 * k + 1], v[4 * k + 2] + u[4 * k + 2],
-                            v[4 * k + 3] + u[4 * k + 3]);
+      for (int s = 0; s < 8; ++s) {
+        tc_mma(tmem + 64, th + 16 * s, mb + 16 * s, (s > 0 || since > 0) ? 1 : 0);
+        tc_mma(tmem + 64, tl + 16 * s, mb + 16 * s, 1);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(barM)
+                   : "memory");
     }
-    if (++since == TC_FLUSH) {
+    ++nM;
+    ++since;
+    if (p >= 0) update(b ^ 1);  // P and l_c of chunk p, while the tensor cores work on chunk c
+    pp = p;
+  }
+  if (ok && k > 0) {
+    // the last chunk p: its Lambda1 rows, then P, l_c; then mu and P into the partials
+    const int bl = (k - 1) & 1;
+    __syncthreads();  // the last update's reads of sQ are done before its rows are replaced
+    bool wok = mbar_wait_bounded(barL, (k - 1) & 1);
+    tc_fence_after();
+    readout(bl);
+    wok = mbar_wait_bounded(barM, (k - 1) & 1) && wok;
+    tc_fence_after();
+    ok = __syncthreads_and(wok ? 1 : 0) != 0;
+    if (ok) {
+      if (pp >= 0) lall_sum(pp);
+      __syncthreads();
+      update(bl);
+      __syncthreads();
+      lall_sum(p);
       flush_mu();
       flush_p();
-      since = 0;
-      mu_acc = false;
     }
-    tc_fence_before();
-    cprev = c;
-  }
-  if (ok) {
-    __syncthreads();
-    if (cprev >= 0) update_prev(cprev, par ^ 1);
-    if (since > 0) flush_mu();
-    flush_p();
   }
   cp_async_wait<0>();
   if (!ok) {
-    // a wait ran out: poison this CTA's partials, give the MMAs another bounded wait
+    // a wait ran out: poison this CTA's partials; tensor memory is freed only once both
+    // mbarriers report their last commit complete
     for (int i = tid; i < gr.v1; i += TC_NT) part[i] = __longlong_as_double(0x7ff8000000000000LL);
-    ok = __syncthreads_and(mbar_wait_bounded(bar, phase) ? 1 : 0) != 0;
+    bool done = true;
+    if (nL > 0) done = mbar_wait_bounded(barL, (nL - 1) & 1) && done;
+    if (nM > 0) done = mbar_wait_bounded(barM, (nM - 1) & 1) && done;
+    ok = __syncthreads_and(done ? 1 : 0) != 0;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (w == 0 && ok) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+  if (w == 0 && ok) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
 // High qubits: block (x, q - 13) takes chunks 256 x .. 256 x + 255 and qubit q.
