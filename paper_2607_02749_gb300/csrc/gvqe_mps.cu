@@ -933,8 +933,11 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
 // The rest stays on the FP32 pipe: R_c, m = M R_c and, for the previous chunk
 // while the tensor cores work on this one, P += Lambda1 (x) R_c and
 // l_c = sum Lambda1 M (each thread keeps its two rows of the mid matrices in
-// registers for the whole pass).  mu stays in tensor memory for FLUSH chunks,
-// then both mu and P are added into the FP64 partials.
+// registers for the whole pass).  Each chunk's mu starts afresh in tensor memory
+// and is added, in FP32 with round-to-nearest, into a shared-memory sum (the
+// tensor cores' own accumulation over many chunks drifted: 9e-6 relative after
+// 32 chunks against 2e-7 on the FP32 pipe); every FLUSH chunks that sum and P
+// are added into the FP64 partials.
 //
 // Pipeline.  lambda is copied (cp.async) straight into the Lambda1 operand
 // layout: those FP32 values are lambda_hi as the tensor cores read them (the
@@ -952,7 +955,7 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
 // partials, so the job's gradients come out NaN, and frees tensor memory only
 // once both mbarriers report their last commit complete.
 constexpr int TC_NT = 512;
-constexpr int TC_FLUSH = 16;
+constexpr int TC_FLUSH = 32;
 // float offsets of the shared-memory regions
 constexpr int TC_HALF = 8 * 1152;         // 64 rows of the Lambda1 operand: 8 groups x 4608 bytes
 constexpr int TC_A1 = 0;                  // lambda for Lambda1: [hi 0 | lo | hi 1]
@@ -963,7 +966,8 @@ constexpr int TC_Q = TC_MB + 2048;        // Lambda1 rows from tensor memory: 12
 constexpr int TC_SB = TC_Q + 128 * 20;    // staged M_h1 and r_h2: [2][272]
 constexpr int TC_SR = TC_SB + 2 * 272;    // R_c: [2][16]
 constexpr int TC_LC = TC_SR + 32;         // l_c per warp: [16][16]
-constexpr int TC_BAR = TC_LC + 256;       // mbarriers barL, barM (8 bytes each), the tensor-memory address
+constexpr int TC_MU = TC_LC + 256;        // mu summed over chunks in FP32: [128 yl][20]
+constexpr int TC_BAR = TC_MU + 128 * 20;  // mbarriers barL, barM (8 bytes each), the tensor-memory address
 constexpr size_t TC_SMEM = (size_t)(TC_BAR + 8) * sizeof(float);
 static_assert(TC_SMEM <= 232448, "the bond-16 tensor-core pass needs at most 227 KB of shared memory");
 
@@ -1015,6 +1019,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
   constexpr int D = 16, DD = 256;
   extern __shared__ __align__(16) float dyn[];
   float *sAT = dyn + TC_AT, *sQ = dyn + TC_Q, *sb = dyn + TC_SB, *sr = dyn + TC_SR, *sLc = dyn + TC_LC;
+  float *sMu = dyn + TC_MU;
   const uint32_t barL = smem_u32(dyn + TC_BAR), barM = barL + 8;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(dyn + TC_BAR + 4);
   const MpsDims d = mps_dims(A.n, 4);
@@ -1035,6 +1040,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
   const int rc_t = tid - 8 * 32, ls_t = tid - 9 * 32;
 #pragma unroll
   for (int k = 0; k < 4; ++k) part[tid + TC_NT * k] = 0.0;  // mu: [a][yl]
+  for (int i = tid; i < 128 * 20; i += TC_NT) sMu[i] = 0.f;
 #pragma unroll
   for (int p = 0; p < 2; ++p)
 #pragma unroll
@@ -1179,13 +1185,30 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
       lall[cp * D + ls_t] = t;
     }
   };
-  auto flush_mu = [&]() {
+  // the finished mu of one chunk into the FP32 sum (warps 4..7, row yl = 32 (w % 4) + lane each)
+  auto add_mu = [&]() {
     if (rw) {
       float v[16], u[16];
-      tc_ld16(tw + 64, v);  // mu rows yl = 32 (w % 4) + lane: lambda^T m_hi and lambda^T m_lo
+      tc_ld16(tw + 64, v);  // lambda^T m_hi and lambda^T m_lo
       tc_ld16(tw + 80, u);
+      float4 *row = reinterpret_cast<float4 *>(sMu + (32 * (w & 3) + lane) * 20);
 #pragma unroll
-      for (int a = 0; a < D; ++a) part[a * 128 + 32 * (w & 3) + lane] += (double)(v[a] + u[a]);
+      for (int j = 0; j < 4; ++j) {
+        const float4 o = row[j];
+        row[j] = make_float4(o.x + (v[4 * j] + u[4 * j]), o.y + (v[4 * j + 1] + u[4 * j + 1]),
+                             o.z + (v[4 * j + 2] + u[4 * j + 2]), o.w + (v[4 * j + 3] + u[4 * j + 3]));
+      }
+    }
+  };
+  auto flush_mu = [&]() {
+    if (rw) {
+      const int yl = 32 * (w & 3) + lane;
+      float *row = sMu + yl * 20;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        part[a * 128 + yl] += (double)row[a];
+        row[a] = 0.f;
+      }
     }
   };
   // P into the FP64 partials [pair][b]: each warp's 32 pairs x 16 values go through its own
@@ -1263,6 +1286,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
     if (p >= 0) {
       wok = mbar_wait_bounded(barM, (k - 1) & 1);  // mu(p) done: the mu copy and m free
       tc_fence_after();
+      add_mu();
     }
     if (since == TC_FLUSH) {
       flush_mu();
@@ -1311,7 +1335,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
       const uint64_t mb = tc_desc(smem_u32(dyn + TC_MB), 128, 2048);
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
-        tc_mma(tmem + 64, th + 16 * s, mb + 16 * s, (s > 0 || since > 0) ? 1 : 0);
+        tc_mma(tmem + 64, th + 16 * s, mb + 16 * s, s > 0);
         tc_mma(tmem + 64, tl + 16 * s, mb + 16 * s, 1);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(barM)
@@ -1331,6 +1355,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
     readout(bl);
     wok = mbar_wait_bounded(barM, (k - 1) & 1) && wok;
     tc_fence_after();
+    add_mu();
     ok = __syncthreads_and(wok ? 1 : 0) != 0;
     if (ok) {
       if (pp >= 0) lall_sum(pp);

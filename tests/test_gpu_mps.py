@@ -183,10 +183,10 @@ def _run_opts(n, reps, ham, th, ent, mps, tensor):
 
 # bond dimension 16 (four closed-form layers): the tensor-core gradient pass
 # (TF32 split operands) against the FP32-pipe pass and against plans with every
-# layer as tile passes; n = 25 gives 4096 chunks, 27 per CTA (the FP64 flush of
-# the tensor-memory accumulators inside the loop), batch 3 three CTA waves
+# layer as tile passes; n = 26 gives 8192 chunks, 54 per CTA (the FP64 flush of
+# the accumulators every 32 chunks inside the loop), batch 3 three CTA waves
 @pytest.mark.parametrize("n,reps,batch,ent", [(17, 5, 2, gv.GVQE_ENT_LINEAR), (21, 6, 3, gv.GVQE_ENT_FULL),
-                                              (25, 5, 3, gv.GVQE_ENT_LINEAR),
+                                              (25, 5, 3, gv.GVQE_ENT_LINEAR), (26, 5, 2, gv.GVQE_ENT_LINEAR),
                                               (23, 5, 1, gv.GVQE_ENT_REVERSE_LINEAR)])
 def test_tensor_core_gradient_pass(n, reps, batch, ent):
     ham = wl.z_hamiltonian(n, 4 * n, seed=n)
@@ -210,5 +210,8 @@ def test_tensor_core_gradient_pass(n, reps, batch, ent):
         print(f"n={n} reps={reps} b={b}: tensor vs FP32 pipe {r_f:.2e}, tensor vs tile passes {r_t:.2e} "
               f"(layers 0..4 {r_lo:.2e}), FP32 pipe vs tile passes {r_ft:.2e}")
         assert r_t <= FP32_G and r_f <= FP32_G and r_lo <= FP32_G
+        # tighter: the split TF32 products keep the FP32 level (measured 4e-7 to 7e-7 at
+        # n = 17..26); a drift of the sums over chunks would show here first
+        assert r_t <= 1e-5 and r_f <= 1e-5
     if n <= 17:
         _check_oracle(e_tc, g_tc, n, reps, th, ham, ent, "tensor-core pass")
