@@ -87,11 +87,12 @@ extern "C" {
                                  from contracted tables of those matrices (a write-only pass per state)
                                  instead of running their tile passes.  Same results up to FP32 rounding;
                                  the last layer always runs as tile passes. */
-#define GVQE_OPT_MPS_TENSOR 6 /* gradient pass of the closed-form layers at bond dimension 16 (four closed-form
-                                 layers): 0 = auto (its two lambda contractions per 2^13-amplitude chunk,
-                                 64 x 128 x 16 and 128 x 64 x 16, on the tensor cores as tcgen05 TF32 MMAs with
-                                 every operand split into two TF32 parts, FP32 accumulators), -1 = on the FP32
-                                 pipe.  Same results up to FP32 rounding. */
+#define GVQE_OPT_MPS_TENSOR 6 /* closed-form layers at bond dimension 16 (four closed-form layers): 0 = auto
+                                 (the writer's product per 2^13-amplitude chunk, 128 x 16 x 64, and the
+                                 gradient pass's two lambda contractions, 64 x 128 x 16 and 128 x 64 x 16, on
+                                 the tensor cores as tcgen05 TF32 MMAs with every operand split into two TF32
+                                 parts, FP32 accumulators), -1 = both on the FP32 pipe.  Same results up to
+                                 FP32 rounding. */
 
 /* gate sets of a rotation layer (Eq. 8).
  * RY:    RY on every qubit; P = n (reps+1), theta[r*n + q]; real amplitudes.

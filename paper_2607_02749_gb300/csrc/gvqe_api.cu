@@ -682,7 +682,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
   // whose table region then also keeps the site matrices for the gradients)
   pl.mps_layers = R;
   pl.mps_grad = mgrad;
-  pl.mps_tc = mgrad && R == MPS_MAX_LAYERS && mps_tc;
+  pl.mps_tc = R == MPS_MAX_LAYERS && mps_tc;
   for (int r = 1; r <= R; ++r) {
     uint32_t rot = 0;
     for (int j = 0; j < p; ++j) {
@@ -702,7 +702,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
       pl.steps.push_back(tab);
       PassStep st = tab;
       st.A.kind = K_MPS;
-      st.A.flags = 0;
+      st.A.flags = (r == MPS_MAX_LAYERS && mps_tc) ? F_MPS_TC : 0;
       st.A.tiles = 1LL << (n - MPS_CHUNK_BITS);
       st.A.store_mode = ST_PLAIN;
       st.out = want_grad ? state_id(r, j) : PP0;
@@ -902,7 +902,7 @@ std::string describe_plan(const Plan &pl) {
   if (pl.mps_layers > 0) {
     snprintf(buf, sizeof(buf), "  closed-form layers 1..%d (bond dimension up to %d), %lld table floats per job%s\n",
              pl.mps_layers, 1 << pl.mps_layers, pl.mps_elems,
-             !pl.mps_grad ? ""
+             !pl.mps_grad ? (pl.mps_tc ? " (tensor cores, TF32 split)" : "")
              : pl.mps_tc  ? "; their gradients from lambda and the matrix product (tensor cores, TF32 split)"
                           : "; their gradients from lambda and the matrix product");
     s += buf;

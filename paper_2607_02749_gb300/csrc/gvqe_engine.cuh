@@ -164,7 +164,7 @@ enum PassFlags : int {
   F_ACCUM = 16,        // K_LAMBDA_XY: add onto lambda already written (group chunks)
   F_COMPLEX = 64,      // the complex path (full EfficientSU2 layers: RY then RZ)
   F_MPS_SITES = 128,   // K_MPS_TAB: also write the site matrices and their derivatives
-  F_MPS_TC = 256,      // K_MPS_GRAD at bond 16: the lambda contractions on the tensor cores
+  F_MPS_TC = 256,      // K_MPS / K_MPS_GRAD at bond 16: the chunk contractions on the tensor cores
 };
 
 struct PassArgs {

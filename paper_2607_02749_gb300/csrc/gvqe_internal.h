@@ -62,7 +62,7 @@ struct Plan {
   int final_buf = -1;         // state-only plans: buffer of the final state
   int mps_layers = 0;         // leading layers written in closed form (K_MPS steps)
   bool mps_grad = false;      // ... and their gradients from lambda and the matrix product
-  bool mps_tc = false;        // ... with the bond-16 lambda contractions on the tensor cores
+  bool mps_tc = false;        // ... with the bond-16 chunk contractions on the tensor cores
   long long mps_elems = 0;    // floats of closed-form tables per job (one stage at a time)
   DevBuf d_dir;
   int d_dir_count = 0;
@@ -80,7 +80,7 @@ void count_launches(int k);
 // xy_tb: tile bits of the X-mask pass (0: those of the layer's first pass).
 // mps_layers: the leading layers after layer 0 whose states K_MPS steps write
 // in closed form (0: none; see mps_layers_for).  mps_tc: at bond dimension 16
-// the gradient pass over lambda contracts on the tensor cores (F_MPS_TC).
+// the writer and the gradient pass over lambda contract on the tensor cores (F_MPS_TC).
 Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool diag, bool tile_grad_l0 = false,
                 bool state_only = false, int ent = ENT_LINEAR, int gates = 1, int split = SPLIT_AUTO, int xy_tb = 0,
                 int mps_layers = 0, bool mps_tc = true);

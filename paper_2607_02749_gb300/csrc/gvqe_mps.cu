@@ -1383,6 +1383,167 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mps_grad16tc(const PassArgs A) {
   if (w == 0 && ok) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
+// ----------------------------------------------- bond-16 writer, tensor cores --
+// Per 2^13-amplitude chunk the writer's product psi(ym, yl) = sum_a L(yl, a) m(ym, a)
+// (L: 128 x 16, m = M_mid R_c: 64 x 16) is one GEMM, 128 x 64 with K = 16.  It runs
+// as tcgen05.mma kind::tf32 (M = 128 rows yl, N = 64 columns ym) with the operands
+// split into TF32 parts along K: A = [L_hi | L_lo | L_hi], B = [m_hi | m_hi | m_lo]
+// (K = 48, six MMAs), which sums L_hi m_hi + L_lo m_hi + L_hi m_lo.  The
+// accumulator is double: chunk c - 1 is read out of tensor memory and stored
+// (lanes = consecutive yl, 128-byte rows) while chunk c's MMAs run.  m stays on the
+// FP32 pipe (thread: one ym, four consecutive a, from the transposed mid matrices in
+// shared memory; a 16-byte store per K group of B).  Operand layouts as in the
+// gradient pass: K-major, no swizzle, LBO 128 bytes along K, SBO 1536 bytes per
+// 8-row group.  The mbarrier waits are bounded; one that runs out stores NaN for
+// that chunk, and tensor memory is freed only once the last commits are complete.
+constexpr int WT_NT = 512;
+constexpr int WT_MLD = 276;                 // floats per ym of the transposed mid matrices (16-byte rows, distinct banks)
+constexpr int WT_M = 0;                     // [64 ym][b][a], WT_MLD per ym
+constexpr int WT_A = WT_M + 64 * WT_MLD;    // A = [L_hi | L_lo | L_hi]: 16 groups x 1536 bytes
+constexpr int WT_B = WT_A + 16 * 384;       // B = [m_hi | m_hi | m_lo], two buffers of 8 groups x 1536 bytes
+constexpr int WT_SB = WT_B + 2 * 8 * 384;   // staged M_h1 and r_h2: [2][272]
+constexpr int WT_SR = WT_SB + 2 * 272;      // R_c
+constexpr int WT_BAR = WT_SR + 16;          // two mbarriers (8 bytes each), tensor-memory address
+constexpr size_t WT_SMEM = (size_t)(WT_BAR + 6) * sizeof(float);
+// instruction descriptor: FP32 accumulator, TF32 A and B, K-major, M = 128, N = 64
+constexpr uint32_t WT_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__global__ void __launch_bounds__(WT_NT, 1) k_mps_write16tc(const PassArgs A) {
+  constexpr int D = 16, DD = 256;
+  extern __shared__ __align__(16) float dyn[];
+  float *sM = dyn + WT_M, *sb = dyn + WT_SB, *sr = dyn + WT_SR;
+  // one mbarrier per accumulator buffer: chunk k commits to bar(k % 2) as its (k / 2)-th
+  // phase, and every thread waits on it before the next commit to the same barrier (a
+  // single barrier could complete two phases before a thread polls it)
+  const uint32_t bar0 = smem_u32(dyn + WT_BAR);
+  auto bar = [&](int b) { return bar0 + 8 * b; };
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(dyn + WT_BAR + 4);
+  const MpsDims d = mps_dims(A.n, 4);
+  const int job = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const float *tab = reinterpret_cast<const float *>(A.in) + (size_t)job * A.in_stride;
+  float *out = reinterpret_cast<float *>(A.out) + (size_t)job * A.out_stride;
+  const long long chunks = A.tiles;
+  const long long mask1 = (1LL << d.h1) - 1;
+  const int rc_t = tid - 15 * 32;  // warp 15 lanes 0..15 form R_c
+  for (int i = tid; i < 64 * DD; i += WT_NT) {
+    const int ym = i / DD, a = (i / D) % D, b = i % D;  // tab: M(ym)(a, b) at (ym D + a) D + b
+    sM[ym * WT_MLD + b * D + a] = tab[d.mid + i];
+  }
+  for (int i = tid; i < 128 * 48; i += WT_NT) {
+    const int yl = i / 48, k = i % 48, a = k & 15;
+    const float x = tab[d.lo + a * 128 + yl], h = tf32_hi(x);
+    dyn[WT_A + (yl >> 3) * 384 + (k >> 2) * 32 + (yl & 7) * 4 + (k & 3)] = (k >> 4) == 1 ? x - h : h;
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(0)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(1)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  auto stage = [&](long long c, int b) {
+    if (tid < 68) {
+      const float *src = (tid < DD / 4) ? tab + d.m1 + (c & mask1) * DD + 4 * tid
+                                        : tab + d.r2 + (c >> d.h1) * D + 4 * (tid - DD / 4);
+      cp_async16(sb + b * 272 + 4 * tid, src);
+    }
+    cp_async_commit();
+  };
+  stage(blockIdx.x, 0);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  // readout: warp w takes tensor-memory lanes 32 (w % 4) .. + 31 (rows yl) and the
+  // 16 columns 16 (w / 4) .. + 15 (ym) of an accumulator
+  const int sp = w & 3, cb = w >> 2;
+  const uint32_t tw = tmem + ((uint32_t)(32 * sp) << 16) + 16 * cb;
+  auto store = [&](long long cp, int b, bool good) {
+    float v[16];
+    tc_ld16(tw + 64 * b, v);
+    float *o = out + (cp << MPS_CHUNK_BITS) + (16 * cb) * 128 + 32 * sp + lane;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) o[j * 128] = good ? v[j] : __int_as_float(0x7fc00000);
+  };
+  bool ok = true;
+  int k = 0, nc = 0;
+  long long p = -1;
+  for (long long c = blockIdx.x; c < chunks; p = c, c += gridDim.x, ++k) {
+    const int b = k & 1;
+    cp_async_wait<0>();
+    __syncthreads();  // sb[b] staged
+    if (rc_t >= 0 && rc_t < D) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < D; ++j) acc = fmaf(sb[b * 272 + rc_t * D + j], sb[b * 272 + DD + j], acc);
+      sr[rc_t] = acc;
+    }
+    if (c + gridDim.x < chunks) stage(c + gridDim.x, b ^ 1);
+    __syncthreads();  // R_c in sr
+    if (tid < 256) {
+      // m(ym)(a) for a = 4 ag .. 4 ag + 3, split into B buffer b (the MMAs that read it,
+      // two chunks ago, are complete)
+      const int ym = tid & 63, ag = tid >> 6;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const float4 mv = *reinterpret_cast<const float4 *>(sM + ym * WT_MLD + j * D + 4 * ag);
+        const float rj = sr[j];
+        acc.x = fmaf(mv.x, rj, acc.x);
+        acc.y = fmaf(mv.y, rj, acc.y);
+        acc.z = fmaf(mv.z, rj, acc.z);
+        acc.w = fmaf(mv.w, rj, acc.w);
+      }
+      const float4 h = make_float4(tf32_hi(acc.x), tf32_hi(acc.y), tf32_hi(acc.z), tf32_hi(acc.w));
+      const float4 l = make_float4(acc.x - h.x, acc.y - h.y, acc.z - h.z, acc.w - h.w);
+      float *bb = dyn + WT_B + b * 3072 + (ym >> 3) * 384 + (ym & 7) * 4;
+      *reinterpret_cast<float4 *>(bb + ag * 32) = h;
+      *reinterpret_cast<float4 *>(bb + (4 + ag) * 32) = h;
+      *reinterpret_cast<float4 *>(bb + (8 + ag) * 32) = l;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    if (!__syncthreads_and(ok ? 1 : 0)) break;  // B operand of chunk c in place
+    tc_fence_after();
+    if (tid == 0) {
+      const uint64_t da = tc_desc(smem_u32(dyn + WT_A), 128, 1536);
+      const uint64_t db = tc_desc(smem_u32(dyn + WT_B + b * 3072), 128, 1536);
+#pragma unroll
+      for (int s = 0; s < 6; ++s)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + 64 * b),
+            "l"(da + 16 * s), "l"(db + 16 * s), "r"(WT_IDESC), "r"(s > 0 ? 1 : 0));
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar(b))
+                   : "memory");
+    }
+    ++nc;
+    if (p >= 0) {
+      ok = mbar_wait_bounded(bar(b ^ 1), ((k - 1) >> 1) & 1);  // chunk p's MMAs done
+      tc_fence_after();
+      store(p, b ^ 1, ok);
+    }
+    tc_fence_before();
+  }
+  if (__syncthreads_and(ok ? 1 : 0) && p >= 0) {
+    const bool good = mbar_wait_bounded(bar((k - 1) & 1), ((k - 1) >> 1) & 1);  // the last chunk
+    tc_fence_after();
+    store(p, (k - 1) & 1, good);
+  }
+  cp_async_wait<0>();
+  // tensor memory is freed once the last commit is complete
+  tc_fence_before();
+  const int n0 = (nc + 1) / 2, n1 = nc / 2;  // commits to bar(0), bar(1)
+  const bool done = __syncthreads_and(((n0 == 0 || mbar_wait_bounded(bar(0), (n0 - 1) & 1)) &&
+                                       (n1 == 0 || mbar_wait_bounded(bar(1), (n1 - 1) & 1)))
+                                          ? 1
+                                          : 0) != 0;
+  tc_fence_after();
+  if (w == 0 && done) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
 // High qubits: block (x, q - 13) takes chunks 256 x .. 256 x + 255 and qubit q.
 // Thread c forms u = l_c A_13 .. A_{q-1} and s = A_{q+1} .. A_{n-1} 1 and adds
 // u dA_q^k s for every layer k <= r; the block's FP64 sums go to its partials.
@@ -1639,6 +1800,14 @@ cudaError_t launch_mps_d(const PassArgs &A, int jobs, cudaStream_t s) {
       k_mps_tab<D, EF_DIFF><<<grid, TAB_NT, smem, s>>>(A);
     }
     return cudaGetLastError();
+  }
+  if constexpr (D >= 16) {
+    if (A.flags & F_MPS_TC) {
+      const long long ctas = num_sms_cached();
+      cudaFuncSetAttribute(k_mps_write16tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WT_SMEM);
+      k_mps_write16tc<<<dim3((unsigned)(A.tiles < ctas ? A.tiles : ctas), (unsigned)jobs), WT_NT, WT_SMEM, s>>>(A);
+      return cudaGetLastError();
+    }
   }
   const long long cap = (long long)num_sms_cached() * (D >= 16 ? 2 : 4);
   const dim3 grid((unsigned)(A.tiles < cap ? A.tiles : cap), (unsigned)jobs);
