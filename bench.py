@@ -784,7 +784,7 @@ def run_gvqe(args):
     # whole state) give the per-pass figure beside it.
     prof = {k: _lib.gvqe_profile_read(k) for k in range(11)}
     names = {0: "k_fwd", 1: "k_bwd", 2: "k_grad_l0", 3: "k_lambda_xy", 4: "k_wht", 5: "k_mps_write",
-             6: "k_mps_tab", 7: "k_mps_grad", 8: "k_mps_ghigh", 9: "k_mps_gred", 10: "k_mps_genv"}
+             6: "k_mps_tab", 7: "k_mps_grad", 8: "k_mps_gtree", 9: "k_mps_gred", 10: "k_mps_genv"}
     dom = max(prof, key=lambda k: prof[k]["ms"])
     pk = prof[dom]
     peak, peak_src = measured_peaks()
@@ -838,7 +838,7 @@ def run_gvqe(args):
     cfg_ms = sum(prof[k]["ms"] for k in (7, 8, 9, 10))
     if R_cf and cfg_ms > 0:
         roofline["per_kind"]["closed_form_gradients"] = {
-            "kinds": "k_mps_grad + k_mps_ghigh + k_mps_gred + k_mps_genv", "ms": cfg_ms, "layers": R_cf,
+            "kinds": "k_mps_grad + k_mps_gtree + k_mps_gred + k_mps_genv", "ms": cfg_ms, "layers": R_cf,
             "GBps_algorithmic": (4 * R_cf + 2) * S_b * evals / (cfg_ms / 1000.0) / 1e9,
             "rule": "stand-in for the backward of layers R..1 and layer 0: (4R + 2) S of the algorithmic count"}
     _lib.gvqe_profile_reset()

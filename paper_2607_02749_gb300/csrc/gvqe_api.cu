@@ -143,6 +143,7 @@ static std::atomic<long long> g_launches{0};
 struct ProfRec {
   cudaEvent_t a, b;
   int kind;
+  int kernels;  // kernels the step launched
   double bytes;
 };
 static std::mutex g_prof_mu;
@@ -201,10 +202,12 @@ cudaError_t launch_step(int prec, const PassArgs &A, int jobs, int nterm, cudaSt
     cudaEventRecord(rec.a, s);
   }
   const cudaError_t e = launch_pass(prec, A, jobs, nterm, s);
-  ++g_launches;
+  const int nk = A.kind >= K_MPS ? mps_step_kernels(A) : 1;
+  g_launches += nk;
   if (prof) {
     cudaEventRecord(rec.b, s);
     rec.kind = A.kind;
+    rec.kernels = nk;
     rec.bytes = pass_bytes(prec, A, jobs);
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_pending.push_back(rec);
@@ -218,7 +221,7 @@ static void prof_drain() {
     float ms = 0.f;
     cudaEventSynchronize(r.b);
     if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess && r.kind >= 0 && r.kind < PROF_KINDS) {
-      g_prof_n[r.kind] += 1;
+      g_prof_n[r.kind] += r.kernels;
       g_prof_ms[r.kind] += ms;
       g_prof_bytes[r.kind] += r.bytes;
     }

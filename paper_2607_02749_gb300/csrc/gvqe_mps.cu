@@ -1544,98 +1544,158 @@ __global__ void __launch_bounds__(WT_NT, 1) k_mps_write16tc(const PassArgs A) {
   if (w == 0 && done) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
-// High qubits: block (x, q - 13) takes chunks 256 x .. 256 x + 255 and qubit q.
-// Thread c forms u = l_c A_13 .. A_{q-1} and s = A_{q+1} .. A_{n-1} 1 and adds
-// u dA_q^k s for every layer k <= r; the block's FP64 sums go to its partials.
+// High qubits by a tree over the chunk index bits (level t <-> qubit 13 + t,
+// K = n - 13 levels).  With E_t(j) the left environment of the chunks c with
+// c >> t == j (l_c A_13 .. A_{12+t}, summed over the low t bits) and R_t(j')
+// the right environment A_{14+t} .. A_{n-1} 1 of the bits above t
+// (j' = c >> (t + 1)),
+//
+//   g(k, 13 + t) = sum_j E_t(j) dA^k_{13+t}[j & 1] R_t(j >> 1),
+//   E_{t+1}(j)   = E_t(2j) A_{13+t}[0] + E_t(2j + 1) A_{13+t}[1],
+//
+// which is the per-chunk, per-qubit product of k_mps_ghigh regrouped: D^2 work
+// per vector and level instead of D^2 per chunk, qubit and qubit in between.
+// Stage 1 (block = 2^B consecutive chunks, B = min(8, K)) runs levels 0..B-1 inside
+// the block from the right environment of its own index bits and leaves E_B in
+// the block's first chunk vector; stage 2 (one block per job) runs levels B..K-1
+// over those.  Each (vector, layer) term is formed in FP32 and summed in FP64 in
+// a fixed order; the sums go to the same partial slots k_mps_ghigh fills.
+constexpr int GT_NT = 256;
+constexpr int GT_BLOCK_BITS = 8;  // stage 1: 2^8 chunks per block, one block per partial slot
+constexpr int GT_VMAX = 512;      // vectors per block (2^9: stage 2 at n = 30)
 template <int D>
-__global__ void __launch_bounds__(256) k_mps_ghigh(const PassArgs A) {
+__global__ void __launch_bounds__(GT_NT) k_mps_gtree(const PassArgs A, int t0, int L, int sh) {
   constexpr int DD = D * D;
-  constexpr int ML = DD + 4;  // per-matrix stride: a warp's two matrices (y = 0, 1) on distinct banks
   constexpr int RMAX = 4;
-  __shared__ float sA[17 * 2 * ML];
-  __shared__ float sdA[(RMAX + 1) * 2 * ML];
-  __shared__ double red[8][RMAX + 1];
   const int r = (D == 2) ? 1 : (D == 4 ? 2 : (D == 8 ? 3 : 4));
-  const int n = A.n, K = n - MPS_CHUNK_BITS, q = MPS_CHUNK_BITS + blockIdx.y, job = blockIdx.z;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int n = A.n, K = n - MPS_CHUNK_BITS, job = blockIdx.y, tid = threadIdx.x;
+  const long long blk = blockIdx.x;
+  const int NV = 1 << L;
   const MpsDims d = mps_dims(n, r);
   const MpsGradRegions gr = mps_grad_regions(n, r);
   const float *tab = reinterpret_cast<const float *>(A.in) + (size_t)job * A.in_stride;
-  const float *lall = reinterpret_cast<const float *>(A.lam_in) + (size_t)job * A.lam_stride;
+  // the chunk vectors sit in this step's partial region (writable): stage 1 leaves each
+  // block's E_B there for stage 2
+  float *lall = const_cast<float *>(reinterpret_cast<const float *>(A.lam_in)) + (size_t)job * A.lam_stride;
   double *part = A.part + (size_t)job * A.part_stride;
-  for (int i = tid; i < K * 2 * DD; i += 256) sA[(i / DD) * ML + i % DD] = tab[d.sites + (long long)MPS_CHUNK_BITS * 2 * DD + i];
-  for (int i = tid; i < (r + 1) * 2 * DD; i += 256) {
-    const int k = i / (2 * DD), e = i % (2 * DD);
-    sdA[(i / DD) * ML + i % DD] = tab[d.dsites + ((long long)k * n + q) * 2 * DD + e];
+  extern __shared__ __align__(16) float gdyn[];
+  float *sA = gdyn;                   // A_{13+t}[y] for t < K: [K][2][DD]
+  float *sE = sA + K * 2 * DD;        // E ping-pong: [2][GT_VMAX][D]
+  float *sR = sE + 2 * GT_VMAX * D;   // R of every level of this block: [GT_VMAX][D] (offset 2^(L-1-lt) - 1 ...)
+  float *sd = sR + GT_VMAX * D;       // dA^k_q[y]: [RMAX + 1][2][DD]
+  double *sv = reinterpret_cast<double *>(sd + (RMAX + 1) * 2 * DD);  // terms [RMAX + 1][GT_VMAX / 2]
+  __shared__ float sRt[D];
+  __shared__ double sg[RMAX + 1];
+  for (int i = tid; i < K * 2 * DD; i += GT_NT) sA[i] = tab[d.sites + (long long)MPS_CHUNK_BITS * 2 * DD + i];
+  for (int i = tid; i < NV * D; i += GT_NT) {
+    const int v = i / D, a = i % D;
+    sE[i] = lall[(((blk << L) + v) << sh) * D + a];
   }
   __syncthreads();
-  const long long c = (long long)blockIdx.x * 256 + tid;
-  float val[RMAX + 1] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  if (c < A.tiles) {
-    float u[D], sv[D];
+  // the right environment of the bits above this block: levels t0 + L .. K - 1
+  if (tid < 32) {
+    float x = (tid < D) ? 1.f : 0.f;
+    for (int t = K - 1; t >= t0 + L; --t) {
+      const int y = (int)((blk >> (t - t0 - L)) & 1);
+      const float *M = sA + (t * 2 + y) * DD;
+      float acc = 0.f;
+      if (tid < D) {
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      u[a] = lall[c * D + a];
-      sv[a] = 1.f;
-    }
-    for (int j = MPS_CHUNK_BITS; j < q; ++j) {
-      const float *M = sA + ((j - MPS_CHUNK_BITS) * 2 + (int)((c >> (j - MPS_CHUNK_BITS)) & 1)) * ML;
-      float t[D];
+        for (int b = 0; b < D; ++b) acc = fmaf(M[tid * D + b], __shfl_sync(0xffffffffu, x, b), acc);
+      } else {
 #pragma unroll
-      for (int b = 0; b < D; ++b) {
-        float acc = 0.f;
-#pragma unroll
-        for (int a = 0; a < D; ++a) acc = fmaf(u[a], M[a * D + b], acc);
-        t[b] = acc;
+        for (int b = 0; b < D; ++b) (void)__shfl_sync(0xffffffffu, x, b);
       }
-#pragma unroll
-      for (int b = 0; b < D; ++b) u[b] = t[b];
+      x = acc;
     }
-    for (int j = n - 1; j > q; --j) {
-      const float *M = sA + ((j - MPS_CHUNK_BITS) * 2 + (int)((c >> (j - MPS_CHUNK_BITS)) & 1)) * ML;
-      float t[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        float acc = 0.f;
-#pragma unroll
-        for (int b = 0; b < D; ++b) acc = fmaf(M[a * D + b], sv[b], acc);
-        t[a] = acc;
-      }
-#pragma unroll
-      for (int a = 0; a < D; ++a) sv[a] = t[a];
-    }
-    const int yq = (int)((c >> (q - MPS_CHUNK_BITS)) & 1);
-    for (int k = 0; k <= r; ++k) {
-      const float *M = sdA + (k * 2 + yq) * ML;
+    if (tid < D) sRt[tid] = x;
+  }
+  __syncthreads();
+  // R of level lt (local) holds 2^(L-1-lt) vectors at sR + (2^(L-1-lt) - 1) D: level L-1 is
+  // R_top, level lt from level lt + 1 through A_{14+t0+lt}
+  if (tid < D) sR[tid] = sRt[tid];
+  __syncthreads();
+  for (int lt = L - 2; lt >= 0; --lt) {
+    const int cnt = 1 << (L - 1 - lt), t = t0 + lt;
+    float *dst = sR + (cnt - 1) * D;
+    const float *src = sR + (cnt / 2 - 1) * D;
+    for (int i = tid; i < cnt * D; i += GT_NT) {
+      const int jp = i / D, a = i % D;
+      const float *M = sA + ((t + 1) * 2 + (jp & 1)) * DD;
+      const float *s = src + (jp >> 1) * D;
       float acc = 0.f;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        float ra = 0.f;
-#pragma unroll
-        for (int b = 0; b < D; ++b) ra = fmaf(M[a * D + b], sv[b], ra);
-        acc = fmaf(u[a], ra, acc);
-      }
-      val[k] = acc;
+      for (int b = 0; b < D; ++b) acc = fmaf(M[a * D + b], s[b], acc);
+      dst[i] = acc;
     }
+    __syncthreads();
   }
+  int cur = 0;
+  for (int lt = 0; lt < L; ++lt) {
+    const int t = t0 + lt, q = MPS_CHUNK_BITS + t, nv = 1 << (L - lt);
+    for (int i = tid; i < (r + 1) * 2 * DD; i += GT_NT) {
+      const int k = i / (2 * DD), e = i % (2 * DD);
+      sd[i] = tab[d.dsites + ((long long)k * n + q) * 2 * DD + e];
+    }
+    __syncthreads();
+    const float *E = sE + cur * GT_VMAX * D;
+    const float *R = sR + (nv / 2 - 1) * D;
+    // term (k, j) = E(j) dA^k[j & 1] R(j >> 1); pairs of vectors j = 2 i, 2 i + 1 share R
+    for (int i = tid; i < (r + 1) * (nv / 2); i += GT_NT) {
+      const int k = i / (nv / 2), jj = i % (nv / 2);
+      const float *Rv = R + jj * D;
+      double tsum = 0.0;
 #pragma unroll
-  for (int k = 0; k <= RMAX; ++k) {
-    float x = val[k];
+      for (int y = 0; y < 2; ++y) {
+        const float *M = sd + (k * 2 + y) * DD;
+        const float *Ev = E + (2 * jj + y) * D;
+        float acc = 0.f;
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    if (lane == 0) red[w][k] = (double)x;
+        for (int a = 0; a < D; ++a) {
+          float ra = 0.f;
+#pragma unroll
+          for (int b = 0; b < D; ++b) ra = fmaf(M[a * D + b], Rv[b], ra);
+          acc = fmaf(Ev[a], ra, acc);
+        }
+        tsum += (double)acc;
+      }
+      sv[k * (GT_VMAX / 2) + jj] = tsum;
+    }
+    // E of the next level
+    float *En = sE + (cur ^ 1) * GT_VMAX * D;
+    for (int i = tid; i < (nv / 2) * D; i += GT_NT) {
+      const int j = i / D, b = i % D;
+      const float *M0 = sA + (t * 2) * DD, *M1 = M0 + DD;
+      const float *E0 = E + (2 * j) * D, *E1 = E0 + D;
+      float acc = 0.f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc = fmaf(E1[a], M1[a * D + b], fmaf(E0[a], M0[a * D + b], acc));
+      En[i] = acc;
+    }
+    __syncthreads();
+    if (tid <= r) {
+      double s = 0.0;
+      for (int jj = 0; jj < nv / 2; ++jj) s += sv[tid * (GT_VMAX / 2) + jj];
+      sg[tid] = s;
+    }
+    __syncthreads();
+    if (tid <= r) part[gr.part3 + ((long long)t * (r + 1) + tid) * gr.nb3 + (t0 == 0 ? blk : 0)] = sg[tid];
+    cur ^= 1;
   }
-  __syncthreads();
-  if (tid <= r) {
-    double t = 0.0;
-#pragma unroll
-    for (int ww = 0; ww < 8; ++ww) t += red[ww][tid];
-    part[gr.part3 + ((long long)(q - MPS_CHUNK_BITS) * (r + 1) + tid) * gr.nb3 + blockIdx.x] = t;
+  if (t0 == 0) {
+    // E_L of this block into its first chunk vector (all of the block's reads are done);
+    // the levels above this stage start at zero in this block's slot, and slots no
+    // block of this stage owns are zero
+    if (tid < D) lall[((blk << L) << sh) * D + tid] = sE[cur * GT_VMAX * D + tid];
+    for (int i = tid; i < (K - L) * (r + 1); i += GT_NT)
+      part[gr.part3 + ((long long)(L + i / (r + 1)) * (r + 1) + i % (r + 1)) * gr.nb3 + blk] = 0.0;
+    for (long long s = blk + gridDim.x; s < gr.nb3; s += gridDim.x)
+      for (int i = tid; i < K * (r + 1); i += GT_NT) part[gr.part3 + (long long)i * gr.nb3 + s] = 0.0;
   }
 }
 
 // Fixed-order FP64 sums: value v < v1 over the CTAs of k_mps_grad, the rest
-// (high qubit, layer) over the blocks of k_mps_ghigh.
+// (high qubit, layer) over the slots of k_mps_gtree.
 __global__ void __launch_bounds__(128) k_mps_gred(const PassArgs A) {
   const int r = A.layer, job = blockIdx.y;
   const MpsGradRegions gr = mps_grad_regions(A.n, r);
@@ -1767,9 +1827,15 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
       }
       break;
     }
-    case K_MPS_GHIGH:
-      k_mps_ghigh<D><<<dim3((unsigned)gr.nb3, (unsigned)gr.k, (unsigned)jobs), 256, 0, s>>>(A);
+    case K_MPS_GHIGH: {
+      const int K = A.n - MPS_CHUNK_BITS, B = K < GT_BLOCK_BITS ? K : GT_BLOCK_BITS;
+      const size_t smem = (size_t)(K * 2 * D * D + 3 * GT_VMAX * D + 10 * D * D) * sizeof(float) +
+                          (size_t)5 * (GT_VMAX / 2) * sizeof(double);
+      cudaFuncSetAttribute(k_mps_gtree<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_mps_gtree<D><<<dim3((unsigned)(1LL << (K - B)), (unsigned)jobs), GT_NT, smem, s>>>(A, 0, B, 0);
+      if (K > B) k_mps_gtree<D><<<dim3(1, (unsigned)jobs), GT_NT, smem, s>>>(A, B, K - B, B);
       break;
+    }
     case K_MPS_GRED:
       k_mps_gred<<<dim3((unsigned)((gr.v1 + gr.k * (A.layer + 1) + 127) / 128), (unsigned)jobs), 128, 0, s>>>(A);
       break;
@@ -1818,6 +1884,11 @@ cudaError_t launch_mps_d(const PassArgs &A, int jobs, cudaStream_t s) {
 }
 
 }  // namespace
+
+int mps_step_kernels(const PassArgs &A) {
+  if (A.kind == K_MPS_GHIGH) return (A.n - MPS_CHUNK_BITS > GT_BLOCK_BITS) ? 2 : 1;
+  return 1;
+}
 
 cudaError_t launch_mps(int prec, const PassArgs &A, int jobs, cudaStream_t s) {
   if (prec != 0 || A.n < MPS_MIN_QUBITS || A.n > 30 || A.layer < 1 || A.layer > MPS_MAX_LAYERS ||
