@@ -1562,7 +1562,7 @@ __global__ void __launch_bounds__(WT_NT, 1) k_mps_write16tc(const PassArgs A) {
 // a fixed order; the sums go to the same partial slots k_mps_ghigh fills.
 constexpr int GT_NT = 256;
 constexpr int GT_BLOCK_BITS = 8;  // stage 1: 2^8 chunks per block, one block per partial slot
-constexpr int GT_VMAX = 512;      // vectors per block (2^9: stage 2 at n = 30)
+// (stage 2 takes the other n - 21 <= 9 levels: at most 2^9 vectors, 150 KB at D = 16)
 template <int D>
 __global__ void __launch_bounds__(GT_NT) k_mps_gtree(const PassArgs A, int t0, int L, int sh) {
   constexpr int DD = D * D;
@@ -1579,11 +1579,12 @@ __global__ void __launch_bounds__(GT_NT) k_mps_gtree(const PassArgs A, int t0, i
   float *lall = const_cast<float *>(reinterpret_cast<const float *>(A.lam_in)) + (size_t)job * A.lam_stride;
   double *part = A.part + (size_t)job * A.part_stride;
   extern __shared__ __align__(16) float gdyn[];
-  float *sA = gdyn;                   // A_{13+t}[y] for t < K: [K][2][DD]
-  float *sE = sA + K * 2 * DD;        // E ping-pong: [2][GT_VMAX][D]
-  float *sR = sE + 2 * GT_VMAX * D;   // R of every level of this block: [GT_VMAX][D] (offset 2^(L-1-lt) - 1 ...)
-  float *sd = sR + GT_VMAX * D;       // dA^k_q[y]: [RMAX + 1][2][DD]
-  double *sv = reinterpret_cast<double *>(sd + (RMAX + 1) * 2 * DD);  // terms [RMAX + 1][GT_VMAX / 2]
+  // shared memory sized by this stage's NV vectors (gtree_smem)
+  float *sA = gdyn;              // A_{13+t}[y] for t < K: [K][2][DD]
+  float *sE = sA + K * 2 * DD;   // E ping-pong: [2][NV][D]
+  float *sR = sE + 2 * NV * D;   // R of every level: level lt's 2^(L-1-lt) vectors from vector 2^(L-1-lt) - 1
+  float *sd = sR + NV * D;       // dA^k_q[y]: [RMAX + 1][2][DD]
+  double *sv = reinterpret_cast<double *>(sd + (RMAX + 1) * 2 * DD);  // terms [RMAX + 1][NV / 2]
   __shared__ float sRt[D];
   __shared__ double sg[RMAX + 1];
   for (int i = tid; i < K * 2 * DD; i += GT_NT) sA[i] = tab[d.sites + (long long)MPS_CHUNK_BITS * 2 * DD + i];
@@ -1638,7 +1639,7 @@ __global__ void __launch_bounds__(GT_NT) k_mps_gtree(const PassArgs A, int t0, i
       sd[i] = tab[d.dsites + ((long long)k * n + q) * 2 * DD + e];
     }
     __syncthreads();
-    const float *E = sE + cur * GT_VMAX * D;
+    const float *E = sE + cur * NV * D;
     const float *R = sR + (nv / 2 - 1) * D;
     // term (k, j) = E(j) dA^k[j & 1] R(j >> 1); pairs of vectors j = 2 i, 2 i + 1 share R
     for (int i = tid; i < (r + 1) * (nv / 2); i += GT_NT) {
@@ -1659,10 +1660,10 @@ __global__ void __launch_bounds__(GT_NT) k_mps_gtree(const PassArgs A, int t0, i
         }
         tsum += (double)acc;
       }
-      sv[k * (GT_VMAX / 2) + jj] = tsum;
+      sv[k * (NV / 2) + jj] = tsum;
     }
     // E of the next level
-    float *En = sE + (cur ^ 1) * GT_VMAX * D;
+    float *En = sE + (cur ^ 1) * NV * D;
     for (int i = tid; i < (nv / 2) * D; i += GT_NT) {
       const int j = i / D, b = i % D;
       const float *M0 = sA + (t * 2) * DD, *M1 = M0 + DD;
@@ -1675,7 +1676,7 @@ __global__ void __launch_bounds__(GT_NT) k_mps_gtree(const PassArgs A, int t0, i
     __syncthreads();
     if (tid <= r) {
       double s = 0.0;
-      for (int jj = 0; jj < nv / 2; ++jj) s += sv[tid * (GT_VMAX / 2) + jj];
+      for (int jj = 0; jj < nv / 2; ++jj) s += sv[tid * (NV / 2) + jj];
       sg[tid] = s;
     }
     __syncthreads();
@@ -1686,7 +1687,7 @@ __global__ void __launch_bounds__(GT_NT) k_mps_gtree(const PassArgs A, int t0, i
     // E_L of this block into its first chunk vector (all of the block's reads are done);
     // the levels above this stage start at zero in this block's slot, and slots no
     // block of this stage owns are zero
-    if (tid < D) lall[((blk << L) << sh) * D + tid] = sE[cur * GT_VMAX * D + tid];
+    if (tid < D) lall[((blk << L) << sh) * D + tid] = sE[cur * NV * D + tid];
     for (int i = tid; i < (K - L) * (r + 1); i += GT_NT)
       part[gr.part3 + ((long long)(L + i / (r + 1)) * (r + 1) + i % (r + 1)) * gr.nb3 + blk] = 0.0;
     for (long long s = blk + gridDim.x; s < gr.nb3; s += gridDim.x)
@@ -1829,11 +1830,15 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
     }
     case K_MPS_GHIGH: {
       const int K = A.n - MPS_CHUNK_BITS, B = K < GT_BLOCK_BITS ? K : GT_BLOCK_BITS;
-      const size_t smem = (size_t)(K * 2 * D * D + 3 * GT_VMAX * D + 10 * D * D) * sizeof(float) +
-                          (size_t)5 * (GT_VMAX / 2) * sizeof(double);
-      cudaFuncSetAttribute(k_mps_gtree<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_mps_gtree<D><<<dim3((unsigned)(1LL << (K - B)), (unsigned)jobs), GT_NT, smem, s>>>(A, 0, B, 0);
-      if (K > B) k_mps_gtree<D><<<dim3(1, (unsigned)jobs), GT_NT, smem, s>>>(A, B, K - B, B);
+      // shared memory of a stage with NV = 2^L vectors
+      auto gtree_smem = [&](int L) {
+        const size_t nv = (size_t)1 << L;
+        return (size_t)(K * 2 * D * D + 3 * nv * D + 10 * D * D) * sizeof(float) + 5 * (nv / 2) * sizeof(double);
+      };
+      cudaFuncSetAttribute(k_mps_gtree<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)gtree_smem(K > B ? (K - B > B ? K - B : B) : B));
+      k_mps_gtree<D><<<dim3((unsigned)(1LL << (K - B)), (unsigned)jobs), GT_NT, gtree_smem(B), s>>>(A, 0, B, 0);
+      if (K > B) k_mps_gtree<D><<<dim3(1, (unsigned)jobs), GT_NT, gtree_smem(K - B), s>>>(A, B, K - B, B);
       break;
     }
     case K_MPS_GRED:
