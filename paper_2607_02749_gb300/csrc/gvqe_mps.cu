@@ -921,8 +921,8 @@ __global__ void __launch_bounds__(G16_NT, 1) k_mps_grad16(const PassArgs A) {
 // 64 x 16 blocks add up to Lambda1; mu takes A = lambda_hi^T, then lambda_lo^T,
 // against B = [m_hi | m_lo] into a 128 x 32 accumulator, whose two column halves
 // add up to mu: 16 + 16 MMAs (M = 128, N = 32, K = 8) per chunk.  Both contractions read lambda
-// with K-major operands (the tensor cores' MN-major form came out zero for
-// TF32 on this part), so each chunk's split lambda is written twice: rows ym
+// with K-major operands (the MN-major operand form gave zeros for TF32 on
+// sm_103a), so each chunk's split lambda is written twice: rows ym
 // with runs of yl for Lambda1, rows yl with runs of ym for mu.  Operand
 // layout: no swizzle, core matrices of 8 rows x 16 bytes; LBO steps along K,
 // SBO along the rows.  The K strides are padded (144 bytes between the
