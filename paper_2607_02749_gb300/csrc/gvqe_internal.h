@@ -90,7 +90,7 @@ Plan build_plan(int n, int reps, int prec, int tile_bits, bool want_grad, bool d
 // layer (which carries the energy epilogue); `want` is GVQE_OPT_MPS_LAYERS
 // (0 = up to MPS_AUTO_LAYERS, -1 = none, 1..MPS_MAX_LAYERS = at most that many).
 int mps_layers_for(int n, int reps, int prec, int ent, int gates, int want);
-// Kernels one closed-form step launches (the high-qubit gradient tree takes two above n = 21).
+// Kernels one closed-form step launches (the high-qubit gradient tree, from n = 28, takes two).
 int mps_step_kernels(const PassArgs &A);
 std::string describe_plan(const Plan &pl);
 // One tile-pass launch, counted by gvqe_launch_count and timed by the event

@@ -1544,6 +1544,99 @@ __global__ void __launch_bounds__(WT_NT, 1) k_mps_write16tc(const PassArgs A) {
   if (w == 0 && done) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
+// High qubits, per (chunk, qubit): block (x, q - 13) takes chunks 256 x .. 256 x + 255
+// and qubit q.  Thread c forms u = l_c A_13 .. A_{q-1} and s = A_{q+1} .. A_{n-1} 1
+// and adds u dA_q^k s for every layer k <= r; the block's FP64 sums go to its
+// partials.  Up to n = 27 (K <= GT_MIN_LEVELS - 1 chunk bits) this is faster than the
+// tree below, whose cost is a fixed time per level (measured at n = 27: 82 us
+// against 109; at n = 30 the tree takes 0.28 ms against 0.77).
+template <int D>
+__global__ void __launch_bounds__(256) k_mps_ghigh(const PassArgs A) {
+  constexpr int DD = D * D;
+  constexpr int ML = DD + 4;  // per-matrix stride: a warp's two matrices (y = 0, 1) on distinct banks
+  constexpr int RMAX = 4;
+  __shared__ float sA[17 * 2 * ML];
+  __shared__ float sdA[(RMAX + 1) * 2 * ML];
+  __shared__ double red[8][RMAX + 1];
+  const int r = (D == 2) ? 1 : (D == 4 ? 2 : (D == 8 ? 3 : 4));
+  const int n = A.n, K = n - MPS_CHUNK_BITS, q = MPS_CHUNK_BITS + blockIdx.y, job = blockIdx.z;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const MpsDims d = mps_dims(n, r);
+  const MpsGradRegions gr = mps_grad_regions(n, r);
+  const float *tab = reinterpret_cast<const float *>(A.in) + (size_t)job * A.in_stride;
+  const float *lall = reinterpret_cast<const float *>(A.lam_in) + (size_t)job * A.lam_stride;
+  double *part = A.part + (size_t)job * A.part_stride;
+  for (int i = tid; i < K * 2 * DD; i += 256) sA[(i / DD) * ML + i % DD] = tab[d.sites + (long long)MPS_CHUNK_BITS * 2 * DD + i];
+  for (int i = tid; i < (r + 1) * 2 * DD; i += 256) {
+    const int k = i / (2 * DD), e = i % (2 * DD);
+    sdA[(i / DD) * ML + i % DD] = tab[d.dsites + ((long long)k * n + q) * 2 * DD + e];
+  }
+  __syncthreads();
+  const long long c = (long long)blockIdx.x * 256 + tid;
+  float val[RMAX + 1] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  if (c < A.tiles) {
+    float u[D], sv[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      u[a] = lall[c * D + a];
+      sv[a] = 1.f;
+    }
+    for (int j = MPS_CHUNK_BITS; j < q; ++j) {
+      const float *M = sA + ((j - MPS_CHUNK_BITS) * 2 + (int)((c >> (j - MPS_CHUNK_BITS)) & 1)) * ML;
+      float t[D];
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc = fmaf(u[a], M[a * D + b], acc);
+        t[b] = acc;
+      }
+#pragma unroll
+      for (int b = 0; b < D; ++b) u[b] = t[b];
+    }
+    for (int j = n - 1; j > q; --j) {
+      const float *M = sA + ((j - MPS_CHUNK_BITS) * 2 + (int)((c >> (j - MPS_CHUNK_BITS)) & 1)) * ML;
+      float t[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) acc = fmaf(M[a * D + b], sv[b], acc);
+        t[a] = acc;
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) sv[a] = t[a];
+    }
+    const int yq = (int)((c >> (q - MPS_CHUNK_BITS)) & 1);
+    for (int k = 0; k <= r; ++k) {
+      const float *M = sdA + (k * 2 + yq) * ML;
+      float acc = 0.f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float ra = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) ra = fmaf(M[a * D + b], sv[b], ra);
+        acc = fmaf(u[a], ra, acc);
+      }
+      val[k] = acc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k <= RMAX; ++k) {
+    float x = val[k];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) red[w][k] = (double)x;
+  }
+  __syncthreads();
+  if (tid <= r) {
+    double t = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) t += red[ww][tid];
+    part[gr.part3 + ((long long)(q - MPS_CHUNK_BITS) * (r + 1) + tid) * gr.nb3 + blockIdx.x] = t;
+  }
+}
+
 // High qubits by a tree over the chunk index bits (level t <-> qubit 13 + t,
 // K = n - 13 levels).  With E_t(j) the left environment of the chunks c with
 // c >> t == j (l_c A_13 .. A_{12+t}, summed over the low t bits) and R_t(j')
@@ -1562,6 +1655,7 @@ __global__ void __launch_bounds__(WT_NT, 1) k_mps_write16tc(const PassArgs A) {
 // a fixed order; the sums go to the same partial slots k_mps_ghigh fills.
 constexpr int GT_NT = 256;
 constexpr int GT_BLOCK_BITS = 8;  // stage 1: 2^8 chunks per block, one block per partial slot
+constexpr int GT_MIN_LEVELS = 15; // the tree from n = 28 (15 chunk bits); per (chunk, qubit) below
 // (stage 2 takes the other n - 21 <= 9 levels: at most 2^9 vectors, 150 KB at D = 16)
 template <int D>
 __global__ void __launch_bounds__(GT_NT) k_mps_gtree(const PassArgs A, int t0, int L, int sh) {
@@ -1696,7 +1790,7 @@ __global__ void __launch_bounds__(GT_NT) k_mps_gtree(const PassArgs A, int t0, i
 }
 
 // Fixed-order FP64 sums: value v < v1 over the CTAs of k_mps_grad, the rest
-// (high qubit, layer) over the slots of k_mps_gtree.
+// (high qubit, layer) over the slots of k_mps_ghigh or k_mps_gtree.
 __global__ void __launch_bounds__(128) k_mps_gred(const PassArgs A) {
   const int r = A.layer, job = blockIdx.y;
   const MpsGradRegions gr = mps_grad_regions(A.n, r);
@@ -1830,6 +1924,10 @@ cudaError_t launch_mps_grad_d(const PassArgs &A, int jobs, cudaStream_t s) {
     }
     case K_MPS_GHIGH: {
       const int K = A.n - MPS_CHUNK_BITS, B = K < GT_BLOCK_BITS ? K : GT_BLOCK_BITS;
+      if (K < GT_MIN_LEVELS) {
+        k_mps_ghigh<D><<<dim3((unsigned)gr.nb3, (unsigned)gr.k, (unsigned)jobs), 256, 0, s>>>(A);
+        break;
+      }
       // shared memory of a stage with NV = 2^L vectors
       auto gtree_smem = [&](int L) {
         const size_t nv = (size_t)1 << L;
@@ -1891,7 +1989,7 @@ cudaError_t launch_mps_d(const PassArgs &A, int jobs, cudaStream_t s) {
 }  // namespace
 
 int mps_step_kernels(const PassArgs &A) {
-  if (A.kind == K_MPS_GHIGH) return (A.n - MPS_CHUNK_BITS > GT_BLOCK_BITS) ? 2 : 1;
+  if (A.kind == K_MPS_GHIGH) return (A.n - MPS_CHUNK_BITS >= GT_MIN_LEVELS) ? 2 : 1;
   return 1;
 }
 
